@@ -1,0 +1,380 @@
+"""Pins of the CPU oracle against facts fixed by the paper and by mathematics.
+
+Each test checks the oracle against something other than itself: closed
+forms (Section 4.3), textbook perturbation theory (App. B), the paper's
+printed 3x3 multiplier polynomials (App. D.3, fixture in tests/golden/),
+LAPACK and a brute-force Jacobi eigensolver, the convergence theorem of
+Section 4.1, and invariants of the map.  Chosen so that a dropped term, a
+wrong sign or index of G, or a transposed operand fails at least one.
+"""
+
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2012_14702_gb300 import workloads as w
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------- helpers
+def jacobi_eigh(A, tol=1e-15, max_sweeps=50):
+    """Cyclic Jacobi eigensolver for a symmetric matrix (textbook brute force)."""
+    A = np.array(A, dtype=np.float64, copy=True)
+    n = len(A)
+    V = np.eye(n)
+    for _ in range(max_sweeps):
+        off = np.linalg.norm(A - np.diag(np.diag(A)))
+        if off <= tol * np.linalg.norm(A):
+            break
+        for p in range(n - 1):
+            for q in range(p + 1, n):
+                if A[p, q] == 0.0:
+                    continue
+                th = (A[q, q] - A[p, p]) / (2.0 * A[p, q])
+                t = np.sign(th) / (abs(th) + np.sqrt(th * th + 1.0)) if th != 0 else 1.0
+                c = 1.0 / np.sqrt(t * t + 1.0)
+                s = t * c
+                cp, cq = A[:, p].copy(), A[:, q].copy()
+                A[:, p], A[:, q] = c * cp - s * cq, s * cp + c * cq
+                rp, rq = A[p, :].copy(), A[q, :].copy()
+                A[p, :], A[q, :] = c * rp - s * rq, s * rp + c * rq
+                vp, vq = V[:, p].copy(), V[:, q].copy()
+                V[:, p], V[:, q] = c * vp - s * vq, s * vp + c * vq
+    return np.diag(A).copy(), V
+
+
+def match_eigvecs(V, cols):
+    """For each requested index i_c, the eigenvector with the largest |V[i_c, :]|, scaled so z_{i_c} = 1."""
+    Z = np.zeros((V.shape[0], len(cols)), dtype=V.dtype)
+    idx = []
+    for c, i in enumerate(cols):
+        j = int(np.argmax(np.abs(V[i, :])))
+        idx.append(j)
+        Z[:, c] = V[:, j] / V[i, j]
+    return Z, np.array(idx)
+
+
+def load_polys():
+    terms = {}
+    with open(os.path.join(GOLDEN, "app_d3_multiplier_polynomials.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            z, c, a, b = line.split()
+            terms.setdefault(z, []).append((int(c), int(a), int(b)))
+    return terms
+
+
+# ---------------------------------------------------------------- 2 x 2 closed form (Section 4.3)
+@pytest.mark.parametrize("eps", [0.1, 0.3, 0.6, -0.45])
+def test_2x2_iterates_match_closed_form(eps):
+    """Z^(k) = [[1, -f^k(0)], [f^k(0), 1]] with f(x) = eps (x^2 - 1), Eq. (2by2)."""
+    M, th = w.two_by_two(eps)
+    Delta, th = oracle.partition(M, th)
+    cols = np.arange(2)
+    Z = np.eye(2)
+    x = 0.0
+    for _ in range(12):
+        Z, _, _ = oracle.ipt_map(Delta, th, cols, Z)
+        x = eps * (x * x - 1.0)
+        np.testing.assert_allclose(Z, [[1.0, -x], [x, 1.0]], rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("eps", [0.05, 0.3, 0.7, -0.8])
+def test_2x2_eigenvalues_closed_form(eps):
+    """Column 0 converges to lambda_- and column 1 to lambda_+ = (1 +- sqrt(1+4 eps^2))/2."""
+    M, th = w.two_by_two(eps)
+    r = oracle.ipt_solve(M, th, tol=1e-14, max_iter=5000)
+    assert r["status"] == oracle.OK
+    s = np.sqrt(1.0 + 4.0 * eps * eps)
+    np.testing.assert_allclose(r["lam"], [(1 - s) / 2, (1 + s) / 2], rtol=0, atol=1e-12)
+
+
+def test_2x2_flip_bifurcation():
+    """Stable below |eps| = sqrt(3)/2, a 2-cycle above it; diverges far outside (Section 4.3)."""
+    for eps, status in [(0.85, oracle.OK), (-0.85, oracle.OK), (0.87, oracle.MAXITER),
+                        (-0.87, oracle.MAXITER), (3.0, oracle.DIVERGED)]:
+        M, th = w.two_by_two(eps)
+        r = oracle.ipt_solve(M, th, tol=1e-12, max_iter=4000)
+        assert r["status"] == status, (eps, r["status"])
+    # the 2-cycle: two successive iterates alternate
+    M, th = w.two_by_two(0.87)
+    Delta, th = oracle.partition(M, th)
+    Z = np.eye(2)
+    for _ in range(4000):
+        Z, _, _ = oracle.ipt_map(Delta, th, np.arange(2), Z)
+    Z1, _, _ = oracle.ipt_map(Delta, th, np.arange(2), Z)
+    Z2, _, _ = oracle.ipt_map(Delta, th, np.arange(2), Z1)
+    assert abs(Z1[1, 0] - Z[1, 0]) > 1e-2 and abs(Z2[1, 0] - Z[1, 0]) < 1e-8
+
+
+# ---------------------------------------------------------------- 3 x 3 example (App. D.3)
+@pytest.mark.parametrize("eps", [0.1, 0.3, -0.2])
+@pytest.mark.parametrize("col", [0, 1, 2])
+def test_3x3_multipliers_are_roots_of_printed_polynomials(eps, col):
+    """The multipliers of the converged fixed point of f_i are zeros of the printed P(eps, mu)."""
+    terms = load_polys()["z%d" % (col + 1)]
+    M, th = w.three_by_three(eps)
+    Delta, th = oracle.partition(M, th)
+    r = oracle.ipt_solve(M, th, cols=[col], tol=1e-15, max_iter=5000)
+    assert r["status"] == oracle.OK
+    J = oracle.chart_jacobian(Delta, th, col, r["Z"][:, 0])
+    for mu in np.linalg.eigvals(J):
+        vals = [c * eps ** a * mu ** b for c, a, b in terms]
+        assert abs(sum(vals)) <= 1e-12 * sum(abs(v) for v in vals)
+    # the converged point is an eigenvector of M (intermediate normalisation)
+    lam = r["lam"][0]
+    z = r["Z"][:, 0]
+    assert np.linalg.norm(M @ z - lam * z) < 1e-12
+
+
+def test_3x3_z2_loses_stability_near_minus_049():
+    """App. D.3: the z_2 fixed point continued from eps = 0 loses stability at eps ~ -0.49
+    through a complex-conjugate pair of multipliers (Neimark-Sacker)."""
+    def multipliers(eps):
+        M, th = w.three_by_three(eps)
+        Delta, _ = oracle.partition(M, th)
+        ev, V = np.linalg.eig(M)
+        j = int(np.argmax(np.abs(V[1, :])))
+        z = (V[:, j] / V[1, j]).real
+        return np.linalg.eigvals(oracle.chart_jacobian(Delta, th, 1, z))
+    assert max(abs(multipliers(-0.45))) < 1.0
+    assert max(abs(multipliers(-0.48))) < 1.0
+    mu = multipliers(-0.50)
+    assert max(abs(mu)) > 1.0
+    assert abs(mu[0].imag) > 1e-3 and abs(mu[0] - np.conj(mu[1])) < 1e-12
+
+
+# ---------------------------------------------------------------- textbook perturbation theory
+def test_first_iterate_is_first_order_rs():
+    """F(I) = I - G o Delta: the first-order RS eigenvector correction
+    z_j = Delta_ji / (theta_i - theta_j); the second evaluation's eigenvalue is
+    the second-order RS energy theta_i + Delta_ii + sum_j Delta_ij Delta_ji / (theta_i - theta_j)."""
+    g = w.rng(5)
+    n = 9
+    th = np.sort(g.random(n) * 10)
+    Delta = g.standard_normal((n, n)) * 0.05  # non-symmetric, non-zero diagonal
+    M = np.diag(th) + Delta
+    cols = np.arange(n)
+    F, _, d = oracle.ipt_map(Delta, th, cols, np.eye(n))
+    for i in range(n):
+        for j in range(n):
+            want = 1.0 if i == j else Delta[j, i] / (th[i] - th[j])
+            assert abs(F[j, i] - want) < 1e-15
+        assert abs(th[i] + d[i] - (th[i] + Delta[i, i])) < 1e-15  # first-order energy
+    r = oracle.ipt_solve(M, th, tol=0.0, max_iter=2)
+    assert r["status"] == oracle.MAXITER and r["iterations"] == 2
+    for i in range(n):
+        e2 = th[i] + Delta[i, i] + sum(Delta[i, j] * Delta[j, i] / (th[i] - th[j])
+                                       for j in range(n) if j != i)
+        assert abs(r["lam"][i] - e2) < 1e-13
+
+
+def test_rs_corrections_sum_to_lapack_eigenvalues():
+    """Eigenvalue corrections lambda^[l] = D(Delta Z^[l-1]) of App. B sum to the exact
+    eigenvalues with an O(eps^(K+1)) remainder."""
+    g = w.rng(7)
+    n = 6
+    th = np.arange(n, dtype=float)
+    D0 = g.standard_normal((n, n))
+    D0 = D0 + D0.T
+    np.fill_diagonal(D0, 0.0)
+    K = 4
+    Zs = oracle.rs_corrections(D0, th, K)
+    errs = []
+    for eps in [0.02, 0.01]:
+        lam = th.copy()
+        for l in range(1, K + 1):
+            lam = lam + eps ** l * np.diag(D0 @ Zs[l - 1])
+        exact = np.linalg.eigvalsh(np.diag(th) + eps * D0)
+        errs.append(np.max(np.abs(np.sort(lam) - exact)))
+    slope = np.log2(errs[0] / errs[1])
+    assert K + 0.6 < slope < K + 1.6, slope
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 4])
+def test_ipt_contains_rs_series(k):
+    """Z^(k) = sum_{l<=k} eps^l Z^[l] + O(eps^(k+1)) (Section 4.2, App. C).
+
+    For k = 1 both sides are I - eps G o Delta exactly."""
+    g = w.rng(11)
+    n = 7
+    th = np.arange(n, dtype=float) * 1.3
+    D0 = g.standard_normal((n, n))  # non-symmetric on purpose
+    np.fill_diagonal(D0, 0.0)
+    Zs = oracle.rs_corrections(D0, th, k)
+    errs = []
+    for eps in [0.01, 0.005, 0.0025]:
+        Delta = eps * D0
+        Z = np.eye(n)
+        for _ in range(k):
+            Z, _, _ = oracle.ipt_map(Delta, th, np.arange(n), Z)
+        rs = sum(eps ** l * Zs[l] for l in range(k + 1))
+        errs.append(np.max(np.abs(Z - rs)))
+    if k == 1:
+        assert max(errs) < 1e-16
+        return
+    s1, s2 = np.log2(errs[0] / errs[1]), np.log2(errs[1] / errs[2])
+    assert k + 0.7 < s1 < k + 1.3 and k + 0.7 < s2 < k + 1.3, (s1, s2)
+
+
+# ---------------------------------------------------------------- fixed points vs eigensolvers
+@pytest.mark.parametrize("n", [8, 24, 64])
+def test_fixed_point_matches_jacobi_bruteforce(n):
+    M, th = w.dense_symmetric(n, 0.02, seed=100 + n)
+    r = oracle.ipt_solve(M, th, tol=1e-14, max_iter=500)
+    assert r["status"] == oracle.OK
+    ev, V = jacobi_eigh(M)
+    Zj, idx = match_eigvecs(V, np.arange(n))
+    assert len(set(idx.tolist())) == n
+    np.testing.assert_allclose(r["lam"], ev[idx], rtol=1e-13, atol=0)
+    np.testing.assert_allclose(r["Z"], Zj, rtol=0, atol=1e-11)
+
+
+def test_jacobi_helper_agrees_with_lapack():
+    M, _ = w.dense_symmetric(20, 0.3, seed=3)
+    ev, V = jacobi_eigh(M)
+    np.testing.assert_allclose(np.sort(ev), np.linalg.eigvalsh(M), atol=1e-12)
+    np.testing.assert_allclose(V.T @ V, np.eye(20), atol=1e-12)
+
+
+def test_nonsymmetric_paper_family_matches_lapack_eig():
+    """Eq. (dense_matrix) with eps = 1e-2 (non-symmetric, U[0,1] entries): IPT = eig."""
+    M, th = w.dense_paper(120, 1e-2, seed=9)
+    r = oracle.ipt_solve(M, th, tol=1e-13, max_iter=500)
+    assert r["status"] == oracle.OK
+    ev, V = np.linalg.eig(M)
+    Zl, idx = match_eigvecs(V, np.arange(120))
+    assert np.max(np.abs(ev.imag)) < 1e-12
+    np.testing.assert_allclose(r["lam"], ev[idx].real, rtol=1e-12)
+    np.testing.assert_allclose(r["Z"], Zl.real, atol=1e-10)
+
+
+def test_partial_spectrum_with_permuted_columns():
+    """Columns are independent (Alg. 1 per column): any column subset, any order."""
+    M, th = w.dense_symmetric(40, 0.03, seed=4)
+    cols = np.array([17, 3, 29, 0])
+    r = oracle.ipt_solve(M, th, cols=cols, tol=1e-14, max_iter=500)
+    assert r["status"] == oracle.OK
+    ev, V = np.linalg.eigh(M)
+    Zl, idx = match_eigvecs(V, cols)
+    np.testing.assert_allclose(r["lam"], ev[idx], rtol=1e-13)
+    np.testing.assert_allclose(r["Z"], Zl, atol=1e-11)
+    full = oracle.ipt_solve(M, th, tol=1e-14, max_iter=500)
+    np.testing.assert_allclose(r["Z"], full["Z"][:, cols], atol=1e-12)
+
+
+# ---------------------------------------------------------------- convergence theorem (Section 4.1)
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_theorem_condition_implies_convergence_in_ball(seed):
+    """||G|| ||Delta|| < 3 - 2 sqrt(2): convergence from I to a full-rank Z* in B_sqrt2(I)."""
+    g = w.rng(seed)
+    n = 30
+    th = np.sort(g.random(n)) * n
+    D0 = g.standard_normal((n, n))
+    np.fill_diagonal(D0, 0.0)
+    G = oracle.inverse_gaps(th, np.arange(n))
+    scale = 0.16 / (np.linalg.norm(G, 2) * np.linalg.norm(D0, 2))
+    Delta = scale * D0
+    assert np.linalg.norm(G, 2) * np.linalg.norm(Delta, 2) < 3 - 2 * np.sqrt(2)
+    r = oracle.ipt_solve(np.diag(th) + Delta, th, tol=1e-14, max_iter=2000)
+    assert r["status"] == oracle.OK
+    Zs = r["Z"]
+    assert np.linalg.norm(Zs - np.eye(n), 2) <= np.sqrt(2)
+    assert np.linalg.svd(Zs, compute_uv=False)[-1] > 1e-3
+
+
+# ---------------------------------------------------------------- invariants and special cases
+def test_diagonal_matrix_is_fixed_at_identity():
+    th = np.array([3.0, -1.0, 2.5, 7.0])
+    r = oracle.ipt_solve(np.diag(th), th, tol=1e-12)
+    assert r["status"] == oracle.OK and r["iterations"] == 1
+    np.testing.assert_array_equal(r["Z"], np.eye(4))
+    np.testing.assert_array_equal(r["lam"], th)
+    assert r["rho"] == 0.0
+
+
+def test_intermediate_normalisation_and_residual_identity():
+    """Z_{i_c, c} = 1 on every iterate, and for any such Z:
+    (M Z - Z Lambda)_jc = (theta_j - theta_{i_c}) (Z - F(Z))_jc, j != i_c."""
+    M, th = w.dense_symmetric(30, 0.05, seed=8)
+    Delta, th = oracle.partition(M, th)
+    cols = np.array([4, 11, 20])
+    g = w.rng(8)
+    Z = g.standard_normal((30, 3)) * 0.1
+    Z[cols, np.arange(3)] = 1.0
+    F, P, d = oracle.ipt_map(Delta, th, cols, Z)
+    assert np.all(F[cols, np.arange(3)] == 1.0)
+    lam = th[cols] + d
+    R = oracle.residual(M, Z, lam)
+    ident = (th[:, None] - th[cols][None, :]) * (Z - F)
+    np.testing.assert_allclose(R, ident, atol=1e-15)
+    assert np.all(np.abs(R[cols, np.arange(3)]) < 1e-15)
+
+
+def test_rho_definition():
+    M, th = w.dense_symmetric(50, 0.01, seed=2)
+    r = oracle.ipt_solve(M, th, tol=0.0, max_iter=1)
+    assert r["iterations"] == 1 and abs(r["rho"] - 1.0) < 1e-15
+    Delta, _ = oracle.partition(M, th)
+    r = oracle.ipt_solve(M, th, tol=1e-13, max_iter=100)
+    R = oracle.residual(M, r["Z"], r["lam"])
+    off = Delta - np.diag(np.diag(Delta))
+    assert abs(r["rho"] - np.linalg.norm(R) / np.linalg.norm(off)) < 1e-12
+
+
+def test_argument_errors():
+    th = np.array([1.0, 2.0, 2.0, 4.0])
+    M = np.diag(th) + 0.01
+    assert oracle.ipt_solve(M, th)["status"] == oracle.DEGENERATE_THETA
+    assert oracle.ipt_solve(M, th, cols=[0, 3])["status"] == oracle.OK
+    assert oracle.ipt_solve(M, th, cols=[0, 0])["status"] == oracle.INVALID_ARG
+    assert oracle.ipt_solve(M, th, cols=[])["status"] == oracle.INVALID_ARG
+    assert oracle.ipt_solve(M, th, cols=[0], max_iter=0)["status"] == oracle.INVALID_ARG
+    assert oracle.ipt_solve(M, np.array([1.0, np.nan, 3, 4]), cols=[0])["status"] == oracle.DEGENERATE_THETA
+    Mn = M.copy()
+    Mn[0, 3] = np.nan
+    assert oracle.ipt_solve(Mn, th, cols=[3])["status"] == oracle.DIVERGED
+
+
+# ---------------------------------------------------------------- sparse oracle and paper workloads
+def test_csr_oracle_equals_dense_oracle():
+    rowptr, colind, vals, th = w.csr_banded(400, 4, 30, 1e-2, seed=5, theta_step=0.1)
+    import scipy.sparse as sp
+    Mo = sp.csr_matrix((vals, colind, rowptr), shape=(400, 400)).toarray()
+    assert np.allclose(Mo, Mo.T) and np.all(np.diag(Mo) == 0)
+    # M = diag(theta) + off-diagonal part, handed to the sparse oracle with its diagonal
+    M = Mo + np.diag(th)
+    Ms = sp.csr_matrix(M)
+    cols = w.lowest_columns(th, 8)
+    rs = oracle.ipt_solve_csr(Ms.indptr, Ms.indices, Ms.data, 400, cols=cols, tol=1e-13)
+    rd = oracle.ipt_solve(M, th, cols=cols, tol=1e-13)
+    assert rs["status"] == rd["status"] == oracle.OK
+    assert rs["iterations"] == rd["iterations"]
+    np.testing.assert_allclose(rs["Z"], rd["Z"], atol=1e-14)
+    np.testing.assert_allclose(rs["lam"], rd["lam"], rtol=1e-14)
+
+
+def test_csr_generator_structure():
+    n, per_row, band = 3000, 8, 64
+    rowptr, colind, vals, th = w.csr_banded(n, per_row, band, 1e-3, seed=3)
+    nnz = len(colind)
+    assert rowptr[0] == 0 and rowptr[-1] == nnz
+    rows = np.repeat(np.arange(n), np.diff(rowptr))
+    assert np.all(np.abs(colind - rows) <= band) and np.all(colind != rows)
+    assert 2 * per_row * n - 2 * band * per_row <= nnz <= 2 * per_row * n
+    for i in range(0, n, 97):
+        seg = colind[rowptr[i]:rowptr[i + 1]]
+        assert np.all(np.diff(seg) > 0)
+    assert np.all(np.diff(th) > 0)
+
+
+def test_morgan_tridiagonal_threshold_qualitative():
+    """Section 6.1: IPT converges for small off-diagonal eps and stops converging beyond ~0.5."""
+    M, th = w.morgan_tridiagonal(400, 0.3)
+    assert oracle.ipt_solve(M, th, cols=[0], tol=1e-10, max_iter=2000)["status"] == oracle.OK
+    M, th = w.morgan_tridiagonal(400, 1.0)
+    assert oracle.ipt_solve(M, th, cols=[0], tol=1e-10, max_iter=2000)["status"] != oracle.OK
