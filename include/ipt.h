@@ -1,0 +1,181 @@
+/*
+ * ipt.h - C ABI of libipt, a GB300 (sm_103a) implementation of Iterative
+ * Perturbation Theory (IPT): Kenmoe, Kriemann, Smerlak, Zadorin, "A fast
+ * iterative algorithm for near-diagonal eigenvalue problems" (2020).
+ *
+ * Problem (Section 3): for an n x n real matrix M and a partition
+ * M = D + Delta with D = diag(theta) (theta pairwise distinct), the
+ * eigenvectors z_i normalised by z_i[i] = 1 are the fixed points of
+ *     f_i(z) = e_i + g_i o (z (Delta z)_i - Delta z),        Eq. (single_line_dyn)
+ * and all of them together the fixed points of
+ *     F(Z)   = I + G o (Z D(Delta Z) - Delta Z),             Eq. (dyn)
+ * with G_jk = 1/(theta_j - theta_k), G_jj = 0.  Alg. 1 / Alg. 2 iterate
+ * Z <- F(Z) from Z = I and return Lambda = D(M Z).  This library applies the
+ * map to k requested columns cols[0..k-1] (k = n: the full spectrum).
+ *
+ * Conventions shared by every entry point:
+ *  - Pointers marked "device" are CUDA device memory owned by the caller;
+ *    the library never frees them.  Pointers marked "host" are host memory.
+ *  - Z (iterates, warm starts, results) is column-major n x k with leading
+ *    dimension ldz >= n: entry (j, c) is Z[c*ldz + j], so column c (the
+ *    eigenvector continued from e_{cols[c]}) is contiguous.
+ *  - Dense M is row-major with leading dimension ldm >= n: M[j*ldm + m].
+ *  - Calls are ordered on the handle's stream and synchronise it before
+ *    returning; outputs are valid on return.  A handle serves one host
+ *    thread at a time.
+ *  - Errors are returned, never raised or aborted on.  Argument errors are
+ *    detected before any kernel runs; on IPT_MAXITER / IPT_DIVERGED the
+ *    outputs hold the last iterate at which F was evaluated.
+ */
+#ifndef IPT_H
+#define IPT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+typedef enum {
+  IPT_OK = 0,               /* stopping test met                                     */
+  IPT_MAXITER = 1,          /* max_iter evaluations of F without meeting the test    */
+  IPT_DIVERGED = 2,         /* non-finite increment/residual or ||Z||_F > bound*sqrt(k) */
+  IPT_DEGENERATE_THETA = 3, /* theta non-finite, or theta_j == theta_{cols[c]}, j != cols[c]
+                               (Section 3 requires simple unperturbed eigenvalues)   */
+  IPT_INVALID_ARG = 4,      /* bad size, pointer, dtype, column index or option      */
+  IPT_CUDA_ERROR = 5,       /* a CUDA runtime call failed                            */
+  IPT_DEVICE_TIMEOUT = 6,   /* a bounded device-side wait gave up                    */
+  IPT_UNSUPPORTED = 7       /* valid request this build cannot serve                 */
+} ipt_status;
+
+/* Element types of inputs and outputs. */
+typedef enum { IPT_DTYPE_F64 = 0, IPT_DTYPE_F32 = 1 } ipt_dtype;
+
+/* Arithmetic of the product Delta Z (the dominant step, Section 4.2). */
+typedef enum {
+  IPT_PREC_F64 = 0,    /* FP64 product and iterate (CUDA cores)                        */
+  IPT_PREC_F32 = 1,    /* plain FP32: FP32 product and iterate (CUDA cores)            */
+  IPT_PREC_BF16 = 2,   /* BF16 tensor-core product (tcgen05), FP32 accumulate/iterate  */
+  IPT_PREC_BF16X3 = 3, /* split-BF16 x3 tensor-core product (hi*hi + hi*lo + lo*hi)    */
+  IPT_PREC_STAGED = 4  /* BF16 until the residual stops improving, then BF16 x3;
+                          only the BF16 x3 stage may declare convergence              */
+} ipt_precision;
+
+/* Stopping test. */
+typedef enum {
+  IPT_STOP_INCREMENT = 0, /* ||F(Z) - Z||_F / ||Z||_F <= tol (Alg. 1/2)                 */
+  IPT_STOP_RESIDUAL = 1   /* rho(Z) = ||M Z - Z Lambda||_F / ||M Z0 - Z0 Lambda0||_F <= tol,
+                             Z0 the unit columns e_{cols[c]}                           */
+} ipt_stop;
+
+typedef struct {
+  int precision;        /* ipt_precision; default IPT_PREC_STAGED                          */
+  int stop;             /* ipt_stop; default IPT_STOP_RESIDUAL                             */
+  double diverge_bound; /* IPT_DIVERGED when ||Z||_F > diverge_bound*sqrt(k); default 1e8  */
+  double stage_switch;  /* STAGED: leave BF16 once the predicted next residual is below
+                           this; default 1e-4                                              */
+  int verify_fp64;      /* nonzero: recompute ||M Z - Z Lambda||_F of the result in FP64
+                           (result.rho_fp64); adds one FP64 product                        */
+  const void* z0;       /* optional warm start (device, Z layout, dtype = z_dtype);
+                           column c is rescaled so that z0[cols[c], c] = 1                 */
+} ipt_options;
+
+#define IPT_MAX_HISTORY 128
+
+typedef struct {
+  int status;           /* ipt_status                                                     */
+  int iterations;       /* evaluations of F (products with Delta)                         */
+  int stage_iters[2];   /* STAGED: evaluations in the BF16 and in the BF16 x3 stage       */
+  double increment;     /* ||F(Z) - Z||_F / ||Z||_F at the returned Z                     */
+  double rho;           /* relative residual of the returned pair, in the product's
+                           arithmetic                                                     */
+  double rho_fp64;      /* same, recomputed in FP64 (verify_fp64), else -1                */
+  double r0;            /* ||M Z0 - Z0 Lambda0||_F, the residual normaliser               */
+  int history_len;      /* min(iterations, IPT_MAX_HISTORY)                               */
+  double hist_increment[IPT_MAX_HISTORY];
+  double hist_rho[IPT_MAX_HISTORY];
+  int hist_stage[IPT_MAX_HISTORY]; /* precision used by each evaluation (ipt_precision)   */
+} ipt_result;
+
+typedef struct ipt_handle ipt_handle;
+
+/* Fill *opt with the defaults listed above. */
+void ipt_options_default(ipt_options* opt);
+
+/* Human-readable name of a status code (static string). */
+const char* ipt_status_string(int status);
+
+/* Create a handle bound to `stream` (a cudaStream_t; NULL = the legacy default
+ * stream) on the current device.  The handle owns a grow-only device
+ * workspace (sized by the largest problem seen) and nothing else. */
+ipt_status ipt_create(ipt_handle** h, void* stream);
+
+/* Release the handle and its workspace.  NULL is accepted. */
+ipt_status ipt_destroy(ipt_handle* h);
+
+/*
+ * Dense solve, Alg. 2 (k = n) or Alg. 1 per column (k < n).
+ *   n        matrix order, >= 1
+ *   M        device, row-major n x n, element type m_dtype, leading dim ldm >= n
+ *   theta    device, n doubles: the diagonal D of the partition; NULL = diag(M)
+ *   k        number of requested columns, 1 <= k <= n
+ *   cols     device, k distinct int32 in [0, n): requested e_i; NULL = 0..k-1
+ *   tol      stopping tolerance (>= 0) for opt->stop
+ *   max_iter maximum evaluations of F, >= 1
+ *   opt      options; NULL = defaults
+ *   lambda   device, k doubles out: Lambda_c = theta_{cols[c]} + (Delta Z)_{cols[c], c}
+ *   Z        device out, n x k column-major (ldz >= n), element type z_dtype
+ *   out      host, filled with status, counts, norms and history
+ * Returns the status also stored in out->status.
+ */
+ipt_status ipt_solve_dense(ipt_handle* h, int64_t n, const void* M, int64_t ldm, int m_dtype,
+                           const double* theta, int64_t k, const int32_t* cols, double tol,
+                           int max_iter, const ipt_options* opt, double* lambda, void* Z,
+                           int64_t ldz, int z_dtype, ipt_result* out);
+
+/*
+ * ipt_solve_dense with HOST buffers: M, theta, cols, lambda and Z are host
+ * pointers (pinned memory gives the fastest copies).  The call copies the
+ * inputs to the handle's workspace, solves, and copies Lambda and Z back.
+ */
+ipt_status ipt_solve_dense_host(ipt_handle* h, int64_t n, const void* M, int64_t ldm, int m_dtype,
+                                const double* theta, int64_t k, const int32_t* cols, double tol,
+                                int max_iter, const ipt_options* opt, double* lambda, void* Z,
+                                int64_t ldz, int z_dtype, ipt_result* out);
+
+/*
+ * One evaluation of the map, Eq. (dyn): F = F(Z) for a given Z, with
+ * lambda_c = theta_{cols[c]} + (Delta Z)_{cols[c], c}.  Arguments as in
+ * ipt_solve_dense; Zin (device, read) and Fout (device, written) use the Z
+ * layout with ldz and z_dtype; `precision` is an ipt_precision (STAGED is
+ * invalid here).  norms (host, 3 doubles, may be NULL) receives
+ * ||F - Z||_F, ||Z||_F and ||M Z - Z Lambda||_F in the product's arithmetic.
+ */
+ipt_status ipt_step_dense(ipt_handle* h, int64_t n, const void* M, int64_t ldm, int m_dtype,
+                          const double* theta, int64_t k, const int32_t* cols, int precision,
+                          const void* Zin, void* Fout, int64_t ldz, int z_dtype, double* lambda,
+                          double* norms);
+
+/*
+ * Sparse solve with M in CSR form (Section 6.1 workloads: a few extremal
+ * eigenpairs of a large sparse near-diagonal matrix).
+ *   rowptr device, n+1 int32; colind device, nnz int32 (0-based, any order
+ *   within a row, no duplicates); vals device, nnz of v_dtype.  The CSR
+ *   holds all stored entries of M, diagonal ones included; Delta = M - diag(theta).
+ *   theta  device, n doubles; NULL = diag(M) (0 where a row stores no diagonal)
+ * Every other argument as in ipt_solve_dense.  Product arithmetic: FP32
+ * (IPT_PREC_F32, the default for this call) or FP64 (IPT_PREC_F64); other
+ * precisions return IPT_UNSUPPORTED.
+ */
+ipt_status ipt_solve_csr(ipt_handle* h, int64_t n, int64_t nnz, const int32_t* rowptr,
+                         const int32_t* colind, const void* vals, int v_dtype,
+                         const double* theta, int64_t k, const int32_t* cols, double tol,
+                         int max_iter, const ipt_options* opt, double* lambda, void* Z,
+                         int64_t ldz, int z_dtype, ipt_result* out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* IPT_H */

@@ -1,0 +1,520 @@
+// C ABI of libipt (declared in include/ipt.h): argument validation, the
+// handle's workspace, and the host loop that drives Alg. 2 on the device.
+//
+// Per evaluation of F the host enqueues  d = D(Delta Z)  ->  product + map
+// epilogue  ->  k_control,  then reads the controller's few words back.
+// Every kernel returns at entry once the controller has set `done`.
+#include "ipt_internal.cuh"
+
+#include <stddef.h>
+#include <string.h>
+
+#include <algorithm>
+
+using namespace ipt;
+
+namespace {
+
+struct Buf {
+  void* p = nullptr;
+  size_t cap = 0;
+};
+
+cudaError_t ensure(Buf& b, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  if (b.cap >= bytes) return cudaSuccess;
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.cap = 0;
+  cudaError_t e = cudaMalloc(&b.p, bytes);
+  if (e == cudaSuccess) b.cap = bytes;
+  return e;
+}
+
+}  // namespace
+
+struct ipt_handle {
+  cudaStream_t s = nullptr;
+  int dev = 0;
+  Buf drow, dt, dh, dl, z[2], wh[2], wl[2];
+  Buf theta, thh, thl, icol, count, d, st;
+  Buf m64, z64, racc;
+  Buf hM, hTheta, hCols, hLam, hZ;  // device staging of the host-buffer entry point
+  DevState* hst = nullptr;          // pinned mirror of the controller's words
+};
+
+namespace {
+
+constexpr size_t kStateHead = offsetof(DevState, hist_inc);
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+    else prev = -1;
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+#define CK(x)                                   \
+  do {                                          \
+    cudaError_t e_ = (x);                       \
+    if (e_ != cudaSuccess) return IPT_CUDA_ERROR; \
+  } while (0)
+
+inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+inline bool tensor_core(int prec) {
+  return prec == IPT_PREC_BF16 || prec == IPT_PREC_BF16X3 || prec == IPT_PREC_STAGED;
+}
+
+// Problem geometry and buffer plan for one dense solve / step.
+struct Plan {
+  int n, k, npad, kpad, prec;
+  bool f64;  // FP64 iterate and product
+  bool tc;   // tensor-core buffers
+};
+
+ipt_status check_dense_args(ipt_handle* h, int64_t n, const void* M, int64_t ldm, int m_dtype,
+                            int64_t k, int prec, int64_t ldz, int z_dtype) {
+  if (!h || !M) return IPT_INVALID_ARG;
+  if (n < 1 || n > (1 << 20) || k < 1 || k > n || ldm < n || ldz < n) return IPT_INVALID_ARG;
+  if (m_dtype != IPT_DTYPE_F64 && m_dtype != IPT_DTYPE_F32) return IPT_INVALID_ARG;
+  if (z_dtype != IPT_DTYPE_F64 && z_dtype != IPT_DTYPE_F32) return IPT_INVALID_ARG;
+  if (prec < IPT_PREC_F64 || prec > IPT_PREC_STAGED) return IPT_INVALID_ARG;
+  return IPT_OK;
+}
+
+ipt_status alloc_dense(ipt_handle* h, const Plan& p) {
+  const size_t nn = (size_t)p.npad * p.npad, kn = (size_t)p.kpad * p.npad;
+  const size_t ez = p.f64 ? 8 : 4;
+  CK(ensure(h->drow, nn * ez));
+  CK(ensure(h->z[0], kn * ez));
+  CK(ensure(h->z[1], kn * ez));
+  if (p.tc) {
+    CK(ensure(h->dt, nn * 4));
+    CK(ensure(h->dh, nn * 2));
+    CK(ensure(h->dl, nn * 2));
+    for (int b = 0; b < 2; ++b) {
+      CK(ensure(h->wh[b], kn * 2));
+      CK(ensure(h->wl[b], kn * 2));
+    }
+  }
+  CK(ensure(h->theta, (size_t)p.npad * 8));
+  CK(ensure(h->thh, (size_t)p.npad * 4));
+  CK(ensure(h->thl, (size_t)p.npad * 4));
+  CK(ensure(h->icol, (size_t)p.kpad * 4));
+  CK(ensure(h->count, (size_t)p.npad * 4));
+  CK(ensure(h->d, (size_t)p.kpad * 8));
+  CK(ensure(h->st, sizeof(DevState)));
+  return IPT_OK;
+}
+
+DevState* dst(ipt_handle* h) { return static_cast<DevState*>(h->st.p); }
+
+ipt_status status_from_flags(int flags) {
+  if (flags & (FLAG_COL_RANGE | FLAG_COL_DUP | FLAG_ZERO_PIVOT)) return IPT_INVALID_ARG;
+  if (flags & (FLAG_THETA_NONFINITE | FLAG_THETA_DEGENERATE)) return IPT_DEGENERATE_THETA;
+  return IPT_OK;
+}
+
+// Partition, validation and starting point; leaves the controller state
+// initialised with the first stage.  z0 (optional) is copied into Z buffer 0,
+// rescaled to z0[cols[c], c] = 1 when `rescale`.
+ipt_status setup_dense(ipt_handle* h, const Plan& p, const void* M, int64_t ldm, int m_dtype,
+                       const double* theta, const int32_t* cols, const void* z0, int64_t ldz0,
+                       int z0_dtype, bool rescale, int first_stage) {
+  cudaStream_t s = h->s;
+  DevState* st = dst(h);
+  CK(cudaMemsetAsync(st, 0, sizeof(DevState), s));
+  {
+    DevState init;
+    memset(&init, 0, kStateHead);
+    init.stage = first_stage;
+    CK(cudaMemcpyAsync(st, &init, kStateHead, cudaMemcpyHostToDevice, s));
+  }
+  CK(cudaMemsetAsync(h->count.p, 0, (size_t)p.npad * 4, s));
+  launch_theta(M, ldm, m_dtype, theta, p.n, p.npad, (double*)h->theta.p, (float*)h->thh.p,
+               (float*)h->thl.p, s);
+  launch_validate(cols, p.n, p.k, p.kpad, (const double*)h->theta.p, (int32_t*)h->icol.p,
+                  (int*)h->count.p, st, s);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(h->hst, st, kStateHead, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  ipt_status v = status_from_flags(h->hst->flags);
+  if (v != IPT_OK) return v;
+
+  launch_form_delta(M, ldm, m_dtype, (const double*)h->theta.p, p.n, p.npad,
+                    (const int*)h->count.p, h->drow.p, p.f64 ? 1 : 0,
+                    p.tc ? (float*)h->dt.p : nullptr,
+                    p.tc ? (__nv_bfloat16*)h->dh.p : nullptr,
+                    p.tc ? (__nv_bfloat16*)h->dl.p : nullptr, st, s);
+  const size_t kn = (size_t)p.kpad * p.npad;
+  CK(cudaMemsetAsync(h->z[1].p, 0, kn * (p.f64 ? 8 : 4), s));
+  if (p.tc) {
+    CK(cudaMemsetAsync(h->wh[1].p, 0, kn * 2, s));
+    CK(cudaMemsetAsync(h->wl[1].p, 0, kn * 2, s));
+  }
+  if (z0 && !rescale) {
+    // exact copy (single evaluation at a caller-given Z)
+    CK(cudaMemsetAsync(h->z[0].p, 0, kn * (p.f64 ? 8 : 4), s));
+    launch_copy_z(z0, z0_dtype == IPT_DTYPE_F64, ldz0, p.n, p.k, h->z[0].p, p.npad, p.f64 ? 1 : 0,
+                  s);
+  } else {
+    launch_init_z(z0, ldz0, z0_dtype, (const int32_t*)h->icol.p, p.n, p.k, p.npad, p.kpad,
+                  h->z[0].p, p.f64 ? 1 : 0, st, s);
+  }
+  if (p.tc)
+    launch_split_w((const float*)h->z[0].p, (const int32_t*)h->icol.p, p.npad, p.kpad,
+                   (__nv_bfloat16*)h->wh[0].p, (__nv_bfloat16*)h->wl[0].p, s);
+  CK(cudaGetLastError());
+  if (z0) {
+    CK(cudaMemcpyAsync(h->hst, st, kStateHead, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    v = status_from_flags(h->hst->flags);
+    if (v != IPT_OK) return v;
+  }
+  return IPT_OK;
+}
+
+// One evaluation at Z buffer `cur` in arithmetic `stage`: d, product, map.
+ipt_status evaluate(ipt_handle* h, const Plan& p, int cur, int stage) {
+  cudaStream_t s = h->s;
+  DevState* st = dst(h);
+  launch_prepass(h->drow.p, h->z[cur].p, p.f64 ? 1 : 0, p.npad, (const int32_t*)h->icol.p,
+                 p.kpad, (double*)h->d.p, st, s);
+  const int nxt = cur ^ 1;
+  if (p.f64) {
+    MapArgs<double> a{};
+    a.Zin = (const double*)h->z[cur].p;
+    a.Fout = (double*)h->z[nxt].p;
+    a.d = (const double*)h->d.p;
+    a.icol = (const int32_t*)h->icol.p;
+    a.theta = (const double*)h->theta.p;
+    a.ld = p.npad;
+    a.n = p.n;
+    a.k = p.k;
+    a.st = st;
+    launch_gemm_simt_f64((const double*)h->drow.p, a, p.npad, p.kpad, s);
+  } else {
+    MapArgs<float> a{};
+    a.Zin = (const float*)h->z[cur].p;
+    a.Fout = (float*)h->z[nxt].p;
+    a.d = (const double*)h->d.p;
+    a.icol = (const int32_t*)h->icol.p;
+    a.th_hi = (const float*)h->thh.p;
+    a.th_lo = (const float*)h->thl.p;
+    a.ld = p.npad;
+    a.n = p.n;
+    a.k = p.k;
+    a.st = st;
+    if (stage == IPT_PREC_F32) {
+      launch_gemm_simt_f32((const float*)h->drow.p, a, p.npad, p.kpad, s);
+    } else {
+      a.Wh = (__nv_bfloat16*)h->wh[nxt].p;
+      a.Wl = (__nv_bfloat16*)h->wl[nxt].p;
+      a.DT = (const float*)h->dt.p;
+      CK(launch_gemm_tc((const __nv_bfloat16*)h->dh.p, (const __nv_bfloat16*)h->dl.p,
+                        (const __nv_bfloat16*)h->wh[cur].p, (const __nv_bfloat16*)h->wl[cur].p,
+                        a, p.npad, p.kpad, stage == IPT_PREC_BF16X3 ? 3 : 1, s));
+    }
+  }
+  CK(cudaGetLastError());
+  return IPT_OK;
+}
+
+void fill_result(const DevState& hs, ipt_result* out) {
+  out->status = hs.status;
+  out->iterations = hs.iter;
+  out->stage_iters[0] = hs.stage_iters[0];
+  out->stage_iters[1] = hs.stage_iters[1];
+  out->increment = hs.inc;
+  out->rho = hs.rho;
+  out->r0 = sqrt(hs.r0acc);
+  out->history_len = std::min(hs.iter, IPT_MAX_HISTORY);
+  for (int i = 0; i < out->history_len; ++i) {
+    out->hist_increment[i] = hs.hist_inc[i];
+    out->hist_rho[i] = hs.hist_rho[i];
+    out->hist_stage[i] = hs.hist_stage[i];
+  }
+}
+
+ipt_status verify_fp64(ipt_handle* h, const Plan& p, const void* M, int64_t ldm, int m_dtype,
+                       int zbuf, const double* lambda, double* rho64) {
+  cudaStream_t s = h->s;
+  const size_t nn = (size_t)p.npad * p.npad, kn = (size_t)p.kpad * p.npad;
+  CK(ensure(h->m64, nn * 8));
+  CK(ensure(h->z64, kn * 8));
+  CK(ensure(h->racc, 8));
+  launch_convert_m64(M, ldm, m_dtype, p.n, p.npad, (double*)h->m64.p, s);
+  CK(cudaMemsetAsync(h->z64.p, 0, kn * 8, s));
+  launch_copy_z(h->z[zbuf].p, p.f64 ? 1 : 0, p.npad, p.n, p.k, h->z64.p, p.npad, 1, s);
+  CK(cudaMemsetAsync(h->racc.p, 0, 8, s));
+  launch_residual_f64((const double*)h->m64.p, (const double*)h->z64.p, p.npad, lambda, p.n, p.k,
+                      p.npad, p.kpad, (double*)h->racc.p, s);
+  CK(cudaGetLastError());
+  double r2 = 0.0, r0 = 0.0;
+  CK(cudaMemcpyAsync(&r2, h->racc.p, 8, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(&r0, &dst(h)->r0acc, 8, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  *rho64 = r0 > 0.0 ? sqrt(r2) / sqrt(r0) : 0.0;
+  return IPT_OK;
+}
+
+Plan make_plan(int64_t n, int64_t k, int prec) {
+  Plan p;
+  p.n = (int)n;
+  p.k = (int)k;
+  p.npad = (int)round_up(n, kRowPad);
+  p.kpad = (int)round_up(k, kColPad);
+  p.prec = prec;
+  p.f64 = prec == IPT_PREC_F64;
+  p.tc = tensor_core(prec);
+  return p;
+}
+
+ipt_status solve_dense(ipt_handle* h, int64_t n, const void* M, int64_t ldm, int m_dtype,
+                       const double* theta, int64_t k, const int32_t* cols, double tol,
+                       int max_iter, const ipt_options* opt_in, double* lambda, void* Z,
+                       int64_t ldz, int z_dtype, ipt_result* out) {
+  if (!out) return IPT_INVALID_ARG;
+  memset(out, 0, sizeof(*out));
+  out->rho_fp64 = -1.0;
+  ipt_options opt;
+  ipt_options_default(&opt);
+  if (opt_in) opt = *opt_in;
+  ipt_status v = check_dense_args(h, n, M, ldm, m_dtype, k, opt.precision, ldz, z_dtype);
+  if (v == IPT_OK && (!lambda || !Z || !(tol >= 0.0) || max_iter < 1 ||
+                      (opt.stop != IPT_STOP_INCREMENT && opt.stop != IPT_STOP_RESIDUAL)))
+    v = IPT_INVALID_ARG;
+  if (v != IPT_OK) {
+    out->status = v;
+    return v;
+  }
+  DeviceGuard g(h->dev);
+  const Plan p = make_plan(n, k, opt.precision);
+  v = alloc_dense(h, p);
+  if (v == IPT_OK) {
+    const int first = opt.precision == IPT_PREC_STAGED ? IPT_PREC_BF16 : opt.precision;
+    v = setup_dense(h, p, M, ldm, m_dtype, theta, cols, opt.z0, ldz, z_dtype, true, first);
+  }
+  if (v != IPT_OK) {
+    out->status = v;
+    return v;
+  }
+  ControlArgs ca;
+  ca.tol = tol;
+  ca.diverge_bound = opt.diverge_bound;
+  ca.stage_switch = opt.stage_switch;
+  ca.max_iter = max_iter;
+  ca.stop = opt.stop;
+  ca.mode = opt.precision;
+  ca.k = (int)k;
+  cudaStream_t s = h->s;
+  int cur = 0;
+  int stage = opt.precision == IPT_PREC_STAGED ? IPT_PREC_BF16 : opt.precision;
+  for (int it = 0; it < max_iter; ++it) {
+    v = evaluate(h, p, cur, stage);
+    if (v != IPT_OK) break;
+    launch_control(dst(h), ca, s);
+    if (cudaMemcpyAsync(h->hst, dst(h), kStateHead, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+      v = IPT_CUDA_ERROR;
+      break;
+    }
+    if (h->hst->timeout) {
+      v = IPT_DEVICE_TIMEOUT;
+      break;
+    }
+    if (h->hst->done) break;
+    cur = h->hst->cur;
+    stage = h->hst->stage;
+  }
+  if (v != IPT_OK) {
+    out->status = v;
+    return v;
+  }
+  DevState hs;
+  if (cudaMemcpyAsync(&hs, dst(h), sizeof(DevState), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess) {
+    out->status = IPT_CUDA_ERROR;
+    return IPT_CUDA_ERROR;
+  }
+  const int ans = hs.answer;
+  launch_lambda((const double*)h->theta.p, (const int32_t*)h->icol.p, (const double*)h->d.p,
+                p.k, lambda, s);
+  launch_copy_z(h->z[ans].p, p.f64 ? 1 : 0, p.npad, p.n, p.k, Z, ldz,
+                z_dtype == IPT_DTYPE_F64 ? 1 : 0, s);
+  if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) {
+    out->status = IPT_CUDA_ERROR;
+    return IPT_CUDA_ERROR;
+  }
+  fill_result(hs, out);
+  if (opt.verify_fp64) {
+    v = verify_fp64(h, p, M, ldm, m_dtype, ans, lambda, &out->rho_fp64);
+    if (v != IPT_OK) {
+      out->status = v;
+      return v;
+    }
+  }
+  return (ipt_status)out->status;
+}
+
+}  // namespace
+
+extern "C" {
+
+void ipt_options_default(ipt_options* opt) {
+  if (!opt) return;
+  memset(opt, 0, sizeof(*opt));
+  opt->precision = IPT_PREC_STAGED;
+  opt->stop = IPT_STOP_RESIDUAL;
+  opt->diverge_bound = 1e8;
+  opt->stage_switch = 1e-4;
+  opt->verify_fp64 = 0;
+  opt->z0 = nullptr;
+}
+
+const char* ipt_status_string(int status) {
+  switch (status) {
+    case IPT_OK: return "IPT_OK";
+    case IPT_MAXITER: return "IPT_MAXITER";
+    case IPT_DIVERGED: return "IPT_DIVERGED";
+    case IPT_DEGENERATE_THETA: return "IPT_DEGENERATE_THETA";
+    case IPT_INVALID_ARG: return "IPT_INVALID_ARG";
+    case IPT_CUDA_ERROR: return "IPT_CUDA_ERROR";
+    case IPT_DEVICE_TIMEOUT: return "IPT_DEVICE_TIMEOUT";
+    case IPT_UNSUPPORTED: return "IPT_UNSUPPORTED";
+    default: return "IPT_UNKNOWN_STATUS";
+  }
+}
+
+ipt_status ipt_create(ipt_handle** h, void* stream) {
+  if (!h) return IPT_INVALID_ARG;
+  *h = nullptr;
+  ipt_handle* x = new ipt_handle();
+  x->s = static_cast<cudaStream_t>(stream);
+  if (cudaGetDevice(&x->dev) != cudaSuccess ||
+      cudaMallocHost((void**)&x->hst, sizeof(DevState)) != cudaSuccess) {
+    delete x;
+    return IPT_CUDA_ERROR;
+  }
+  *h = x;
+  return IPT_OK;
+}
+
+ipt_status ipt_destroy(ipt_handle* h) {
+  if (!h) return IPT_OK;
+  DeviceGuard g(h->dev);
+  Buf* all[] = {&h->drow, &h->dt, &h->dh, &h->dl, &h->z[0], &h->z[1], &h->wh[0], &h->wh[1],
+                &h->wl[0], &h->wl[1], &h->theta, &h->thh, &h->thl, &h->icol, &h->count,
+                &h->d, &h->st, &h->m64, &h->z64, &h->racc, &h->hM, &h->hTheta, &h->hCols,
+                &h->hLam, &h->hZ};
+  for (Buf* b : all)
+    if (b->p) cudaFree(b->p);
+  if (h->hst) cudaFreeHost(h->hst);
+  delete h;
+  return IPT_OK;
+}
+
+ipt_status ipt_solve_dense(ipt_handle* h, int64_t n, const void* M, int64_t ldm, int m_dtype,
+                           const double* theta, int64_t k, const int32_t* cols, double tol,
+                           int max_iter, const ipt_options* opt, double* lambda, void* Z,
+                           int64_t ldz, int z_dtype, ipt_result* out) {
+  return solve_dense(h, n, M, ldm, m_dtype, theta, k, cols, tol, max_iter, opt, lambda, Z, ldz,
+                     z_dtype, out);
+}
+
+ipt_status ipt_solve_dense_host(ipt_handle* h, int64_t n, const void* M, int64_t ldm, int m_dtype,
+                                const double* theta, int64_t k, const int32_t* cols, double tol,
+                                int max_iter, const ipt_options* opt, double* lambda, void* Z,
+                                int64_t ldz, int z_dtype, ipt_result* out) {
+  if (!out) return IPT_INVALID_ARG;
+  ipt_options o;
+  ipt_options_default(&o);
+  if (opt) o = *opt;
+  ipt_status v = check_dense_args(h, n, M, ldm, m_dtype, k, o.precision, ldz, z_dtype);
+  if (v != IPT_OK || !lambda || !Z || o.z0) {
+    memset(out, 0, sizeof(*out));
+    out->status = v != IPT_OK ? v : IPT_INVALID_ARG;
+    return (ipt_status)out->status;
+  }
+  DeviceGuard g(h->dev);
+  cudaStream_t s = h->s;
+  const size_t em = m_dtype == IPT_DTYPE_F64 ? 8 : 4, ez = z_dtype == IPT_DTYPE_F64 ? 8 : 4;
+  CK(ensure(h->hM, (size_t)n * n * em));
+  CK(ensure(h->hLam, (size_t)k * 8));
+  CK(ensure(h->hZ, (size_t)n * k * ez));
+  CK(cudaMemcpy2DAsync(h->hM.p, n * em, M, ldm * em, n * em, n, cudaMemcpyHostToDevice, s));
+  const double* dth = nullptr;
+  const int32_t* dcols = nullptr;
+  if (theta) {
+    CK(ensure(h->hTheta, (size_t)n * 8));
+    CK(cudaMemcpyAsync(h->hTheta.p, theta, (size_t)n * 8, cudaMemcpyHostToDevice, s));
+    dth = (const double*)h->hTheta.p;
+  }
+  if (cols) {
+    CK(ensure(h->hCols, (size_t)k * 4));
+    CK(cudaMemcpyAsync(h->hCols.p, cols, (size_t)k * 4, cudaMemcpyHostToDevice, s));
+    dcols = (const int32_t*)h->hCols.p;
+  }
+  v = solve_dense(h, n, h->hM.p, n, m_dtype, dth, k, dcols, tol, max_iter, &o,
+                  (double*)h->hLam.p, h->hZ.p, n, z_dtype, out);
+  if (v == IPT_OK || v == IPT_MAXITER || v == IPT_DIVERGED) {
+    CK(cudaMemcpyAsync(lambda, h->hLam.p, (size_t)k * 8, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpy2DAsync(Z, ldz * ez, h->hZ.p, n * ez, n * ez, k, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+  }
+  return v;
+}
+
+ipt_status ipt_step_dense(ipt_handle* h, int64_t n, const void* M, int64_t ldm, int m_dtype,
+                          const double* theta, int64_t k, const int32_t* cols, int precision,
+                          const void* Zin, void* Fout, int64_t ldz, int z_dtype, double* lambda,
+                          double* norms) {
+  ipt_status v = check_dense_args(h, n, M, ldm, m_dtype, k, precision, ldz, z_dtype);
+  if (v != IPT_OK) return v;
+  if (precision == IPT_PREC_STAGED || !Zin || !Fout || !lambda) return IPT_INVALID_ARG;
+  DeviceGuard g(h->dev);
+  const Plan p = make_plan(n, k, precision);
+  v = alloc_dense(h, p);
+  if (v != IPT_OK) return v;
+  v = setup_dense(h, p, M, ldm, m_dtype, theta, cols, Zin, ldz, z_dtype, false, precision);
+  if (v != IPT_OK) return v;
+  v = evaluate(h, p, 0, precision);
+  if (v != IPT_OK) return v;
+  cudaStream_t s = h->s;
+  launch_lambda((const double*)h->theta.p, (const int32_t*)h->icol.p, (const double*)h->d.p,
+                p.k, lambda, s);
+  launch_copy_z(h->z[1].p, p.f64 ? 1 : 0, p.npad, p.n, p.k, Fout, ldz,
+                z_dtype == IPT_DTYPE_F64 ? 1 : 0, s);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(h->hst, dst(h), kStateHead, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (h->hst->timeout) return IPT_DEVICE_TIMEOUT;
+  if (norms) {
+    norms[0] = sqrt(h->hst->acc_inc2);
+    norms[1] = sqrt(h->hst->acc_z2);
+    norms[2] = sqrt(h->hst->acc_r2);
+  }
+  return IPT_OK;
+}
+
+ipt_status ipt_solve_csr(ipt_handle* h, int64_t n, int64_t nnz, const int32_t* rowptr,
+                         const int32_t* colind, const void* vals, int v_dtype,
+                         const double* theta, int64_t k, const int32_t* cols, double tol,
+                         int max_iter, const ipt_options* opt, double* lambda, void* Z,
+                         int64_t ldz, int z_dtype, ipt_result* out) {
+  (void)h; (void)n; (void)nnz; (void)rowptr; (void)colind; (void)vals; (void)v_dtype;
+  (void)theta; (void)k; (void)cols; (void)tol; (void)max_iter; (void)opt; (void)lambda;
+  (void)Z; (void)ldz; (void)z_dtype;
+  if (out) {
+    memset(out, 0, sizeof(*out));
+    out->status = IPT_UNSUPPORTED;
+  }
+  return IPT_UNSUPPORTED;
+}
+
+}  // extern "C"

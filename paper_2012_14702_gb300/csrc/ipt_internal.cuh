@@ -1,0 +1,152 @@
+// Internal declarations shared by the libipt translation units.
+//
+// Data layout in device memory (npad = n rounded up to 128, kpad = k rounded
+// up to 256; every padded entry is zero so no kernel needs K-edge checks):
+//   Drow  [npad x npad] row-major Delta (FP64 in IPT_PREC_F64, else FP32)
+//   DT    [npad x npad] column-major FP32 Delta (tensor-core modes: exact
+//         Delta term of the epilogue)
+//   Dh,Dl [npad x npad] row-major BF16 split of Delta (Dh + Dl ~ Delta)
+//   Z0,Z1 [kpad x npad] column-major iterates (FP64 or FP32), ping-pong
+//   Wh,Wl [2][kpad x npad] column-major BF16 split of W = Z - E (E = unit
+//         columns), the B operand of the tensor-core product, ping-pong
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "../../include/ipt.h"
+
+namespace ipt {
+
+constexpr int kRowPad = 128;  // npad multiple (tile M of every product kernel)
+constexpr int kColPad = 256;  // kpad multiple (tile N of the tensor-core kernel)
+
+// Validation flags (DevState::flags).
+enum : int {
+  FLAG_COL_RANGE = 1,
+  FLAG_COL_DUP = 2,
+  FLAG_THETA_NONFINITE = 4,
+  FLAG_THETA_DEGENERATE = 8,
+  FLAG_ZERO_PIVOT = 16,
+};
+
+// Device-resident solver state: norm accumulators of the running evaluation,
+// the controller's decisions and the history.  Written by the product
+// kernels (accumulators, atomics) and by k_control (one thread).
+struct DevState {
+  double acc_inc2;  // sum (F - Z)^2
+  double acc_z2;    // sum Z^2
+  double acc_r2;    // sum R^2, R = M Z - Z Lambda
+  double r0acc;     // sum of squared off-diagonal Delta entries of requested columns
+  double inc, rho, prev_rho;
+  int done;    // nonzero: stop; every later kernel of the solve returns at entry
+  int status;  // ipt_status once done
+  int stage;   // ipt_precision of the next evaluation
+  int iter;    // evaluations completed
+  int cur;     // Z buffer (0/1) holding the current iterate
+  int answer;  // Z buffer holding the returned iterate
+  int flags;   // validation flags
+  int timeout; // bounded device wait gave up (code of the waiting role)
+  int stage_iters[2];
+  double hist_inc[IPT_MAX_HISTORY];
+  double hist_rho[IPT_MAX_HISTORY];
+  int hist_stage[IPT_MAX_HISTORY];
+};
+
+// Arguments of the fused map epilogue shared by all product kernels.
+template <typename T>
+struct MapArgs {
+  const T* Zin;          // current iterate, column-major [kpad x npad], leading dim ld
+  T* Fout;               // F(Z), same layout
+  __nv_bfloat16* Wh;     // BF16 hi of W' = F - E (tensor-core modes, else null)
+  __nv_bfloat16* Wl;     // BF16 lo of W'
+  const float* DT;       // column-major FP32 Delta (tensor-core modes, else null)
+  const double* d;       // d_c = (Delta Z)_{cols[c], c}
+  const int32_t* icol;   // cols[c]; -1 in padding columns
+  const double* theta;   // FP64 theta (F64 path)
+  const float* th_hi;    // FP32 hi/lo split of theta (FP32 paths)
+  const float* th_lo;
+  int64_t ld;            // npad
+  int n, k;
+  DevState* st;
+};
+
+// ---------------------------------------------------------------- launchers
+// setup (k_setup.cu)
+void launch_theta(const void* M, int64_t ldm, int m_dtype, const double* theta_in, int n,
+                  int npad, double* theta, float* th_hi, float* th_lo, cudaStream_t s);
+void launch_validate(const int32_t* cols, int n, int k, int kpad, const double* theta,
+                     int32_t* icol, int* count, DevState* st, cudaStream_t s);
+void launch_form_delta(const void* M, int64_t ldm, int m_dtype, const double* theta, int n,
+                       int npad, const int* count, void* Drow, int drow_f64, float* DT,
+                       __nv_bfloat16* Dh, __nv_bfloat16* Dl, DevState* st, cudaStream_t s);
+void launch_init_z(const void* z0, int64_t ldz0, int z0_dtype, const int32_t* icol, int n,
+                   int k, int npad, int kpad, void* Z, int z_f64, DevState* st, cudaStream_t s);
+void launch_split_w(const float* Z, const int32_t* icol, int npad, int kpad, __nv_bfloat16* Wh,
+                    __nv_bfloat16* Wl, cudaStream_t s);
+void launch_lambda(const double* theta, const int32_t* icol, const double* d, int k,
+                   double* lambda, cudaStream_t s);
+void launch_copy_z(const void* Z, int z_f64, int64_t ld, int n, int k, void* out,
+                   int64_t ldo, int out_f64, cudaStream_t s);
+void launch_convert_m64(const void* M, int64_t ldm, int m_dtype, int n, int npad, double* M64,
+                        cudaStream_t s);
+
+// iteration pieces (k_iter.cu)
+void launch_prepass(const void* Drow, const void* Z, int f64, int64_t ld, const int32_t* icol,
+                    int kpad, double* d, DevState* st, cudaStream_t s);
+void launch_gemm_simt_f64(const double* Drow, const MapArgs<double>& a, int npad, int kpad,
+                          cudaStream_t s);
+void launch_gemm_simt_f32(const float* Drow, const MapArgs<float>& a, int npad, int kpad,
+                          cudaStream_t s);
+void launch_residual_f64(const double* M64, const double* Z64, int64_t ld, const double* lam,
+                         int n, int k, int npad, int kpad, double* acc, cudaStream_t s);
+struct ControlArgs {
+  double tol, diverge_bound, stage_switch;
+  int max_iter, stop, mode, k;
+};
+void launch_control(DevState* st, ControlArgs a, cudaStream_t s);
+
+// tensor-core product (k_tc_gemm.cu).  passes = 1 (BF16) or 3 (split BF16 x3).
+// Returns a cudaError_t of the launch or of tensor-map encoding.
+cudaError_t launch_gemm_tc(const __nv_bfloat16* Dh, const __nv_bfloat16* Dl,
+                           const __nv_bfloat16* Wh, const __nv_bfloat16* Wl,
+                           const MapArgs<float>& a, int npad, int kpad, int passes,
+                           cudaStream_t s);
+
+// ---------------------------------------------------------------- device helpers
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// theta_j - theta_i from the two-float split (hi + lo = theta to ~2^-48
+// relative): hi differences of nearby values are exact (Sterbenz), so the
+// gap keeps ~24 significant bits even when |theta| >> |theta_j - theta_i|.
+__device__ __forceinline__ float gap2f(float hj, float lj, float hi, float li) {
+  return (hj - hi) + (lj - li);
+}
+
+// The map of Eq. (dyn) at one entry (j, c), j != cols[c]:
+//   u = Z_jc d_c - P_jc,  F_jc = u / (theta_j - theta_{i_c}),
+//   R_jc = (theta_j - theta_{i_c}) Z_jc - u   (= (M Z - Z Lambda)_jc).
+// At j == cols[c]: F = 1, R = 0.
+template <typename T>
+__device__ __forceinline__ void map_entry(T z, T p, T dc, T gap, bool diag, T& f, T& r) {
+  if (diag) {
+    f = T(1);
+    r = T(0);
+  } else {
+    T u = z * dc - p;
+    f = u / gap;
+    r = gap * z - u;
+  }
+}
+
+}  // namespace ipt

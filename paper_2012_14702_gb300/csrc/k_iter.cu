@@ -1,0 +1,328 @@
+// One IPT evaluation on CUDA cores, and the device-side controller.
+//
+//  k_prepass     d_c = (Delta Z)_{cols[c], c}: the diagonal D(Delta Z) of
+//                Eq. (dyn), computed before the product so that every tile of
+//                the product can apply the map in its epilogue.
+//  k_gemm_simt   P = Delta Z (FP64 or FP32 FMA) with the fused epilogue
+//                F = E + G o (Z D(Delta Z) - P) and the norm partials of the
+//                stopping test (Alg. 2) and of the residual.
+//  k_residual    ||M Z - Z Lambda||_F in FP64 (verification of a result).
+//  k_control     the loop test of Alg. 2 on the device.
+#include "ipt_internal.cuh"
+
+#include <math.h>
+
+namespace ipt {
+
+namespace {
+
+// ---------------------------------------------------------------- d = D(Delta Z)
+// One warp per column c: the contiguous row cols[c] of row-major Delta dotted
+// with the contiguous column c of Z.  FP32 data: compensated FP32 sums per
+// lane, FP64 across lanes; FP64 data: FP64 throughout.
+template <typename T>
+__global__ void k_prepass(const T* __restrict__ Drow, const T* __restrict__ Z, int64_t ld,
+                          const int32_t* __restrict__ icol, int kpad, double* __restrict__ d,
+                          const DevState* st) {
+  if (st->done) return;
+  int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (warp >= kpad) return;
+  int c = warp, i = icol[c];
+  if (i < 0) {
+    if (lane == 0) d[c] = 0.0;
+    return;
+  }
+  const T* a = Drow + (int64_t)i * ld;
+  const T* z = Z + (int64_t)c * ld;
+  double tot;
+  if constexpr (sizeof(T) == 4) {
+    float s = 0.f, comp = 0.f;
+    const float4* a4 = reinterpret_cast<const float4*>(a);
+    const float4* z4 = reinterpret_cast<const float4*>(z);
+    for (int64_t m = lane; m < ld / 4; m += 32) {
+      float4 x = __ldg(a4 + m), y = __ldg(z4 + m);
+      float y0 = x.x * y.x + x.y * y.y + x.z * y.z + x.w * y.w;
+      float yy = y0 - comp;
+      float t = s + yy;
+      comp = (t - s) - yy;
+      s = t;
+    }
+    tot = warp_sum((double)s - (double)comp);
+  } else {
+    double s = 0.0;
+    const double2* a2 = reinterpret_cast<const double2*>(a);
+    const double2* z2 = reinterpret_cast<const double2*>(z);
+    for (int64_t m = lane; m < ld / 2; m += 32) {
+      double2 x = a2[m], y = z2[m];
+      s += x.x * y.x + x.y * y.y;
+    }
+    tot = warp_sum(s);
+  }
+  if (lane == 0) d[c] = tot;
+}
+
+// ---------------------------------------------------------------- SIMT product + map
+// Tile BM x BN x BK, 256 threads as 16 (rows) x 16 (cols); each thread owns
+// TM x TN outputs in two halves: rows tm*HM + [0, HM) and BM/2 + tm*HM + [0, HM)
+// (likewise for columns), so a thread's rows are contiguous in the
+// column-major iterate and the epilogue loads/stores vectors along j.
+// A = Delta row-major (lda = ld), B = Z column-major (K = rows contiguous).
+enum { EPI_MAP = 0, EPI_RESIDUAL = 1 };
+
+template <typename T>
+struct Vec;
+template <>
+struct Vec<float> {
+  using V4 = float4;
+};
+template <>
+struct Vec<double> {
+  using V4 = double2;  // 16-byte vector
+};
+
+template <typename T, int BM, int BN, int BK, int TM, int TN, int EPI>
+__global__ void __launch_bounds__(256)
+    k_gemm_simt(const T* __restrict__ A, MapArgs<T> a, const double* __restrict__ lam,
+                double* __restrict__ racc) {
+  constexpr int HM = TM / 2, HN = TN / 2;
+  constexpr int VEC = 16 / sizeof(T);          // elements per 16-byte load
+  constexpr int LPR = BK / VEC;                // loads per tile row
+  static_assert(BM * BK == 256 * VEC && BN * BK == 256 * VEC, "one vector load per thread");
+  using V = typename Vec<T>::V4;
+  if constexpr (EPI == EPI_MAP) {
+    if (a.st->done) return;
+  }
+  __shared__ __align__(16) T As[2][BK][BM];
+  __shared__ __align__(16) T Bs[2][BK][BN];
+  const int tid = threadIdx.x, tm = tid & 15, tn = tid >> 4;
+  const int m0 = blockIdx.y * BM, c0 = blockIdx.x * BN;
+  const int64_t ld = a.ld;
+  const int K = (int)ld;
+  const int lr = tid / LPR, lk = (tid % LPR) * VEC;  // this thread's load slot
+  const T* Ap = A + (int64_t)(m0 + lr) * ld + lk;
+  const T* Bp = a.Zin + (int64_t)(c0 + lr) * ld + lk;
+
+  T acc[TM][TN];
+#pragma unroll
+  for (int i = 0; i < TM; ++i)
+#pragma unroll
+    for (int j = 0; j < TN; ++j) acc[i][j] = T(0);
+
+  V ra = *reinterpret_cast<const V*>(Ap), rb = *reinterpret_cast<const V*>(Bp);
+  auto stash = [&](int buf) {
+    const T* pa = reinterpret_cast<const T*>(&ra);
+    const T* pb = reinterpret_cast<const T*>(&rb);
+#pragma unroll
+    for (int q = 0; q < VEC; ++q) {
+      As[buf][lk + q][lr] = pa[q];
+      Bs[buf][lk + q][lr] = pb[q];
+    }
+  };
+  stash(0);
+  __syncthreads();
+  const int KT = K / BK;
+  for (int kt = 0; kt < KT; ++kt) {
+    const int buf = kt & 1;
+    if (kt + 1 < KT) {
+      ra = *reinterpret_cast<const V*>(Ap + (kt + 1) * BK);
+      rb = *reinterpret_cast<const V*>(Bp + (kt + 1) * BK);
+    }
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      T av[TM], bv[TN];
+#pragma unroll
+      for (int i = 0; i < HM; ++i) {
+        av[i] = As[buf][kk][tm * HM + i];
+        av[HM + i] = As[buf][kk][BM / 2 + tm * HM + i];
+      }
+#pragma unroll
+      for (int j = 0; j < HN; ++j) {
+        bv[j] = Bs[buf][kk][tn * HN + j];
+        bv[HN + j] = Bs[buf][kk][BN / 2 + tn * HN + j];
+      }
+#pragma unroll
+      for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
+    }
+    if (kt + 1 < KT) stash(buf ^ 1);
+    __syncthreads();
+  }
+
+  // ---------------- fused epilogue
+  T s_inc = T(0), s_z = T(0), s_r = T(0);
+#pragma unroll
+  for (int jj = 0; jj < TN; ++jj) {
+    const int c = c0 + (jj < HN ? tn * HN + jj : BN / 2 + tn * HN + (jj - HN));
+    if (c >= a.k) continue;
+    int ic = -1;
+    T dc = T(0), lamc = T(0);
+    if constexpr (EPI == EPI_MAP) {
+      ic = a.icol[c];
+      dc = (T)a.d[c];
+    } else {
+      lamc = (T)lam[c];
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int jb = m0 + (h == 0 ? tm * HM : BM / 2 + tm * HM);
+      const int64_t o = (int64_t)c * ld + jb;
+      T z[HM], f[HM];
+      *reinterpret_cast<V*>(z) = *reinterpret_cast<const V*>(a.Zin + o);
+      if constexpr (HM * sizeof(T) == 32) {
+        *reinterpret_cast<V*>(z + VEC) = *reinterpret_cast<const V*>(a.Zin + o + VEC);
+      }
+#pragma unroll
+      for (int q = 0; q < HM; ++q) {
+        const int j = jb + q;
+        const T p = acc[h * HM + q][jj];
+        f[q] = z[q];
+        if (j >= a.n) continue;
+        if constexpr (EPI == EPI_MAP) {
+          T gap;
+          if constexpr (sizeof(T) == 8) gap = a.theta[j] - a.theta[ic];
+          else gap = gap2f(a.th_hi[j], a.th_lo[j], a.th_hi[ic], a.th_lo[ic]);
+          T fv, rv;
+          map_entry<T>(z[q], p, dc, gap, j == ic, fv, rv);
+          f[q] = fv;
+          s_inc += (fv - z[q]) * (fv - z[q]);
+          s_z += z[q] * z[q];
+          s_r += rv * rv;
+        } else {
+          const T rv = p - z[q] * lamc;  // (M Z)_jc - Z_jc lambda_c
+          s_r += rv * rv;
+        }
+      }
+      if constexpr (EPI == EPI_MAP) {
+        *reinterpret_cast<V*>(a.Fout + o) = *reinterpret_cast<const V*>(f);
+        if constexpr (HM * sizeof(T) == 32) {
+          *reinterpret_cast<V*>(a.Fout + o + VEC) = *reinterpret_cast<const V*>(f + VEC);
+        }
+      }
+    }
+  }
+  // block reduction of the three partial sums
+  __shared__ double red[3][8];
+  const double b_inc = warp_sum((double)s_inc), b_z = warp_sum((double)s_z),
+               b_r = warp_sum((double)s_r);
+  const int w = tid >> 5, l = tid & 31;
+  if (l == 0) {
+    red[0][w] = b_inc;
+    red[1][w] = b_z;
+    red[2][w] = b_r;
+  }
+  __syncthreads();
+  if (w == 0) {
+    double x0 = l < 8 ? red[0][l] : 0.0, x1 = l < 8 ? red[1][l] : 0.0,
+           x2 = l < 8 ? red[2][l] : 0.0;
+    x0 = warp_sum(x0);
+    x1 = warp_sum(x1);
+    x2 = warp_sum(x2);
+    if (l == 0) {
+      if constexpr (EPI == EPI_MAP) {
+        atomicAdd(&a.st->acc_inc2, x0);
+        atomicAdd(&a.st->acc_z2, x1);
+        atomicAdd(&a.st->acc_r2, x2);
+      } else {
+        atomicAdd(racc, x2);
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------- controller
+// One thread.  Reads the accumulators of the evaluation that just finished
+// (at iterate Z = buffer `cur`), applies the test of Alg. 2, the divergence
+// and iteration caps, the BF16 -> BF16x3 stage switch, records history and
+// clears the accumulators for the next evaluation.
+__global__ void k_control(DevState* st, ControlArgs a) {
+  if (st->done) return;
+  const int it = st->iter;
+  const double z2 = st->acc_z2;
+  const double inc = sqrt(st->acc_inc2) / sqrt(z2);
+  const double r0 = sqrt(st->r0acc);
+  const double rho = r0 > 0.0 ? sqrt(st->acc_r2) / r0 : 0.0;
+  const int stage = st->stage;
+  if (it < IPT_MAX_HISTORY) {
+    st->hist_inc[it] = inc;
+    st->hist_rho[it] = rho;
+    st->hist_stage[it] = stage;
+  }
+  if (stage == IPT_PREC_BF16 && a.mode == IPT_PREC_STAGED) st->stage_iters[0]++;
+  else st->stage_iters[1]++;
+  st->inc = inc;
+  st->rho = rho;
+  st->iter = it + 1;
+  st->acc_inc2 = 0.0;
+  st->acc_z2 = 0.0;
+  st->acc_r2 = 0.0;
+  const double test = a.stop == IPT_STOP_INCREMENT ? inc : rho;
+  const bool staged_bf16 = (a.mode == IPT_PREC_STAGED && stage == IPT_PREC_BF16);
+  if (!isfinite(inc) || !isfinite(rho) || sqrt(z2) > a.diverge_bound * sqrt((double)a.k)) {
+    st->status = IPT_DIVERGED;
+    st->done = 1;
+    st->answer = st->cur;
+  } else if (!staged_bf16 && test <= a.tol) {
+    st->status = IPT_OK;
+    st->done = 1;
+    st->answer = st->cur;
+  } else if (it + 1 >= a.max_iter) {
+    st->status = IPT_MAXITER;
+    st->done = 1;
+    st->answer = st->cur;
+  } else {
+    if (staged_bf16) {
+      // Leave BF16 once the geometric prediction of the next residual falls
+      // under the switch level, once BF16 stops contracting, or once the test
+      // is already met (only the accurate stage may confirm it).
+      const double prev = st->prev_rho;
+      const double q = (it > 0 && prev > 0.0) ? rho / prev : 1.0;
+      if (test <= a.tol || rho * q < a.stage_switch || (it > 0 && q > 0.5))
+        st->stage = IPT_PREC_BF16X3;
+    }
+    st->cur ^= 1;
+  }
+  st->prev_rho = rho;
+}
+
+}  // namespace
+
+void launch_prepass(const void* Drow, const void* Z, int f64, int64_t ld, const int32_t* icol,
+                    int kpad, double* d, DevState* st, cudaStream_t s) {
+  unsigned g = (unsigned)((kpad + 7) / 8);
+  if (f64)
+    k_prepass<double><<<g, 256, 0, s>>>((const double*)Drow, (const double*)Z, ld, icol, kpad, d,
+                                        st);
+  else
+    k_prepass<float><<<g, 256, 0, s>>>((const float*)Drow, (const float*)Z, ld, icol, kpad, d,
+                                       st);
+}
+
+void launch_gemm_simt_f64(const double* Drow, const MapArgs<double>& a, int npad, int kpad,
+                          cudaStream_t s) {
+  dim3 g(kpad / 64, npad / 64);
+  k_gemm_simt<double, 64, 64, 8, 4, 4, EPI_MAP><<<g, 256, 0, s>>>(Drow, a, nullptr, nullptr);
+}
+
+void launch_gemm_simt_f32(const float* Drow, const MapArgs<float>& a, int npad, int kpad,
+                          cudaStream_t s) {
+  dim3 g(kpad / 128, npad / 128);
+  k_gemm_simt<float, 128, 128, 8, 8, 8, EPI_MAP><<<g, 256, 0, s>>>(Drow, a, nullptr, nullptr);
+}
+
+void launch_residual_f64(const double* M64, const double* Z64, int64_t ld, const double* lam,
+                         int n, int k, int npad, int kpad, double* acc, cudaStream_t s) {
+  MapArgs<double> a{};
+  a.Zin = Z64;
+  a.ld = ld;
+  a.n = n;
+  a.k = k;
+  dim3 g(kpad / 64, npad / 64);
+  k_gemm_simt<double, 64, 64, 8, 4, 4, EPI_RESIDUAL><<<g, 256, 0, s>>>(M64, a, lam, acc);
+}
+
+void launch_control(DevState* st, ControlArgs a, cudaStream_t s) {
+  k_control<<<1, 1, 0, s>>>(st, a);
+}
+
+}  // namespace ipt

@@ -1,0 +1,466 @@
+// Tensor-core IPT evaluation for sm_103a: P = Delta Z on tcgen05 with the map
+// of Eq. (dyn) applied in the epilogue.
+//
+// Product.  The identity part of Z is split off, Z = E + W (E = unit columns,
+// W_{cols[c], c} = 0), so P = Delta E + Delta W: the first term is the
+// column cols[c] of Delta, added exactly in FP32 by the epilogue; only
+// Delta W goes through the tensor cores, as BF16 (passes = 1: Dh Wh) or
+// split BF16 x3 (passes = 3: Dh Wh + Dh Wl + Dl Wh), FP32 accumulation in
+// TMEM.  Because |W| << 1 near the fixed point, the BF16 rounding error is
+// scaled by |W| instead of by |Z| ~ 1.
+//
+// Kernel shape: persistent, one CTA per SM, 192 threads.
+//   warp 0      TMA producer: 128x64 A tiles and 256x64 B tiles (BF16,
+//               128-byte swizzle) into a 4-stage shared-memory ring
+//   warp 1      TMEM allocator and single-thread tcgen05.mma issuer,
+//               M=128 N=256 K=16 per instruction, two 256-column
+//               accumulators (512 TMEM columns) so the epilogue of tile t
+//               overlaps the product of tile t+1
+//   warps 2..5  epilogue: tcgen05.ld 32 columns at a time, the map
+//               F = E + G o (Z D(Delta Z) - P), the residual
+//               R = (theta_j - theta_i) Z - (Z d - P), writes F (FP32) and the
+//               BF16 split of W' = F - E for the next product, norm partials.
+// Every mbarrier wait is bounded (globaltimer); on expiry the CTA records a
+// timeout in DevState, drains its TMA loads and MMAs, frees TMEM and returns.
+#include "ipt_internal.cuh"
+
+#include <cuda.h>
+
+namespace ipt {
+
+namespace {
+
+constexpr int BM = 128, BN = 256, BK = 64, STAGES = 4;
+constexpr int A_BYTES = BM * BK * 2;
+constexpr int B_BYTES = BN * BK * 2;
+constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+constexpr int TMEM_COLS = 2 * BN;
+constexpr int NUM_THREADS = 192;
+constexpr int EPI_THREADS = 128;
+constexpr uint64_t kTimeoutNs = 2000000000ull;  // 2 s: far above any legitimate wait
+constexpr int GROUP_M = 16;                      // row blocks per L2 raster group
+
+struct Ctl {
+  uint64_t full[STAGES];
+  uint64_t empty[STAGES];
+  uint64_t tfull[2];
+  uint64_t tempty[2];
+  uint64_t drain;
+  uint32_t tmem_base;
+  int abort;
+};
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + (int)sizeof(Ctl) + 64;
+
+// Instruction descriptor, kind::f16: D = F32 (bits 4-5 = 1), A = B = BF16
+// (bits 7-9, 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at bit 17,
+// M >> 4 at bit 24.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) |
+                            ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+
+__device__ __forceinline__ uint32_t su32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ uint64_t gtimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(b)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(su32(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Wait for the phase `parity` of barrier b.  False on timeout or when another
+// role has aborted (then the caller stops issuing and falls through to drain).
+__device__ __noinline__ bool wait_bounded(uint64_t* b, uint32_t parity, volatile int* abort) {
+  if (mbar_try(b, parity)) return true;
+  const uint64_t t0 = gtimer();
+  for (;;) {
+#pragma unroll 1
+    for (int i = 0; i < 32; ++i)
+      if (mbar_try(b, parity)) return true;
+    if (*abort) return false;
+    if (gtimer() - t0 > kTimeoutNs) return false;
+  }
+}
+
+__device__ __forceinline__ void tma_load(void* dst, const CUtensorMap* map, uint64_t* bar, int x,
+                                         int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4}], [%2];" ::"r"(su32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(su32(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor for a K-major operand tile written by TMA
+// with 128-byte swizzle: rows of 128 B (64 BF16), 8-row atoms 1024 B apart
+// (stride byte offset), leading byte offset unused, version 1, layout 2.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)(1024 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t dt, uint64_t ad, uint64_t bd, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dt),
+      "l"(ad), "l"(bd), "r"(kIdesc), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          su32(bar))
+      : "memory");
+}
+
+// 32 consecutive accumulator columns of this thread's TMEM lane; the load
+// and its completion wait are one asm statement so no use can precede the wait.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+        "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+        "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+        "=r"(r[31])
+      : "r"(taddr)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tile_coords(int t, int num_m, int num_n, int& mb, int& nb) {
+  const int per_group = GROUP_M * num_n;
+  const int g = t / per_group;
+  const int first = g * GROUP_M;
+  const int gm = min(GROUP_M, num_m - first);
+  const int r = t - g * per_group;
+  mb = first + r % gm;
+  nb = r / gm;
+}
+
+__device__ __forceinline__ void fail(Ctl* ctl, DevState* st, int code) {
+  *reinterpret_cast<volatile int*>(&ctl->abort) = 1;
+  atomicCAS(&st->timeout, 0, code);
+}
+
+__global__ void __launch_bounds__(NUM_THREADS, 1)
+    k_gemm_tc(const __grid_constant__ CUtensorMap tmDh, const __grid_constant__ CUtensorMap tmDl,
+              const __grid_constant__ CUtensorMap tmWh, const __grid_constant__ CUtensorMap tmWl,
+              MapArgs<float> a, int num_m, int num_n, int num_kb, int passes) {
+  if (a.st->done) return;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  uint8_t* sA = smem;
+  uint8_t* sB = smem + STAGES * A_BYTES;
+  Ctl* ctl = reinterpret_cast<Ctl*>(smem + STAGES * STAGE_BYTES);
+  volatile int* abort = &ctl->abort;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&ctl->full[s], 1);
+      mbar_init(&ctl->empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&ctl->tfull[b], 1);
+      mbar_init(&ctl->tempty[b], EPI_THREADS);
+    }
+    mbar_init(&ctl->drain, 1);
+    ctl->abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     su32(&ctl->tmem_base)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = ctl->tmem_base;
+  const int num_tiles = num_m * num_n;
+  const int total_kb = passes * num_kb;
+
+  if (warp == 0) {
+    // ------------------------------------------------ TMA producer
+    if (lane == 0) {
+      int pend_parity[STAGES];
+      for (int s = 0; s < STAGES; ++s) pend_parity[s] = -1;
+      int stage = 0;
+      uint32_t phase = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < num_tiles && ok; t += gridDim.x) {
+        int mb, nb;
+        tile_coords(t, num_m, num_n, mb, nb);
+        for (int kb = 0; kb < total_kb; ++kb) {
+          if (!wait_bounded(&ctl->empty[stage], phase ^ 1u, abort)) {
+            fail(ctl, a.st, 1);
+            ok = false;
+            break;
+          }
+          const int pass = kb / num_kb;
+          const int kx = (kb - pass * num_kb) * BK;
+          mbar_expect_tx(&ctl->full[stage], STAGE_BYTES);
+          tma_load(sA + stage * A_BYTES, pass == 2 ? &tmDl : &tmDh, &ctl->full[stage], kx,
+                   mb * BM);
+          tma_load(sB + stage * B_BYTES, pass == 1 ? &tmWl : &tmWh, &ctl->full[stage], kx,
+                   nb * BN);
+          pend_parity[stage] = (int)phase;
+          if (++stage == STAGES) {
+            stage = 0;
+            phase ^= 1u;
+          }
+        }
+      }
+      // drain: every issued load lands before the CTA may exit
+      for (int s = 0; s < STAGES; ++s) {
+        if (pend_parity[s] < 0) continue;
+        const uint64_t t0 = gtimer();
+        while (!mbar_try(&ctl->full[s], (uint32_t)pend_parity[s]))
+          if (gtimer() - t0 > kTimeoutNs) {
+            fail(ctl, a.st, 5);
+            break;
+          }
+      }
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      int stage = 0, acc = 0;
+      uint32_t phase = 0, acc_phase = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < num_tiles && ok; t += gridDim.x) {
+        if (!wait_bounded(&ctl->tempty[acc], acc_phase ^ 1u, abort)) {
+          fail(ctl, a.st, 2);
+          break;
+        }
+        tc_fence_after();
+        const uint32_t dt = tmem + (uint32_t)(acc * BN);
+        for (int kb = 0; kb < total_kb; ++kb) {
+          if (!wait_bounded(&ctl->full[stage], phase, abort)) {
+            fail(ctl, a.st, 3);
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t ab = su32(sA + stage * A_BYTES), bb = su32(sB + stage * B_BYTES);
+#pragma unroll
+          for (int k = 0; k < BK / 16; ++k)
+            mma_bf16(dt, sw128_desc(ab + k * 32), sw128_desc(bb + k * 32), (kb | k) != 0);
+          mma_commit(&ctl->empty[stage]);
+          if (++stage == STAGES) {
+            stage = 0;
+            phase ^= 1u;
+          }
+        }
+        if (!ok) break;
+        mma_commit(&ctl->tfull[acc]);
+        if (++acc == 2) {
+          acc = 0;
+          acc_phase ^= 1u;
+        }
+      }
+      // drain: all issued MMAs complete before TMEM is freed
+      mma_commit(&ctl->drain);
+      const uint64_t t0 = gtimer();
+      while (!mbar_try(&ctl->drain, 0))
+        if (gtimer() - t0 > kTimeoutNs) {
+          fail(ctl, a.st, 6);
+          break;
+        }
+    }
+  } else {
+    // ------------------------------------------------ epilogue (warps 2..5)
+    const int q = warp & 3;  // TMEM lane quarter this warp may access
+    const int row = q * 32 + lane;
+    const int64_t ld = a.ld;
+    int acc = 0;
+    uint32_t acc_phase = 0;
+    float s_inc = 0.f, s_z = 0.f, s_r = 0.f;
+    for (int t = blockIdx.x; t < num_tiles; t += gridDim.x) {
+      int mb, nb;
+      tile_coords(t, num_m, num_n, mb, nb);
+      if (!wait_bounded(&ctl->tfull[acc], acc_phase, abort)) {
+        fail(ctl, a.st, 4);
+        break;
+      }
+      tc_fence_after();
+      const int j = mb * BM + row;
+      const bool jok = j < a.n;
+      const float hj = a.th_hi[j], lj = a.th_lo[j];
+#pragma unroll 1
+      for (int ch = 0; ch < BN / 32; ++ch) {
+        float v[32];
+        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN + ch * 32), v);
+        const int cb = nb * BN + ch * 32;
+        // per-column data, one column per lane, broadcast by shuffles below
+        const int icl = a.icol[cb + lane];
+        const float dl = (float)a.d[cb + lane];
+        const float hil = icl >= 0 ? a.th_hi[icl] : 0.f;
+        const float lil = icl >= 0 ? a.th_lo[icl] : 0.f;
+#pragma unroll
+        for (int hh = 0; hh < 2; ++hh) {
+          float z[16], dlt[16];
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            const int ic = __shfl_sync(0xffffffffu, icl, hh * 16 + i);
+            const int64_t o = (int64_t)(cb + hh * 16 + i) * ld + j;
+            z[i] = (jok && ic >= 0) ? __ldg(a.Zin + o) : 0.f;
+            dlt[i] = (jok && ic >= 0) ? __ldg(a.DT + (int64_t)ic * ld + j) : 0.f;
+          }
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            const int src = hh * 16 + i;
+            const int ic = __shfl_sync(0xffffffffu, icl, src);
+            const float dc = __shfl_sync(0xffffffffu, dl, src);
+            const float hi = __shfl_sync(0xffffffffu, hil, src);
+            const float li = __shfl_sync(0xffffffffu, lil, src);
+            if (!jok || ic < 0) continue;
+            const int64_t o = (int64_t)(cb + src) * ld + j;
+            const float p = v[src] + dlt[i];
+            float f, r;
+            map_entry<float>(z[i], p, dc, gap2f(hj, lj, hi, li), j == ic, f, r);
+            a.Fout[o] = f;
+            const float w = (j == ic) ? 0.f : f;
+            const __nv_bfloat16 wh = __float2bfloat16_rn(w);
+            a.Wh[o] = wh;
+            a.Wl[o] = __float2bfloat16_rn(w - __bfloat162float(wh));
+            const float df = f - z[i];
+            s_inc = fmaf(df, df, s_inc);
+            s_z = fmaf(z[i], z[i], s_z);
+            s_r = fmaf(r, r, s_r);
+          }
+        }
+      }
+      tc_fence_before();
+      mbar_arrive(&ctl->tempty[acc]);
+      if (++acc == 2) {
+        acc = 0;
+        acc_phase ^= 1u;
+      }
+    }
+    const double b0 = warp_sum((double)s_inc), b1 = warp_sum((double)s_z),
+                 b2 = warp_sum((double)s_r);
+    if (lane == 0) {
+      atomicAdd(&a.st->acc_inc2, b0);
+      atomicAdd(&a.st->acc_z2, b1);
+      atomicAdd(&a.st->acc_r2, b2);
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(TMEM_COLS)
+                 : "memory");
+}
+
+// ---------------------------------------------------------------- host side
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
+// 2-D BF16 row-major [outer x inner] tensor, box [box_outer x 64], 128-byte swizzle.
+bool make_map(CUtensorMap* m, const void* base, uint64_t inner, uint64_t outer,
+              uint32_t box_outer) {
+  EncodeTiledFn enc = encode_fn();
+  if (!enc) return false;
+  cuuint64_t dims[2] = {inner, outer};
+  cuuint64_t strides[1] = {inner * 2};
+  cuuint32_t box[2] = {(cuuint32_t)BK, box_outer};
+  cuuint32_t estr[2] = {1, 1};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box,
+             estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+cudaError_t launch_gemm_tc(const __nv_bfloat16* Dh, const __nv_bfloat16* Dl,
+                           const __nv_bfloat16* Wh, const __nv_bfloat16* Wl,
+                           const MapArgs<float>& a, int npad, int kpad, int passes,
+                           cudaStream_t s) {
+  if (npad % BM || kpad % BN || npad % BK || (passes != 1 && passes != 3))
+    return cudaErrorInvalidValue;
+  CUtensorMap mDh, mDl, mWh, mWl;
+  if (!make_map(&mDh, Dh, npad, npad, BM) || !make_map(&mDl, Dl, npad, npad, BM) ||
+      !make_map(&mWh, Wh, npad, kpad, BN) || !make_map(&mWl, Wl, npad, kpad, BN))
+    return cudaErrorInvalidValue;
+  static int configured_device = -1;
+  static int num_sms = 0;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (configured_device != dev) {
+    e = cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    configured_device = dev;
+  }
+  const int num_m = npad / BM, num_n = kpad / BN, num_kb = npad / BK;
+  const int tiles = num_m * num_n;
+  const int grid = tiles < num_sms ? tiles : num_sms;
+  k_gemm_tc<<<grid, NUM_THREADS, SMEM_BYTES, s>>>(mDh, mDl, mWh, mWl, a, num_m, num_n, num_kb,
+                                                  passes);
+  return cudaGetLastError();
+}
+
+}  // namespace ipt

@@ -1,0 +1,239 @@
+"""Python binding of libipt (include/ipt.h): argument marshalling only.
+
+Every step of the solver runs inside libipt's CUDA kernels; this module turns
+torch tensors into pointers, sizes and dtype codes and calls the C ABI with
+ctypes.  Importing it loads ``_lib/libipt.so`` and raises ImportError when
+the library is missing: there is no fallback path.
+
+Layouts: M is row-major (n, n); Z is column-major n x k, i.e. stored as a
+(k, n) tensor whose row c is the eigenvector of column c; the functions
+return it as the (n, k) view ``Zt.T``.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import torch
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "libipt.so")
+if not os.path.exists(_LIB_PATH):
+    raise ImportError(f"libipt.so is not built ({_LIB_PATH}); run __graft_entry__.build() first")
+_lib = C.CDLL(_LIB_PATH)
+
+MAX_HISTORY = 128
+
+STATUS = {0: "OK", 1: "MAXITER", 2: "DIVERGED", 3: "DEGENERATE_THETA", 4: "INVALID_ARG",
+          5: "CUDA_ERROR", 6: "DEVICE_TIMEOUT", 7: "UNSUPPORTED"}
+PRECISION = {"f64": 0, "f32": 1, "bf16": 2, "bf16x3": 3, "staged": 4}
+PRECISION_NAME = {v: k for k, v in PRECISION.items()}
+STOP = {"increment": 0, "residual": 1}
+DTYPE = {torch.float64: 0, torch.float32: 1}
+
+
+class Options(C.Structure):
+    _fields_ = [("precision", C.c_int), ("stop", C.c_int), ("diverge_bound", C.c_double),
+                ("stage_switch", C.c_double), ("verify_fp64", C.c_int), ("z0", C.c_void_p)]
+
+
+class Result(C.Structure):
+    _fields_ = [("status", C.c_int), ("iterations", C.c_int), ("stage_iters", C.c_int * 2),
+                ("increment", C.c_double), ("rho", C.c_double), ("rho_fp64", C.c_double),
+                ("r0", C.c_double), ("history_len", C.c_int),
+                ("hist_increment", C.c_double * MAX_HISTORY),
+                ("hist_rho", C.c_double * MAX_HISTORY),
+                ("hist_stage", C.c_int * MAX_HISTORY)]
+
+    def to_dict(self) -> dict:
+        h = self.history_len
+        return {"status": STATUS.get(self.status, str(self.status)), "status_code": self.status,
+                "iterations": self.iterations, "stage_iters": list(self.stage_iters),
+                "increment": self.increment, "rho": self.rho, "rho_fp64": self.rho_fp64,
+                "r0": self.r0, "hist_increment": list(self.hist_increment[:h]),
+                "hist_rho": list(self.hist_rho[:h]),
+                "hist_stage": [PRECISION_NAME.get(s, s) for s in self.hist_stage[:h]]}
+
+
+_vp, _i64, _i32, _d = C.c_void_p, C.c_int64, C.c_int, C.c_double
+_lib.ipt_options_default.argtypes = [C.POINTER(Options)]
+_lib.ipt_options_default.restype = None
+_lib.ipt_status_string.argtypes = [_i32]
+_lib.ipt_status_string.restype = C.c_char_p
+_lib.ipt_create.argtypes = [C.POINTER(_vp), _vp]
+_lib.ipt_create.restype = _i32
+_lib.ipt_destroy.argtypes = [_vp]
+_lib.ipt_destroy.restype = _i32
+_SOLVE_ARGS = [_vp, _i64, _vp, _i64, _i32, _vp, _i64, _vp, _d, _i32, C.POINTER(Options), _vp, _vp,
+               _i64, _i32, C.POINTER(Result)]
+_lib.ipt_solve_dense.argtypes = _SOLVE_ARGS
+_lib.ipt_solve_dense.restype = _i32
+_lib.ipt_solve_dense_host.argtypes = _SOLVE_ARGS
+_lib.ipt_solve_dense_host.restype = _i32
+_lib.ipt_step_dense.argtypes = [_vp, _i64, _vp, _i64, _i32, _vp, _i64, _vp, _i32, _vp, _vp, _i64,
+                                _i32, _vp, C.POINTER(_d)]
+_lib.ipt_step_dense.restype = _i32
+_lib.ipt_solve_csr.argtypes = [_vp, _i64, _i64, _vp, _vp, _vp, _i32, _vp, _i64, _vp, _d, _i32,
+                               C.POINTER(Options), _vp, _vp, _i64, _i32, C.POINTER(Result)]
+_lib.ipt_solve_csr.restype = _i32
+
+LIB_PATH = _LIB_PATH
+lib = _lib
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _dev(t, dtype=None, name="tensor"):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        t = t.to(dtype)
+    return t.contiguous()
+
+
+def make_options(precision="staged", stop="residual", diverge_bound=1e8, stage_switch=1e-4,
+                 verify_fp64=False, z0=None) -> Options:
+    o = Options()
+    _lib.ipt_options_default(C.byref(o))
+    o.precision = PRECISION[precision] if isinstance(precision, str) else int(precision)
+    o.stop = STOP[stop] if isinstance(stop, str) else int(stop)
+    o.diverge_bound = diverge_bound
+    o.stage_switch = stage_switch
+    o.verify_fp64 = 1 if verify_fp64 else 0
+    o.z0 = None if z0 is None else z0.data_ptr()
+    return o
+
+
+class Solver:
+    """A libipt handle bound to a CUDA stream (default: torch's current stream)."""
+
+    def __init__(self, stream: torch.cuda.Stream | None = None):
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        h = C.c_void_p()
+        st = _lib.ipt_create(C.byref(h), C.c_void_p(self.stream.cuda_stream))
+        if st != 0:
+            raise RuntimeError(f"ipt_create failed: {STATUS.get(st, st)}")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _lib.ipt_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------------ dense
+    def solve_dense(self, M, theta=None, cols=None, tol=1e-6, max_iter=100, precision="staged",
+                    stop="residual", z_dtype=torch.float32, verify_fp64=False, z0=None,
+                    diverge_bound=1e8, stage_switch=1e-4):
+        """Alg. 2 / Alg. 1 on the GPU.  Returns (lam [k] f64, Z (n, k) view, info dict)."""
+        M = _dev(M, name="M")
+        n = M.shape[0]
+        if M.dim() != 2 or M.shape[1] != n or M.dtype not in DTYPE:
+            raise ValueError("M must be a square float32/float64 CUDA matrix")
+        theta = _dev(theta, torch.float64, "theta")
+        cols = _dev(cols, torch.int32, "cols")
+        k = n if cols is None else cols.numel()
+        lam = torch.empty(k, dtype=torch.float64, device=M.device)
+        Zt = torch.empty((k, n), dtype=z_dtype, device=M.device)
+        if z0 is not None:
+            z0 = _dev(z0, z_dtype, "z0")
+            z0t = z0.t().contiguous() if z0.shape == (n, k) else z0
+        else:
+            z0t = None
+        o = make_options(precision, stop, diverge_bound, stage_switch, verify_fp64, z0t)
+        r = Result()
+        _lib.ipt_solve_dense(self._h, n, _ptr(M), M.stride(0), DTYPE[M.dtype], _ptr(theta), k,
+                             _ptr(cols), float(tol), int(max_iter), C.byref(o), _ptr(lam),
+                             _ptr(Zt), n, DTYPE[z_dtype], C.byref(r))
+        return lam, Zt.t(), r.to_dict()
+
+    def solve_dense_host(self, M, theta=None, cols=None, tol=1e-6, max_iter=100,
+                         precision="staged", stop="residual", z_dtype=torch.float32,
+                         lam_out=None, zt_out=None):
+        """The same solve from host tensors (pinned for speed); copies are inside the call."""
+        if M.is_cuda:
+            raise ValueError("solve_dense_host takes host tensors")
+        M = M.contiguous()
+        n = M.shape[0]
+        theta = None if theta is None else theta.to(torch.float64).contiguous()
+        cols = None if cols is None else cols.to(torch.int32).contiguous()
+        k = n if cols is None else cols.numel()
+        lam = lam_out if lam_out is not None else torch.empty(k, dtype=torch.float64)
+        Zt = zt_out if zt_out is not None else torch.empty((k, n), dtype=z_dtype)
+        o = make_options(precision, stop)
+        r = Result()
+        _lib.ipt_solve_dense_host(self._h, n, _ptr(M), M.stride(0), DTYPE[M.dtype], _ptr(theta),
+                                  k, _ptr(cols), float(tol), int(max_iter), C.byref(o), _ptr(lam),
+                                  _ptr(Zt), n, DTYPE[Zt.dtype], C.byref(r))
+        return lam, Zt.t(), r.to_dict()
+
+    def step_dense(self, M, Z, theta=None, cols=None, precision="f32"):
+        """One evaluation of F (Eq. dyn) at Z (n, k).  Returns (F (n, k), lam, norms)."""
+        M = _dev(M, name="M")
+        n = M.shape[0]
+        theta = _dev(theta, torch.float64, "theta")
+        cols = _dev(cols, torch.int32, "cols")
+        k = n if cols is None else cols.numel()
+        Zt = _dev(Z, name="Z").t().contiguous()
+        Ft = torch.empty_like(Zt)
+        lam = torch.empty(k, dtype=torch.float64, device=M.device)
+        norms = (C.c_double * 3)()
+        p = PRECISION[precision] if isinstance(precision, str) else int(precision)
+        st = _lib.ipt_step_dense(self._h, n, _ptr(M), M.stride(0), DTYPE[M.dtype], _ptr(theta), k,
+                                 _ptr(cols), p, _ptr(Zt), _ptr(Ft), n, DTYPE[Zt.dtype], _ptr(lam),
+                                 norms)
+        if st != 0:
+            raise RuntimeError(f"ipt_step_dense: {STATUS.get(st, st)}")
+        return Ft.t(), lam, {"increment_abs": norms[0], "z_norm": norms[1],
+                             "residual_abs": norms[2]}
+
+    # ------------------------------------------------------------------ sparse
+    def solve_csr(self, rowptr, colind, vals, n, theta=None, cols=None, tol=1e-6, max_iter=100,
+                  precision="f32", stop="residual", z_dtype=torch.float32, diverge_bound=1e8):
+        """Sparse M (CSR, all stored entries of M).  Returns (lam, Z (n, k) view, info)."""
+        rowptr = _dev(rowptr, torch.int32, "rowptr")
+        colind = _dev(colind, torch.int32, "colind")
+        vals = _dev(vals, name="vals")
+        theta = _dev(theta, torch.float64, "theta")
+        cols = _dev(cols, torch.int32, "cols")
+        k = n if cols is None else cols.numel()
+        lam = torch.empty(k, dtype=torch.float64, device=vals.device)
+        Zt = torch.empty((k, n), dtype=z_dtype, device=vals.device)
+        o = make_options(precision, stop, diverge_bound)
+        r = Result()
+        _lib.ipt_solve_csr(self._h, n, colind.numel(), _ptr(rowptr), _ptr(colind), _ptr(vals),
+                           DTYPE[vals.dtype], _ptr(theta), k, _ptr(cols), float(tol),
+                           int(max_iter), C.byref(o), _ptr(lam), _ptr(Zt), n, DTYPE[z_dtype],
+                           C.byref(r))
+        return lam, Zt.t(), r.to_dict()
+
+
+_default: Solver | None = None
+
+
+def default_solver() -> Solver:
+    global _default
+    if _default is None:
+        _default = Solver()
+    return _default
+
+
+def solve_dense(M, **kw):
+    return default_solver().solve_dense(M, **kw)
+
+
+def step_dense(M, Z, **kw):
+    return default_solver().step_dense(M, Z, **kw)
+
+
+def solve_csr(rowptr, colind, vals, n, **kw):
+    return default_solver().solve_csr(rowptr, colind, vals, n, **kw)

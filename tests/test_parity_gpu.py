@@ -1,0 +1,250 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Tolerances.  FP64 results follow the benchmark spec's 1e-10 relative eigenvalue
+error.  For the FP32 / tensor-core forms the eigenvalue tolerance is 1e-5
+relative and the stopping residual is rho <= 1e-6; single-step tolerances
+come from the arithmetic of the product P = Delta Z (see each test).
+"""
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2012_14702_gb300 import workloads as w
+
+pytestmark = pytest.mark.gpu
+
+
+def cuda(x, dtype=torch.float64):
+    return torch.as_tensor(np.ascontiguousarray(x), dtype=dtype, device="cuda")
+
+
+def rel_max(a, b, scale):
+    return float(np.max(np.abs(np.asarray(a) - np.asarray(b))) / scale)
+
+
+def near_fixed_point_z(n, cols, seed, amp=1e-2):
+    g = w.rng(seed)
+    Z = g.standard_normal((n, len(cols))) * amp
+    Z[cols, np.arange(len(cols))] = 1.0
+    return Z
+
+
+# ------------------------------------------------------------------ one evaluation of F
+# F - E = G o (Z d - P); an error e in P moves F by G e.  Error model per
+# precision (u = unit roundoff, W = Z - E, entries |W| ~ amp):
+#   f64     P to ~n u64 |Delta||Z|            -> 1e-12 of max|F - E|
+#   f32     P to ~sqrt(n) u32 |Delta||Z|       -> 2e-5
+#   bf16    Delta W to 2^-8 relative (Delta E exact)  -> 2^-8 |W|sqrt(n) ~ 1e-2 at amp 1e-2
+#   bf16x3  Delta W to ~3 * 2^-17 relative     -> 2e-5
+STEP_TOL = {"f64": 1e-12, "f32": 2e-5, "bf16": 1e-2, "bf16x3": 2e-5}
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32", "bf16", "bf16x3"])
+@pytest.mark.parametrize("n,k", [(255, 255), (300, 37), (130, 1)])
+def test_single_step_matches_oracle_map(ipt, precision, n, k):
+    M, th = w.dense_symmetric(n, 0.02, seed=n + k, theta_step=0.5)
+    g = w.rng(7)
+    cols = np.arange(n) if k == n else g.permutation(n)[:k].astype(np.int32)
+    Delta, _ = oracle.partition(M, th)
+    Z = near_fixed_point_z(n, cols, seed=3)
+    F, P, d = oracle.ipt_map(Delta, th, cols, Z)
+    lam_or = th[cols] + d
+    zdt = torch.float64 if precision == "f64" else torch.float32
+    Fg, lam, norms = ipt.Solver().step_dense(cuda(M), cuda(Z, zdt), theta=cuda(th),
+                                             cols=None if k == n else cuda(cols, torch.int32),
+                                             precision=precision)
+    Fg = Fg.double().cpu().numpy()
+    E = oracle.unit_columns(n, cols)
+    scale = np.max(np.abs(F - E))
+    assert rel_max(Fg, F, scale) <= STEP_TOL[precision]
+    assert np.all(Fg[cols, np.arange(k)] == 1.0)
+    assert rel_max(lam.cpu().numpy(), lam_or, np.max(np.abs(lam_or))) <= 1e-10
+    # norms of the step: ||F - Z||, ||Z||, ||M Z - Z Lambda||
+    R = oracle.residual(M, Z, lam_or)
+    np.testing.assert_allclose(norms["z_norm"], np.linalg.norm(Z), rtol=1e-6)
+    np.testing.assert_allclose(norms["increment_abs"], np.linalg.norm(F - Z),
+                               rtol=max(1e-6, 10 * STEP_TOL[precision]))
+    np.testing.assert_allclose(norms["residual_abs"], np.linalg.norm(R),
+                               rtol=max(1e-6, 10 * STEP_TOL[precision]))
+
+
+# ------------------------------------------------------------------ full solves
+def test_small_fp64_config_matches_oracle(ipt):
+    """n = 256, theta_i = i, Delta N(0,1)*0.02, FP64, increment tol 1e-12."""
+    M, th = w.dense_symmetric(256, 0.02, seed=1)
+    ref = oracle.ipt_solve(M, th, tol=1e-12, max_iter=200, history=True)
+    lam, Z, info = ipt.Solver().solve_dense(cuda(M), tol=1e-12, max_iter=200, precision="f64",
+                                            stop="increment", z_dtype=torch.float64,
+                                            verify_fp64=True)
+    assert info["status"] == "OK" and ref["status"] == oracle.OK
+    assert info["iterations"] == ref["iterations"]
+    lam = lam.cpu().numpy()
+    assert np.max(np.abs(lam - ref["lam"]) / np.abs(ref["lam"])) <= 1e-10
+    assert np.max(np.abs(Z.cpu().numpy() - ref["Z"])) <= 1e-10
+    np.testing.assert_allclose(info["hist_increment"], ref["inc_hist"], rtol=1e-6, atol=1e-15)
+    assert info["rho_fp64"] <= 1e-9
+
+
+@pytest.mark.parametrize("precision", ["staged", "f32", "bf16x3"])
+@pytest.mark.parametrize("n", [1000, 385])
+def test_solve_to_residual_matches_converged_oracle(ipt, precision, n):
+    """Dense full spectrum shaped like the large workload (theta_i = i/8,
+    Delta N(0,1)*1e-3), ragged n: the GPU result at rho <= 1e-6 against the
+    FP64 oracle converged to 1e-13."""
+    M, th = w.dense_symmetric(n, 1e-3, seed=22, theta_step=0.125)
+    ref = oracle.ipt_solve(M, th, tol=1e-13, max_iter=200)
+    assert ref["status"] == oracle.OK
+    lam, Z, info = ipt.Solver().solve_dense(cuda(M, torch.float32), theta=cuda(th), tol=1e-6,
+                                            max_iter=50, precision=precision, stop="residual",
+                                            verify_fp64=True)
+    assert info["status"] == "OK", info
+    assert info["rho"] <= 1e-6
+    assert info["rho_fp64"] <= 1.2e-6, info["rho_fp64"]
+    lam = lam.cpu().numpy()
+    assert np.max(np.abs(lam - ref["lam"]) / np.abs(ref["lam"])) <= 1e-5
+    E = np.eye(n)
+    err = np.linalg.norm(Z.double().cpu().numpy() - ref["Z"]) / np.linalg.norm(ref["Z"] - E)
+    assert err <= 1e-4, err
+    if precision == "staged":
+        assert info["stage_iters"][0] >= 1 and info["stage_iters"][1] >= 1
+        assert info["hist_stage"][0] == "bf16" and info["hist_stage"][-1] == "bf16x3"
+
+
+def test_partial_spectrum_dense_permuted_columns(ipt):
+    n, k = 300, 37
+    M, th = w.dense_symmetric(n, 2e-3, seed=5, theta_step=0.25)
+    cols = w.rng(1).permutation(n)[:k].astype(np.int32)
+    ref = oracle.ipt_solve(M, th, cols=cols, tol=1e-13, max_iter=200)
+    for precision in ["f64", "f32", "staged"]:
+        lam, Z, info = ipt.Solver().solve_dense(cuda(M), theta=cuda(th),
+                                                cols=cuda(cols, torch.int32), tol=1e-7,
+                                                max_iter=60, precision=precision,
+                                                verify_fp64=True)
+        assert info["status"] == "OK", (precision, info)
+        assert np.max(np.abs(lam.cpu().numpy() - ref["lam"]) / np.abs(ref["lam"])) <= 1e-5
+        assert np.max(np.abs(Z.double().cpu().numpy() - ref["Z"])) <= 1e-5
+
+
+def test_fixed_iteration_count_f64_matches_oracle_iterates(ipt):
+    """MAXITER semantics: after max_iter evaluations both return the last
+    evaluated iterate Z^(max_iter - 1) and its eigenvalue estimate."""
+    M, th = w.dense_symmetric(200, 0.05, seed=9)
+    for it in [1, 2, 5]:
+        ref = oracle.ipt_solve(M, th, tol=0.0, max_iter=it, history=True)
+        lam, Z, info = ipt.Solver().solve_dense(cuda(M), tol=0.0, max_iter=it, precision="f64",
+                                                stop="increment", z_dtype=torch.float64)
+        assert info["status"] == "MAXITER" and info["iterations"] == it
+        assert np.max(np.abs(Z.cpu().numpy() - ref["Z"])) <= 1e-13
+        assert np.max(np.abs(lam.cpu().numpy() - ref["lam"])) <= 1e-12
+        np.testing.assert_allclose(info["hist_increment"], ref["inc_hist"], rtol=1e-10)
+
+
+# ------------------------------------------------------------------ special cases
+def test_two_by_two_closed_form(ipt):
+    for eps in [0.3, -0.6]:
+        M, th = w.two_by_two(eps)
+        lam, Z, info = ipt.Solver().solve_dense(cuda(M), tol=1e-14, max_iter=500, precision="f64",
+                                                stop="increment", z_dtype=torch.float64)
+        s = np.sqrt(1 + 4 * eps * eps)
+        np.testing.assert_allclose(lam.cpu().numpy(), [(1 - s) / 2, (1 + s) / 2], atol=1e-12)
+
+
+def test_one_by_one_and_diagonal(ipt):
+    lam, Z, info = ipt.Solver().solve_dense(cuda(np.array([[3.5]])), precision="f64",
+                                            z_dtype=torch.float64)
+    assert info["status"] == "OK" and info["iterations"] == 1
+    assert lam.item() == 3.5 and Z.item() == 1.0
+    th = np.array([4.0, -1.0, 2.0, 9.0, 0.5])
+    for precision in ["f64", "f32", "staged"]:
+        lam, Z, info = ipt.Solver().solve_dense(cuda(np.diag(th)), precision=precision, tol=1e-12)
+        assert info["status"] == "OK" and info["iterations"] <= 2, (precision, info)
+        assert np.array_equal(Z.double().cpu().numpy(), np.eye(5))
+        assert np.array_equal(lam.cpu().numpy(), th)
+
+
+def test_argument_errors_are_statuses(ipt):
+    s = ipt.Solver()
+    th = np.array([1.0, 2.0, 2.0, 4.0])
+    M = np.diag(th) + 0.01
+    _, _, info = s.solve_dense(cuda(M), precision="f64")
+    assert info["status"] == "DEGENERATE_THETA"
+    _, _, info = s.solve_dense(cuda(M), cols=cuda([0, 3], torch.int32), precision="f64",
+                               tol=1e-10)
+    assert info["status"] == "OK"
+    _, _, info = s.solve_dense(cuda(M), cols=cuda([0, 0], torch.int32), precision="f64")
+    assert info["status"] == "INVALID_ARG"
+    _, _, info = s.solve_dense(cuda(M), cols=cuda([0, 7], torch.int32), precision="f32")
+    assert info["status"] == "INVALID_ARG"
+    _, _, info = s.solve_dense(cuda(M), theta=cuda([1.0, np.nan, 3.0, 4.0]),
+                               cols=cuda([0], torch.int32), precision="f64")
+    assert info["status"] == "DEGENERATE_THETA"
+    Mn = np.diag([1.0, 2.0, 3.0, 4.0]) + 0.01
+    Mn[0, 3] = np.nan
+    for precision in ["f64", "f32", "staged"]:
+        _, _, info = s.solve_dense(cuda(Mn), precision=precision)
+        assert info["status"] == "DIVERGED", (precision, info)
+
+
+def test_divergence_and_cycle_statuses(ipt):
+    s = ipt.Solver()
+    M, th = w.two_by_two(3.0)
+    _, _, info = s.solve_dense(cuda(M), precision="f64", max_iter=100, stop="increment",
+                               z_dtype=torch.float64)
+    assert info["status"] == "DIVERGED"
+    M, th = w.two_by_two(0.87)
+    _, _, info = s.solve_dense(cuda(M), precision="f64", max_iter=300, stop="increment",
+                               tol=1e-12, z_dtype=torch.float64)
+    assert info["status"] == "MAXITER"
+
+
+def test_host_entry_point_matches_device_entry_point(ipt):
+    M, th = w.dense_symmetric(600, 1e-3, seed=4, theta_step=0.125)
+    Mt = torch.as_tensor(M, dtype=torch.float32).pin_memory()
+    s = ipt.Solver()
+    lam_h, Z_h, info_h = s.solve_dense_host(Mt, tol=1e-6, max_iter=50)
+    lam_d, Z_d, info_d = s.solve_dense(Mt.cuda(), tol=1e-6, max_iter=50)
+    assert info_h["status"] == info_d["status"] == "OK"
+    assert info_h["iterations"] == info_d["iterations"]
+    assert torch.equal(lam_h, lam_d.cpu()) and torch.equal(Z_h, Z_d.cpu())
+
+
+def test_warm_start_from_converged_solution(ipt):
+    M, th = w.dense_symmetric(400, 1e-3, seed=6, theta_step=0.125)
+    s = ipt.Solver()
+    lam, Z, info = s.solve_dense(cuda(M), tol=1e-7, max_iter=50, precision="f32")
+    assert info["status"] == "OK"
+    lam2, Z2, info2 = s.solve_dense(cuda(M), tol=1e-6, max_iter=50, precision="f32",
+                                    z0=Z.contiguous())
+    assert info2["status"] == "OK" and info2["iterations"] == 1
+    # a rescaled warm start is renormalised to z_{i_c} = 1
+    lam3, Z3, info3 = s.solve_dense(cuda(M), tol=1e-6, max_iter=50, precision="f32",
+                                    z0=(Z * 3.0).contiguous())
+    assert info3["iterations"] == 1
+    assert torch.allclose(Z3, Z, rtol=1e-6, atol=1e-7)
+
+
+# ------------------------------------------------------------------ full size, sampled
+def test_n8192_staged_sampled_columns_match_oracle(ipt):
+    """The benchmark workload (n = 8192, theta_i = i/8, Delta N(0,1)*1e-3) in
+    the benchmark's launch configuration; the oracle solves 48 sampled columns
+    (Alg. 1 per column, FP64) and the GPU's full-spectrum result must match
+    them.  The FP64 residual of the whole GPU result is recomputed on the GPU."""
+    n = 8192
+    M, th = w.dense_symmetric(n, 1e-3, seed=22, theta_step=0.125)
+    Mg = cuda(M, torch.float32)
+    lam, Z, info = ipt.Solver().solve_dense(Mg, theta=cuda(th), tol=1e-6, max_iter=40,
+                                            precision="staged", verify_fp64=True)
+    assert info["status"] == "OK", info
+    assert info["rho_fp64"] <= 1.2e-6, info
+    sample = np.sort(w.rng(99).choice(n, 48, replace=False)).astype(np.int64)
+    sample = np.concatenate([[0, n - 1], sample])
+    ref = oracle.ipt_solve(M, th, cols=sample, tol=1e-12, max_iter=100)
+    assert ref["status"] == oracle.OK
+    lam_s = lam.cpu().numpy()[sample]
+    assert np.max(np.abs(lam_s - ref["lam"]) / np.abs(ref["lam"])) <= 1e-5
+    Zs = Z[:, torch.as_tensor(sample, device="cuda")].double().cpu().numpy()
+    E = oracle.unit_columns(n, sample)
+    err = np.linalg.norm(Zs - ref["Z"]) / np.linalg.norm(ref["Z"] - E)
+    assert err <= 1e-4, err
