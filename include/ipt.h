@@ -52,14 +52,21 @@ typedef enum {
 /* Element types of inputs and outputs. */
 typedef enum { IPT_DTYPE_F64 = 0, IPT_DTYPE_F32 = 1 } ipt_dtype;
 
-/* Arithmetic of the product Delta Z (the dominant step, Section 4.2). */
+/* Arithmetic of the product Delta Z (the dominant step, Section 4.2).
+ * Tensor-core forms split Z = E + W (E = unit columns) and add the Delta E
+ * term exactly in FP32, so only Delta W is rounded; operands carry a
+ * power-of-two scale per row of Delta and per column of W (exact, undone in
+ * the epilogue) so FP16's 5-bit exponent never overflows. */
 typedef enum {
   IPT_PREC_F64 = 0,    /* FP64 product and iterate (CUDA cores)                        */
-  IPT_PREC_F32 = 1,    /* plain FP32: FP32 product and iterate (CUDA cores)            */
+  IPT_PREC_F32 = 1,    /* plain FP32: FP32 FMA product of Delta W, FP32 iterate         */
   IPT_PREC_BF16 = 2,   /* BF16 tensor-core product (tcgen05), FP32 accumulate/iterate  */
   IPT_PREC_BF16X3 = 3, /* split-BF16 x3 tensor-core product (hi*hi + hi*lo + lo*hi)    */
-  IPT_PREC_STAGED = 4  /* BF16 until the residual stops improving, then BF16 x3;
-                          only the BF16 x3 stage may declare convergence              */
+  IPT_PREC_STAGED = 4, /* FP16 until the residual stops improving, then FP16 x3 (BF16 /
+                          BF16 x3 with ipt_options.staged_bf16); only the x3 stage may
+                          declare convergence                                         */
+  IPT_PREC_FP16 = 5,   /* FP16 tensor-core product, FP32 accumulate/iterate            */
+  IPT_PREC_FP16X3 = 6  /* split-FP16 x3 tensor-core product                            */
 } ipt_precision;
 
 /* Stopping test. */
@@ -73,10 +80,13 @@ typedef struct {
   int precision;        /* ipt_precision; default IPT_PREC_STAGED                          */
   int stop;             /* ipt_stop; default IPT_STOP_RESIDUAL                             */
   double diverge_bound; /* IPT_DIVERGED when ||Z||_F > diverge_bound*sqrt(k); default 1e8  */
-  double stage_switch;  /* STAGED: leave BF16 once the predicted next residual is below
-                           this; default 1e-4                                              */
+  double stage_switch;  /* STAGED: leave the 1-pass stage once the predicted next residual
+                           is below this; default 1e-4                                     */
+  int staged_bf16;      /* STAGED: nonzero = BF16 / BF16 x3 stages instead of FP16 / FP16 x3 */
   int verify_fp64;      /* nonzero: recompute ||M Z - Z Lambda||_F of the result in FP64
                            (result.rho_fp64); adds one FP64 product                        */
+  int record_timing;    /* nonzero: time the pre-pass and product kernels with CUDA events
+                           on the handle's stream (result.*_ms)                            */
   const void* z0;       /* optional warm start (device, Z layout, dtype = z_dtype);
                            column c is rescaled so that z0[cols[c], c] = 1                 */
 } ipt_options;
@@ -86,12 +96,17 @@ typedef struct {
 typedef struct {
   int status;           /* ipt_status                                                     */
   int iterations;       /* evaluations of F (products with Delta)                         */
-  int stage_iters[2];   /* STAGED: evaluations in the BF16 and in the BF16 x3 stage       */
+  int stage_iters[2];   /* evaluations in the 1-pass (FP16/BF16) stage and in the others  */
   double increment;     /* ||F(Z) - Z||_F / ||Z||_F at the returned Z                     */
   double rho;           /* relative residual of the returned pair, in the product's
                            arithmetic                                                     */
   double rho_fp64;      /* same, recomputed in FP64 (verify_fp64), else -1                */
   double r0;            /* ||M Z0 - Z0 Lambda0||_F, the residual normaliser               */
+  int kernel_launches;  /* CUDA kernels this call launched                                */
+  int product_launches[2]; /* product kernel launches: [0] 1-pass (FP16/BF16/FP32/FP64),
+                              [1] 3-pass (FP16 x3 / BF16 x3)                             */
+  double product_ms[2]; /* their summed device time (record_timing), else 0               */
+  double prepass_ms;    /* summed device time of the D(Delta Z) / operand-split pre-pass  */
   int history_len;      /* min(iterations, IPT_MAX_HISTORY)                               */
   double hist_increment[IPT_MAX_HISTORY];
   double hist_rho[IPT_MAX_HISTORY];

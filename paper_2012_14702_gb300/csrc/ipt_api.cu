@@ -36,11 +36,13 @@ cudaError_t ensure(Buf& b, size_t bytes) {
 struct ipt_handle {
   cudaStream_t s = nullptr;
   int dev = 0;
-  Buf drow, dt, dh, dl, z[2], wh[2], wl[2];
+  Buf drow, dt, dh, dl, z[2], wh, wl, rinv, sinv;
   Buf theta, thh, thl, icol, count, d, st;
   Buf m64, z64, racc;
   Buf hM, hTheta, hCols, hLam, hZ;  // device staging of the host-buffer entry point
   DevState* hst = nullptr;          // pinned mirror of the controller's words
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // pre-pass / product brackets
+  int launches = 0;                 // kernels launched by the current call
 };
 
 namespace {
@@ -67,14 +69,21 @@ struct DeviceGuard {
 inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
 inline bool tensor_core(int prec) {
-  return prec == IPT_PREC_BF16 || prec == IPT_PREC_BF16X3 || prec == IPT_PREC_STAGED;
+  return prec == IPT_PREC_BF16 || prec == IPT_PREC_BF16X3 || prec == IPT_PREC_STAGED ||
+         prec == IPT_PREC_FP16 || prec == IPT_PREC_FP16X3;
+}
+inline bool bf16_operands(int prec, bool staged_bf16) {
+  return prec == IPT_PREC_BF16 || prec == IPT_PREC_BF16X3 ||
+         (prec == IPT_PREC_STAGED && staged_bf16);
 }
 
 // Problem geometry and buffer plan for one dense solve / step.
 struct Plan {
   int n, k, npad, kpad, prec;
-  bool f64;  // FP64 iterate and product
-  bool tc;   // tensor-core buffers
+  bool f64;   // FP64 iterate and product
+  bool tc;    // tensor-core buffers
+  bool bf16;  // tensor-core operands are BF16 (else FP16)
+  bool dt;    // column-major FP32 Delta (W-form epilogues)
 };
 
 ipt_status check_dense_args(ipt_handle* h, int64_t n, const void* M, int64_t ldm, int m_dtype,
@@ -83,7 +92,7 @@ ipt_status check_dense_args(ipt_handle* h, int64_t n, const void* M, int64_t ldm
   if (n < 1 || n > (1 << 20) || k < 1 || k > n || ldm < n || ldz < n) return IPT_INVALID_ARG;
   if (m_dtype != IPT_DTYPE_F64 && m_dtype != IPT_DTYPE_F32) return IPT_INVALID_ARG;
   if (z_dtype != IPT_DTYPE_F64 && z_dtype != IPT_DTYPE_F32) return IPT_INVALID_ARG;
-  if (prec < IPT_PREC_F64 || prec > IPT_PREC_STAGED) return IPT_INVALID_ARG;
+  if (prec < IPT_PREC_F64 || prec > IPT_PREC_FP16X3) return IPT_INVALID_ARG;
   return IPT_OK;
 }
 
@@ -93,14 +102,14 @@ ipt_status alloc_dense(ipt_handle* h, const Plan& p) {
   CK(ensure(h->drow, nn * ez));
   CK(ensure(h->z[0], kn * ez));
   CK(ensure(h->z[1], kn * ez));
+  if (p.dt) CK(ensure(h->dt, nn * 4));
   if (p.tc) {
-    CK(ensure(h->dt, nn * 4));
     CK(ensure(h->dh, nn * 2));
     CK(ensure(h->dl, nn * 2));
-    for (int b = 0; b < 2; ++b) {
-      CK(ensure(h->wh[b], kn * 2));
-      CK(ensure(h->wl[b], kn * 2));
-    }
+    CK(ensure(h->wh, kn * 2));
+    CK(ensure(h->wl, kn * 2));
+    CK(ensure(h->rinv, (size_t)p.npad * 4));
+    CK(ensure(h->sinv, (size_t)p.kpad * 4));
   }
   CK(ensure(h->theta, (size_t)p.npad * 8));
   CK(ensure(h->thh, (size_t)p.npad * 4));
@@ -140,6 +149,7 @@ ipt_status setup_dense(ipt_handle* h, const Plan& p, const void* M, int64_t ldm,
                (float*)h->thl.p, s);
   launch_validate(cols, p.n, p.k, p.kpad, (const double*)h->theta.p, (int32_t*)h->icol.p,
                   (int*)h->count.p, st, s);
+  h->launches += 3;
   CK(cudaGetLastError());
   CK(cudaMemcpyAsync(h->hst, st, kStateHead, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
@@ -148,15 +158,21 @@ ipt_status setup_dense(ipt_handle* h, const Plan& p, const void* M, int64_t ldm,
 
   launch_form_delta(M, ldm, m_dtype, (const double*)h->theta.p, p.n, p.npad,
                     (const int*)h->count.p, h->drow.p, p.f64 ? 1 : 0,
-                    p.tc ? (float*)h->dt.p : nullptr,
-                    p.tc ? (__nv_bfloat16*)h->dh.p : nullptr,
-                    p.tc ? (__nv_bfloat16*)h->dl.p : nullptr, st, s);
+                    p.dt ? (float*)h->dt.p : nullptr, st, s);
+  h->launches += 2;  // form_delta + init/copy of Z below
+  if (p.tc) {
+    launch_split_delta((const float*)h->drow.p, p.npad, p.bf16 ? 1 : 0, (uint16_t*)h->dh.p,
+                       (uint16_t*)h->dl.p, (float*)h->rinv.p, s);
+    h->launches += 1;
+    // padding columns of the W operand stay zero (the pre-pass skips them)
+    const size_t pad = (size_t)(p.kpad - p.k) * p.npad * 2;
+    if (pad) {
+      CK(cudaMemsetAsync((char*)h->wh.p + (size_t)p.k * p.npad * 2, 0, pad, s));
+      CK(cudaMemsetAsync((char*)h->wl.p + (size_t)p.k * p.npad * 2, 0, pad, s));
+    }
+  }
   const size_t kn = (size_t)p.kpad * p.npad;
   CK(cudaMemsetAsync(h->z[1].p, 0, kn * (p.f64 ? 8 : 4), s));
-  if (p.tc) {
-    CK(cudaMemsetAsync(h->wh[1].p, 0, kn * 2, s));
-    CK(cudaMemsetAsync(h->wl[1].p, 0, kn * 2, s));
-  }
   if (z0 && !rescale) {
     // exact copy (single evaluation at a caller-given Z)
     CK(cudaMemsetAsync(h->z[0].p, 0, kn * (p.f64 ? 8 : 4), s));
@@ -166,9 +182,6 @@ ipt_status setup_dense(ipt_handle* h, const Plan& p, const void* M, int64_t ldm,
     launch_init_z(z0, ldz0, z0_dtype, (const int32_t*)h->icol.p, p.n, p.k, p.npad, p.kpad,
                   h->z[0].p, p.f64 ? 1 : 0, st, s);
   }
-  if (p.tc)
-    launch_split_w((const float*)h->z[0].p, (const int32_t*)h->icol.p, p.npad, p.kpad,
-                   (__nv_bfloat16*)h->wh[0].p, (__nv_bfloat16*)h->wl[0].p, s);
   CK(cudaGetLastError());
   if (z0) {
     CK(cudaMemcpyAsync(h->hst, st, kStateHead, cudaMemcpyDeviceToHost, s));
@@ -179,14 +192,32 @@ ipt_status setup_dense(ipt_handle* h, const Plan& p, const void* M, int64_t ldm,
   return IPT_OK;
 }
 
+struct Timing {
+  bool on = false;
+  double product_ms[2] = {0.0, 0.0};
+  int product_launches[2] = {0, 0};
+  double prepass_ms = 0.0;
+};
+
+ipt_status ensure_events(ipt_handle* h) {
+  for (int i = 0; i < 4; ++i)
+    if (!h->ev[i]) CK(cudaEventCreate(&h->ev[i]));
+  return IPT_OK;
+}
+
 // One evaluation at Z buffer `cur` in arithmetic `stage`: d, product, map.
-ipt_status evaluate(ipt_handle* h, const Plan& p, int cur, int stage) {
+// With timing on, the pre-pass and the product are bracketed by events on the
+// handle's stream; collect_timing() reads them after the stream is synchronised.
+ipt_status evaluate(ipt_handle* h, const Plan& p, int cur, int stage, Timing* tm) {
   cudaStream_t s = h->s;
   DevState* st = dst(h);
-  launch_prepass(h->drow.p, h->z[cur].p, p.f64 ? 1 : 0, p.npad, (const int32_t*)h->icol.p,
-                 p.kpad, (double*)h->d.p, st, s);
   const int nxt = cur ^ 1;
+  const bool t = tm && tm->on;
+  if (t) CK(cudaEventRecord(h->ev[0], s));
   if (p.f64) {
+    launch_prepass(h->drow.p, h->z[cur].p, 1, p.npad, (const int32_t*)h->icol.p, p.kpad,
+                   (double*)h->d.p, st, s);
+    if (t) CK(cudaEventRecord(h->ev[1], s));
     MapArgs<double> a{};
     a.Zin = (const double*)h->z[cur].p;
     a.Fout = (double*)h->z[nxt].p;
@@ -197,11 +228,13 @@ ipt_status evaluate(ipt_handle* h, const Plan& p, int cur, int stage) {
     a.n = p.n;
     a.k = p.k;
     a.st = st;
+    if (t) CK(cudaEventRecord(h->ev[2], s));
     launch_gemm_simt_f64((const double*)h->drow.p, a, p.npad, p.kpad, s);
   } else {
     MapArgs<float> a{};
     a.Zin = (const float*)h->z[cur].p;
     a.Fout = (float*)h->z[nxt].p;
+    a.DT = (const float*)h->dt.p;
     a.d = (const double*)h->d.p;
     a.icol = (const int32_t*)h->icol.p;
     a.th_hi = (const float*)h->thh.p;
@@ -211,21 +244,48 @@ ipt_status evaluate(ipt_handle* h, const Plan& p, int cur, int stage) {
     a.k = p.k;
     a.st = st;
     if (stage == IPT_PREC_F32) {
+      launch_prepass(h->drow.p, h->z[cur].p, 0, p.npad, (const int32_t*)h->icol.p, p.kpad,
+                     (double*)h->d.p, st, s);
+      if (t) CK(cudaEventRecord(h->ev[1], s));
+      if (t) CK(cudaEventRecord(h->ev[2], s));
       launch_gemm_simt_f32((const float*)h->drow.p, a, p.npad, p.kpad, s);
     } else {
-      a.Wh = (__nv_bfloat16*)h->wh[nxt].p;
-      a.Wl = (__nv_bfloat16*)h->wl[nxt].p;
-      a.DT = (const float*)h->dt.p;
-      CK(launch_gemm_tc((const __nv_bfloat16*)h->dh.p, (const __nv_bfloat16*)h->dl.p,
-                        (const __nv_bfloat16*)h->wh[cur].p, (const __nv_bfloat16*)h->wl[cur].p,
-                        a, p.npad, p.kpad, stage == IPT_PREC_BF16X3 ? 3 : 1, s));
+      launch_prepass_tc((const float*)h->drow.p, (const float*)h->z[cur].p, p.npad,
+                        (const int32_t*)h->icol.p, p.kpad, p.bf16 ? 1 : 0, (double*)h->d.p,
+                        (uint16_t*)h->wh.p, (uint16_t*)h->wl.p, (float*)h->sinv.p, st, s);
+      if (t) CK(cudaEventRecord(h->ev[1], s));
+      a.rinv = (const float*)h->rinv.p;
+      a.sinv = (const float*)h->sinv.p;
+      const int passes = (stage == IPT_PREC_BF16X3 || stage == IPT_PREC_FP16X3) ? 3 : 1;
+      if (t) CK(cudaEventRecord(h->ev[2], s));
+      CK(launch_gemm_tc((const uint16_t*)h->dh.p, (const uint16_t*)h->dl.p,
+                        (const uint16_t*)h->wh.p, (const uint16_t*)h->wl.p, a, p.npad, p.kpad,
+                        passes, p.bf16 ? 1 : 0, s));
     }
   }
   CK(cudaGetLastError());
+  if (t) CK(cudaEventRecord(h->ev[3], s));
+  h->launches += 2;
   return IPT_OK;
 }
 
-void fill_result(const DevState& hs, ipt_result* out) {
+// After the stream is synchronised: add this evaluation's event times.
+void collect_timing(ipt_handle* h, int stage, Timing* tm) {
+  if (!tm || !tm->on) return;
+  float a = 0.f, b = 0.f;
+  if (cudaEventElapsedTime(&a, h->ev[0], h->ev[1]) == cudaSuccess) tm->prepass_ms += a;
+  const int slot = (stage == IPT_PREC_BF16X3 || stage == IPT_PREC_FP16X3) ? 1 : 0;
+  if (cudaEventElapsedTime(&b, h->ev[2], h->ev[3]) == cudaSuccess) tm->product_ms[slot] += b;
+  tm->product_launches[slot] += 1;
+}
+
+void fill_result(const DevState& hs, const Timing& tm, int launches, ipt_result* out) {
+  out->kernel_launches = launches;
+  for (int i = 0; i < 2; ++i) {
+    out->product_launches[i] = tm.product_launches[i];
+    out->product_ms[i] = tm.product_ms[i];
+  }
+  out->prepass_ms = tm.prepass_ms;
   out->status = hs.status;
   out->iterations = hs.iter;
   out->stage_iters[0] = hs.stage_iters[0];
@@ -254,6 +314,7 @@ ipt_status verify_fp64(ipt_handle* h, const Plan& p, const void* M, int64_t ldm,
   CK(cudaMemsetAsync(h->racc.p, 0, 8, s));
   launch_residual_f64((const double*)h->m64.p, (const double*)h->z64.p, p.npad, lambda, p.n, p.k,
                       p.npad, p.kpad, (double*)h->racc.p, s);
+  h->launches += 3;
   CK(cudaGetLastError());
   double r2 = 0.0, r0 = 0.0;
   CK(cudaMemcpyAsync(&r2, h->racc.p, 8, cudaMemcpyDeviceToHost, s));
@@ -263,7 +324,7 @@ ipt_status verify_fp64(ipt_handle* h, const Plan& p, const void* M, int64_t ldm,
   return IPT_OK;
 }
 
-Plan make_plan(int64_t n, int64_t k, int prec) {
+Plan make_plan(int64_t n, int64_t k, int prec, bool staged_bf16) {
   Plan p;
   p.n = (int)n;
   p.k = (int)k;
@@ -272,6 +333,8 @@ Plan make_plan(int64_t n, int64_t k, int prec) {
   p.prec = prec;
   p.f64 = prec == IPT_PREC_F64;
   p.tc = tensor_core(prec);
+  p.bf16 = bf16_operands(prec, staged_bf16);
+  p.dt = !p.f64;
   return p;
 }
 
@@ -294,10 +357,19 @@ ipt_status solve_dense(ipt_handle* h, int64_t n, const void* M, int64_t ldm, int
     return v;
   }
   DeviceGuard g(h->dev);
-  const Plan p = make_plan(n, k, opt.precision);
+  h->launches = 0;
+  Timing tm;
+  tm.on = opt.record_timing != 0;
+  if (tm.on && ensure_events(h) != IPT_OK) {
+    out->status = IPT_CUDA_ERROR;
+    return IPT_CUDA_ERROR;
+  }
+  const Plan p = make_plan(n, k, opt.precision, opt.staged_bf16 != 0);
+  const int low = p.bf16 ? IPT_PREC_BF16 : IPT_PREC_FP16;
+  const int high = p.bf16 ? IPT_PREC_BF16X3 : IPT_PREC_FP16X3;
   v = alloc_dense(h, p);
   if (v == IPT_OK) {
-    const int first = opt.precision == IPT_PREC_STAGED ? IPT_PREC_BF16 : opt.precision;
+    const int first = opt.precision == IPT_PREC_STAGED ? low : opt.precision;
     v = setup_dense(h, p, M, ldm, m_dtype, theta, cols, opt.z0, ldz, z_dtype, true, first);
   }
   if (v != IPT_OK) {
@@ -312,18 +384,22 @@ ipt_status solve_dense(ipt_handle* h, int64_t n, const void* M, int64_t ldm, int
   ca.stop = opt.stop;
   ca.mode = opt.precision;
   ca.k = (int)k;
+  ca.low_stage = low;
+  ca.high_stage = high;
   cudaStream_t s = h->s;
   int cur = 0;
-  int stage = opt.precision == IPT_PREC_STAGED ? IPT_PREC_BF16 : opt.precision;
+  int stage = opt.precision == IPT_PREC_STAGED ? low : opt.precision;
   for (int it = 0; it < max_iter; ++it) {
-    v = evaluate(h, p, cur, stage);
+    v = evaluate(h, p, cur, stage, &tm);
     if (v != IPT_OK) break;
     launch_control(dst(h), ca, s);
+    h->launches += 1;
     if (cudaMemcpyAsync(h->hst, dst(h), kStateHead, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess) {
       v = IPT_CUDA_ERROR;
       break;
     }
+    collect_timing(h, stage, &tm);
     if (h->hst->timeout) {
       v = IPT_DEVICE_TIMEOUT;
       break;
@@ -347,11 +423,12 @@ ipt_status solve_dense(ipt_handle* h, int64_t n, const void* M, int64_t ldm, int
                 p.k, lambda, s);
   launch_copy_z(h->z[ans].p, p.f64 ? 1 : 0, p.npad, p.n, p.k, Z, ldz,
                 z_dtype == IPT_DTYPE_F64 ? 1 : 0, s);
+  h->launches += 2;
   if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) {
     out->status = IPT_CUDA_ERROR;
     return IPT_CUDA_ERROR;
   }
-  fill_result(hs, out);
+  fill_result(hs, tm, h->launches, out);
   if (opt.verify_fp64) {
     v = verify_fp64(h, p, M, ldm, m_dtype, ans, lambda, &out->rho_fp64);
     if (v != IPT_OK) {
@@ -373,7 +450,9 @@ void ipt_options_default(ipt_options* opt) {
   opt->stop = IPT_STOP_RESIDUAL;
   opt->diverge_bound = 1e8;
   opt->stage_switch = 1e-4;
+  opt->staged_bf16 = 0;
   opt->verify_fp64 = 0;
+  opt->record_timing = 0;
   opt->z0 = nullptr;
 }
 
@@ -408,12 +487,14 @@ ipt_status ipt_create(ipt_handle** h, void* stream) {
 ipt_status ipt_destroy(ipt_handle* h) {
   if (!h) return IPT_OK;
   DeviceGuard g(h->dev);
-  Buf* all[] = {&h->drow, &h->dt, &h->dh, &h->dl, &h->z[0], &h->z[1], &h->wh[0], &h->wh[1],
-                &h->wl[0], &h->wl[1], &h->theta, &h->thh, &h->thl, &h->icol, &h->count,
+  Buf* all[] = {&h->drow, &h->dt, &h->dh, &h->dl, &h->z[0], &h->z[1], &h->wh, &h->wl,
+                &h->rinv, &h->sinv, &h->theta, &h->thh, &h->thl, &h->icol, &h->count,
                 &h->d, &h->st, &h->m64, &h->z64, &h->racc, &h->hM, &h->hTheta, &h->hCols,
                 &h->hLam, &h->hZ};
   for (Buf* b : all)
     if (b->p) cudaFree(b->p);
+  for (int i = 0; i < 4; ++i)
+    if (h->ev[i]) cudaEventDestroy(h->ev[i]);
   if (h->hst) cudaFreeHost(h->hst);
   delete h;
   return IPT_OK;
@@ -478,12 +559,12 @@ ipt_status ipt_step_dense(ipt_handle* h, int64_t n, const void* M, int64_t ldm, 
   if (v != IPT_OK) return v;
   if (precision == IPT_PREC_STAGED || !Zin || !Fout || !lambda) return IPT_INVALID_ARG;
   DeviceGuard g(h->dev);
-  const Plan p = make_plan(n, k, precision);
+  const Plan p = make_plan(n, k, precision, false);
   v = alloc_dense(h, p);
   if (v != IPT_OK) return v;
   v = setup_dense(h, p, M, ldm, m_dtype, theta, cols, Zin, ldz, z_dtype, false, precision);
   if (v != IPT_OK) return v;
-  v = evaluate(h, p, 0, precision);
+  v = evaluate(h, p, 0, precision, nullptr);
   if (v != IPT_OK) return v;
   cudaStream_t s = h->s;
   launch_lambda((const double*)h->theta.p, (const int32_t*)h->icol.p, (const double*)h->d.p,

@@ -3,16 +3,19 @@
 // Data layout in device memory (npad = n rounded up to 128, kpad = k rounded
 // up to 256; every padded entry is zero so no kernel needs K-edge checks):
 //   Drow  [npad x npad] row-major Delta (FP64 in IPT_PREC_F64, else FP32)
-//   DT    [npad x npad] column-major FP32 Delta (tensor-core modes: exact
-//         Delta term of the epilogue)
-//   Dh,Dl [npad x npad] row-major BF16 split of Delta (Dh + Dl ~ Delta)
+//   DT    [npad x npad] column-major FP32 Delta (FP32 and tensor-core modes:
+//         the exact Delta E term of the epilogue, P = Delta E + Delta W)
+//   Dh,Dl [npad x npad] row-major 16-bit (FP16 or BF16) split of r_j Delta_j.,
+//         r_j a power-of-two row scale (rinv[j] = 1 / r_j)
 //   Z0,Z1 [kpad x npad] column-major iterates (FP64 or FP32), ping-pong
-//   Wh,Wl [2][kpad x npad] column-major BF16 split of W = Z - E (E = unit
-//         columns), the B operand of the tensor-core product, ping-pong
+//   Wh,Wl [kpad x npad] column-major 16-bit split of s_c W_.c, W = Z - E
+//         (E = unit columns), s_c a power-of-two column scale (sinv[c] = 1/s_c);
+//         rewritten by the pre-pass of every tensor-core evaluation
 #pragma once
 
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <stdint.h>
 
 #include "../../include/ipt.h"
@@ -59,9 +62,9 @@ template <typename T>
 struct MapArgs {
   const T* Zin;          // current iterate, column-major [kpad x npad], leading dim ld
   T* Fout;               // F(Z), same layout
-  __nv_bfloat16* Wh;     // BF16 hi of W' = F - E (tensor-core modes, else null)
-  __nv_bfloat16* Wl;     // BF16 lo of W'
-  const float* DT;       // column-major FP32 Delta (tensor-core modes, else null)
+  const float* DT;       // column-major FP32 Delta (FP32 / tensor-core modes, else null)
+  const float* rinv;     // per-row inverse operand scale (tensor-core modes)
+  const float* sinv;     // per-column inverse operand scale (tensor-core modes)
   const double* d;       // d_c = (Delta Z)_{cols[c], c}
   const int32_t* icol;   // cols[c]; -1 in padding columns
   const double* theta;   // FP64 theta (F64 path)
@@ -80,11 +83,11 @@ void launch_validate(const int32_t* cols, int n, int k, int kpad, const double* 
                      int32_t* icol, int* count, DevState* st, cudaStream_t s);
 void launch_form_delta(const void* M, int64_t ldm, int m_dtype, const double* theta, int n,
                        int npad, const int* count, void* Drow, int drow_f64, float* DT,
-                       __nv_bfloat16* Dh, __nv_bfloat16* Dl, DevState* st, cudaStream_t s);
+                       DevState* st, cudaStream_t s);
+void launch_split_delta(const float* Drow, int npad, int bf16, uint16_t* Dh, uint16_t* Dl,
+                        float* rinv, cudaStream_t s);
 void launch_init_z(const void* z0, int64_t ldz0, int z0_dtype, const int32_t* icol, int n,
                    int k, int npad, int kpad, void* Z, int z_f64, DevState* st, cudaStream_t s);
-void launch_split_w(const float* Z, const int32_t* icol, int npad, int kpad, __nv_bfloat16* Wh,
-                    __nv_bfloat16* Wl, cudaStream_t s);
 void launch_lambda(const double* theta, const int32_t* icol, const double* d, int k,
                    double* lambda, cudaStream_t s);
 void launch_copy_z(const void* Z, int z_f64, int64_t ld, int n, int k, void* out,
@@ -95,6 +98,9 @@ void launch_convert_m64(const void* M, int64_t ldm, int m_dtype, int n, int npad
 // iteration pieces (k_iter.cu)
 void launch_prepass(const void* Drow, const void* Z, int f64, int64_t ld, const int32_t* icol,
                     int kpad, double* d, DevState* st, cudaStream_t s);
+void launch_prepass_tc(const float* Drow, const float* Z, int64_t ld, const int32_t* icol,
+                       int kpad, int bf16, double* d, uint16_t* Wh, uint16_t* Wl, float* sinv,
+                       DevState* st, cudaStream_t s);
 void launch_gemm_simt_f64(const double* Drow, const MapArgs<double>& a, int npad, int kpad,
                           cudaStream_t s);
 void launch_gemm_simt_f32(const float* Drow, const MapArgs<float>& a, int npad, int kpad,
@@ -104,15 +110,16 @@ void launch_residual_f64(const double* M64, const double* Z64, int64_t ld, const
 struct ControlArgs {
   double tol, diverge_bound, stage_switch;
   int max_iter, stop, mode, k;
+  int low_stage, high_stage;  // STAGED: the 1-pass stage and the split stage it switches to
 };
 void launch_control(DevState* st, ControlArgs a, cudaStream_t s);
 
-// tensor-core product (k_tc_gemm.cu).  passes = 1 (BF16) or 3 (split BF16 x3).
-// Returns a cudaError_t of the launch or of tensor-map encoding.
-cudaError_t launch_gemm_tc(const __nv_bfloat16* Dh, const __nv_bfloat16* Dl,
-                           const __nv_bfloat16* Wh, const __nv_bfloat16* Wl,
-                           const MapArgs<float>& a, int npad, int kpad, int passes,
-                           cudaStream_t s);
+// tensor-core product (k_tc_gemm.cu).  passes = 1 (Dh Wh) or 3 (+ Dh Wl + Dl Wh);
+// bf16 selects BF16 operands, else FP16.  Returns a cudaError_t of the launch
+// or of tensor-map encoding.
+cudaError_t launch_gemm_tc(const uint16_t* Dh, const uint16_t* Dl, const uint16_t* Wh,
+                           const uint16_t* Wl, const MapArgs<float>& a, int npad, int kpad,
+                           int passes, int bf16, cudaStream_t s);
 
 // ---------------------------------------------------------------- device helpers
 __device__ __forceinline__ double warp_sum(double v) {
@@ -124,6 +131,35 @@ __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
+}
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Power-of-two operand scale s with mx * s in [2^13, 2^14): keeps scaled
+// values inside FP16's range (max 65504) with headroom; exponent clamped to
+// +-60 so products of two scales stay finite.  1 for zero / non-finite mx.
+__device__ __forceinline__ float pow2_scale(float mx) {
+  if (!(mx > 0.f) || !isfinite(mx)) return 1.f;
+  int ex;
+  frexpf(mx, &ex);
+  const int e = max(-60, min(60, 14 - ex));
+  return ldexpf(1.f, e);
+}
+
+// 16-bit hi/lo split of x: hi = rn(x), lo = rn(x - hi), as raw bits.
+__device__ __forceinline__ void split16(float x, bool bf16, uint16_t& hi, uint16_t& lo) {
+  if (bf16) {
+    const __nv_bfloat16 h = __float2bfloat16_rn(x);
+    hi = __bfloat16_as_ushort(h);
+    lo = __bfloat16_as_ushort(__float2bfloat16_rn(x - __bfloat162float(h)));
+  } else {
+    const __half h = __float2half_rn(x);
+    hi = __half_as_ushort(h);
+    lo = __half_as_ushort(__float2half_rn(x - __half2float(h)));
+  }
 }
 
 // theta_j - theta_i from the two-float split (hi + lo = theta to ~2^-48

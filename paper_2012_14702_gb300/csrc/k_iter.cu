@@ -3,6 +3,8 @@
 //  k_prepass     d_c = (Delta Z)_{cols[c], c}: the diagonal D(Delta Z) of
 //                Eq. (dyn), computed before the product so that every tile of
 //                the product can apply the map in its epilogue.
+//  k_prepass_tc  the same, plus the tensor-core B operand: W = Z - E scaled by
+//                a power of two per column and split into 16-bit hi + lo.
 //  k_gemm_simt   P = Delta Z (FP64 or FP32 FMA) with the fused epilogue
 //                F = E + G o (Z D(Delta Z) - P) and the norm partials of the
 //                stopping test (Alg. 2) and of the residual.
@@ -61,12 +63,163 @@ __global__ void k_prepass(const T* __restrict__ Drow, const T* __restrict__ Z, i
   if (lane == 0) d[c] = tot;
 }
 
+// One warp per column c: d_c as in k_prepass (compensated FP32 per lane,
+// FP64 across lanes) and max |W_.c|; then W_.c * s_c split into hi/lo
+// (the column is re-read from cache).  Padding columns only get d = 0.
+template <bool BF16>
+__global__ void k_prepass_tc(const float* __restrict__ Drow, const float* __restrict__ Z,
+                             int64_t ld, const int32_t* __restrict__ icol, int kpad,
+                             double* __restrict__ d, uint16_t* __restrict__ Wh,
+                             uint16_t* __restrict__ Wl, float* __restrict__ sinv,
+                             const DevState* st) {
+  if (st->done) return;
+  const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (c >= kpad) return;
+  const int i = icol[c];
+  if (i < 0) {
+    if (lane == 0) {
+      d[c] = 0.0;
+      sinv[c] = 1.f;
+    }
+    return;
+  }
+  const float4* a4 = reinterpret_cast<const float4*>(Drow + (int64_t)i * ld);
+  const float4* z4 = reinterpret_cast<const float4*>(Z + (int64_t)c * ld);
+  float s = 0.f, comp = 0.f, mx = 0.f;
+  for (int m = lane; m < ld / 4; m += 32) {
+    const float4 x = __ldg(a4 + m);
+    float4 y = z4[m];
+    const float y0 = x.x * y.x + x.y * y.y + x.z * y.z + x.w * y.w;
+    const float yy = y0 - comp;
+    const float t = s + yy;
+    comp = (t - s) - yy;
+    s = t;
+    const int off = i - 4 * m;  // the unit entry of E in this float4, if any
+    if (off == 0) y.x -= 1.f;
+    if (off == 1) y.y -= 1.f;
+    if (off == 2) y.z -= 1.f;
+    if (off == 3) y.w -= 1.f;
+    mx = fmaxf(mx, fmaxf(fmaxf(fabsf(y.x), fabsf(y.y)), fmaxf(fabsf(y.z), fabsf(y.w))));
+  }
+  const double tot = warp_sum((double)s - (double)comp);
+  mx = warp_max(mx);
+  const float sc = pow2_scale(mx);
+  uint2* h2 = reinterpret_cast<uint2*>(Wh + (int64_t)c * ld);
+  uint2* l2 = reinterpret_cast<uint2*>(Wl + (int64_t)c * ld);
+  for (int m = lane; m < ld / 4; m += 32) {
+    float4 y = z4[m];
+    const int off = i - 4 * m;
+    if (off == 0) y.x -= 1.f;
+    if (off == 1) y.y -= 1.f;
+    if (off == 2) y.z -= 1.f;
+    if (off == 3) y.w -= 1.f;
+    uint16_t h[4], l[4];
+    split16(y.x * sc, BF16, h[0], l[0]);
+    split16(y.y * sc, BF16, h[1], l[1]);
+    split16(y.z * sc, BF16, h[2], l[2]);
+    split16(y.w * sc, BF16, h[3], l[3]);
+    h2[m] = make_uint2(h[0] | ((uint32_t)h[1] << 16), h[2] | ((uint32_t)h[3] << 16));
+    l2[m] = make_uint2(l[0] | ((uint32_t)l[1] << 16), l[2] | ((uint32_t)l[3] << 16));
+  }
+  if (lane == 0) {
+    d[c] = tot;
+    sinv[c] = 1.f / sc;
+  }
+}
+
+// The same pre-pass with the column held in registers: one CTA per column,
+// each thread owns up to VPT float4 slots of it, so Z is read from memory
+// once (the two-pass warp kernel above re-reads the column, which at n = 8192
+// no longer fits in L1/L2 between its passes).  Used when npad <= 4*VPT*1024.
+template <bool BF16, int VPT>
+__global__ void __launch_bounds__(1024)
+    k_prepass_tc_reg(const float* __restrict__ Drow, const float* __restrict__ Z, int64_t ld,
+                     const int32_t* __restrict__ icol, double* __restrict__ d,
+                     uint16_t* __restrict__ Wh, uint16_t* __restrict__ Wl,
+                     float* __restrict__ sinv, const DevState* st) {
+  if (st->done) return;
+  const int c = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int nw = blockDim.x >> 5;
+  const int i = icol[c];
+  if (i < 0) {
+    if (tid == 0) {
+      d[c] = 0.0;
+      sinv[c] = 1.f;
+    }
+    return;
+  }
+  const int n4 = (int)(ld / 4);
+  const float4* a4 = reinterpret_cast<const float4*>(Drow + (int64_t)i * ld);
+  const float4* z4 = reinterpret_cast<const float4*>(Z + (int64_t)c * ld);
+  float4 y[VPT];
+  float s = 0.f, comp = 0.f, mx = 0.f;
+#pragma unroll
+  for (int q = 0; q < VPT; ++q) {
+    const int m = tid + q * blockDim.x;
+    y[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (m < n4) {
+      const float4 x = __ldg(a4 + m);
+      y[q] = __ldg(z4 + m);
+      const float y0 = x.x * y[q].x + x.y * y[q].y + x.z * y[q].z + x.w * y[q].w;
+      const float yy = y0 - comp;
+      const float t = s + yy;
+      comp = (t - s) - yy;
+      s = t;
+      const int off = i - 4 * m;  // the unit entry of E in this float4, if any
+      if (off == 0) y[q].x -= 1.f;
+      if (off == 1) y[q].y -= 1.f;
+      if (off == 2) y[q].z -= 1.f;
+      if (off == 3) y[q].w -= 1.f;
+      mx = fmaxf(mx, fmaxf(fmaxf(fabsf(y[q].x), fabsf(y[q].y)),
+                           fmaxf(fabsf(y[q].z), fabsf(y[q].w))));
+    }
+  }
+  __shared__ double rs[32];
+  __shared__ float rm[32];
+  const double ws = warp_sum((double)s - (double)comp);
+  const float wm = warp_max(mx);
+  if (lane == 0) {
+    rs[wid] = ws;
+    rm[wid] = wm;
+  }
+  __syncthreads();
+  double tot = 0.0;
+  float cmax = 0.f;
+  for (int w = 0; w < nw; ++w) {
+    tot += rs[w];
+    cmax = fmaxf(cmax, rm[w]);
+  }
+  const float sc = pow2_scale(cmax);
+  uint2* h2 = reinterpret_cast<uint2*>(Wh + (int64_t)c * ld);
+  uint2* l2 = reinterpret_cast<uint2*>(Wl + (int64_t)c * ld);
+#pragma unroll
+  for (int q = 0; q < VPT; ++q) {
+    const int m = tid + q * blockDim.x;
+    if (m < n4) {
+      uint16_t h[4], l[4];
+      split16(y[q].x * sc, BF16, h[0], l[0]);
+      split16(y[q].y * sc, BF16, h[1], l[1]);
+      split16(y[q].z * sc, BF16, h[2], l[2]);
+      split16(y[q].w * sc, BF16, h[3], l[3]);
+      h2[m] = make_uint2(h[0] | ((uint32_t)h[1] << 16), h[2] | ((uint32_t)h[3] << 16));
+      l2[m] = make_uint2(l[0] | ((uint32_t)l[1] << 16), l[2] | ((uint32_t)l[3] << 16));
+    }
+  }
+  if (tid == 0) {
+    d[c] = tot;
+    sinv[c] = 1.f / sc;
+  }
+}
+
 // ---------------------------------------------------------------- SIMT product + map
 // Tile BM x BN x BK, 256 threads as 16 (rows) x 16 (cols); each thread owns
 // TM x TN outputs in two halves: rows tm*HM + [0, HM) and BM/2 + tm*HM + [0, HM)
 // (likewise for columns), so a thread's rows are contiguous in the
 // column-major iterate and the epilogue loads/stores vectors along j.
 // A = Delta row-major (lda = ld), B = Z column-major (K = rows contiguous).
+// FP32 (WFORM): B = W = Z - E (the unit entry is subtracted as the tile is
+// loaded) and the epilogue adds the exact column Delta_{., cols[c]} from the
+// column-major copy DT, so the FP32 accumulators carry only Delta W.
 enum { EPI_MAP = 0, EPI_RESIDUAL = 1 };
 
 template <typename T>
@@ -89,6 +242,7 @@ __global__ void __launch_bounds__(256)
   constexpr int LPR = BK / VEC;                // loads per tile row
   static_assert(BM * BK == 256 * VEC && BN * BK == 256 * VEC, "one vector load per thread");
   using V = typename Vec<T>::V4;
+  constexpr bool WFORM = (EPI == EPI_MAP) && sizeof(T) == 4;
   if constexpr (EPI == EPI_MAP) {
     if (a.st->done) return;
   }
@@ -108,7 +262,20 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
     for (int j = 0; j < TN; ++j) acc[i][j] = T(0);
 
+  // column this thread loads, and the row of its unit entry (W-form)
+  const int ic_load = WFORM ? a.icol[c0 + lr] : -1;
   V ra = *reinterpret_cast<const V*>(Ap), rb = *reinterpret_cast<const V*>(Bp);
+  auto unit = [&](int k0) {
+    if constexpr (WFORM) {
+      const int off = ic_load - (k0 + lk);
+      float4& v = reinterpret_cast<float4&>(rb);
+      v.x -= off == 0 ? 1.f : 0.f;
+      v.y -= off == 1 ? 1.f : 0.f;
+      v.z -= off == 2 ? 1.f : 0.f;
+      v.w -= off == 3 ? 1.f : 0.f;
+    }
+  };
+  unit(0);
   auto stash = [&](int buf) {
     const T* pa = reinterpret_cast<const T*>(&ra);
     const T* pb = reinterpret_cast<const T*>(&rb);
@@ -126,6 +293,7 @@ __global__ void __launch_bounds__(256)
     if (kt + 1 < KT) {
       ra = *reinterpret_cast<const V*>(Ap + (kt + 1) * BK);
       rb = *reinterpret_cast<const V*>(Bp + (kt + 1) * BK);
+      unit((kt + 1) * BK);
     }
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
@@ -167,15 +335,20 @@ __global__ void __launch_bounds__(256)
     for (int h = 0; h < 2; ++h) {
       const int jb = m0 + (h == 0 ? tm * HM : BM / 2 + tm * HM);
       const int64_t o = (int64_t)c * ld + jb;
-      T z[HM], f[HM];
+      T z[HM], f[HM], dcol[HM];
       *reinterpret_cast<V*>(z) = *reinterpret_cast<const V*>(a.Zin + o);
+      if constexpr (WFORM) {
+        *reinterpret_cast<V*>(dcol) =
+            *reinterpret_cast<const V*>(a.DT + (int64_t)ic * ld + jb);
+      }
       if constexpr (HM * sizeof(T) == 32) {
         *reinterpret_cast<V*>(z + VEC) = *reinterpret_cast<const V*>(a.Zin + o + VEC);
       }
 #pragma unroll
       for (int q = 0; q < HM; ++q) {
         const int j = jb + q;
-        const T p = acc[h * HM + q][jj];
+        T p = acc[h * HM + q][jj];
+        if constexpr (WFORM) p += dcol[q];
         f[q] = z[q];
         if (j >= a.n) continue;
         if constexpr (EPI == EPI_MAP) {
@@ -248,7 +421,7 @@ __global__ void k_control(DevState* st, ControlArgs a) {
     st->hist_rho[it] = rho;
     st->hist_stage[it] = stage;
   }
-  if (stage == IPT_PREC_BF16 && a.mode == IPT_PREC_STAGED) st->stage_iters[0]++;
+  if (stage == IPT_PREC_BF16 || stage == IPT_PREC_FP16) st->stage_iters[0]++;
   else st->stage_iters[1]++;
   st->inc = inc;
   st->rho = rho;
@@ -257,12 +430,12 @@ __global__ void k_control(DevState* st, ControlArgs a) {
   st->acc_z2 = 0.0;
   st->acc_r2 = 0.0;
   const double test = a.stop == IPT_STOP_INCREMENT ? inc : rho;
-  const bool staged_bf16 = (a.mode == IPT_PREC_STAGED && stage == IPT_PREC_BF16);
+  const bool staged_low = (a.mode == IPT_PREC_STAGED && stage == a.low_stage);
   if (!isfinite(inc) || !isfinite(rho) || sqrt(z2) > a.diverge_bound * sqrt((double)a.k)) {
     st->status = IPT_DIVERGED;
     st->done = 1;
     st->answer = st->cur;
-  } else if (!staged_bf16 && test <= a.tol) {
+  } else if (!staged_low && test <= a.tol) {
     st->status = IPT_OK;
     st->done = 1;
     st->answer = st->cur;
@@ -271,14 +444,14 @@ __global__ void k_control(DevState* st, ControlArgs a) {
     st->done = 1;
     st->answer = st->cur;
   } else {
-    if (staged_bf16) {
-      // Leave BF16 once the geometric prediction of the next residual falls
-      // under the switch level, once BF16 stops contracting, or once the test
-      // is already met (only the accurate stage may confirm it).
+    if (staged_low) {
+      // Leave the 1-pass stage once the geometric prediction of the next
+      // residual falls under the switch level, once it stops contracting, or
+      // once the test is already met (only the split stage may confirm it).
       const double prev = st->prev_rho;
       const double q = (it > 0 && prev > 0.0) ? rho / prev : 1.0;
       if (test <= a.tol || rho * q < a.stage_switch || (it > 0 && q > 0.5))
-        st->stage = IPT_PREC_BF16X3;
+        st->stage = a.high_stage;
     }
     st->cur ^= 1;
   }
@@ -296,6 +469,28 @@ void launch_prepass(const void* Drow, const void* Z, int f64, int64_t ld, const 
   else
     k_prepass<float><<<g, 256, 0, s>>>((const float*)Drow, (const float*)Z, ld, icol, kpad, d,
                                        st);
+}
+
+void launch_prepass_tc(const float* Drow, const float* Z, int64_t ld, const int32_t* icol,
+                       int kpad, int bf16, double* d, uint16_t* Wh, uint16_t* Wl, float* sinv,
+                       DevState* st, cudaStream_t s) {
+  constexpr int VPT = 8;
+  const int64_t n4 = ld / 4;
+  if (n4 <= (int64_t)VPT * 1024) {
+    int threads = (int)((n4 + VPT - 1) / VPT);
+    threads = ((threads + 31) / 32) * 32;
+    if (bf16)
+      k_prepass_tc_reg<true, VPT><<<kpad, threads, 0, s>>>(Drow, Z, ld, icol, d, Wh, Wl, sinv, st);
+    else
+      k_prepass_tc_reg<false, VPT><<<kpad, threads, 0, s>>>(Drow, Z, ld, icol, d, Wh, Wl, sinv,
+                                                             st);
+    return;
+  }
+  unsigned g = (unsigned)((kpad + 7) / 8);
+  if (bf16)
+    k_prepass_tc<true><<<g, 256, 0, s>>>(Drow, Z, ld, icol, kpad, d, Wh, Wl, sinv, st);
+  else
+    k_prepass_tc<false><<<g, 256, 0, s>>>(Drow, Z, ld, icol, kpad, d, Wh, Wl, sinv, st);
 }
 
 void launch_gemm_simt_f64(const double* Drow, const MapArgs<double>& a, int npad, int kpad,

@@ -72,13 +72,12 @@ __global__ void k_theta_check(const double* theta, const int32_t* icol, const in
 }
 
 // Delta = M - diag(theta), formed in FP64 before any rounding, then stored
-// as FP64/FP32 row-major, FP32 column-major (transposed through shared
-// memory) and the BF16 hi/lo split.  Also sums the squared off-diagonal
-// entries of the requested columns (the residual normaliser ||R0||^2).
-// Block 32x8 threads, tile 32x32.
+// as FP64/FP32 row-major and (optionally) FP32 column-major, transposed
+// through shared memory.  Also sums the squared off-diagonal entries of the
+// requested columns (the residual normaliser ||R0||^2).  Block 32x8, tile 32x32.
 __global__ void k_form_delta(const void* M, int64_t ldm, int m_dtype, const double* theta, int n,
                              int npad, const int* count, void* Drow, int drow_f64, float* DT,
-                             __nv_bfloat16* Dh, __nv_bfloat16* Dl, DevState* st) {
+                             DevState* st) {
   __shared__ float tile[32][33];
   int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
   int tx = threadIdx.x, ty = threadIdx.y;
@@ -94,12 +93,6 @@ __global__ void k_form_delta(const void* M, int64_t ldm, int m_dtype, const doub
     int64_t o = (int64_t)i * npad + j;
     if (drow_f64) static_cast<double*>(Drow)[o] = v;
     else static_cast<float*>(Drow)[o] = (float)v;
-    if (Dh) {
-      float vf = (float)v;
-      __nv_bfloat16 h = __float2bfloat16_rn(vf);
-      Dh[o] = h;
-      Dl[o] = __float2bfloat16_rn(vf - __bfloat162float(h));
-    }
     tile[ty + 8 * q][tx] = (float)v;
   }
   if (DT) {
@@ -111,6 +104,37 @@ __global__ void k_form_delta(const void* M, int64_t ldm, int m_dtype, const doub
   }
   r0sum = warp_sum(r0sum);
   if (tx == 0 && r0sum != 0.0) atomicAdd(&st->r0acc, r0sum);
+}
+
+// Tensor-core A operand: row j of Delta scaled by the power of two r_j that
+// brings its largest entry into [2^13, 2^14), split into 16-bit hi + lo.
+// One warp per row (all npad rows; padding rows are zero).
+__global__ void k_split_delta(const float* __restrict__ Drow, int npad, int bf16,
+                              uint16_t* __restrict__ Dh, uint16_t* __restrict__ Dl,
+                              float* __restrict__ rinv) {
+  const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (row >= npad) return;
+  const float4* a = reinterpret_cast<const float4*>(Drow + (int64_t)row * npad);
+  float mx = 0.f;
+  for (int m = lane; m < npad / 4; m += 32) {
+    const float4 x = a[m];
+    mx = fmaxf(mx, fmaxf(fmaxf(fabsf(x.x), fabsf(x.y)), fmaxf(fabsf(x.z), fabsf(x.w))));
+  }
+  mx = warp_max(mx);
+  const float sc = pow2_scale(mx);
+  uint2* h2 = reinterpret_cast<uint2*>(Dh + (int64_t)row * npad);
+  uint2* l2 = reinterpret_cast<uint2*>(Dl + (int64_t)row * npad);
+  for (int m = lane; m < npad / 4; m += 32) {
+    const float4 x = a[m];
+    uint16_t h[4], l[4];
+    split16(x.x * sc, bf16, h[0], l[0]);
+    split16(x.y * sc, bf16, h[1], l[1]);
+    split16(x.z * sc, bf16, h[2], l[2]);
+    split16(x.w * sc, bf16, h[3], l[3]);
+    h2[m] = make_uint2(h[0] | ((uint32_t)h[1] << 16), h[2] | ((uint32_t)h[3] << 16));
+    l2[m] = make_uint2(l[0] | ((uint32_t)l[1] << 16), l[2] | ((uint32_t)l[3] << 16));
+  }
+  if (lane == 0) rinv[row] = 1.f / sc;
 }
 
 // Z = unit columns E (or the rescaled warm start), padding zero.
@@ -136,18 +160,6 @@ __global__ void k_init_z(const void* z0, int64_t ldz0, int z0_dtype, const int32
     }
   }
   Z[idx] = (TZ)z;
-}
-
-// BF16 hi/lo split of W = Z - E, the tensor-core B operand.
-__global__ void k_split_w(const float* Z, const int32_t* icol, int npad, int kpad,
-                          __nv_bfloat16* Wh, __nv_bfloat16* Wl) {
-  int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (int64_t)kpad * npad) return;
-  int c = (int)(idx / npad), j = (int)(idx % npad);
-  float w = Z[idx] - (j == icol[c] ? 1.f : 0.f);
-  __nv_bfloat16 h = __float2bfloat16_rn(w);
-  Wh[idx] = h;
-  Wl[idx] = __float2bfloat16_rn(w - __bfloat162float(h));
 }
 
 // Lambda_c = theta_{i_c} + d_c (Alg. 2: Lambda = D(M Z), Z_{i_c, c} = 1).
@@ -192,10 +204,14 @@ void launch_validate(const int32_t* cols, int n, int k, int kpad, const double* 
 
 void launch_form_delta(const void* M, int64_t ldm, int m_dtype, const double* theta, int n,
                        int npad, const int* count, void* Drow, int drow_f64, float* DT,
-                       __nv_bfloat16* Dh, __nv_bfloat16* Dl, DevState* st, cudaStream_t s) {
+                       DevState* st, cudaStream_t s) {
   dim3 g(npad / 32, npad / 32), b(32, 8);
-  k_form_delta<<<g, b, 0, s>>>(M, ldm, m_dtype, theta, n, npad, count, Drow, drow_f64, DT, Dh,
-                               Dl, st);
+  k_form_delta<<<g, b, 0, s>>>(M, ldm, m_dtype, theta, n, npad, count, Drow, drow_f64, DT, st);
+}
+
+void launch_split_delta(const float* Drow, int npad, int bf16, uint16_t* Dh, uint16_t* Dl,
+                        float* rinv, cudaStream_t s) {
+  k_split_delta<<<(unsigned)((npad + 7) / 8), 256, 0, s>>>(Drow, npad, bf16, Dh, Dl, rinv);
 }
 
 void launch_init_z(const void* z0, int64_t ldz0, int z0_dtype, const int32_t* icol, int n,
@@ -207,11 +223,6 @@ void launch_init_z(const void* z0, int64_t ldz0, int z0_dtype, const int32_t* ic
   else
     k_init_z<float><<<blocks(total, 256), 256, 0, s>>>(z0, ldz0, z0_dtype, icol, n, k, npad,
                                                        kpad, (float*)Z, st);
-}
-
-void launch_split_w(const float* Z, const int32_t* icol, int npad, int kpad, __nv_bfloat16* Wh,
-                    __nv_bfloat16* Wl, cudaStream_t s) {
-  k_split_w<<<blocks((int64_t)kpad * npad, 256), 256, 0, s>>>(Z, icol, npad, kpad, Wh, Wl);
 }
 
 void launch_lambda(const double* theta, const int32_t* icol, const double* d, int k,

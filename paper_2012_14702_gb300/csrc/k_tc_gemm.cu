@@ -4,13 +4,17 @@
 // Product.  The identity part of Z is split off, Z = E + W (E = unit columns,
 // W_{cols[c], c} = 0), so P = Delta E + Delta W: the first term is the
 // column cols[c] of Delta, added exactly in FP32 by the epilogue; only
-// Delta W goes through the tensor cores, as BF16 (passes = 1: Dh Wh) or
-// split BF16 x3 (passes = 3: Dh Wh + Dh Wl + Dl Wh), FP32 accumulation in
-// TMEM.  Because |W| << 1 near the fixed point, the BF16 rounding error is
-// scaled by |W| instead of by |Z| ~ 1.
+// Delta W goes through the tensor cores.  Operands are 16-bit (FP16, or BF16)
+// hi/lo splits of r_j Delta_j. and s_c W_.c with power-of-two scales r_j, s_c
+// (the pre-pass and the setup write them), so
+//   passes = 1:  P~ = Dh Wh                      (FP16: ~2^-11 relative)
+//   passes = 3:  P~ = Dh Wh + Dh Wl + Dl Wh      (FP16: ~2^-22 relative)
+// accumulated in FP32 in TMEM, and Delta W = P~ / (r_j s_c) exactly.  Because
+// |W| << 1 near the fixed point, the rounding error is scaled by |W| instead of
+// by |Z| ~ 1.
 //
 // Kernel shape: persistent, one CTA per SM, 192 threads.
-//   warp 0      TMA producer: 128x64 A tiles and 256x64 B tiles (BF16,
+//   warp 0      TMA producer: 128x64 A tiles and 256x64 B tiles (16-bit,
 //               128-byte swizzle) into a 4-stage shared-memory ring
 //   warp 1      TMEM allocator and single-thread tcgen05.mma issuer,
 //               M=128 N=256 K=16 per instruction, two 256-column
@@ -18,8 +22,8 @@
 //               overlaps the product of tile t+1
 //   warps 2..5  epilogue: tcgen05.ld 32 columns at a time, the map
 //               F = E + G o (Z D(Delta Z) - P), the residual
-//               R = (theta_j - theta_i) Z - (Z d - P), writes F (FP32) and the
-//               BF16 split of W' = F - E for the next product, norm partials.
+//               R = (theta_j - theta_i) Z - (Z d - P), writes F (FP32) and
+//               the norm partials of the stopping test.
 // Every mbarrier wait is bounded (globaltimer); on expiry the CTA records a
 // timeout in DevState, drains its TMA loads and MMAs, frees TMEM and returns.
 #include "ipt_internal.cuh"
@@ -40,6 +44,15 @@ constexpr int EPI_THREADS = 128;
 constexpr uint64_t kTimeoutNs = 2000000000ull;  // 2 s: far above any legitimate wait
 constexpr int GROUP_M = 16;                      // row blocks per L2 raster group
 
+// Order of the three split products in one accumulator.  The two correction
+// products (Dh Wl, Dl Wh; ~2^-11 of the total) go first, into a still-small
+// accumulator, and the main product Dh Wh last: adding ~1000 tiny partial
+// sums into an accumulator that already holds the whole product would round
+// each of them against the large value.
+#ifndef IPT_CORRECTIONS_FIRST
+#define IPT_CORRECTIONS_FIRST 1
+#endif
+
 struct Ctl {
   uint64_t full[STAGES];
   uint64_t empty[STAGES];
@@ -51,11 +64,13 @@ struct Ctl {
 };
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + (int)sizeof(Ctl) + 64;
 
-// Instruction descriptor, kind::f16: D = F32 (bits 4-5 = 1), A = B = BF16
-// (bits 7-9, 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at bit 17,
-// M >> 4 at bit 24.
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) |
-                            ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+// Instruction descriptor, kind::f16: D = F32 (bits 4-5 = 1), A and B both
+// FP16 (0) or both BF16 (1) at bits 7-9 / 10-12, both K-major (bits 15, 16 =
+// 0), N >> 3 at bit 17, M >> 4 at bit 24.
+constexpr uint32_t idesc_for(bool bf16) {
+  return (1u << 4) | ((bf16 ? 1u : 0u) << 7) | ((bf16 ? 1u : 0u) << 10) |
+         ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+}
 
 __device__ __forceinline__ uint32_t su32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -129,12 +144,13 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
   return d;
 }
 
-__device__ __forceinline__ void mma_bf16(uint32_t dt, uint64_t ad, uint64_t bd, uint32_t acc) {
+__device__ __forceinline__ void mma_f16(uint32_t dt, uint64_t ad, uint64_t bd, uint32_t idesc,
+                                        uint32_t acc) {
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
       "setp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dt),
-      "l"(ad), "l"(bd), "r"(kIdesc), "r"(acc)
+      "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
       : "memory");
 }
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
@@ -183,7 +199,7 @@ __device__ __forceinline__ void fail(Ctl* ctl, DevState* st, int code) {
 __global__ void __launch_bounds__(NUM_THREADS, 1)
     k_gemm_tc(const __grid_constant__ CUtensorMap tmDh, const __grid_constant__ CUtensorMap tmDl,
               const __grid_constant__ CUtensorMap tmWh, const __grid_constant__ CUtensorMap tmWl,
-              MapArgs<float> a, int num_m, int num_n, int num_kb, int passes) {
+              MapArgs<float> a, int num_m, int num_n, int num_kb, int passes, uint32_t idesc) {
   if (a.st->done) return;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>(
@@ -240,10 +256,13 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
           }
           const int pass = kb / num_kb;
           const int kx = (kb - pass * num_kb) * BK;
+          // passes = 1: Dh Wh.  passes = 3: (Dh Wl, Dl Wh, Dh Wh), or with the
+          // main product first (Dh Wh, Dh Wl, Dl Wh).
+          const int role = passes == 1 ? 0 : (IPT_CORRECTIONS_FIRST ? (pass + 1) % 3 : pass);
           mbar_expect_tx(&ctl->full[stage], STAGE_BYTES);
-          tma_load(sA + stage * A_BYTES, pass == 2 ? &tmDl : &tmDh, &ctl->full[stage], kx,
+          tma_load(sA + stage * A_BYTES, role == 2 ? &tmDl : &tmDh, &ctl->full[stage], kx,
                    mb * BM);
-          tma_load(sB + stage * B_BYTES, pass == 1 ? &tmWl : &tmWh, &ctl->full[stage], kx,
+          tma_load(sB + stage * B_BYTES, role == 1 ? &tmWl : &tmWh, &ctl->full[stage], kx,
                    nb * BN);
           pend_parity[stage] = (int)phase;
           if (++stage == STAGES) {
@@ -286,7 +305,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
           const uint32_t ab = su32(sA + stage * A_BYTES), bb = su32(sB + stage * B_BYTES);
 #pragma unroll
           for (int k = 0; k < BK / 16; ++k)
-            mma_bf16(dt, sw128_desc(ab + k * 32), sw128_desc(bb + k * 32), (kb | k) != 0);
+            mma_f16(dt, sw128_desc(ab + k * 32), sw128_desc(bb + k * 32), idesc, (kb | k) != 0);
           mma_commit(&ctl->empty[stage]);
           if (++stage == STAGES) {
             stage = 0;
@@ -327,7 +346,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       tc_fence_after();
       const int j = mb * BM + row;
       const bool jok = j < a.n;
-      const float hj = a.th_hi[j], lj = a.th_lo[j];
+      const float hj = a.th_hi[j], lj = a.th_lo[j], rj = a.rinv[j];
 #pragma unroll 1
       for (int ch = 0; ch < BN / 32; ++ch) {
         float v[32];
@@ -336,6 +355,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         // per-column data, one column per lane, broadcast by shuffles below
         const int icl = a.icol[cb + lane];
         const float dl = (float)a.d[cb + lane];
+        const float sl = a.sinv[cb + lane];
         const float hil = icl >= 0 ? a.th_hi[icl] : 0.f;
         const float lil = icl >= 0 ? a.th_lo[icl] : 0.f;
 #pragma unroll
@@ -353,18 +373,15 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             const int src = hh * 16 + i;
             const int ic = __shfl_sync(0xffffffffu, icl, src);
             const float dc = __shfl_sync(0xffffffffu, dl, src);
+            const float sc = __shfl_sync(0xffffffffu, sl, src);
             const float hi = __shfl_sync(0xffffffffu, hil, src);
             const float li = __shfl_sync(0xffffffffu, lil, src);
             if (!jok || ic < 0) continue;
             const int64_t o = (int64_t)(cb + src) * ld + j;
-            const float p = v[src] + dlt[i];
+            const float p = fmaf(v[src], rj * sc, dlt[i]);  // Delta E + Delta W
             float f, r;
             map_entry<float>(z[i], p, dc, gap2f(hj, lj, hi, li), j == ic, f, r);
             a.Fout[o] = f;
-            const float w = (j == ic) ? 0.f : f;
-            const __nv_bfloat16 wh = __float2bfloat16_rn(w);
-            a.Wh[o] = wh;
-            a.Wl[o] = __float2bfloat16_rn(w - __bfloat162float(wh));
             const float df = f - z[i];
             s_inc = fmaf(df, df, s_inc);
             s_z = fmaf(z[i], z[i], s_z);
@@ -416,16 +433,17 @@ EncodeTiledFn encode_fn() {
   return fn;
 }
 
-// 2-D BF16 row-major [outer x inner] tensor, box [box_outer x 64], 128-byte swizzle.
+// 2-D 16-bit row-major [outer x inner] tensor, box [box_outer x 64], 128-byte swizzle.
 bool make_map(CUtensorMap* m, const void* base, uint64_t inner, uint64_t outer,
-              uint32_t box_outer) {
+              uint32_t box_outer, bool bf16) {
   EncodeTiledFn enc = encode_fn();
   if (!enc) return false;
   cuuint64_t dims[2] = {inner, outer};
   cuuint64_t strides[1] = {inner * 2};
   cuuint32_t box[2] = {(cuuint32_t)BK, box_outer};
   cuuint32_t estr[2] = {1, 1};
-  return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box,
+  return enc(m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2,
+             const_cast<void*>(base), dims, strides, box,
              estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
              CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
@@ -433,15 +451,15 @@ bool make_map(CUtensorMap* m, const void* base, uint64_t inner, uint64_t outer,
 
 }  // namespace
 
-cudaError_t launch_gemm_tc(const __nv_bfloat16* Dh, const __nv_bfloat16* Dl,
-                           const __nv_bfloat16* Wh, const __nv_bfloat16* Wl,
-                           const MapArgs<float>& a, int npad, int kpad, int passes,
-                           cudaStream_t s) {
+cudaError_t launch_gemm_tc(const uint16_t* Dh, const uint16_t* Dl, const uint16_t* Wh,
+                           const uint16_t* Wl, const MapArgs<float>& a, int npad, int kpad,
+                           int passes, int bf16, cudaStream_t s) {
   if (npad % BM || kpad % BN || npad % BK || (passes != 1 && passes != 3))
     return cudaErrorInvalidValue;
+  const bool bf = bf16 != 0;
   CUtensorMap mDh, mDl, mWh, mWl;
-  if (!make_map(&mDh, Dh, npad, npad, BM) || !make_map(&mDl, Dl, npad, npad, BM) ||
-      !make_map(&mWh, Wh, npad, kpad, BN) || !make_map(&mWl, Wl, npad, kpad, BN))
+  if (!make_map(&mDh, Dh, npad, npad, BM, bf) || !make_map(&mDl, Dl, npad, npad, BM, bf) ||
+      !make_map(&mWh, Wh, npad, kpad, BN, bf) || !make_map(&mWl, Wl, npad, kpad, BN, bf))
     return cudaErrorInvalidValue;
   static int configured_device = -1;
   static int num_sms = 0;
@@ -459,7 +477,7 @@ cudaError_t launch_gemm_tc(const __nv_bfloat16* Dh, const __nv_bfloat16* Dl,
   const int tiles = num_m * num_n;
   const int grid = tiles < num_sms ? tiles : num_sms;
   k_gemm_tc<<<grid, NUM_THREADS, SMEM_BYTES, s>>>(mDh, mDl, mWh, mWl, a, num_m, num_n, num_kb,
-                                                  passes);
+                                                  passes, idesc_for(bf));
   return cudaGetLastError();
 }
 

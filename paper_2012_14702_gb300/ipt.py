@@ -26,7 +26,7 @@ MAX_HISTORY = 128
 
 STATUS = {0: "OK", 1: "MAXITER", 2: "DIVERGED", 3: "DEGENERATE_THETA", 4: "INVALID_ARG",
           5: "CUDA_ERROR", 6: "DEVICE_TIMEOUT", 7: "UNSUPPORTED"}
-PRECISION = {"f64": 0, "f32": 1, "bf16": 2, "bf16x3": 3, "staged": 4}
+PRECISION = {"f64": 0, "f32": 1, "bf16": 2, "bf16x3": 3, "staged": 4, "fp16": 5, "fp16x3": 6}
 PRECISION_NAME = {v: k for k, v in PRECISION.items()}
 STOP = {"increment": 0, "residual": 1}
 DTYPE = {torch.float64: 0, torch.float32: 1}
@@ -34,13 +34,16 @@ DTYPE = {torch.float64: 0, torch.float32: 1}
 
 class Options(C.Structure):
     _fields_ = [("precision", C.c_int), ("stop", C.c_int), ("diverge_bound", C.c_double),
-                ("stage_switch", C.c_double), ("verify_fp64", C.c_int), ("z0", C.c_void_p)]
+                ("stage_switch", C.c_double), ("staged_bf16", C.c_int), ("verify_fp64", C.c_int),
+                ("record_timing", C.c_int), ("z0", C.c_void_p)]
 
 
 class Result(C.Structure):
     _fields_ = [("status", C.c_int), ("iterations", C.c_int), ("stage_iters", C.c_int * 2),
                 ("increment", C.c_double), ("rho", C.c_double), ("rho_fp64", C.c_double),
-                ("r0", C.c_double), ("history_len", C.c_int),
+                ("r0", C.c_double), ("kernel_launches", C.c_int),
+                ("product_launches", C.c_int * 2), ("product_ms", C.c_double * 2),
+                ("prepass_ms", C.c_double), ("history_len", C.c_int),
                 ("hist_increment", C.c_double * MAX_HISTORY),
                 ("hist_rho", C.c_double * MAX_HISTORY),
                 ("hist_stage", C.c_int * MAX_HISTORY)]
@@ -50,7 +53,10 @@ class Result(C.Structure):
         return {"status": STATUS.get(self.status, str(self.status)), "status_code": self.status,
                 "iterations": self.iterations, "stage_iters": list(self.stage_iters),
                 "increment": self.increment, "rho": self.rho, "rho_fp64": self.rho_fp64,
-                "r0": self.r0, "hist_increment": list(self.hist_increment[:h]),
+                "r0": self.r0, "kernel_launches": self.kernel_launches,
+                "product_launches": list(self.product_launches),
+                "product_ms": list(self.product_ms), "prepass_ms": self.prepass_ms,
+                "hist_increment": list(self.hist_increment[:h]),
                 "hist_rho": list(self.hist_rho[:h]),
                 "hist_stage": [PRECISION_NAME.get(s, s) for s in self.hist_stage[:h]]}
 
@@ -96,7 +102,7 @@ def _dev(t, dtype=None, name="tensor"):
 
 
 def make_options(precision="staged", stop="residual", diverge_bound=1e8, stage_switch=1e-4,
-                 verify_fp64=False, z0=None) -> Options:
+                 verify_fp64=False, z0=None, staged_bf16=False, record_timing=False) -> Options:
     o = Options()
     _lib.ipt_options_default(C.byref(o))
     o.precision = PRECISION[precision] if isinstance(precision, str) else int(precision)
@@ -104,6 +110,8 @@ def make_options(precision="staged", stop="residual", diverge_bound=1e8, stage_s
     o.diverge_bound = diverge_bound
     o.stage_switch = stage_switch
     o.verify_fp64 = 1 if verify_fp64 else 0
+    o.staged_bf16 = 1 if staged_bf16 else 0
+    o.record_timing = 1 if record_timing else 0
     o.z0 = None if z0 is None else z0.data_ptr()
     return o
 
@@ -133,7 +141,8 @@ class Solver:
     # ------------------------------------------------------------------ dense
     def solve_dense(self, M, theta=None, cols=None, tol=1e-6, max_iter=100, precision="staged",
                     stop="residual", z_dtype=torch.float32, verify_fp64=False, z0=None,
-                    diverge_bound=1e8, stage_switch=1e-4):
+                    diverge_bound=1e8, stage_switch=1e-4, staged_bf16=False,
+                    record_timing=False):
         """Alg. 2 / Alg. 1 on the GPU.  Returns (lam [k] f64, Z (n, k) view, info dict)."""
         M = _dev(M, name="M")
         n = M.shape[0]
@@ -149,7 +158,8 @@ class Solver:
             z0t = z0.t().contiguous() if z0.shape == (n, k) else z0
         else:
             z0t = None
-        o = make_options(precision, stop, diverge_bound, stage_switch, verify_fp64, z0t)
+        o = make_options(precision, stop, diverge_bound, stage_switch, verify_fp64, z0t,
+                         staged_bf16, record_timing)
         r = Result()
         _lib.ipt_solve_dense(self._h, n, _ptr(M), M.stride(0), DTYPE[M.dtype], _ptr(theta), k,
                              _ptr(cols), float(tol), int(max_iter), C.byref(o), _ptr(lam),
@@ -158,7 +168,7 @@ class Solver:
 
     def solve_dense_host(self, M, theta=None, cols=None, tol=1e-6, max_iter=100,
                          precision="staged", stop="residual", z_dtype=torch.float32,
-                         lam_out=None, zt_out=None):
+                         lam_out=None, zt_out=None, record_timing=False):
         """The same solve from host tensors (pinned for speed); copies are inside the call."""
         if M.is_cuda:
             raise ValueError("solve_dense_host takes host tensors")
@@ -169,7 +179,7 @@ class Solver:
         k = n if cols is None else cols.numel()
         lam = lam_out if lam_out is not None else torch.empty(k, dtype=torch.float64)
         Zt = zt_out if zt_out is not None else torch.empty((k, n), dtype=z_dtype)
-        o = make_options(precision, stop)
+        o = make_options(precision, stop, record_timing=record_timing)
         r = Result()
         _lib.ipt_solve_dense_host(self._h, n, _ptr(M), M.stride(0), DTYPE[M.dtype], _ptr(theta),
                                   k, _ptr(cols), float(tol), int(max_iter), C.byref(o), _ptr(lam),

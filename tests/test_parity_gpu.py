@@ -38,10 +38,13 @@ def near_fixed_point_z(n, cols, seed, amp=1e-2):
 #   f32     P to ~sqrt(n) u32 |Delta||Z|       -> 2e-5
 #   bf16    Delta W to 2^-8 relative (Delta E exact)  -> 2^-8 |W|sqrt(n) ~ 1e-2 at amp 1e-2
 #   bf16x3  Delta W to ~3 * 2^-17 relative     -> 2e-5
-STEP_TOL = {"f64": 1e-12, "f32": 2e-5, "bf16": 1e-2, "bf16x3": 2e-5}
+#   fp16    Delta W to 2^-11 relative          -> 2e-3
+#   fp16x3  Delta W to ~3 * 2^-22 relative     -> 2e-6 (FP32 accumulation dominates)
+STEP_TOL = {"f64": 1e-12, "f32": 2e-5, "bf16": 1e-2, "bf16x3": 2e-5, "fp16": 2e-3,
+            "fp16x3": 2e-6}
 
 
-@pytest.mark.parametrize("precision", ["f64", "f32", "bf16", "bf16x3"])
+@pytest.mark.parametrize("precision", ["f64", "f32", "bf16", "bf16x3", "fp16", "fp16x3"])
 @pytest.mark.parametrize("n,k", [(255, 255), (300, 37), (130, 1)])
 def test_single_step_matches_oracle_map(ipt, precision, n, k):
     M, th = w.dense_symmetric(n, 0.02, seed=n + k, theta_step=0.5)
@@ -87,7 +90,7 @@ def test_small_fp64_config_matches_oracle(ipt):
     assert info["rho_fp64"] <= 1e-9
 
 
-@pytest.mark.parametrize("precision", ["staged", "f32", "bf16x3"])
+@pytest.mark.parametrize("precision", ["staged", "f32", "fp16x3", "bf16x3"])
 @pytest.mark.parametrize("n", [1000, 385])
 def test_solve_to_residual_matches_converged_oracle(ipt, precision, n):
     """Dense full spectrum shaped like the large workload (theta_i = i/8,
@@ -109,7 +112,7 @@ def test_solve_to_residual_matches_converged_oracle(ipt, precision, n):
     assert err <= 1e-4, err
     if precision == "staged":
         assert info["stage_iters"][0] >= 1 and info["stage_iters"][1] >= 1
-        assert info["hist_stage"][0] == "bf16" and info["hist_stage"][-1] == "bf16x3"
+        assert info["hist_stage"][0] == "fp16" and info["hist_stage"][-1] == "fp16x3"
 
 
 def test_partial_spectrum_dense_permuted_columns(ipt):
@@ -226,18 +229,20 @@ def test_warm_start_from_converged_solution(ipt):
 
 
 # ------------------------------------------------------------------ full size, sampled
-def test_n8192_staged_sampled_columns_match_oracle(ipt):
-    """The benchmark workload (n = 8192, theta_i = i/8, Delta N(0,1)*1e-3) in
-    the benchmark's launch configuration; the oracle solves 48 sampled columns
-    (Alg. 1 per column, FP64) and the GPU's full-spectrum result must match
-    them.  The FP64 residual of the whole GPU result is recomputed on the GPU."""
+@pytest.mark.parametrize("eps,seed", [(1e-4, 21), (1e-3, 22), (3e-3, 23)])
+def test_n8192_staged_sampled_columns_match_oracle(ipt, eps, seed):
+    """The large dense workload (n = 8192, theta_i = i/8, Delta N(0,1)*eps,
+    eps in {1e-4, 1e-3, 3e-3}) in the benchmark's launch configuration; the
+    oracle solves 50 sampled columns (Alg. 1 per column, FP64) and the GPU's
+    full-spectrum result must match them.  The FP64 residual of the whole GPU
+    result is recomputed on the GPU and must meet the 1e-6 target."""
     n = 8192
-    M, th = w.dense_symmetric(n, 1e-3, seed=22, theta_step=0.125)
+    M, th = w.dense_symmetric(n, eps, seed=seed, theta_step=0.125)
     Mg = cuda(M, torch.float32)
     lam, Z, info = ipt.Solver().solve_dense(Mg, theta=cuda(th), tol=1e-6, max_iter=40,
                                             precision="staged", verify_fp64=True)
     assert info["status"] == "OK", info
-    assert info["rho_fp64"] <= 1.2e-6, info
+    assert info["rho_fp64"] <= 1e-6, info
     sample = np.sort(w.rng(99).choice(n, 48, replace=False)).astype(np.int64)
     sample = np.concatenate([[0, n - 1], sample])
     ref = oracle.ipt_solve(M, th, cols=sample, tol=1e-12, max_iter=100)
