@@ -189,6 +189,32 @@ ipt_status ipt_solve_csr(ipt_handle* h, int64_t n, int64_t nnz, const int32_t* r
                          int max_iter, const ipt_options* opt, double* lambda, void* Z,
                          int64_t ldz, int z_dtype, ipt_result* out);
 
+/*
+ * ||M Z - Z Lambda||_F in FP64, allocating no device memory.  The paper has
+ * no counterpart: this is a library service for callers that cannot call
+ * cudaMalloc -- work recorded by CUDA stream capture, processes whose device
+ * memory belongs to another allocator (e.g. a framework's caching pool), and
+ * loops where an allocation's implicit device synchronisation is not
+ * acceptable.  Its only scratch is a fixed file-scope device array of 16384
+ * FP64 partial sums (128 KiB per device, held until the library is unloaded).
+ *   n, M, ldm, m_dtype   dense M as for ipt_solve_dense (device)
+ *   k, Z, ldz, z_dtype   n x k column-major eigenvector block (device)
+ *   lambda               device, k doubles
+ *   out                  device, 1 double: the norm is written there
+ *   stream               cudaStream_t the two kernels are enqueued on (NULL =
+ *                        legacy default stream); the call does not synchronise
+ * Limit: ceil(n/64) * ceil(k/64) <= 16384 (e.g. n = k = 8192); larger sizes
+ * return IPT_UNSUPPORTED without launching anything.  The first call on a
+ * device looks up the array's device address (once per device); make that
+ * first call before any stream capture begins.  All calls share the array:
+ * calls whose kernels overlap on the GPU (different streams, no ordering)
+ * race on it and may return wrong norms.  Nothing in the array needs to start
+ * at zero; each call overwrites the slots it reads.
+ */
+ipt_status ipt_residual_dense_noalloc(int64_t n, const void* M, int64_t ldm, int m_dtype,
+                                      int64_t k, const void* Z, int64_t ldz, int z_dtype,
+                                      const double* lambda, double* out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

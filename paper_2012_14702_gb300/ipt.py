@@ -83,6 +83,10 @@ _lib.ipt_solve_csr.argtypes = [_vp, _i64, _i64, _vp, _vp, _vp, _i32, _vp, _i64, 
                                C.POINTER(Options), _vp, _vp, _i64, _i32, C.POINTER(Result)]
 _lib.ipt_solve_csr.restype = _i32
 
+_lib.ipt_residual_dense_noalloc.argtypes = [_i64, _vp, _i64, _i32, _i64, _vp, _i64, _i32, _vp,
+                                           _vp, _vp]
+_lib.ipt_residual_dense_noalloc.restype = _i32
+
 LIB_PATH = _LIB_PATH
 lib = _lib
 
@@ -225,6 +229,29 @@ class Solver:
                            int(max_iter), C.byref(o), _ptr(lam), _ptr(Zt), n, DTYPE[z_dtype],
                            C.byref(r))
         return lam, Zt.t(), r.to_dict()
+
+
+def residual_dense_noalloc(M, Z, lam, out=None, stream=None):
+    """||M Z - Z Lambda||_F in FP64 through the allocation-free C entry point.
+
+    M (n, n) and Z (n, k) CUDA float32/float64 matrices (Z given as the (n, k)
+    view the solvers return, i.e. column-major storage), lam (k,) float64.
+    Writes the norm into ``out`` (a CUDA float64 tensor of one element,
+    created here when not given) without synchronising; returns
+    (status code, out).  The library itself allocates nothing on the device.
+    """
+    n = M.shape[0]
+    k = Z.shape[1]
+    Zt = Z.t()
+    if not Zt.is_contiguous():
+        raise ValueError("Z must be column-major (the (n, k) view of a (k, n) tensor)")
+    if out is None:
+        out = torch.empty(1, dtype=torch.float64, device=M.device)
+    s = stream if stream is not None else torch.cuda.current_stream()
+    st = _lib.ipt_residual_dense_noalloc(n, _ptr(M), M.stride(0), DTYPE[M.dtype], k, _ptr(Zt),
+                                         Zt.stride(0), DTYPE[Zt.dtype], _ptr(lam), _ptr(out),
+                                         C.c_void_p(s.cuda_stream))
+    return st, out
 
 
 _default: Solver | None = None
