@@ -326,6 +326,15 @@ def run_ours(args, rank, world, local_rank):
     del Mh, zt_h
 
     launches = sum(i["kernel_launches"] for i in infos)
+    K = len(infos)
+    breakdown = {
+        "product_1pass": t1 / K, "product_3pass": t3 / K, "prepass": tp / K,
+        "setup": sum(i["setup_ms"] for i in infos) / K,
+        "finalize": sum(i["finalize_ms"] for i in infos) / K,
+        "host_wall_per_call": sum(i["wall_ms"] for i in infos) / K,
+    }
+    breakdown["other_device_and_host_gaps"] = ms - sum(
+        breakdown[x] for x in ["product_1pass", "product_3pass", "prepass", "setup", "finalize"])
     line = {
         "metric": METRIC, "value": ms, "unit": "ms", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False,
@@ -339,6 +348,7 @@ def run_ours(args, rank, world, local_rank):
         "stage_iters": infos[-1]["stage_iters"],
         "rho": infos[-1]["rho"], "rho_fp64": vinfo["rho_fp64"],
         "tflops_per_iter": tflops_iter,
+        "breakdown_ms": breakdown,
         "plain_fp32": {"ms": plain_ms, "iterations": pinfo["iterations"],
                        "rho": pinfo["rho"], "rho_fp64": pvinfo["rho_fp64"],
                        "speedup": plain_ms / ms},

@@ -23,9 +23,11 @@
  *  - Calls are ordered on the handle's stream and synchronise it before
  *    returning; outputs are valid on return.  A handle serves one host
  *    thread at a time.
- *  - Errors are returned, never raised or aborted on.  Argument errors are
- *    detected before any kernel runs; on IPT_MAXITER / IPT_DIVERGED the
- *    outputs hold the last iterate at which F was evaluated.
+ *  - Errors are returned, never raised or aborted on.  Size, pointer and
+ *    option errors are detected before any kernel runs; column and theta
+ *    errors (checked on the device) before any output is written.  On
+ *    IPT_MAXITER / IPT_DIVERGED the outputs hold the last iterate at which F
+ *    was evaluated.
  */
 #ifndef IPT_H
 #define IPT_H
@@ -107,6 +109,9 @@ typedef struct {
                               [1] 3-pass (FP16 x3 / BF16 x3)                             */
   double product_ms[2]; /* their summed device time (record_timing), else 0               */
   double prepass_ms;    /* summed device time of the D(Delta Z) / operand-split pre-pass  */
+  double setup_ms;      /* device time of the partition / validation / Z0 kernels (timing) */
+  double finalize_ms;   /* device time of the Lambda / Z output kernels (timing)           */
+  double wall_ms;       /* host wall-clock time of the whole call                         */
   int history_len;      /* min(iterations, IPT_MAX_HISTORY)                               */
   double hist_increment[IPT_MAX_HISTORY];
   double hist_rho[IPT_MAX_HISTORY];

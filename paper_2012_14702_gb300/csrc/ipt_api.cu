@@ -10,6 +10,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <chrono>
 
 using namespace ipt;
 
@@ -37,11 +38,11 @@ struct ipt_handle {
   cudaStream_t s = nullptr;
   int dev = 0;
   Buf drow, dt, dh, dl, z[2], wh, wl, rinv, sinv;
-  Buf theta, thh, thl, icol, count, d, st;
+  Buf theta, thh, thl, icol, count, d, st, r0part;
   Buf m64, z64, racc;
   Buf hM, hTheta, hCols, hLam, hZ;  // device staging of the host-buffer entry point
   DevState* hst = nullptr;          // pinned mirror of the controller's words
-  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // pre-pass / product brackets
+  cudaEvent_t ev[8] = {};           // pre-pass / product / setup / finalize brackets
   int launches = 0;                 // kernels launched by the current call
 };
 
@@ -118,6 +119,7 @@ ipt_status alloc_dense(ipt_handle* h, const Plan& p) {
   CK(ensure(h->count, (size_t)p.npad * 4));
   CK(ensure(h->d, (size_t)p.kpad * 8));
   CK(ensure(h->st, sizeof(DevState)));
+  CK(ensure(h->r0part, (size_t)(p.npad / 32) * (p.npad / 32) * 8));
   return IPT_OK;
 }
 
@@ -131,10 +133,13 @@ ipt_status status_from_flags(int flags) {
 
 // Partition, validation and starting point; leaves the controller state
 // initialised with the first stage.  z0 (optional) is copied into Z buffer 0,
-// rescaled to z0[cols[c], c] = 1 when `rescale`.
+// rescaled to z0[cols[c], c] = 1 when `rescale`.  With `sync_check` the
+// validation flags are read back here; otherwise the caller reads them at
+// its first synchronisation, before writing any output (every setup kernel
+// is memory-safe on invalid columns or theta).
 ipt_status setup_dense(ipt_handle* h, const Plan& p, const void* M, int64_t ldm, int m_dtype,
                        const double* theta, const int32_t* cols, const void* z0, int64_t ldz0,
-                       int z0_dtype, bool rescale, int first_stage) {
+                       int z0_dtype, bool rescale, int first_stage, bool sync_check) {
   cudaStream_t s = h->s;
   DevState* st = dst(h);
   CK(cudaMemsetAsync(st, 0, sizeof(DevState), s));
@@ -146,20 +151,23 @@ ipt_status setup_dense(ipt_handle* h, const Plan& p, const void* M, int64_t ldm,
   }
   CK(cudaMemsetAsync(h->count.p, 0, (size_t)p.npad * 4, s));
   launch_theta(M, ldm, m_dtype, theta, p.n, p.npad, (double*)h->theta.p, (float*)h->thh.p,
-               (float*)h->thl.p, s);
+               (float*)h->thl.p, st, s);
   launch_validate(cols, p.n, p.k, p.kpad, (const double*)h->theta.p, (int32_t*)h->icol.p,
                   (int*)h->count.p, st, s);
   h->launches += 3;
   CK(cudaGetLastError());
-  CK(cudaMemcpyAsync(h->hst, st, kStateHead, cudaMemcpyDeviceToHost, s));
-  CK(cudaStreamSynchronize(s));
-  ipt_status v = status_from_flags(h->hst->flags);
-  if (v != IPT_OK) return v;
+  ipt_status v = IPT_OK;
+  if (sync_check) {
+    CK(cudaMemcpyAsync(h->hst, st, kStateHead, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    v = status_from_flags(h->hst->flags);
+    if (v != IPT_OK) return v;
+  }
 
   launch_form_delta(M, ldm, m_dtype, (const double*)h->theta.p, p.n, p.npad,
                     (const int*)h->count.p, h->drow.p, p.f64 ? 1 : 0,
-                    p.dt ? (float*)h->dt.p : nullptr, st, s);
-  h->launches += 2;  // form_delta + init/copy of Z below
+                    p.dt ? (float*)h->dt.p : nullptr, (double*)h->r0part.p, st, s);
+  h->launches += 3;  // form_delta, sum of partials, init/copy of Z below
   if (p.tc) {
     launch_split_delta((const float*)h->drow.p, p.npad, p.bf16 ? 1 : 0, (uint16_t*)h->dh.p,
                        (uint16_t*)h->dl.p, (float*)h->rinv.p, s);
@@ -172,7 +180,14 @@ ipt_status setup_dense(ipt_handle* h, const Plan& p, const void* M, int64_t ldm,
     }
   }
   const size_t kn = (size_t)p.kpad * p.npad;
-  CK(cudaMemsetAsync(h->z[1].p, 0, kn * (p.f64 ? 8 : 4), s));
+  const size_t ez = p.f64 ? 8 : 4;
+  // Z buffer 1 receives F only at rows < n of columns < k: zero the rest once
+  if (p.npad > p.n)
+    CK(cudaMemset2DAsync((char*)h->z[1].p + (size_t)p.n * ez, (size_t)p.npad * ez, 0,
+                         (size_t)(p.npad - p.n) * ez, (size_t)p.kpad, s));
+  if (p.kpad > p.k)
+    CK(cudaMemsetAsync((char*)h->z[1].p + (size_t)p.k * p.npad * ez, 0,
+                       (size_t)(p.kpad - p.k) * p.npad * ez, s));
   if (z0 && !rescale) {
     // exact copy (single evaluation at a caller-given Z)
     CK(cudaMemsetAsync(h->z[0].p, 0, kn * (p.f64 ? 8 : 4), s));
@@ -183,7 +198,7 @@ ipt_status setup_dense(ipt_handle* h, const Plan& p, const void* M, int64_t ldm,
                   h->z[0].p, p.f64 ? 1 : 0, st, s);
   }
   CK(cudaGetLastError());
-  if (z0) {
+  if (sync_check) {
     CK(cudaMemcpyAsync(h->hst, st, kStateHead, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     v = status_from_flags(h->hst->flags);
@@ -197,10 +212,11 @@ struct Timing {
   double product_ms[2] = {0.0, 0.0};
   int product_launches[2] = {0, 0};
   double prepass_ms = 0.0;
+  double setup_ms = 0.0, finalize_ms = 0.0;
 };
 
 ipt_status ensure_events(ipt_handle* h) {
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < 8; ++i)
     if (!h->ev[i]) CK(cudaEventCreate(&h->ev[i]));
   return IPT_OK;
 }
@@ -281,6 +297,8 @@ void collect_timing(ipt_handle* h, int stage, Timing* tm) {
 
 void fill_result(const DevState& hs, const Timing& tm, int launches, ipt_result* out) {
   out->kernel_launches = launches;
+  out->setup_ms = tm.setup_ms;
+  out->finalize_ms = tm.finalize_ms;
   for (int i = 0; i < 2; ++i) {
     out->product_launches[i] = tm.product_launches[i];
     out->product_ms[i] = tm.product_ms[i];
@@ -357,6 +375,7 @@ ipt_status solve_dense(ipt_handle* h, int64_t n, const void* M, int64_t ldm, int
     return v;
   }
   DeviceGuard g(h->dev);
+  const auto t_start = std::chrono::steady_clock::now();
   h->launches = 0;
   Timing tm;
   tm.on = opt.record_timing != 0;
@@ -370,7 +389,10 @@ ipt_status solve_dense(ipt_handle* h, int64_t n, const void* M, int64_t ldm, int
   v = alloc_dense(h, p);
   if (v == IPT_OK) {
     const int first = opt.precision == IPT_PREC_STAGED ? low : opt.precision;
-    v = setup_dense(h, p, M, ldm, m_dtype, theta, cols, opt.z0, ldz, z_dtype, true, first);
+    if (tm.on) cudaEventRecord(h->ev[4], h->s);
+    v = setup_dense(h, p, M, ldm, m_dtype, theta, cols, opt.z0, ldz, z_dtype, true, first,
+                    false);
+    if (tm.on) cudaEventRecord(h->ev[5], h->s);
   }
   if (v != IPT_OK) {
     out->status = v;
@@ -399,6 +421,15 @@ ipt_status solve_dense(ipt_handle* h, int64_t n, const void* M, int64_t ldm, int
       v = IPT_CUDA_ERROR;
       break;
     }
+    if (it == 0) {
+      // validation flags of the setup kernels, before any output is written
+      v = status_from_flags(h->hst->flags);
+      if (v != IPT_OK) break;
+      if (tm.on) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, h->ev[4], h->ev[5]) == cudaSuccess) tm.setup_ms = ms;
+      }
+    }
     collect_timing(h, stage, &tm);
     if (h->hst->timeout) {
       v = IPT_DEVICE_TIMEOUT;
@@ -419,16 +450,24 @@ ipt_status solve_dense(ipt_handle* h, int64_t n, const void* M, int64_t ldm, int
     return IPT_CUDA_ERROR;
   }
   const int ans = hs.answer;
+  if (tm.on) cudaEventRecord(h->ev[6], s);
   launch_lambda((const double*)h->theta.p, (const int32_t*)h->icol.p, (const double*)h->d.p,
                 p.k, lambda, s);
   launch_copy_z(h->z[ans].p, p.f64 ? 1 : 0, p.npad, p.n, p.k, Z, ldz,
                 z_dtype == IPT_DTYPE_F64 ? 1 : 0, s);
   h->launches += 2;
+  if (tm.on) cudaEventRecord(h->ev[7], s);
   if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) {
     out->status = IPT_CUDA_ERROR;
     return IPT_CUDA_ERROR;
   }
+  if (tm.on) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, h->ev[6], h->ev[7]) == cudaSuccess) tm.finalize_ms = ms;
+  }
   fill_result(hs, tm, h->launches, out);
+  out->wall_ms =
+      std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
   if (opt.verify_fp64) {
     v = verify_fp64(h, p, M, ldm, m_dtype, ans, lambda, &out->rho_fp64);
     if (v != IPT_OK) {
@@ -489,11 +528,12 @@ ipt_status ipt_destroy(ipt_handle* h) {
   DeviceGuard g(h->dev);
   Buf* all[] = {&h->drow, &h->dt, &h->dh, &h->dl, &h->z[0], &h->z[1], &h->wh, &h->wl,
                 &h->rinv, &h->sinv, &h->theta, &h->thh, &h->thl, &h->icol, &h->count,
+                &h->r0part,
                 &h->d, &h->st, &h->m64, &h->z64, &h->racc, &h->hM, &h->hTheta, &h->hCols,
                 &h->hLam, &h->hZ};
   for (Buf* b : all)
     if (b->p) cudaFree(b->p);
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < 8; ++i)
     if (h->ev[i]) cudaEventDestroy(h->ev[i]);
   if (h->hst) cudaFreeHost(h->hst);
   delete h;
@@ -562,11 +602,15 @@ ipt_status ipt_step_dense(ipt_handle* h, int64_t n, const void* M, int64_t ldm, 
   const Plan p = make_plan(n, k, precision, false);
   v = alloc_dense(h, p);
   if (v != IPT_OK) return v;
-  v = setup_dense(h, p, M, ldm, m_dtype, theta, cols, Zin, ldz, z_dtype, false, precision);
+  v = setup_dense(h, p, M, ldm, m_dtype, theta, cols, Zin, ldz, z_dtype, false, precision, true);
   if (v != IPT_OK) return v;
   v = evaluate(h, p, 0, precision, nullptr);
   if (v != IPT_OK) return v;
   cudaStream_t s = h->s;
+  CK(cudaMemcpyAsync(h->hst, dst(h), kStateHead, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  v = status_from_flags(h->hst->flags);  // theta_j == theta_{cols[c]} is found in the epilogue
+  if (v != IPT_OK) return v;
   launch_lambda((const double*)h->theta.p, (const int32_t*)h->icol.p, (const double*)h->d.p,
                 p.k, lambda, s);
   launch_copy_z(h->z[1].p, p.f64 ? 1 : 0, p.npad, p.n, p.k, Fout, ldz,

@@ -78,12 +78,13 @@ struct MapArgs {
 // ---------------------------------------------------------------- launchers
 // setup (k_setup.cu)
 void launch_theta(const void* M, int64_t ldm, int m_dtype, const double* theta_in, int n,
-                  int npad, double* theta, float* th_hi, float* th_lo, cudaStream_t s);
+                  int npad, double* theta, float* th_hi, float* th_lo, DevState* st,
+                  cudaStream_t s);
 void launch_validate(const int32_t* cols, int n, int k, int kpad, const double* theta,
                      int32_t* icol, int* count, DevState* st, cudaStream_t s);
 void launch_form_delta(const void* M, int64_t ldm, int m_dtype, const double* theta, int n,
                        int npad, const int* count, void* Drow, int drow_f64, float* DT,
-                       DevState* st, cudaStream_t s);
+                       double* r0part, DevState* st, cudaStream_t s);
 void launch_split_delta(const float* Drow, int npad, int bf16, uint16_t* Dh, uint16_t* Dl,
                         float* rinv, cudaStream_t s);
 void launch_init_z(const void* z0, int64_t ldz0, int z0_dtype, const int32_t* icol, int n,
@@ -183,6 +184,12 @@ __device__ __forceinline__ void map_entry(T z, T p, T dc, T gap, bool diag, T& f
     f = u / gap;
     r = gap * z - u;
   }
+}
+
+// theta_j == theta_{cols[c]} off the unit entry: the gap of Eq. (single_line_dyn)
+// does not exist (Section 3 requires distinct unperturbed eigenvalues).
+__device__ __forceinline__ void flag_degenerate(DevState* st) {
+  atomicOr(&st->flags, FLAG_THETA_DEGENERATE);
 }
 
 }  // namespace ipt

@@ -356,6 +356,7 @@ __global__ void __launch_bounds__(256)
           if constexpr (sizeof(T) == 8) gap = a.theta[j] - a.theta[ic];
           else gap = gap2f(a.th_hi[j], a.th_lo[j], a.th_hi[ic], a.th_lo[ic]);
           T fv, rv;
+          if (gap == T(0) && j != ic) flag_degenerate(a.st);
           map_entry<T>(z[q], p, dc, gap, j == ic, fv, rv);
           f[q] = fv;
           s_inc += (fv - z[q]) * (fv - z[q]);

@@ -15,12 +15,16 @@ __device__ __forceinline__ double load_m(const void* M, int64_t idx, int m_dtype
 }
 
 // theta (given, or diag(M)) and its two-float split; padding rows get 0.
+// Non-finite theta is flagged here; equal theta_j == theta_{cols[c]} is
+// detected where the product epilogues form the gap (gap == 0 off the
+// unit entry), at no extra pass over the n x k pairs.
 __global__ void k_theta(const void* M, int64_t ldm, int m_dtype, const double* theta_in, int n,
-                        int npad, double* theta, float* th_hi, float* th_lo) {
+                        int npad, double* theta, float* th_hi, float* th_lo, DevState* st) {
   int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= npad) return;
   double t = 0.0;
   if (j < n) t = theta_in ? theta_in[j] : load_m(M, (int64_t)j * ldm + j, m_dtype);
+  if (j < n && !isfinite(t)) atomicOr(&st->flags, FLAG_THETA_NONFINITE);
   theta[j] = t;
   float h = (float)t;
   th_hi[j] = h;
@@ -46,72 +50,127 @@ __global__ void k_cols(const int32_t* cols, int n, int k, int kpad, int32_t* ico
   atomicAdd(&count[i], 1);
 }
 
-// Duplicate columns, non-finite theta, theta_j == theta_{cols[c]} (j != cols[c]).
-// Grid: (k, ceil(n / (blockDim*4))).
-__global__ void k_theta_check(const double* theta, const int32_t* icol, const int* count, int n,
-                              DevState* st) {
-  int c = blockIdx.x;
-  int i = icol[c];
-  if (i < 0) return;
-  double ti = theta[i];
-  if (blockIdx.y == 0 && threadIdx.x == 0) {
-    if (count[i] > 1) atomicOr(&st->flags, FLAG_COL_DUP);
-    if (!isfinite(ti)) atomicOr(&st->flags, FLAG_THETA_NONFINITE);
-  }
-  int base = blockIdx.y * blockDim.x * 4;
-  bool bad = false;
-  for (int q = 0; q < 4; ++q) {
-    int j = base + q * blockDim.x + threadIdx.x;
-    if (j < n && j != i) {
-      double tj = theta[j];
-      bad |= (tj == ti) || !isfinite(tj);
-    }
-  }
-  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0)
-    atomicOr(&st->flags, FLAG_THETA_DEGENERATE);
+// Duplicate requested columns (after k_cols has counted occurrences).
+__global__ void k_cols_dup(const int32_t* icol, const int* count, int k, DevState* st) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= k) return;
+  const int i = icol[c];
+  if (i >= 0 && count[i] > 1) atomicOr(&st->flags, FLAG_COL_DUP);
 }
 
-// Delta = M - diag(theta), formed in FP64 before any rounding, then stored
-// as FP64/FP32 row-major and (optionally) FP32 column-major, transposed
-// through shared memory.  Also sums the squared off-diagonal entries of the
-// requested columns (the residual normaliser ||R0||^2).  Block 32x8, tile 32x32.
-__global__ void k_form_delta(const void* M, int64_t ldm, int m_dtype, const double* theta, int n,
-                             int npad, const int* count, void* Drow, int drow_f64, float* DT,
-                             DevState* st) {
+// Delta = M - diag(theta) (Alg. 1/2 step 1).  Off-diagonal entries are M's
+// own values, copied without arithmetic; the n diagonal ones are formed in
+// FP64 before rounding, M_ii - theta_i (theta_i ~ 1e3 would otherwise swamp
+// Delta_ii ~ 1e-3 in any 16- or 32-bit format).  Stored as FP64/FP32
+// row-major and (optionally) FP32 column-major, transposed through shared
+// memory.  Also sums the squared off-diagonal entries of the requested
+// columns (the residual normaliser ||R0||^2).  Block 32x8, tile 32x32.
+template <typename TM, typename TD>
+__global__ void k_form_delta(const TM* __restrict__ M, int64_t ldm, const double* theta, int n,
+                             int npad, const int* count, TD* __restrict__ Drow,
+                             float* __restrict__ DT, double* __restrict__ r0part) {
   __shared__ float tile[32][33];
-  int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
-  int tx = threadIdx.x, ty = threadIdx.y;
-  double r0sum = 0.0;
+  const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int j = c0 + tx;
+  const bool req = j < n && count[j] > 0;
+  float r0sum = 0.f;
   for (int q = 0; q < 4; ++q) {
-    int i = r0 + ty + 8 * q, j = c0 + tx;
-    double v = 0.0;
+    const int i = r0 + ty + 8 * q;
+    TD v = TD(0);
     if (i < n && j < n) {
-      v = load_m(M, (int64_t)i * ldm + j, m_dtype);
-      if (i == j) v -= theta[i];
-      else if (count[j] > 0) r0sum += v * v;
+      if (i == j) {
+        v = (TD)((double)M[(int64_t)i * ldm + j] - theta[i]);
+      } else {
+        v = (TD)M[(int64_t)i * ldm + j];
+        if (req) r0sum = fmaf((float)v, (float)v, r0sum);
+      }
     }
-    int64_t o = (int64_t)i * npad + j;
-    if (drow_f64) static_cast<double*>(Drow)[o] = v;
-    else static_cast<float*>(Drow)[o] = (float)v;
+    Drow[(int64_t)i * npad + j] = v;
     tile[ty + 8 * q][tx] = (float)v;
   }
   if (DT) {
     __syncthreads();
     for (int q = 0; q < 4; ++q) {
-      int j = c0 + ty + 8 * q, i = r0 + tx;
-      DT[(int64_t)j * npad + i] = tile[tx][ty + 8 * q];
+      const int jj = c0 + ty + 8 * q, i = r0 + tx;
+      DT[(int64_t)jj * npad + i] = tile[tx][ty + 8 * q];
     }
   }
-  r0sum = warp_sum(r0sum);
-  if (tx == 0 && r0sum != 0.0) atomicAdd(&st->r0acc, r0sum);
+  // block partial of ||R0||^2 (one slot per block; summed by k_sum_partials)
+  __shared__ float red[8];
+  const float w = warp_sum(r0sum);
+  if (tx == 0) red[ty] = w;
+  __syncthreads();
+  if (tx == 0 && ty == 0) {
+    double t = 0.0;
+    for (int q = 0; q < 8; ++q) t += (double)red[q];
+    r0part[(int64_t)blockIdx.y * gridDim.x + blockIdx.x] = t;
+  }
+}
+
+// One block: st->r0acc = sum of the per-block partials, in a fixed order.
+__global__ void k_sum_partials(const double* __restrict__ part, int64_t count, DevState* st) {
+  __shared__ double red[1024];
+  double t = 0.0;
+  for (int64_t i = threadIdx.x; i < count; i += blockDim.x) t += part[i];
+  red[threadIdx.x] = t;
+  __syncthreads();
+  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+    if ((int)threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) st->r0acc = red[0];
 }
 
 // Tensor-core A operand: row j of Delta scaled by the power of two r_j that
 // brings its largest entry into [2^13, 2^14), split into 16-bit hi + lo.
-// One warp per row (all npad rows; padding rows are zero).
-__global__ void k_split_delta(const float* __restrict__ Drow, int npad, int bf16,
-                              uint16_t* __restrict__ Dh, uint16_t* __restrict__ Dl,
-                              float* __restrict__ rinv) {
+// One CTA per row (all npad rows; padding rows are zero); the row stays in
+// registers between the max and the split (VPT float4 per thread).
+template <int VPT>
+__global__ void __launch_bounds__(1024)
+    k_split_delta(const float* __restrict__ Drow, int npad, int bf16,
+                  uint16_t* __restrict__ Dh, uint16_t* __restrict__ Dl,
+                  float* __restrict__ rinv) {
+  const int row = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int n4 = npad / 4;
+  const float4* a = reinterpret_cast<const float4*>(Drow + (int64_t)row * npad);
+  float4 x[VPT];
+  float mx = 0.f;
+#pragma unroll
+  for (int q = 0; q < VPT; ++q) {
+    const int m = tid + q * blockDim.x;
+    x[q] = m < n4 ? __ldg(a + m) : make_float4(0.f, 0.f, 0.f, 0.f);
+    mx = fmaxf(mx, fmaxf(fmaxf(fabsf(x[q].x), fabsf(x[q].y)), fmaxf(fabsf(x[q].z), fabsf(x[q].w))));
+  }
+  __shared__ float rm[32];
+  mx = warp_max(mx);
+  if (lane == 0) rm[wid] = mx;
+  __syncthreads();
+  float rmax = 0.f;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) rmax = fmaxf(rmax, rm[w]);
+  const float sc = pow2_scale(rmax);
+  uint2* h2 = reinterpret_cast<uint2*>(Dh + (int64_t)row * npad);
+  uint2* l2 = reinterpret_cast<uint2*>(Dl + (int64_t)row * npad);
+#pragma unroll
+  for (int q = 0; q < VPT; ++q) {
+    const int m = tid + q * blockDim.x;
+    if (m < n4) {
+      uint16_t h[4], l[4];
+      split16(x[q].x * sc, bf16, h[0], l[0]);
+      split16(x[q].y * sc, bf16, h[1], l[1]);
+      split16(x[q].z * sc, bf16, h[2], l[2]);
+      split16(x[q].w * sc, bf16, h[3], l[3]);
+      h2[m] = make_uint2(h[0] | ((uint32_t)h[1] << 16), h[2] | ((uint32_t)h[3] << 16));
+      l2[m] = make_uint2(l[0] | ((uint32_t)l[1] << 16), l[2] | ((uint32_t)l[3] << 16));
+    }
+  }
+  if (tid == 0) rinv[row] = 1.f / sc;
+}
+
+// Rows longer than 4 * 8 * 1024 entries: one warp per row, two passes.
+__global__ void k_split_delta_wide(const float* __restrict__ Drow, int npad, int bf16,
+                                   uint16_t* __restrict__ Dh, uint16_t* __restrict__ Dl,
+                                   float* __restrict__ rinv) {
   const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (row >= npad) return;
   const float4* a = reinterpret_cast<const float4*>(Drow + (int64_t)row * npad);
@@ -138,15 +197,14 @@ __global__ void k_split_delta(const float* __restrict__ Drow, int npad, int bf16
 }
 
 // Z = unit columns E (or the rescaled warm start), padding zero.
+// Grid (ceil(npad/256), kpad): blockIdx.y is the column.
 template <typename TZ>
 __global__ void k_init_z(const void* z0, int64_t ldz0, int z0_dtype, const int32_t* icol, int n,
-                         int k, int npad, int kpad, TZ* Z, DevState* st) {
-  int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  int64_t total = (int64_t)kpad * npad;
-  if (idx >= total) return;
-  int c = (int)(idx / npad), j = (int)(idx % npad);
-  int i = icol[c];
-  double z = 0.0;
+                         int k, int npad, TZ* Z, DevState* st) {
+  const int c = blockIdx.y, j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= npad) return;
+  const int i = icol[c];
+  TZ z = TZ(0);
   if (c < k && j < n && i >= 0) {
     if (z0) {
       double piv = load_m(z0, (int64_t)c * ldz0 + i, z0_dtype);
@@ -154,12 +212,12 @@ __global__ void k_init_z(const void* z0, int64_t ldz0, int z0_dtype, const int32
         if (j == i) atomicOr(&st->flags, FLAG_ZERO_PIVOT);
         piv = 1.0;
       }
-      z = (j == i) ? 1.0 : load_m(z0, (int64_t)c * ldz0 + j, z0_dtype) / piv;
+      z = (j == i) ? TZ(1) : (TZ)(load_m(z0, (int64_t)c * ldz0 + j, z0_dtype) / piv);
     } else {
-      z = (j == i) ? 1.0 : 0.0;
+      z = (j == i) ? TZ(1) : TZ(0);
     }
   }
-  Z[idx] = (TZ)z;
+  Z[(int64_t)c * npad + j] = z;
 }
 
 // Lambda_c = theta_{i_c} + d_c (Alg. 2: Lambda = D(M Z), Z_{i_c, c} = 1).
@@ -169,12 +227,12 @@ __global__ void k_lambda(const double* theta, const int32_t* icol, const double*
   if (c < k) lambda[c] = theta[icol[c]] + d[c];
 }
 
+// Grid (ceil(n/256), k): blockIdx.y is the column.
 template <typename TI, typename TO>
-__global__ void k_copy_z(const TI* Z, int64_t ld, int n, int k, TO* out, int64_t ldo) {
-  int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (int64_t)n * k) return;
-  int c = (int)(idx / n), j = (int)(idx % n);
-  out[(int64_t)c * ldo + j] = (TO)Z[(int64_t)c * ld + j];
+__global__ void k_copy_z(const TI* __restrict__ Z, int64_t ld, int n, TO* __restrict__ out,
+                         int64_t ldo) {
+  const int c = blockIdx.y, j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < n) out[(int64_t)c * ldo + j] = (TO)Z[(int64_t)c * ld + j];
 }
 
 __global__ void k_convert_m64(const void* M, int64_t ldm, int m_dtype, int n, int npad,
@@ -190,39 +248,57 @@ inline unsigned blocks(int64_t total, int bs) { return (unsigned)((total + bs - 
 }  // namespace
 
 void launch_theta(const void* M, int64_t ldm, int m_dtype, const double* theta_in, int n,
-                  int npad, double* theta, float* th_hi, float* th_lo, cudaStream_t s) {
+                  int npad, double* theta, float* th_hi, float* th_lo, DevState* st,
+                  cudaStream_t s) {
   k_theta<<<blocks(npad, 256), 256, 0, s>>>(M, ldm, m_dtype, theta_in, n, npad, theta, th_hi,
-                                            th_lo);
+                                            th_lo, st);
 }
 
 void launch_validate(const int32_t* cols, int n, int k, int kpad, const double* theta,
                      int32_t* icol, int* count, DevState* st, cudaStream_t s) {
+  (void)theta;
   k_cols<<<blocks(kpad, 256), 256, 0, s>>>(cols, n, k, kpad, icol, count, st);
-  dim3 g(k, (unsigned)((n + 1023) / 1024));
-  k_theta_check<<<g, 256, 0, s>>>(theta, icol, count, n, st);
+  k_cols_dup<<<blocks(k, 256), 256, 0, s>>>(icol, count, k, st);
 }
 
 void launch_form_delta(const void* M, int64_t ldm, int m_dtype, const double* theta, int n,
                        int npad, const int* count, void* Drow, int drow_f64, float* DT,
-                       DevState* st, cudaStream_t s) {
+                       double* r0part, DevState* st, cudaStream_t s) {
   dim3 g(npad / 32, npad / 32), b(32, 8);
-  k_form_delta<<<g, b, 0, s>>>(M, ldm, m_dtype, theta, n, npad, count, Drow, drow_f64, DT, st);
+  if (m_dtype == IPT_DTYPE_F64 && drow_f64)
+    k_form_delta<double, double><<<g, b, 0, s>>>((const double*)M, ldm, theta, n, npad, count,
+                                                 (double*)Drow, DT, r0part);
+  else if (m_dtype == IPT_DTYPE_F64)
+    k_form_delta<double, float><<<g, b, 0, s>>>((const double*)M, ldm, theta, n, npad, count,
+                                                (float*)Drow, DT, r0part);
+  else if (drow_f64)
+    k_form_delta<float, double><<<g, b, 0, s>>>((const float*)M, ldm, theta, n, npad, count,
+                                                (double*)Drow, DT, r0part);
+  else
+    k_form_delta<float, float><<<g, b, 0, s>>>((const float*)M, ldm, theta, n, npad, count,
+                                               (float*)Drow, DT, r0part);
+  k_sum_partials<<<1, 1024, 0, s>>>(r0part, (int64_t)g.x * g.y, st);
 }
 
 void launch_split_delta(const float* Drow, int npad, int bf16, uint16_t* Dh, uint16_t* Dl,
                         float* rinv, cudaStream_t s) {
-  k_split_delta<<<(unsigned)((npad + 7) / 8), 256, 0, s>>>(Drow, npad, bf16, Dh, Dl, rinv);
+  constexpr int VPT = 8;
+  const int n4 = npad / 4;
+  if (n4 <= VPT * 1024) {
+    int threads = ((n4 + VPT - 1) / VPT + 31) / 32 * 32;
+    k_split_delta<VPT><<<npad, threads, 0, s>>>(Drow, npad, bf16, Dh, Dl, rinv);
+  } else {
+    k_split_delta_wide<<<(unsigned)((npad + 7) / 8), 256, 0, s>>>(Drow, npad, bf16, Dh, Dl, rinv);
+  }
 }
 
 void launch_init_z(const void* z0, int64_t ldz0, int z0_dtype, const int32_t* icol, int n,
                    int k, int npad, int kpad, void* Z, int z_f64, DevState* st, cudaStream_t s) {
-  int64_t total = (int64_t)kpad * npad;
+  dim3 g(blocks(npad, 256), kpad);
   if (z_f64)
-    k_init_z<double><<<blocks(total, 256), 256, 0, s>>>(z0, ldz0, z0_dtype, icol, n, k, npad,
-                                                        kpad, (double*)Z, st);
+    k_init_z<double><<<g, 256, 0, s>>>(z0, ldz0, z0_dtype, icol, n, k, npad, (double*)Z, st);
   else
-    k_init_z<float><<<blocks(total, 256), 256, 0, s>>>(z0, ldz0, z0_dtype, icol, n, k, npad,
-                                                       kpad, (float*)Z, st);
+    k_init_z<float><<<g, 256, 0, s>>>(z0, ldz0, z0_dtype, icol, n, k, npad, (float*)Z, st);
 }
 
 void launch_lambda(const double* theta, const int32_t* icol, const double* d, int k,
@@ -232,15 +308,15 @@ void launch_lambda(const double* theta, const int32_t* icol, const double* d, in
 
 void launch_copy_z(const void* Z, int z_f64, int64_t ld, int n, int k, void* out, int64_t ldo,
                    int out_f64, cudaStream_t s) {
-  unsigned g = blocks((int64_t)n * k, 256);
+  dim3 g(blocks(n, 256), k);
   if (z_f64 && out_f64)
-    k_copy_z<double, double><<<g, 256, 0, s>>>((const double*)Z, ld, n, k, (double*)out, ldo);
+    k_copy_z<double, double><<<g, 256, 0, s>>>((const double*)Z, ld, n, (double*)out, ldo);
   else if (z_f64)
-    k_copy_z<double, float><<<g, 256, 0, s>>>((const double*)Z, ld, n, k, (float*)out, ldo);
+    k_copy_z<double, float><<<g, 256, 0, s>>>((const double*)Z, ld, n, (float*)out, ldo);
   else if (out_f64)
-    k_copy_z<float, double><<<g, 256, 0, s>>>((const float*)Z, ld, n, k, (double*)out, ldo);
+    k_copy_z<float, double><<<g, 256, 0, s>>>((const float*)Z, ld, n, (double*)out, ldo);
   else
-    k_copy_z<float, float><<<g, 256, 0, s>>>((const float*)Z, ld, n, k, (float*)out, ldo);
+    k_copy_z<float, float><<<g, 256, 0, s>>>((const float*)Z, ld, n, (float*)out, ldo);
 }
 
 void launch_convert_m64(const void* M, int64_t ldm, int m_dtype, int n, int npad, double* M64,

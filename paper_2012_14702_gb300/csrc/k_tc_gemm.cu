@@ -365,8 +365,9 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
           for (int i = 0; i < 16; ++i) {
             const int ic = __shfl_sync(0xffffffffu, icl, hh * 16 + i);
             const int64_t o = (int64_t)(cb + hh * 16 + i) * ld + j;
-            z[i] = (jok && ic >= 0) ? __ldg(a.Zin + o) : 0.f;
-            dlt[i] = (jok && ic >= 0) ? __ldg(a.DT + (int64_t)ic * ld + j) : 0.f;
+            // streamed once: evict-first, so the reused operand panels stay in L2
+            z[i] = (jok && ic >= 0) ? __ldcs(a.Zin + o) : 0.f;
+            dlt[i] = (jok && ic >= 0) ? __ldcs(a.DT + (int64_t)ic * ld + j) : 0.f;
           }
 #pragma unroll
           for (int i = 0; i < 16; ++i) {
@@ -380,8 +381,10 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             const int64_t o = (int64_t)(cb + src) * ld + j;
             const float p = fmaf(v[src], rj * sc, dlt[i]);  // Delta E + Delta W
             float f, r;
-            map_entry<float>(z[i], p, dc, gap2f(hj, lj, hi, li), j == ic, f, r);
-            a.Fout[o] = f;
+            const float gap = gap2f(hj, lj, hi, li);
+            if (gap == 0.f && j != ic) flag_degenerate(a.st);
+            map_entry<float>(z[i], p, dc, gap, j == ic, f, r);
+            __stcs(a.Fout + o, f);
             const float df = f - z[i];
             s_inc = fmaf(df, df, s_inc);
             s_z = fmaf(z[i], z[i], s_z);

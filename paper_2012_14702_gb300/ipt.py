@@ -43,7 +43,8 @@ class Result(C.Structure):
                 ("increment", C.c_double), ("rho", C.c_double), ("rho_fp64", C.c_double),
                 ("r0", C.c_double), ("kernel_launches", C.c_int),
                 ("product_launches", C.c_int * 2), ("product_ms", C.c_double * 2),
-                ("prepass_ms", C.c_double), ("history_len", C.c_int),
+                ("prepass_ms", C.c_double), ("setup_ms", C.c_double),
+                ("finalize_ms", C.c_double), ("wall_ms", C.c_double), ("history_len", C.c_int),
                 ("hist_increment", C.c_double * MAX_HISTORY),
                 ("hist_rho", C.c_double * MAX_HISTORY),
                 ("hist_stage", C.c_int * MAX_HISTORY)]
@@ -56,6 +57,8 @@ class Result(C.Structure):
                 "r0": self.r0, "kernel_launches": self.kernel_launches,
                 "product_launches": list(self.product_launches),
                 "product_ms": list(self.product_ms), "prepass_ms": self.prepass_ms,
+                "setup_ms": self.setup_ms, "finalize_ms": self.finalize_ms,
+                "wall_ms": self.wall_ms,
                 "hist_increment": list(self.hist_increment[:h]),
                 "hist_rho": list(self.hist_rho[:h]),
                 "hist_stage": [PRECISION_NAME.get(s, s) for s in self.hist_stage[:h]]}
