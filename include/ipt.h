@@ -64,9 +64,13 @@ typedef enum {
   IPT_PREC_F32 = 1,    /* plain FP32: FP32 FMA product of Delta W, FP32 iterate         */
   IPT_PREC_BF16 = 2,   /* BF16 tensor-core product (tcgen05), FP32 accumulate/iterate  */
   IPT_PREC_BF16X3 = 3, /* split-BF16 x3 tensor-core product (hi*hi + hi*lo + lo*hi)    */
-  IPT_PREC_STAGED = 4, /* FP16 until the residual stops improving, then FP16 x3 (BF16 /
-                          BF16 x3 with ipt_options.staged_bf16); only the x3 stage may
-                          declare convergence                                         */
+  IPT_PREC_STAGED = 4, /* Products of V = Z - Z_b against a base iterate Z_b whose
+                          product P_b is known accurately (first E, P_b = Delta E):
+                          1-pass FP16 while its predicted error is small against the
+                          predicted next residual, else one split FP16 x3 product
+                          whose P becomes the new base (BF16 / BF16 x3 with
+                          ipt_options.staged_bf16).  Only evaluations whose predicted
+                          product error is below tol / 10 may declare convergence   */
   IPT_PREC_FP16 = 5,   /* FP16 tensor-core product, FP32 accumulate/iterate            */
   IPT_PREC_FP16X3 = 6  /* split-FP16 x3 tensor-core product                            */
 } ipt_precision;
@@ -82,8 +86,8 @@ typedef struct {
   int precision;        /* ipt_precision; default IPT_PREC_STAGED                          */
   int stop;             /* ipt_stop; default IPT_STOP_RESIDUAL                             */
   double diverge_bound; /* IPT_DIVERGED when ||Z||_F > diverge_bound*sqrt(k); default 1e8  */
-  double stage_switch;  /* STAGED: leave the 1-pass stage once the predicted next residual
-                           is below this; default 1e-4                                     */
+  double stage_switch;  /* STAGED: a 1-pass product is used while its predicted error is
+                           below stage_switch x the predicted next residual; default 0.1  */
   int staged_bf16;      /* STAGED: nonzero = BF16 / BF16 x3 stages instead of FP16 / FP16 x3 */
   int verify_fp64;      /* nonzero: recompute ||M Z - Z Lambda||_F of the result in FP64
                            (result.rho_fp64); adds one FP64 product                        */
@@ -98,7 +102,9 @@ typedef struct {
 typedef struct {
   int status;           /* ipt_status                                                     */
   int iterations;       /* evaluations of F (products with Delta)                         */
-  int stage_iters[2];   /* evaluations in the 1-pass (FP16/BF16) stage and in the others  */
+  int stage_iters[2];   /* evaluations with a 1-pass FP16/BF16 product, and with any other
+                           product; the product-free first evaluation at Z = E (P = Delta E
+                           exactly) counts in neither                                     */
   double increment;     /* ||F(Z) - Z||_F / ||Z||_F at the returned Z                     */
   double rho;           /* relative residual of the returned pair, in the product's
                            arithmetic                                                     */
@@ -115,7 +121,8 @@ typedef struct {
   int history_len;      /* min(iterations, IPT_MAX_HISTORY)                               */
   double hist_increment[IPT_MAX_HISTORY];
   double hist_rho[IPT_MAX_HISTORY];
-  int hist_stage[IPT_MAX_HISTORY]; /* precision used by each evaluation (ipt_precision)   */
+  int hist_stage[IPT_MAX_HISTORY]; /* precision of each evaluation's product (ipt_precision),
+                                      -1 for the product-free first evaluation           */
 } ipt_result;
 
 typedef struct ipt_handle ipt_handle;

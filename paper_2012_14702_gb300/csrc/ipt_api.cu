@@ -37,7 +37,7 @@ cudaError_t ensure(Buf& b, size_t bytes) {
 struct ipt_handle {
   cudaStream_t s = nullptr;
   int dev = 0;
-  Buf drow, dt, dh, dl, z[2], wh, wl, rinv, sinv;
+  Buf drow, dt, dh, dl, z[3], pbuf, wh, wl, rinv, sinv;
   Buf theta, thh, thl, icol, count, d, st, r0part;
   Buf m64, z64, racc;
   Buf hM, hTheta, hCols, hLam, hZ;  // device staging of the host-buffer entry point
@@ -81,10 +81,11 @@ inline bool bf16_operands(int prec, bool staged_bf16) {
 // Problem geometry and buffer plan for one dense solve / step.
 struct Plan {
   int n, k, npad, kpad, prec;
-  bool f64;   // FP64 iterate and product
-  bool tc;    // tensor-core buffers
-  bool bf16;  // tensor-core operands are BF16 (else FP16)
-  bool dt;    // column-major FP32 Delta (W-form epilogues)
+  bool f64;     // FP64 iterate and product
+  bool tc;      // tensor-core buffers
+  bool bf16;    // tensor-core operands are BF16 (else FP16)
+  bool dt;      // column-major FP32 Delta (W-form epilogues)
+  bool staged;  // third Z buffer and stored-P buffer (base re-use)
 };
 
 ipt_status check_dense_args(ipt_handle* h, int64_t n, const void* M, int64_t ldm, int m_dtype,
@@ -103,6 +104,10 @@ ipt_status alloc_dense(ipt_handle* h, const Plan& p) {
   CK(ensure(h->drow, nn * ez));
   CK(ensure(h->z[0], kn * ez));
   CK(ensure(h->z[1], kn * ez));
+  if (p.staged) {
+    CK(ensure(h->z[2], kn * ez));
+    CK(ensure(h->pbuf, kn * 4));
+  }
   if (p.dt) CK(ensure(h->dt, nn * 4));
   if (p.tc) {
     CK(ensure(h->dh, nn * 2));
@@ -137,16 +142,26 @@ ipt_status status_from_flags(int flags) {
 // validation flags are read back here; otherwise the caller reads them at
 // its first synchronisation, before writing any output (every setup kernel
 // is memory-safe on invalid columns or theta).
+// Initial controller state: the first evaluation's stage, product passes
+// (0 = product-free evaluation at Z = E), base and accuracy class.
+struct FirstEval {
+  int stage, passes, rebase, accurate;
+};
+
 ipt_status setup_dense(ipt_handle* h, const Plan& p, const void* M, int64_t ldm, int m_dtype,
                        const double* theta, const int32_t* cols, const void* z0, int64_t ldz0,
-                       int z0_dtype, bool rescale, int first_stage, bool sync_check) {
+                       int z0_dtype, bool rescale, FirstEval fe, bool sync_check) {
   cudaStream_t s = h->s;
   DevState* st = dst(h);
   CK(cudaMemsetAsync(st, 0, sizeof(DevState), s));
   {
     DevState init;
     memset(&init, 0, kStateHead);
-    init.stage = first_stage;
+    init.stage = fe.stage;
+    init.passes = fe.passes;
+    init.rebase = fe.rebase;
+    init.accurate = fe.accurate;
+    init.base = -1;
     CK(cudaMemcpyAsync(st, &init, kStateHead, cudaMemcpyHostToDevice, s));
   }
   CK(cudaMemsetAsync(h->count.p, 0, (size_t)p.npad * 4, s));
@@ -181,13 +196,15 @@ ipt_status setup_dense(ipt_handle* h, const Plan& p, const void* M, int64_t ldm,
   }
   const size_t kn = (size_t)p.kpad * p.npad;
   const size_t ez = p.f64 ? 8 : 4;
-  // Z buffer 1 receives F only at rows < n of columns < k: zero the rest once
-  if (p.npad > p.n)
-    CK(cudaMemset2DAsync((char*)h->z[1].p + (size_t)p.n * ez, (size_t)p.npad * ez, 0,
-                         (size_t)(p.npad - p.n) * ez, (size_t)p.kpad, s));
-  if (p.kpad > p.k)
-    CK(cudaMemsetAsync((char*)h->z[1].p + (size_t)p.k * p.npad * ez, 0,
-                       (size_t)(p.kpad - p.k) * p.npad * ez, s));
+  // Z buffers 1 and 2 receive F only at rows < n of columns < k: zero the rest once
+  for (int b = 1; b < (p.staged ? 3 : 2); ++b) {
+    if (p.npad > p.n)
+      CK(cudaMemset2DAsync((char*)h->z[b].p + (size_t)p.n * ez, (size_t)p.npad * ez, 0,
+                           (size_t)(p.npad - p.n) * ez, (size_t)p.kpad, s));
+    if (p.kpad > p.k)
+      CK(cudaMemsetAsync((char*)h->z[b].p + (size_t)p.k * p.npad * ez, 0,
+                         (size_t)(p.kpad - p.k) * p.npad * ez, s));
+  }
   if (z0 && !rescale) {
     // exact copy (single evaluation at a caller-given Z)
     CK(cudaMemsetAsync(h->z[0].p, 0, kn * (p.f64 ? 8 : 4), s));
@@ -221,13 +238,21 @@ ipt_status ensure_events(ipt_handle* h) {
   return IPT_OK;
 }
 
-// One evaluation at Z buffer `cur` in arithmetic `stage`: d, product, map.
-// With timing on, the pre-pass and the product are bracketed by events on the
-// handle's stream; collect_timing() reads them after the stream is synchronised.
-ipt_status evaluate(ipt_handle* h, const Plan& p, int cur, int stage, Timing* tm) {
+// Buffer receiving F: neither the current iterate nor the base.
+int free_buffer(int cur, int base) {
+  for (int b = 0; b < 3; ++b)
+    if (b != cur && b != base) return b;
+  return 0;
+}
+
+// One evaluation at Z buffer `cur`: d, product of V = Z - Z_base (in `passes`
+// passes of arithmetic `stage`; 0 = product-free first evaluation at Z = E),
+// map.  `rebase` stores P as the new base product.
+ipt_status evaluate(ipt_handle* h, const Plan& p, int cur, int base, int stage, int passes,
+                    int rebase, Timing* tm) {
   cudaStream_t s = h->s;
   DevState* st = dst(h);
-  const int nxt = cur ^ 1;
+  const int nxt = free_buffer(cur, base);
   const bool t = tm && tm->on;
   if (t) CK(cudaEventRecord(h->ev[0], s));
   if (p.f64) {
@@ -259,20 +284,30 @@ ipt_status evaluate(ipt_handle* h, const Plan& p, int cur, int stage, Timing* tm
     a.n = p.n;
     a.k = p.k;
     a.st = st;
-    if (stage == IPT_PREC_F32) {
+    if (passes == 0) {
+      // Z = E: P = Delta E exactly, no product (counted with the pre-pass time)
+      launch_map_first(a, p.npad, p.kpad, (double*)h->d.p, s);
+      if (t) {
+        CK(cudaEventRecord(h->ev[1], s));
+        CK(cudaEventRecord(h->ev[2], s));
+      }
+    } else if (stage == IPT_PREC_F32) {
       launch_prepass(h->drow.p, h->z[cur].p, 0, p.npad, (const int32_t*)h->icol.p, p.kpad,
                      (double*)h->d.p, st, s);
       if (t) CK(cudaEventRecord(h->ev[1], s));
       if (t) CK(cudaEventRecord(h->ev[2], s));
       launch_gemm_simt_f32((const float*)h->drow.p, a, p.npad, p.kpad, s);
     } else {
-      launch_prepass_tc((const float*)h->drow.p, (const float*)h->z[cur].p, p.npad,
+      const float* zb = base >= 0 ? (const float*)h->z[base].p : nullptr;
+      launch_prepass_tc((const float*)h->drow.p, (const float*)h->z[cur].p, zb, p.npad,
                         (const int32_t*)h->icol.p, p.kpad, p.bf16 ? 1 : 0, (double*)h->d.p,
                         (uint16_t*)h->wh.p, (uint16_t*)h->wl.p, (float*)h->sinv.p, st, s);
       if (t) CK(cudaEventRecord(h->ev[1], s));
       a.rinv = (const float*)h->rinv.p;
       a.sinv = (const float*)h->sinv.p;
-      const int passes = (stage == IPT_PREC_BF16X3 || stage == IPT_PREC_FP16X3) ? 3 : 1;
+      a.Pbase = base >= 0 ? (const float*)h->pbuf.p : (const float*)h->dt.p;
+      a.pbase_by_icol = base >= 0 ? 0 : 1;
+      a.Pout = rebase ? (float*)h->pbuf.p : nullptr;
       if (t) CK(cudaEventRecord(h->ev[2], s));
       CK(launch_gemm_tc((const uint16_t*)h->dh.p, (const uint16_t*)h->dl.p,
                         (const uint16_t*)h->wh.p, (const uint16_t*)h->wl.p, a, p.npad, p.kpad,
@@ -281,16 +316,17 @@ ipt_status evaluate(ipt_handle* h, const Plan& p, int cur, int stage, Timing* tm
   }
   CK(cudaGetLastError());
   if (t) CK(cudaEventRecord(h->ev[3], s));
-  h->launches += 2;
+  h->launches += (passes == 0 && !p.f64) ? 1 : 2;
   return IPT_OK;
 }
 
 // After the stream is synchronised: add this evaluation's event times.
-void collect_timing(ipt_handle* h, int stage, Timing* tm) {
+void collect_timing(ipt_handle* h, int passes, Timing* tm) {
   if (!tm || !tm->on) return;
   float a = 0.f, b = 0.f;
   if (cudaEventElapsedTime(&a, h->ev[0], h->ev[1]) == cudaSuccess) tm->prepass_ms += a;
-  const int slot = (stage == IPT_PREC_BF16X3 || stage == IPT_PREC_FP16X3) ? 1 : 0;
+  if (passes == 0) return;
+  const int slot = passes == 3 ? 1 : 0;
   if (cudaEventElapsedTime(&b, h->ev[2], h->ev[3]) == cudaSuccess) tm->product_ms[slot] += b;
   tm->product_launches[slot] += 1;
 }
@@ -353,6 +389,7 @@ Plan make_plan(int64_t n, int64_t k, int prec, bool staged_bf16) {
   p.tc = tensor_core(prec);
   p.bf16 = bf16_operands(prec, staged_bf16);
   p.dt = !p.f64;
+  p.staged = prec == IPT_PREC_STAGED;
   return p;
 }
 
@@ -386,12 +423,20 @@ ipt_status solve_dense(ipt_handle* h, int64_t n, const void* M, int64_t ldm, int
   const Plan p = make_plan(n, k, opt.precision, opt.staged_bf16 != 0);
   const int low = p.bf16 ? IPT_PREC_BF16 : IPT_PREC_FP16;
   const int high = p.bf16 ? IPT_PREC_BF16X3 : IPT_PREC_FP16X3;
+  // First evaluation: product-free at Z = E (FP32 / tensor-core paths), else
+  // a product; a staged solve from a warm start begins with a split product
+  // and re-bases on it.
+  FirstEval fe;
+  fe.stage = opt.precision == IPT_PREC_STAGED ? (opt.z0 ? high : low) : opt.precision;
+  fe.passes = (!p.f64 && !opt.z0)
+                  ? 0
+                  : ((fe.stage == IPT_PREC_BF16X3 || fe.stage == IPT_PREC_FP16X3) ? 3 : 1);
+  fe.rebase = (p.staged && opt.z0) ? 1 : 0;
+  fe.accurate = 1;
   v = alloc_dense(h, p);
   if (v == IPT_OK) {
-    const int first = opt.precision == IPT_PREC_STAGED ? low : opt.precision;
     if (tm.on) cudaEventRecord(h->ev[4], h->s);
-    v = setup_dense(h, p, M, ldm, m_dtype, theta, cols, opt.z0, ldz, z_dtype, true, first,
-                    false);
+    v = setup_dense(h, p, M, ldm, m_dtype, theta, cols, opt.z0, ldz, z_dtype, true, fe, false);
     if (tm.on) cudaEventRecord(h->ev[5], h->s);
   }
   if (v != IPT_OK) {
@@ -408,11 +453,11 @@ ipt_status solve_dense(ipt_handle* h, int64_t n, const void* M, int64_t ldm, int
   ca.k = (int)k;
   ca.low_stage = low;
   ca.high_stage = high;
+  ca.low_unit = p.bf16 ? 1.0 / 128.0 : 1.0 / 1024.0;  // 2^-7 (BF16), 2^-10 (FP16)
   cudaStream_t s = h->s;
-  int cur = 0;
-  int stage = opt.precision == IPT_PREC_STAGED ? low : opt.precision;
+  int cur = 0, base = -1, stage = fe.stage, passes = fe.passes, rebase = fe.rebase;
   for (int it = 0; it < max_iter; ++it) {
-    v = evaluate(h, p, cur, stage, &tm);
+    v = evaluate(h, p, cur, base, stage, passes, rebase, &tm);
     if (v != IPT_OK) break;
     launch_control(dst(h), ca, s);
     h->launches += 1;
@@ -430,14 +475,17 @@ ipt_status solve_dense(ipt_handle* h, int64_t n, const void* M, int64_t ldm, int
         if (cudaEventElapsedTime(&ms, h->ev[4], h->ev[5]) == cudaSuccess) tm.setup_ms = ms;
       }
     }
-    collect_timing(h, stage, &tm);
+    collect_timing(h, passes, &tm);
     if (h->hst->timeout) {
       v = IPT_DEVICE_TIMEOUT;
       break;
     }
     if (h->hst->done) break;
     cur = h->hst->cur;
+    base = h->hst->base;
     stage = h->hst->stage;
+    passes = h->hst->passes;
+    rebase = h->hst->rebase;
   }
   if (v != IPT_OK) {
     out->status = v;
@@ -488,7 +536,7 @@ void ipt_options_default(ipt_options* opt) {
   opt->precision = IPT_PREC_STAGED;
   opt->stop = IPT_STOP_RESIDUAL;
   opt->diverge_bound = 1e8;
-  opt->stage_switch = 1e-4;
+  opt->stage_switch = 0.1;
   opt->staged_bf16 = 0;
   opt->verify_fp64 = 0;
   opt->record_timing = 0;
@@ -526,7 +574,8 @@ ipt_status ipt_create(ipt_handle** h, void* stream) {
 ipt_status ipt_destroy(ipt_handle* h) {
   if (!h) return IPT_OK;
   DeviceGuard g(h->dev);
-  Buf* all[] = {&h->drow, &h->dt, &h->dh, &h->dl, &h->z[0], &h->z[1], &h->wh, &h->wl,
+  Buf* all[] = {&h->drow, &h->dt, &h->dh, &h->dl, &h->z[0], &h->z[1], &h->z[2], &h->pbuf,
+                &h->wh, &h->wl,
                 &h->rinv, &h->sinv, &h->theta, &h->thh, &h->thl, &h->icol, &h->count,
                 &h->r0part,
                 &h->d, &h->st, &h->m64, &h->z64, &h->racc, &h->hM, &h->hTheta, &h->hCols,
@@ -602,9 +651,14 @@ ipt_status ipt_step_dense(ipt_handle* h, int64_t n, const void* M, int64_t ldm, 
   const Plan p = make_plan(n, k, precision, false);
   v = alloc_dense(h, p);
   if (v != IPT_OK) return v;
-  v = setup_dense(h, p, M, ldm, m_dtype, theta, cols, Zin, ldz, z_dtype, false, precision, true);
+  FirstEval fe;
+  fe.stage = precision;
+  fe.passes = (precision == IPT_PREC_BF16X3 || precision == IPT_PREC_FP16X3) ? 3 : 1;
+  fe.rebase = 0;
+  fe.accurate = 1;
+  v = setup_dense(h, p, M, ldm, m_dtype, theta, cols, Zin, ldz, z_dtype, false, fe, true);
   if (v != IPT_OK) return v;
-  v = evaluate(h, p, 0, precision, nullptr);
+  v = evaluate(h, p, 0, -1, precision, fe.passes, 0, nullptr);
   if (v != IPT_OK) return v;
   cudaStream_t s = h->s;
   CK(cudaMemcpyAsync(h->hst, dst(h), kStateHead, cudaMemcpyDeviceToHost, s));

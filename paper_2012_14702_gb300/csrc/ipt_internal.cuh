@@ -41,13 +41,20 @@ struct DevState {
   double acc_inc2;  // sum (F - Z)^2
   double acc_z2;    // sum Z^2
   double acc_r2;    // sum R^2, R = M Z - Z Lambda
+  double acc_pv2;   // sum (Delta V)^2 of this evaluation's product (tensor-core epilogue)
   double r0acc;     // sum of squared off-diagonal Delta entries of requested columns
   double inc, rho, prev_rho;
+  double kappa;     // ||Delta V|| / ||V|| of the last product (staged schedule)
+  double sv;        // bound on ||Z - Z_base|| of the current iterate (staged schedule)
   int done;    // nonzero: stop; every later kernel of the solve returns at entry
   int status;  // ipt_status once done
   int stage;   // ipt_precision of the next evaluation
+  int passes;  // product passes of the next evaluation: 0 (no product), 1 or 3
+  int rebase;  // next evaluation stores P and becomes the new base
+  int accurate;  // next evaluation's product error is small enough to stop on
   int iter;    // evaluations completed
-  int cur;     // Z buffer (0/1) holding the current iterate
+  int cur;     // Z buffer (0..2) holding the current iterate
+  int base;    // Z buffer of the base iterate Z_b, or -1 for Z_b = E (P_b = Delta E)
   int answer;  // Z buffer holding the returned iterate
   int flags;   // validation flags
   int timeout; // bounded device wait gave up (code of the waiting role)
@@ -63,6 +70,12 @@ struct MapArgs {
   const T* Zin;          // current iterate, column-major [kpad x npad], leading dim ld
   T* Fout;               // F(Z), same layout
   const float* DT;       // column-major FP32 Delta (FP32 / tensor-core modes, else null)
+  // Tensor-core epilogues: P = Pbase + Delta V with V = Z - Z_base.  Pbase is
+  // DT indexed by cols[c] (Z_base = E) or a stored P indexed by c; Pout, when
+  // set, receives P (the evaluation becomes the new base).
+  const float* Pbase;
+  int pbase_by_icol;
+  float* Pout;
   const float* rinv;     // per-row inverse operand scale (tensor-core modes)
   const float* sinv;     // per-column inverse operand scale (tensor-core modes)
   const double* d;       // d_c = (Delta Z)_{cols[c], c}
@@ -99,9 +112,11 @@ void launch_convert_m64(const void* M, int64_t ldm, int m_dtype, int n, int npad
 // iteration pieces (k_iter.cu)
 void launch_prepass(const void* Drow, const void* Z, int f64, int64_t ld, const int32_t* icol,
                     int kpad, double* d, DevState* st, cudaStream_t s);
-void launch_prepass_tc(const float* Drow, const float* Z, int64_t ld, const int32_t* icol,
-                       int kpad, int bf16, double* d, uint16_t* Wh, uint16_t* Wl, float* sinv,
-                       DevState* st, cudaStream_t s);
+void launch_prepass_tc(const float* Drow, const float* Z, const float* Zbase, int64_t ld,
+                       const int32_t* icol, int kpad, int bf16, double* d, uint16_t* Wh,
+                       uint16_t* Wl, float* sinv, DevState* st, cudaStream_t s);
+// The evaluation at Z = E with no product (P = Delta E exactly): F = E - G o Delta_{., cols}.
+void launch_map_first(const MapArgs<float>& a, int npad, int kpad, double* d, cudaStream_t s);
 void launch_gemm_simt_f64(const double* Drow, const MapArgs<double>& a, int npad, int kpad,
                           cudaStream_t s);
 void launch_gemm_simt_f32(const float* Drow, const MapArgs<float>& a, int npad, int kpad,
@@ -109,9 +124,10 @@ void launch_gemm_simt_f32(const float* Drow, const MapArgs<float>& a, int npad, 
 void launch_residual_f64(const double* M64, const double* Z64, int64_t ld, const double* lam,
                          int n, int k, int npad, int kpad, double* acc, cudaStream_t s);
 struct ControlArgs {
-  double tol, diverge_bound, stage_switch;
+  double tol, diverge_bound, stage_switch;  // stage_switch: safety fraction of the staged rule
   int max_iter, stop, mode, k;
   int low_stage, high_stage;  // STAGED: the 1-pass stage and the split stage it switches to
+  double low_unit;            // STAGED: relative error model of a 1-pass product
 };
 void launch_control(DevState* st, ControlArgs a, cudaStream_t s);
 

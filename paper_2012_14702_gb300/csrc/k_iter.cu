@@ -63,12 +63,31 @@ __global__ void k_prepass(const T* __restrict__ Drow, const T* __restrict__ Z, i
   if (lane == 0) d[c] = tot;
 }
 
+// V = Z - Z_base on one float4 of column c: Z_base = E (the unit entry at
+// row i) when b4 is null, else the stored base iterate.
+__device__ __forceinline__ void subtract_base(float4& y, const float4* b4, int m, int i) {
+  if (b4) {
+    const float4 b = b4[m];
+    y.x -= b.x;
+    y.y -= b.y;
+    y.z -= b.z;
+    y.w -= b.w;
+  } else {
+    const int off = i - 4 * m;
+    y.x -= off == 0 ? 1.f : 0.f;
+    y.y -= off == 1 ? 1.f : 0.f;
+    y.z -= off == 2 ? 1.f : 0.f;
+    y.w -= off == 3 ? 1.f : 0.f;
+  }
+}
+
 // One warp per column c: d_c as in k_prepass (compensated FP32 per lane,
 // FP64 across lanes) and max |W_.c|; then W_.c * s_c split into hi/lo
 // (the column is re-read from cache).  Padding columns only get d = 0.
 template <bool BF16>
 __global__ void k_prepass_tc(const float* __restrict__ Drow, const float* __restrict__ Z,
-                             int64_t ld, const int32_t* __restrict__ icol, int kpad,
+                             const float* __restrict__ Zbase, int64_t ld,
+                             const int32_t* __restrict__ icol, int kpad,
                              double* __restrict__ d, uint16_t* __restrict__ Wh,
                              uint16_t* __restrict__ Wl, float* __restrict__ sinv,
                              const DevState* st) {
@@ -85,6 +104,7 @@ __global__ void k_prepass_tc(const float* __restrict__ Drow, const float* __rest
   }
   const float4* a4 = reinterpret_cast<const float4*>(Drow + (int64_t)i * ld);
   const float4* z4 = reinterpret_cast<const float4*>(Z + (int64_t)c * ld);
+  const float4* b4 = Zbase ? reinterpret_cast<const float4*>(Zbase + (int64_t)c * ld) : nullptr;
   float s = 0.f, comp = 0.f, mx = 0.f;
   for (int m = lane; m < ld / 4; m += 32) {
     const float4 x = __ldg(a4 + m);
@@ -94,11 +114,7 @@ __global__ void k_prepass_tc(const float* __restrict__ Drow, const float* __rest
     const float t = s + yy;
     comp = (t - s) - yy;
     s = t;
-    const int off = i - 4 * m;  // the unit entry of E in this float4, if any
-    if (off == 0) y.x -= 1.f;
-    if (off == 1) y.y -= 1.f;
-    if (off == 2) y.z -= 1.f;
-    if (off == 3) y.w -= 1.f;
+    subtract_base(y, b4, m, i);
     mx = fmaxf(mx, fmaxf(fmaxf(fabsf(y.x), fabsf(y.y)), fmaxf(fabsf(y.z), fabsf(y.w))));
   }
   const double tot = warp_sum((double)s - (double)comp);
@@ -108,11 +124,7 @@ __global__ void k_prepass_tc(const float* __restrict__ Drow, const float* __rest
   uint2* l2 = reinterpret_cast<uint2*>(Wl + (int64_t)c * ld);
   for (int m = lane; m < ld / 4; m += 32) {
     float4 y = z4[m];
-    const int off = i - 4 * m;
-    if (off == 0) y.x -= 1.f;
-    if (off == 1) y.y -= 1.f;
-    if (off == 2) y.z -= 1.f;
-    if (off == 3) y.w -= 1.f;
+    subtract_base(y, b4, m, i);
     uint16_t h[4], l[4];
     split16(y.x * sc, BF16, h[0], l[0]);
     split16(y.y * sc, BF16, h[1], l[1]);
@@ -127,13 +139,14 @@ __global__ void k_prepass_tc(const float* __restrict__ Drow, const float* __rest
   }
 }
 
-// The same pre-pass with the column held in registers: one CTA per column,
+// The same pre-pass with the column held in registers (V = Z - Z_base): one CTA per column,
 // each thread owns up to VPT float4 slots of it, so Z is read from memory
 // once (the two-pass warp kernel above re-reads the column, which at n = 8192
 // no longer fits in L1/L2 between its passes).  Used when npad <= 4*VPT*1024.
 template <bool BF16, int VPT>
 __global__ void __launch_bounds__(1024)
-    k_prepass_tc_reg(const float* __restrict__ Drow, const float* __restrict__ Z, int64_t ld,
+    k_prepass_tc_reg(const float* __restrict__ Drow, const float* __restrict__ Z,
+                     const float* __restrict__ Zbase, int64_t ld,
                      const int32_t* __restrict__ icol, double* __restrict__ d,
                      uint16_t* __restrict__ Wh, uint16_t* __restrict__ Wl,
                      float* __restrict__ sinv, const DevState* st) {
@@ -151,6 +164,7 @@ __global__ void __launch_bounds__(1024)
   const int n4 = (int)(ld / 4);
   const float4* a4 = reinterpret_cast<const float4*>(Drow + (int64_t)i * ld);
   const float4* z4 = reinterpret_cast<const float4*>(Z + (int64_t)c * ld);
+  const float4* b4 = Zbase ? reinterpret_cast<const float4*>(Zbase + (int64_t)c * ld) : nullptr;
   float4 y[VPT];
   float s = 0.f, comp = 0.f, mx = 0.f;
 #pragma unroll
@@ -165,11 +179,7 @@ __global__ void __launch_bounds__(1024)
       const float t = s + yy;
       comp = (t - s) - yy;
       s = t;
-      const int off = i - 4 * m;  // the unit entry of E in this float4, if any
-      if (off == 0) y[q].x -= 1.f;
-      if (off == 1) y[q].y -= 1.f;
-      if (off == 2) y[q].z -= 1.f;
-      if (off == 3) y[q].w -= 1.f;
+      subtract_base(y[q], b4, m, i);
       mx = fmaxf(mx, fmaxf(fmaxf(fabsf(y[q].x), fabsf(y[q].y)),
                            fmaxf(fabsf(y[q].z), fabsf(y[q].w))));
     }
@@ -404,11 +414,83 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+// ---------------------------------------------------------------- first evaluation
+// F(E) needs no product: at Z = E, P = Delta E is the column cols[c] of Delta
+// (DT, exact), d_c = Delta_{cols[c], cols[c]}, and Eq. (dyn) gives
+// F_jc = -Delta_{j, cols[c]} / (theta_j - theta_{cols[c]}) off the unit entry,
+// R = Delta_{., cols[c]} off the unit entry.  One block per column.
+__global__ void __launch_bounds__(1024)
+    k_map_first(MapArgs<float> a, double* __restrict__ d) {
+  if (a.st->done) return;
+  const int c = blockIdx.x;
+  const int ic = a.icol[c];
+  if (ic < 0) {
+    if (threadIdx.x == 0) d[c] = 0.0;
+    return;
+  }
+  const int64_t ld = a.ld;
+  const float* pc = a.DT + (int64_t)ic * ld;
+  float* fc = a.Fout + (int64_t)c * ld;
+  const float hi = a.th_hi[ic], li = a.th_lo[ic];
+  float s_inc = 0.f, s_z = 0.f, s_r = 0.f;
+  for (int j = threadIdx.x; j < a.n; j += blockDim.x) {
+    const float p = pc[j];
+    const float z = j == ic ? 1.f : 0.f;
+    const float gap = gap2f(a.th_hi[j], a.th_lo[j], hi, li);
+    if (gap == 0.f && j != ic) flag_degenerate(a.st);
+    float f, r;
+    map_entry<float>(z, p, pc[ic], gap, j == ic, f, r);
+    fc[j] = f;
+    s_inc = fmaf(f - z, f - z, s_inc);
+    s_z = fmaf(z, z, s_z);
+    s_r = fmaf(r, r, s_r);
+  }
+  __shared__ double red[3][32];
+  const double b0 = warp_sum((double)s_inc), b1 = warp_sum((double)s_z),
+               b2 = warp_sum((double)s_r);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) {
+    red[0][w] = b0;
+    red[1][w] = b1;
+    red[2][w] = b2;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t0 = 0.0, t1 = 0.0, t2 = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) {
+      t0 += red[0][q];
+      t1 += red[1][q];
+      t2 += red[2][q];
+    }
+    atomicAdd(&a.st->acc_inc2, t0);
+    atomicAdd(&a.st->acc_z2, t1);
+    atomicAdd(&a.st->acc_r2, t2);
+    d[c] = (double)pc[ic];
+  }
+}
+
 // ---------------------------------------------------------------- controller
 // One thread.  Reads the accumulators of the evaluation that just finished
 // (at iterate Z = buffer `cur`), applies the test of Alg. 2, the divergence
-// and iteration caps, the BF16 -> BF16x3 stage switch, records history and
-// clears the accumulators for the next evaluation.
+// and iteration caps, records history, chooses the next evaluation and
+// clears the accumulators.
+//
+// Staged schedule.  Every tensor-core evaluation computes P = P_b + Delta V,
+// V = Z - Z_b, for a base (Z_b, P_b) whose product is known accurately
+// (first E with P_b = Delta E exactly).  A 1-pass product of V errs by about
+// low_unit * ||Delta V||; the controller predicts ||Delta V|| of the next
+// evaluation as kappa * (bound on ||V||) and uses the 1-pass product when that
+// error is below stage_switch (0.1) times the predicted next residual, or
+// below tol / 10;
+// otherwise the next evaluation uses the split product and stores its P as
+// the new base.  Only evaluations whose predicted product error is below a
+// tenth of tol may declare convergence.
+__device__ __forceinline__ int free_buffer(int cur, int base) {
+  for (int b = 0; b < 3; ++b)
+    if (b != cur && b != base) return b;
+  return 0;
+}
+
 __global__ void k_control(DevState* st, ControlArgs a) {
   if (st->done) return;
   const int it = st->iter;
@@ -416,27 +498,30 @@ __global__ void k_control(DevState* st, ControlArgs a) {
   const double inc = sqrt(st->acc_inc2) / sqrt(z2);
   const double r0 = sqrt(st->r0acc);
   const double rho = r0 > 0.0 ? sqrt(st->acc_r2) / r0 : 0.0;
-  const int stage = st->stage;
+  const double pv = sqrt(st->acc_pv2);
+  const int stage = st->stage, passes = st->passes;
   if (it < IPT_MAX_HISTORY) {
     st->hist_inc[it] = inc;
     st->hist_rho[it] = rho;
-    st->hist_stage[it] = stage;
+    st->hist_stage[it] = passes == 0 ? -1 : stage;
   }
-  if (stage == IPT_PREC_BF16 || stage == IPT_PREC_FP16) st->stage_iters[0]++;
-  else st->stage_iters[1]++;
+  if (passes == 1 && (stage == IPT_PREC_BF16 || stage == IPT_PREC_FP16)) st->stage_iters[0]++;
+  else if (passes != 0) st->stage_iters[1]++;
   st->inc = inc;
   st->rho = rho;
   st->iter = it + 1;
   st->acc_inc2 = 0.0;
   st->acc_z2 = 0.0;
   st->acc_r2 = 0.0;
+  st->acc_pv2 = 0.0;
   const double test = a.stop == IPT_STOP_INCREMENT ? inc : rho;
-  const bool staged_low = (a.mode == IPT_PREC_STAGED && stage == a.low_stage);
+  const bool staged = a.mode == IPT_PREC_STAGED;
+  const bool can_stop = !staged || st->accurate;
   if (!isfinite(inc) || !isfinite(rho) || sqrt(z2) > a.diverge_bound * sqrt((double)a.k)) {
     st->status = IPT_DIVERGED;
     st->done = 1;
     st->answer = st->cur;
-  } else if (!staged_low && test <= a.tol) {
+  } else if (can_stop && test <= a.tol) {
     st->status = IPT_OK;
     st->done = 1;
     st->answer = st->cur;
@@ -445,16 +530,37 @@ __global__ void k_control(DevState* st, ControlArgs a) {
     st->done = 1;
     st->answer = st->cur;
   } else {
-    if (staged_low) {
-      // Leave the 1-pass stage once the geometric prediction of the next
-      // residual falls under the switch level, once it stops contracting, or
-      // once the test is already met (only the split stage may confirm it).
+    const int cur = st->cur, base = st->base;
+    const int out = free_buffer(cur, base);  // where this evaluation wrote F
+    if (staged) {
+      double kappa = st->kappa > 0.0 ? st->kappa : r0 / sqrt((double)a.k);
+      if (passes > 0 && st->sv > 0.0 && pv > 0.0) kappa = pv / st->sv;
+      st->kappa = kappa;
+      const double sv_after = st->rebase ? 0.0 : st->sv;  // ||Z_t - Z_b|| bound
+      const double sv_next = sv_after + inc * sqrt(z2);    // ||Z_{t+1} - Z_b|| bound
+      if (st->rebase) st->base = cur;
       const double prev = st->prev_rho;
-      const double q = (it > 0 && prev > 0.0) ? rho / prev : 1.0;
-      if (test <= a.tol || rho * q < a.stage_switch || (it > 0 && q > 0.5))
+      double q = (it > 0 && prev > 0.0) ? rho / prev : inc;
+      q = fmin(fmax(q, 1e-3), 1.0);
+      const double need = fmax(a.stage_switch * rho * q, 0.1 * a.tol);
+      const double e_low = r0 > 0.0 ? a.low_unit * kappa * sv_next / r0 : 0.0;
+      if (e_low <= need) {
+        st->stage = a.low_stage;
+        st->passes = 1;
+        st->rebase = 0;
+        st->accurate = e_low <= 0.1 * a.tol;
+      } else {
         st->stage = a.high_stage;
+        st->passes = 3;
+        st->rebase = 1;
+        st->accurate = 1;
+      }
+      st->sv = sv_next;
+    } else if (passes == 0) {
+      // non-staged tensor-core / FP32 solve after its product-free first evaluation
+      st->passes = (stage == IPT_PREC_BF16X3 || stage == IPT_PREC_FP16X3) ? 3 : 1;
     }
-    st->cur ^= 1;
+    st->cur = out;
   }
   st->prev_rho = rho;
 }
@@ -472,26 +578,27 @@ void launch_prepass(const void* Drow, const void* Z, int f64, int64_t ld, const 
                                        st);
 }
 
-void launch_prepass_tc(const float* Drow, const float* Z, int64_t ld, const int32_t* icol,
-                       int kpad, int bf16, double* d, uint16_t* Wh, uint16_t* Wl, float* sinv,
-                       DevState* st, cudaStream_t s) {
+void launch_prepass_tc(const float* Drow, const float* Z, const float* Zbase, int64_t ld,
+                       const int32_t* icol, int kpad, int bf16, double* d, uint16_t* Wh,
+                       uint16_t* Wl, float* sinv, DevState* st, cudaStream_t s) {
   constexpr int VPT = 8;
   const int64_t n4 = ld / 4;
   if (n4 <= (int64_t)VPT * 1024) {
     int threads = (int)((n4 + VPT - 1) / VPT);
     threads = ((threads + 31) / 32) * 32;
     if (bf16)
-      k_prepass_tc_reg<true, VPT><<<kpad, threads, 0, s>>>(Drow, Z, ld, icol, d, Wh, Wl, sinv, st);
+      k_prepass_tc_reg<true, VPT><<<kpad, threads, 0, s>>>(Drow, Z, Zbase, ld, icol, d, Wh, Wl,
+                                                            sinv, st);
     else
-      k_prepass_tc_reg<false, VPT><<<kpad, threads, 0, s>>>(Drow, Z, ld, icol, d, Wh, Wl, sinv,
-                                                             st);
+      k_prepass_tc_reg<false, VPT><<<kpad, threads, 0, s>>>(Drow, Z, Zbase, ld, icol, d, Wh, Wl,
+                                                             sinv, st);
     return;
   }
   unsigned g = (unsigned)((kpad + 7) / 8);
   if (bf16)
-    k_prepass_tc<true><<<g, 256, 0, s>>>(Drow, Z, ld, icol, kpad, d, Wh, Wl, sinv, st);
+    k_prepass_tc<true><<<g, 256, 0, s>>>(Drow, Z, Zbase, ld, icol, kpad, d, Wh, Wl, sinv, st);
   else
-    k_prepass_tc<false><<<g, 256, 0, s>>>(Drow, Z, ld, icol, kpad, d, Wh, Wl, sinv, st);
+    k_prepass_tc<false><<<g, 256, 0, s>>>(Drow, Z, Zbase, ld, icol, kpad, d, Wh, Wl, sinv, st);
 }
 
 void launch_gemm_simt_f64(const double* Drow, const MapArgs<double>& a, int npad, int kpad,
@@ -519,6 +626,11 @@ void launch_residual_f64(const double* M64, const double* Z64, int64_t ld, const
 
 void launch_control(DevState* st, ControlArgs a, cudaStream_t s) {
   k_control<<<1, 1, 0, s>>>(st, a);
+}
+
+void launch_map_first(const MapArgs<float>& a, int npad, int kpad, double* d, cudaStream_t s) {
+  (void)npad;
+  k_map_first<<<kpad, 1024, 0, s>>>(a, d);
 }
 
 }  // namespace ipt

@@ -1,17 +1,18 @@
 // Tensor-core IPT evaluation for sm_103a: P = Delta Z on tcgen05 with the map
 // of Eq. (dyn) applied in the epilogue.
 //
-// Product.  The identity part of Z is split off, Z = E + W (E = unit columns,
-// W_{cols[c], c} = 0), so P = Delta E + Delta W: the first term is the
-// column cols[c] of Delta, added exactly in FP32 by the epilogue; only
-// Delta W goes through the tensor cores.  Operands are 16-bit (FP16, or BF16)
+// Product.  A base iterate with an accurately known product is split off,
+// Z = Z_b + V, so P = P_b + Delta V.  Initially Z_b = E (unit columns) and
+// P_b = Delta E is the column cols[c] of Delta, read exactly in FP32; later a
+// staged solve re-bases on an iterate whose P it stored.  Only Delta V goes
+// through the tensor cores.  Operands are 16-bit (FP16, or BF16)
 // hi/lo splits of r_j Delta_j. and s_c W_.c with power-of-two scales r_j, s_c
 // (the pre-pass and the setup write them), so
 //   passes = 1:  P~ = Dh Wh                      (FP16: ~2^-11 relative)
 //   passes = 3:  P~ = Dh Wh + Dh Wl + Dl Wh      (FP16: ~2^-22 relative)
-// accumulated in FP32 in TMEM, and Delta W = P~ / (r_j s_c) exactly.  Because
-// |W| << 1 near the fixed point, the rounding error is scaled by |W| instead of
-// by |Z| ~ 1.
+// accumulated in FP32 in TMEM, and Delta V = P~ / (r_j s_c) exactly.  Because
+// |V| << 1 near the fixed point, the rounding error is scaled by |V| instead of
+// by |Z| ~ 1.  (Dh/Dl/Wh/Wl below hold the splits of Delta and of V.)
 //
 // Kernel shape: persistent, one CTA per SM, 192 threads.
 //   warp 0      TMA producer: 128x64 A tiles and 256x64 B tiles (16-bit,
@@ -335,7 +336,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     const int64_t ld = a.ld;
     int acc = 0;
     uint32_t acc_phase = 0;
-    float s_inc = 0.f, s_z = 0.f, s_r = 0.f;
+    float s_inc = 0.f, s_z = 0.f, s_r = 0.f, s_pv = 0.f;
     for (int t = blockIdx.x; t < num_tiles; t += gridDim.x) {
       int mb, nb;
       tile_coords(t, num_m, num_n, mb, nb);
@@ -365,9 +366,11 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
           for (int i = 0; i < 16; ++i) {
             const int ic = __shfl_sync(0xffffffffu, icl, hh * 16 + i);
             const int64_t o = (int64_t)(cb + hh * 16 + i) * ld + j;
-            // streamed once: evict-first, so the reused operand panels stay in L2
+            // P_base: column cols[c] of Delta (Z_base = E) or the stored P of column c.
+            // Streamed once: evict-first, so the reused operand panels stay in L2.
+            const int64_t ob = a.pbase_by_icol ? (int64_t)ic * ld + j : o;
             z[i] = (jok && ic >= 0) ? __ldcs(a.Zin + o) : 0.f;
-            dlt[i] = (jok && ic >= 0) ? __ldcs(a.DT + (int64_t)ic * ld + j) : 0.f;
+            dlt[i] = (jok && ic >= 0) ? __ldcs(a.Pbase + ob) : 0.f;
           }
 #pragma unroll
           for (int i = 0; i < 16; ++i) {
@@ -379,7 +382,10 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             const float li = __shfl_sync(0xffffffffu, lil, src);
             if (!jok || ic < 0) continue;
             const int64_t o = (int64_t)(cb + src) * ld + j;
-            const float p = fmaf(v[src], rj * sc, dlt[i]);  // Delta E + Delta W
+            const float dv = v[src] * (rj * sc);  // Delta V, scales undone exactly
+            const float p = dlt[i] + dv;          // P = P_base + Delta V
+            if (a.Pout) __stcs(a.Pout + o, p);
+            s_pv = fmaf(dv, dv, s_pv);
             float f, r;
             const float gap = gap2f(hj, lj, hi, li);
             if (gap == 0.f && j != ic) flag_degenerate(a.st);
@@ -400,11 +406,12 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       }
     }
     const double b0 = warp_sum((double)s_inc), b1 = warp_sum((double)s_z),
-                 b2 = warp_sum((double)s_r);
+                 b2 = warp_sum((double)s_r), b3 = warp_sum((double)s_pv);
     if (lane == 0) {
       atomicAdd(&a.st->acc_inc2, b0);
       atomicAdd(&a.st->acc_z2, b1);
       atomicAdd(&a.st->acc_r2, b2);
+      atomicAdd(&a.st->acc_pv2, b3);
     }
   }
 

@@ -28,6 +28,7 @@ STATUS = {0: "OK", 1: "MAXITER", 2: "DIVERGED", 3: "DEGENERATE_THETA", 4: "INVAL
           5: "CUDA_ERROR", 6: "DEVICE_TIMEOUT", 7: "UNSUPPORTED"}
 PRECISION = {"f64": 0, "f32": 1, "bf16": 2, "bf16x3": 3, "staged": 4, "fp16": 5, "fp16x3": 6}
 PRECISION_NAME = {v: k for k, v in PRECISION.items()}
+PRECISION_NAME[-1] = "none"  # product-free first evaluation (Z = E, P = Delta E)
 STOP = {"increment": 0, "residual": 1}
 DTYPE = {torch.float64: 0, torch.float32: 1}
 
@@ -108,7 +109,7 @@ def _dev(t, dtype=None, name="tensor"):
     return t.contiguous()
 
 
-def make_options(precision="staged", stop="residual", diverge_bound=1e8, stage_switch=1e-4,
+def make_options(precision="staged", stop="residual", diverge_bound=1e8, stage_switch=0.1,
                  verify_fp64=False, z0=None, staged_bf16=False, record_timing=False) -> Options:
     o = Options()
     _lib.ipt_options_default(C.byref(o))
@@ -148,7 +149,7 @@ class Solver:
     # ------------------------------------------------------------------ dense
     def solve_dense(self, M, theta=None, cols=None, tol=1e-6, max_iter=100, precision="staged",
                     stop="residual", z_dtype=torch.float32, verify_fp64=False, z0=None,
-                    diverge_bound=1e8, stage_switch=1e-4, staged_bf16=False,
+                    diverge_bound=1e8, stage_switch=0.1, staged_bf16=False,
                     record_timing=False):
         """Alg. 2 / Alg. 1 on the GPU.  Returns (lam [k] f64, Z (n, k) view, info dict)."""
         M = _dev(M, name="M")

@@ -111,8 +111,10 @@ def test_solve_to_residual_matches_converged_oracle(ipt, precision, n):
     err = np.linalg.norm(Z.double().cpu().numpy() - ref["Z"]) / np.linalg.norm(ref["Z"] - E)
     assert err <= 1e-4, err
     if precision == "staged":
+        # product-free first evaluation, then 1-pass FP16 and one split re-base
+        assert info["hist_stage"][0] == "none"
         assert info["stage_iters"][0] >= 1 and info["stage_iters"][1] >= 1
-        assert info["hist_stage"][0] == "fp16" and info["hist_stage"][-1] == "fp16x3"
+        assert "fp16x3" in info["hist_stage"]
 
 
 def test_partial_spectrum_dense_permuted_columns(ipt):
