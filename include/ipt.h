@@ -192,8 +192,10 @@ ipt_status ipt_step_dense(ipt_handle* h, int64_t n, const void* M, int64_t ldm, 
  *   holds all stored entries of M, diagonal ones included; Delta = M - diag(theta).
  *   theta  device, n doubles; NULL = diag(M) (0 where a row stores no diagonal)
  * Every other argument as in ipt_solve_dense.  Product arithmetic: FP32
- * (IPT_PREC_F32, the default for this call) or FP64 (IPT_PREC_F64); other
- * precisions return IPT_UNSUPPORTED.
+ * (IPT_PREC_F32; IPT_PREC_STAGED, the option default, also selects it) or
+ * FP64 (IPT_PREC_F64); other precisions return IPT_UNSUPPORTED.  A warm start
+ * (opt->z0) is not accepted here (IPT_INVALID_ARG); verify_fp64 is ignored
+ * (rho_fp64 = -1).  n < 2^30, nnz < 2^31.
  */
 ipt_status ipt_solve_csr(ipt_handle* h, int64_t n, int64_t nnz, const int32_t* rowptr,
                          const int32_t* colind, const void* vals, int v_dtype,

@@ -40,6 +40,7 @@ struct ipt_handle {
   Buf drow, dt, dh, dl, z[3], pbuf, wh, wl, rinv, sinv;
   Buf theta, thh, thl, icol, count, d, st, r0part;
   Buf m64, z64, racc;
+  Buf delta, cpart;                 // sparse path: delta_j = M_jj - theta_j, r0 partials
   Buf hM, hTheta, hCols, hLam, hZ;  // device staging of the host-buffer entry point
   DevState* hst = nullptr;          // pinned mirror of the controller's words
   cudaEvent_t ev[8] = {};           // pre-pass / product / setup / finalize brackets
@@ -577,7 +578,7 @@ ipt_status ipt_destroy(ipt_handle* h) {
   Buf* all[] = {&h->drow, &h->dt, &h->dh, &h->dl, &h->z[0], &h->z[1], &h->z[2], &h->pbuf,
                 &h->wh, &h->wl,
                 &h->rinv, &h->sinv, &h->theta, &h->thh, &h->thl, &h->icol, &h->count,
-                &h->r0part,
+                &h->r0part, &h->delta, &h->cpart,
                 &h->d, &h->st, &h->m64, &h->z64, &h->racc, &h->hM, &h->hTheta, &h->hCols,
                 &h->hLam, &h->hZ};
   for (Buf* b : all)
@@ -684,16 +685,155 @@ ipt_status ipt_step_dense(ipt_handle* h, int64_t n, const void* M, int64_t ldm, 
 ipt_status ipt_solve_csr(ipt_handle* h, int64_t n, int64_t nnz, const int32_t* rowptr,
                          const int32_t* colind, const void* vals, int v_dtype,
                          const double* theta, int64_t k, const int32_t* cols, double tol,
-                         int max_iter, const ipt_options* opt, double* lambda, void* Z,
+                         int max_iter, const ipt_options* opt_in, double* lambda, void* Z,
                          int64_t ldz, int z_dtype, ipt_result* out) {
-  (void)h; (void)n; (void)nnz; (void)rowptr; (void)colind; (void)vals; (void)v_dtype;
-  (void)theta; (void)k; (void)cols; (void)tol; (void)max_iter; (void)opt; (void)lambda;
-  (void)Z; (void)ldz; (void)z_dtype;
-  if (out) {
-    memset(out, 0, sizeof(*out));
-    out->status = IPT_UNSUPPORTED;
+  if (!out) return IPT_INVALID_ARG;
+  memset(out, 0, sizeof(*out));
+  out->rho_fp64 = -1.0;
+  ipt_options opt;
+  ipt_options_default(&opt);
+  if (opt_in) opt = *opt_in;
+  ipt_status v = IPT_OK;
+  if (!h || !rowptr || !vals || (nnz > 0 && !colind) || !lambda || !Z || n < 1 ||
+      n > (int64_t)1 << 30 || nnz < 0 || nnz >= ((int64_t)1 << 31) || k < 1 || k > n ||
+      ldz < n || !(tol >= 0.0) || max_iter < 1 ||
+      (v_dtype != IPT_DTYPE_F64 && v_dtype != IPT_DTYPE_F32) ||
+      (z_dtype != IPT_DTYPE_F64 && z_dtype != IPT_DTYPE_F32) ||
+      (opt.stop != IPT_STOP_INCREMENT && opt.stop != IPT_STOP_RESIDUAL) || opt.z0)
+    v = IPT_INVALID_ARG;
+  int prec = opt.precision == IPT_PREC_STAGED ? IPT_PREC_F32 : opt.precision;
+  if (v == IPT_OK && prec != IPT_PREC_F32 && prec != IPT_PREC_F64) v = IPT_UNSUPPORTED;
+  if (v != IPT_OK) {
+    out->status = v;
+    return v;
   }
-  return IPT_UNSUPPORTED;
+  DeviceGuard g(h->dev);
+  const auto t_start = std::chrono::steady_clock::now();
+  h->launches = 0;
+  Timing tm;
+  tm.on = opt.record_timing != 0;
+  if (tm.on && ensure_events(h) != IPT_OK) {
+    out->status = IPT_CUDA_ERROR;
+    return IPT_CUDA_ERROR;
+  }
+  const bool f64 = prec == IPT_PREC_F64;
+  const int ni = (int)n, ki = (int)k, kk = (int)round_up(k, 64);
+  const size_t ez = f64 ? 8 : 4, nk = (size_t)n * kk;
+  int nsm = 0, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const int nblk = (nsm > 0 ? nsm : 148) * 8;
+  CK(ensure(h->z[0], nk * ez));
+  CK(ensure(h->z[1], nk * ez));
+  CK(ensure(h->theta, (size_t)n * 8));
+  CK(ensure(h->thh, (size_t)n * 4));
+  CK(ensure(h->thl, (size_t)n * 4));
+  CK(ensure(h->delta, (size_t)n * 8));
+  CK(ensure(h->icol, (size_t)kk * 4));
+  CK(ensure(h->count, (size_t)n * 4));
+  CK(ensure(h->d, (size_t)kk * 8));
+  CK(ensure(h->st, sizeof(DevState)));
+  CK(ensure(h->cpart, (size_t)nblk * 8));
+  cudaStream_t s = h->s;
+  DevState* st = dst(h);
+  if (tm.on) cudaEventRecord(h->ev[4], s);
+  CK(cudaMemsetAsync(st, 0, sizeof(DevState), s));
+  {
+    DevState init;
+    memset(&init, 0, kStateHead);
+    init.stage = prec;
+    init.passes = 1;
+    init.accurate = 1;
+    init.base = -1;
+    CK(cudaMemcpyAsync(st, &init, kStateHead, cudaMemcpyHostToDevice, s));
+  }
+  CK(cudaMemsetAsync(h->count.p, 0, (size_t)n * 4, s));
+  launch_csr_theta(rowptr, colind, vals, v_dtype, theta, ni, (double*)h->theta.p,
+                   (float*)h->thh.p, (float*)h->thl.p, (double*)h->delta.p, st, s);
+  launch_validate(cols, ni, ki, kk, (const double*)h->theta.p, (int32_t*)h->icol.p,
+                  (int*)h->count.p, st, s);
+  launch_csr_r0(rowptr, colind, vals, v_dtype, ni, (const int*)h->count.p,
+                (double*)h->cpart.p, nblk, st, s);
+  launch_csr_init_z((const int32_t*)h->icol.p, ni, kk, h->z[0].p, f64 ? 1 : 0, s);
+  h->launches += 6;
+  CK(cudaGetLastError());
+  if (tm.on) cudaEventRecord(h->ev[5], s);
+  ControlArgs ca;
+  ca.tol = tol;
+  ca.diverge_bound = opt.diverge_bound;
+  ca.stage_switch = opt.stage_switch;
+  ca.max_iter = max_iter;
+  ca.stop = opt.stop;
+  ca.mode = prec;
+  ca.k = ki;
+  ca.low_stage = prec;
+  ca.high_stage = prec;
+  ca.low_unit = 0.0;
+  int cur = 0;
+  for (int it = 0; it < max_iter; ++it) {
+    if (tm.on) cudaEventRecord(h->ev[0], s);
+    launch_csr_prepass(rowptr, colind, vals, v_dtype, (const double*)h->delta.p,
+                       (const int32_t*)h->icol.p, kk, h->z[cur].p, f64 ? 1 : 0,
+                       (double*)h->d.p, st, s);
+    if (tm.on) {
+      cudaEventRecord(h->ev[1], s);
+      cudaEventRecord(h->ev[2], s);
+    }
+    launch_csr_spmm_map(rowptr, colind, vals, v_dtype, (const double*)h->delta.p,
+                        (const double*)h->theta.p, (const float*)h->thh.p,
+                        (const float*)h->thl.p, (const int32_t*)h->icol.p,
+                        (const double*)h->d.p, ni, ki, kk, h->z[cur].p, h->z[cur ^ 1].p,
+                        f64 ? 1 : 0, nblk, st, s);
+    if (tm.on) cudaEventRecord(h->ev[3], s);
+    launch_control(st, ca, s);
+    h->launches += 3;
+    if (cudaGetLastError() != cudaSuccess ||
+        cudaMemcpyAsync(h->hst, st, kStateHead, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+      v = IPT_CUDA_ERROR;
+      break;
+    }
+    if (it == 0) {
+      v = status_from_flags(h->hst->flags);
+      if (v != IPT_OK) break;
+      if (tm.on) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, h->ev[4], h->ev[5]) == cudaSuccess) tm.setup_ms = ms;
+      }
+    }
+    collect_timing(h, 1, &tm);
+    if (h->hst->done) break;
+    cur = h->hst->cur;
+  }
+  if (v != IPT_OK) {
+    out->status = v;
+    return v;
+  }
+  DevState hs;
+  if (cudaMemcpyAsync(&hs, st, sizeof(DevState), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess) {
+    out->status = IPT_CUDA_ERROR;
+    return IPT_CUDA_ERROR;
+  }
+  if (tm.on) cudaEventRecord(h->ev[6], s);
+  launch_lambda((const double*)h->theta.p, (const int32_t*)h->icol.p, (const double*)h->d.p, ki,
+                lambda, s);
+  launch_csr_out(h->z[hs.answer].p, f64 ? 1 : 0, ni, ki, kk, Z, ldz,
+                 z_dtype == IPT_DTYPE_F64 ? 1 : 0, s);
+  h->launches += 2;
+  if (tm.on) cudaEventRecord(h->ev[7], s);
+  if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) {
+    out->status = IPT_CUDA_ERROR;
+    return IPT_CUDA_ERROR;
+  }
+  if (tm.on) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, h->ev[6], h->ev[7]) == cudaSuccess) tm.finalize_ms = ms;
+  }
+  fill_result(hs, tm, h->launches, out);
+  out->wall_ms =
+      std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+  return (ipt_status)out->status;
 }
 
 }  // extern "C"

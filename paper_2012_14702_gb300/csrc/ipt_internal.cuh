@@ -138,6 +138,25 @@ cudaError_t launch_gemm_tc(const uint16_t* Dh, const uint16_t* Dl, const uint16_
                            const uint16_t* Wl, const MapArgs<float>& a, int npad, int kpad,
                            int passes, int bf16, cudaStream_t s);
 
+// sparse path (k_csr.cu): Z row-major n x kk, kk = k rounded up to 64
+void launch_csr_theta(const int32_t* rowptr, const int32_t* colind, const void* vals, int v_dtype,
+                      const double* theta_in, int n, double* theta, float* th_hi, float* th_lo,
+                      double* delta, DevState* st, cudaStream_t s);
+void launch_csr_r0(const int32_t* rowptr, const int32_t* colind, const void* vals, int v_dtype,
+                   int n, const int* count, double* part, int nblk, DevState* st,
+                   cudaStream_t s);
+void launch_csr_init_z(const int32_t* icol, int n, int kk, void* Z, int f64, cudaStream_t s);
+void launch_csr_prepass(const int32_t* rowptr, const int32_t* colind, const void* vals,
+                        int v_dtype, const double* delta, const int32_t* icol, int kk,
+                        const void* Z, int f64, double* d, DevState* st, cudaStream_t s);
+void launch_csr_spmm_map(const int32_t* rowptr, const int32_t* colind, const void* vals,
+                         int v_dtype, const double* delta, const double* theta,
+                         const float* th_hi, const float* th_lo, const int32_t* icol,
+                         const double* d, int n, int k, int kk, const void* Zin, void* Fout,
+                         int f64, int nblk, DevState* st, cudaStream_t s);
+void launch_csr_out(const void* Z, int f64, int n, int k, int kk, void* out, int64_t ldo,
+                    int out_f64, cudaStream_t s);
+
 // ---------------------------------------------------------------- device helpers
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll

@@ -111,15 +111,17 @@ def three_by_three(eps: float):
 
 
 def csr_banded(n: int, per_row: int, band: int, scale: float, seed: int,
-               theta_step: float = 1e-2, theta_jitter: float = 1e-3):
+               theta_step: float = 1e-2, theta_jitter: float = 1e-3,
+               with_diagonal: bool = True):
     """Symmetric banded CSR near-diagonal matrix (the sparse workload).
 
     For every row i, ``per_row`` distinct offsets o in {1..band} are drawn and
     the pair (i, i+o) gets a N(0,1)*scale value, mirrored to (i+o, i); pairs
-    past the last row are dropped.  The diagonal is theta (stored separately,
-    not in the CSR arrays): theta_i = i*theta_step + U(0, theta_jitter),
-    i = 1..n.  Returns (rowptr int32[n+1], colind int32[nnz], vals f64[nnz],
-    theta f64[n]); column indices are sorted within each row.
+    past the last row are dropped.  The diagonal is theta_i = i*theta_step +
+    U(0, theta_jitter), i = 1..n, stored in the CSR arrays as M_ii (unless
+    ``with_diagonal`` is False) and also returned.  Returns (rowptr int32[n+1],
+    colind int32[nnz], vals f64[nnz], theta f64[n]); column indices are
+    sorted within each row.
     """
     g = rng(seed)
     offs = g.integers(1, band + 1, size=(n, per_row), dtype=np.int64)
@@ -137,9 +139,10 @@ def csr_banded(n: int, per_row: int, band: int, scale: float, seed: int,
     v = vals.reshape(-1)
     keep = cols < n
     rows, cols, v = rows[keep], cols[keep], v[keep]
-    r_all = np.concatenate([rows, cols])
-    c_all = np.concatenate([cols, rows])
-    v_all = np.concatenate([v, v])
+    diag = np.arange(n, dtype=np.int64) if with_diagonal else np.zeros(0, dtype=np.int64)
+    r_all = np.concatenate([rows, cols, diag])
+    c_all = np.concatenate([cols, rows, diag])
+    v_all = np.concatenate([v, v, theta[diag]])
     order = np.lexsort((c_all, r_all))
     r_all, c_all, v_all = r_all[order], c_all[order], v_all[order]
     rowptr = np.zeros(n + 1, dtype=np.int64)

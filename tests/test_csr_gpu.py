@@ -1,0 +1,136 @@
+"""GPU parity of the sparse path (ipt_solve_csr) against the CPU oracle.
+
+Workloads are the banded symmetric CSR family of the sparse configuration
+(theta_i = i*theta_step + U(0, 1e-3), N(0,1)*scale off-diagonal entries) and
+the Morgan tridiagonal matrix of Section 6.1.  Tolerances: FP64 eigenvalues
+1e-10 relative, FP32 1e-5 relative; eigenvectors to the converged oracle
+within 1e-4 (relative to ||Z - E||) at rho <= 1e-6.
+"""
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2012_14702_gb300 import workloads as w
+
+pytestmark = pytest.mark.gpu
+
+
+def cuda(x, dtype):
+    return torch.as_tensor(np.ascontiguousarray(x), dtype=dtype, device="cuda")
+
+
+def csr_on_gpu(rowptr, colind, vals, dtype=torch.float32):
+    return cuda(rowptr, torch.int32), cuda(colind, torch.int32), cuda(vals, dtype)
+
+
+@pytest.mark.parametrize("precision,vdt,lam_tol", [("f64", torch.float64, 1e-10),
+                                                   ("f32", torch.float32, 1e-5)])
+@pytest.mark.parametrize("k,permute", [(8, False), (37, True), (100, False)])
+def test_csr_solve_matches_oracle(ipt, precision, vdt, lam_tol, k, permute):
+    n = 3000
+    rowptr, colind, vals, th = w.csr_banded(n, 4, 64, 1e-2, seed=3, theta_step=0.1)
+    cols = w.lowest_columns(th, k)
+    if permute:
+        cols = w.rng(2).permutation(n)[:k].astype(np.int32)
+    ref = oracle.ipt_solve_csr(rowptr, colind, vals, n, cols=cols, tol=1e-13, max_iter=200)
+    assert ref["status"] == oracle.OK
+    rp, ci, vv = csr_on_gpu(rowptr, colind, vals, vdt)
+    lam, Z, info = ipt.Solver().solve_csr(rp, ci, vv, n, cols=cuda(cols, torch.int32),
+                                          tol=1e-6 if precision == "f32" else 1e-12,
+                                          max_iter=100, precision=precision,
+                                          z_dtype=torch.float64)
+    assert info["status"] == "OK", info
+    lam = lam.cpu().numpy()
+    assert np.max(np.abs(lam - ref["lam"]) / np.abs(ref["lam"])) <= lam_tol
+    E = oracle.unit_columns(n, cols)
+    err = np.linalg.norm(Z.cpu().numpy() - ref["Z"]) / np.linalg.norm(ref["Z"] - E)
+    assert err <= (1e-4 if precision == "f32" else 1e-9), err
+
+
+def test_csr_fixed_iterations_f64_match_oracle_iterates(ipt):
+    """Same map, same iterates: max_iter evaluations in FP64 give the oracle's Z^(max_iter-1)."""
+    n = 2000
+    rowptr, colind, vals, th = w.csr_banded(n, 3, 40, 2e-2, seed=8, theta_step=0.05)
+    cols = w.lowest_columns(th, 5)
+    rp, ci, vv = csr_on_gpu(rowptr, colind, vals, torch.float64)
+    for it in [1, 3]:
+        ref = oracle.ipt_solve_csr(rowptr, colind, vals, n, cols=cols, tol=0.0, max_iter=it,
+                                   history=True)
+        lam, Z, info = ipt.Solver().solve_csr(rp, ci, vv, n, cols=cuda(cols, torch.int32),
+                                              tol=0.0, max_iter=it, precision="f64",
+                                              stop="increment", z_dtype=torch.float64)
+        assert info["status"] == "MAXITER" and info["iterations"] == it
+        assert np.max(np.abs(Z.cpu().numpy() - ref["Z"])) <= 1e-13
+        assert np.max(np.abs(lam.cpu().numpy() - ref["lam"])) <= 1e-12
+        np.testing.assert_allclose(info["hist_increment"], ref["inc_hist"], rtol=1e-10)
+
+
+def test_csr_morgan_tridiagonal_lowest_eigenpair(ipt):
+    """Section 6.1: tridiagonal M_ii = i, off-diagonal eps, lowest eigenpair (k = 1)."""
+    n, eps = 5000, 0.3
+    i = np.arange(n)
+    rows = np.concatenate([i, i[:-1], i[1:]])
+    cols = np.concatenate([i, i[1:], i[:-1]])
+    vals = np.concatenate([i + 1.0, np.full(n - 1, eps), np.full(n - 1, eps)])
+    order = np.lexsort((cols, rows))
+    rows, cols, vals = rows[order], cols[order], vals[order]
+    rowptr = np.zeros(n + 1, dtype=np.int64)
+    np.add.at(rowptr, rows + 1, 1)
+    rowptr = np.cumsum(rowptr)
+    ref = oracle.ipt_solve_csr(rowptr, cols, vals, n, cols=[0], tol=1e-12, max_iter=500,
+                               stop="increment")
+    rp, ci, vv = csr_on_gpu(rowptr, cols, vals, torch.float64)
+    lam, Z, info = ipt.Solver().solve_csr(rp, ci, vv, n, cols=cuda([0], torch.int32), tol=1e-12,
+                                          max_iter=500, precision="f64", stop="increment",
+                                          z_dtype=torch.float64)
+    assert info["status"] == "OK" and info["iterations"] == ref["iterations"]
+    assert abs(lam.item() - ref["lam"][0]) <= 1e-12 * abs(ref["lam"][0])
+    M = np.diag(i + 1.0) + eps * (np.eye(n, k=1) + np.eye(n, k=-1))
+    assert abs(lam.item() - np.linalg.eigvalsh(M[:200, :200])[0]) < 1e-10
+
+
+def test_csr_statuses(ipt):
+    n = 500
+    rowptr, colind, vals, th = w.csr_banded(n, 3, 20, 1e-2, seed=4, theta_step=0.1)
+    rp, ci, vv = csr_on_gpu(rowptr, colind, vals)
+    s = ipt.Solver()
+    _, _, info = s.solve_csr(rp, ci, vv, n, cols=cuda([0, 0], torch.int32))
+    assert info["status"] == "INVALID_ARG"
+    _, _, info = s.solve_csr(rp, ci, vv, n, cols=cuda([3, n], torch.int32))
+    assert info["status"] == "INVALID_ARG"
+    _, _, info = s.solve_csr(rp, ci, vv, n, cols=cuda([1, 2], torch.int32), precision="bf16")
+    assert info["status"] == "UNSUPPORTED"
+    thd = th.copy()
+    thd[7] = thd[3]
+    _, _, info = s.solve_csr(rp, ci, vv, n, theta=cuda(thd, torch.float64),
+                             cols=cuda([3], torch.int32))
+    assert info["status"] == "DEGENERATE_THETA"
+    _, _, info = s.solve_csr(rp, ci, vv, n, cols=cuda([3], torch.int32), precision="staged",
+                             tol=1e-6)
+    assert info["status"] == "OK" and info["hist_stage"][0] == "f32"
+
+
+def test_csr_full_size_sampled_columns_match_oracle(ipt):
+    """The sparse configuration at full size: n = 2^20, 8 offsets per row in
+    {1..2048} mirrored, values N(0,1)*1e-3, theta_i = i*1e-2 + U(0,1e-3); the 64
+    lowest eigenpairs in FP32 to rho <= 1e-6.  The oracle re-solves 8 of the 64
+    columns (Alg. 1 per column, FP64) and they must match."""
+    n = 1 << 20
+    rowptr, colind, vals, th = w.csr_banded(n, 8, 2048, 1e-3, seed=3)
+    cols = w.lowest_columns(th, 64)
+    rp, ci, vv = csr_on_gpu(rowptr, colind, vals)
+    lam, Z, info = ipt.Solver().solve_csr(rp, ci, vv, n, cols=cuda(cols, torch.int32),
+                                          tol=1e-6, max_iter=50)
+    assert info["status"] == "OK", info
+    assert info["rho"] <= 1e-6
+    pick = np.array([0, 9, 21, 33, 40, 51, 58, 63])
+    ref = oracle.ipt_solve_csr(rowptr, colind, vals, n, cols=cols[pick], tol=1e-12,
+                               max_iter=100)
+    assert ref["status"] == oracle.OK
+    assert np.max(np.abs(lam.cpu().numpy()[pick] - ref["lam"]) / np.abs(ref["lam"])) <= 1e-5
+    Zs = Z[:, torch.as_tensor(pick, device="cuda")].double().cpu().numpy()
+    E = oracle.unit_columns(n, cols[pick])
+    err = np.linalg.norm(Zs - ref["Z"]) / np.linalg.norm(ref["Z"] - E)
+    assert err <= 1e-4, err

@@ -344,10 +344,8 @@ def test_argument_errors():
 def test_csr_oracle_equals_dense_oracle():
     rowptr, colind, vals, th = w.csr_banded(400, 4, 30, 1e-2, seed=5, theta_step=0.1)
     import scipy.sparse as sp
-    Mo = sp.csr_matrix((vals, colind, rowptr), shape=(400, 400)).toarray()
-    assert np.allclose(Mo, Mo.T) and np.all(np.diag(Mo) == 0)
-    # M = diag(theta) + off-diagonal part, handed to the sparse oracle with its diagonal
-    M = Mo + np.diag(th)
+    M = sp.csr_matrix((vals, colind, rowptr), shape=(400, 400)).toarray()
+    assert np.allclose(M, M.T) and np.array_equal(np.diag(M), th)
     Ms = sp.csr_matrix(M)
     cols = w.lowest_columns(th, 8)
     rs = oracle.ipt_solve_csr(Ms.indptr, Ms.indices, Ms.data, 400, cols=cols, tol=1e-13)
@@ -364,8 +362,10 @@ def test_csr_generator_structure():
     nnz = len(colind)
     assert rowptr[0] == 0 and rowptr[-1] == nnz
     rows = np.repeat(np.arange(n), np.diff(rowptr))
-    assert np.all(np.abs(colind - rows) <= band) and np.all(colind != rows)
-    assert 2 * per_row * n - 2 * band * per_row <= nnz <= 2 * per_row * n
+    assert np.all(np.abs(colind - rows) <= band)
+    on_diag = colind == rows
+    assert on_diag.sum() == n and np.array_equal(vals[on_diag], th)
+    assert 2 * per_row * n - 2 * band * per_row <= nnz - n <= 2 * per_row * n
     for i in range(0, n, 97):
         seg = colind[rowptr[i]:rowptr[i + 1]]
         assert np.all(np.diff(seg) > 0)
