@@ -58,6 +58,8 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-cols", type=int, default=0,
                     help="columns of the oracle sample (0: sized for ~10 s)")
+    ap.add_argument("--no-csr", action="store_true",
+                    help="skip the sparse configuration's measurement")
     return ap.parse_args()
 
 
@@ -190,6 +192,62 @@ def measured_peak():
         d = json.load(open(p))
         return d.get("bf16_tflops"), d.get("bf16_tflops_sustained"), "measured"
     return 1900.0, 1700.0, "fallback"
+
+
+# ---------------------------------------------------------------- sparse configuration
+CSR_N, CSR_K = 1 << 20, 64
+
+
+def run_csr(steps, warmup, hbm_peak):
+    """Sparse partial spectrum: n = 2^20 banded symmetric CSR (8 offsets per row
+    in {1..2048}, mirrored, N(0,1)*1e-3; theta_i = i*1e-2 + U(0,1e-3)), the 64
+    lowest eigenpairs in FP32 to rho <= 1e-6.  Roofline of the SpMM + map
+    kernel against HBM bandwidth with its algorithmic bytes per launch."""
+    import torch
+    from paper_2012_14702_gb300 import ipt, workloads
+    rowptr, colind, vals, th = workloads.csr_banded(CSR_N, 8, 2048, 1e-3, seed=3)
+    cols = workloads.lowest_columns(th, CSR_K)
+    rp = torch.as_tensor(rowptr, device="cuda")
+    ci = torch.as_tensor(colind, device="cuda")
+    vv = torch.as_tensor(vals, dtype=torch.float32, device="cuda")
+    cg = torch.as_tensor(cols, device="cuda")
+    solver = ipt.Solver()
+    for _ in range(warmup):
+        solver.solve_csr(rp, ci, vv, CSR_N, cols=cg, tol=TOL, max_iter=50)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    infos = []
+    e0.record(solver.stream)
+    for _ in range(steps):
+        _, _, info = solver.solve_csr(rp, ci, vv, CSR_N, cols=cg, tol=TOL, max_iter=50,
+                                      record_timing=True)
+        infos.append(info)
+    e1.record(solver.stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    assert all(i["status"] == "OK" for i in infos), infos[-1]
+    nnz = len(colind)
+    kk = 64 * ((CSR_K + 63) // 64)
+    # rowptr + (colind, FP32 value) per entry + delta (f64) and theta hi/lo per row
+    # + the iterate read once + F written once
+    bytes_launch = 4 * (CSR_N + 1) + 8 * nnz + 16 * CSR_N + 8 * CSR_N * kk
+    launches = sum(i["product_launches"][0] for i in infos)
+    t_spmm = sum(i["product_ms"][0] for i in infos)
+    achieved = bytes_launch * launches / (t_spmm / 1e3) / 1e9
+    return {
+        "workload": f"CSR n=2^20, nnz={nnz}, 8 offsets/row in 1..2048 mirrored + diagonal, "
+                    f"N(0,1)*1e-3, theta_i=i*1e-2+U(0,1e-3), seed 3, k=64 lowest, FP32",
+        "ms_to_tol": ms, "iterations": infos[-1]["iterations"], "rho": infos[-1]["rho"],
+        "roofline": {"kernel": "k_csr_spmm_map (warp-per-row SpMM + fused IPT map)",
+                     "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": achieved / hbm_peak, "traffic": None,
+                     "bytes_per_launch": bytes_launch,
+                     "avg_launch_ms": t_spmm / max(launches, 1)},
+        "breakdown_ms": {"spmm": t_spmm / steps,
+                         "prepass": sum(i["prepass_ms"] for i in infos) / steps,
+                         "setup": sum(i["setup_ms"] for i in infos) / steps,
+                         "finalize": sum(i["finalize_ms"] for i in infos) / steps},
+    }
 
 
 # ---------------------------------------------------------------- reference arm
@@ -358,6 +416,10 @@ def run_ours(args, rank, world, local_rank):
         "gpu_launches": launches,
         "clocks": clocks,
     }
+    if not args.no_csr:
+        hbm = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("hbm_gbs", 6800.0) \
+            if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6800.0
+        line["csr"] = run_csr(max(3, min(args.steps, 10)), 2, hbm)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(M, th, args.cpu_sample_cols)
     if rank == 0:

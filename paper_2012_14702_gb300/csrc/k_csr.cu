@@ -16,6 +16,8 @@
 
 #include <math.h>
 
+#include <algorithm>
+
 namespace ipt {
 
 namespace {
@@ -35,11 +37,13 @@ __global__ void k_csr_theta(const int32_t* __restrict__ rowptr, const int32_t* _
                             double* __restrict__ delta, DevState* st) {
   const int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (j >= n) return;
-  double mjj = 0.0;
+  // the stored diagonal entry, found with integer compares (entries are unique)
+  int ediag = -1;
   for (int e = rowptr[j] + lane; e < rowptr[j + 1]; e += 32)
-    if (colind[e] == j) mjj += ldval<double>(vals, e, v_dtype);
-  mjj = warp_sum(mjj);
+    if (colind[e] == j) ediag = e;
+  for (int o = 16; o > 0; o >>= 1) ediag = max(ediag, __shfl_xor_sync(0xffffffffu, ediag, o));
   if (lane == 0) {
+    const double mjj = ediag >= 0 ? ldval<double>(vals, ediag, v_dtype) : 0.0;
     const double t = theta_in ? theta_in[j] : mjj;
     if (!isfinite(t)) atomicOr(&st->flags, FLAG_THETA_NONFINITE);
     theta[j] = t;
@@ -90,13 +94,14 @@ __global__ void k_csr_sum_r0(const double* __restrict__ part, int count, DevStat
   if (threadIdx.x == 0) st->r0acc = red[0];
 }
 
-// Z = E in the row-major layout (Z[j*kk + c] = 1 at j = cols[c]); padding zero.
+// Z = E in the row-major layout (Z[j*kk + c] = 1 at j = cols[c]); padding
+// zero.  Block: 64 columns x 4 rows; each thread writes one entry per row step.
 template <typename T>
 __global__ void k_csr_init_z(const int32_t* __restrict__ icol, int n, int kk, T* __restrict__ Z) {
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (int64_t)n * kk) return;
-  const int j = (int)(idx / kk), c = (int)(idx - (int64_t)j * kk);
-  Z[idx] = icol[c] == j ? T(1) : T(0);
+  const int c = blockIdx.y * 64 + (threadIdx.x & 63);
+  const int ic = icol[c];
+  for (int j = blockIdx.x * 4 + (threadIdx.x >> 6); j < n; j += gridDim.x * 4)
+    Z[(int64_t)j * kk + c] = ic == j ? T(1) : T(0);
 }
 
 // d_c = sum_m Delta_{i_c, m} Z_{m, c} = delta_{i_c} Z_{i_c, c} + sum over the
@@ -135,11 +140,26 @@ struct Two<double> {
   using V = double2;
 };
 
-// SpMM + map.  Persistent: a grid of `blocks` CTAs of 8 warps walks the rows;
-// each warp accumulates its row's 64-column chunk in registers (2 per lane),
-// then applies the map and writes F.  Norm partials: one atomic per warp.
 template <typename T>
-__global__ void __launch_bounds__(256)
+struct Four;
+template <>
+struct Four<float> {
+  using V = float4;
+};
+template <>
+struct Four<double> {
+  using V = double4;
+};
+
+// SpMM + map.  Persistent: a grid of CTAs of 8 warps walks the rows; each
+// half-warp owns one row at a time (two independent rows per warp, so two
+// rowptr -> colind -> gather chains are in flight), lane l of the half owns
+// the 4 columns 64*chunk + 4l .. 4l+3 and gathers them as one 16-byte vector.
+// The half loads up to 16 (column, value) pairs at once and broadcasts them
+// with width-16 shuffles; the stored diagonal gets weight 0 (delta_j is
+// applied in the epilogue).  Norm partials: one atomic per warp.
+template <typename T>
+__global__ void __launch_bounds__(256, 4)
     k_csr_spmm_map(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colind,
                    const void* __restrict__ vals, int v_dtype, const double* __restrict__ delta,
                    const double* __restrict__ theta, const float* __restrict__ th_hi,
@@ -147,77 +167,80 @@ __global__ void __launch_bounds__(256)
                    const double* __restrict__ d, int n, int k, int kk, const T* __restrict__ Zin,
                    T* __restrict__ Fout, DevState* st) {
   if (st->done) return;
-  using V2 = typename Two<T>::V;
-  const int lane = threadIdx.x & 31;
-  const int warp0 = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  const int nwarps = gridDim.x * (blockDim.x >> 5);
+  using V4 = typename Four<T>::V;
+  const int lane = threadIdx.x & 31, hl = lane & 15;
+  const unsigned hmask = (lane < 16) ? 0x0000ffffu : 0xffff0000u;
+  const int half0 = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 2 + (lane >> 4);
+  const int nhalves = gridDim.x * (blockDim.x >> 5) * 2;
   T s_inc = T(0), s_z = T(0), s_r = T(0);
   for (int ch = 0; ch < kk; ch += 64) {
-    const int c0 = ch + 2 * lane, c1 = c0 + 1;
-    const int ic0 = icol[c0], ic1 = icol[c1];
-    const T d0 = (T)d[c0], d1 = (T)d[c1];
-    double tc0 = 0.0, tc1 = 0.0;
-    float hc0 = 0.f, lc0 = 0.f, hc1 = 0.f, lc1 = 0.f;
-    if (ic0 >= 0) {
-      tc0 = theta[ic0];
-      hc0 = th_hi[ic0];
-      lc0 = th_lo[ic0];
+    const int cb = ch + 4 * hl;
+    int ic[4];
+    T dc[4];
+    double tc[4];
+    float hc[4], lc[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      ic[u] = icol[cb + u];
+      dc[u] = (T)d[cb + u];
+      tc[u] = ic[u] >= 0 ? theta[ic[u]] : 0.0;
+      hc[u] = ic[u] >= 0 ? th_hi[ic[u]] : 0.f;
+      lc[u] = ic[u] >= 0 ? th_lo[ic[u]] : 0.f;
     }
-    if (ic1 >= 0) {
-      tc1 = theta[ic1];
-      hc1 = th_hi[ic1];
-      lc1 = th_lo[ic1];
-    }
-    for (int j = warp0; j < n; j += nwarps) {
-      const int e0 = rowptr[j], e1 = rowptr[j + 1];
-      T a0 = T(0), a1 = T(0);
-      for (int eb = e0; eb < e1; eb += 32) {
-        // the warp loads up to 32 (column, value) pairs, then broadcasts them
-        const int e = eb + lane;
-        int m = -1;
+    // both halves of a warp iterate together; a half past the last row idles
+    for (int jb = half0 - (lane >> 4); jb < n; jb += nhalves) {
+      const int j = jb + (lane >> 4);
+      const bool live = j < n;
+      const int e0 = live ? rowptr[j] : 0, e1 = live ? rowptr[j + 1] : 0;
+      T acc[4] = {T(0), T(0), T(0), T(0)};
+      for (int eb = e0; eb < e1; eb += 16) {
+        const int e = eb + hl;
+        int m = j;
         T v = T(0);
         if (e < e1) {
           m = colind[e];
-          v = ldval<T>(vals, e, v_dtype);
+          v = m == j ? T(0) : ldval<T>(vals, e, v_dtype);
         }
-        const int cnt = min(32, e1 - eb);
+        const int cnt = min(16, e1 - eb);
         for (int q = 0; q < cnt; ++q) {
-          const int mq = __shfl_sync(0xffffffffu, m, q);
-          const T vq = __shfl_sync(0xffffffffu, v, q);
-          if (mq == j) continue;  // the diagonal is delta_j, applied below
-          const V2 z = *reinterpret_cast<const V2*>(Zin + (int64_t)mq * kk + c0);
-          a0 = fma(vq, z.x, a0);
-          a1 = fma(vq, z.y, a1);
+          const int mq = __shfl_sync(hmask, m, q, 16);
+          const T vq = __shfl_sync(hmask, v, q, 16);
+          const V4 z = *reinterpret_cast<const V4*>(Zin + (int64_t)mq * kk + cb);
+          acc[0] = fma(vq, z.x, acc[0]);
+          acc[1] = fma(vq, z.y, acc[1]);
+          acc[2] = fma(vq, z.z, acc[2]);
+          acc[3] = fma(vq, z.w, acc[3]);
         }
       }
-      const V2 zj = *reinterpret_cast<const V2*>(Zin + (int64_t)j * kk + c0);
+      if (!live) continue;
+      const V4 zj4 = *reinterpret_cast<const V4*>(Zin + (int64_t)j * kk + cb);
+      const T zj[4] = {zj4.x, zj4.y, zj4.z, zj4.w};
       const T dj = (T)delta[j];
-      const T p0 = fma(dj, zj.x, a0), p1 = fma(dj, zj.y, a1);
-      T f0 = T(0), f1 = T(0), r0 = T(0), r1 = T(0);
-      if (c0 < k) {
-        T gap;
-        if constexpr (sizeof(T) == 8) gap = theta[j] - tc0;
-        else gap = gap2f(th_hi[j], th_lo[j], hc0, lc0);
-        if (gap == T(0) && j != ic0) flag_degenerate(st);
-        map_entry<T>(zj.x, p0, d0, gap, j == ic0, f0, r0);
-        s_inc += (f0 - zj.x) * (f0 - zj.x);
-        s_z += zj.x * zj.x;
-        s_r += r0 * r0;
+      const float hj = th_hi[j], lj = th_lo[j];
+      T fo[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        fo[u] = T(0);
+        if (cb + u < k) {
+          const T p = fma(dj, zj[u], acc[u]);
+          T gap;
+          if constexpr (sizeof(T) == 8) gap = theta[j] - tc[u];
+          else gap = gap2f(hj, lj, hc[u], lc[u]);
+          if (gap == T(0) && j != ic[u]) flag_degenerate(st);
+          T f, r;
+          map_entry<T>(zj[u], p, dc[u], gap, j == ic[u], f, r);
+          fo[u] = f;
+          s_inc += (f - zj[u]) * (f - zj[u]);
+          s_z += zj[u] * zj[u];
+          s_r += r * r;
+        }
       }
-      if (c1 < k) {
-        T gap;
-        if constexpr (sizeof(T) == 8) gap = theta[j] - tc1;
-        else gap = gap2f(th_hi[j], th_lo[j], hc1, lc1);
-        if (gap == T(0) && j != ic1) flag_degenerate(st);
-        map_entry<T>(zj.y, p1, d1, gap, j == ic1, f1, r1);
-        s_inc += (f1 - zj.y) * (f1 - zj.y);
-        s_z += zj.y * zj.y;
-        s_r += r1 * r1;
-      }
-      V2 fo;
-      fo.x = f0;
-      fo.y = f1;
-      *reinterpret_cast<V2*>(Fout + (int64_t)j * kk + c0) = fo;
+      V4 out;
+      out.x = fo[0];
+      out.y = fo[1];
+      out.z = fo[2];
+      out.w = fo[3];
+      *reinterpret_cast<V4*>(Fout + (int64_t)j * kk + cb) = out;
     }
   }
   const double b0 = warp_sum((double)s_inc), b1 = warp_sum((double)s_z),
@@ -268,7 +291,7 @@ void launch_csr_r0(const int32_t* rowptr, const int32_t* colind, const void* val
 }
 
 void launch_csr_init_z(const int32_t* icol, int n, int kk, void* Z, int f64, cudaStream_t s) {
-  const unsigned g = nblocks((int64_t)n * kk, 256);
+  dim3 g(std::min(nblocks(n, 4), 65535u), kk / 64);
   if (f64) k_csr_init_z<double><<<g, 256, 0, s>>>(icol, n, kk, (double*)Z);
   else k_csr_init_z<float><<<g, 256, 0, s>>>(icol, n, kk, (float*)Z);
 }

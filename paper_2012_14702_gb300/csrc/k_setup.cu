@@ -196,13 +196,10 @@ __global__ void k_split_delta_wide(const float* __restrict__ Drow, int npad, int
   if (lane == 0) rinv[row] = 1.f / sc;
 }
 
-// Z = unit columns E (or the rescaled warm start), padding zero.
-// Grid (ceil(npad/256), kpad): blockIdx.y is the column.
 template <typename TZ>
-__global__ void k_init_z(const void* z0, int64_t ldz0, int z0_dtype, const int32_t* icol, int n,
-                         int k, int npad, TZ* Z, DevState* st) {
-  const int c = blockIdx.y, j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= npad) return;
+__device__ __forceinline__ void init_z_entry(const void* z0, int64_t ldz0, int z0_dtype,
+                                             const int32_t* icol, int n, int k, int npad, int c,
+                                             int j, TZ* Z, DevState* st) {
   const int i = icol[c];
   TZ z = TZ(0);
   if (c < k && j < n && i >= 0) {
@@ -220,6 +217,18 @@ __global__ void k_init_z(const void* z0, int64_t ldz0, int z0_dtype, const int32
   Z[(int64_t)c * npad + j] = z;
 }
 
+// Z = unit columns E (or the rescaled warm start), padding zero.
+// Grid (ceil(npad/1024), kpad): blockIdx.y is the column, 4 rows per thread.
+template <typename TZ>
+__global__ void k_init_z(const void* z0, int64_t ldz0, int z0_dtype, const int32_t* icol, int n,
+                         int k, int npad, TZ* Z, DevState* st) {
+  const int c = blockIdx.y;
+  for (int q = 0; q < 4; ++q) {
+    const int j = (blockIdx.x * 4 + q) * blockDim.x + threadIdx.x;
+    if (j < npad) init_z_entry(z0, ldz0, z0_dtype, icol, n, k, npad, c, j, Z, st);
+  }
+}
+
 // Lambda_c = theta_{i_c} + d_c (Alg. 2: Lambda = D(M Z), Z_{i_c, c} = 1).
 __global__ void k_lambda(const double* theta, const int32_t* icol, const double* d, int k,
                          double* lambda) {
@@ -227,12 +236,18 @@ __global__ void k_lambda(const double* theta, const int32_t* icol, const double*
   if (c < k) lambda[c] = theta[icol[c]] + d[c];
 }
 
-// Grid (ceil(n/256), k): blockIdx.y is the column.
+// Grid (ceil(n/1024), k): blockIdx.y is the column, 4 rows per thread.
 template <typename TI, typename TO>
 __global__ void k_copy_z(const TI* __restrict__ Z, int64_t ld, int n, TO* __restrict__ out,
                          int64_t ldo) {
-  const int c = blockIdx.y, j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j < n) out[(int64_t)c * ldo + j] = (TO)Z[(int64_t)c * ld + j];
+  const int c = blockIdx.y;
+  const TI* src = Z + (int64_t)c * ld;
+  TO* dst = out + (int64_t)c * ldo;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int j = (blockIdx.x * 4 + q) * blockDim.x + threadIdx.x;
+    if (j < n) dst[j] = (TO)src[j];
+  }
 }
 
 __global__ void k_convert_m64(const void* M, int64_t ldm, int m_dtype, int n, int npad,
@@ -294,7 +309,7 @@ void launch_split_delta(const float* Drow, int npad, int bf16, uint16_t* Dh, uin
 
 void launch_init_z(const void* z0, int64_t ldz0, int z0_dtype, const int32_t* icol, int n,
                    int k, int npad, int kpad, void* Z, int z_f64, DevState* st, cudaStream_t s) {
-  dim3 g(blocks(npad, 256), kpad);
+  dim3 g(blocks(npad, 1024), kpad);
   if (z_f64)
     k_init_z<double><<<g, 256, 0, s>>>(z0, ldz0, z0_dtype, icol, n, k, npad, (double*)Z, st);
   else
@@ -308,7 +323,7 @@ void launch_lambda(const double* theta, const int32_t* icol, const double* d, in
 
 void launch_copy_z(const void* Z, int z_f64, int64_t ld, int n, int k, void* out, int64_t ldo,
                    int out_f64, cudaStream_t s) {
-  dim3 g(blocks(n, 256), k);
+  dim3 g(blocks(n, 1024), k);
   if (z_f64 && out_f64)
     k_copy_z<double, double><<<g, 256, 0, s>>>((const double*)Z, ld, n, (double*)out, ldo);
   else if (z_f64)

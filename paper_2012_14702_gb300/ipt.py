@@ -216,7 +216,8 @@ class Solver:
 
     # ------------------------------------------------------------------ sparse
     def solve_csr(self, rowptr, colind, vals, n, theta=None, cols=None, tol=1e-6, max_iter=100,
-                  precision="f32", stop="residual", z_dtype=torch.float32, diverge_bound=1e8):
+                  precision="f32", stop="residual", z_dtype=torch.float32, diverge_bound=1e8,
+                  record_timing=False):
         """Sparse M (CSR, all stored entries of M).  Returns (lam, Z (n, k) view, info)."""
         rowptr = _dev(rowptr, torch.int32, "rowptr")
         colind = _dev(colind, torch.int32, "colind")
@@ -226,7 +227,7 @@ class Solver:
         k = n if cols is None else cols.numel()
         lam = torch.empty(k, dtype=torch.float64, device=vals.device)
         Zt = torch.empty((k, n), dtype=z_dtype, device=vals.device)
-        o = make_options(precision, stop, diverge_bound)
+        o = make_options(precision, stop, diverge_bound, record_timing=record_timing)
         r = Result()
         _lib.ipt_solve_csr(self._h, n, colind.numel(), _ptr(rowptr), _ptr(colind), _ptr(vals),
                            DTYPE[vals.dtype], _ptr(theta), k, _ptr(cols), float(tol),
