@@ -14,14 +14,15 @@
 // |V| << 1 near the fixed point, the rounding error is scaled by |V| instead of
 // by |Z| ~ 1.  (Dh/Dl/Wh/Wl below hold the splits of Delta and of V.)
 //
-// Kernel shape: persistent, one CTA per SM, 192 threads.
+// Kernel shape: persistent, one CTA per SM, 320 threads.
 //   warp 0      TMA producer: 128x64 A tiles and 256x64 B tiles (16-bit,
 //               128-byte swizzle) into a 4-stage shared-memory ring
 //   warp 1      TMEM allocator and single-thread tcgen05.mma issuer,
 //               M=128 N=256 K=16 per instruction, two 256-column
 //               accumulators (512 TMEM columns) so the epilogue of tile t
 //               overlaps the product of tile t+1
-//   warps 2..5  epilogue: tcgen05.ld 32 columns at a time, the map
+//   warps 2..9  epilogue, two warps per TMEM lane quarter (each owns half of
+//               the tile's 256 columns): tcgen05.ld 16 columns at a time, the map
 //               F = E + G o (Z D(Delta Z) - P), the residual
 //               R = (theta_j - theta_i) Z - (Z d - P), writes F (FP32) and
 //               the norm partials of the stopping test.
@@ -40,10 +41,15 @@ constexpr int A_BYTES = BM * BK * 2;
 constexpr int B_BYTES = BN * BK * 2;
 constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
 constexpr int TMEM_COLS = 2 * BN;
-constexpr int NUM_THREADS = 192;
-constexpr int EPI_THREADS = 128;
+constexpr int EPI_WARPS = 8;  // two per TMEM lane quarter, each owning half of the columns
+constexpr int NUM_THREADS = 64 + 32 * EPI_WARPS;
+constexpr int EPI_THREADS = 32 * EPI_WARPS;
+constexpr int EPI_COLS = BN / 2;  // columns of a tile one epilogue warp handles
 constexpr uint64_t kTimeoutNs = 2000000000ull;  // 2 s: far above any legitimate wait
-constexpr int GROUP_M = 16;                      // row blocks per L2 raster group
+#ifndef IPT_GROUP_M
+#define IPT_GROUP_M 16
+#endif
+constexpr int GROUP_M = IPT_GROUP_M;             // row blocks per L2 raster group
 
 // Order of the three split products in one accumulator.  The two correction
 // products (Dh Wl, Dl Wh; ~2^-11 of the total) go first, into a still-small
@@ -54,7 +60,18 @@ constexpr int GROUP_M = 16;                      // row blocks per L2 raster gro
 #define IPT_CORRECTIONS_FIRST 1
 #endif
 
+// Per-column data of the current tile, staged by each epilogue warp for the
+// columns it owns (one 16-byte load per column instead of five shuffles).
+struct __align__(16) ColInfo {
+  float d;   // d_c
+  float s;   // 1 / s_c (column scale of the W operand)
+  float hi;  // theta_{cols[c]} hi / lo
+  float lo;
+};
+
 struct Ctl {
+  ColInfo wcol[EPI_WARPS][EPI_COLS];
+  int wic[EPI_WARPS][EPI_COLS];
   uint64_t full[STAGES];
   uint64_t empty[STAGES];
   uint64_t tfull[2];
@@ -126,6 +143,28 @@ __device__ __forceinline__ void tma_load(void* dst, const CUtensorMap* map, uint
       : "memory");
 }
 
+// The same load with cluster multicast: the box lands at the same shared
+// memory offset in every CTA of `mask`, and each one's mbarrier at the same
+// offset receives the byte count.
+__device__ __forceinline__ void tma_load_mc(void* dst, const CUtensorMap* map, uint64_t* bar,
+                                            int x, int y, uint16_t mask) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      ".multicast::cluster [%0], [%1, {%3, %4}], [%2], %5;" ::"r"(su32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(su32(bar)), "r"(x), "r"(y), "h"(mask)
+      : "memory");
+}
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::
+                   : "memory");
+}
+
 __device__ __forceinline__ void tc_fence_before() {
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
 }
@@ -159,6 +198,32 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
       "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
           su32(bar))
       : "memory");
+}
+// Completion of this CTA's MMAs arrives on the barrier at the same offset in
+// every CTA of `mask` (releases a shared operand stage in both CTAs).
+__device__ __forceinline__ void mma_commit_mc(uint64_t* bar, uint16_t mask) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
+      " [%0], %1;" ::"r"(su32(bar)),
+      "h"(mask)
+      : "memory");
+}
+
+// 16 consecutive accumulator columns of this thread's TMEM lane; the load and
+// its completion wait are one asm statement so no use can precede the wait.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+        "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
 // 32 consecutive accumulator columns of this thread's TMEM lane; the load
@@ -197,11 +262,18 @@ __device__ __forceinline__ void fail(Ctl* ctl, DevState* st, int code) {
   atomicCAS(&st->timeout, 0, code);
 }
 
+// MC (cluster of 2 along M): the two CTAs of a cluster compute the vertically
+// adjacent tiles (2p, nb) and (2p+1, nb), which share the B tile; each CTA
+// loads one 128-row half of it and multicasts the half to both.  A stage is
+// released only when both CTAs' MMAs are done with it (two arrivals on the
+// empty barrier, one multicast commit from each CTA).  tmWh / tmWl then have
+// a 128-row box.
+template <bool MC>
 __global__ void __launch_bounds__(NUM_THREADS, 1)
     k_gemm_tc(const __grid_constant__ CUtensorMap tmDh, const __grid_constant__ CUtensorMap tmDl,
               const __grid_constant__ CUtensorMap tmWh, const __grid_constant__ CUtensorMap tmWl,
               MapArgs<float> a, int num_m, int num_n, int num_kb, int passes, uint32_t idesc) {
-  if (a.st->done) return;
+  if (a.st->done) return;  // uniform over the grid, so over each cluster
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
@@ -211,10 +283,11 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   volatile int* abort = &ctl->abort;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
+  const int rank = MC ? (int)cluster_rank() : 0;
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&ctl->full[s], 1);
-      mbar_init(&ctl->empty[s], 1);
+      mbar_init(&ctl->empty[s], MC ? 2 : 1);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&ctl->tfull[b], 1);
@@ -233,9 +306,14 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   }
   tc_fence_before();
   __syncthreads();
+  if constexpr (MC) cluster_sync();  // the peer's barriers are initialised before any multicast
   tc_fence_after();
   const uint32_t tmem = ctl->tmem_base;
-  const int num_tiles = num_m * num_n;
+  // tiles of the schedule: single tiles, or vertical tile pairs per cluster
+  const int sched_m = MC ? num_m / 2 : num_m;
+  const int num_tiles = sched_m * num_n;
+  const int t_first = MC ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;
+  const int t_step = MC ? (int)(gridDim.x >> 1) : (int)gridDim.x;
   const int total_kb = passes * num_kb;
 
   if (warp == 0) {
@@ -246,9 +324,10 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       int stage = 0;
       uint32_t phase = 0;
       bool ok = true;
-      for (int t = blockIdx.x; t < num_tiles && ok; t += gridDim.x) {
+      for (int t = t_first; t < num_tiles && ok; t += t_step) {
         int mb, nb;
-        tile_coords(t, num_m, num_n, mb, nb);
+        tile_coords(t, sched_m, num_n, mb, nb);
+        if (MC) mb = 2 * mb + rank;
         for (int kb = 0; kb < total_kb; ++kb) {
           if (!wait_bounded(&ctl->empty[stage], phase ^ 1u, abort)) {
             fail(ctl, a.st, 1);
@@ -263,8 +342,12 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
           mbar_expect_tx(&ctl->full[stage], STAGE_BYTES);
           tma_load(sA + stage * A_BYTES, role == 2 ? &tmDl : &tmDh, &ctl->full[stage], kx,
                    mb * BM);
-          tma_load(sB + stage * B_BYTES, role == 1 ? &tmWl : &tmWh, &ctl->full[stage], kx,
-                   nb * BN);
+          if constexpr (MC)
+            tma_load_mc(sB + stage * B_BYTES + rank * (B_BYTES / 2), role == 1 ? &tmWl : &tmWh,
+                        &ctl->full[stage], kx, nb * BN + rank * (BN / 2), (uint16_t)0x3);
+          else
+            tma_load(sB + stage * B_BYTES, role == 1 ? &tmWl : &tmWh, &ctl->full[stage], kx,
+                     nb * BN);
           pend_parity[stage] = (int)phase;
           if (++stage == STAGES) {
             stage = 0;
@@ -289,7 +372,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       int stage = 0, acc = 0;
       uint32_t phase = 0, acc_phase = 0;
       bool ok = true;
-      for (int t = blockIdx.x; t < num_tiles && ok; t += gridDim.x) {
+      for (int t = t_first; t < num_tiles && ok; t += t_step) {
         if (!wait_bounded(&ctl->tempty[acc], acc_phase ^ 1u, abort)) {
           fail(ctl, a.st, 2);
           break;
@@ -307,7 +390,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
 #pragma unroll
           for (int k = 0; k < BK / 16; ++k)
             mma_f16(dt, sw128_desc(ab + k * 32), sw128_desc(bb + k * 32), idesc, (kb | k) != 0);
-          mma_commit(&ctl->empty[stage]);
+          if constexpr (MC) mma_commit_mc(&ctl->empty[stage], (uint16_t)0x3);
+          else mma_commit(&ctl->empty[stage]);
           if (++stage == STAGES) {
             stage = 0;
             phase ^= 1u;
@@ -330,16 +414,37 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         }
     }
   } else {
-    // ------------------------------------------------ epilogue (warps 2..5)
-    const int q = warp & 3;  // TMEM lane quarter this warp may access
+    // ------------------------------------------------ epilogue (warps 2..9)
+    const int e = warp - 2;      // epilogue warp index
+    const int q = warp & 3;      // TMEM lane quarter this warp may access
+    const int h = e >> 2;        // which half of the tile's columns it owns
     const int row = q * 32 + lane;
     const int64_t ld = a.ld;
+    ColInfo* wcol = ctl->wcol[e];
+    int* wic = ctl->wic[e];
     int acc = 0;
     uint32_t acc_phase = 0;
     float s_inc = 0.f, s_z = 0.f, s_r = 0.f, s_pv = 0.f;
-    for (int t = blockIdx.x; t < num_tiles; t += gridDim.x) {
+    for (int t = t_first; t < num_tiles; t += t_step) {
       int mb, nb;
-      tile_coords(t, num_m, num_n, mb, nb);
+      tile_coords(t, sched_m, num_n, mb, nb);
+      if (MC) mb = 2 * mb + rank;
+      const int cbase = nb * BN + h * EPI_COLS;
+      // stage this warp's column data (its reads of the previous tile are done)
+      __syncwarp();
+#pragma unroll
+      for (int u = 0; u < EPI_COLS / 32; ++u) {
+        const int cc = lane + 32 * u, c = cbase + cc;
+        const int ic = a.icol[c];
+        ColInfo ci;
+        ci.d = (float)a.d[c];
+        ci.s = a.sinv[c];
+        ci.hi = ic >= 0 ? a.th_hi[ic] : 0.f;
+        ci.lo = ic >= 0 ? a.th_lo[ic] : 0.f;
+        wcol[cc] = ci;
+        wic[cc] = ic;
+      }
+      __syncwarp();
       if (!wait_bounded(&ctl->tfull[acc], acc_phase, abort)) {
         fail(ctl, a.st, 4);
         break;
@@ -349,53 +454,42 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       const bool jok = j < a.n;
       const float hj = a.th_hi[j], lj = a.th_lo[j], rj = a.rinv[j];
 #pragma unroll 1
-      for (int ch = 0; ch < BN / 32; ++ch) {
-        float v[32];
-        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN + ch * 32), v);
-        const int cb = nb * BN + ch * 32;
-        // per-column data, one column per lane, broadcast by shuffles below
-        const int icl = a.icol[cb + lane];
-        const float dl = (float)a.d[cb + lane];
-        const float sl = a.sinv[cb + lane];
-        const float hil = icl >= 0 ? a.th_hi[icl] : 0.f;
-        const float lil = icl >= 0 ? a.th_lo[icl] : 0.f;
+      for (int ch = 0; ch < EPI_COLS / 16; ++ch) {
+        float v[16];
+        tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) +
+                      (uint32_t)(acc * BN + h * EPI_COLS + ch * 16),
+                  v);
+        const int c0 = ch * 16;  // first owned column of this chunk
+        float z[16], pb[16];
 #pragma unroll
-        for (int hh = 0; hh < 2; ++hh) {
-          float z[16], dlt[16];
+        for (int i = 0; i < 16; ++i) {
+          const int ic = wic[c0 + i];
+          const int64_t o = (int64_t)(cbase + c0 + i) * ld + j;
+          // P_base: column cols[c] of Delta (Z_base = E) or the stored P of column c.
+          // Streamed once: evict-first, so the reused operand panels stay in L2.
+          const int64_t ob = a.pbase_by_icol ? (int64_t)ic * ld + j : o;
+          z[i] = (jok && ic >= 0) ? __ldcs(a.Zin + o) : 0.f;
+          pb[i] = (jok && ic >= 0) ? __ldcs(a.Pbase + ob) : 0.f;
+        }
 #pragma unroll
-          for (int i = 0; i < 16; ++i) {
-            const int ic = __shfl_sync(0xffffffffu, icl, hh * 16 + i);
-            const int64_t o = (int64_t)(cb + hh * 16 + i) * ld + j;
-            // P_base: column cols[c] of Delta (Z_base = E) or the stored P of column c.
-            // Streamed once: evict-first, so the reused operand panels stay in L2.
-            const int64_t ob = a.pbase_by_icol ? (int64_t)ic * ld + j : o;
-            z[i] = (jok && ic >= 0) ? __ldcs(a.Zin + o) : 0.f;
-            dlt[i] = (jok && ic >= 0) ? __ldcs(a.Pbase + ob) : 0.f;
-          }
-#pragma unroll
-          for (int i = 0; i < 16; ++i) {
-            const int src = hh * 16 + i;
-            const int ic = __shfl_sync(0xffffffffu, icl, src);
-            const float dc = __shfl_sync(0xffffffffu, dl, src);
-            const float sc = __shfl_sync(0xffffffffu, sl, src);
-            const float hi = __shfl_sync(0xffffffffu, hil, src);
-            const float li = __shfl_sync(0xffffffffu, lil, src);
-            if (!jok || ic < 0) continue;
-            const int64_t o = (int64_t)(cb + src) * ld + j;
-            const float dv = v[src] * (rj * sc);  // Delta V, scales undone exactly
-            const float p = dlt[i] + dv;          // P = P_base + Delta V
-            if (a.Pout) __stcs(a.Pout + o, p);
-            s_pv = fmaf(dv, dv, s_pv);
-            float f, r;
-            const float gap = gap2f(hj, lj, hi, li);
-            if (gap == 0.f && j != ic) flag_degenerate(a.st);
-            map_entry<float>(z[i], p, dc, gap, j == ic, f, r);
-            __stcs(a.Fout + o, f);
-            const float df = f - z[i];
-            s_inc = fmaf(df, df, s_inc);
-            s_z = fmaf(z[i], z[i], s_z);
-            s_r = fmaf(r, r, s_r);
-          }
+        for (int i = 0; i < 16; ++i) {
+          const int ic = wic[c0 + i];
+          const ColInfo ci = wcol[c0 + i];
+          if (!jok || ic < 0) continue;
+          const int64_t o = (int64_t)(cbase + c0 + i) * ld + j;
+          const float dv = v[i] * (rj * ci.s);  // Delta V, scales undone exactly
+          const float p = pb[i] + dv;           // P = P_base + Delta V
+          if (a.Pout) __stcs(a.Pout + o, p);
+          s_pv = fmaf(dv, dv, s_pv);
+          float f, r;
+          const float gap = gap2f(hj, lj, ci.hi, ci.lo);
+          if (gap == 0.f && j != ic) flag_degenerate(a.st);
+          map_entry<float>(z[i], p, ci.d, gap, j == ic, f, r);
+          __stcs(a.Fout + o, f);
+          const float df = f - z[i];
+          s_inc = fmaf(df, df, s_inc);
+          s_z = fmaf(z[i], z[i], s_z);
+          s_r = fmaf(r, r, s_r);
         }
       }
       tc_fence_before();
@@ -417,6 +511,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
 
   tc_fence_before();
   __syncthreads();
+  // the peer may still multicast into / arrive on this CTA until it is done
+  if constexpr (MC) cluster_sync();
   tc_fence_after();
   if (warp == 1)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
@@ -461,15 +557,26 @@ bool make_map(CUtensorMap* m, const void* base, uint64_t inner, uint64_t outer,
 
 }  // namespace
 
+// Two-CTA clusters with multicast B halves (IPT_TC_CLUSTER=1 at compile time,
+// used when the number of 128-row blocks is even) halve each CTA's L2 operand
+// reads; at n = 8192 they measured no faster than single CTAs, so single CTAs
+// are the default.
+#ifndef IPT_TC_CLUSTER
+#define IPT_TC_CLUSTER 0
+#endif
+
 cudaError_t launch_gemm_tc(const uint16_t* Dh, const uint16_t* Dl, const uint16_t* Wh,
                            const uint16_t* Wl, const MapArgs<float>& a, int npad, int kpad,
                            int passes, int bf16, cudaStream_t s) {
   if (npad % BM || kpad % BN || npad % BK || (passes != 1 && passes != 3))
     return cudaErrorInvalidValue;
   const bool bf = bf16 != 0;
+  const int num_m = npad / BM, num_n = kpad / BN, num_kb = npad / BK;
+  const bool mc = IPT_TC_CLUSTER && (num_m % 2 == 0);
   CUtensorMap mDh, mDl, mWh, mWl;
+  const uint32_t bbox = mc ? BN / 2 : BN;
   if (!make_map(&mDh, Dh, npad, npad, BM, bf) || !make_map(&mDl, Dl, npad, npad, BM, bf) ||
-      !make_map(&mWh, Wh, npad, kpad, BN, bf) || !make_map(&mWl, Wl, npad, kpad, BN, bf))
+      !make_map(&mWh, Wh, npad, kpad, bbox, bf) || !make_map(&mWl, Wl, npad, kpad, bbox, bf))
     return cudaErrorInvalidValue;
   static int configured_device = -1;
   static int num_sms = 0;
@@ -477,18 +584,40 @@ cudaError_t launch_gemm_tc(const uint16_t* Dh, const uint16_t* Dl, const uint16_
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (configured_device != dev) {
-    e = cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    e = cudaFuncSetAttribute(k_gemm_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_gemm_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             SMEM_BYTES);
     if (e != cudaSuccess) return e;
     e = cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
     configured_device = dev;
   }
-  const int num_m = npad / BM, num_n = kpad / BN, num_kb = npad / BK;
-  const int tiles = num_m * num_n;
-  const int grid = tiles < num_sms ? tiles : num_sms;
-  k_gemm_tc<<<grid, NUM_THREADS, SMEM_BYTES, s>>>(mDh, mDl, mWh, mWl, a, num_m, num_n, num_kb,
-                                                  passes, idesc_for(bf));
-  return cudaGetLastError();
+  const uint32_t idesc = idesc_for(bf);
+  if (!mc) {
+    const int tiles = num_m * num_n;
+    const int grid = tiles < num_sms ? tiles : num_sms;
+    k_gemm_tc<false><<<grid, NUM_THREADS, SMEM_BYTES, s>>>(mDh, mDl, mWh, mWl, a, num_m, num_n,
+                                                           num_kb, passes, idesc);
+    return cudaGetLastError();
+  }
+  const int pairs = (num_m / 2) * num_n;
+  const int clusters = pairs < num_sms / 2 ? pairs : num_sms / 2;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(2 * clusters);
+  cfg.blockDim = dim3(NUM_THREADS);
+  cfg.dynamicSmemBytes = SMEM_BYTES;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 2;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_gemm_tc<true>, mDh, mDl, mWh, mWl, a, num_m, num_n, num_kb,
+                            passes, idesc);
 }
 
 }  // namespace ipt
