@@ -125,7 +125,9 @@ ipt_status alloc_dense(ipt_handle* h, const Plan& p) {
   CK(ensure(h->count, (size_t)p.npad * 4));
   CK(ensure(h->d, (size_t)p.kpad * 8));
   CK(ensure(h->st, sizeof(DevState)));
-  CK(ensure(h->r0part, (size_t)(p.npad / 32) * (p.npad / 32) * 8));
+  // per-block partial sums: setup's ||R0||^2 and the first evaluation's norms
+  CK(ensure(h->r0part, std::max((size_t)(p.npad / 32) * (p.npad / 32),
+                                (size_t)p.kpad * ((p.npad / 4 + 255) / 256) * 3) * 8));
   return IPT_OK;
 }
 
@@ -287,7 +289,7 @@ ipt_status evaluate(ipt_handle* h, const Plan& p, int cur, int base, int stage, 
     a.st = st;
     if (passes == 0) {
       // Z = E: P = Delta E exactly, no product (counted with the pre-pass time)
-      launch_map_first(a, p.npad, p.kpad, (double*)h->d.p, s);
+      launch_map_first(a, p.npad, p.kpad, (double*)h->d.p, (double*)h->r0part.p, s);
       if (t) {
         CK(cudaEventRecord(h->ev[1], s));
         CK(cudaEventRecord(h->ev[2], s));
@@ -317,7 +319,7 @@ ipt_status evaluate(ipt_handle* h, const Plan& p, int cur, int base, int stage, 
   }
   CK(cudaGetLastError());
   if (t) CK(cudaEventRecord(h->ev[3], s));
-  h->launches += (passes == 0 && !p.f64) ? 1 : 2;
+  h->launches += 2;
   return IPT_OK;
 }
 

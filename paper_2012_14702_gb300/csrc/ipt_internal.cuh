@@ -116,7 +116,8 @@ void launch_prepass_tc(const float* Drow, const float* Z, const float* Zbase, in
                        const int32_t* icol, int kpad, int bf16, double* d, uint16_t* Wh,
                        uint16_t* Wl, float* sinv, DevState* st, cudaStream_t s);
 // The evaluation at Z = E with no product (P = Delta E exactly): F = E - G o Delta_{., cols}.
-void launch_map_first(const MapArgs<float>& a, int npad, int kpad, double* d, cudaStream_t s);
+void launch_map_first(const MapArgs<float>& a, int npad, int kpad, double* d, double* part,
+                      cudaStream_t s);
 void launch_gemm_simt_f64(const double* Drow, const MapArgs<double>& a, int npad, int kpad,
                           cudaStream_t s);
 void launch_gemm_simt_f32(const float* Drow, const MapArgs<float>& a, int npad, int kpad,

@@ -418,54 +418,83 @@ __global__ void __launch_bounds__(256)
 // F(E) needs no product: at Z = E, P = Delta E is the column cols[c] of Delta
 // (DT, exact), d_c = Delta_{cols[c], cols[c]}, and Eq. (dyn) gives
 // F_jc = -Delta_{j, cols[c]} / (theta_j - theta_{cols[c]}) off the unit entry,
-// R = Delta_{., cols[c]} off the unit entry.  One block per column.
-__global__ void __launch_bounds__(1024)
-    k_map_first(MapArgs<float> a, double* __restrict__ d) {
+// R = Delta_{., cols[c]} off the unit entry.  Grid (column c, row block);
+// each thread maps 4 consecutive rows with 16-byte loads and stores.
+__global__ void __launch_bounds__(256)
+    k_map_first(MapArgs<float> a, double* __restrict__ d, double* __restrict__ part) {
   if (a.st->done) return;
   const int c = blockIdx.x;
   const int ic = a.icol[c];
-  if (ic < 0) {
-    if (threadIdx.x == 0) d[c] = 0.0;
-    return;
-  }
   const int64_t ld = a.ld;
-  const float* pc = a.DT + (int64_t)ic * ld;
-  float* fc = a.Fout + (int64_t)c * ld;
-  const float hi = a.th_hi[ic], li = a.th_lo[ic];
+  const int j0 = (blockIdx.y * blockDim.x + threadIdx.x) * 4;
   float s_inc = 0.f, s_z = 0.f, s_r = 0.f;
-  for (int j = threadIdx.x; j < a.n; j += blockDim.x) {
-    const float p = pc[j];
-    const float z = j == ic ? 1.f : 0.f;
-    const float gap = gap2f(a.th_hi[j], a.th_lo[j], hi, li);
-    if (gap == 0.f && j != ic) flag_degenerate(a.st);
-    float f, r;
-    map_entry<float>(z, p, pc[ic], gap, j == ic, f, r);
-    fc[j] = f;
-    s_inc = fmaf(f - z, f - z, s_inc);
-    s_z = fmaf(z, z, s_z);
-    s_r = fmaf(r, r, s_r);
+  if (ic >= 0 && j0 < a.n) {
+    const float* pc = a.DT + (int64_t)ic * ld;
+    const float4 p4 = *reinterpret_cast<const float4*>(pc + j0);
+    const float4 h4 = *reinterpret_cast<const float4*>(a.th_hi + j0);
+    const float4 l4 = *reinterpret_cast<const float4*>(a.th_lo + j0);
+    const float hi = a.th_hi[ic], li = a.th_lo[ic], dc = pc[ic];
+    const float pp[4] = {p4.x, p4.y, p4.z, p4.w};
+    const float hh[4] = {h4.x, h4.y, h4.z, h4.w};
+    const float ll[4] = {l4.x, l4.y, l4.z, l4.w};
+    float f[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int j = j0 + u;
+      const float z = j == ic ? 1.f : 0.f;
+      const float gap = gap2f(hh[u], ll[u], hi, li);
+      if (j < a.n && gap == 0.f && j != ic) flag_degenerate(a.st);
+      float r;
+      map_entry<float>(z, pp[u], dc, gap, j == ic, f[u], r);
+      if (j >= a.n) f[u] = 0.f, r = 0.f;  // padding rows stay zero
+      s_inc = fmaf(f[u] - z, f[u] - z, s_inc);
+      s_z = fmaf(z, z, s_z);
+      s_r = fmaf(r, r, s_r);
+    }
+    *reinterpret_cast<float4*>(a.Fout + (int64_t)c * ld + j0) = make_float4(f[0], f[1], f[2], f[3]);
+    if (ic >= j0 && ic < j0 + 4) d[c] = (double)dc;
+  } else if (ic < 0 && blockIdx.y == 0 && threadIdx.x == 0) {
+    d[c] = 0.0;
   }
-  __shared__ double red[3][32];
-  const double b0 = warp_sum((double)s_inc), b1 = warp_sum((double)s_z),
-               b2 = warp_sum((double)s_r);
+  // block partials of the three norms (summed by k_sum_norms)
+  __shared__ float red[3][8];
+  const float w0 = warp_sum(s_inc), w1 = warp_sum(s_z), w2 = warp_sum(s_r);
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
   if (l == 0) {
-    red[0][w] = b0;
-    red[1][w] = b1;
-    red[2][w] = b2;
+    red[0][w] = w0;
+    red[1][w] = w1;
+    red[2][w] = w2;
   }
   __syncthreads();
+  if (threadIdx.x < 3) {
+    double t = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += (double)red[threadIdx.x][q];
+    part[((int64_t)blockIdx.x * gridDim.y + blockIdx.y) * 3 + threadIdx.x] = t;
+  }
+}
+
+// One block: the evaluation's norm accumulators from per-block partials.
+__global__ void k_sum_norms(const double* __restrict__ part, int64_t count, DevState* st) {
+  __shared__ double red[3][256];
+  double t0 = 0.0, t1 = 0.0, t2 = 0.0;
+  for (int64_t i = threadIdx.x; i < count; i += blockDim.x) {
+    t0 += part[3 * i];
+    t1 += part[3 * i + 1];
+    t2 += part[3 * i + 2];
+  }
+  red[0][threadIdx.x] = t0;
+  red[1][threadIdx.x] = t1;
+  red[2][threadIdx.x] = t2;
+  __syncthreads();
+  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+    if ((int)threadIdx.x < h)
+      for (int q = 0; q < 3; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + h];
+    __syncthreads();
+  }
   if (threadIdx.x == 0) {
-    double t0 = 0.0, t1 = 0.0, t2 = 0.0;
-    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) {
-      t0 += red[0][q];
-      t1 += red[1][q];
-      t2 += red[2][q];
-    }
-    atomicAdd(&a.st->acc_inc2, t0);
-    atomicAdd(&a.st->acc_z2, t1);
-    atomicAdd(&a.st->acc_r2, t2);
-    d[c] = (double)pc[ic];
+    st->acc_inc2 += red[0][0];
+    st->acc_z2 += red[1][0];
+    st->acc_r2 += red[2][0];
   }
 }
 
@@ -628,9 +657,11 @@ void launch_control(DevState* st, ControlArgs a, cudaStream_t s) {
   k_control<<<1, 1, 0, s>>>(st, a);
 }
 
-void launch_map_first(const MapArgs<float>& a, int npad, int kpad, double* d, cudaStream_t s) {
-  (void)npad;
-  k_map_first<<<kpad, 1024, 0, s>>>(a, d);
+void launch_map_first(const MapArgs<float>& a, int npad, int kpad, double* d, double* part,
+                      cudaStream_t s) {
+  dim3 g(kpad, (npad / 4 + 255) / 256);
+  k_map_first<<<g, 256, 0, s>>>(a, d, part);
+  k_sum_norms<<<1, 256, 0, s>>>(part, (int64_t)g.x * g.y, a.st);
 }
 
 }  // namespace ipt

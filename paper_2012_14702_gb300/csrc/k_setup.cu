@@ -108,6 +108,73 @@ __global__ void k_form_delta(const TM* __restrict__ M, int64_t ldm, const double
   }
 }
 
+// The same for FP32 M with 16-byte aligned rows: tile 32 rows x 128 columns,
+// block 32 x 8, each thread moves 4 consecutive columns of 4 rows with 16-byte
+// loads and stores; the transposed FP32 copy goes through a 129-float padded
+// shared tile (conflict-free column reads) as 128-byte column segments.
+template <typename TD>
+__global__ void __launch_bounds__(256)
+    k_form_delta4(const float* __restrict__ M, int64_t ldm, const double* theta, int n,
+                  int npad, const int* count, TD* __restrict__ Drow, float* __restrict__ DT,
+                  double* __restrict__ r0part) {
+  __shared__ float tile[32][129];
+  const int c0 = blockIdx.x * 128, r0 = blockIdx.y * 32;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int j = c0 + 4 * tx;
+  bool req[4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) req[u] = (j + u < n) && count[j + u] > 0;
+  float r0sum = 0.f;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int i = r0 + ty + 8 * q;
+    float v[4] = {0.f, 0.f, 0.f, 0.f};
+    if (i < n) {
+      if (j + 3 < n) {
+        const float4 m4 = *reinterpret_cast<const float4*>(M + (int64_t)i * ldm + j);
+        v[0] = m4.x;
+        v[1] = m4.y;
+        v[2] = m4.z;
+        v[3] = m4.w;
+      } else {
+        for (int u = 0; u < 4; ++u)
+          if (j + u < n) v[u] = M[(int64_t)i * ldm + j + u];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (j + u == i) v[u] = (float)((double)v[u] - theta[i]);  // Delta_ii, formed in FP64
+        else if (req[u]) r0sum = fmaf(v[u], v[u], r0sum);
+      }
+    }
+    TD* dst = Drow + (int64_t)i * npad + j;
+    if constexpr (sizeof(TD) == 4) {
+      *reinterpret_cast<float4*>(dst) = make_float4(v[0], v[1], v[2], v[3]);
+    } else {
+      for (int u = 0; u < 4; ++u) dst[u] = (TD)v[u];
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) tile[ty + 8 * q][4 * tx + u] = v[u];
+  }
+  if (DT) {
+    __syncthreads();
+    const int w = ty;  // 8 warps, 16 columns each
+#pragma unroll 4
+    for (int cc = 0; cc < 16; ++cc) {
+      const int col = w * 16 + cc;
+      DT[(int64_t)(c0 + col) * npad + r0 + tx] = tile[tx][col];
+    }
+  }
+  __shared__ float red[8];
+  const float wsum = warp_sum(r0sum);
+  if (tx == 0) red[ty] = wsum;
+  __syncthreads();
+  if (tx == 0 && ty == 0) {
+    double t = 0.0;
+    for (int q = 0; q < 8; ++q) t += (double)red[q];
+    r0part[(int64_t)blockIdx.y * gridDim.x + blockIdx.x] = t;
+  }
+}
+
 // One block: st->r0acc = sum of the per-block partials, in a fixed order.
 __global__ void k_sum_partials(const double* __restrict__ part, int64_t count, DevState* st) {
   __shared__ double red[1024];
@@ -279,7 +346,16 @@ void launch_validate(const int32_t* cols, int n, int k, int kpad, const double* 
 void launch_form_delta(const void* M, int64_t ldm, int m_dtype, const double* theta, int n,
                        int npad, const int* count, void* Drow, int drow_f64, float* DT,
                        double* r0part, DevState* st, cudaStream_t s) {
-  dim3 g(npad / 32, npad / 32), b(32, 8);
+  dim3 b(32, 8);
+  if (m_dtype == IPT_DTYPE_F32 && !drow_f64 && ldm % 4 == 0 &&
+      (reinterpret_cast<uintptr_t>(M) & 15) == 0) {
+    dim3 g4(npad / 128, npad / 32);
+    k_form_delta4<float><<<g4, b, 0, s>>>((const float*)M, ldm, theta, n, npad, count,
+                                          (float*)Drow, DT, r0part);
+    k_sum_partials<<<1, 1024, 0, s>>>(r0part, (int64_t)g4.x * g4.y, st);
+    return;
+  }
+  dim3 g(npad / 32, npad / 32);
   if (m_dtype == IPT_DTYPE_F64 && drow_f64)
     k_form_delta<double, double><<<g, b, 0, s>>>((const double*)M, ldm, theta, n, npad, count,
                                                  (double*)Drow, DT, r0part);
