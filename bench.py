@@ -65,6 +65,7 @@ def parse_args():
 
 def workload(n):
     from paper_2012_14702_gb300 import workloads
+    assert workloads.DENSE_CONFIGS["dense_n8192_eps1e-3"] == (8192, THETA_STEP, EPS, SEED)
     return workloads.dense_symmetric(n, EPS, SEED, theta_step=THETA_STEP)
 
 
@@ -166,24 +167,43 @@ class ClockSampler:
                 "reasons": sorted(reasons)}
 
 
+# ---------------------------------------------------------------- ranks
+def max_over_ranks(x, world, device):
+    """The largest of every rank's `x` (the timed region's max over ranks); `device`
+    is where the backend's tensors live (cuda for NCCL, cpu for gloo)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 # ---------------------------------------------------------------- profile summary
-def kernel_source_hash():
-    p = os.path.join(ROOT, "paper_2012_14702_gb300", "csrc", "k_tc_gemm.cu")
+def kernel_source_hash(source):
+    p = os.path.join(ROOT, "paper_2012_14702_gb300", "csrc", source)
     return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
 
 
-def profiled_traffic():
-    """DRAM bytes per launch of the product kernel from the committed ncu
-    summary, if it was taken from the current kernel source."""
-    p = os.path.join(ROOT, "profiles", "k_gemm_tc_dense_n8192.md")
+def profiled_traffic(profile, source, keys):
+    """DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from a
+    committed ncu summary, for each of `keys`, if the summary was taken from the
+    current kernel source; else None."""
+    p = os.path.join(ROOT, "profiles", profile)
     if not os.path.exists(p):
         return None
     text = open(p).read()
     h = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", text)
-    t = re.search(r"traffic_bytes_per_launch_3pass:\s*([0-9.eE+]+)", text)
-    if not h or not t or h.group(1) != kernel_source_hash():
+    if not h or h.group(1) != kernel_source_hash(source):
         return None
-    return float(t.group(1))
+    out = {}
+    for k in keys:
+        t = re.search(k + r":\s*([0-9.eE+]+)", text)
+        if not t:
+            return None
+        out[k] = float(t.group(1))
+    return out
 
 
 def measured_peak():
@@ -205,7 +225,9 @@ def run_csr(steps, warmup, hbm_peak):
     kernel against HBM bandwidth with its algorithmic bytes per launch."""
     import torch
     from paper_2012_14702_gb300 import ipt, workloads
-    rowptr, colind, vals, th = workloads.csr_banded(CSR_N, 8, 2048, 1e-3, seed=3)
+    n_, per_row, band, scale, seed, k_ = workloads.CSR_CONFIGS["csr_n2p20_k64"]
+    assert (n_, k_) == (CSR_N, CSR_K)
+    rowptr, colind, vals, th = workloads.csr_banded(CSR_N, per_row, band, scale, seed=seed)
     cols = workloads.lowest_columns(th, CSR_K)
     rp = torch.as_tensor(rowptr, device="cuda")
     ci = torch.as_tensor(colind, device="cuda")
@@ -240,7 +262,10 @@ def run_csr(steps, warmup, hbm_peak):
         "ms_to_tol": ms, "iterations": infos[-1]["iterations"], "rho": infos[-1]["rho"],
         "roofline": {"kernel": "k_csr_spmm_map (warp-per-row SpMM + fused IPT map)",
                      "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                     "frac": achieved / hbm_peak, "traffic": None,
+                     "frac": achieved / hbm_peak,
+                     "traffic": (profiled_traffic("k_csr_spmm_map_csr_n2p20_k64.md", "k_csr.cu",
+                                                  ["traffic_bytes_per_launch"]) or {}).get(
+                                                      "traffic_bytes_per_launch"),
                      "bytes_per_launch": bytes_launch,
                      "avg_launch_ms": t_spmm / max(launches, 1)},
         "breakdown_ms": {"spmm": t_spmm / steps,
@@ -317,11 +342,7 @@ def run_ours(args, rank, world, local_rank):
     e1.record(stream)
     barrier()
     clocks = sampler.stop()
-    ms = e0.elapsed_time(e1) / args.steps
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world, dev)
     assert all(i["status"] == "OK" for i in infos)
 
     # per-iteration and roofline figures from the library's event timing
@@ -336,11 +357,20 @@ def run_ours(args, rank, world, local_rank):
     timed_s = ms * args.steps / 1e3
     peak = sustained if timed_s >= 1.0 else burst
     achieved = (l1 * gemm_flops + 3 * l3 * gemm_flops) / ((t1 + t3) / 1e3) / 1e12
-    traffic = profiled_traffic()
+    tr = profiled_traffic("k_gemm_tc_dense_n8192.md", "k_tc_gemm.cu",
+                          ["traffic_bytes_per_launch_1pass", "traffic_bytes_per_launch_3pass"])
+    # per launch of the timed mix of 1-pass and 3-pass launches, like `achieved`
+    traffic = None if tr is None else (
+        (l1 * tr["traffic_bytes_per_launch_1pass"] + l3 * tr["traffic_bytes_per_launch_3pass"])
+        / max(l1 + l3, 1))
     roofline = {
         "kernel": "k_gemm_tc (tcgen05 FP16 product + fused IPT map epilogue)",
         "bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
         "frac": achieved / peak if peak else None, "traffic": traffic,
+        "traffic_per_launch": None if tr is None else {
+            "1pass": tr["traffic_bytes_per_launch_1pass"],
+            "3pass": tr["traffic_bytes_per_launch_3pass"]},
+        "algorithmic_bytes_per_launch": {"1pass": 16 * n * n, "3pass": 24 * n * n},
         "peak_source": f"{peak_src} {'sustained' if peak == sustained else 'burst'} bf16 "
                        f"(FP16 dense rate equals BF16)",
         "flops_per_launch": {"1pass": gemm_flops, "3pass": 3 * gemm_flops},

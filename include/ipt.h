@@ -188,7 +188,9 @@ ipt_status ipt_step_dense(ipt_handle* h, int64_t n, const void* M, int64_t ldm, 
  * Sparse solve with M in CSR form (Section 6.1 workloads: a few extremal
  * eigenpairs of a large sparse near-diagonal matrix).
  *   rowptr device, n+1 int32; colind device, nnz int32 (0-based, any order
- *   within a row, no duplicates); vals device, nnz of v_dtype.  The CSR
+ *   within a row, no duplicates); vals device, nnz of v_dtype.  rowptr must
+ *   start at 0, ascend and end at nnz, and colind lie in [0, n): a violation
+ *   is found on the device before any product and returns IPT_INVALID_ARG.  The CSR
  *   holds all stored entries of M, diagonal ones included; Delta = M - diag(theta).
  *   theta  device, n doubles; NULL = diag(M) (0 where a row stores no diagonal)
  * Every other argument as in ipt_solve_dense.  Product arithmetic: FP32

@@ -134,7 +134,8 @@ ipt_status alloc_dense(ipt_handle* h, const Plan& p) {
 DevState* dst(ipt_handle* h) { return static_cast<DevState*>(h->st.p); }
 
 ipt_status status_from_flags(int flags) {
-  if (flags & (FLAG_COL_RANGE | FLAG_COL_DUP | FLAG_ZERO_PIVOT)) return IPT_INVALID_ARG;
+  if (flags & (FLAG_COL_RANGE | FLAG_COL_DUP | FLAG_ZERO_PIVOT | FLAG_CSR_INDEX))
+    return IPT_INVALID_ARG;
   if (flags & (FLAG_THETA_NONFINITE | FLAG_THETA_DEGENERATE)) return IPT_DEGENERATE_THETA;
   return IPT_OK;
 }
@@ -721,7 +722,7 @@ ipt_status ipt_solve_csr(ipt_handle* h, int64_t n, int64_t nnz, const int32_t* r
   const bool f64 = prec == IPT_PREC_F64;
   const int ni = (int)n, ki = (int)k, kk = (int)round_up(k, 64);
   const size_t ez = f64 ? 8 : 4, nk = (size_t)n * kk;
-  int nsm = 0, dev = 0;
+  int nsm = 0, dev = 0;  // persistent SpMM grid: 8 CTAs of 256 threads per SM
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   const int nblk = (nsm > 0 ? nsm : 148) * 8;
@@ -735,7 +736,7 @@ ipt_status ipt_solve_csr(ipt_handle* h, int64_t n, int64_t nnz, const int32_t* r
   CK(ensure(h->count, (size_t)n * 4));
   CK(ensure(h->d, (size_t)kk * 8));
   CK(ensure(h->st, sizeof(DevState)));
-  CK(ensure(h->cpart, (size_t)nblk * 8));
+  CK(ensure(h->cpart, (size_t)((n + 255) / 256) * 8));
   cudaStream_t s = h->s;
   DevState* st = dst(h);
   if (tm.on) cudaEventRecord(h->ev[4], s);
@@ -750,12 +751,10 @@ ipt_status ipt_solve_csr(ipt_handle* h, int64_t n, int64_t nnz, const int32_t* r
     CK(cudaMemcpyAsync(st, &init, kStateHead, cudaMemcpyHostToDevice, s));
   }
   CK(cudaMemsetAsync(h->count.p, 0, (size_t)n * 4, s));
-  launch_csr_theta(rowptr, colind, vals, v_dtype, theta, ni, (double*)h->theta.p,
-                   (float*)h->thh.p, (float*)h->thl.p, (double*)h->delta.p, st, s);
-  launch_validate(cols, ni, ki, kk, (const double*)h->theta.p, (int32_t*)h->icol.p,
-                  (int*)h->count.p, st, s);
-  launch_csr_r0(rowptr, colind, vals, v_dtype, ni, (const int*)h->count.p,
-                (double*)h->cpart.p, nblk, st, s);
+  launch_validate(cols, ni, ki, kk, nullptr, (int32_t*)h->icol.p, (int*)h->count.p, st, s);
+  launch_csr_rows(rowptr, colind, vals, v_dtype, theta, ni, nnz, (const int*)h->count.p,
+                  (double*)h->theta.p, (float*)h->thh.p, (float*)h->thl.p, (double*)h->delta.p,
+                  (double*)h->cpart.p, st, s);
   launch_csr_init_z((const int32_t*)h->icol.p, ni, kk, h->z[0].p, f64 ? 1 : 0, s);
   h->launches += 6;
   CK(cudaGetLastError());

@@ -32,6 +32,7 @@ enum : int {
   FLAG_THETA_NONFINITE = 4,
   FLAG_THETA_DEGENERATE = 8,
   FLAG_ZERO_PIVOT = 16,
+  FLAG_CSR_INDEX = 32,  // CSR row bounds or a column index out of range
 };
 
 // Device-resident solver state: norm accumulators of the running evaluation,
@@ -140,12 +141,10 @@ cudaError_t launch_gemm_tc(const uint16_t* Dh, const uint16_t* Dl, const uint16_
                            int passes, int bf16, cudaStream_t s);
 
 // sparse path (k_csr.cu): Z row-major n x kk, kk = k rounded up to 64
-void launch_csr_theta(const int32_t* rowptr, const int32_t* colind, const void* vals, int v_dtype,
-                      const double* theta_in, int n, double* theta, float* th_hi, float* th_lo,
-                      double* delta, DevState* st, cudaStream_t s);
-void launch_csr_r0(const int32_t* rowptr, const int32_t* colind, const void* vals, int v_dtype,
-                   int n, const int* count, double* part, int nblk, DevState* st,
-                   cudaStream_t s);
+void launch_csr_rows(const int32_t* rowptr, const int32_t* colind, const void* vals, int v_dtype,
+                     const double* theta_in, int n, int64_t nnz, const int* count, double* theta,
+                     float* th_hi, float* th_lo, double* delta, double* part, DevState* st,
+                     cudaStream_t s);
 void launch_csr_init_z(const int32_t* icol, int n, int kk, void* Z, int f64, cudaStream_t s);
 void launch_csr_prepass(const int32_t* rowptr, const int32_t* colind, const void* vals,
                         int v_dtype, const double* delta, const int32_t* icol, int kk,

@@ -28,22 +28,40 @@ __device__ __forceinline__ T ldval(const void* v, int64_t i, int dt) {
                              : (T) static_cast<const float*>(v)[i];
 }
 
-// theta_j (given or the stored M_jj, 0 if the row stores none), its FP32
-// split, delta_j = M_jj - theta_j; non-finite theta is flagged.  One warp per row.
-__global__ void k_csr_theta(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colind,
-                            const void* __restrict__ vals, int v_dtype,
-                            const double* __restrict__ theta_in, int n, double* __restrict__ theta,
-                            float* __restrict__ th_hi, float* __restrict__ th_lo,
-                            double* __restrict__ delta, DevState* st) {
-  const int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-  if (j >= n) return;
-  // the stored diagonal entry, found with integer compares (entries are unique)
-  int ediag = -1;
-  for (int e = rowptr[j] + lane; e < rowptr[j + 1]; e += 32)
-    if (colind[e] == j) ediag = e;
-  for (int o = 16; o > 0; o >>= 1) ediag = max(ediag, __shfl_xor_sync(0xffffffffu, ediag, o));
-  if (lane == 0) {
-    const double mjj = ediag >= 0 ? ldval<double>(vals, ediag, v_dtype) : 0.0;
+// One pass over the rows (one thread per row): the CSR structure check (row
+// bounds within [0, nnz] and ascending, column indices in [0, n); a bad row is
+// flagged and skipped, and the later CSR kernels then do nothing), the stored
+// diagonal M_jj (0 if the row stores none), theta_j (given, or M_jj), its FP32 split and
+// delta_j = M_jj - theta_j; non-finite theta is flagged; and the per-block
+// partial of ||M Z0 - Z0 Lambda0||^2, the squared off-diagonal entries in
+// requested columns (count[col] > 0).
+__global__ void __launch_bounds__(256)
+    k_csr_rows(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colind,
+               const void* __restrict__ vals, int v_dtype, const double* __restrict__ theta_in,
+               int n, int64_t nnz, const int* __restrict__ count, double* __restrict__ theta,
+               float* __restrict__ th_hi, float* __restrict__ th_lo, double* __restrict__ delta,
+               double* __restrict__ part, DevState* st) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  float r0 = 0.f;
+  if (j < n) {
+    double mjj = 0.0;
+    const int e0 = rowptr[j], e1 = rowptr[j + 1];
+    const bool rows_ok = e0 >= 0 && e0 <= e1 && (int64_t)e1 <= nnz && (j > 0 || e0 == 0) &&
+                         (j + 1 < n || (int64_t)e1 == nnz);
+    if (!rows_ok) atomicOr(&st->flags, FLAG_CSR_INDEX);
+    for (int e = e0; rows_ok && e < e1; ++e) {
+      const int m = colind[e];
+      if (m < 0 || m >= n) {
+        atomicOr(&st->flags, FLAG_CSR_INDEX);
+        break;
+      }
+      if (m == j) {
+        mjj = ldval<double>(vals, e, v_dtype);
+      } else if (count[m] > 0) {
+        const float v = ldval<float>(vals, e, v_dtype);
+        r0 = fmaf(v, v, r0);
+      }
+    }
     const double t = theta_in ? theta_in[j] : mjj;
     if (!isfinite(t)) atomicOr(&st->flags, FLAG_THETA_NONFINITE);
     theta[j] = t;
@@ -52,37 +70,20 @@ __global__ void k_csr_theta(const int32_t* __restrict__ rowptr, const int32_t* _
     th_lo[j] = (float)(t - (double)h);
     delta[j] = mjj - t;
   }
-}
-
-// ||M Z0 - Z0 Lambda0||^2: squared off-diagonal entries of the requested
-// columns of M (count[col] > 0), one per-block partial.  Grid-stride over nnz.
-__global__ void k_csr_r0(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colind,
-                         const void* __restrict__ vals, int v_dtype, int n,
-                         const int* __restrict__ count, double* __restrict__ part) {
-  double s = 0.0;
-  for (int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); j < n;
-       j += gridDim.x * (blockDim.x >> 5)) {
-    for (int e = rowptr[j] + (threadIdx.x & 31); e < rowptr[j + 1]; e += 32) {
-      const int m = colind[e];
-      if (m != j && count[m] > 0) {
-        const double v = ldval<double>(vals, e, v_dtype);
-        s += v * v;
-      }
-    }
-  }
-  s = warp_sum(s);
-  __shared__ double red[32];
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __shared__ float red[8];
+  const float w = warp_sum(r0);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = w;
   __syncthreads();
   if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
-    part[blockIdx.x] = t;
+    double tot = 0.0;
+    for (int q = 0; q < 8; ++q) tot += (double)red[q];
+    part[blockIdx.x] = tot;
   }
 }
 
-__global__ void k_csr_sum_r0(const double* __restrict__ part, int count, DevState* st) {
-  __shared__ double red[256];
+__global__ void __launch_bounds__(1024)
+    k_csr_sum_r0(const double* __restrict__ part, int count, DevState* st) {
+  __shared__ double red[1024];
   double t = 0.0;
   for (int i = threadIdx.x; i < count; i += blockDim.x) t += part[i];
   red[threadIdx.x] = t;
@@ -112,7 +113,7 @@ __global__ void k_csr_prepass(const int32_t* __restrict__ rowptr, const int32_t*
                               const double* __restrict__ delta, const int32_t* __restrict__ icol,
                               int kk, const T* __restrict__ Z, double* __restrict__ d,
                               const DevState* st) {
-  if (st->done) return;
+  if (st->done || (st->flags & FLAG_CSR_INDEX)) return;
   const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (c >= kk) return;
   const int i = icol[c];
@@ -166,7 +167,7 @@ __global__ void __launch_bounds__(256, 4)
                    const float* __restrict__ th_lo, const int32_t* __restrict__ icol,
                    const double* __restrict__ d, int n, int k, int kk, const T* __restrict__ Zin,
                    T* __restrict__ Fout, DevState* st) {
-  if (st->done) return;
+  if (st->done || (st->flags & FLAG_CSR_INDEX)) return;
   using V4 = typename Four<T>::V;
   const int lane = threadIdx.x & 31, hl = lane & 15;
   const unsigned hmask = (lane < 16) ? 0x0000ffffu : 0xffff0000u;
@@ -275,19 +276,14 @@ inline unsigned nblocks(int64_t total, int bs) { return (unsigned)((total + bs -
 }  // namespace
 
 // ---------------------------------------------------------------- launchers
-void launch_csr_theta(const int32_t* rowptr, const int32_t* colind, const void* vals, int v_dtype,
-                      const double* theta_in, int n, double* theta, float* th_hi, float* th_lo,
-                      double* delta, DevState* st, cudaStream_t s) {
-  k_csr_theta<<<nblocks((int64_t)n * 32, 256), 256, 0, s>>>(rowptr, colind, vals, v_dtype,
-                                                            theta_in, n, theta, th_hi, th_lo,
-                                                            delta, st);
-}
-
-void launch_csr_r0(const int32_t* rowptr, const int32_t* colind, const void* vals, int v_dtype,
-                   int n, const int* count, double* part, int nblk, DevState* st,
-                   cudaStream_t s) {
-  k_csr_r0<<<nblk, 256, 0, s>>>(rowptr, colind, vals, v_dtype, n, count, part);
-  k_csr_sum_r0<<<1, 256, 0, s>>>(part, nblk, st);
+void launch_csr_rows(const int32_t* rowptr, const int32_t* colind, const void* vals, int v_dtype,
+                     const double* theta_in, int n, int64_t nnz, const int* count, double* theta,
+                     float* th_hi, float* th_lo, double* delta, double* part, DevState* st,
+                     cudaStream_t s) {
+  const unsigned g = nblocks(n, 256);
+  k_csr_rows<<<g, 256, 0, s>>>(rowptr, colind, vals, v_dtype, theta_in, n, nnz, count, theta, th_hi,
+                               th_lo, delta, part, st);
+  k_csr_sum_r0<<<1, 1024, 0, s>>>(part, (int)g, st);
 }
 
 void launch_csr_init_z(const int32_t* icol, int n, int kk, void* Z, int f64, cudaStream_t s) {

@@ -428,6 +428,7 @@ __global__ void __launch_bounds__(256)
   const int64_t ld = a.ld;
   const int j0 = (blockIdx.y * blockDim.x + threadIdx.x) * 4;
   float s_inc = 0.f, s_z = 0.f, s_r = 0.f;
+  if (ic < 0 && blockIdx.y == 0 && threadIdx.x == 0) d[c] = 0.0;
   if (ic >= 0 && j0 < a.n) {
     const float* pc = a.DT + (int64_t)ic * ld;
     const float4 p4 = *reinterpret_cast<const float4*>(pc + j0);
@@ -453,8 +454,6 @@ __global__ void __launch_bounds__(256)
     }
     *reinterpret_cast<float4*>(a.Fout + (int64_t)c * ld + j0) = make_float4(f[0], f[1], f[2], f[3]);
     if (ic >= j0 && ic < j0 + 4) d[c] = (double)dc;
-  } else if (ic < 0 && blockIdx.y == 0 && threadIdx.x == 0) {
-    d[c] = 0.0;
   }
   // block partials of the three norms (summed by k_sum_norms)
   __shared__ float red[3][8];
@@ -474,8 +473,9 @@ __global__ void __launch_bounds__(256)
 }
 
 // One block: the evaluation's norm accumulators from per-block partials.
-__global__ void k_sum_norms(const double* __restrict__ part, int64_t count, DevState* st) {
-  __shared__ double red[3][256];
+__global__ void __launch_bounds__(1024)
+    k_sum_norms(const double* __restrict__ part, int64_t count, DevState* st) {
+  __shared__ double red[3][1024];
   double t0 = 0.0, t1 = 0.0, t2 = 0.0;
   for (int64_t i = threadIdx.x; i < count; i += blockDim.x) {
     t0 += part[3 * i];
@@ -661,7 +661,7 @@ void launch_map_first(const MapArgs<float>& a, int npad, int kpad, double* d, do
                       cudaStream_t s) {
   dim3 g(kpad, (npad / 4 + 255) / 256);
   k_map_first<<<g, 256, 0, s>>>(a, d, part);
-  k_sum_norms<<<1, 256, 0, s>>>(part, (int64_t)g.x * g.y, a.st);
+  k_sum_norms<<<1, 1024, 0, s>>>(part, (int64_t)g.x * g.y, a.st);
 }
 
 }  // namespace ipt

@@ -1,0 +1,78 @@
+"""Run repeated solves of one named workload (for profilers and quick checks).
+
+    python -m paper_2012_14702_gb300.run_case dense_n8192_eps1e-3 --solves 3
+    python -m paper_2012_14702_gb300.run_case csr_n2p20_k64 --solves 2
+
+Each solve goes through the C ABI exactly as a user's call would (inputs
+resident on the device); the line printed per solve gives its status,
+evaluations, residual and wall time.  Under a kernel profiler, ``--solves``
+and the kernel-name filter select which launches are captured.
+"""
+
+from __future__ import annotations
+
+import argparse
+import time
+
+from paper_2012_14702_gb300 import workloads
+
+
+def run_dense(name, solves, precision, tol):
+    import torch
+    from paper_2012_14702_gb300 import ipt
+    n, step, scale, seed = workloads.DENSE_CONFIGS[name]
+    M, th = workloads.dense_symmetric(n, scale, seed, theta_step=step)
+    Mg = torch.as_tensor(M, dtype=torch.float32, device="cuda")
+    thg = torch.as_tensor(th, dtype=torch.float64, device="cuda")
+    del M
+    s = ipt.Solver()
+    for i in range(solves):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, _, info = s.solve_dense(Mg, theta=thg, tol=tol, max_iter=40, precision=precision)
+        torch.cuda.synchronize()
+        print(f"{name} solve {i}: {info['status']} iterations {info['iterations']} "
+              f"rho {info['rho']:.3e} {1e3 * (time.perf_counter() - t0):.2f} ms", flush=True)
+        if info["status"] != "OK":
+            raise SystemExit(1)
+
+
+def run_csr(name, solves, precision, tol):
+    import torch
+    from paper_2012_14702_gb300 import ipt
+    n, per_row, band, scale, seed, k = workloads.CSR_CONFIGS[name]
+    rowptr, colind, vals, th = workloads.csr_banded(n, per_row, band, scale, seed=seed)
+    cols = workloads.lowest_columns(th, k)
+    rp = torch.as_tensor(rowptr, device="cuda")
+    ci = torch.as_tensor(colind, device="cuda")
+    vv = torch.as_tensor(vals, dtype=torch.float32, device="cuda")
+    cg = torch.as_tensor(cols, device="cuda")
+    s = ipt.Solver()
+    for i in range(solves):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, _, info = s.solve_csr(rp, ci, vv, n, cols=cg, tol=tol, max_iter=50,
+                                 precision="f32" if precision == "staged" else precision)
+        torch.cuda.synchronize()
+        print(f"{name} solve {i}: {info['status']} iterations {info['iterations']} "
+              f"rho {info['rho']:.3e} {1e3 * (time.perf_counter() - t0):.2f} ms", flush=True)
+        if info["status"] != "OK":
+            raise SystemExit(1)
+
+
+def main(argv=None):
+    names = sorted(workloads.DENSE_CONFIGS) + sorted(workloads.CSR_CONFIGS)
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("workload", choices=names)
+    ap.add_argument("--solves", type=int, default=2)
+    ap.add_argument("--precision", default="staged")
+    ap.add_argument("--tol", type=float, default=1e-6)
+    a = ap.parse_args(argv)
+    if a.workload in workloads.DENSE_CONFIGS:
+        run_dense(a.workload, a.solves, a.precision, a.tol)
+    else:
+        run_csr(a.workload, a.solves, a.precision, a.tol)
+
+
+if __name__ == "__main__":
+    main()

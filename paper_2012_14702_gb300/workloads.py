@@ -36,6 +36,7 @@ __all__ = [
     "three_by_three",
     "lowest_columns",
     "DENSE_CONFIGS",
+    "CSR_CONFIGS",
 ]
 
 
@@ -162,4 +163,10 @@ DENSE_CONFIGS = {
     "dense_n8192_eps1e-4": (8192, 0.125, 1e-4, 21),
     "dense_n8192_eps1e-3": (8192, 0.125, 1e-3, 22),
     "dense_n8192_eps3e-3": (8192, 0.125, 3e-3, 23),
+}
+
+# The sparse workloads by name: (n, per_row, band, scale, seed, k lowest).
+CSR_CONFIGS = {
+    "csr_n2p20_k64": (1 << 20, 8, 2048, 1e-3, 3, 64),
+    "csr_n2p16_k64": (1 << 16, 8, 2048, 1e-3, 3, 64),
 }

@@ -110,6 +110,17 @@ def test_csr_statuses(ipt):
     _, _, info = s.solve_csr(rp, ci, vv, n, cols=cuda([3], torch.int32), precision="staged",
                              tol=1e-6)
     assert info["status"] == "OK" and info["hist_stage"][0] == "f32"
+    # CSR structure errors are found on the device before any product reads Z
+    bad = colind.copy()
+    bad[len(bad) // 2] = n
+    _, _, info = s.solve_csr(rp, cuda(bad, torch.int32), vv, n, cols=cuda([3], torch.int32))
+    assert info["status"] == "INVALID_ARG"
+    badp = rowptr.copy()
+    badp[-1] -= 1
+    _, _, info = s.solve_csr(cuda(badp, torch.int32), ci, vv, n, cols=cuda([3], torch.int32))
+    assert info["status"] == "INVALID_ARG"
+    _, _, info = s.solve_csr(rp, ci, vv, n, cols=cuda([3], torch.int32), tol=1e-6)
+    assert info["status"] == "OK"
 
 
 def test_csr_full_size_sampled_columns_match_oracle(ipt):
