@@ -95,7 +95,15 @@ typedef struct {
                            on the handle's stream (result.*_ms)                            */
   const void* z0;       /* optional warm start (device, Z layout, dtype = z_dtype);
                            column c is rescaled so that z0[cols[c], c] = 1                 */
+  int product_kernel;   /* dense tensor-core product kernel: IPT_PRODUCT_AUTO (default),
+                           IPT_PRODUCT_SINGLE (one CTA per 128 x 256 tile) or
+                           IPT_PRODUCT_PAIR (two CTAs per 256 x 256 tile, one paired MMA;
+                           needs an even number of 128-row blocks, else SINGLE is used).
+                           Results are identical; only speed differs                     */
 } ipt_options;
+
+/* Values of ipt_options.product_kernel. */
+enum { IPT_PRODUCT_AUTO = 0, IPT_PRODUCT_SINGLE = 1, IPT_PRODUCT_PAIR = 2 };
 
 #define IPT_MAX_HISTORY 128
 

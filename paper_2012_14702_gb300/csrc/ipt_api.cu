@@ -87,6 +87,7 @@ struct Plan {
   bool bf16;    // tensor-core operands are BF16 (else FP16)
   bool dt;      // column-major FP32 Delta (W-form epilogues)
   bool staged;  // third Z buffer and stored-P buffer (base re-use)
+  int product_kernel = IPT_PRODUCT_AUTO;  // tensor-core product kernel variant
 };
 
 ipt_status check_dense_args(ipt_handle* h, int64_t n, const void* M, int64_t ldm, int m_dtype,
@@ -315,7 +316,7 @@ ipt_status evaluate(ipt_handle* h, const Plan& p, int cur, int base, int stage, 
       if (t) CK(cudaEventRecord(h->ev[2], s));
       CK(launch_gemm_tc((const uint16_t*)h->dh.p, (const uint16_t*)h->dl.p,
                         (const uint16_t*)h->wh.p, (const uint16_t*)h->wl.p, a, p.npad, p.kpad,
-                        passes, p.bf16 ? 1 : 0, s));
+                        passes, p.bf16 ? 1 : 0, p.product_kernel, s));
     }
   }
   CK(cudaGetLastError());
@@ -409,7 +410,9 @@ ipt_status solve_dense(ipt_handle* h, int64_t n, const void* M, int64_t ldm, int
   if (opt_in) opt = *opt_in;
   ipt_status v = check_dense_args(h, n, M, ldm, m_dtype, k, opt.precision, ldz, z_dtype);
   if (v == IPT_OK && (!lambda || !Z || !(tol >= 0.0) || max_iter < 1 ||
-                      (opt.stop != IPT_STOP_INCREMENT && opt.stop != IPT_STOP_RESIDUAL)))
+                      (opt.stop != IPT_STOP_INCREMENT && opt.stop != IPT_STOP_RESIDUAL) ||
+                      opt.product_kernel < IPT_PRODUCT_AUTO ||
+                      opt.product_kernel > IPT_PRODUCT_PAIR))
     v = IPT_INVALID_ARG;
   if (v != IPT_OK) {
     out->status = v;
@@ -424,7 +427,8 @@ ipt_status solve_dense(ipt_handle* h, int64_t n, const void* M, int64_t ldm, int
     out->status = IPT_CUDA_ERROR;
     return IPT_CUDA_ERROR;
   }
-  const Plan p = make_plan(n, k, opt.precision, opt.staged_bf16 != 0);
+  Plan p = make_plan(n, k, opt.precision, opt.staged_bf16 != 0);
+  p.product_kernel = opt.product_kernel;
   const int low = p.bf16 ? IPT_PREC_BF16 : IPT_PREC_FP16;
   const int high = p.bf16 ? IPT_PREC_BF16X3 : IPT_PREC_FP16X3;
   // First evaluation: product-free at Z = E (FP32 / tensor-core paths), else
@@ -545,6 +549,7 @@ void ipt_options_default(ipt_options* opt) {
   opt->verify_fp64 = 0;
   opt->record_timing = 0;
   opt->z0 = nullptr;
+  opt->product_kernel = IPT_PRODUCT_AUTO;
 }
 
 const char* ipt_status_string(int status) {

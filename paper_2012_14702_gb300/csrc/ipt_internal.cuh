@@ -136,9 +136,11 @@ void launch_control(DevState* st, ControlArgs a, cudaStream_t s);
 // tensor-core product (k_tc_gemm.cu).  passes = 1 (Dh Wh) or 3 (+ Dh Wl + Dl Wh);
 // bf16 selects BF16 operands, else FP16.  Returns a cudaError_t of the launch
 // or of tensor-map encoding.
+// mode: IPT_PRODUCT_SINGLE or IPT_PRODUCT_PAIR (AUTO = PAIR); PAIR falls back
+// to SINGLE when npad / 128 is odd.
 cudaError_t launch_gemm_tc(const uint16_t* Dh, const uint16_t* Dl, const uint16_t* Wh,
                            const uint16_t* Wl, const MapArgs<float>& a, int npad, int kpad,
-                           int passes, int bf16, cudaStream_t s);
+                           int passes, int bf16, int mode, cudaStream_t s);
 
 // sparse path (k_csr.cu): Z row-major n x kk, kk = k rounded up to 64
 void launch_csr_rows(const int32_t* rowptr, const int32_t* colind, const void* vals, int v_dtype,

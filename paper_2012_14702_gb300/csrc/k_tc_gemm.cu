@@ -36,11 +36,24 @@ namespace ipt {
 
 namespace {
 
-constexpr int BM = 128, BN = 256, BK = 64, STAGES = 4;
+constexpr int BM = 128, BN = 256, BK = 64;
 constexpr int A_BYTES = BM * BK * 2;
-constexpr int B_BYTES = BN * BK * 2;
-constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
 constexpr int TMEM_COLS = 2 * BN;
+
+// Kernel modes.  SINGLE: one CTA per 128 x 256 tile.  MULTICAST: 2-CTA
+// clusters computing two vertically adjacent single tiles whose shared B tile
+// is loaded half by each CTA and multicast.  PAIR: 2-CTA clusters issuing one
+// paired MMA (cta_group::2, M = 256) per K step; each CTA holds its own 128 A
+// rows and one 128-row half of B, so a CTA's shared memory takes 32 KB per
+// K step instead of 48 KB for the same 128 x 256 x 64 of its own output.
+enum { MODE_SINGLE = 0, MODE_MULTICAST = 1, MODE_PAIR = 2 };
+template <int MODE>
+struct Shape {
+  static constexpr int B_BYTES = (MODE == MODE_PAIR ? BN / 2 : BN) * BK * 2;  // per CTA
+  static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;                       // per CTA
+  static constexpr int STAGES = MODE == MODE_PAIR ? 6 : 4;
+};
+constexpr int MAX_STAGES = 6;
 constexpr int EPI_WARPS = 8;  // two per TMEM lane quarter, each owning half of the columns
 constexpr int NUM_THREADS = 64 + 32 * EPI_WARPS;
 constexpr int EPI_THREADS = 32 * EPI_WARPS;
@@ -72,22 +85,28 @@ struct __align__(16) ColInfo {
 struct Ctl {
   ColInfo wcol[EPI_WARPS][EPI_COLS];
   int wic[EPI_WARPS][EPI_COLS];
-  uint64_t full[STAGES];
-  uint64_t empty[STAGES];
+  uint64_t full[MAX_STAGES];
+  uint64_t empty[MAX_STAGES];
   uint64_t tfull[2];
   uint64_t tempty[2];
   uint64_t drain;
   uint32_t tmem_base;
   int abort;
 };
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + (int)sizeof(Ctl) + 64;
+template <int MODE>
+constexpr int smem_bytes() {
+  return Shape<MODE>::STAGES * Shape<MODE>::STAGE_BYTES + 1024 + (int)sizeof(Ctl) + 64;
+}
+static_assert(smem_bytes<MODE_PAIR>() <= 227 * 1024, "shared memory");
+static_assert(smem_bytes<MODE_SINGLE>() <= 227 * 1024, "shared memory");
 
 // Instruction descriptor, kind::f16: D = F32 (bits 4-5 = 1), A and B both
 // FP16 (0) or both BF16 (1) at bits 7-9 / 10-12, both K-major (bits 15, 16 =
-// 0), N >> 3 at bit 17, M >> 4 at bit 24.
-constexpr uint32_t idesc_for(bool bf16) {
+// 0), N >> 3 at bit 17, M >> 4 at bit 24 (M of the whole instruction: 256
+// for a CTA pair).
+constexpr uint32_t idesc_for(bool bf16, int m) {
   return (1u << 4) | ((bf16 ? 1u : 0u) << 7) | ((bf16 ? 1u : 0u) << 10) |
-         ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+         ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
 }
 
 __device__ __forceinline__ uint32_t su32(const void* p) {
@@ -120,18 +139,45 @@ __device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
+// The same test with cluster-scope acquire: for barriers that threads of the
+// peer CTA arrive on.
+__device__ __forceinline__ bool mbar_try_cluster(uint64_t* b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(su32(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
 // Wait for the phase `parity` of barrier b.  False on timeout or when another
 // role has aborted (then the caller stops issuing and falls through to drain).
+template <bool CLUSTER = false>
 __device__ __noinline__ bool wait_bounded(uint64_t* b, uint32_t parity, volatile int* abort) {
-  if (mbar_try(b, parity)) return true;
+  auto test = [&]() { return CLUSTER ? mbar_try_cluster(b, parity) : mbar_try(b, parity); };
+  if (test()) return true;
   const uint64_t t0 = gtimer();
   for (;;) {
 #pragma unroll 1
     for (int i = 0; i < 32; ++i)
-      if (mbar_try(b, parity)) return true;
+      if (test()) return true;
     if (*abort) return false;
     if (gtimer() - t0 > kTimeoutNs) return false;
   }
+}
+// Shared::cluster address of the object at the same offset as `p` in the CTA
+// of cluster rank `rank`.
+__device__ __forceinline__ uint32_t peer_addr(const void* p, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(su32(p)), "r"(rank));
+  return r;
+}
+// Arrive (release, cluster scope) on a barrier given by its shared::cluster address.
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t cluster_addr) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr)
+               : "memory");
 }
 
 __device__ __forceinline__ void tma_load(void* dst, const CUtensorMap* map, uint64_t* bar, int x,
@@ -152,6 +198,17 @@ __device__ __forceinline__ void tma_load_mc(void* dst, const CUtensorMap* map, u
       "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
       ".multicast::cluster [%0], [%1, {%3, %4}], [%2], %5;" ::"r"(su32(dst)),
       "l"(reinterpret_cast<uint64_t>(map)), "r"(su32(bar)), "r"(x), "r"(y), "h"(mask)
+      : "memory");
+}
+
+// Load whose completion is counted on an mbarrier of either CTA of the pair
+// (`bar` is a shared::cluster address, here always the pair's first CTA).
+__device__ __forceinline__ void tma_load_pair(void* dst, const CUtensorMap* map, uint32_t bar,
+                                              int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4}], [%2];" ::"r"(su32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(x), "r"(y)
       : "memory");
 }
 
@@ -199,6 +256,32 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
           su32(bar))
       : "memory");
 }
+// Paired MMA (issued by the pair's first CTA): D of each CTA (128 lanes x 256
+// columns) += its A rows x both CTAs' B halves.
+__device__ __forceinline__ void mma_f16_pair(uint32_t dt, uint64_t ad, uint64_t bd,
+                                             uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dt),
+      "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+      : "memory");
+}
+// Completion of the pair's MMAs arrives on the barrier at the same offset in
+// each CTA of `mask`.
+__device__ __forceinline__ void mma_commit_pair_mc(uint64_t* bar, uint16_t mask) {
+  asm volatile(
+      "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
+      " [%0], %1;" ::"r"(su32(bar)),
+      "h"(mask)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit_pair(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          su32(bar))
+      : "memory");
+}
 // Completion of this CTA's MMAs arrives on the barrier at the same offset in
 // every CTA of `mask` (releases a shared operand stage in both CTAs).
 __device__ __forceinline__ void mma_commit_mc(uint64_t* bar, uint16_t mask) {
@@ -226,27 +309,6 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// 32 consecutive accumulator columns of this thread's TMEM lane; the load
-// and its completion wait are one asm statement so no use can precede the wait.
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
-  uint32_t r[32];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n\t"
-      "tcgen05.wait::ld.sync.aligned;"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
-        "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
-        "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
-        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
-        "=r"(r[31])
-      : "r"(taddr)
-      : "memory");
-#pragma unroll
-  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
-}
-
 __device__ __forceinline__ void tile_coords(int t, int num_m, int num_n, int& mb, int& nb) {
   const int per_group = GROUP_M * num_n;
   const int g = t / per_group;
@@ -262,17 +324,29 @@ __device__ __forceinline__ void fail(Ctl* ctl, DevState* st, int code) {
   atomicCAS(&st->timeout, 0, code);
 }
 
-// MC (cluster of 2 along M): the two CTAs of a cluster compute the vertically
-// adjacent tiles (2p, nb) and (2p+1, nb), which share the B tile; each CTA
-// loads one 128-row half of it and multicasts the half to both.  A stage is
-// released only when both CTAs' MMAs are done with it (two arrivals on the
-// empty barrier, one multicast commit from each CTA).  tmWh / tmWl then have
-// a 128-row box.
-template <bool MC>
+// MULTICAST (cluster of 2 along M): the two CTAs of a cluster compute the
+// vertically adjacent tiles (2p, nb) and (2p+1, nb), which share the B tile;
+// each CTA loads one 128-row half of it and multicasts the half to both.  A
+// stage is released only when both CTAs' MMAs are done with it (two arrivals
+// on the empty barrier, one multicast commit from each CTA).
+//
+// PAIR (cluster of 2 along M): the same two tiles as one 256 x 256 paired
+// product.  Each CTA's producer loads its 128 A rows and its half of B into
+// its own shared memory, counting the bytes on the first CTA's full barrier
+// (armed by the first CTA for both CTAs' bytes).  Only the first CTA's MMA
+// thread issues, and its commits arrive on both CTAs' barriers (stage free,
+// accumulator full).  Both CTAs' epilogues read their own TMEM and release
+// the accumulator on the first CTA's barrier (16 warp arrivals).
+template <int MODE>
 __global__ void __launch_bounds__(NUM_THREADS, 1)
     k_gemm_tc(const __grid_constant__ CUtensorMap tmDh, const __grid_constant__ CUtensorMap tmDl,
               const __grid_constant__ CUtensorMap tmWh, const __grid_constant__ CUtensorMap tmWl,
               MapArgs<float> a, int num_m, int num_n, int num_kb, int passes, uint32_t idesc) {
+  constexpr bool CLUSTER = MODE != MODE_SINGLE;
+  constexpr bool PAIR = MODE == MODE_PAIR;
+  constexpr int STAGES = Shape<MODE>::STAGES;
+  constexpr int B_BYTES = Shape<MODE>::B_BYTES;
+  constexpr int STAGE_BYTES = Shape<MODE>::STAGE_BYTES;
   if (a.st->done) return;  // uniform over the grid, so over each cluster
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>(
@@ -283,37 +357,47 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   volatile int* abort = &ctl->abort;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
-  const int rank = MC ? (int)cluster_rank() : 0;
+  const int rank = CLUSTER ? (int)cluster_rank() : 0;
+  const bool leader = rank == 0;
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&ctl->full[s], 1);
-      mbar_init(&ctl->empty[s], MC ? 2 : 1);
+      mbar_init(&ctl->empty[s], MODE == MODE_MULTICAST ? 2 : 1);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&ctl->tfull[b], 1);
-      mbar_init(&ctl->tempty[b], EPI_THREADS);
+      mbar_init(&ctl->tempty[b], PAIR ? 2 * EPI_WARPS : EPI_THREADS);
     }
     mbar_init(&ctl->drain, 1);
     ctl->abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                     su32(&ctl->tmem_base)),
-                 "r"(TMEM_COLS)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    if constexpr (PAIR) {
+      // one warp of each CTA of the pair allocates, collectively
+      asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                       su32(&ctl->tmem_base)),
+                   "r"(TMEM_COLS)
+                   : "memory");
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+    } else {
+      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                       su32(&ctl->tmem_base)),
+                   "r"(TMEM_COLS)
+                   : "memory");
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
   }
   tc_fence_before();
   __syncthreads();
-  if constexpr (MC) cluster_sync();  // the peer's barriers are initialised before any multicast
+  if constexpr (CLUSTER) cluster_sync();  // the peer's barriers are initialised before use
   tc_fence_after();
   const uint32_t tmem = ctl->tmem_base;
   // tiles of the schedule: single tiles, or vertical tile pairs per cluster
-  const int sched_m = MC ? num_m / 2 : num_m;
+  const int sched_m = CLUSTER ? num_m / 2 : num_m;
   const int num_tiles = sched_m * num_n;
-  const int t_first = MC ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;
-  const int t_step = MC ? (int)(gridDim.x >> 1) : (int)gridDim.x;
+  const int t_first = CLUSTER ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;
+  const int t_step = CLUSTER ? (int)(gridDim.x >> 1) : (int)gridDim.x;
   const int total_kb = passes * num_kb;
 
   if (warp == 0) {
@@ -327,7 +411,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       for (int t = t_first; t < num_tiles && ok; t += t_step) {
         int mb, nb;
         tile_coords(t, sched_m, num_n, mb, nb);
-        if (MC) mb = 2 * mb + rank;
+        if (CLUSTER) mb = 2 * mb + rank;
         for (int kb = 0; kb < total_kb; ++kb) {
           if (!wait_bounded(&ctl->empty[stage], phase ^ 1u, abort)) {
             fail(ctl, a.st, 1);
@@ -339,15 +423,22 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
           // passes = 1: Dh Wh.  passes = 3: (Dh Wl, Dl Wh, Dh Wh), or with the
           // main product first (Dh Wh, Dh Wl, Dl Wh).
           const int role = passes == 1 ? 0 : (IPT_CORRECTIONS_FIRST ? (pass + 1) % 3 : pass);
-          mbar_expect_tx(&ctl->full[stage], STAGE_BYTES);
-          tma_load(sA + stage * A_BYTES, role == 2 ? &tmDl : &tmDh, &ctl->full[stage], kx,
-                   mb * BM);
-          if constexpr (MC)
-            tma_load_mc(sB + stage * B_BYTES + rank * (B_BYTES / 2), role == 1 ? &tmWl : &tmWh,
-                        &ctl->full[stage], kx, nb * BN + rank * (BN / 2), (uint16_t)0x3);
-          else
-            tma_load(sB + stage * B_BYTES, role == 1 ? &tmWl : &tmWh, &ctl->full[stage], kx,
-                     nb * BN);
+          const CUtensorMap* mA = role == 2 ? &tmDl : &tmDh;
+          const CUtensorMap* mB = role == 1 ? &tmWl : &tmWh;
+          if constexpr (PAIR) {
+            const uint32_t fb = peer_addr(&ctl->full[stage], 0);
+            if (leader) mbar_expect_tx(&ctl->full[stage], 2 * STAGE_BYTES);
+            tma_load_pair(sA + stage * A_BYTES, mA, fb, kx, mb * BM);
+            tma_load_pair(sB + stage * B_BYTES, mB, fb, kx, nb * BN + rank * (BN / 2));
+          } else {
+            mbar_expect_tx(&ctl->full[stage], STAGE_BYTES);
+            tma_load(sA + stage * A_BYTES, mA, &ctl->full[stage], kx, mb * BM);
+            if constexpr (MODE == MODE_MULTICAST)
+              tma_load_mc(sB + stage * B_BYTES + rank * (B_BYTES / 2), mB, &ctl->full[stage], kx,
+                          nb * BN + rank * (BN / 2), (uint16_t)0x3);
+            else
+              tma_load(sB + stage * B_BYTES, mB, &ctl->full[stage], kx, nb * BN);
+          }
           pend_parity[stage] = (int)phase;
           if (++stage == STAGES) {
             stage = 0;
@@ -355,25 +446,34 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
           }
         }
       }
-      // drain: every issued load lands before the CTA may exit
-      for (int s = 0; s < STAGES; ++s) {
-        if (pend_parity[s] < 0) continue;
+      if (!PAIR || leader) {
+        // drain: every issued load lands before the CTA may exit (in a pair
+        // the first CTA's full barrier also counts the peer's loads)
+        for (int s = 0; s < STAGES; ++s) {
+          if (pend_parity[s] < 0) continue;
+          const uint64_t t0 = gtimer();
+          while (!mbar_try(&ctl->full[s], (uint32_t)pend_parity[s]))
+            if (gtimer() - t0 > kTimeoutNs) {
+              fail(ctl, a.st, 5);
+              break;
+            }
+        }
+      } else if (!ok) {
+        // the second CTA of a pair cannot observe its loads (they count on the
+        // first CTA's barrier): after an abort give any in flight time to land
         const uint64_t t0 = gtimer();
-        while (!mbar_try(&ctl->full[s], (uint32_t)pend_parity[s]))
-          if (gtimer() - t0 > kTimeoutNs) {
-            fail(ctl, a.st, 5);
-            break;
-          }
+        while (gtimer() - t0 < 200000ull) {
+        }
       }
     }
   } else if (warp == 1) {
     // ------------------------------------------------ MMA issuer
-    if (lane == 0) {
+    if (lane == 0 && (!PAIR || leader)) {
       int stage = 0, acc = 0;
       uint32_t phase = 0, acc_phase = 0;
       bool ok = true;
       for (int t = t_first; t < num_tiles && ok; t += t_step) {
-        if (!wait_bounded(&ctl->tempty[acc], acc_phase ^ 1u, abort)) {
+        if (!wait_bounded<PAIR>(&ctl->tempty[acc], acc_phase ^ 1u, abort)) {
           fail(ctl, a.st, 2);
           break;
         }
@@ -388,9 +488,16 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
           tc_fence_after();
           const uint32_t ab = su32(sA + stage * A_BYTES), bb = su32(sB + stage * B_BYTES);
 #pragma unroll
-          for (int k = 0; k < BK / 16; ++k)
-            mma_f16(dt, sw128_desc(ab + k * 32), sw128_desc(bb + k * 32), idesc, (kb | k) != 0);
-          if constexpr (MC) mma_commit_mc(&ctl->empty[stage], (uint16_t)0x3);
+          for (int k = 0; k < BK / 16; ++k) {
+            if constexpr (PAIR)
+              mma_f16_pair(dt, sw128_desc(ab + k * 32), sw128_desc(bb + k * 32), idesc,
+                           (kb | k) != 0);
+            else
+              mma_f16(dt, sw128_desc(ab + k * 32), sw128_desc(bb + k * 32), idesc, (kb | k) != 0);
+          }
+          if constexpr (PAIR) mma_commit_pair_mc(&ctl->empty[stage], (uint16_t)0x3);
+          else if constexpr (MODE == MODE_MULTICAST)
+            mma_commit_mc(&ctl->empty[stage], (uint16_t)0x3);
           else mma_commit(&ctl->empty[stage]);
           if (++stage == STAGES) {
             stage = 0;
@@ -398,14 +505,16 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
           }
         }
         if (!ok) break;
-        mma_commit(&ctl->tfull[acc]);
+        if constexpr (PAIR) mma_commit_pair_mc(&ctl->tfull[acc], (uint16_t)0x3);
+        else mma_commit(&ctl->tfull[acc]);
         if (++acc == 2) {
           acc = 0;
           acc_phase ^= 1u;
         }
       }
       // drain: all issued MMAs complete before TMEM is freed
-      mma_commit(&ctl->drain);
+      if constexpr (PAIR) mma_commit_pair(&ctl->drain);
+      else mma_commit(&ctl->drain);
       const uint64_t t0 = gtimer();
       while (!mbar_try(&ctl->drain, 0))
         if (gtimer() - t0 > kTimeoutNs) {
@@ -425,10 +534,12 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     int acc = 0;
     uint32_t acc_phase = 0;
     float s_inc = 0.f, s_z = 0.f, s_r = 0.f, s_pv = 0.f;
+    const uint32_t tempty_pair[2] = {PAIR ? peer_addr(&ctl->tempty[0], 0) : 0u,
+                                     PAIR ? peer_addr(&ctl->tempty[1], 0) : 0u};
     for (int t = t_first; t < num_tiles; t += t_step) {
       int mb, nb;
       tile_coords(t, sched_m, num_n, mb, nb);
-      if (MC) mb = 2 * mb + rank;
+      if (CLUSTER) mb = 2 * mb + rank;
       const int cbase = nb * BN + h * EPI_COLS;
       // stage this warp's column data (its reads of the previous tile are done)
       __syncwarp();
@@ -493,7 +604,13 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         }
       }
       tc_fence_before();
-      mbar_arrive(&ctl->tempty[acc]);
+      if constexpr (PAIR) {
+        // every lane's TMEM loads have completed; one release per warp to the first CTA
+        __syncwarp();
+        if (lane == 0) mbar_arrive_cluster(tempty_pair[acc]);
+      } else {
+        mbar_arrive(&ctl->tempty[acc]);
+      }
       if (++acc == 2) {
         acc = 0;
         acc_phase ^= 1u;
@@ -511,13 +628,19 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
 
   tc_fence_before();
   __syncthreads();
-  // the peer may still multicast into / arrive on this CTA until it is done
-  if constexpr (MC) cluster_sync();
+  // the peer may still load into / arrive on / multiply from this CTA until it is done
+  if constexpr (CLUSTER) cluster_sync();
   tc_fence_after();
-  if (warp == 1)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                 "r"(TMEM_COLS)
-                 : "memory");
+  if (warp == 1) {
+    if constexpr (PAIR)
+      asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                   "r"(TMEM_COLS)
+                   : "memory");
+    else
+      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                   "r"(TMEM_COLS)
+                   : "memory");
+  }
 }
 
 // ---------------------------------------------------------------- host side
@@ -557,67 +680,95 @@ bool make_map(CUtensorMap* m, const void* base, uint64_t inner, uint64_t outer,
 
 }  // namespace
 
-// Two-CTA clusters with multicast B halves (IPT_TC_CLUSTER=1 at compile time,
-// used when the number of 128-row blocks is even) halve each CTA's L2 operand
-// reads; at n = 8192 they measured no faster than single CTAs, so single CTAs
-// are the default.
-#ifndef IPT_TC_CLUSTER
-#define IPT_TC_CLUSTER 0
+// Two-CTA clusters with multicast B halves (IPT_TC_MULTICAST=1 at compile
+// time, in place of the single-CTA kernel) halve each CTA's L2 operand reads
+// but not its shared-memory traffic; at n = 8192 they measured no faster than
+// single CTAs.
+#ifndef IPT_TC_MULTICAST
+#define IPT_TC_MULTICAST 0
 #endif
 
-cudaError_t launch_gemm_tc(const uint16_t* Dh, const uint16_t* Dl, const uint16_t* Wh,
-                           const uint16_t* Wl, const MapArgs<float>& a, int npad, int kpad,
-                           int passes, int bf16, cudaStream_t s) {
-  if (npad % BM || kpad % BN || npad % BK || (passes != 1 && passes != 3))
-    return cudaErrorInvalidValue;
-  const bool bf = bf16 != 0;
-  const int num_m = npad / BM, num_n = kpad / BN, num_kb = npad / BK;
-  const bool mc = IPT_TC_CLUSTER && (num_m % 2 == 0);
-  CUtensorMap mDh, mDl, mWh, mWl;
-  const uint32_t bbox = mc ? BN / 2 : BN;
-  if (!make_map(&mDh, Dh, npad, npad, BM, bf) || !make_map(&mDl, Dl, npad, npad, BM, bf) ||
-      !make_map(&mWh, Wh, npad, kpad, bbox, bf) || !make_map(&mWl, Wl, npad, kpad, bbox, bf))
-    return cudaErrorInvalidValue;
-  static int configured_device = -1;
-  static int num_sms = 0;
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return e;
-  if (configured_device != dev) {
-    e = cudaFuncSetAttribute(k_gemm_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             SMEM_BYTES);
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_gemm_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             SMEM_BYTES);
-    if (e != cudaSuccess) return e;
-    e = cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e != cudaSuccess) return e;
-    configured_device = dev;
-  }
-  const uint32_t idesc = idesc_for(bf);
-  if (!mc) {
-    const int tiles = num_m * num_n;
-    const int grid = tiles < num_sms ? tiles : num_sms;
-    k_gemm_tc<false><<<grid, NUM_THREADS, SMEM_BYTES, s>>>(mDh, mDl, mWh, mWl, a, num_m, num_n,
-                                                           num_kb, passes, idesc);
-    return cudaGetLastError();
-  }
-  const int pairs = (num_m / 2) * num_n;
-  const int clusters = pairs < num_sms / 2 ? pairs : num_sms / 2;
+template <int MODE>
+cudaError_t configure(int dev) {
+  static int configured = -1;
+  if (configured == dev) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(k_gemm_tc<MODE>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       smem_bytes<MODE>());
+  if (e == cudaSuccess) configured = dev;
+  return e;
+}
+
+template <int MODE>
+cudaError_t launch_cluster(const CUtensorMap& mDh, const CUtensorMap& mDl, const CUtensorMap& mWh,
+                           const CUtensorMap& mWl, const MapArgs<float>& a, int num_m, int num_n,
+                           int num_kb, int passes, uint32_t idesc, int num_sms, cudaStream_t s) {
+  static int max_clusters = 0;
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(2 * clusters);
-  cfg.blockDim = dim3(NUM_THREADS);
-  cfg.dynamicSmemBytes = SMEM_BYTES;
-  cfg.stream = s;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = 2;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
+  cfg.blockDim = dim3(NUM_THREADS);
+  cfg.dynamicSmemBytes = smem_bytes<MODE>();
+  cfg.stream = s;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_gemm_tc<true>, mDh, mDl, mWh, mWl, a, num_m, num_n, num_kb,
+  if (max_clusters <= 0) {
+    // clusters that fit at once (one CTA per SM); pairs need two free SMs of a GPC
+    cfg.gridDim = dim3(num_sms);
+    int c = 0;
+    if (cudaOccupancyMaxActiveClusters(&c, k_gemm_tc<MODE>, &cfg) != cudaSuccess || c <= 0)
+      c = num_sms / 2;
+    max_clusters = c;
+  }
+  const int pairs = (num_m / 2) * num_n;
+  const int clusters = pairs < max_clusters ? pairs : max_clusters;
+  cfg.gridDim = dim3(2 * clusters);
+  return cudaLaunchKernelEx(&cfg, k_gemm_tc<MODE>, mDh, mDl, mWh, mWl, a, num_m, num_n, num_kb,
                             passes, idesc);
+}
+
+cudaError_t launch_gemm_tc(const uint16_t* Dh, const uint16_t* Dl, const uint16_t* Wh,
+                           const uint16_t* Wl, const MapArgs<float>& a, int npad, int kpad,
+                           int passes, int bf16, int mode, cudaStream_t s) {
+  if (npad % BM || kpad % BN || npad % BK || (passes != 1 && passes != 3))
+    return cudaErrorInvalidValue;
+  const bool bf = bf16 != 0;
+  const int num_m = npad / BM, num_n = kpad / BN, num_kb = npad / BK;
+  const bool pair = mode != IPT_PRODUCT_SINGLE && num_m % 2 == 0;
+  const bool mc = !pair && IPT_TC_MULTICAST && num_m % 2 == 0;
+  CUtensorMap mDh, mDl, mWh, mWl;
+  const uint32_t bbox = (pair || mc) ? BN / 2 : BN;
+  if (!make_map(&mDh, Dh, npad, npad, BM, bf) || !make_map(&mDl, Dl, npad, npad, BM, bf) ||
+      !make_map(&mWh, Wh, npad, kpad, bbox, bf) || !make_map(&mWl, Wl, npad, kpad, bbox, bf))
+    return cudaErrorInvalidValue;
+  static int num_sms = 0, sms_device = -1;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (sms_device != dev) {
+    e = cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    sms_device = dev;
+  }
+  if (pair) {
+    if ((e = configure<MODE_PAIR>(dev)) != cudaSuccess) return e;
+    return launch_cluster<MODE_PAIR>(mDh, mDl, mWh, mWl, a, num_m, num_n, num_kb, passes,
+                                     idesc_for(bf, 2 * BM), num_sms, s);
+  }
+  if (mc) {
+    if ((e = configure<MODE_MULTICAST>(dev)) != cudaSuccess) return e;
+    return launch_cluster<MODE_MULTICAST>(mDh, mDl, mWh, mWl, a, num_m, num_n, num_kb, passes,
+                                          idesc_for(bf, BM), num_sms, s);
+  }
+  if ((e = configure<MODE_SINGLE>(dev)) != cudaSuccess) return e;
+  const int tiles = num_m * num_n;
+  const int grid = tiles < num_sms ? tiles : num_sms;
+  k_gemm_tc<MODE_SINGLE><<<grid, NUM_THREADS, smem_bytes<MODE_SINGLE>(), s>>>(
+      mDh, mDl, mWh, mWl, a, num_m, num_n, num_kb, passes, idesc_for(bf, BM));
+  return cudaGetLastError();
 }
 
 }  // namespace ipt

@@ -36,7 +36,7 @@ DTYPE = {torch.float64: 0, torch.float32: 1}
 class Options(C.Structure):
     _fields_ = [("precision", C.c_int), ("stop", C.c_int), ("diverge_bound", C.c_double),
                 ("stage_switch", C.c_double), ("staged_bf16", C.c_int), ("verify_fp64", C.c_int),
-                ("record_timing", C.c_int), ("z0", C.c_void_p)]
+                ("record_timing", C.c_int), ("z0", C.c_void_p), ("product_kernel", C.c_int)]
 
 
 class Result(C.Structure):
@@ -109,8 +109,12 @@ def _dev(t, dtype=None, name="tensor"):
     return t.contiguous()
 
 
+PRODUCT_KERNEL = {"auto": 0, "single": 1, "pair": 2}
+
+
 def make_options(precision="staged", stop="residual", diverge_bound=1e8, stage_switch=0.1,
-                 verify_fp64=False, z0=None, staged_bf16=False, record_timing=False) -> Options:
+                 verify_fp64=False, z0=None, staged_bf16=False, record_timing=False,
+                 product_kernel="auto") -> Options:
     o = Options()
     _lib.ipt_options_default(C.byref(o))
     o.precision = PRECISION[precision] if isinstance(precision, str) else int(precision)
@@ -121,6 +125,8 @@ def make_options(precision="staged", stop="residual", diverge_bound=1e8, stage_s
     o.staged_bf16 = 1 if staged_bf16 else 0
     o.record_timing = 1 if record_timing else 0
     o.z0 = None if z0 is None else z0.data_ptr()
+    o.product_kernel = (PRODUCT_KERNEL[product_kernel] if isinstance(product_kernel, str)
+                        else int(product_kernel))
     return o
 
 
@@ -150,8 +156,11 @@ class Solver:
     def solve_dense(self, M, theta=None, cols=None, tol=1e-6, max_iter=100, precision="staged",
                     stop="residual", z_dtype=torch.float32, verify_fp64=False, z0=None,
                     diverge_bound=1e8, stage_switch=0.1, staged_bf16=False,
-                    record_timing=False):
-        """Alg. 2 / Alg. 1 on the GPU.  Returns (lam [k] f64, Z (n, k) view, info dict)."""
+                    record_timing=False, product_kernel="auto"):
+        """Alg. 2 / Alg. 1 on the GPU.  Returns (lam [k] f64, Z (n, k) view, info dict).
+
+        product_kernel: "auto", "single" (one CTA per tile) or "pair" (two CTAs
+        per 256-row tile); selects the tensor-core product kernel only."""
         M = _dev(M, name="M")
         n = M.shape[0]
         if M.dim() != 2 or M.shape[1] != n or M.dtype not in DTYPE:
@@ -167,7 +176,7 @@ class Solver:
         else:
             z0t = None
         o = make_options(precision, stop, diverge_bound, stage_switch, verify_fp64, z0t,
-                         staged_bf16, record_timing)
+                         staged_bf16, record_timing, product_kernel)
         r = Result()
         _lib.ipt_solve_dense(self._h, n, _ptr(M), M.stride(0), DTYPE[M.dtype], _ptr(theta), k,
                              _ptr(cols), float(tol), int(max_iter), C.byref(o), _ptr(lam),

@@ -74,6 +74,28 @@ def test_single_step_matches_oracle_map(ipt, precision, n, k):
 
 
 # ------------------------------------------------------------------ full solves
+@pytest.mark.parametrize("precision", ["fp16", "fp16x3", "bf16x3", "staged"])
+@pytest.mark.parametrize("n,k", [(1024, 1024), (1000, 300), (2048, 512)])
+def test_product_kernels_single_and_pair_agree(ipt, precision, n, k):
+    """One CTA per 128 x 256 tile and two CTAs per 256 x 256 tile (paired MMA)
+    compute the same sums in the same K order: same iterates to FP32 rounding."""
+    M, th = w.dense_symmetric(n, 2e-3, seed=5, theta_step=0.25)
+    cols = np.sort(w.rng(6).permutation(n)[:k]).astype(np.int32)
+    Mg, tg, cg = cuda(M, torch.float32), cuda(th), cuda(cols, torch.int32)
+    out = {}
+    for kern in ["single", "pair"]:
+        lam, Z, info = ipt.Solver().solve_dense(Mg, theta=tg, cols=cg, tol=0.0, max_iter=4,
+                                                precision=precision, stop="increment",
+                                                product_kernel=kern)
+        assert info["status"] == "MAXITER", info
+        out[kern] = (lam.cpu().numpy(), Z.cpu().numpy(), info)
+    (l1, z1, i1), (l2, z2, i2) = out["single"], out["pair"]
+    scale = np.max(np.abs(z1 - oracle.unit_columns(n, cols)))
+    assert rel_max(z1, z2, scale) <= 1e-6
+    assert np.max(np.abs(l1 - l2) / np.abs(l1)) <= 1e-9
+    np.testing.assert_allclose(i1["hist_increment"], i2["hist_increment"], rtol=1e-5)
+
+
 def test_small_fp64_config_matches_oracle(ipt):
     """n = 256, theta_i = i, Delta N(0,1)*0.02, FP64, increment tol 1e-12."""
     M, th = w.dense_symmetric(256, 0.02, seed=1)
