@@ -45,6 +45,7 @@ struct ipt_handle {
   DevState* hst = nullptr;          // pinned mirror of the controller's words
   cudaEvent_t ev[8] = {};           // pre-pass / product / setup / finalize brackets
   int launches = 0;                 // kernels launched by the current call
+  bool e_pending = false;           // Z buffer 0 does not hold the unit columns yet
 };
 
 namespace {
@@ -187,7 +188,7 @@ ipt_status setup_dense(ipt_handle* h, const Plan& p, const void* M, int64_t ldm,
   launch_form_delta(M, ldm, m_dtype, (const double*)h->theta.p, p.n, p.npad,
                     (const int*)h->count.p, h->drow.p, p.f64 ? 1 : 0,
                     p.dt ? (float*)h->dt.p : nullptr, (double*)h->r0part.p, st, s);
-  h->launches += 3;  // form_delta, sum of partials, init/copy of Z below
+  h->launches += 2;  // form_delta, sum of partials
   if (p.tc) {
     launch_split_delta((const float*)h->drow.p, p.npad, p.bf16 ? 1 : 0, (uint16_t*)h->dh.p,
                        (uint16_t*)h->dl.p, (float*)h->rinv.p, s);
@@ -210,14 +211,21 @@ ipt_status setup_dense(ipt_handle* h, const Plan& p, const void* M, int64_t ldm,
       CK(cudaMemsetAsync((char*)h->z[b].p + (size_t)p.k * p.npad * ez, 0,
                          (size_t)(p.kpad - p.k) * p.npad * ez, s));
   }
+  h->e_pending = false;
   if (z0 && !rescale) {
     // exact copy (single evaluation at a caller-given Z)
     CK(cudaMemsetAsync(h->z[0].p, 0, kn * (p.f64 ? 8 : 4), s));
     launch_copy_z(z0, z0_dtype == IPT_DTYPE_F64, ldz0, p.n, p.k, h->z[0].p, p.npad, p.f64 ? 1 : 0,
                   s);
+    h->launches += 1;
+  } else if (!z0 && fe.passes == 0) {
+    // the product-free first evaluation knows Z = E without reading it: the
+    // unit columns are written only if the solve returns that iterate
+    h->e_pending = true;
   } else {
     launch_init_z(z0, ldz0, z0_dtype, (const int32_t*)h->icol.p, p.n, p.k, p.npad, p.kpad,
                   h->z[0].p, p.f64 ? 1 : 0, st, s);
+    h->launches += 1;
   }
   CK(cudaGetLastError());
   if (sync_check) {
@@ -507,6 +515,14 @@ ipt_status solve_dense(ipt_handle* h, int64_t n, const void* M, int64_t ldm, int
   }
   const int ans = hs.answer;
   if (tm.on) cudaEventRecord(h->ev[6], s);
+  // buffer 0 holds E only while no evaluation has written into it: the solve
+  // stopped at its first evaluation
+  if (ans == 0 && h->e_pending && hs.iter == 1) {
+    launch_init_z(nullptr, 0, 0, (const int32_t*)h->icol.p, p.n, p.k, p.npad, p.kpad, h->z[0].p,
+                  p.f64 ? 1 : 0, dst(h), s);
+    h->e_pending = false;
+    h->launches += 1;
+  }
   launch_lambda((const double*)h->theta.p, (const int32_t*)h->icol.p, (const double*)h->d.p,
                 p.k, lambda, s);
   launch_copy_z(h->z[ans].p, p.f64 ? 1 : 0, p.npad, p.n, p.k, Z, ldz,

@@ -108,67 +108,69 @@ __global__ void k_form_delta(const TM* __restrict__ M, int64_t ldm, const double
   }
 }
 
-// The same for FP32 M with 16-byte aligned rows: tile 32 rows x 128 columns,
-// block 32 x 8, each thread moves 4 consecutive columns of 4 rows with 16-byte
-// loads and stores; the transposed FP32 copy goes through a 129-float padded
-// shared tile (conflict-free column reads) as 128-byte column segments.
-template <typename TD>
+// The same for FP32 M with 16-byte aligned rows: tile 64 x 64, block 16 x 16.
+// Each thread moves 4 consecutive columns of 4 rows with 16-byte loads and
+// stores (a row segment is 256 contiguous bytes); the transposed FP32 copy
+// goes through a 65-float padded shared tile and leaves as 256-byte column
+// segments (one float2 per lane).
 __global__ void __launch_bounds__(256)
     k_form_delta4(const float* __restrict__ M, int64_t ldm, const double* theta, int n,
-                  int npad, const int* count, TD* __restrict__ Drow, float* __restrict__ DT,
+                  int npad, const int* count, float* __restrict__ Drow, float* __restrict__ DT,
                   double* __restrict__ r0part) {
-  __shared__ float tile[32][129];
-  const int c0 = blockIdx.x * 128, r0 = blockIdx.y * 32;
+  __shared__ float tile[64][65];
+  const int c0 = blockIdx.x * 64, r0 = blockIdx.y * 64;
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int j = c0 + 4 * tx;
   bool req[4];
 #pragma unroll
   for (int u = 0; u < 4; ++u) req[u] = (j + u < n) && count[j + u] > 0;
   float r0sum = 0.f;
+  float4 m4[4];
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const int i = r0 + ty + 8 * q;
-    float v[4] = {0.f, 0.f, 0.f, 0.f};
+  for (int q = 0; q < 4; ++q) {  // all loads first
+    const int i = r0 + ty + 16 * q;
+    m4[q] = make_float4(0.f, 0.f, 0.f, 0.f);
     if (i < n) {
       if (j + 3 < n) {
-        const float4 m4 = *reinterpret_cast<const float4*>(M + (int64_t)i * ldm + j);
-        v[0] = m4.x;
-        v[1] = m4.y;
-        v[2] = m4.z;
-        v[3] = m4.w;
+        m4[q] = *reinterpret_cast<const float4*>(M + (int64_t)i * ldm + j);
       } else {
+        float t[4] = {0.f, 0.f, 0.f, 0.f};
         for (int u = 0; u < 4; ++u)
-          if (j + u < n) v[u] = M[(int64_t)i * ldm + j + u];
+          if (j + u < n) t[u] = M[(int64_t)i * ldm + j + u];
+        m4[q] = make_float4(t[0], t[1], t[2], t[3]);
       }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int i = r0 + ty + 16 * q;
+    float v[4] = {m4[q].x, m4[q].y, m4[q].z, m4[q].w};
+    if (i < n) {
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         if (j + u == i) v[u] = (float)((double)v[u] - theta[i]);  // Delta_ii, formed in FP64
         else if (req[u]) r0sum = fmaf(v[u], v[u], r0sum);
       }
     }
-    TD* dst = Drow + (int64_t)i * npad + j;
-    if constexpr (sizeof(TD) == 4) {
-      *reinterpret_cast<float4*>(dst) = make_float4(v[0], v[1], v[2], v[3]);
-    } else {
-      for (int u = 0; u < 4; ++u) dst[u] = (TD)v[u];
-    }
+    *reinterpret_cast<float4*>(Drow + (int64_t)i * npad + j) = make_float4(v[0], v[1], v[2], v[3]);
 #pragma unroll
-    for (int u = 0; u < 4; ++u) tile[ty + 8 * q][4 * tx + u] = v[u];
+    for (int u = 0; u < 4; ++u) tile[ty + 16 * q][4 * tx + u] = v[u];
   }
+  const int tid = ty * 16 + tx, lane = tid & 31, w = tid >> 5;
   if (DT) {
     __syncthreads();
-    const int w = ty;  // 8 warps, 16 columns each
-#pragma unroll 4
-    for (int cc = 0; cc < 16; ++cc) {
-      const int col = w * 16 + cc;
-      DT[(int64_t)(c0 + col) * npad + r0 + tx] = tile[tx][col];
+#pragma unroll
+    for (int cc = 0; cc < 8; ++cc) {  // 8 warps x 8 columns, rows 2 lane, 2 lane + 1
+      const int col = w * 8 + cc;
+      *reinterpret_cast<float2*>(DT + (int64_t)(c0 + col) * npad + r0 + 2 * lane) =
+          make_float2(tile[2 * lane][col], tile[2 * lane + 1][col]);
     }
   }
   __shared__ float red[8];
-  const float wsum = warp_sum(r0sum);
-  if (tx == 0) red[ty] = wsum;
+  const float ws = warp_sum(r0sum);
+  if (lane == 0) red[w] = ws;
   __syncthreads();
-  if (tx == 0 && ty == 0) {
+  if (tid == 0) {
     double t = 0.0;
     for (int q = 0; q < 8; ++q) t += (double)red[q];
     r0part[(int64_t)blockIdx.y * gridDim.x + blockIdx.x] = t;
@@ -349,9 +351,9 @@ void launch_form_delta(const void* M, int64_t ldm, int m_dtype, const double* th
   dim3 b(32, 8);
   if (m_dtype == IPT_DTYPE_F32 && !drow_f64 && ldm % 4 == 0 &&
       (reinterpret_cast<uintptr_t>(M) & 15) == 0) {
-    dim3 g4(npad / 128, npad / 32);
-    k_form_delta4<float><<<g4, b, 0, s>>>((const float*)M, ldm, theta, n, npad, count,
-                                          (float*)Drow, DT, r0part);
+    dim3 g4(npad / 64, npad / 64), b4(16, 16);
+    k_form_delta4<<<g4, b4, 0, s>>>((const float*)M, ldm, theta, n, npad, count, (float*)Drow,
+                                    DT, r0part);
     k_sum_partials<<<1, 1024, 0, s>>>(r0part, (int64_t)g4.x * g4.y, st);
     return;
   }

@@ -47,13 +47,17 @@ constexpr int TMEM_COLS = 2 * BN;
 // rows and one 128-row half of B, so a CTA's shared memory takes 32 KB per
 // K step instead of 48 KB for the same 128 x 256 x 64 of its own output.
 enum { MODE_SINGLE = 0, MODE_MULTICAST = 1, MODE_PAIR = 2 };
+#ifndef IPT_PAIR_STAGES
+#define IPT_PAIR_STAGES 6
+#endif
 template <int MODE>
 struct Shape {
   static constexpr int B_BYTES = (MODE == MODE_PAIR ? BN / 2 : BN) * BK * 2;  // per CTA
   static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;                       // per CTA
-  static constexpr int STAGES = MODE == MODE_PAIR ? 6 : 4;
+  static constexpr int STAGES = MODE == MODE_PAIR ? IPT_PAIR_STAGES : 4;
 };
 constexpr int MAX_STAGES = 6;
+static_assert(IPT_PAIR_STAGES >= 2 && IPT_PAIR_STAGES <= MAX_STAGES, "pipeline depth");
 constexpr int EPI_WARPS = 8;  // two per TMEM lane quarter, each owning half of the columns
 constexpr int NUM_THREADS = 64 + 32 * EPI_WARPS;
 constexpr int EPI_THREADS = 32 * EPI_WARPS;

@@ -96,6 +96,26 @@ def test_product_kernels_single_and_pair_agree(ipt, precision, n, k):
     np.testing.assert_allclose(i1["hist_increment"], i2["hist_increment"], rtol=1e-5)
 
 
+@pytest.mark.parametrize("precision", ["staged", "f32", "fp16", "f64"])
+def test_stop_at_first_evaluation_returns_unit_columns(ipt, precision):
+    """Alg. 2 returns the Z whose F passed the test: stopping at the first
+    evaluation (a loose tolerance, or max_iter = 1) returns Z = E exactly, with
+    Lambda = theta_cols + Delta_{cols, cols}."""
+    n, k = 300, 40
+    M, th = w.dense_symmetric(n, 1e-2, seed=9, theta_step=0.5)
+    cols = np.arange(5, 5 + k, dtype=np.int32)
+    Mg, tg, cg = cuda(M, torch.float32), cuda(th), cuda(cols, torch.int32)
+    E = oracle.unit_columns(n, cols)
+    s = ipt.Solver()
+    for kw, status in [({"tol": 10.0, "max_iter": 20}, "OK"), ({"tol": 0.0, "max_iter": 1}, "MAXITER")]:
+        # a full solve first leaves every workspace buffer holding a later iterate
+        s.solve_dense(Mg, theta=tg, cols=cg, tol=1e-6, max_iter=30, precision=precision)
+        lam, Z, info = s.solve_dense(Mg, theta=tg, cols=cg, precision=precision, **kw)
+        assert info["status"] == status and info["iterations"] == 1, info
+        assert np.array_equal(Z.cpu().numpy(), E)
+        np.testing.assert_allclose(lam.cpu().numpy(), np.diag(M)[cols], rtol=1e-6)
+
+
 def test_small_fp64_config_matches_oracle(ipt):
     """n = 256, theta_i = i, Delta N(0,1)*0.02, FP64, increment tol 1e-12."""
     M, th = w.dense_symmetric(256, 0.02, seed=1)
