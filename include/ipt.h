@@ -100,6 +100,10 @@ typedef struct {
                            IPT_PRODUCT_PAIR (two CTAs per 256 x 256 tile, one paired MMA;
                            needs an even number of 128-row blocks, else SINGLE is used).
                            Results are identical; only speed differs                     */
+  int csr_window;       /* ipt_solve_csr: nonzero (default) = each product evaluates only the
+                           rows that can be nonzero: the rows of the current iterate's
+                           nonzero rows widened by the band max|j - m| of the stored
+                           entries (exact: other rows of Z and F are zero).  0 = all rows */
 } ipt_options;
 
 /* Values of ipt_options.product_kernel. */
@@ -131,6 +135,8 @@ typedef struct {
   double hist_rho[IPT_MAX_HISTORY];
   int hist_stage[IPT_MAX_HISTORY]; /* precision of each evaluation's product (ipt_precision),
                                       -1 for the product-free first evaluation           */
+  long long rows_evaluated; /* ipt_solve_csr: rows the products evaluated, summed over
+                               evaluations (n per evaluation without the active window)  */
 } ipt_result;
 
 typedef struct ipt_handle ipt_handle;

@@ -32,6 +32,9 @@ cudaError_t ensure(Buf& b, size_t bytes) {
   return e;
 }
 
+// Sparse solves enqueue this many evaluations per host synchronisation.
+constexpr int kCsrChunk = 4;
+
 }  // namespace
 
 struct ipt_handle {
@@ -43,9 +46,16 @@ struct ipt_handle {
   Buf delta, cpart;                 // sparse path: delta_j = M_jj - theta_j, r0 partials
   Buf hM, hTheta, hCols, hLam, hZ;  // device staging of the host-buffer entry point
   DevState* hst = nullptr;          // pinned mirror of the controller's words
+  DevState* hinit = nullptr;        // pinned initial controller words of a solve
   cudaEvent_t ev[8] = {};           // pre-pass / product / setup / finalize brackets
+  cudaEvent_t evb[4 * kCsrChunk] = {};  // per-evaluation brackets of a sparse chunk
   int launches = 0;                 // kernels launched by the current call
   bool e_pending = false;           // Z buffer 0 does not hold the unit columns yet
+  // Sparse path: Z buffers 0 and 1 are zero outside rows [csr_dirty_lo, csr_dirty_hi)
+  // for the row-major layout (csr_n, csr_kk, csr_es) at these addresses; csr_n < 0
+  // = unknown contents.
+  int csr_n = -1, csr_kk = 0, csr_es = 0, csr_dirty_lo = 0, csr_dirty_hi = 0;
+  void* csr_z[2] = {nullptr, nullptr};
 };
 
 namespace {
@@ -159,16 +169,17 @@ ipt_status setup_dense(ipt_handle* h, const Plan& p, const void* M, int64_t ldm,
                        int z0_dtype, bool rescale, FirstEval fe, bool sync_check) {
   cudaStream_t s = h->s;
   DevState* st = dst(h);
+  h->csr_n = -1;  // the dense path overwrites the shared Z buffers
   CK(cudaMemsetAsync(st, 0, sizeof(DevState), s));
   {
-    DevState init;
+    DevState& init = *h->hinit;  // pinned: the copy below is truly asynchronous
     memset(&init, 0, kStateHead);
     init.stage = fe.stage;
     init.passes = fe.passes;
     init.rebase = fe.rebase;
     init.accurate = fe.accurate;
     init.base = -1;
-    CK(cudaMemcpyAsync(st, &init, kStateHead, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(st, h->hinit, kStateHead, cudaMemcpyHostToDevice, s));
   }
   CK(cudaMemsetAsync(h->count.p, 0, (size_t)p.npad * 4, s));
   launch_theta(M, ldm, m_dtype, theta, p.n, p.npad, (double*)h->theta.p, (float*)h->thh.p,
@@ -248,6 +259,8 @@ struct Timing {
 ipt_status ensure_events(ipt_handle* h) {
   for (int i = 0; i < 8; ++i)
     if (!h->ev[i]) CK(cudaEventCreate(&h->ev[i]));
+  for (int i = 0; i < 4 * kCsrChunk; ++i)
+    if (!h->evb[i]) CK(cudaEventCreate(&h->evb[i]));
   return IPT_OK;
 }
 
@@ -360,6 +373,7 @@ void fill_result(const DevState& hs, const Timing& tm, int launches, ipt_result*
   out->increment = hs.inc;
   out->rho = hs.rho;
   out->r0 = sqrt(hs.r0acc);
+  out->rows_evaluated = hs.rows_eval;
   out->history_len = std::min(hs.iter, IPT_MAX_HISTORY);
   for (int i = 0; i < out->history_len; ++i) {
     out->hist_increment[i] = hs.hist_inc[i];
@@ -566,6 +580,7 @@ void ipt_options_default(ipt_options* opt) {
   opt->record_timing = 0;
   opt->z0 = nullptr;
   opt->product_kernel = IPT_PRODUCT_AUTO;
+  opt->csr_window = 1;
 }
 
 const char* ipt_status_string(int status) {
@@ -588,7 +603,9 @@ ipt_status ipt_create(ipt_handle** h, void* stream) {
   ipt_handle* x = new ipt_handle();
   x->s = static_cast<cudaStream_t>(stream);
   if (cudaGetDevice(&x->dev) != cudaSuccess ||
-      cudaMallocHost((void**)&x->hst, sizeof(DevState)) != cudaSuccess) {
+      cudaMallocHost((void**)&x->hst, sizeof(DevState)) != cudaSuccess ||
+      cudaMallocHost((void**)&x->hinit, sizeof(DevState)) != cudaSuccess) {
+    if (x->hst) cudaFreeHost(x->hst);
     delete x;
     return IPT_CUDA_ERROR;
   }
@@ -609,7 +626,10 @@ ipt_status ipt_destroy(ipt_handle* h) {
     if (b->p) cudaFree(b->p);
   for (int i = 0; i < 8; ++i)
     if (h->ev[i]) cudaEventDestroy(h->ev[i]);
+  for (int i = 0; i < 4 * kCsrChunk; ++i)
+    if (h->evb[i]) cudaEventDestroy(h->evb[i]);
   if (h->hst) cudaFreeHost(h->hst);
+  if (h->hinit) cudaFreeHost(h->hinit);
   delete h;
   return IPT_OK;
 }
@@ -757,27 +777,45 @@ ipt_status ipt_solve_csr(ipt_handle* h, int64_t n, int64_t nnz, const int32_t* r
   CK(ensure(h->count, (size_t)n * 4));
   CK(ensure(h->d, (size_t)kk * 8));
   CK(ensure(h->st, sizeof(DevState)));
-  CK(ensure(h->cpart, (size_t)((n + 255) / 256) * 8));
+  CK(ensure(h->cpart, (size_t)((n + 255) / 256) * 8));  // one partial per row-pass block
   cudaStream_t s = h->s;
   DevState* st = dst(h);
   if (tm.on) cudaEventRecord(h->ev[4], s);
   CK(cudaMemsetAsync(st, 0, sizeof(DevState), s));
   {
-    DevState init;
+    DevState& init = *h->hinit;  // pinned: the copy below is truly asynchronous
     memset(&init, 0, kStateHead);
     init.stage = prec;
     init.passes = 1;
     init.accurate = 1;
     init.base = -1;
-    CK(cudaMemcpyAsync(st, &init, kStateHead, cudaMemcpyHostToDevice, s));
+    init.z_lo = ni;
+    init.z_hi = -1;
+    init.nz_lo = ni;
+    init.nz_hi = -1;
+    init.win_lo = 0;
+    init.win_hi = ni;
+    CK(cudaMemcpyAsync(st, h->hinit, kStateHead, cudaMemcpyHostToDevice, s));
   }
+  // Z buffers: zero everywhere but at the unit entries.  Only rows a previous
+  // sparse solve of the same layout may have written need clearing.
+  const bool known = h->csr_n == ni && h->csr_kk == kk && h->csr_es == (int)ez &&
+                     h->csr_z[0] == h->z[0].p && h->csr_z[1] == h->z[1].p;
+  const size_t row_bytes = (size_t)kk * ez;
+  const size_t clr_lo = known ? (size_t)h->csr_dirty_lo : 0;
+  const size_t clr_hi = known ? (size_t)h->csr_dirty_hi : (size_t)n;
+  for (int b = 0; b < 2; ++b)
+    if (clr_hi > clr_lo)
+      CK(cudaMemsetAsync((char*)h->z[b].p + clr_lo * row_bytes, 0, (clr_hi - clr_lo) * row_bytes,
+                         s));
+  h->csr_n = -1;  // contents unknown until this solve ends
   CK(cudaMemsetAsync(h->count.p, 0, (size_t)n * 4, s));
   launch_validate(cols, ni, ki, kk, nullptr, (int32_t*)h->icol.p, (int*)h->count.p, st, s);
   launch_csr_rows(rowptr, colind, vals, v_dtype, theta, ni, nnz, (const int*)h->count.p,
                   (double*)h->theta.p, (float*)h->thh.p, (float*)h->thl.p, (double*)h->delta.p,
-                  (double*)h->cpart.p, st, s);
-  launch_csr_init_z((const int32_t*)h->icol.p, ni, kk, h->z[0].p, f64 ? 1 : 0, s);
-  h->launches += 6;
+                  (double*)h->cpart.p, opt.csr_window ? 1 : 0, st, s);
+  launch_csr_units((const int32_t*)h->icol.p, ki, kk, h->z[0].p, f64 ? 1 : 0, s);
+  h->launches += 5;
   CK(cudaGetLastError());
   if (tm.on) cudaEventRecord(h->ev[5], s);
   ControlArgs ca;
@@ -791,31 +829,39 @@ ipt_status ipt_solve_csr(ipt_handle* h, int64_t n, int64_t nnz, const int32_t* r
   ca.low_stage = prec;
   ca.high_stage = prec;
   ca.low_unit = 0.0;
-  int cur = 0;
-  for (int it = 0; it < max_iter; ++it) {
-    if (tm.on) cudaEventRecord(h->ev[0], s);
-    launch_csr_prepass(rowptr, colind, vals, v_dtype, (const double*)h->delta.p,
-                       (const int32_t*)h->icol.p, kk, h->z[cur].p, f64 ? 1 : 0,
-                       (double*)h->d.p, st, s);
-    if (tm.on) {
-      cudaEventRecord(h->ev[1], s);
-      cudaEventRecord(h->ev[2], s);
+  ca.csr_n = ni;
+  ca.csr_window = opt.csr_window ? 1 : 0;
+  // Evaluations are enqueued kCsrChunk at a time with one host sync per chunk:
+  // every kernel returns at entry once the controller has stopped, and with
+  // two Z buffers the iterate alternates (evaluation i reads buffer i & 1).
+  for (int it0 = 0; it0 < max_iter; it0 += kCsrChunk) {
+    const int nb = std::min(kCsrChunk, max_iter - it0);
+    for (int q = 0; q < nb; ++q) {
+      const int cur = (it0 + q) & 1;
+      if (tm.on) cudaEventRecord(h->evb[4 * q], s);
+      launch_csr_prepass(rowptr, colind, vals, v_dtype, (const double*)h->delta.p,
+                         (const int32_t*)h->icol.p, kk, h->z[cur].p, f64 ? 1 : 0,
+                         (double*)h->d.p, st, s);
+      if (tm.on) {
+        cudaEventRecord(h->evb[4 * q + 1], s);
+        cudaEventRecord(h->evb[4 * q + 2], s);
+      }
+      launch_csr_spmm_map(rowptr, colind, vals, v_dtype, (const double*)h->delta.p,
+                          (const double*)h->theta.p, (const float*)h->thh.p,
+                          (const float*)h->thl.p, (const int32_t*)h->icol.p,
+                          (const double*)h->d.p, ni, ki, kk, h->z[cur].p, h->z[cur ^ 1].p,
+                          f64 ? 1 : 0, nblk, st, s);
+      if (tm.on) cudaEventRecord(h->evb[4 * q + 3], s);
+      launch_control(st, ca, s);
+      h->launches += 3;
     }
-    launch_csr_spmm_map(rowptr, colind, vals, v_dtype, (const double*)h->delta.p,
-                        (const double*)h->theta.p, (const float*)h->thh.p,
-                        (const float*)h->thl.p, (const int32_t*)h->icol.p,
-                        (const double*)h->d.p, ni, ki, kk, h->z[cur].p, h->z[cur ^ 1].p,
-                        f64 ? 1 : 0, nblk, st, s);
-    if (tm.on) cudaEventRecord(h->ev[3], s);
-    launch_control(st, ca, s);
-    h->launches += 3;
     if (cudaGetLastError() != cudaSuccess ||
         cudaMemcpyAsync(h->hst, st, kStateHead, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess) {
       v = IPT_CUDA_ERROR;
       break;
     }
-    if (it == 0) {
+    if (it0 == 0) {
       v = status_from_flags(h->hst->flags);
       if (v != IPT_OK) break;
       if (tm.on) {
@@ -823,9 +869,18 @@ ipt_status ipt_solve_csr(ipt_handle* h, int64_t n, int64_t nnz, const int32_t* r
         if (cudaEventElapsedTime(&ms, h->ev[4], h->ev[5]) == cudaSuccess) tm.setup_ms = ms;
       }
     }
-    collect_timing(h, 1, &tm);
+    if (tm.on) {  // the evaluations of this chunk that ran before the stop
+      const int ran = std::min(nb, h->hst->iter - it0);
+      for (int q = 0; q < ran; ++q) {
+        float a_ = 0.f, b_ = 0.f;
+        if (cudaEventElapsedTime(&a_, h->evb[4 * q], h->evb[4 * q + 1]) == cudaSuccess)
+          tm.prepass_ms += a_;
+        if (cudaEventElapsedTime(&b_, h->evb[4 * q + 2], h->evb[4 * q + 3]) == cudaSuccess)
+          tm.product_ms[0] += b_;
+        tm.product_launches[0] += 1;
+      }
+    }
     if (h->hst->done) break;
-    cur = h->hst->cur;
   }
   if (v != IPT_OK) {
     out->status = v;
@@ -840,7 +895,14 @@ ipt_status ipt_solve_csr(ipt_handle* h, int64_t n, int64_t nnz, const int32_t* r
   if (tm.on) cudaEventRecord(h->ev[6], s);
   launch_lambda((const double*)h->theta.p, (const int32_t*)h->icol.p, (const double*)h->d.p, ki,
                 lambda, s);
-  launch_csr_out(h->z[hs.answer].p, f64 ? 1 : 0, ni, ki, kk, Z, ldz,
+  // rows outside the last window are zero in the returned iterate
+  const int wl = hs.win_lo, wh = hs.win_hi;
+  const size_t oes = z_dtype == IPT_DTYPE_F64 ? 8 : 4;
+  if (wl > 0) CK(cudaMemset2DAsync(Z, (size_t)ldz * oes, 0, (size_t)wl * oes, (size_t)ki, s));
+  if (wh < ni)
+    CK(cudaMemset2DAsync((char*)Z + (size_t)wh * oes, (size_t)ldz * oes, 0,
+                         (size_t)(ni - wh) * oes, (size_t)ki, s));
+  launch_csr_out(h->z[hs.answer].p, f64 ? 1 : 0, wl, wh, ki, kk, Z, ldz,
                  z_dtype == IPT_DTYPE_F64 ? 1 : 0, s);
   h->launches += 2;
   if (tm.on) cudaEventRecord(h->ev[7], s);
@@ -852,6 +914,14 @@ ipt_status ipt_solve_csr(ipt_handle* h, int64_t n, int64_t nnz, const int32_t* r
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, h->ev[6], h->ev[7]) == cudaSuccess) tm.finalize_ms = ms;
   }
+  // both Z buffers were written only inside the (growing) windows
+  h->csr_n = ni;
+  h->csr_kk = kk;
+  h->csr_es = (int)ez;
+  h->csr_z[0] = h->z[0].p;
+  h->csr_z[1] = h->z[1].p;
+  h->csr_dirty_lo = wl;
+  h->csr_dirty_hi = wh;
   fill_result(hs, tm, h->launches, out);
   out->wall_ms =
       std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();

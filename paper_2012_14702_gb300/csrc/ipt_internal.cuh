@@ -60,6 +60,12 @@ struct DevState {
   int flags;   // validation flags
   int timeout; // bounded device wait gave up (code of the waiting role)
   int stage_iters[2];
+  // CSR active window (rows outside it are exactly zero in Z and in F):
+  int band;            // largest |j - m| over the stored entries of M
+  int z_lo, z_hi;      // every nonzero row of the current iterate lies in [z_lo, z_hi]
+  int nz_lo, nz_hi;    // the same for the F this evaluation writes
+  int win_lo, win_hi;  // rows [win_lo, win_hi) evaluated by the next product
+  long long rows_eval; // rows the products evaluated so far
   double hist_inc[IPT_MAX_HISTORY];
   double hist_rho[IPT_MAX_HISTORY];
   int hist_stage[IPT_MAX_HISTORY];
@@ -130,6 +136,8 @@ struct ControlArgs {
   int max_iter, stop, mode, k;
   int low_stage, high_stage;  // STAGED: the 1-pass stage and the split stage it switches to
   double low_unit;            // STAGED: relative error model of a 1-pass product
+  int csr_n = 0;              // CSR solves: n (the window is clipped to [0, n)); 0 = dense
+  int csr_window = 0;         // CSR: nonzero = evaluate only rows that can be nonzero
 };
 void launch_control(DevState* st, ControlArgs a, cudaStream_t s);
 
@@ -145,9 +153,10 @@ cudaError_t launch_gemm_tc(const uint16_t* Dh, const uint16_t* Dl, const uint16_
 // sparse path (k_csr.cu): Z row-major n x kk, kk = k rounded up to 64
 void launch_csr_rows(const int32_t* rowptr, const int32_t* colind, const void* vals, int v_dtype,
                      const double* theta_in, int n, int64_t nnz, const int* count, double* theta,
-                     float* th_hi, float* th_lo, double* delta, double* part, DevState* st,
-                     cudaStream_t s);
-void launch_csr_init_z(const int32_t* icol, int n, int kk, void* Z, int f64, cudaStream_t s);
+                     float* th_hi, float* th_lo, double* delta, double* part, int window,
+                     DevState* st, cudaStream_t s);
+// Z[cols[c], c] = 1 in the row-major n x kk iterate (the rest already zero).
+void launch_csr_units(const int32_t* icol, int k, int kk, void* Z, int f64, cudaStream_t s);
 void launch_csr_prepass(const int32_t* rowptr, const int32_t* colind, const void* vals,
                         int v_dtype, const double* delta, const int32_t* icol, int kk,
                         const void* Z, int f64, double* d, DevState* st, cudaStream_t s);
@@ -156,8 +165,9 @@ void launch_csr_spmm_map(const int32_t* rowptr, const int32_t* colind, const voi
                          const float* th_hi, const float* th_lo, const int32_t* icol,
                          const double* d, int n, int k, int kk, const void* Zin, void* Fout,
                          int f64, int nblk, DevState* st, cudaStream_t s);
-void launch_csr_out(const void* Z, int f64, int n, int k, int kk, void* out, int64_t ldo,
-                    int out_f64, cudaStream_t s);
+// rows [j_lo, n) of the row-major iterate into the caller's column-major Z
+void launch_csr_out(const void* Z, int f64, int j_lo, int n, int k, int kk, void* out,
+                    int64_t ldo, int out_f64, cudaStream_t s);
 
 // ---------------------------------------------------------------- device helpers
 __device__ __forceinline__ double warp_sum(double v) {
@@ -168,6 +178,14 @@ __device__ __forceinline__ double warp_sum(double v) {
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ int warp_min_int(int v) {
+  for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ int warp_max_int(int v) {
+  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
   return v;
 }
 __device__ __forceinline__ float warp_max(float v) {

@@ -28,13 +28,16 @@ __device__ __forceinline__ T ldval(const void* v, int64_t i, int dt) {
                              : (T) static_cast<const float*>(v)[i];
 }
 
-// One pass over the rows (one thread per row): the CSR structure check (row
-// bounds within [0, nnz] and ascending, column indices in [0, n); a bad row is
-// flagged and skipped, and the later CSR kernels then do nothing), the stored
-// diagonal M_jj (0 if the row stores none), theta_j (given, or M_jj), its FP32 split and
-// delta_j = M_jj - theta_j; non-finite theta is flagged; and the per-block
-// partial of ||M Z0 - Z0 Lambda0||^2, the squared off-diagonal entries in
-// requested columns (count[col] > 0).
+// One pass over the rows, one thread per row (measured faster than 8 lanes
+// per row, whose extra warps cost more than the coalescing gains): the CSR
+// structure check (row bounds within [0, nnz] and ascending, column indices in [0, n); a
+// bad row is flagged and skipped, and the later CSR kernels then do nothing),
+// the stored diagonal M_jj (0 if the row stores none), theta_j (given, or
+// M_jj), its FP32 split and delta_j = M_jj - theta_j; non-finite theta is
+// flagged; the per-block partial of ||M Z0 - Z0 Lambda0||^2, the squared
+// off-diagonal entries in requested columns (count[col] > 0); the band
+// max |j - m| of the stored entries and the row range of the requested rows
+// (the support of Z0 = E).
 __global__ void __launch_bounds__(256)
     k_csr_rows(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colind,
                const void* __restrict__ vals, int v_dtype, const double* __restrict__ theta_in,
@@ -43,7 +46,9 @@ __global__ void __launch_bounds__(256)
                double* __restrict__ part, DevState* st) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   float r0 = 0.f;
+  int band = 0, lo = n, hi = -1;
   if (j < n) {
+    if (count[j] > 0) lo = hi = j;
     double mjj = 0.0;
     const int e0 = rowptr[j], e1 = rowptr[j + 1];
     const bool rows_ok = e0 >= 0 && e0 <= e1 && (int64_t)e1 <= nnz && (j > 0 || e0 == 0) &&
@@ -55,6 +60,7 @@ __global__ void __launch_bounds__(256)
         atomicOr(&st->flags, FLAG_CSR_INDEX);
         break;
       }
+      band = max(band, abs(m - j));
       if (m == j) {
         mjj = ldval<double>(vals, e, v_dtype);
       } else if (count[m] > 0) {
@@ -70,19 +76,45 @@ __global__ void __launch_bounds__(256)
     th_lo[j] = (float)(t - (double)h);
     delta[j] = mjj - t;
   }
+  // block reduction; the shared words take one atomic per block, and only
+  // when the block's value would change them (most blocks see the same band)
   __shared__ float red[8];
+  __shared__ int rb[8], rl[8], rh[8];
+  const int wq = threadIdx.x >> 5;
   const float w = warp_sum(r0);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = w;
+  band = warp_max_int(band);
+  lo = warp_min_int(lo);
+  hi = warp_max_int(hi);
+  if ((threadIdx.x & 31) == 0) {
+    red[wq] = w;
+    rb[wq] = band;
+    rl[wq] = lo;
+    rh[wq] = hi;
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
     double tot = 0.0;
-    for (int q = 0; q < 8; ++q) tot += (double)red[q];
+    int b = 0, l = n, hh = -1;
+    for (int q = 0; q < 8; ++q) {
+      tot += (double)red[q];
+      b = max(b, rb[q]);
+      l = min(l, rl[q]);
+      hh = max(hh, rh[q]);
+    }
     part[blockIdx.x] = tot;
+    if (b > *(volatile int*)&st->band) atomicMax(&st->band, b);
+    if (hh >= 0) {
+      atomicMin(&st->z_lo, l);
+      atomicMax(&st->z_hi, hh);
+    }
   }
 }
 
+// One block: ||R0||^2 from the row pass's partials, and the rows the first
+// product evaluates: all of them, or (window) the requested rows widened by
+// the band (rows further away have no stored entry in a nonzero row of E).
 __global__ void __launch_bounds__(1024)
-    k_csr_sum_r0(const double* __restrict__ part, int count, DevState* st) {
+    k_csr_sum_r0(const double* __restrict__ part, int count, int n, int window, DevState* st) {
   __shared__ double red[1024];
   double t = 0.0;
   for (int i = threadIdx.x; i < count; i += blockDim.x) t += part[i];
@@ -92,17 +124,28 @@ __global__ void __launch_bounds__(1024)
     if ((int)threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
     __syncthreads();
   }
-  if (threadIdx.x == 0) st->r0acc = red[0];
+  if (threadIdx.x == 0) {
+    st->r0acc = red[0];
+    st->nz_lo = n;
+    st->nz_hi = -1;
+    if (window && st->z_hi >= st->z_lo) {
+      st->win_lo = max(0, st->z_lo - st->band);
+      st->win_hi = (int)min((int64_t)n, (int64_t)st->z_hi + 1 + st->band);
+    } else {
+      st->win_lo = 0;
+      st->win_hi = n;
+    }
+  }
 }
 
 // Z = E in the row-major layout (Z[j*kk + c] = 1 at j = cols[c]); padding
 // zero.  Block: 64 columns x 4 rows; each thread writes one entry per row step.
 template <typename T>
-__global__ void k_csr_init_z(const int32_t* __restrict__ icol, int n, int kk, T* __restrict__ Z) {
-  const int c = blockIdx.y * 64 + (threadIdx.x & 63);
-  const int ic = icol[c];
-  for (int j = blockIdx.x * 4 + (threadIdx.x >> 6); j < n; j += gridDim.x * 4)
-    Z[(int64_t)j * kk + c] = ic == j ? T(1) : T(0);
+__global__ void k_csr_units(const int32_t* __restrict__ icol, int k, int kk, T* __restrict__ Z) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= k) return;
+  const int i = icol[c];  // -1 for a column index out of range (flagged)
+  if (i >= 0) Z[(int64_t)i * kk + c] = T(1);
 }
 
 // d_c = sum_m Delta_{i_c, m} Z_{m, c} = delta_{i_c} Z_{i_c, c} + sum over the
@@ -158,7 +201,9 @@ struct Four<double> {
 // the 4 columns 64*chunk + 4l .. 4l+3 and gathers them as one 16-byte vector.
 // The half loads up to 16 (column, value) pairs at once and broadcasts them
 // with width-16 shuffles; the stored diagonal gets weight 0 (delta_j is
-// applied in the epilogue).  Norm partials: one atomic per warp.
+// applied in the epilogue).  Only rows [win_lo, win_hi) are evaluated (all
+// rows unless the active window is on); the row range of the nonzero rows of
+// F is recorded for the next window.  Norm partials: one atomic per warp.
 template <typename T>
 __global__ void __launch_bounds__(256, 4)
     k_csr_spmm_map(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colind,
@@ -173,7 +218,9 @@ __global__ void __launch_bounds__(256, 4)
   const unsigned hmask = (lane < 16) ? 0x0000ffffu : 0xffff0000u;
   const int half0 = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 2 + (lane >> 4);
   const int nhalves = gridDim.x * (blockDim.x >> 5) * 2;
+  const int wlo = st->win_lo, whi = st->win_hi;
   T s_inc = T(0), s_z = T(0), s_r = T(0);
+  int f_lo = n, f_hi = -1;
   for (int ch = 0; ch < kk; ch += 64) {
     const int cb = ch + 4 * hl;
     int ic[4];
@@ -189,9 +236,9 @@ __global__ void __launch_bounds__(256, 4)
       lc[u] = ic[u] >= 0 ? th_lo[ic[u]] : 0.f;
     }
     // both halves of a warp iterate together; a half past the last row idles
-    for (int jb = half0 - (lane >> 4); jb < n; jb += nhalves) {
+    for (int jb = wlo + half0 - (lane >> 4); jb < whi; jb += nhalves) {
       const int j = jb + (lane >> 4);
-      const bool live = j < n;
+      const bool live = j < whi;
       const int e0 = live ? rowptr[j] : 0, e1 = live ? rowptr[j + 1] : 0;
       T acc[4] = {T(0), T(0), T(0), T(0)};
       for (int eb = e0; eb < e1; eb += 16) {
@@ -231,6 +278,10 @@ __global__ void __launch_bounds__(256, 4)
           T f, r;
           map_entry<T>(zj[u], p, dc[u], gap, j == ic[u], f, r);
           fo[u] = f;
+          if (f != T(0)) {
+            f_lo = min(f_lo, j);
+            f_hi = max(f_hi, j);
+          }
           s_inc += (f - zj[u]) * (f - zj[u]);
           s_z += zj[u] * zj[u];
           s_r += r * r;
@@ -244,21 +295,55 @@ __global__ void __launch_bounds__(256, 4)
       *reinterpret_cast<V4*>(Fout + (int64_t)j * kk + cb) = out;
     }
   }
+  // one set of atomics per block that evaluated a row (they all hit the same
+  // few words, so idle blocks of the persistent grid must not add any)
+  __shared__ double red[3][8];
+  __shared__ int rlo[8], rhi[8], rwork[8];
+  const int w = threadIdx.x >> 5;
   const double b0 = warp_sum((double)s_inc), b1 = warp_sum((double)s_z),
                b2 = warp_sum((double)s_r);
+  f_lo = warp_min_int(f_lo);
+  f_hi = warp_max_int(f_hi);
+  const int worked = __any_sync(0xffffffffu, wlo + half0 - (lane >> 4) < whi);
   if (lane == 0) {
-    atomicAdd(&st->acc_inc2, b0);
-    atomicAdd(&st->acc_z2, b1);
-    atomicAdd(&st->acc_r2, b2);
+    red[0][w] = b0;
+    red[1][w] = b1;
+    red[2][w] = b2;
+    rlo[w] = f_lo;
+    rhi[w] = f_hi;
+    rwork[w] = worked;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t0 = 0.0, t1 = 0.0, t2 = 0.0;
+    int lo = n, hi = -1, any = 0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) {
+      t0 += red[0][q];
+      t1 += red[1][q];
+      t2 += red[2][q];
+      lo = min(lo, rlo[q]);
+      hi = max(hi, rhi[q]);
+      any |= rwork[q];
+    }
+    if (any) {
+      atomicAdd(&st->acc_inc2, t0);
+      atomicAdd(&st->acc_z2, t1);
+      atomicAdd(&st->acc_r2, t2);
+    }
+    if (hi >= 0) {
+      atomicMin(&st->nz_lo, lo);
+      atomicMax(&st->nz_hi, hi);
+    }
   }
 }
 
-// Row-major n x kk iterate -> column-major n x k output (ldo), 32x32 tiles.
+// Rows [j_lo, n) of the row-major n x kk iterate -> column-major n x k output
+// (ldo), 32x32 tiles.
 template <typename TI, typename TO>
-__global__ void k_csr_transpose_out(const TI* __restrict__ Z, int n, int k, int kk,
+__global__ void k_csr_transpose_out(const TI* __restrict__ Z, int j_lo, int n, int k, int kk,
                                     TO* __restrict__ out, int64_t ldo) {
   __shared__ TI tile[32][33];
-  const int j0 = blockIdx.x * 32, c0 = blockIdx.y * 32;
+  const int j0 = j_lo + blockIdx.x * 32, c0 = blockIdx.y * 32;
   const int tx = threadIdx.x, ty = threadIdx.y;
   for (int q = 0; q < 32; q += 8) {
     const int j = j0 + ty + q, c = c0 + tx;
@@ -278,18 +363,17 @@ inline unsigned nblocks(int64_t total, int bs) { return (unsigned)((total + bs -
 // ---------------------------------------------------------------- launchers
 void launch_csr_rows(const int32_t* rowptr, const int32_t* colind, const void* vals, int v_dtype,
                      const double* theta_in, int n, int64_t nnz, const int* count, double* theta,
-                     float* th_hi, float* th_lo, double* delta, double* part, DevState* st,
-                     cudaStream_t s) {
+                     float* th_hi, float* th_lo, double* delta, double* part, int window,
+                     DevState* st, cudaStream_t s) {
   const unsigned g = nblocks(n, 256);
   k_csr_rows<<<g, 256, 0, s>>>(rowptr, colind, vals, v_dtype, theta_in, n, nnz, count, theta, th_hi,
                                th_lo, delta, part, st);
-  k_csr_sum_r0<<<1, 1024, 0, s>>>(part, (int)g, st);
+  k_csr_sum_r0<<<1, 1024, 0, s>>>(part, (int)g, n, window, st);
 }
 
-void launch_csr_init_z(const int32_t* icol, int n, int kk, void* Z, int f64, cudaStream_t s) {
-  dim3 g(std::min(nblocks(n, 4), 65535u), kk / 64);
-  if (f64) k_csr_init_z<double><<<g, 256, 0, s>>>(icol, n, kk, (double*)Z);
-  else k_csr_init_z<float><<<g, 256, 0, s>>>(icol, n, kk, (float*)Z);
+void launch_csr_units(const int32_t* icol, int k, int kk, void* Z, int f64, cudaStream_t s) {
+  if (f64) k_csr_units<double><<<nblocks(k, 256), 256, 0, s>>>(icol, k, kk, (double*)Z);
+  else k_csr_units<float><<<nblocks(k, 256), 256, 0, s>>>(icol, k, kk, (float*)Z);
 }
 
 void launch_csr_prepass(const int32_t* rowptr, const int32_t* colind, const void* vals,
@@ -319,21 +403,22 @@ void launch_csr_spmm_map(const int32_t* rowptr, const int32_t* colind, const voi
                                                (const float*)Zin, (float*)Fout, st);
 }
 
-void launch_csr_out(const void* Z, int f64, int n, int k, int kk, void* out, int64_t ldo,
-                    int out_f64, cudaStream_t s) {
-  dim3 g(nblocks(n, 32), nblocks(kk, 32)), b(32, 8);
+void launch_csr_out(const void* Z, int f64, int j_lo, int n, int k, int kk, void* out,
+                    int64_t ldo, int out_f64, cudaStream_t s) {
+  if (n <= j_lo) return;
+  dim3 g(nblocks(n - j_lo, 32), nblocks(kk, 32)), b(32, 8);
   if (f64 && out_f64)
-    k_csr_transpose_out<double, double><<<g, b, 0, s>>>((const double*)Z, n, k, kk,
-                                                        (double*)out, ldo);
+    k_csr_transpose_out<double, double><<<g, b, 0, s>>>((const double*)Z, j_lo, n, k,
+                                                        kk, (double*)out, ldo);
   else if (f64)
-    k_csr_transpose_out<double, float><<<g, b, 0, s>>>((const double*)Z, n, k, kk, (float*)out,
-                                                       ldo);
+    k_csr_transpose_out<double, float><<<g, b, 0, s>>>((const double*)Z, j_lo, n, k, kk,
+                                                       (float*)out, ldo);
   else if (out_f64)
-    k_csr_transpose_out<float, double><<<g, b, 0, s>>>((const float*)Z, n, k, kk, (double*)out,
-                                                       ldo);
+    k_csr_transpose_out<float, double><<<g, b, 0, s>>>((const float*)Z, j_lo, n, k, kk,
+                                                       (double*)out, ldo);
   else
-    k_csr_transpose_out<float, float><<<g, b, 0, s>>>((const float*)Z, n, k, kk, (float*)out,
-                                                      ldo);
+    k_csr_transpose_out<float, float><<<g, b, 0, s>>>((const float*)Z, j_lo, n, k, kk,
+                                                      (float*)out, ldo);
 }
 
 }  // namespace ipt

@@ -534,6 +534,7 @@ __global__ void k_control(DevState* st, ControlArgs a) {
     st->hist_rho[it] = rho;
     st->hist_stage[it] = passes == 0 ? -1 : stage;
   }
+  if (a.csr_n > 0) st->rows_eval += st->win_hi - st->win_lo;
   if (passes == 1 && (stage == IPT_PREC_BF16 || stage == IPT_PREC_FP16)) st->stage_iters[0]++;
   else if (passes != 0) st->stage_iters[1]++;
   st->inc = inc;
@@ -588,6 +589,20 @@ __global__ void k_control(DevState* st, ControlArgs a) {
     } else if (passes == 0) {
       // non-staged tensor-core / FP32 solve after its product-free first evaluation
       st->passes = (stage == IPT_PREC_BF16X3 || stage == IPT_PREC_FP16X3) ? 3 : 1;
+    }
+    if (a.csr_n > 0) {
+      // CSR: the next iterate is this evaluation's F; its nonzero rows widened
+      // by the band bound the rows where the next F can be nonzero (the window
+      // only grows, so rows outside it were never written and are still zero)
+      st->z_lo = st->nz_lo;
+      st->z_hi = st->nz_hi;
+      if (a.csr_window && st->z_hi >= st->z_lo) {
+        st->win_lo = min(st->win_lo, max(0, st->z_lo - st->band));
+        st->win_hi = (int)max((int64_t)st->win_hi,
+                              min((int64_t)a.csr_n, (int64_t)st->z_hi + 1 + st->band));
+      }
+      st->nz_lo = a.csr_n;
+      st->nz_hi = -1;
     }
     st->cur = out;
   }

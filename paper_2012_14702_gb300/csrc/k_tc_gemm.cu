@@ -620,13 +620,26 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         acc_phase ^= 1u;
       }
     }
+    // norm partials: warp sums, then one set of atomics per CTA (the slot of
+    // this warp's column data is free once its last tile is done)
     const double b0 = warp_sum((double)s_inc), b1 = warp_sum((double)s_z),
                  b2 = warp_sum((double)s_r), b3 = warp_sum((double)s_pv);
+    double* wsum = reinterpret_cast<double*>(ctl->wcol[e]);
+    __syncwarp();
     if (lane == 0) {
-      atomicAdd(&a.st->acc_inc2, b0);
-      atomicAdd(&a.st->acc_z2, b1);
-      atomicAdd(&a.st->acc_r2, b2);
-      atomicAdd(&a.st->acc_pv2, b3);
+      wsum[0] = b0;
+      wsum[1] = b1;
+      wsum[2] = b2;
+      wsum[3] = b3;
+    }
+    asm volatile("bar.sync 1, %0;" ::"n"(EPI_THREADS) : "memory");  // the epilogue warps only
+    if (e == 0 && lane < 4) {
+      double t = 0.0;
+      for (int w = 0; w < EPI_WARPS; ++w) t += reinterpret_cast<double*>(ctl->wcol[w])[lane];
+      double* dst = lane == 0 ? &a.st->acc_inc2
+                              : lane == 1 ? &a.st->acc_z2 : lane == 2 ? &a.st->acc_r2
+                                                                      : &a.st->acc_pv2;
+      atomicAdd(dst, t);
     }
   }
 

@@ -36,7 +36,8 @@ DTYPE = {torch.float64: 0, torch.float32: 1}
 class Options(C.Structure):
     _fields_ = [("precision", C.c_int), ("stop", C.c_int), ("diverge_bound", C.c_double),
                 ("stage_switch", C.c_double), ("staged_bf16", C.c_int), ("verify_fp64", C.c_int),
-                ("record_timing", C.c_int), ("z0", C.c_void_p), ("product_kernel", C.c_int)]
+                ("record_timing", C.c_int), ("z0", C.c_void_p), ("product_kernel", C.c_int),
+                ("csr_window", C.c_int)]
 
 
 class Result(C.Structure):
@@ -48,7 +49,7 @@ class Result(C.Structure):
                 ("finalize_ms", C.c_double), ("wall_ms", C.c_double), ("history_len", C.c_int),
                 ("hist_increment", C.c_double * MAX_HISTORY),
                 ("hist_rho", C.c_double * MAX_HISTORY),
-                ("hist_stage", C.c_int * MAX_HISTORY)]
+                ("hist_stage", C.c_int * MAX_HISTORY), ("rows_evaluated", C.c_longlong)]
 
     def to_dict(self) -> dict:
         h = self.history_len
@@ -62,7 +63,8 @@ class Result(C.Structure):
                 "wall_ms": self.wall_ms,
                 "hist_increment": list(self.hist_increment[:h]),
                 "hist_rho": list(self.hist_rho[:h]),
-                "hist_stage": [PRECISION_NAME.get(s, s) for s in self.hist_stage[:h]]}
+                "hist_stage": [PRECISION_NAME.get(s, s) for s in self.hist_stage[:h]],
+                "rows_evaluated": self.rows_evaluated}
 
 
 _vp, _i64, _i32, _d = C.c_void_p, C.c_int64, C.c_int, C.c_double
@@ -226,8 +228,10 @@ class Solver:
     # ------------------------------------------------------------------ sparse
     def solve_csr(self, rowptr, colind, vals, n, theta=None, cols=None, tol=1e-6, max_iter=100,
                   precision="f32", stop="residual", z_dtype=torch.float32, diverge_bound=1e8,
-                  record_timing=False):
-        """Sparse M (CSR, all stored entries of M).  Returns (lam, Z (n, k) view, info)."""
+                  record_timing=False, window=True):
+        """Sparse M (CSR, all stored entries of M).  Returns (lam, Z (n, k) view, info).
+
+        window: evaluate only the rows that can be nonzero (exact); False = all rows."""
         rowptr = _dev(rowptr, torch.int32, "rowptr")
         colind = _dev(colind, torch.int32, "colind")
         vals = _dev(vals, name="vals")
@@ -237,6 +241,7 @@ class Solver:
         lam = torch.empty(k, dtype=torch.float64, device=vals.device)
         Zt = torch.empty((k, n), dtype=z_dtype, device=vals.device)
         o = make_options(precision, stop, diverge_bound, record_timing=record_timing)
+        o.csr_window = 1 if window else 0
         r = Result()
         _lib.ipt_solve_csr(self._h, n, colind.numel(), _ptr(rowptr), _ptr(colind), _ptr(vals),
                            DTYPE[vals.dtype], _ptr(theta), k, _ptr(cols), float(tol),

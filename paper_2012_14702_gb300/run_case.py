@@ -37,7 +37,7 @@ def run_dense(name, solves, precision, tol):
             raise SystemExit(1)
 
 
-def run_csr(name, solves, precision, tol):
+def run_csr(name, solves, precision, tol, window=True):
     import torch
     from paper_2012_14702_gb300 import ipt
     n, per_row, band, scale, seed, k = workloads.CSR_CONFIGS[name]
@@ -52,7 +52,8 @@ def run_csr(name, solves, precision, tol):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         _, _, info = s.solve_csr(rp, ci, vv, n, cols=cg, tol=tol, max_iter=50,
-                                 precision="f32" if precision == "staged" else precision)
+                                 precision="f32" if precision == "staged" else precision,
+                                 window=window)
         torch.cuda.synchronize()
         print(f"{name} solve {i}: {info['status']} iterations {info['iterations']} "
               f"rho {info['rho']:.3e} {1e3 * (time.perf_counter() - t0):.2f} ms", flush=True)
@@ -67,11 +68,13 @@ def main(argv=None):
     ap.add_argument("--solves", type=int, default=2)
     ap.add_argument("--precision", default="staged")
     ap.add_argument("--tol", type=float, default=1e-6)
+    ap.add_argument("--all-rows", action="store_true",
+                    help="sparse workloads: evaluate every row (no active window)")
     a = ap.parse_args(argv)
     if a.workload in workloads.DENSE_CONFIGS:
         run_dense(a.workload, a.solves, a.precision, a.tol)
     else:
-        run_csr(a.workload, a.solves, a.precision, a.tol)
+        run_csr(a.workload, a.solves, a.precision, a.tol, window=not a.all_rows)
 
 
 if __name__ == "__main__":

@@ -145,3 +145,100 @@ def test_csr_full_size_sampled_columns_match_oracle(ipt):
     E = oracle.unit_columns(n, cols[pick])
     err = np.linalg.norm(Zs - ref["Z"]) / np.linalg.norm(ref["Z"] - E)
     assert err <= 1e-4, err
+
+
+def _random_pattern_csr(n, per_row, scale, seed):
+    """Symmetric CSR with off-diagonal entries at uniformly random columns (no band)."""
+    g = w.rng(seed)
+    rows = np.repeat(np.arange(n), per_row)
+    cols = g.integers(0, n, size=n * per_row)
+    keep = rows != cols
+    rows, cols = rows[keep], cols[keep]
+    a = np.zeros((n, n))
+    a[rows, cols] = g.standard_normal(rows.size) * scale
+    a = np.triu(a, 1)
+    a = a + a.T
+    th = np.arange(1, n + 1) * 0.1
+    a[np.arange(n), np.arange(n)] = th
+    r, c = np.nonzero(a)
+    rowptr = np.zeros(n + 1, dtype=np.int64)
+    np.add.at(rowptr, r + 1, 1)
+    return np.cumsum(rowptr).astype(np.int32), c.astype(np.int32), a[r, c], th
+
+
+@pytest.mark.parametrize("precision,vdt", [("f32", torch.float32), ("f64", torch.float64)])
+@pytest.mark.parametrize("case", ["banded_low", "banded_middle", "random_pattern", "tridiagonal"])
+def test_csr_active_window_equals_all_rows(ipt, precision, vdt, case):
+    """The active window (rows of the current iterate's support widened by the band)
+    evaluates exactly the rows that can be nonzero: the same iterates, bit for bit,
+    as evaluating every row."""
+    n = 6000
+    if case == "random_pattern":
+        rowptr, colind, vals, th = _random_pattern_csr(n, 2, 1e-2, seed=12)
+    elif case == "tridiagonal":
+        i = np.arange(n)
+        rows = np.concatenate([i, i[:-1], i[1:]])
+        cc = np.concatenate([i, i[1:], i[:-1]])
+        vv = np.concatenate([i + 1.0, np.full(n - 1, 0.3), np.full(n - 1, 0.3)])
+        order = np.lexsort((cc, rows))
+        rowptr = np.zeros(n + 1, dtype=np.int64)
+        np.add.at(rowptr, rows[order] + 1, 1)
+        rowptr, colind, vals, th = (np.cumsum(rowptr).astype(np.int32),
+                                    cc[order].astype(np.int32), vv[order], i + 1.0)
+    else:
+        rowptr, colind, vals, th = w.csr_banded(n, 4, 100, 1e-3, seed=13, theta_step=0.05)
+    k = 16
+    if case == "banded_middle":
+        cols = np.arange(3000, 3000 + k, dtype=np.int32)[::-1].copy()
+    else:
+        cols = w.lowest_columns(th, k)
+    rp, ci, vv = csr_on_gpu(rowptr, colind, vals, vdt)
+    cg = cuda(cols, torch.int32)
+    out = {}
+    for win in [True, False]:
+        for it in [1, 2, 6]:
+            lam, Z, info = ipt.Solver().solve_csr(rp, ci, vv, n, cols=cg, tol=0.0, max_iter=it,
+                                                  precision=precision, stop="increment",
+                                                  window=win, z_dtype=torch.float64)
+            assert info["status"] == "MAXITER", info
+            out[(win, it)] = (lam.cpu().numpy(), Z.cpu().numpy(), info["hist_increment"])
+    for it in [1, 2, 6]:
+        a, b = out[(True, it)], out[(False, it)]
+        assert np.array_equal(a[1], b[1]), it
+        assert np.array_equal(a[0], b[0])
+        np.testing.assert_allclose(a[2], b[2], rtol=1e-12)
+    # the window result also matches the oracle's iterate
+    ref = oracle.ipt_solve_csr(rowptr, colind, vals, n, cols=cols, tol=0.0, max_iter=6,
+                               stop="increment")
+    E = oracle.unit_columns(n, cols)
+    err = np.linalg.norm(out[(True, 6)][1] - ref["Z"]) / np.linalg.norm(ref["Z"] - E)
+    assert err <= (1e-10 if precision == "f64" else 1e-4), err
+
+
+def test_csr_handle_reuse_across_problems_and_dense(ipt):
+    """One handle, several problems: the sparse path clears only the rows an
+    earlier solve wrote, so results must not depend on what ran before."""
+    n = 5000
+    rowptr, colind, vals, th = w.csr_banded(n, 4, 60, 1e-3, seed=14, theta_step=0.05)
+    rp, ci, vv = csr_on_gpu(rowptr, colind, vals)
+    ca = cuda(np.arange(10, 30, dtype=np.int32), torch.int32)
+    cb = cuda(np.arange(4000, 4012, dtype=np.int32), torch.int32)
+    fresh = {}
+    for name, cg in [("a", ca), ("b", cb)]:
+        lam, Z, info = ipt.Solver().solve_csr(rp, ci, vv, n, cols=cg, tol=1e-7, max_iter=40)
+        assert info["status"] == "OK"
+        fresh[name] = Z.cpu().numpy()
+    s = ipt.Solver()
+    M, thd = w.dense_symmetric(512, 1e-3, seed=2, theta_step=0.5)
+    for name, cg in [("a", ca), ("b", cb), ("a", ca), ("dense", None), ("b", cb),
+                     ("window-off", None), ("a", ca)]:
+        if name == "dense":
+            s.solve_dense(cuda(M, torch.float32), theta=cuda(thd, torch.float64), tol=1e-6,
+                          max_iter=30)
+            continue
+        if name == "window-off":
+            s.solve_csr(rp, ci, vv, n, cols=cb, tol=1e-7, max_iter=40, window=False)
+            continue
+        lam, Z, info = s.solve_csr(rp, ci, vv, n, cols=cg, tol=1e-7, max_iter=40)
+        assert info["status"] == "OK"
+        assert np.array_equal(Z.cpu().numpy(), fresh[name]), name
