@@ -3,4 +3,5 @@ from .ipt_oracle import *  # noqa: F401,F403
 from .ipt_oracle import (OK, MAXITER, DIVERGED, DEGENERATE_THETA, INVALID_ARG,  # noqa: F401
                          partition, unit_columns, inverse_gaps, ipt_map, residual,
                          initial_residual_norm, ipt_solve, ipt_solve_csr,
-                         rs_corrections, chart_jacobian)
+                         rs_corrections, chart_jacobian, acx_differences, acx_sigma,
+                         acx_update, ipt_solve_acx)

@@ -16,6 +16,8 @@ near-diagonal eigenvalue problems"), step by step and in its notation:
 * Rayleigh-Schroedinger corrections Z^[l]           -- Eq. (ARS-alpha), App. B
 * the chart Jacobian of f_i whose multipliers the 3x3 polynomials of
   App. D.3 annihilate                               -- App. D.1
+* Alternating Cyclic Extrapolation in place of the Picard update
+  (IPT-ACX)                                         -- Alg. 3, Section 5
 
 Everything is float64 and dense numpy (the sparse variant multiplies with
 scipy's CSR product).  Library primitives (``@``, ``numpy.linalg``) serve as
@@ -37,6 +39,18 @@ Readings of the paper this oracle takes (the paper is silent or garbled):
 6. Divergence: a non-finite increment or residual, or ||Z||_F > bound*sqrt(k).
 7. theta must be pairwise distinct over the requested columns and every row
    (Section 3 requires simple unperturbed eigenvalues), else DEGENERATE_THETA.
+8. Alg. 3 (ACX) as printed is garbled in three places; read as: the step
+   length is sigma = |<D^p, D^(p-1)>| / ||D^p||^2 (squared norm: the update
+   must not change under z -> scale); the update keeps the D^0 = z term,
+   z <- z + 2 sigma D^1 + sigma^2 D^2 (p = 2) and
+   z <- z + 3 sigma D^1 + 3 sigma^2 D^2 + sigma^3 D^3 (p = 3); the order
+   index advances once per extrapolation, p = 3, 2, 3, 2, ...  For k
+   columns each column has its own sigma (each column is its own fixed-point
+   problem f_i of Alg. 1) unless a single global sigma is asked for; a column
+   with D^p = 0 takes sigma = 1 (the update is then the plain iterate f^p(z)).
+   ``iterations`` counts evaluations of F; the stopping test is made at the
+   extrapolated points z only (Alg. 3's loop condition), and the returned pair
+   is the last such z with Lambda from its evaluation.
 """
 
 from __future__ import annotations
@@ -187,6 +201,120 @@ def ipt_solve_csr(rowptr, colind, vals, n, theta=None, cols=None, **kw):
     Delta = (M - sp.diags(theta)).tocsr()
     return ipt_solve(None, theta=theta, cols=cols, Delta=Delta,
                      product=lambda Z: np.asarray(Delta @ Z), **kw)
+
+
+def acx_differences(z, fs):
+    """Alg. 3 lines 4-6 and 11: the differences of the iterates z, f(z), f^2(z), ...
+
+    ``fs`` = [f(z), f^2(z), (f^3(z))]; returns [D^1, D^2, (D^3)] with
+    D^1 = f(z) - z, D^2 = f^2(z) - 2 f(z) + z, D^3 = f^3(z) - 3 f^2(z) + 3 f(z) - z.
+    """
+    D = [fs[0] - z, fs[1] - 2.0 * fs[0] + z]
+    if len(fs) >= 3:
+        D.append(fs[2] - 3.0 * fs[1] + 3.0 * fs[0] - z)
+    return D
+
+
+def acx_sigma(Dp, Dq, per_column=True):
+    """Alg. 3 lines 8 / 12 (reading 8): sigma = |<D^p, D^(p-1)>| / ||D^p||^2.
+
+    Inner products over each column (per_column) or over the whole block;
+    a zero ||D^p|| gives sigma = 1.  Returns a length-k array (global: repeated).
+    """
+    if per_column:
+        num = np.abs(np.sum(Dp * Dq, axis=0))
+        den = np.sum(Dp * Dp, axis=0)
+    else:
+        num = np.full(Dp.shape[1], abs(float(np.sum(Dp * Dq))))
+        den = np.full(Dp.shape[1], float(np.sum(Dp * Dp)))
+    safe = np.where(den > 0, den, 1.0)
+    return np.where(den > 0, num / safe, 1.0)
+
+
+def acx_update(z, fs, per_column=True):
+    """Alg. 3 lines 7-14: the order-p extrapolation (p = len(fs)) from z, f(z), ..., f^p(z)."""
+    D = acx_differences(z, fs)
+    p = len(fs)
+    if p == 2:
+        s = acx_sigma(D[1], D[0], per_column)[None, :]
+        return z + 2.0 * s * D[0] + s * s * D[1]
+    if p == 3:
+        s = acx_sigma(D[2], D[1], per_column)[None, :]
+        return z + 3.0 * s * D[0] + 3.0 * s * s * D[1] + s * s * s * D[2]
+    raise ValueError("ACX order must be 2 or 3")
+
+
+def ipt_solve_acx(M, theta=None, cols=None, tol=1e-12, max_iter=1000, stop="increment",
+                  diverge_bound=1e8, history=False, Delta=None, product=None,
+                  sigma="column", orders=(3, 2)):
+    """IPT-ACX: Alg. 1 / Alg. 2 with the Picard update replaced by Alg. 3.
+
+    Each extrapolation evaluates F at z (where Alg. 3's test is made), at
+    f(z) and, for order 3, at f^2(z), then moves z by acx_update.  Orders
+    cycle through ``orders``.  Same arguments, statuses and result dict as
+    ipt_solve (reading 8 for what ``iterations`` and the returned pair are).
+    """
+    if Delta is None:
+        Delta, theta = partition(M, theta)
+    theta = np.asarray(theta, dtype=np.float64)
+    n = len(theta)
+    cols = np.arange(n) if cols is None else np.asarray(cols, dtype=np.int64)
+    k = len(cols)
+    out = {"status": INVALID_ARG, "iterations": 0, "Z": None, "lam": None,
+           "increment": np.nan, "rho": np.nan, "inc_hist": [], "rho_hist": []}
+    if k == 0 or len(set(cols.tolist())) != k or cols.min() < 0 or cols.max() >= n:
+        return out
+    if max_iter < 1 or not (tol >= 0) or sigma not in ("column", "global"):
+        return out
+    if not _check_theta(theta, cols):
+        out["status"] = DEGENERATE_THETA
+        return out
+    G = inverse_gaps(theta, cols)
+    r0 = initial_residual_norm(Delta, cols)
+
+    def evaluate(x):
+        F, P, d = ipt_map(Delta, theta, cols, x, G=G, product=product)
+        xnorm = np.linalg.norm(x)
+        inc = np.linalg.norm(F - x) / xnorm
+        lam = theta[cols] + d
+        R = theta[:, None] * x + P - x * lam[None, :]
+        rho = np.linalg.norm(R) / r0 if r0 > 0 else 0.0
+        if history:
+            out["inc_hist"].append(inc)
+            out["rho_hist"].append(rho)
+        bad = not (np.isfinite(inc) and np.isfinite(rho)) or xnorm > diverge_bound * np.sqrt(k)
+        return F, lam, inc, rho, bad
+
+    z = unit_columns(n, cols)
+    evals, step = 0, 0
+    while True:
+        p = orders[step % len(orders)]
+        F, lam, inc, rho, bad = evaluate(z)
+        evals += 1
+        out.update(Z=z, lam=lam, iterations=evals, increment=inc, rho=rho)
+        if bad:
+            out["status"] = DIVERGED
+            return out
+        if (inc if stop == "increment" else rho) <= tol:
+            out["status"] = OK
+            return out
+        if evals == max_iter:
+            out["status"] = MAXITER
+            return out
+        fs = [F]
+        for _ in range(p - 1):
+            Fq, _, _, _, bad = evaluate(fs[-1])
+            evals += 1
+            out["iterations"] = evals
+            if bad:
+                out["status"] = DIVERGED
+                return out
+            if evals == max_iter:
+                out["status"] = MAXITER
+                return out
+            fs.append(Fq)
+        z = acx_update(z, fs, per_column=(sigma == "column"))
+        step += 1
 
 
 def rs_corrections(Delta, theta, order):

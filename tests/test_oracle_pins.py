@@ -378,3 +378,106 @@ def test_morgan_tridiagonal_threshold_qualitative():
     assert oracle.ipt_solve(M, th, cols=[0], tol=1e-10, max_iter=2000)["status"] == oracle.OK
     M, th = w.morgan_tridiagonal(400, 1.0)
     assert oracle.ipt_solve(M, th, cols=[0], tol=1e-10, max_iter=2000)["status"] != oracle.OK
+
+
+# ------------------------------------------------------------------ ACX (Alg. 3)
+@pytest.mark.parametrize("order", [2, 3])
+def test_acx_solves_columnwise_affine_maps_in_one_extrapolation(order):
+    """For a contraction f(x) = a x + b (a < 1, a scalar per column) the
+    differences are D^q = (a - 1)^q (x - x*), the step is s = 1/(1 - a), and the
+    order-p update of Alg. 3 (with the z term and the squared norm, reading 8)
+    lands exactly on x* = b / (1 - a).  A dropped term, a wrong coefficient, a
+    sign or an unsquared norm all miss x*."""
+    g = np.random.default_rng(3)
+    n, k = 40, 5
+    a = np.array([0.9, -0.7, 0.3, 0.55, -0.2])
+    b = g.standard_normal((n, k))
+    x = g.standard_normal((n, k))
+    f = lambda y: a[None, :] * y + b
+    fs = [f(x)]
+    for _ in range(order - 1):
+        fs.append(f(fs[-1]))
+    z = oracle.acx_update(x, fs, per_column=True)
+    np.testing.assert_allclose(z, b / (1.0 - a[None, :]), rtol=1e-12, atol=1e-12)
+    # one step length for the whole block is exact only when the factors agree
+    z_glob = oracle.acx_update(x, fs, per_column=False)
+    assert np.max(np.abs(z_glob - b / (1.0 - a[None, :]))) > 1e-3
+    same = lambda y: 0.4 * y + b
+    fs2 = [same(x)]
+    for _ in range(order - 1):
+        fs2.append(same(fs2[-1]))
+    np.testing.assert_allclose(oracle.acx_update(x, fs2, per_column=False), b / 0.6,
+                               rtol=1e-12, atol=1e-12)
+
+
+def test_acx_differences_are_binomial_and_sigma_degenerate_column():
+    """D^q are the forward differences of z, f(z), f^2(z), f^3(z); a column with
+    D^p = 0 takes s = 1, so the update there is the plain iterate f^p(z)."""
+    g = np.random.default_rng(4)
+    z, f1, f2, f3 = (g.standard_normal((6, 3)) for _ in range(4))
+    D = oracle.acx_differences(z, [f1, f2, f3])
+    np.testing.assert_allclose(D[0], f1 - z)
+    np.testing.assert_allclose(D[1], (f2 - f1) - (f1 - z))
+    np.testing.assert_allclose(D[2], ((f3 - f2) - (f2 - f1)) - ((f2 - f1) - (f1 - z)))
+    # column 0 sits at a fixed point (D^1 = D^2 = 0): s = 1 and z stays; column 1
+    # moves by a constant (D^1 != 0, D^2 = 0): s = 1 and z -> f^2(z)
+    zz = np.zeros((4, 2))
+    c = np.ones(4)
+    fs = [np.stack([c, c], 1), np.stack([c, 2 * c], 1)]
+    zz[:, 0] = 1.0
+    out = oracle.acx_update(zz, fs, per_column=True)
+    np.testing.assert_allclose(out[:, 0], c)
+    np.testing.assert_allclose(out[:, 1], 2 * c)
+
+
+def test_acx_keeps_unit_entries_and_matches_plain_fixed_point():
+    """f_i(z)_i = 1 for every z, so every difference vanishes at the unit entry
+    and IPT-ACX keeps Z_{i_c, c} = 1 exactly; it converges to the same eigenpairs
+    as the Picard iteration and LAPACK."""
+    M, th = w.dense_symmetric(120, 0.01, seed=5, theta_step=0.5)
+    cols = np.array([3, 50, 7, 99])
+    r = oracle.ipt_solve_acx(M, th, cols=cols, tol=1e-13, max_iter=200)
+    assert r["status"] == oracle.OK
+    assert np.all(r["Z"][cols, np.arange(len(cols))] == 1.0)
+    p = oracle.ipt_solve(M, th, cols=cols, tol=1e-13, max_iter=200)
+    np.testing.assert_allclose(r["lam"], p["lam"], rtol=1e-12)
+    np.testing.assert_allclose(r["Z"], p["Z"], atol=1e-11)
+    ev, V = np.linalg.eigh(M)
+    for c, i in enumerate(cols):
+        j = np.argmin(np.abs(ev - r["lam"][c]))
+        np.testing.assert_allclose(r["Z"][:, c], V[:, j] / V[i, j], atol=1e-10)
+
+
+def test_acx_morgan_tridiagonal_domain_and_matvecs():
+    """Section 5 / Fig. (morgan): on the tridiagonal M_ii = i, M_{i,i+-1} = eps,
+    IPT-ACX needs far fewer matvecs than IPT at eps = 0.5, and converges where IPT
+    no longer does (eps = 1, 5; IPT stops converging beyond eps ~ 0.5), to the
+    lowest eigenpair."""
+    n = 600
+    M, th = w.morgan_tridiagonal(n, 0.5)
+    plain = oracle.ipt_solve(M, th, cols=[0], tol=1e-10, max_iter=400)
+    acx = oracle.ipt_solve_acx(M, th, cols=[0], tol=1e-10, max_iter=400)
+    assert plain["status"] == acx["status"] == oracle.OK
+    assert acx["iterations"] * 2 < plain["iterations"]
+    ev = np.linalg.eigvalsh(M)[0]
+    assert abs(acx["lam"][0] - ev) < 1e-9 and abs(plain["lam"][0] - ev) < 1e-9
+    for eps in [1.0, 5.0]:
+        M, th = w.morgan_tridiagonal(n, eps)
+        plain = oracle.ipt_solve(M, th, cols=[0], tol=1e-10, max_iter=400)
+        acx = oracle.ipt_solve_acx(M, th, cols=[0], tol=1e-10, max_iter=400)
+        assert plain["status"] in (oracle.DIVERGED, oracle.MAXITER)
+        assert acx["status"] == oracle.OK, (eps, acx["status"], acx["iterations"])
+        assert abs(acx["lam"][0] - np.linalg.eigvalsh(M)[0]) < 1e-8 * max(1.0, eps)
+
+
+@pytest.mark.parametrize("sigma", ["column", "global"])
+def test_acx_full_spectrum_beyond_picard_domain(sigma):
+    """Dense full spectrum at a perturbation where the Picard iteration no longer
+    converges (n = 256, theta_i = i/8, Delta N(0,1)*0.03): IPT-ACX converges to
+    all eigenvalues of LAPACK's eigvalsh."""
+    M, th = w.dense_symmetric(256, 0.03, seed=7, theta_step=0.125)
+    plain = oracle.ipt_solve(M, th, tol=1e-9, max_iter=150, stop="residual")
+    assert plain["status"] == oracle.MAXITER
+    r = oracle.ipt_solve_acx(M, th, tol=1e-9, max_iter=300, stop="residual", sigma=sigma)
+    assert r["status"] == oracle.OK
+    np.testing.assert_allclose(np.sort(r["lam"]), np.linalg.eigvalsh(M), atol=1e-9)
