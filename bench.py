@@ -60,6 +60,8 @@ def parse_args():
                     help="columns of the oracle sample (0: sized for ~10 s)")
     ap.add_argument("--no-csr", action="store_true",
                     help="skip the sparse configuration's measurement")
+    ap.add_argument("--no-acx", action="store_true",
+                    help="skip the IPT-ACX configuration's measurement")
     return ap.parse_args()
 
 
@@ -289,6 +291,43 @@ def run_csr(steps, warmup, hbm_peak):
     }
 
 
+# ---------------------------------------------------------------- ACX configuration
+def run_acx(steps, warmup):
+    """IPT-ACX (Alg. 3) past the Picard iteration's domain: n = 4096, theta_i = i/4,
+    Delta symmetric N(0,1)*0.06 (seed 31), all 4096 eigenpairs to rho <= 1e-6 with
+    split-FP16 tensor-core products; the plain staged solve on the same matrix is
+    run beside it for its status (it diverges here)."""
+    import torch
+    from paper_2012_14702_gb300 import ipt, workloads
+    n, step, scale, seed = workloads.DENSE_CONFIGS["dense_n4096_edge_sd6e-2"]
+    M, th = workloads.dense_symmetric(n, scale, seed, theta_step=step)
+    Mg = torch.as_tensor(M, dtype=torch.float32, device="cuda")
+    tg = torch.as_tensor(th, dtype=torch.float64, device="cuda")
+    del M
+    solver = ipt.Solver()
+    out = {"workload": f"dense symmetric n={n}, theta_i=i/4, Delta N(0,1)*{scale}, seed {seed}, "
+                       f"k=n, tol 1e-6 residual"}
+    for sig in ["column", "global"]:
+        for _ in range(warmup):
+            solver.solve_dense(Mg, theta=tg, tol=TOL, max_iter=400, accel="acx", acx_sigma=sig)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(solver.stream)
+        for _ in range(steps):
+            _, _, info = solver.solve_dense(Mg, theta=tg, tol=TOL, max_iter=400, accel="acx",
+                                            acx_sigma=sig)
+        e1.record(solver.stream)
+        torch.cuda.synchronize()
+        _, _, v = solver.solve_dense(Mg, theta=tg, tol=TOL, max_iter=400, accel="acx",
+                                     acx_sigma=sig, verify_fp64=True)
+        out[f"acx_{sig}_sigma"] = {"ms_to_tol": e0.elapsed_time(e1) / steps,
+                                   "status": info["status"], "evaluations": info["iterations"],
+                                   "rho": info["rho"], "rho_fp64": v["rho_fp64"]}
+    _, _, plain = solver.solve_dense(Mg, theta=tg, tol=TOL, max_iter=400)
+    out["plain_staged"] = {"status": plain["status"], "evaluations": plain["iterations"]}
+    return out
+
+
 # ---------------------------------------------------------------- reference arm
 def run_reference(args, rank):
     if rank != 0:
@@ -464,6 +503,8 @@ def run_ours(args, rank, world, local_rank):
         hbm = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("hbm_gbs", 6800.0) \
             if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6800.0
         line["csr"] = run_csr(max(3, min(args.steps, 10)), 2, hbm)
+    if not args.no_acx:
+        line["acx"] = run_acx(max(3, min(args.steps, 10)), 2)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(M, th, args.cpu_sample_cols)
     if rank == 0:

@@ -100,11 +100,22 @@ typedef struct {
                            IPT_PRODUCT_PAIR (two CTAs per 256 x 256 tile, one paired MMA;
                            needs an even number of 128-row blocks, else SINGLE is used).
                            Results are identical; only speed differs                     */
+  int accel;            /* ipt_solve_dense: IPT_ACCEL_NONE (default, the Picard update of
+                           Alg. 1/2) or IPT_ACCEL_ACX (Alg. 3: each extrapolation evaluates
+                           F at z, f(z) [, f^2(z)] and moves z by the order-3 / order-2
+                           extrapolation, orders 3, 2, 3, 2, ...; the stopping test is made
+                           at the extrapolated points; `iterations` counts evaluations).
+                           With IPT_PREC_STAGED the products are FP16 x3 (BF16 x3 with
+                           staged_bf16)                                                    */
+  int acx_sigma;        /* ACX step length: 0 (default) one per column, 1 one for all     */
   int csr_window;       /* ipt_solve_csr: nonzero (default) = each product evaluates only the
                            rows that can be nonzero: the rows of the current iterate's
                            nonzero rows widened by the band max|j - m| of the stored
                            entries (exact: other rows of Z and F are zero).  0 = all rows */
 } ipt_options;
+
+/* Values of ipt_options.accel. */
+enum { IPT_ACCEL_NONE = 0, IPT_ACCEL_ACX = 1 };
 
 /* Values of ipt_options.product_kernel. */
 enum { IPT_PRODUCT_AUTO = 0, IPT_PRODUCT_SINGLE = 1, IPT_PRODUCT_PAIR = 2 };

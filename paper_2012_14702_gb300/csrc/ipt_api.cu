@@ -40,7 +40,8 @@ constexpr int kCsrChunk = 4;
 struct ipt_handle {
   cudaStream_t s = nullptr;
   int dev = 0;
-  Buf drow, dt, dh, dl, z[3], pbuf, wh, wl, rinv, sinv;
+  Buf drow, dt, dh, dl, z[4], pbuf, wh, wl, rinv, sinv;
+  Buf acx_d, acx_acc, acx_sigma;    // ACX: d of the inner evaluations, step-length sums, steps
   Buf theta, thh, thl, icol, count, d, st, r0part;
   Buf m64, z64, racc;
   Buf delta, cpart;                 // sparse path: delta_j = M_jj - theta_j, r0 partials
@@ -99,6 +100,7 @@ struct Plan {
   bool dt;      // column-major FP32 Delta (W-form epilogues)
   bool staged;  // third Z buffer and stored-P buffer (base re-use)
   int product_kernel = IPT_PRODUCT_AUTO;  // tensor-core product kernel variant
+  bool acx = false;  // four Z buffers (z, f, f^2, f^3) and the extrapolation scratch
 };
 
 ipt_status check_dense_args(ipt_handle* h, int64_t n, const void* M, int64_t ldm, int m_dtype,
@@ -120,6 +122,13 @@ ipt_status alloc_dense(ipt_handle* h, const Plan& p) {
   if (p.staged) {
     CK(ensure(h->z[2], kn * ez));
     CK(ensure(h->pbuf, kn * 4));
+  }
+  if (p.acx) {
+    CK(ensure(h->z[2], kn * ez));
+    CK(ensure(h->z[3], kn * ez));
+    CK(ensure(h->acx_d, (size_t)p.kpad * 2 * 8));
+    CK(ensure(h->acx_acc, (size_t)p.kpad * 2 * 8));
+    CK(ensure(h->acx_sigma, (size_t)p.kpad * 8));
   }
   if (p.dt) CK(ensure(h->dt, nn * 4));
   if (p.tc) {
@@ -162,6 +171,7 @@ ipt_status status_from_flags(int flags) {
 // (0 = product-free evaluation at Z = E), base and accuracy class.
 struct FirstEval {
   int stage, passes, rebase, accurate;
+  bool defer_e = true;  // the unit columns may be written only if returned
 };
 
 ipt_status setup_dense(ipt_handle* h, const Plan& p, const void* M, int64_t ldm, int m_dtype,
@@ -213,8 +223,8 @@ ipt_status setup_dense(ipt_handle* h, const Plan& p, const void* M, int64_t ldm,
   }
   const size_t kn = (size_t)p.kpad * p.npad;
   const size_t ez = p.f64 ? 8 : 4;
-  // Z buffers 1 and 2 receive F only at rows < n of columns < k: zero the rest once
-  for (int b = 1; b < (p.staged ? 3 : 2); ++b) {
+  // Z buffers 1.. receive F only at rows < n of columns < k: zero the rest once
+  for (int b = 1; b < (p.acx ? 4 : p.staged ? 3 : 2); ++b) {
     if (p.npad > p.n)
       CK(cudaMemset2DAsync((char*)h->z[b].p + (size_t)p.n * ez, (size_t)p.npad * ez, 0,
                            (size_t)(p.npad - p.n) * ez, (size_t)p.kpad, s));
@@ -229,7 +239,7 @@ ipt_status setup_dense(ipt_handle* h, const Plan& p, const void* M, int64_t ldm,
     launch_copy_z(z0, z0_dtype == IPT_DTYPE_F64, ldz0, p.n, p.k, h->z[0].p, p.npad, p.f64 ? 1 : 0,
                   s);
     h->launches += 1;
-  } else if (!z0 && fe.passes == 0) {
+  } else if (!z0 && fe.passes == 0 && fe.defer_e) {
     // the product-free first evaluation knows Z = E without reading it: the
     // unit columns are written only if the solve returns that iterate
     h->e_pending = true;
@@ -274,35 +284,40 @@ int free_buffer(int cur, int base) {
 // One evaluation at Z buffer `cur`: d, product of V = Z - Z_base (in `passes`
 // passes of arithmetic `stage`; 0 = product-free first evaluation at Z = E),
 // map.  `rebase` stores P as the new base product.
+// `out` >= 0 names the buffer receiving F (else the free one), `dv` the vector
+// receiving d (else the handle's), `ev` the four timing events (else the handle's).
 ipt_status evaluate(ipt_handle* h, const Plan& p, int cur, int base, int stage, int passes,
-                    int rebase, Timing* tm) {
+                    int rebase, Timing* tm, int out = -1, double* dv = nullptr,
+                    cudaEvent_t* ev = nullptr) {
   cudaStream_t s = h->s;
   DevState* st = dst(h);
-  const int nxt = free_buffer(cur, base);
+  const int nxt = out >= 0 ? out : free_buffer(cur, base);
+  double* dd = dv ? dv : (double*)h->d.p;
+  if (!ev) ev = h->ev;
   const bool t = tm && tm->on;
-  if (t) CK(cudaEventRecord(h->ev[0], s));
+  if (t) CK(cudaEventRecord(ev[0], s));
   if (p.f64) {
     launch_prepass(h->drow.p, h->z[cur].p, 1, p.npad, (const int32_t*)h->icol.p, p.kpad,
-                   (double*)h->d.p, st, s);
-    if (t) CK(cudaEventRecord(h->ev[1], s));
+                   dd, st, s);
+    if (t) CK(cudaEventRecord(ev[1], s));
     MapArgs<double> a{};
     a.Zin = (const double*)h->z[cur].p;
     a.Fout = (double*)h->z[nxt].p;
-    a.d = (const double*)h->d.p;
+    a.d = dd;
     a.icol = (const int32_t*)h->icol.p;
     a.theta = (const double*)h->theta.p;
     a.ld = p.npad;
     a.n = p.n;
     a.k = p.k;
     a.st = st;
-    if (t) CK(cudaEventRecord(h->ev[2], s));
+    if (t) CK(cudaEventRecord(ev[2], s));
     launch_gemm_simt_f64((const double*)h->drow.p, a, p.npad, p.kpad, s);
   } else {
     MapArgs<float> a{};
     a.Zin = (const float*)h->z[cur].p;
     a.Fout = (float*)h->z[nxt].p;
     a.DT = (const float*)h->dt.p;
-    a.d = (const double*)h->d.p;
+    a.d = dd;
     a.icol = (const int32_t*)h->icol.p;
     a.th_hi = (const float*)h->thh.p;
     a.th_lo = (const float*)h->thl.p;
@@ -312,48 +327,49 @@ ipt_status evaluate(ipt_handle* h, const Plan& p, int cur, int base, int stage, 
     a.st = st;
     if (passes == 0) {
       // Z = E: P = Delta E exactly, no product (counted with the pre-pass time)
-      launch_map_first(a, p.npad, p.kpad, (double*)h->d.p, (double*)h->r0part.p, s);
+      launch_map_first(a, p.npad, p.kpad, dd, (double*)h->r0part.p, s);
       if (t) {
-        CK(cudaEventRecord(h->ev[1], s));
-        CK(cudaEventRecord(h->ev[2], s));
+        CK(cudaEventRecord(ev[1], s));
+        CK(cudaEventRecord(ev[2], s));
       }
     } else if (stage == IPT_PREC_F32) {
       launch_prepass(h->drow.p, h->z[cur].p, 0, p.npad, (const int32_t*)h->icol.p, p.kpad,
-                     (double*)h->d.p, st, s);
-      if (t) CK(cudaEventRecord(h->ev[1], s));
-      if (t) CK(cudaEventRecord(h->ev[2], s));
+                     dd, st, s);
+      if (t) CK(cudaEventRecord(ev[1], s));
+      if (t) CK(cudaEventRecord(ev[2], s));
       launch_gemm_simt_f32((const float*)h->drow.p, a, p.npad, p.kpad, s);
     } else {
       const float* zb = base >= 0 ? (const float*)h->z[base].p : nullptr;
       launch_prepass_tc((const float*)h->drow.p, (const float*)h->z[cur].p, zb, p.npad,
-                        (const int32_t*)h->icol.p, p.kpad, p.bf16 ? 1 : 0, (double*)h->d.p,
+                        (const int32_t*)h->icol.p, p.kpad, p.bf16 ? 1 : 0, dd,
                         (uint16_t*)h->wh.p, (uint16_t*)h->wl.p, (float*)h->sinv.p, st, s);
-      if (t) CK(cudaEventRecord(h->ev[1], s));
+      if (t) CK(cudaEventRecord(ev[1], s));
       a.rinv = (const float*)h->rinv.p;
       a.sinv = (const float*)h->sinv.p;
       a.Pbase = base >= 0 ? (const float*)h->pbuf.p : (const float*)h->dt.p;
       a.pbase_by_icol = base >= 0 ? 0 : 1;
       a.Pout = rebase ? (float*)h->pbuf.p : nullptr;
-      if (t) CK(cudaEventRecord(h->ev[2], s));
+      if (t) CK(cudaEventRecord(ev[2], s));
       CK(launch_gemm_tc((const uint16_t*)h->dh.p, (const uint16_t*)h->dl.p,
                         (const uint16_t*)h->wh.p, (const uint16_t*)h->wl.p, a, p.npad, p.kpad,
                         passes, p.bf16 ? 1 : 0, p.product_kernel, s));
     }
   }
   CK(cudaGetLastError());
-  if (t) CK(cudaEventRecord(h->ev[3], s));
+  if (t) CK(cudaEventRecord(ev[3], s));
   h->launches += 2;
   return IPT_OK;
 }
 
 // After the stream is synchronised: add this evaluation's event times.
-void collect_timing(ipt_handle* h, int passes, Timing* tm) {
+void collect_timing(ipt_handle* h, int passes, Timing* tm, const cudaEvent_t* ev = nullptr) {
   if (!tm || !tm->on) return;
+  if (!ev) ev = h->ev;
   float a = 0.f, b = 0.f;
-  if (cudaEventElapsedTime(&a, h->ev[0], h->ev[1]) == cudaSuccess) tm->prepass_ms += a;
+  if (cudaEventElapsedTime(&a, ev[0], ev[1]) == cudaSuccess) tm->prepass_ms += a;
   if (passes == 0) return;
   const int slot = passes == 3 ? 1 : 0;
-  if (cudaEventElapsedTime(&b, h->ev[2], h->ev[3]) == cudaSuccess) tm->product_ms[slot] += b;
+  if (cudaEventElapsedTime(&b, ev[2], ev[3]) == cudaSuccess) tm->product_ms[slot] += b;
   tm->product_launches[slot] += 1;
 }
 
@@ -420,6 +436,66 @@ Plan make_plan(int64_t n, int64_t k, int prec, bool staged_bf16) {
   return p;
 }
 
+// IPT-ACX (Alg. 3 in place of the Picard update of Alg. 1/2).  Buffer 0
+// holds the extrapolated iterate z, buffers 1..3 hold f(z), f^2(z), f^3(z).
+// An extrapolation of order p evaluates F at z (with Alg. 3's stopping test;
+// d goes to the handle's d, so Lambda is z's) and at f(z) [, f^2(z)] (no
+// test), then moves z in place.  Orders 3, 2, 3, 2, ...  One host
+// synchronisation per extrapolation; every kernel returns at entry once the
+// controller has stopped.
+ipt_status acx_loop(ipt_handle* h, const Plan& p, const ControlArgs& ca, const FirstEval& fe,
+                    int max_iter, int sigma_global, Timing* tm) {
+  cudaStream_t s = h->s;
+  DevState* st = dst(h);
+  const int split = (fe.stage == IPT_PREC_BF16X3 || fe.stage == IPT_PREC_FP16X3) ? 3 : 1;
+  double* dinner = (double*)h->acx_d.p;
+  CK(cudaMemsetAsync(h->acx_acc.p, 0, (size_t)p.kpad * 2 * 8, s));
+  int done_evals = 0;
+  for (int step = 0; done_evals < max_iter; ++step) {
+    const int order = (step % 2 == 0) ? 3 : 2;
+    const int planned = std::min(order, max_iter - done_evals);
+    for (int q = 0; q < planned; ++q) {
+      const int passes = (done_evals + q == 0) ? fe.passes : (p.f64 ? 1 : split);
+      ControlArgs cq = ca;
+      cq.acx = 1;
+      cq.test = q == 0 ? 1 : 0;
+      ipt_status v = evaluate(h, p, q, -1, fe.stage, passes, 0, tm, q + 1,
+                              q == 0 ? nullptr : dinner + (size_t)(q - 1) * p.kpad,
+                              h->evb + 4 * q);
+      if (v != IPT_OK) return v;
+      launch_control(st, cq, s);
+      h->launches += 1;
+    }
+    if (planned == order) {
+      launch_acx_combine(h->z[0].p, h->z[1].p, h->z[2].p, h->z[order == 3 ? 3 : 2].p,
+                         p.f64 ? 1 : 0, order, p.n, p.k, p.npad, sigma_global,
+                         (double*)h->acx_acc.p, (double*)h->acx_sigma.p, st, s);
+      h->launches += 3;
+    }
+    if (cudaGetLastError() != cudaSuccess ||
+        cudaMemcpyAsync(h->hst, st, kStateHead, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      return IPT_CUDA_ERROR;
+    if (step == 0) {
+      const ipt_status v = status_from_flags(h->hst->flags);
+      if (v != IPT_OK) return v;
+      if (tm && tm->on) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, h->ev[4], h->ev[5]) == cudaSuccess) tm->setup_ms = ms;
+      }
+    }
+    const int ran = std::min(planned, h->hst->iter - done_evals);
+    for (int q = 0; q < ran; ++q) {
+      const int passes = (done_evals + q == 0) ? fe.passes : (p.f64 ? 1 : split);
+      collect_timing(h, passes, tm, h->evb + 4 * q);
+    }
+    done_evals = h->hst->iter;
+    if (h->hst->timeout) return IPT_DEVICE_TIMEOUT;
+    if (h->hst->done) break;
+  }
+  return IPT_OK;
+}
+
 ipt_status solve_dense(ipt_handle* h, int64_t n, const void* M, int64_t ldm, int m_dtype,
                        const double* theta, int64_t k, const int32_t* cols, double tol,
                        int max_iter, const ipt_options* opt_in, double* lambda, void* Z,
@@ -434,7 +510,9 @@ ipt_status solve_dense(ipt_handle* h, int64_t n, const void* M, int64_t ldm, int
   if (v == IPT_OK && (!lambda || !Z || !(tol >= 0.0) || max_iter < 1 ||
                       (opt.stop != IPT_STOP_INCREMENT && opt.stop != IPT_STOP_RESIDUAL) ||
                       opt.product_kernel < IPT_PRODUCT_AUTO ||
-                      opt.product_kernel > IPT_PRODUCT_PAIR))
+                      opt.product_kernel > IPT_PRODUCT_PAIR ||
+                      (opt.accel != IPT_ACCEL_NONE && opt.accel != IPT_ACCEL_ACX) ||
+                      (opt.acx_sigma != 0 && opt.acx_sigma != 1)))
     v = IPT_INVALID_ARG;
   if (v != IPT_OK) {
     out->status = v;
@@ -449,20 +527,28 @@ ipt_status solve_dense(ipt_handle* h, int64_t n, const void* M, int64_t ldm, int
     out->status = IPT_CUDA_ERROR;
     return IPT_CUDA_ERROR;
   }
-  Plan p = make_plan(n, k, opt.precision, opt.staged_bf16 != 0);
+  const bool acx = opt.accel == IPT_ACCEL_ACX;
+  // ACX moves the iterate by extrapolation, outside the staged schedule's
+  // error model: a staged request runs every product as the split stage
+  const int prec = (acx && opt.precision == IPT_PREC_STAGED)
+                       ? (opt.staged_bf16 ? IPT_PREC_BF16X3 : IPT_PREC_FP16X3)
+                       : opt.precision;
+  Plan p = make_plan(n, k, prec, opt.staged_bf16 != 0);
   p.product_kernel = opt.product_kernel;
+  p.acx = acx;
   const int low = p.bf16 ? IPT_PREC_BF16 : IPT_PREC_FP16;
   const int high = p.bf16 ? IPT_PREC_BF16X3 : IPT_PREC_FP16X3;
   // First evaluation: product-free at Z = E (FP32 / tensor-core paths), else
   // a product; a staged solve from a warm start begins with a split product
   // and re-bases on it.
   FirstEval fe;
-  fe.stage = opt.precision == IPT_PREC_STAGED ? (opt.z0 ? high : low) : opt.precision;
+  fe.stage = prec == IPT_PREC_STAGED ? (opt.z0 ? high : low) : prec;
   fe.passes = (!p.f64 && !opt.z0)
                   ? 0
                   : ((fe.stage == IPT_PREC_BF16X3 || fe.stage == IPT_PREC_FP16X3) ? 3 : 1);
   fe.rebase = (p.staged && opt.z0) ? 1 : 0;
   fe.accurate = 1;
+  fe.defer_e = !acx;  // the extrapolation reads z = E from buffer 0
   v = alloc_dense(h, p);
   if (v == IPT_OK) {
     if (tm.on) cudaEventRecord(h->ev[4], h->s);
@@ -479,13 +565,17 @@ ipt_status solve_dense(ipt_handle* h, int64_t n, const void* M, int64_t ldm, int
   ca.stage_switch = opt.stage_switch;
   ca.max_iter = max_iter;
   ca.stop = opt.stop;
-  ca.mode = opt.precision;
+  ca.mode = prec;
   ca.k = (int)k;
   ca.low_stage = low;
   ca.high_stage = high;
   ca.low_unit = p.bf16 ? 1.0 / 128.0 : 1.0 / 1024.0;  // 2^-7 (BF16), 2^-10 (FP16)
   cudaStream_t s = h->s;
   int cur = 0, base = -1, stage = fe.stage, passes = fe.passes, rebase = fe.rebase;
+  if (acx) {
+    v = acx_loop(h, p, ca, fe, max_iter, opt.acx_sigma, &tm);
+    max_iter = 0;  // the Picard loop below does not run
+  }
   for (int it = 0; it < max_iter; ++it) {
     v = evaluate(h, p, cur, base, stage, passes, rebase, &tm);
     if (v != IPT_OK) break;
@@ -616,7 +706,8 @@ ipt_status ipt_create(ipt_handle** h, void* stream) {
 ipt_status ipt_destroy(ipt_handle* h) {
   if (!h) return IPT_OK;
   DeviceGuard g(h->dev);
-  Buf* all[] = {&h->drow, &h->dt, &h->dh, &h->dl, &h->z[0], &h->z[1], &h->z[2], &h->pbuf,
+  Buf* all[] = {&h->drow, &h->dt, &h->dh, &h->dl, &h->z[0], &h->z[1], &h->z[2], &h->z[3],
+                &h->acx_d, &h->acx_acc, &h->acx_sigma, &h->pbuf,
                 &h->wh, &h->wl,
                 &h->rinv, &h->sinv, &h->theta, &h->thh, &h->thl, &h->icol, &h->count,
                 &h->r0part, &h->delta, &h->cpart,

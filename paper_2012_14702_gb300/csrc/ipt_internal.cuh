@@ -138,7 +138,16 @@ struct ControlArgs {
   double low_unit;            // STAGED: relative error model of a 1-pass product
   int csr_n = 0;              // CSR solves: n (the window is clipped to [0, n)); 0 = dense
   int csr_window = 0;         // CSR: nonzero = evaluate only rows that can be nonzero
+  int acx = 0;                // ACX: the iterate stays in buffer 0 (no ping-pong)
+  int test = 1;               // 0: no stopping test at this evaluation (ACX inner ones)
 };
+
+// Alg. 3 extrapolation of order p (2 or 3) in place: z (buffer of the
+// extrapolated iterate) from f1 = f(z), f2, f3 (column-major, leading dim ld).
+// acc: 2 * k FP64 scratch (zero on entry, left zero); sigma: k FP64.
+void launch_acx_combine(void* z, const void* f1, const void* f2, const void* f3, int f64, int p,
+                        int n, int k, int64_t ld, int global, double* acc, double* sigma,
+                        DevState* st, cudaStream_t s);
 void launch_control(DevState* st, ControlArgs a, cudaStream_t s);
 
 // tensor-core product (k_tc_gemm.cu).  passes = 1 (Dh Wh) or 3 (+ Dh Wl + Dl Wh);

@@ -1,0 +1,155 @@
+// Alternating Cyclic Extrapolation (Alg. 3, Section 5) on the device: after
+// an extrapolation's evaluations z -> f(z) -> f^2(z) [-> f^3(z)] the iterate
+// moves to
+//   p = 2:  z + 2 s D1 + s^2 D2
+//   p = 3:  z + 3 s D1 + 3 s^2 D2 + s^3 D3
+// with the differences D1 = f - z, D2 = f^2 - 2 f + z,
+// D3 = f^3 - 3 f^2 + 3 f - z and the step s = |<Dp, D(p-1)>| / ||Dp||^2 of
+// each column (or one s for the whole block); a column with Dp = 0 takes
+// s = 1, which makes the update the plain iterate f^p(z).
+//
+// Iterates are column-major (element (j, c) at c * ld + j).  The differences,
+// inner products and the update are formed in FP64 from the stored iterates
+// (FP32 inputs are exact in FP64, so no cancellation is lost); the result is
+// rounded once to the iterate's type.  Every kernel returns at entry once the
+// controller has stopped the solve.
+#include "ipt_internal.cuh"
+
+namespace ipt {
+
+namespace {
+
+constexpr int ROWS_PER_THREAD = 4;
+
+template <typename T>
+__device__ __forceinline__ void differences(const T* z, const T* f1, const T* f2, const T* f3,
+                                            int64_t o, int p, double& d1, double& d2,
+                                            double& d3) {
+  const double x = (double)z[o], a = (double)f1[o], b = (double)f2[o];
+  d1 = a - x;
+  d2 = b - 2.0 * a + x;
+  d3 = p == 3 ? ((double)f3[o] - 3.0 * b + 3.0 * a - x) : 0.0;
+}
+
+// Per column: <Dp, D(p-1)> and ||Dp||^2 over rows, FP64 block partials added
+// into acc[2c], acc[2c + 1].  Grid (column, row block).
+template <typename T>
+__global__ void __launch_bounds__(256)
+    k_acx_dots(const T* __restrict__ z, const T* __restrict__ f1, const T* __restrict__ f2,
+               const T* __restrict__ f3, int p, int n, int64_t ld, double* __restrict__ acc,
+               const DevState* st) {
+  if (st->done) return;
+  const int c = blockIdx.x;
+  const int64_t col = (int64_t)c * ld;
+  double num = 0.0, den = 0.0;
+#pragma unroll
+  for (int q = 0; q < ROWS_PER_THREAD; ++q) {
+    const int j = (blockIdx.y * ROWS_PER_THREAD + q) * blockDim.x + threadIdx.x;
+    if (j < n) {
+      double d1, d2, d3;
+      differences(z, f1, f2, f3, col + j, p, d1, d2, d3);
+      const double dp = p == 3 ? d3 : d2, dq = p == 3 ? d2 : d1;
+      num += dp * dq;
+      den += dp * dp;
+    }
+  }
+  __shared__ double rn[8], rd[8];
+  num = warp_sum(num);
+  den = warp_sum(den);
+  if ((threadIdx.x & 31) == 0) {
+    rn[threadIdx.x >> 5] = num;
+    rd[threadIdx.x >> 5] = den;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      a += rn[w];
+      b += rd[w];
+    }
+    atomicAdd(&acc[2 * c], a);
+    atomicAdd(&acc[2 * c + 1], b);
+  }
+}
+
+// One block: the step of every column (or the global step) into sigma[c];
+// clears acc for the next extrapolation.
+__global__ void __launch_bounds__(1024)
+    k_acx_sigma(double* __restrict__ acc, int k, int global, double* __restrict__ sigma,
+                const DevState* st) {
+  if (st->done) return;
+  __shared__ double rn[1024], rd[1024];
+  if (global) {
+    double a = 0.0, b = 0.0;
+    for (int c = threadIdx.x; c < k; c += blockDim.x) {
+      a += acc[2 * c];
+      b += acc[2 * c + 1];
+    }
+    rn[threadIdx.x] = a;
+    rd[threadIdx.x] = b;
+    __syncthreads();
+    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+      if ((int)threadIdx.x < h) {
+        rn[threadIdx.x] += rn[threadIdx.x + h];
+        rd[threadIdx.x] += rd[threadIdx.x + h];
+      }
+      __syncthreads();
+    }
+    const double s = rd[0] > 0.0 ? fabs(rn[0]) / rd[0] : 1.0;
+    for (int c = threadIdx.x; c < k; c += blockDim.x) sigma[c] = s;
+  } else {
+    for (int c = threadIdx.x; c < k; c += blockDim.x) {
+      const double a = acc[2 * c], b = acc[2 * c + 1];
+      sigma[c] = b > 0.0 ? fabs(a) / b : 1.0;
+    }
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < k; c += blockDim.x) acc[2 * c] = acc[2 * c + 1] = 0.0;
+}
+
+// z <- the order-p extrapolation, in place.  Grid (column, row block).
+template <typename T>
+__global__ void __launch_bounds__(256)
+    k_acx_update(T* __restrict__ z, const T* __restrict__ f1, const T* __restrict__ f2,
+                 const T* __restrict__ f3, int p, int n, int64_t ld,
+                 const double* __restrict__ sigma, const DevState* st) {
+  if (st->done) return;
+  const int c = blockIdx.x;
+  const int64_t col = (int64_t)c * ld;
+  const double s = sigma[c];
+#pragma unroll
+  for (int q = 0; q < ROWS_PER_THREAD; ++q) {
+    const int j = (blockIdx.y * ROWS_PER_THREAD + q) * blockDim.x + threadIdx.x;
+    if (j < n) {
+      double d1, d2, d3;
+      differences(z, f1, f2, f3, col + j, p, d1, d2, d3);
+      const double x = (double)z[col + j];
+      const double y = p == 3 ? x + 3.0 * s * d1 + 3.0 * s * s * d2 + s * s * s * d3
+                              : x + 2.0 * s * d1 + s * s * d2;
+      z[col + j] = (T)y;
+    }
+  }
+}
+
+}  // namespace
+
+void launch_acx_combine(void* z, const void* f1, const void* f2, const void* f3, int f64, int p,
+                        int n, int k, int64_t ld, int global, double* acc, double* sigma,
+                        DevState* st, cudaStream_t s) {
+  const dim3 g((unsigned)k, (unsigned)((n + 256 * ROWS_PER_THREAD - 1) / (256 * ROWS_PER_THREAD)));
+  if (f64) {
+    k_acx_dots<double><<<g, 256, 0, s>>>((const double*)z, (const double*)f1, (const double*)f2,
+                                         (const double*)f3, p, n, ld, acc, st);
+    k_acx_sigma<<<1, 1024, 0, s>>>(acc, k, global, sigma, st);
+    k_acx_update<double><<<g, 256, 0, s>>>((double*)z, (const double*)f1, (const double*)f2,
+                                           (const double*)f3, p, n, ld, sigma, st);
+  } else {
+    k_acx_dots<float><<<g, 256, 0, s>>>((const float*)z, (const float*)f1, (const float*)f2,
+                                        (const float*)f3, p, n, ld, acc, st);
+    k_acx_sigma<<<1, 1024, 0, s>>>(acc, k, global, sigma, st);
+    k_acx_update<float><<<g, 256, 0, s>>>((float*)z, (const float*)f1, (const float*)f2,
+                                          (const float*)f3, p, n, ld, sigma, st);
+  }
+}
+
+}  // namespace ipt

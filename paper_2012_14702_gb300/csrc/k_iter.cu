@@ -537,8 +537,10 @@ __global__ void k_control(DevState* st, ControlArgs a) {
   if (a.csr_n > 0) st->rows_eval += st->win_hi - st->win_lo;
   if (passes == 1 && (stage == IPT_PREC_BF16 || stage == IPT_PREC_FP16)) st->stage_iters[0]++;
   else if (passes != 0) st->stage_iters[1]++;
-  st->inc = inc;
-  st->rho = rho;
+  if (a.test) {  // the reported pair is the last tested iterate
+    st->inc = inc;
+    st->rho = rho;
+  }
   st->iter = it + 1;
   st->acc_inc2 = 0.0;
   st->acc_z2 = 0.0;
@@ -546,7 +548,7 @@ __global__ void k_control(DevState* st, ControlArgs a) {
   st->acc_pv2 = 0.0;
   const double test = a.stop == IPT_STOP_INCREMENT ? inc : rho;
   const bool staged = a.mode == IPT_PREC_STAGED;
-  const bool can_stop = !staged || st->accurate;
+  const bool can_stop = (!staged || st->accurate) && a.test;
   if (!isfinite(inc) || !isfinite(rho) || sqrt(z2) > a.diverge_bound * sqrt((double)a.k)) {
     st->status = IPT_DIVERGED;
     st->done = 1;
@@ -604,7 +606,7 @@ __global__ void k_control(DevState* st, ControlArgs a) {
       st->nz_lo = a.csr_n;
       st->nz_hi = -1;
     }
-    st->cur = out;
+    if (!a.acx) st->cur = out;
   }
   st->prev_rho = rho;
 }

@@ -37,7 +37,7 @@ class Options(C.Structure):
     _fields_ = [("precision", C.c_int), ("stop", C.c_int), ("diverge_bound", C.c_double),
                 ("stage_switch", C.c_double), ("staged_bf16", C.c_int), ("verify_fp64", C.c_int),
                 ("record_timing", C.c_int), ("z0", C.c_void_p), ("product_kernel", C.c_int),
-                ("csr_window", C.c_int)]
+                ("accel", C.c_int), ("acx_sigma", C.c_int), ("csr_window", C.c_int)]
 
 
 class Result(C.Structure):
@@ -158,11 +158,14 @@ class Solver:
     def solve_dense(self, M, theta=None, cols=None, tol=1e-6, max_iter=100, precision="staged",
                     stop="residual", z_dtype=torch.float32, verify_fp64=False, z0=None,
                     diverge_bound=1e8, stage_switch=0.1, staged_bf16=False,
-                    record_timing=False, product_kernel="auto"):
+                    record_timing=False, product_kernel="auto", accel=None,
+                    acx_sigma="column"):
         """Alg. 2 / Alg. 1 on the GPU.  Returns (lam [k] f64, Z (n, k) view, info dict).
 
         product_kernel: "auto", "single" (one CTA per tile) or "pair" (two CTAs
-        per 256-row tile); selects the tensor-core product kernel only."""
+        per 256-row tile); selects the tensor-core product kernel only.
+        accel: None (Picard update) or "acx" (Alg. 3), with acx_sigma "column"
+        (one step length per column) or "global"."""
         M = _dev(M, name="M")
         n = M.shape[0]
         if M.dim() != 2 or M.shape[1] != n or M.dtype not in DTYPE:
@@ -179,6 +182,10 @@ class Solver:
             z0t = None
         o = make_options(precision, stop, diverge_bound, stage_switch, verify_fp64, z0t,
                          staged_bf16, record_timing, product_kernel)
+        if accel not in (None, "none", "acx") or acx_sigma not in ("column", "global"):
+            raise ValueError("accel must be None or 'acx'; acx_sigma 'column' or 'global'")
+        o.accel = 1 if accel == "acx" else 0
+        o.acx_sigma = 1 if acx_sigma == "global" else 0
         r = Result()
         _lib.ipt_solve_dense(self._h, n, _ptr(M), M.stride(0), DTYPE[M.dtype], _ptr(theta), k,
                              _ptr(cols), float(tol), int(max_iter), C.byref(o), _ptr(lam),

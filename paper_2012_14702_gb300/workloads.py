@@ -163,6 +163,8 @@ DENSE_CONFIGS = {
     "dense_n8192_eps1e-4": (8192, 0.125, 1e-4, 21),
     "dense_n8192_eps1e-3": (8192, 0.125, 1e-3, 22),
     "dense_n8192_eps3e-3": (8192, 0.125, 3e-3, 23),
+    # beyond the Picard iteration's domain (it diverges), inside IPT-ACX's
+    "dense_n4096_edge_sd6e-2": (4096, 0.25, 6e-2, 31),
 }
 
 # The sparse workloads by name: (n, per_row, band, scale, seed, k lowest).

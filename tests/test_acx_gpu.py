@@ -1,0 +1,111 @@
+"""GPU parity of IPT-ACX (Alg. 3 in place of the Picard update) against the oracle.
+
+FP64: the same evaluations and extrapolations as the oracle's ipt_solve_acx,
+compared iterate by iterate (1e-11 of the largest entry of Z - E).  FP32 and
+tensor-core precisions: converged results against the oracle's converged
+result (eigenvalues 1e-6 relative, eigenvectors 1e-4 of ||Z - E||) on a
+matrix outside the Picard iteration's domain.
+"""
+
+import ctypes as C
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2012_14702_gb300 import workloads as w
+
+pytestmark = pytest.mark.gpu
+
+
+def cuda(x, dtype=torch.float64):
+    return torch.as_tensor(np.ascontiguousarray(x), dtype=dtype, device="cuda")
+
+
+@pytest.mark.parametrize("sigma", ["column", "global"])
+@pytest.mark.parametrize("n,k", [(200, 200), (300, 23)])
+def test_acx_f64_iterates_match_oracle(ipt, sigma, n, k):
+    """Stops at every position of the 3, 2, 3 extrapolation cycle: at the tested
+    point, after one or two inner evaluations (MAXITER returns the tested z)."""
+    M, th = w.dense_symmetric(n, 0.03, seed=11, theta_step=0.125)
+    cols = (np.arange(n) if k == n else w.rng(12).permutation(n)[:k]).astype(np.int32)
+    Mg, tg, cg = cuda(M), cuda(th), cuda(cols, torch.int32)
+    E = oracle.unit_columns(n, cols)
+    for m in [1, 2, 3, 4, 5, 6, 8, 9]:
+        ref = oracle.ipt_solve_acx(M, th, cols=cols, tol=0.0, max_iter=m, stop="increment",
+                                   sigma=sigma, history=True)
+        lam, Z, info = ipt.Solver().solve_dense(Mg, theta=tg, cols=cg, tol=0.0, max_iter=m,
+                                                precision="f64", stop="increment",
+                                                accel="acx", acx_sigma=sigma,
+                                                z_dtype=torch.float64)
+        assert info["status"] == "MAXITER" and info["iterations"] == m, (m, info)
+        Zg = Z.cpu().numpy()
+        scale = max(np.max(np.abs(ref["Z"] - E)), 1e-3)
+        assert np.max(np.abs(Zg - ref["Z"])) <= 1e-11 * scale, m
+        np.testing.assert_allclose(lam.cpu().numpy(), ref["lam"], rtol=1e-12)
+        np.testing.assert_allclose(info["hist_increment"], ref["inc_hist"], rtol=1e-9)
+        np.testing.assert_allclose(info["increment"], ref["increment"], rtol=1e-9)
+
+
+@pytest.mark.parametrize("precision", ["f32", "fp16x3", "bf16x3", "staged", "f64"])
+def test_acx_converges_outside_picard_domain(ipt, precision):
+    """n = 512, theta_i = i/8, Delta N(0,1)*0.03: the Picard iteration does not
+    converge (150 evaluations), IPT-ACX reaches rho <= 1e-6 and matches the
+    oracle's converged IPT-ACX result."""
+    n = 512
+    M, th = w.dense_symmetric(n, 0.03, seed=7, theta_step=0.125)
+    Mg, tg = cuda(M, torch.float32 if precision != "f64" else torch.float64), cuda(th)
+    s = ipt.Solver()
+    _, _, plain = s.solve_dense(Mg, theta=tg, tol=1e-6, max_iter=150, precision="f32")
+    assert plain["status"] in ("MAXITER", "DIVERGED"), plain["status"]
+    lam, Z, info = s.solve_dense(Mg, theta=tg, tol=1e-6, max_iter=400, precision=precision,
+                                 accel="acx", verify_fp64=True)
+    assert info["status"] == "OK", info
+    # the FP64 residual exceeds the product-arithmetic one by the product error:
+    # ~2^-22 of ||Delta|| ||Z - E|| for split FP16, ~2^-16 for split BF16, whose
+    # share at ||Z - E|| ~ 0.3 is about 1.5e-6 of ||R0|| (the test's BF16 margin)
+    assert info["rho_fp64"] <= (4e-6 if precision == "bf16x3" else 2e-6), info["rho_fp64"]
+    ref = oracle.ipt_solve_acx(M, th, tol=1e-12, max_iter=600, stop="residual")
+    assert ref["status"] == oracle.OK
+    np.testing.assert_allclose(lam.cpu().numpy(), ref["lam"], rtol=1e-6, atol=1e-6)
+    E = oracle.unit_columns(n, np.arange(n))
+    err = np.linalg.norm(Z.double().cpu().numpy() - ref["Z"]) / np.linalg.norm(ref["Z"] - E)
+    assert err <= 1e-4, err
+
+
+def test_acx_morgan_lowest_eigenpair_beyond_picard(ipt):
+    """Section 5: the tridiagonal Morgan matrix at eps = 1 (dense storage), k = 1:
+    Picard diverges, IPT-ACX converges to LAPACK's lowest eigenpair."""
+    n, eps = 600, 1.0
+    M, th = w.morgan_tridiagonal(n, eps)
+    Mg, tg, cg = cuda(M), cuda(th), cuda([0], torch.int32)
+    s = ipt.Solver()
+    _, _, plain = s.solve_dense(Mg, theta=tg, cols=cg, tol=1e-10, max_iter=300,
+                                precision="f64", stop="increment")
+    assert plain["status"] in ("MAXITER", "DIVERGED")
+    lam, Z, info = s.solve_dense(Mg, theta=tg, cols=cg, tol=1e-12, max_iter=300,
+                                 precision="f64", stop="increment", accel="acx",
+                                 z_dtype=torch.float64)
+    assert info["status"] == "OK", info
+    ev, V = np.linalg.eigh(M)
+    assert abs(lam.item() - ev[0]) < 1e-9
+    np.testing.assert_allclose(Z.cpu().numpy()[:, 0], V[:, 0] / V[0, 0], atol=1e-8)
+    ref = oracle.ipt_solve_acx(M, th, cols=[0], tol=1e-12, max_iter=300)
+    assert abs(info["iterations"] - ref["iterations"]) <= 2
+
+
+def test_acx_option_errors(ipt):
+    M, th = w.dense_symmetric(64, 1e-3, seed=1)
+    Mg = cuda(M, torch.float32)
+    s = ipt.Solver()
+    with pytest.raises(ValueError):
+        s.solve_dense(Mg, accel="anderson")
+    o = ipt.make_options("f32", "residual")
+    o.accel = 7
+    r = ipt.Result()
+    lam = torch.empty(64, dtype=torch.float64, device="cuda")
+    Zt = torch.empty((64, 64), dtype=torch.float32, device="cuda")
+    st = ipt._lib.ipt_solve_dense(s._h, 64, Mg.data_ptr(), 64, 1, None, 64, None, 1e-6, 10,
+                                  C.byref(o), lam.data_ptr(), Zt.data_ptr(), 64, 1, C.byref(r))
+    assert r.to_dict()["status"] == "INVALID_ARG" and st == r.status
