@@ -231,6 +231,35 @@ ipt_status ipt_solve_csr(ipt_handle* h, int64_t n, int64_t nnz, const int32_t* r
                          int64_t ldz, int z_dtype, ipt_result* out);
 
 /*
+ * Many independent dense problems, each solved by Alg. 2 (all n_p eigenpairs,
+ * theta = the given partition or diag(M_p)) with its own stopping test, in
+ * one persistent launch: the GPU takes the problems largest first and runs
+ * every evaluation of a problem without host involvement.  FP32 product and
+ * iterate with the exact Delta E term (as IPT_PREC_F32).
+ *   count          number of problems (>= 1)
+ *   n              HOST array of count problem orders, 1 <= n_p <= 1024
+ *   M              device, FP32, the problems packed back to back: problem p is
+ *                  row-major n_p x n_p at element offset sum_{q<p} n_q^2
+ *   theta          device FP64, packed at offset sum_{q<p} n_q, or NULL = diag(M_p)
+ *   tol, max_iter  as in ipt_solve_dense (max_iter per problem)
+ *   opt            stop and diverge_bound are used (NULL = defaults)
+ *   lambda         device FP64, packed like theta (written)
+ *   Z              device FP32, packed like M, each block column-major (column c =
+ *                  eigenvector continued from e_c) (written)
+ *   status, iters  device int32[count] (written): each problem's ipt_status and
+ *                  evaluations of F
+ *   out            host: status IPT_OK when every problem converged, else the
+ *                  status of the first problem (by index) that did not;
+ *                  iterations = the largest evaluation count; product_ms[0] =
+ *                  the kernel's device time with record_timing
+ * Returns out->status (argument errors before any launch: IPT_INVALID_ARG).
+ */
+ipt_status ipt_solve_batched(ipt_handle* h, int64_t count, const int64_t* n, const float* M,
+                             const double* theta, double tol, int max_iter,
+                             const ipt_options* opt, double* lambda, float* Z, int32_t* status,
+                             int32_t* iters, ipt_result* out);
+
+/*
  * ||M Z - Z Lambda||_F in FP64, allocating no device memory.  The paper has
  * no counterpart: this is a library service for callers that cannot call
  * cudaMalloc -- work recorded by CUDA stream capture, processes whose device

@@ -42,6 +42,11 @@ struct ipt_handle {
   int dev = 0;
   Buf drow, dt, dh, dl, z[4], pbuf, wh, wl, rinv, sinv;
   Buf acx_d, acx_acc, acx_sigma;    // ACX: d of the inner evaluations, step-length sums, steps
+  Buf bmeta, bscratch;              // batched: schedule and offsets, per-CTA iterate pairs
+  void* hmeta = nullptr;            // pinned staging of the batched schedule
+  size_t hmeta_cap = 0;
+  int* hstat = nullptr;             // pinned copy of per-problem statuses and counts
+  size_t hstat_cap = 0;
   Buf theta, thh, thl, icol, count, d, st, r0part;
   Buf m64, z64, racc;
   Buf delta, cpart;                 // sparse path: delta_j = M_jj - theta_j, r0 partials
@@ -707,7 +712,7 @@ ipt_status ipt_destroy(ipt_handle* h) {
   if (!h) return IPT_OK;
   DeviceGuard g(h->dev);
   Buf* all[] = {&h->drow, &h->dt, &h->dh, &h->dl, &h->z[0], &h->z[1], &h->z[2], &h->z[3],
-                &h->acx_d, &h->acx_acc, &h->acx_sigma, &h->pbuf,
+                &h->acx_d, &h->acx_acc, &h->acx_sigma, &h->bmeta, &h->bscratch, &h->pbuf,
                 &h->wh, &h->wl,
                 &h->rinv, &h->sinv, &h->theta, &h->thh, &h->thl, &h->icol, &h->count,
                 &h->r0part, &h->delta, &h->cpart,
@@ -721,6 +726,8 @@ ipt_status ipt_destroy(ipt_handle* h) {
     if (h->evb[i]) cudaEventDestroy(h->evb[i]);
   if (h->hst) cudaFreeHost(h->hst);
   if (h->hinit) cudaFreeHost(h->hinit);
+  if (h->hmeta) cudaFreeHost(h->hmeta);
+  if (h->hstat) cudaFreeHost(h->hstat);
   delete h;
   return IPT_OK;
 }
@@ -1017,6 +1024,112 @@ ipt_status ipt_solve_csr(ipt_handle* h, int64_t n, int64_t nnz, const int32_t* r
   out->wall_ms =
       std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
   return (ipt_status)out->status;
+}
+
+ipt_status ipt_solve_batched(ipt_handle* h, int64_t count, const int64_t* n, const float* M,
+                             const double* theta, double tol, int max_iter,
+                             const ipt_options* opt_in, double* lambda, float* Z, int32_t* status,
+                             int32_t* iters, ipt_result* out) {
+  if (!out) return IPT_INVALID_ARG;
+  memset(out, 0, sizeof(*out));
+  out->rho_fp64 = -1.0;
+  ipt_options opt;
+  ipt_options_default(&opt);
+  if (opt_in) opt = *opt_in;
+  ipt_status v = IPT_OK;
+  if (!h || count < 1 || count > (1 << 30) || !n || !M || !lambda || !Z || !status || !iters ||
+      !(tol >= 0.0) || max_iter < 1 ||
+      (opt.stop != IPT_STOP_INCREMENT && opt.stop != IPT_STOP_RESIDUAL))
+    v = IPT_INVALID_ARG;
+  int64_t max_n = 0;
+  for (int64_t p = 0; v == IPT_OK && p < count; ++p) {
+    if (n[p] < 1 || n[p] > kBatchMaxN) v = IPT_INVALID_ARG;
+    max_n = std::max(max_n, n[p]);
+  }
+  if (v != IPT_OK) {
+    out->status = v;
+    return v;
+  }
+  DeviceGuard g(h->dev);
+  const auto t_start = std::chrono::steady_clock::now();
+  cudaStream_t s = h->s;
+  // schedule: offsets in input order, problems largest first
+  const size_t cnt = (size_t)count;
+  const size_t meta_bytes = cnt * (8 + 8 + 4 + 4) + 16;
+  if (h->hmeta_cap < meta_bytes) {
+    if (h->hmeta) cudaFreeHost(h->hmeta);
+    h->hmeta = nullptr;
+    h->hmeta_cap = 0;
+    CK(cudaMallocHost(&h->hmeta, meta_bytes));
+    h->hmeta_cap = meta_bytes;
+  }
+  int64_t* m_off = static_cast<int64_t*>(h->hmeta);
+  int64_t* v_off = m_off + cnt;
+  int* nsz = reinterpret_cast<int*>(v_off + cnt);
+  int* order = nsz + cnt;
+  int64_t mo = 0, vo = 0;
+  for (size_t p = 0; p < cnt; ++p) {
+    m_off[p] = mo;
+    v_off[p] = vo;
+    nsz[p] = (int)n[p];
+    order[p] = (int)p;
+    mo += n[p] * n[p];
+    vo += n[p];
+  }
+  std::stable_sort(order, order + cnt, [&](int a, int b) { return nsz[a] > nsz[b]; });
+  int dev = 0, nsm = 0;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  const int ctas = (int)std::min<int64_t>(count, (int64_t)nsm * batched_ctas_per_sm());
+  const int64_t max_n2 = max_n * max_n;
+  CK(ensure(h->bmeta, meta_bytes + 16));
+  CK(ensure(h->bscratch, (size_t)ctas * 2 * (size_t)max_n2 * 4));
+  char* dm = static_cast<char*>(h->bmeta.p);
+  CK(cudaMemcpyAsync(dm, h->hmeta, cnt * (8 + 8 + 4 + 4), cudaMemcpyHostToDevice, s));
+  int* queue = reinterpret_cast<int*>(dm + cnt * (8 + 8 + 4 + 4));
+  CK(cudaMemsetAsync(queue, 0, sizeof(int), s));
+  Timing tm;
+  tm.on = opt.record_timing != 0;
+  if (tm.on && ensure_events(h) != IPT_OK) {
+    out->status = IPT_CUDA_ERROR;
+    return IPT_CUDA_ERROR;
+  }
+  if (tm.on) cudaEventRecord(h->ev[2], s);
+  CK(launch_batched(M, theta, reinterpret_cast<const int64_t*>(dm),
+                    reinterpret_cast<const int64_t*>(dm) + cnt,
+                    reinterpret_cast<const int*>(dm + cnt * 16),
+                    reinterpret_cast<const int*>(dm + cnt * 20), (int)count, max_n2, tol,
+                    max_iter, opt.stop, opt.diverge_bound, lambda, Z, status, iters,
+                    static_cast<float*>(h->bscratch.p), queue, ctas, s));
+  if (tm.on) cudaEventRecord(h->ev[3], s);
+  // per-problem outcomes for the aggregate result
+  const size_t stat_bytes = cnt * 2 * sizeof(int);
+  if (h->hstat_cap < stat_bytes) {
+    if (h->hstat) cudaFreeHost(h->hstat);
+    h->hstat = nullptr;
+    h->hstat_cap = 0;
+    CK(cudaMallocHost((void**)&h->hstat, stat_bytes));
+    h->hstat_cap = stat_bytes;
+  }
+  CK(cudaMemcpyAsync(h->hstat, status, cnt * sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(h->hstat + cnt, iters, cnt * sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  int agg = IPT_OK, most = 0;
+  for (size_t p = 0; p < cnt; ++p) {
+    if (agg == IPT_OK && h->hstat[p] != IPT_OK) agg = h->hstat[p];
+    most = std::max(most, h->hstat[cnt + p]);
+  }
+  out->status = agg;
+  out->iterations = most;
+  out->kernel_launches = 1;
+  out->product_launches[0] = 1;
+  if (tm.on) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, h->ev[2], h->ev[3]) == cudaSuccess) out->product_ms[0] = ms;
+  }
+  out->wall_ms =
+      std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+  return (ipt_status)agg;
 }
 
 }  // extern "C"

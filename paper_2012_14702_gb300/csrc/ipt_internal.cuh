@@ -142,6 +142,15 @@ struct ControlArgs {
   int test = 1;               // 0: no stopping test at this evaluation (ACX inner ones)
 };
 
+// Batched solve (k_batched.cu): largest problem order n.
+constexpr int kBatchMaxN = 1024;
+cudaError_t launch_batched(const float* M, const double* theta, const int64_t* m_off,
+                           const int64_t* v_off, const int* nsz, const int* order, int count,
+                           int64_t max_n2, double tol, int max_iter, int stop,
+                           double diverge_bound, double* lambda, float* Z, int* status,
+                           int* iters, float* scratch, int* queue, int ctas, cudaStream_t s);
+int batched_ctas_per_sm();
+
 // Alg. 3 extrapolation of order p (2 or 3) in place: z (buffer of the
 // extrapolated iterate) from f1 = f(z), f2, f3 (column-major, leading dim ld).
 // acc: 2 * k FP64 scratch (zero on entry, left zero); sigma: k FP64.

@@ -1,0 +1,301 @@
+// Many independent dense problems in one persistent launch: Alg. 2 (full
+// spectrum, k = n) for each problem, with its own stopping test, inside one
+// CTA.  CTAs take problems from a queue ordered largest first, iterate the
+// map of Eq. (dyn) on them to the end without any host round trip, write
+// Lambda, Z, a status and an evaluation count, and take the next problem.
+//
+// Per evaluation and problem (n <= kBatchMaxN):
+//   first evaluation, Z = E: no product; F_jc = -Delta_jc / (theta_j - theta_c)
+//     off the diagonal, d_c = Delta_cc, R = the off-diagonal part of Delta
+//     (its norm is ||R0||, so rho(E) = 1);
+//   later ones: P = Delta_{:,c} + Delta W (W = Z - E, FP32 SIMT product in
+//     64 x 64 tiles staged through shared memory, the next stage fetched into
+//     registers during the current one) with the map applied in the tile
+//     epilogue; each column block's diagonal tile goes first and yields
+//     d_c = P_cc for the block.
+// The iterate lives row-major in a per-CTA scratch pair (ping-pong); the
+// returned Z is transposed into the caller's column-major block.
+#include "ipt_internal.cuh"
+
+namespace ipt {
+
+namespace {
+
+constexpr int TB = 64;   // output tile (rows and columns)
+constexpr int TK = 32;   // product depth per shared-memory stage
+constexpr int NT = 256;  // threads per CTA (16 x 16, 4 x 4 outputs each)
+
+struct BatchArgs {
+  const float* M;         // packed row-major problems
+  const double* theta;    // packed partitions (null: diag(M))
+  const int64_t* m_off;   // element offset of problem p in M and Z
+  const int64_t* v_off;   // element offset of problem p in theta and lambda
+  const int* nsz;         // n of problem p
+  const int* order;       // schedule: problem indices, largest first
+  double* lambda;         // packed eigenvalues
+  float* Z;               // packed column-major eigenvector blocks
+  int* status;            // per problem: ipt_status
+  int* iters;             // per problem: evaluations of F
+  float* scratch;         // per CTA: 2 * max_n2 floats
+  int* queue;             // next schedule slot (zero at launch)
+  int64_t max_n2;
+  int count;
+  int max_iter, stop;
+  double tol, diverge_bound;
+};
+
+struct __align__(16) Shared {
+  float As[TB][TK + 1];  // Delta tile, [row][k]
+  float Bs[TK][TB + 4];  // W tile, [k][column]
+  float th_hi[kBatchMaxN], th_lo[kBatchMaxN];
+  float ddiag[kBatchMaxN];  // Delta_jj = M_jj - theta_j (formed in FP64 once per problem)
+  double d[kBatchMaxN];
+  double red[3][NT / 32];
+  int prob, flag;
+  double inc, rho;
+};
+
+// Sum over the CTA (every thread gets the total); `red` must not be in use.
+__device__ __forceinline__ double block_sum(double v, double* red) {
+  v = warp_sum(v);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double t = 0.0;
+  for (int w = 0; w < NT / 32; ++w) t += red[w];
+  return t;
+}
+
+__global__ void __launch_bounds__(NT, 3)
+    k_batched(BatchArgs a) {
+  __shared__ Shared sh;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  float* z0 = a.scratch + (int64_t)blockIdx.x * 2 * a.max_n2;
+  for (;;) {
+    if (tid == 0) {
+      const int slot = atomicAdd(a.queue, 1);
+      sh.prob = slot < a.count ? a.order[slot] : -1;
+    }
+    __syncthreads();
+    const int p = sh.prob;
+    __syncthreads();
+    if (p < 0) return;
+    const int n = a.nsz[p];
+    const float* M = a.M + a.m_off[p];
+    const int64_t vo = a.v_off[p];
+    // theta (given or diag(M)) as an exact FP32 pair; degenerate / non-finite check
+    int bad = 0;
+    for (int j = tid; j < n; j += NT) {
+      const double t = a.theta ? a.theta[vo + j] : (double)M[(int64_t)j * n + j];
+      if (!isfinite(t)) bad = 1;
+      const float h = (float)t;
+      sh.th_hi[j] = h;
+      sh.th_lo[j] = (float)(t - (double)h);
+      sh.ddiag[j] = (float)((double)M[(int64_t)j * n + j] - t);
+    }
+    if (tid == 0) sh.flag = 0;
+    __syncthreads();
+    if (bad) atomicOr(&sh.flag, 1);
+    float* zc = z0;
+    float* zn = z0 + a.max_n2;
+    double r0 = 0.0;
+    int status = IPT_MAXITER, it = 0;
+    // ---------------------------------------------------------- evaluations
+    for (it = 0; it < a.max_iter; ++it) {
+      // FP32 per-thread sums (FP64 arithmetic is a small fraction of the FP32
+      // rate here); the CTA reduction is FP64
+      float s_inc = 0.f, s_z = 0.f, s_r = 0.f;
+      if (it == 0) {
+        // Z = E: product-free
+        for (int j = ty; j < n; j += NT / 16)
+          for (int c = tx; c < n; c += 16) {
+            const float djc = M[(int64_t)j * n + c];
+            float f = 1.f, r = 0.f;
+            if (j != c) {
+              const float gap = gap2f(sh.th_hi[j], sh.th_lo[j], sh.th_hi[c], sh.th_lo[c]);
+              if (gap == 0.f) atomicOr(&sh.flag, 2);
+              f = -djc * recip_nr(gap);
+              r = djc;
+              s_inc = fmaf(f, f, s_inc);
+            } else {
+              sh.d[c] = (double)sh.ddiag[c];
+            }
+            s_r = fmaf(r, r, s_r);
+            zn[(int64_t)j * n + c] = f;
+          }
+        s_z = tid == 0 ? (float)n : 0.f;
+      } else {
+        // P = Delta_{:,c} + Delta W tile by tile, the map in the epilogue.  Each
+        // column block starts with its diagonal tile, whose P_cc give the d_c
+        // (d_c = (Delta Z)_cc, Eq. dyn) that every tile of the block needs.
+        const int nt = (n + TB - 1) / TB;
+        for (int cb = 0; cb < nt; ++cb)
+          for (int rb = 0; rb < nt; ++rb) {
+            const int c0t = cb * TB, r0t = ((cb + rb) % nt) * TB;
+            float acc[4][4] = {};
+            // the next stage's tiles are fetched into registers while the
+            // current one is multiplied (A: Delta rows r0t.., columns k0..,
+            // Delta_jj = M_jj - theta_j formed in FP64; B: W rows k0..,
+            // columns c0t.., W_cc = Z_cc - 1 = 0)
+            float pa[TB * TK / NT], pb[TB * TK / NT];
+            auto fetch = [&](int k0) {
+#pragma unroll
+              for (int r = 0; r < TB * TK / NT; ++r) {
+                const int e = tid + r * NT;
+                const int j = r0t + e / TK, m = k0 + e % TK;
+                float v = 0.f;
+                if (j < n && m < n) v = j != m ? M[(int64_t)j * n + m] : sh.ddiag[j];
+                pa[r] = v;
+                const int m2 = k0 + e / TB, c = c0t + e % TB;
+                pb[r] = (m2 < n && c < n && m2 != c) ? zc[(int64_t)m2 * n + c] : 0.f;
+              }
+            };
+            auto stage = [&]() {
+#pragma unroll
+              for (int r = 0; r < TB * TK / NT; ++r) {
+                const int e = tid + r * NT;
+                sh.As[e / TK][e % TK] = pa[r];
+                sh.Bs[e / TB][e % TB] = pb[r];
+              }
+            };
+            fetch(0);
+            stage();
+            __syncthreads();
+            for (int k0 = 0; k0 < n; k0 += TK) {
+              const bool more = k0 + TK < n;
+              if (more) fetch(k0 + TK);
+#pragma unroll 8
+              for (int kk = 0; kk < TK; ++kk) {
+                float av[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) av[i] = sh.As[ty * 4 + i][kk];
+                const float4 b4 = *reinterpret_cast<const float4*>(&sh.Bs[kk][tx * 4]);
+                const float bv[4] = {b4.x, b4.y, b4.z, b4.w};
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                  for (int q = 0; q < 4; ++q) acc[i][q] = fmaf(av[i], bv[q], acc[i][q]);
+              }
+              __syncthreads();
+              if (more) {
+                stage();
+                __syncthreads();
+              }
+            }
+            if (rb == 0) {  // diagonal tile (uniform over the CTA)
+#pragma unroll
+              for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                  const int c = c0t + tx * 4 + q;
+                  if (ty * 4 + i == tx * 4 + q && c < n)
+                    sh.d[c] = (double)(sh.ddiag[c] + acc[i][q]);
+                }
+              __syncthreads();
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+              const int j = r0t + ty * 4 + i;
+              if (j >= n) continue;
+#pragma unroll
+              for (int q = 0; q < 4; ++q) {
+                const int c = c0t + tx * 4 + q;
+                if (c >= n) continue;
+                const float z = zc[(int64_t)j * n + c];
+                // P_jc = Delta_jc (the E part, exact) + (Delta W)_jc
+                const float pjc = (j != c ? M[(int64_t)j * n + c] : 0.f) + acc[i][q];
+                const float gap = gap2f(sh.th_hi[j], sh.th_lo[j], sh.th_hi[c], sh.th_lo[c]);
+                float f, r;
+                map_entry<float>(z, pjc, (float)sh.d[c], gap, j == c, f, r);
+                zn[(int64_t)j * n + c] = f;
+                s_inc = fmaf(f - z, f - z, s_inc);
+                s_z = fmaf(z, z, s_z);
+                s_r = fmaf(r, r, s_r);
+              }
+            }
+          }
+      }
+      // norms of this evaluation, Alg. 2's test, divergence, cap
+      const double t_inc = block_sum((double)s_inc, sh.red[0]);
+      const double t_z = block_sum((double)s_z, sh.red[1]);
+      const double t_r = block_sum((double)s_r, sh.red[2]);
+      if (it == 0) r0 = sqrt(t_r);
+      const double inc = sqrt(t_inc) / sqrt(t_z);
+      const double rho = r0 > 0.0 ? sqrt(t_r) / r0 : 0.0;
+      const int fl = sh.flag;
+      __syncthreads();
+      if (fl) {
+        status = IPT_DEGENERATE_THETA;
+        break;
+      }
+      if (!isfinite(inc) || !isfinite(rho) || sqrt(t_z) > a.diverge_bound * sqrt((double)n)) {
+        status = IPT_DIVERGED;
+        break;
+      }
+      if ((a.stop == IPT_STOP_INCREMENT ? inc : rho) <= a.tol) {
+        status = IPT_OK;
+        break;
+      }
+      if (it + 1 == a.max_iter) break;  // MAXITER: the returned Z is the last evaluated
+      float* t = zc;
+      zc = zn;
+      zn = t;
+    }
+    // ---------------------------------------------------------- outputs
+    const int evals = status == IPT_MAXITER ? a.max_iter : it + 1;
+    // the returned iterate: E if the test passed (or failed hard) at the first evaluation
+    const bool is_e = (it == 0);
+    float* Zout = a.Z + a.m_off[p];
+    for (int c = ty; c < n; c += NT / 16)
+      for (int j = tx; j < n; j += 16)
+        Zout[(int64_t)c * n + j] = is_e ? (j == c ? 1.f : 0.f) : zc[(int64_t)j * n + c];
+    for (int c = tid; c < n; c += NT) {
+      const double t = a.theta ? a.theta[vo + c] : (double)M[(int64_t)c * n + c];
+      a.lambda[vo + c] = t + sh.d[c];
+    }
+    if (tid == 0) {
+      a.status[p] = status;
+      a.iters[p] = evals;
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_batched(const float* M, const double* theta, const int64_t* m_off,
+                           const int64_t* v_off, const int* nsz, const int* order, int count,
+                           int64_t max_n2, double tol, int max_iter, int stop,
+                           double diverge_bound, double* lambda, float* Z, int* status,
+                           int* iters, float* scratch, int* queue, int ctas, cudaStream_t s) {
+  BatchArgs a;
+  a.M = M;
+  a.theta = theta;
+  a.m_off = m_off;
+  a.v_off = v_off;
+  a.nsz = nsz;
+  a.order = order;
+  a.lambda = lambda;
+  a.Z = Z;
+  a.status = status;
+  a.iters = iters;
+  a.scratch = scratch;
+  a.queue = queue;
+  a.max_n2 = max_n2;
+  a.count = count;
+  a.max_iter = max_iter;
+  a.stop = stop;
+  a.tol = tol;
+  a.diverge_bound = diverge_bound;
+  k_batched<<<ctas, NT, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+int batched_ctas_per_sm() {
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batched, NT, 0) != cudaSuccess ||
+      nb < 1)
+    nb = 1;
+  return nb;
+}
+
+}  // namespace ipt

@@ -15,6 +15,7 @@ from __future__ import annotations
 import ctypes as C
 import os
 
+import numpy as np
 import torch
 
 _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "libipt.so")
@@ -212,6 +213,32 @@ class Solver:
                                   _ptr(Zt), n, DTYPE[Zt.dtype], C.byref(r))
         return lam, Zt.t(), r.to_dict()
 
+    def solve_batched(self, sizes, M, theta=None, tol=1e-6, max_iter=100, stop="residual",
+                      diverge_bound=1e8, record_timing=False):
+        """Many dense problems in one launch (Alg. 2 on each, all eigenpairs).
+
+        sizes: the problem orders (host sequence); M: CUDA float32 tensor with the
+        problems packed row-major back to back; theta: packed CUDA float64 or None.
+        Returns (lam packed f64, Z packed f32 (each block column-major), status
+        int32[count], iterations int32[count], info dict)."""
+        sizes = np.ascontiguousarray(np.asarray(sizes, dtype=np.int64))
+        M = _dev(M, torch.float32, "M").reshape(-1)
+        theta = _dev(theta, torch.float64, "theta")
+        count = len(sizes)
+        if M.numel() != int(np.sum(sizes * sizes)):
+            raise ValueError("M does not hold the packed problems of the given sizes")
+        lam = torch.empty(int(np.sum(sizes)), dtype=torch.float64, device=M.device)
+        Z = torch.empty(M.numel(), dtype=torch.float32, device=M.device)
+        status = torch.empty(count, dtype=torch.int32, device=M.device)
+        iters = torch.empty(count, dtype=torch.int32, device=M.device)
+        o = make_options("f32", stop, diverge_bound, record_timing=record_timing)
+        r = Result()
+        _lib.ipt_solve_batched(self._h, count,
+                               sizes.ctypes.data_as(C.POINTER(C.c_int64)), _ptr(M),
+                               _ptr(theta), float(tol), int(max_iter), C.byref(o), _ptr(lam),
+                               _ptr(Z), _ptr(status), _ptr(iters), C.byref(r))
+        return lam, Z, status, iters, r.to_dict()
+
     def step_dense(self, M, Z, theta=None, cols=None, precision="f32"):
         """One evaluation of F (Eq. dyn) at Z (n, k).  Returns (F (n, k), lam, norms)."""
         M = _dev(M, name="M")
@@ -255,6 +282,16 @@ class Solver:
                            int(max_iter), C.byref(o), _ptr(lam), _ptr(Zt), n, DTYPE[z_dtype],
                            C.byref(r))
         return lam, Zt.t(), r.to_dict()
+
+
+def _batched_argtypes():
+    _lib.ipt_solve_batched.argtypes = [_vp, _i64, C.POINTER(C.c_int64), _vp, _vp, _d, _i32,
+                                       C.POINTER(Options), _vp, _vp, _vp, _vp,
+                                       C.POINTER(Result)]
+    _lib.ipt_solve_batched.restype = _i32
+
+
+_batched_argtypes()
 
 
 def residual_dense_noalloc(M, Z, lam, out=None, stream=None):

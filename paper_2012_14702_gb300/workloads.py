@@ -37,6 +37,8 @@ __all__ = [
     "lowest_columns",
     "DENSE_CONFIGS",
     "CSR_CONFIGS",
+    "batched_dense",
+    "BATCHED_CONFIGS",
 ]
 
 
@@ -152,6 +154,33 @@ def csr_banded(n: int, per_row: int, band: int, scale: float, seed: int,
     return rowptr.astype(np.int32), c_all.astype(np.int32), v_all, theta
 
 
+def batched_dense(count: int, nmin: int, nmax: int, scale: float, seed: int,
+                  dtype=np.float32):
+    """Many small dense problems packed back to back (the batched workload).
+
+    Problem p has order n_p ~ U{nmin..nmax}, theta_i = i (i = 1..n_p) on the
+    diagonal and a symmetric zero-diagonal perturbation with N(0,1)*scale/sqrt(n_p)
+    entries.  Returns (sizes int64[count], M packed row-major in ``dtype``,
+    theta packed float64): problem p starts at sum_{q<p} n_q^2 in M and at
+    sum_{q<p} n_q in theta.
+    """
+    g = rng(seed)
+    sizes = g.integers(nmin, nmax + 1, size=count).astype(np.int64)
+    m = np.empty(int(np.sum(sizes * sizes)), dtype=dtype)
+    th = np.empty(int(np.sum(sizes)), dtype=np.float64)
+    mo = vo = 0
+    for n in sizes:
+        n = int(n)
+        a = _sym_offdiag(n, scale / np.sqrt(n), g)
+        t = np.arange(1, n + 1, dtype=np.float64)
+        a[np.diag_indices(n)] = t
+        m[mo:mo + n * n] = a.reshape(-1)
+        th[vo:vo + n] = t
+        mo += n * n
+        vo += n
+    return sizes, m, th
+
+
 def lowest_columns(theta: np.ndarray, k: int) -> np.ndarray:
     """Indices of the k smallest theta, ascending (target choice of Section 6.1)."""
     return np.argsort(theta, kind="stable")[:k].astype(np.int32)
@@ -171,4 +200,9 @@ DENSE_CONFIGS = {
 CSR_CONFIGS = {
     "csr_n2p20_k64": (1 << 20, 8, 2048, 1e-3, 3, 64),
     "csr_n2p16_k64": (1 << 16, 8, 2048, 1e-3, 3, 64),
+}
+
+# The batched workloads by name: (count, nmin, nmax, scale, seed).
+BATCHED_CONFIGS = {
+    "batched_4096_n32_512": (4096, 32, 512, 1e-2, 4),
 }
