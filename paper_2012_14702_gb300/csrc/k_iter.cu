@@ -465,10 +465,11 @@ __global__ void __launch_bounds__(256)
     red[2][w] = w2;
   }
   __syncthreads();
-  if (threadIdx.x < 3) {
+  if (threadIdx.x < 3) {  // three arrays of per-block partials, one per norm
     double t = 0.0;
     for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += (double)red[threadIdx.x][q];
-    part[((int64_t)blockIdx.x * gridDim.y + blockIdx.y) * 3 + threadIdx.x] = t;
+    const int64_t nb = (int64_t)gridDim.x * gridDim.y;
+    part[threadIdx.x * nb + (int64_t)blockIdx.x * gridDim.y + blockIdx.y] = t;
   }
 }
 
@@ -477,10 +478,11 @@ __global__ void __launch_bounds__(1024)
     k_sum_norms(const double* __restrict__ part, int64_t count, DevState* st) {
   __shared__ double red[3][1024];
   double t0 = 0.0, t1 = 0.0, t2 = 0.0;
-  for (int64_t i = threadIdx.x; i < count; i += blockDim.x) {
-    t0 += part[3 * i];
-    t1 += part[3 * i + 1];
-    t2 += part[3 * i + 2];
+#pragma unroll 8
+  for (int64_t i = threadIdx.x; i < count; i += blockDim.x) {  // coalesced, loads in flight
+    t0 += part[i];
+    t1 += part[count + i];
+    t2 += part[2 * count + i];
   }
   red[0][threadIdx.x] = t0;
   red[1][threadIdx.x] = t1;

@@ -181,6 +181,7 @@ __global__ void __launch_bounds__(256)
 __global__ void k_sum_partials(const double* __restrict__ part, int64_t count, DevState* st) {
   __shared__ double red[1024];
   double t = 0.0;
+#pragma unroll 8
   for (int64_t i = threadIdx.x; i < count; i += blockDim.x) t += part[i];
   red[threadIdx.x] = t;
   __syncthreads();

@@ -61,8 +61,27 @@ def run_csr(name, solves, precision, tol, window=True):
             raise SystemExit(1)
 
 
+def run_batched(name, solves, tol):
+    import torch
+    from paper_2012_14702_gb300 import ipt
+    count, nmin, nmax, scale, seed = workloads.BATCHED_CONFIGS[name]
+    sizes, flat, _ = workloads.batched_dense(count, nmin, nmax, scale, seed)
+    Mg = torch.as_tensor(flat, device="cuda")
+    s = ipt.Solver()
+    for i in range(solves):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, _, _, iters, info = s.solve_batched(sizes, Mg, tol=tol, max_iter=30)
+        torch.cuda.synchronize()
+        print(f"{name} solve {i}: {info['status']} evaluations {info['iterations']} (max) "
+              f"{1e3 * (time.perf_counter() - t0):.2f} ms", flush=True)
+        if info["status"] != "OK":
+            raise SystemExit(1)
+
+
 def main(argv=None):
-    names = sorted(workloads.DENSE_CONFIGS) + sorted(workloads.CSR_CONFIGS)
+    names = (sorted(workloads.DENSE_CONFIGS) + sorted(workloads.CSR_CONFIGS) +
+             sorted(workloads.BATCHED_CONFIGS))
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("workload", choices=names)
     ap.add_argument("--solves", type=int, default=2)
@@ -73,6 +92,8 @@ def main(argv=None):
     a = ap.parse_args(argv)
     if a.workload in workloads.DENSE_CONFIGS:
         run_dense(a.workload, a.solves, a.precision, a.tol)
+    elif a.workload in workloads.BATCHED_CONFIGS:
+        run_batched(a.workload, a.solves, a.tol)
     else:
         run_csr(a.workload, a.solves, a.precision, a.tol, window=not a.all_rows)
 

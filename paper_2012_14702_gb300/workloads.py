@@ -205,4 +205,5 @@ CSR_CONFIGS = {
 # The batched workloads by name: (count, nmin, nmax, scale, seed).
 BATCHED_CONFIGS = {
     "batched_4096_n32_512": (4096, 32, 512, 1e-2, 4),
+    "batched_512_n32_512": (512, 32, 512, 1e-2, 4),  # the same mix, small enough to profile
 }
