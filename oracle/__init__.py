@@ -5,3 +5,4 @@ from .ipt_oracle import (OK, MAXITER, DIVERGED, DEGENERATE_THETA, INVALID_ARG,  
                          initial_residual_norm, ipt_solve, ipt_solve_csr,
                          rs_corrections, chart_jacobian, acx_differences, acx_sigma,
                          acx_update, ipt_solve_acx)
+from . import damping  # noqa: F401,E402

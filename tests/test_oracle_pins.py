@@ -481,3 +481,79 @@ def test_acx_full_spectrum_beyond_picard_domain(sigma):
     r = oracle.ipt_solve_acx(M, th, tol=1e-9, max_iter=300, stop="residual", sigma=sigma)
     assert r["status"] == oracle.OK
     np.testing.assert_allclose(np.sort(r["lam"]), np.linalg.eigvalsh(M), atol=1e-9)
+
+
+# ------------------------------------------------------------------ learned damping model
+def test_damping_model_gradient_matches_finite_differences():
+    """The backward pass of the damping perceptron against central differences of
+    its own forward pass in float64 (the FP16 parameters perturbed in float64)."""
+    from oracle import damping as dm
+    g = np.random.default_rng(5)
+    p16 = dm.init_params(3)
+    X = g.standard_normal((40, 6))
+    t = g.uniform(0.1, 1.9, 40)
+    _, grad = dm.loss_and_grad(p16, X, t)
+    base = p16.astype(np.float64)
+
+    def loss_at(flat64):
+        pp = dm.unpack(flat64)
+        h1 = np.tanh(X @ pp["W1"] + pp["b1"])
+        h2 = np.tanh(h1 @ pp["W2"] + pp["b2"])
+        y = (h2 @ pp["W3"] + pp["b3"])[:, 0]
+        a = 2.0 / (1.0 + np.exp(-y))
+        return np.mean((a - t) ** 2)
+
+    idx = g.choice(dm.N_PARAMS, 60, replace=False)
+    for i in idx:
+        e = np.zeros(dm.N_PARAMS)
+        e[i] = 1e-6
+        fd = (loss_at(base + e) - loss_at(base - e)) / 2e-6
+        assert abs(fd - grad[i]) <= 1e-6 + 1e-5 * abs(fd), (i, fd, grad[i])
+
+
+def test_damping_features_and_secant_step():
+    """Features of geometric histories, and the secant damping alpha* = 1/(1 - a)
+    of a contraction f(x) = a x + b (which makes one damped step exact)."""
+    from oracle import damping as dm
+    a = 0.5
+    inc = np.array([[1.0], [a], [a * a]])
+    lam = np.array([[1.0], [1.0 + 0.1], [1.0 + 0.1 - 0.05]])
+    X = dm.features(inc, lam)
+    np.testing.assert_allclose(X[0, :3], [np.log10(a * a), np.log10(a), np.log10(a)],
+                               atol=1e-12)
+    np.testing.assert_allclose(X[0, 3], -0.5, atol=1e-12)  # (l0 - l1) / (l1 - l2)
+    g = np.random.default_rng(6)
+    for av in [0.9, -0.8, 0.2, -2.5]:
+        b = g.standard_normal((7, 1))
+        x = g.standard_normal((7, 1))
+        f = lambda y: av * y + b
+        D1 = f(x) - x
+        D2 = f(f(x)) - 2 * f(x) + x
+        alpha = dm.secant_alpha(D1, D2, lo=-1e9, hi=1e9)[0]
+        np.testing.assert_allclose(alpha, 1.0 / (1.0 - av), rtol=1e-12)
+        np.testing.assert_allclose(x + alpha * D1, b / (1.0 - av), atol=1e-12)
+
+
+def test_damped_solve_with_unit_damping_is_picard():
+    """alpha = 1 everywhere gives exactly the Picard iteration of Alg. 2."""
+    from oracle import damping as dm
+    M, th = w.dense_symmetric(90, 0.01, seed=8, theta_step=0.5)
+    a = dm.damped_solve(M, th, tol=1e-12, max_iter=60, alpha_fn=lambda X: np.ones(len(X)))
+    b = oracle.ipt_solve(M, th, tol=1e-12, max_iter=60, stop="residual")
+    assert a["status"] == b["status"] == oracle.OK and a["iterations"] == b["iterations"]
+    np.testing.assert_array_equal(a["Z"], b["Z"])
+
+
+def test_damped_solve_secant_rule_extends_domain():
+    """Damping each column by 1 / (1 - q) (q the Rayleigh-quotient change ratio,
+    the secant rule the model is trained to imitate) converges on a matrix where
+    the Picard iteration does not, to LAPACK's eigenvalues."""
+    from oracle import damping as dm
+    M, th = w.dense_symmetric(256, 0.03, seed=7, theta_step=0.125)
+    plain = oracle.ipt_solve(M, th, tol=1e-8, max_iter=300, stop="residual")
+    assert plain["status"] == oracle.MAXITER
+    rule = lambda X: np.clip(1.0 / np.where(np.abs(1.0 - X[:, 3]) > 1e-12, 1.0 - X[:, 3],
+                                            1e-12), 0.05, 2.0)
+    r = dm.damped_solve(M, th, tol=1e-8, max_iter=400, alpha_fn=rule)
+    assert r["status"] == oracle.OK
+    np.testing.assert_allclose(np.sort(r["lam"]), np.linalg.eigvalsh(M), atol=1e-8)
