@@ -108,14 +108,23 @@ typedef struct {
                            With IPT_PREC_STAGED the products are FP16 x3 (BF16 x3 with
                            staged_bf16)                                                    */
   int acx_sigma;        /* ACX step length: 0 (default) one per column, 1 one for all     */
+  const void* damping_model; /* IPT_ACCEL_DAMPED: the damping model's parameters (device,
+                                FP16, IPT_DAMPING_PARAMS values, layout of
+                                ipt_damping_forward)                                       */
   int csr_window;       /* ipt_solve_csr: nonzero (default) = each product evaluates only the
                            rows that can be nonzero: the rows of the current iterate's
                            nonzero rows widened by the band max|j - m| of the stored
                            entries (exact: other rows of Z and F are zero).  0 = all rows */
 } ipt_options;
 
-/* Values of ipt_options.accel. */
-enum { IPT_ACCEL_NONE = 0, IPT_ACCEL_ACX = 1 };
+/* Values of ipt_options.accel.  IPT_ACCEL_DAMPED: learned damping (no counterpart in
+ * the paper, whose Section 5 points to fixed-point acceleration in general): after each
+ * evaluation Z <- Z + alpha_c (F(Z) - Z), alpha_c in (0, 2) predicted per column by the
+ * damping model from the column's increment-norm and Rayleigh-quotient-change history
+ * (see ipt_damping_forward); plain Picard steps for the first three evaluations and
+ * after a fallback (a residual above ten times the smallest seen).  Precision as for
+ * ACX. */
+enum { IPT_ACCEL_NONE = 0, IPT_ACCEL_ACX = 1, IPT_ACCEL_DAMPED = 2 };
 
 /* Values of ipt_options.product_kernel. */
 enum { IPT_PRODUCT_AUTO = 0, IPT_PRODUCT_SINGLE = 1, IPT_PRODUCT_PAIR = 2 };
@@ -258,6 +267,33 @@ ipt_status ipt_solve_batched(ipt_handle* h, int64_t count, const int64_t* n, con
                              const double* theta, double tol, int max_iter,
                              const ipt_options* opt, double* lambda, float* Z, int32_t* status,
                              int32_t* iters, ipt_result* out);
+
+/*
+ * The damping model of IPT_ACCEL_DAMPED and its training (no counterpart in the
+ * paper).  A 6 -> 64 -> 64 -> 1 perceptron: h1 = tanh(x W1 + b1),
+ * h2 = tanh(h1 W2 + b2), y = h2 W3 + b3, alpha = 2 / (1 + exp(-y)).  Parameters:
+ * IPT_DAMPING_PARAMS FP16 values on the device, packed row-major in the order
+ * W1[6][64], b1[64], W2[64][64], b2[64], W3[64][1], b3[1]; FP32 arithmetic.
+ * Inputs x: rows of 6 FP32 features (device, B x 6 row-major; their definition is
+ * the solver's, listed with IPT_ACCEL_DAMPED's kernels).  All calls are ordered on
+ * `stream` (a cudaStream_t; NULL = the legacy default stream) and do not synchronise.
+ *   ipt_damping_forward: alpha[b] for b < B (device FP32).
+ *   ipt_damping_grad: ADDS the gradient of mean_b (alpha_b - target_b)^2 over the B
+ *     samples to grad (device FP32[IPT_DAMPING_PARAMS]) and the mean to *loss
+ *     (device FP64); the caller zeroes them.
+ *   ipt_damping_adam: one Adam step (Kingma & Ba) on FP32 master parameters
+ *     (device, IPT_DAMPING_PARAMS) with moments m, v (device FP32, zero at step 1),
+ *     step >= 1; writes the FP16 parameters and zeroes grad.
+ * Returns IPT_INVALID_ARG for a null pointer or B < 0, IPT_CUDA_ERROR on a launch error.
+ */
+#define IPT_DAMPING_PARAMS 4673
+ipt_status ipt_damping_forward(int64_t B, const void* params, const float* x, float* alpha,
+                               void* stream);
+ipt_status ipt_damping_grad(int64_t B, const void* params, const float* x, const float* target,
+                            float* grad, double* loss, void* stream);
+ipt_status ipt_damping_adam(float* master, void* params, float* grad, float* m, float* v,
+                            float lr, float beta1, float beta2, float eps, int step,
+                            void* stream);
 
 /*
  * ||M Z - Z Lambda||_F in FP64, allocating no device memory.  The paper has

@@ -42,6 +42,7 @@ struct ipt_handle {
   int dev = 0;
   Buf drow, dt, dh, dl, z[4], pbuf, wh, wl, rinv, sinv;
   Buf acx_d, acx_acc, acx_sigma;    // ACX: d of the inner evaluations, step-length sums, steps
+  Buf damp;                         // learned damping: history, features, alphas, state
   Buf bmeta, bscratch;              // batched: schedule and offsets, per-CTA iterate pairs
   void* hmeta = nullptr;            // pinned staging of the batched schedule
   size_t hmeta_cap = 0;
@@ -106,6 +107,7 @@ struct Plan {
   bool staged;  // third Z buffer and stored-P buffer (base re-use)
   int product_kernel = IPT_PRODUCT_AUTO;  // tensor-core product kernel variant
   bool acx = false;  // four Z buffers (z, f, f^2, f^3) and the extrapolation scratch
+  bool damped = false;  // learned damping buffers
 };
 
 ipt_status check_dense_args(ipt_handle* h, int64_t n, const void* M, int64_t ldm, int m_dtype,
@@ -127,6 +129,10 @@ ipt_status alloc_dense(ipt_handle* h, const Plan& p) {
   if (p.staged) {
     CK(ensure(h->z[2], kn * ez));
     CK(ensure(h->pbuf, kn * 4));
+  }
+  if (p.damped) {
+    CK(ensure(h->acx_acc, (size_t)p.kpad * 2 * 8));
+    CK(ensure(h->damp, (size_t)p.kpad * (3 * 8 + 3 * 4 + 6 * 4 + 4) + 64));
   }
   if (p.acx) {
     CK(ensure(h->z[2], kn * ez));
@@ -501,6 +507,65 @@ ipt_status acx_loop(ipt_handle* h, const Plan& p, const ControlArgs& ca, const F
   return IPT_OK;
 }
 
+// Learned damping: buffer 0 holds Z (updated in place), buffer 1 receives
+// F(Z).  Each step: one evaluation with the stopping test, then the damping
+// kernels (per-column history, features, the model, Z <- Z + alpha (F - Z)).
+// Four steps per host synchronisation; every kernel returns at entry once the
+// controller has stopped.
+ipt_status damped_loop(ipt_handle* h, const Plan& p, const ControlArgs& ca, const FirstEval& fe,
+                       int max_iter, const void* model, Timing* tm) {
+  cudaStream_t s = h->s;
+  DevState* st = dst(h);
+  const int split = (fe.stage == IPT_PREC_BF16X3 || fe.stage == IPT_PREC_FP16X3) ? 3 : 1;
+  // layout: lam history (3 kpad FP64), inc history (3 kpad), features (6 kpad),
+  // alphas (kpad), state (kpad is a multiple of 256, so every part is aligned)
+  double* hlam = (double*)h->damp.p;
+  float* hinc = (float*)(hlam + (size_t)3 * p.kpad);
+  float* X = hinc + (size_t)3 * p.kpad;
+  float* alpha = X + (size_t)6 * p.kpad;
+  DampState* ds = reinterpret_cast<DampState*>(alpha + p.kpad);
+  CK(cudaMemsetAsync(h->damp.p, 0, (size_t)p.kpad * (3 * 8 + 3 * 4 + 6 * 4 + 4) + 64, s));
+  CK(cudaMemsetAsync(h->acx_acc.p, 0, (size_t)p.kpad * 2 * 8, s));
+  ControlArgs cq = ca;
+  cq.acx = 1;  // the iterate stays in buffer 0
+  int done_evals = 0;
+  for (int chunk = 0; done_evals < max_iter; ++chunk) {
+    const int nb = std::min(4, max_iter - done_evals);
+    for (int q = 0; q < nb; ++q) {
+      const int passes = (done_evals + q == 0) ? fe.passes : (p.f64 ? 1 : split);
+      ipt_status v = evaluate(h, p, 0, -1, fe.stage, passes, 0, tm, 1, nullptr, h->evb + 4 * q);
+      if (v != IPT_OK) return v;
+      launch_control(st, cq, s);
+      CK(launch_damp_step(h->z[0].p, h->z[1].p, p.f64 ? 1 : 0, p.n, p.k, p.npad,
+                          (const double*)h->theta.p, (const int32_t*)h->icol.p,
+                          (const double*)h->d.p, model, (double*)h->acx_acc.p, hinc, hlam, X,
+                          alpha, ds, st, s));
+      h->launches += 6;
+    }
+    if (cudaGetLastError() != cudaSuccess ||
+        cudaMemcpyAsync(h->hst, st, kStateHead, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      return IPT_CUDA_ERROR;
+    if (chunk == 0) {
+      const ipt_status v = status_from_flags(h->hst->flags);
+      if (v != IPT_OK) return v;
+      if (tm && tm->on) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, h->ev[4], h->ev[5]) == cudaSuccess) tm->setup_ms = ms;
+      }
+    }
+    const int ran = std::min(nb, h->hst->iter - done_evals);
+    for (int q = 0; q < ran; ++q) {
+      const int passes = (done_evals + q == 0) ? fe.passes : (p.f64 ? 1 : split);
+      collect_timing(h, passes, tm, h->evb + 4 * q);
+    }
+    done_evals = h->hst->iter;
+    if (h->hst->timeout) return IPT_DEVICE_TIMEOUT;
+    if (h->hst->done) break;
+  }
+  return IPT_OK;
+}
+
 ipt_status solve_dense(ipt_handle* h, int64_t n, const void* M, int64_t ldm, int m_dtype,
                        const double* theta, int64_t k, const int32_t* cols, double tol,
                        int max_iter, const ipt_options* opt_in, double* lambda, void* Z,
@@ -516,7 +581,9 @@ ipt_status solve_dense(ipt_handle* h, int64_t n, const void* M, int64_t ldm, int
                       (opt.stop != IPT_STOP_INCREMENT && opt.stop != IPT_STOP_RESIDUAL) ||
                       opt.product_kernel < IPT_PRODUCT_AUTO ||
                       opt.product_kernel > IPT_PRODUCT_PAIR ||
-                      (opt.accel != IPT_ACCEL_NONE && opt.accel != IPT_ACCEL_ACX) ||
+                      (opt.accel != IPT_ACCEL_NONE && opt.accel != IPT_ACCEL_ACX &&
+                       opt.accel != IPT_ACCEL_DAMPED) ||
+                      (opt.accel == IPT_ACCEL_DAMPED && !opt.damping_model) ||
                       (opt.acx_sigma != 0 && opt.acx_sigma != 1)))
     v = IPT_INVALID_ARG;
   if (v != IPT_OK) {
@@ -533,14 +600,16 @@ ipt_status solve_dense(ipt_handle* h, int64_t n, const void* M, int64_t ldm, int
     return IPT_CUDA_ERROR;
   }
   const bool acx = opt.accel == IPT_ACCEL_ACX;
-  // ACX moves the iterate by extrapolation, outside the staged schedule's
-  // error model: a staged request runs every product as the split stage
-  const int prec = (acx && opt.precision == IPT_PREC_STAGED)
+  const bool damped = opt.accel == IPT_ACCEL_DAMPED;
+  // ACX and damping move the iterate outside the staged schedule's error
+  // model: a staged request runs every product as the split stage
+  const int prec = ((acx || damped) && opt.precision == IPT_PREC_STAGED)
                        ? (opt.staged_bf16 ? IPT_PREC_BF16X3 : IPT_PREC_FP16X3)
                        : opt.precision;
   Plan p = make_plan(n, k, prec, opt.staged_bf16 != 0);
   p.product_kernel = opt.product_kernel;
   p.acx = acx;
+  p.damped = damped;
   const int low = p.bf16 ? IPT_PREC_BF16 : IPT_PREC_FP16;
   const int high = p.bf16 ? IPT_PREC_BF16X3 : IPT_PREC_FP16X3;
   // First evaluation: product-free at Z = E (FP32 / tensor-core paths), else
@@ -553,7 +622,7 @@ ipt_status solve_dense(ipt_handle* h, int64_t n, const void* M, int64_t ldm, int
                   : ((fe.stage == IPT_PREC_BF16X3 || fe.stage == IPT_PREC_FP16X3) ? 3 : 1);
   fe.rebase = (p.staged && opt.z0) ? 1 : 0;
   fe.accurate = 1;
-  fe.defer_e = !acx;  // the extrapolation reads z = E from buffer 0
+  fe.defer_e = !acx && !damped;  // the update reads z = E from buffer 0
   v = alloc_dense(h, p);
   if (v == IPT_OK) {
     if (tm.on) cudaEventRecord(h->ev[4], h->s);
@@ -580,6 +649,9 @@ ipt_status solve_dense(ipt_handle* h, int64_t n, const void* M, int64_t ldm, int
   if (acx) {
     v = acx_loop(h, p, ca, fe, max_iter, opt.acx_sigma, &tm);
     max_iter = 0;  // the Picard loop below does not run
+  } else if (damped) {
+    v = damped_loop(h, p, ca, fe, max_iter, opt.damping_model, &tm);
+    max_iter = 0;
   }
   for (int it = 0; it < max_iter; ++it) {
     v = evaluate(h, p, cur, base, stage, passes, rebase, &tm);
@@ -712,7 +784,8 @@ ipt_status ipt_destroy(ipt_handle* h) {
   if (!h) return IPT_OK;
   DeviceGuard g(h->dev);
   Buf* all[] = {&h->drow, &h->dt, &h->dh, &h->dl, &h->z[0], &h->z[1], &h->z[2], &h->z[3],
-                &h->acx_d, &h->acx_acc, &h->acx_sigma, &h->bmeta, &h->bscratch, &h->pbuf,
+                &h->acx_d, &h->acx_acc, &h->acx_sigma, &h->damp, &h->bmeta, &h->bscratch,
+                &h->pbuf,
                 &h->wh, &h->wl,
                 &h->rinv, &h->sinv, &h->theta, &h->thh, &h->thl, &h->icol, &h->count,
                 &h->r0part, &h->delta, &h->cpart,
@@ -1130,6 +1203,37 @@ ipt_status ipt_solve_batched(ipt_handle* h, int64_t count, const int64_t* n, con
   out->wall_ms =
       std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
   return (ipt_status)agg;
+}
+
+ipt_status ipt_damping_forward(int64_t B, const void* params, const float* x, float* alpha,
+                               void* stream) {
+  if (B < 0 || B > (int64_t)1 << 30 || (B > 0 && (!params || !x || !alpha)))
+    return IPT_INVALID_ARG;
+  return launch_mlp_forward(params, x, (int)B, alpha, static_cast<cudaStream_t>(stream)) ==
+                 cudaSuccess
+             ? IPT_OK
+             : IPT_CUDA_ERROR;
+}
+
+ipt_status ipt_damping_grad(int64_t B, const void* params, const float* x, const float* target,
+                            float* grad, double* loss, void* stream) {
+  if (B < 0 || B > (int64_t)1 << 30 || !grad || !loss ||
+      (B > 0 && (!params || !x || !target)))
+    return IPT_INVALID_ARG;
+  return launch_mlp_grad(params, x, target, (int)B, grad, loss,
+                         static_cast<cudaStream_t>(stream)) == cudaSuccess
+             ? IPT_OK
+             : IPT_CUDA_ERROR;
+}
+
+ipt_status ipt_damping_adam(float* master, void* params, float* grad, float* m, float* v,
+                            float lr, float beta1, float beta2, float eps, int step,
+                            void* stream) {
+  if (!master || !params || !grad || !m || !v || step < 1) return IPT_INVALID_ARG;
+  return launch_mlp_adam(master, params, grad, m, v, lr, beta1, beta2, eps, step,
+                         static_cast<cudaStream_t>(stream)) == cudaSuccess
+             ? IPT_OK
+             : IPT_CUDA_ERROR;
 }
 
 }  // extern "C"

@@ -142,6 +142,33 @@ struct ControlArgs {
   int test = 1;               // 0: no stopping test at this evaluation (ACX inner ones)
 };
 
+// Learned-damping model (k_mlp.cu): 6 -> 64 -> 64 -> 1, FP16 parameters.
+constexpr int kMlpInputs = 6, kMlpHidden = 64;
+constexpr int kMlpParams = kMlpInputs * kMlpHidden + kMlpHidden + kMlpHidden * kMlpHidden +
+                           kMlpHidden + kMlpHidden + 1;
+cudaError_t launch_mlp_forward(const void* params, const float* X, int B, float* alpha,
+                               cudaStream_t s);
+cudaError_t launch_mlp_grad(const void* params, const float* X, const float* target, int B,
+                            float* grad, double* loss, cudaStream_t s);
+cudaError_t launch_mlp_adam(float* master, void* params, float* grad, float* m, float* v,
+                            float lr, float b1, float b2, float eps, int step, cudaStream_t s);
+
+// Learned damping in the solve (k_damp.cu): per-solve state of the model's use.
+struct DampState {
+  double best_rho;  // smallest residual seen
+  int steps;        // column histories recorded so far
+  int fallback;     // nonzero: plain Picard steps from now on
+};
+// After an evaluation at z (buffer) with F in f: per-column increments and
+// eigenvalues into the history, features, the model's alphas, and
+// z <- z + alpha (f - z).  acc: 2k FP64 (zero on entry, left zero); hinc: 3k
+// floats; hlam: 3k FP64; X: 6k floats; alpha: k floats.
+cudaError_t launch_damp_step(void* z, const void* f, int f64, int n, int k, int64_t ld,
+                             const double* theta, const int32_t* icol, const double* d,
+                             const void* model, double* acc, float* hinc, double* hlam,
+                             float* X, float* alpha, DampState* ds, DevState* st,
+                             cudaStream_t s);
+
 // Batched solve (k_batched.cu): largest problem order n.
 constexpr int kBatchMaxN = 1024;
 cudaError_t launch_batched(const float* M, const double* theta, const int64_t* m_off,

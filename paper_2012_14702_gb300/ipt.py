@@ -38,7 +38,8 @@ class Options(C.Structure):
     _fields_ = [("precision", C.c_int), ("stop", C.c_int), ("diverge_bound", C.c_double),
                 ("stage_switch", C.c_double), ("staged_bf16", C.c_int), ("verify_fp64", C.c_int),
                 ("record_timing", C.c_int), ("z0", C.c_void_p), ("product_kernel", C.c_int),
-                ("accel", C.c_int), ("acx_sigma", C.c_int), ("csr_window", C.c_int)]
+                ("accel", C.c_int), ("acx_sigma", C.c_int), ("damping_model", C.c_void_p),
+                ("csr_window", C.c_int)]
 
 
 class Result(C.Structure):
@@ -160,13 +161,14 @@ class Solver:
                     stop="residual", z_dtype=torch.float32, verify_fp64=False, z0=None,
                     diverge_bound=1e8, stage_switch=0.1, staged_bf16=False,
                     record_timing=False, product_kernel="auto", accel=None,
-                    acx_sigma="column"):
+                    acx_sigma="column", damping_model=None):
         """Alg. 2 / Alg. 1 on the GPU.  Returns (lam [k] f64, Z (n, k) view, info dict).
 
         product_kernel: "auto", "single" (one CTA per tile) or "pair" (two CTAs
         per 256-row tile); selects the tensor-core product kernel only.
-        accel: None (Picard update) or "acx" (Alg. 3), with acx_sigma "column"
-        (one step length per column) or "global"."""
+        accel: None (Picard update), "acx" (Alg. 3, with acx_sigma "column" —
+        one step length per column — or "global") or "damped" (learned damping,
+        damping_model = the model's FP16 parameters as a CUDA tensor)."""
         M = _dev(M, name="M")
         n = M.shape[0]
         if M.dim() != 2 or M.shape[1] != n or M.dtype not in DTYPE:
@@ -183,10 +185,14 @@ class Solver:
             z0t = None
         o = make_options(precision, stop, diverge_bound, stage_switch, verify_fp64, z0t,
                          staged_bf16, record_timing, product_kernel)
-        if accel not in (None, "none", "acx") or acx_sigma not in ("column", "global"):
-            raise ValueError("accel must be None or 'acx'; acx_sigma 'column' or 'global'")
-        o.accel = 1 if accel == "acx" else 0
+        if accel not in (None, "none", "acx", "damped") or acx_sigma not in ("column", "global"):
+            raise ValueError("accel must be None, 'acx' or 'damped'; acx_sigma 'column' or "
+                             "'global'")
+        o.accel = {"acx": 1, "damped": 2}.get(accel, 0)
         o.acx_sigma = 1 if acx_sigma == "global" else 0
+        if damping_model is not None:
+            damping_model = _dev(damping_model, torch.float16, "damping_model")
+            o.damping_model = damping_model.data_ptr()
         r = Result()
         _lib.ipt_solve_dense(self._h, n, _ptr(M), M.stride(0), DTYPE[M.dtype], _ptr(theta), k,
                              _ptr(cols), float(tol), int(max_iter), C.byref(o), _ptr(lam),
@@ -292,6 +298,54 @@ def _batched_argtypes():
 
 
 _batched_argtypes()
+
+
+_lib.ipt_damping_forward.argtypes = [_i64, _vp, _vp, _vp, _vp]
+_lib.ipt_damping_forward.restype = _i32
+_lib.ipt_damping_grad.argtypes = [_i64, _vp, _vp, _vp, _vp, _vp, _vp]
+_lib.ipt_damping_grad.restype = _i32
+_lib.ipt_damping_adam.argtypes = [_vp, _vp, _vp, _vp, _vp, C.c_float, C.c_float, C.c_float,
+                                  C.c_float, _i32, _vp]
+_lib.ipt_damping_adam.restype = _i32
+DAMPING_PARAMS = 4673
+
+
+def _stream_ptr(stream):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def damping_forward(params, X, alpha=None, stream=None):
+    """alpha (B,) float32 of the damping model (params: CUDA float16 [4673]) at
+    feature rows X (B, 6) float32; runs on ``stream`` without synchronising."""
+    X = _dev(X, torch.float32, "X").contiguous()
+    params = _dev(params, torch.float16, "params")
+    if alpha is None:
+        alpha = torch.empty(X.shape[0], dtype=torch.float32, device=X.device)
+    st = _lib.ipt_damping_forward(X.shape[0], _ptr(params), _ptr(X), _ptr(alpha),
+                                  _stream_ptr(stream))
+    if st != 0:
+        raise RuntimeError(f"ipt_damping_forward: {STATUS.get(st, st)}")
+    return alpha
+
+
+def damping_grad(params, X, target, grad, loss, stream=None):
+    """Adds the mean-squared-error gradient (and the loss) of the model over (X, target)."""
+    X = _dev(X, torch.float32, "X").contiguous()
+    st = _lib.ipt_damping_grad(X.shape[0], _ptr(params), _ptr(X), _ptr(target), _ptr(grad),
+                               _ptr(loss), _stream_ptr(stream))
+    if st != 0:
+        raise RuntimeError(f"ipt_damping_grad: {STATUS.get(st, st)}")
+
+
+def damping_adam(master, params, grad, m, v, lr, step, beta1=0.9, beta2=0.999, eps=1e-8,
+                 stream=None):
+    """One Adam step on the FP32 master parameters; writes the FP16 params, zeroes grad."""
+    st = _lib.ipt_damping_adam(_ptr(master), _ptr(params), _ptr(grad), _ptr(m), _ptr(v),
+                               float(lr), float(beta1), float(beta2), float(eps), int(step),
+                               _stream_ptr(stream))
+    if st != 0:
+        raise RuntimeError(f"ipt_damping_adam: {STATUS.get(st, st)}")
 
 
 def residual_dense_noalloc(M, Z, lam, out=None, stream=None):
