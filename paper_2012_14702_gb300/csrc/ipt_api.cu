@@ -56,6 +56,9 @@ struct ipt_handle {
   DevState* hinit = nullptr;        // pinned initial controller words of a solve
   cudaEvent_t ev[8] = {};           // pre-pass / product / setup / finalize brackets
   cudaEvent_t evb[4 * kCsrChunk] = {};  // per-evaluation brackets of a sparse chunk
+  cudaStream_t cs = nullptr;        // host-buffer entry point: device-to-host copy stream
+  cudaEvent_t zready = nullptr;     // an iterate is complete on the solve stream
+  cudaEvent_t zcopied[3] = {};      // the last copy out of Z buffer b has finished
   int launches = 0;                 // kernels launched by the current call
   bool e_pending = false;           // Z buffer 0 does not hold the unit columns yet
   // Sparse path: Z buffers 0 and 1 are zero outside rows [csr_dirty_lo, csr_dirty_hi)
@@ -178,6 +181,14 @@ ipt_status status_from_flags(int flags) {
 // validation flags are read back here; otherwise the caller reads them at
 // its first synchronisation, before writing any output (every setup kernel
 // is memory-safe on invalid columns or theta).
+// Host destination of the returned iterate (host-buffer entry point): the
+// iterate predicted to be returned is copied out to the host beside the
+// evaluation that tests it.
+struct HostOut {
+  void* Z = nullptr;  // host, column-major n x k, ldz, the iterate's dtype
+  int64_t ldz = 0;
+};
+
 // Initial controller state: the first evaluation's stage, product passes
 // (0 = product-free evaluation at Z = E), base and accuracy class.
 struct FirstEval {
@@ -203,20 +214,19 @@ ipt_status setup_dense(ipt_handle* h, const Plan& p, const void* M, int64_t ldm,
     CK(cudaMemcpyAsync(st, h->hinit, kStateHead, cudaMemcpyHostToDevice, s));
   }
   CK(cudaMemsetAsync(h->count.p, 0, (size_t)p.npad * 4, s));
+  ipt_status v = IPT_OK;
   launch_theta(M, ldm, m_dtype, theta, p.n, p.npad, (double*)h->theta.p, (float*)h->thh.p,
                (float*)h->thl.p, st, s);
   launch_validate(cols, p.n, p.k, p.kpad, (const double*)h->theta.p, (int32_t*)h->icol.p,
                   (int*)h->count.p, st, s);
   h->launches += 3;
   CK(cudaGetLastError());
-  ipt_status v = IPT_OK;
   if (sync_check) {
     CK(cudaMemcpyAsync(h->hst, st, kStateHead, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     v = status_from_flags(h->hst->flags);
     if (v != IPT_OK) return v;
   }
-
   launch_form_delta(M, ldm, m_dtype, (const double*)h->theta.p, p.n, p.npad,
                     (const int*)h->count.p, h->drow.p, p.f64 ? 1 : 0,
                     p.dt ? (float*)h->dt.p : nullptr, (double*)h->r0part.p, st, s);
@@ -225,6 +235,8 @@ ipt_status setup_dense(ipt_handle* h, const Plan& p, const void* M, int64_t ldm,
     launch_split_delta((const float*)h->drow.p, p.npad, p.bf16 ? 1 : 0, (uint16_t*)h->dh.p,
                        (uint16_t*)h->dl.p, (float*)h->rinv.p, s);
     h->launches += 1;
+  }
+  if (p.tc) {
     // padding columns of the W operand stay zero (the pre-pass skips them)
     const size_t pad = (size_t)(p.kpad - p.k) * p.npad * 2;
     if (pad) {
@@ -569,7 +581,8 @@ ipt_status damped_loop(ipt_handle* h, const Plan& p, const ControlArgs& ca, cons
 ipt_status solve_dense(ipt_handle* h, int64_t n, const void* M, int64_t ldm, int m_dtype,
                        const double* theta, int64_t k, const int32_t* cols, double tol,
                        int max_iter, const ipt_options* opt_in, double* lambda, void* Z,
-                       int64_t ldz, int z_dtype, ipt_result* out) {
+                       int64_t ldz, int z_dtype, ipt_result* out,
+                       const HostOut* hz = nullptr) {
   if (!out) return IPT_INVALID_ARG;
   memset(out, 0, sizeof(*out));
   out->rho_fp64 = -1.0;
@@ -622,7 +635,7 @@ ipt_status solve_dense(ipt_handle* h, int64_t n, const void* M, int64_t ldm, int
                   : ((fe.stage == IPT_PREC_BF16X3 || fe.stage == IPT_PREC_FP16X3) ? 3 : 1);
   fe.rebase = (p.staged && opt.z0) ? 1 : 0;
   fe.accurate = 1;
-  fe.defer_e = !acx && !damped;  // the update reads z = E from buffer 0
+  fe.defer_e = !acx && !damped && !hz;  // the update / the copy-out reads z = E
   v = alloc_dense(h, p);
   if (v == IPT_OK) {
     if (tm.on) cudaEventRecord(h->ev[4], h->s);
@@ -653,7 +666,26 @@ ipt_status solve_dense(ipt_handle* h, int64_t n, const void* M, int64_t ldm, int
     v = damped_loop(h, p, ca, fe, max_iter, opt.damping_model, &tm);
     max_iter = 0;
   }
+  const size_t zes = p.f64 ? 8 : 4;
+  // host output: the iterate under test is copied out beside its evaluation
+  // when that evaluation is predicted to pass the test (test value times the
+  // last contraction below tol, and a product accurate enough to stop on);
+  // otherwise the returned iterate is copied after the loop
+  bool likely_final = false;
+  int copied_it = -1;
+  double prev_test = -1.0;
   for (int it = 0; it < max_iter; ++it) {
+    if (hz && likely_final) {
+      // the output buffer of this evaluation must not still be copied out
+      const int nxt = free_buffer(cur, base);
+      if (h->zcopied[nxt]) CK(cudaStreamWaitEvent(s, h->zcopied[nxt], 0));
+      CK(cudaEventRecord(h->zready, s));
+      CK(cudaStreamWaitEvent(h->cs, h->zready, 0));
+      CK(cudaMemcpy2DAsync(hz->Z, (size_t)hz->ldz * zes, h->z[cur].p, (size_t)p.npad * zes,
+                           (size_t)p.n * zes, (size_t)p.k, cudaMemcpyDeviceToHost, h->cs));
+      CK(cudaEventRecord(h->zcopied[cur], h->cs));
+      copied_it = it;
+    }
     v = evaluate(h, p, cur, base, stage, passes, rebase, &tm);
     if (v != IPT_OK) break;
     launch_control(dst(h), ca, s);
@@ -683,6 +715,12 @@ ipt_status solve_dense(ipt_handle* h, int64_t n, const void* M, int64_t ldm, int
     stage = h->hst->stage;
     passes = h->hst->passes;
     rebase = h->hst->rebase;
+    if (hz) {
+      const double test = opt.stop == IPT_STOP_INCREMENT ? h->hst->inc : h->hst->rho;
+      const double q = prev_test > 0.0 ? std::min(test / prev_test, 1.0) : 1.0;
+      likely_final = (!p.staged || h->hst->accurate) && test * q <= tol;
+      prev_test = test;
+    }
   }
   if (v != IPT_OK) {
     out->status = v;
@@ -706,9 +744,21 @@ ipt_status solve_dense(ipt_handle* h, int64_t n, const void* M, int64_t ldm, int
   }
   launch_lambda((const double*)h->theta.p, (const int32_t*)h->icol.p, (const double*)h->d.p,
                 p.k, lambda, s);
-  launch_copy_z(h->z[ans].p, p.f64 ? 1 : 0, p.npad, p.n, p.k, Z, ldz,
-                z_dtype == IPT_DTYPE_F64 ? 1 : 0, s);
-  h->launches += 2;
+  h->launches += 1;
+  if (hz) {
+    if (copied_it != (int)hs.iter - 1) {
+      // the returned iterate was not copied out beside its evaluation
+      CK(cudaStreamSynchronize(h->cs));
+      CK(cudaMemcpy2DAsync(hz->Z, (size_t)hz->ldz * zes, h->z[ans].p, (size_t)p.npad * zes,
+                           (size_t)p.n * zes, (size_t)p.k, cudaMemcpyDeviceToHost, s));
+    } else {
+      CK(cudaStreamSynchronize(h->cs));
+    }
+  } else {
+    launch_copy_z(h->z[ans].p, p.f64 ? 1 : 0, p.npad, p.n, p.k, Z, ldz,
+                  z_dtype == IPT_DTYPE_F64 ? 1 : 0, s);
+    h->launches += 1;
+  }
   if (tm.on) cudaEventRecord(h->ev[7], s);
   if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) {
     out->status = IPT_CUDA_ERROR;
@@ -797,6 +847,10 @@ ipt_status ipt_destroy(ipt_handle* h) {
     if (h->ev[i]) cudaEventDestroy(h->ev[i]);
   for (int i = 0; i < 4 * kCsrChunk; ++i)
     if (h->evb[i]) cudaEventDestroy(h->evb[i]);
+  if (h->zready) cudaEventDestroy(h->zready);
+  for (int b = 0; b < 3; ++b)
+    if (h->zcopied[b]) cudaEventDestroy(h->zcopied[b]);
+  if (h->cs) cudaStreamDestroy(h->cs);
   if (h->hst) cudaFreeHost(h->hst);
   if (h->hinit) cudaFreeHost(h->hinit);
   if (h->hmeta) cudaFreeHost(h->hmeta);
@@ -834,6 +888,15 @@ ipt_status ipt_solve_dense_host(ipt_handle* h, int64_t n, const void* M, int64_t
   CK(ensure(h->hLam, (size_t)k * 8));
   CK(ensure(h->hZ, (size_t)n * k * ez));
   CK(cudaMemcpy2DAsync(h->hM.p, n * em, M, ldm * em, n * em, n, cudaMemcpyHostToDevice, s));
+  const bool iter_f64 = o.precision == IPT_PREC_F64;
+  const bool direct = o.accel == IPT_ACCEL_NONE && (z_dtype == IPT_DTYPE_F64) == iter_f64;
+  HostOut ho;
+  if (direct) {
+    if (!h->cs) CK(cudaStreamCreateWithFlags(&h->cs, cudaStreamNonBlocking));
+    if (!h->zready) CK(cudaEventCreateWithFlags(&h->zready, cudaEventDisableTiming));
+    for (int b = 0; b < 3; ++b)
+      if (!h->zcopied[b]) CK(cudaEventCreateWithFlags(&h->zcopied[b], cudaEventDisableTiming));
+  }
   const double* dth = nullptr;
   const int32_t* dcols = nullptr;
   if (theta) {
@@ -846,13 +909,22 @@ ipt_status ipt_solve_dense_host(ipt_handle* h, int64_t n, const void* M, int64_t
     CK(cudaMemcpyAsync(h->hCols.p, cols, (size_t)k * 4, cudaMemcpyHostToDevice, s));
     dcols = (const int32_t*)h->hCols.p;
   }
+  // the iterate is copied straight from the solver's buffers to Z when its
+  // dtype is Z's (FP32 iterate unless the FP64 product is asked for) and the
+  // Picard loop runs; otherwise through a device copy
+  if (direct) {
+    ho.Z = Z;
+    ho.ldz = ldz;
+  }
   v = solve_dense(h, n, h->hM.p, n, m_dtype, dth, k, dcols, tol, max_iter, &o,
-                  (double*)h->hLam.p, h->hZ.p, n, z_dtype, out);
+                  (double*)h->hLam.p, h->hZ.p, n, z_dtype, out, direct ? &ho : nullptr);
   if (v == IPT_OK || v == IPT_MAXITER || v == IPT_DIVERGED) {
     CK(cudaMemcpyAsync(lambda, h->hLam.p, (size_t)k * 8, cudaMemcpyDeviceToHost, s));
-    CK(cudaMemcpy2DAsync(Z, ldz * ez, h->hZ.p, n * ez, n * ez, k, cudaMemcpyDeviceToHost, s));
+    if (!direct)
+      CK(cudaMemcpy2DAsync(Z, ldz * ez, h->hZ.p, n * ez, n * ez, k, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
   }
+  if (direct && h->cs) cudaStreamSynchronize(h->cs);  // no copy out may outlive the call
   return v;
 }
 

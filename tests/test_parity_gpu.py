@@ -246,13 +246,23 @@ def test_divergence_and_cycle_statuses(ipt):
     assert info["status"] == "MAXITER"
 
 
-def test_host_entry_point_matches_device_entry_point(ipt):
-    M, th = w.dense_symmetric(600, 1e-3, seed=4, theta_step=0.125)
+@pytest.mark.parametrize("precision,z_dtype,max_iter,status", [
+    ("staged", torch.float32, 50, "OK"),      # iterate copied out while it is tested
+    ("staged", torch.float64, 50, "OK"),      # through a device conversion
+    ("f32", torch.float32, 2, "MAXITER"),     # the last tested iterate
+    ("fp16x3", torch.float32, 1, "MAXITER"),  # Z = E
+    ("f64", torch.float64, 50, "OK")])
+def test_host_entry_point_matches_device_entry_point(ipt, precision, z_dtype, max_iter, status):
+    n = 600
+    M, th = w.dense_symmetric(n, 1e-3, seed=4, theta_step=0.125)
     Mt = torch.as_tensor(M, dtype=torch.float32).pin_memory()
     s = ipt.Solver()
-    lam_h, Z_h, info_h = s.solve_dense_host(Mt, tol=1e-6, max_iter=50)
-    lam_d, Z_d, info_d = s.solve_dense(Mt.cuda(), tol=1e-6, max_iter=50)
-    assert info_h["status"] == info_d["status"] == "OK"
+    zt = torch.empty((n, n), dtype=z_dtype).pin_memory()
+    lam_h, Z_h, info_h = s.solve_dense_host(Mt, tol=1e-6, max_iter=max_iter,
+                                            precision=precision, z_dtype=z_dtype, zt_out=zt)
+    lam_d, Z_d, info_d = s.solve_dense(Mt.cuda(), tol=1e-6, max_iter=max_iter,
+                                       precision=precision, z_dtype=z_dtype)
+    assert info_h["status"] == info_d["status"] == status
     assert info_h["iterations"] == info_d["iterations"]
     assert torch.equal(lam_h, lam_d.cpu()) and torch.equal(Z_h, Z_d.cpu())
 
