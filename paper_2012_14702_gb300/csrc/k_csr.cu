@@ -250,14 +250,28 @@ __global__ void __launch_bounds__(256, 4)
           v = m == j ? T(0) : ldval<T>(vals, e, v_dtype);
         }
         const int cnt = min(16, e1 - eb);
-        for (int q = 0; q < cnt; ++q) {
-          const int mq = __shfl_sync(hmask, m, q, 16);
-          const T vq = __shfl_sync(hmask, v, q, 16);
-          const V4 z = *reinterpret_cast<const V4*>(Zin + (int64_t)mq * kk + cb);
-          acc[0] = fma(vq, z.x, acc[0]);
-          acc[1] = fma(vq, z.y, acc[1]);
-          acc[2] = fma(vq, z.z, acc[2]);
-          acc[3] = fma(vq, z.w, acc[3]);
+        // four gathers in flight at a time (entries past the row's end are
+        // (row j, weight 0): valid addresses that add nothing); the sums keep
+        // the entry order
+        for (int q = 0; q < cnt; q += 4) {
+          int mq[4];
+          T vq[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            mq[u] = __shfl_sync(hmask, m, q + u, 16);
+            vq[u] = __shfl_sync(hmask, v, q + u, 16);
+          }
+          V4 z[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+            z[u] = *reinterpret_cast<const V4*>(Zin + (int64_t)mq[u] * kk + cb);
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            acc[0] = fma(vq[u], z[u].x, acc[0]);
+            acc[1] = fma(vq[u], z[u].y, acc[1]);
+            acc[2] = fma(vq[u], z[u].z, acc[2]);
+            acc[3] = fma(vq[u], z[u].w, acc[3]);
+          }
         }
       }
       if (!live) continue;
