@@ -365,7 +365,9 @@ ipt_status evaluate(ipt_handle* h, const Plan& p, int cur, int base, int stage, 
       const float* zb = base >= 0 ? (const float*)h->z[base].p : nullptr;
       launch_prepass_tc((const float*)h->drow.p, (const float*)h->z[cur].p, zb, p.npad,
                         (const int32_t*)h->icol.p, p.kpad, p.bf16 ? 1 : 0, dd,
-                        (uint16_t*)h->wh.p, (uint16_t*)h->wl.p, (float*)h->sinv.p, st, s);
+                        (uint16_t*)h->wh.p,
+                        passes == 1 ? nullptr : (uint16_t*)h->wl.p,  // lo part for 3 passes
+                        (float*)h->sinv.p, st, s);
       if (t) CK(cudaEventRecord(ev[1], s));
       a.rinv = (const float*)h->rinv.p;
       a.sinv = (const float*)h->sinv.p;

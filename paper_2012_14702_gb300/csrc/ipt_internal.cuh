@@ -119,6 +119,7 @@ void launch_convert_m64(const void* M, int64_t ldm, int m_dtype, int n, int npad
 // iteration pieces (k_iter.cu)
 void launch_prepass(const void* Drow, const void* Z, int f64, int64_t ld, const int32_t* icol,
                     int kpad, double* d, DevState* st, cudaStream_t s);
+// Wl == nullptr: the lo part is not written (a 1-pass product follows)
 void launch_prepass_tc(const float* Drow, const float* Z, const float* Zbase, int64_t ld,
                        const int32_t* icol, int kpad, int bf16, double* d, uint16_t* Wh,
                        uint16_t* Wl, float* sinv, DevState* st, cudaStream_t s);

@@ -131,7 +131,7 @@ __global__ void k_prepass_tc(const float* __restrict__ Drow, const float* __rest
     split16(y.z * sc, BF16, h[2], l[2]);
     split16(y.w * sc, BF16, h[3], l[3]);
     h2[m] = make_uint2(h[0] | ((uint32_t)h[1] << 16), h[2] | ((uint32_t)h[3] << 16));
-    l2[m] = make_uint2(l[0] | ((uint32_t)l[1] << 16), l[2] | ((uint32_t)l[3] << 16));
+    if (Wl) l2[m] = make_uint2(l[0] | ((uint32_t)l[1] << 16), l[2] | ((uint32_t)l[3] << 16));
   }
   if (lane == 0) {
     d[c] = tot;
@@ -212,7 +212,7 @@ __global__ void __launch_bounds__(1024)
       split16(y[q].z * sc, BF16, h[2], l[2]);
       split16(y[q].w * sc, BF16, h[3], l[3]);
       h2[m] = make_uint2(h[0] | ((uint32_t)h[1] << 16), h[2] | ((uint32_t)h[3] << 16));
-      l2[m] = make_uint2(l[0] | ((uint32_t)l[1] << 16), l[2] | ((uint32_t)l[3] << 16));
+      if (Wl) l2[m] = make_uint2(l[0] | ((uint32_t)l[1] << 16), l[2] | ((uint32_t)l[3] << 16));
     }
   }
   if (tid == 0) {

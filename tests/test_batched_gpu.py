@@ -150,3 +150,29 @@ def test_batched_full_size_sampled_problems(ipt):
         Zg = Z[offs[p]:offs[p + 1]].cpu().numpy().reshape(n, n).T
         err = np.linalg.norm(Zg - ref["Z"]) / np.linalg.norm(ref["Z"] - np.eye(n))
         assert err <= 1e-4, (p, err)
+
+
+def test_batched_largest_orders(ipt):
+    """Orders up to the 1024 limit in one batch (scratch sized by the largest)."""
+    mats = []
+    g = w.rng(31)
+    for n in [1024, 700, 1, 513]:
+        a = g.standard_normal((n, n)) * 1e-2 / np.sqrt(n)
+        a = np.triu(a, 1)
+        a = a + a.T
+        a[np.diag_indices(n)] = np.arange(1, n + 1) * 1.0
+        mats.append(a)
+    sizes, flat = pack(mats)
+    lam, Z, status, iters, info = ipt.Solver().solve_batched(
+        sizes, torch.as_tensor(flat, dtype=torch.float32, device="cuda"), tol=1e-6, max_iter=30)
+    assert info["status"] == "OK", info
+    Zs = blocks(Z.cpu().numpy(), sizes)
+    lams = blocks(lam.cpu().numpy(), sizes, square=False)
+    for p, M in enumerate(mats):
+        n = M.shape[0]
+        ref = oracle.ipt_solve(M, tol=1e-13, max_iter=100)
+        np.testing.assert_allclose(lams[p], ref["lam"], rtol=1e-5)
+        if n > 1:
+            err = np.linalg.norm(Zs[p].reshape(n, n).T - ref["Z"]) / np.linalg.norm(
+                ref["Z"] - np.eye(n))
+            assert err <= 1e-4, (p, err)
