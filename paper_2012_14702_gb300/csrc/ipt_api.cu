@@ -521,65 +521,6 @@ ipt_status acx_loop(ipt_handle* h, const Plan& p, const ControlArgs& ca, const F
   return IPT_OK;
 }
 
-// Learned damping: buffer 0 holds Z (updated in place), buffer 1 receives
-// F(Z).  Each step: one evaluation with the stopping test, then the damping
-// kernels (per-column history, features, the model, Z <- Z + alpha (F - Z)).
-// Four steps per host synchronisation; every kernel returns at entry once the
-// controller has stopped.
-ipt_status damped_loop(ipt_handle* h, const Plan& p, const ControlArgs& ca, const FirstEval& fe,
-                       int max_iter, const void* model, Timing* tm) {
-  cudaStream_t s = h->s;
-  DevState* st = dst(h);
-  const int split = (fe.stage == IPT_PREC_BF16X3 || fe.stage == IPT_PREC_FP16X3) ? 3 : 1;
-  // layout: lam history (3 kpad FP64), inc history (3 kpad), features (6 kpad),
-  // alphas (kpad), state (kpad is a multiple of 256, so every part is aligned)
-  double* hlam = (double*)h->damp.p;
-  float* hinc = (float*)(hlam + (size_t)3 * p.kpad);
-  float* X = hinc + (size_t)3 * p.kpad;
-  float* alpha = X + (size_t)6 * p.kpad;
-  DampState* ds = reinterpret_cast<DampState*>(alpha + p.kpad);
-  CK(cudaMemsetAsync(h->damp.p, 0, (size_t)p.kpad * (3 * 8 + 3 * 4 + 6 * 4 + 4) + 64, s));
-  CK(cudaMemsetAsync(h->acx_acc.p, 0, (size_t)p.kpad * 2 * 8, s));
-  ControlArgs cq = ca;
-  cq.acx = 1;  // the iterate stays in buffer 0
-  int done_evals = 0;
-  for (int chunk = 0; done_evals < max_iter; ++chunk) {
-    const int nb = std::min(4, max_iter - done_evals);
-    for (int q = 0; q < nb; ++q) {
-      const int passes = (done_evals + q == 0) ? fe.passes : (p.f64 ? 1 : split);
-      ipt_status v = evaluate(h, p, 0, -1, fe.stage, passes, 0, tm, 1, nullptr, h->evb + 4 * q);
-      if (v != IPT_OK) return v;
-      launch_control(st, cq, s);
-      CK(launch_damp_step(h->z[0].p, h->z[1].p, p.f64 ? 1 : 0, p.n, p.k, p.npad,
-                          (const double*)h->theta.p, (const int32_t*)h->icol.p,
-                          (const double*)h->d.p, model, (double*)h->acx_acc.p, hinc, hlam, X,
-                          alpha, ds, st, s));
-      h->launches += 6;
-    }
-    if (cudaGetLastError() != cudaSuccess ||
-        cudaMemcpyAsync(h->hst, st, kStateHead, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-        cudaStreamSynchronize(s) != cudaSuccess)
-      return IPT_CUDA_ERROR;
-    if (chunk == 0) {
-      const ipt_status v = status_from_flags(h->hst->flags);
-      if (v != IPT_OK) return v;
-      if (tm && tm->on) {
-        float ms = 0.f;
-        if (cudaEventElapsedTime(&ms, h->ev[4], h->ev[5]) == cudaSuccess) tm->setup_ms = ms;
-      }
-    }
-    const int ran = std::min(nb, h->hst->iter - done_evals);
-    for (int q = 0; q < ran; ++q) {
-      const int passes = (done_evals + q == 0) ? fe.passes : (p.f64 ? 1 : split);
-      collect_timing(h, passes, tm, h->evb + 4 * q);
-    }
-    done_evals = h->hst->iter;
-    if (h->hst->timeout) return IPT_DEVICE_TIMEOUT;
-    if (h->hst->done) break;
-  }
-  return IPT_OK;
-}
-
 ipt_status solve_dense(ipt_handle* h, int64_t n, const void* M, int64_t ldm, int m_dtype,
                        const double* theta, int64_t k, const int32_t* cols, double tol,
                        int max_iter, const ipt_options* opt_in, double* lambda, void* Z,
@@ -616,9 +557,10 @@ ipt_status solve_dense(ipt_handle* h, int64_t n, const void* M, int64_t ldm, int
   }
   const bool acx = opt.accel == IPT_ACCEL_ACX;
   const bool damped = opt.accel == IPT_ACCEL_DAMPED;
-  // ACX and damping move the iterate outside the staged schedule's error
-  // model: a staged request runs every product as the split stage
-  const int prec = ((acx || damped) && opt.precision == IPT_PREC_STAGED)
+  // ACX moves the iterate by extrapolation, outside the staged schedule's
+  // error model: a staged request runs every product as the split stage.
+  // (Damped steps stay inside it with a step bound of 2 increments.)
+  const int prec = (acx && opt.precision == IPT_PREC_STAGED)
                        ? (opt.staged_bf16 ? IPT_PREC_BF16X3 : IPT_PREC_FP16X3)
                        : opt.precision;
   Plan p = make_plan(n, k, prec, opt.staged_bf16 != 0);
@@ -664,9 +606,25 @@ ipt_status solve_dense(ipt_handle* h, int64_t n, const void* M, int64_t ldm, int
   if (acx) {
     v = acx_loop(h, p, ca, fe, max_iter, opt.acx_sigma, &tm);
     max_iter = 0;  // the Picard loop below does not run
-  } else if (damped) {
-    v = damped_loop(h, p, ca, fe, max_iter, opt.damping_model, &tm);
-    max_iter = 0;
+  }
+  // learned damping: history, features, alphas and the damped next iterate,
+  // formed in F's buffer after each evaluation that does not stop the solve
+  double* dacc = nullptr;
+  double* hlam = nullptr;
+  float *hinc = nullptr, *X = nullptr, *alpha = nullptr;
+  DampState* ds = nullptr;
+  if (damped) {
+    ca.step_scale = 2.0;
+    // layout: lam history (3 kpad FP64), inc history (3 kpad), features
+    // (6 kpad), alphas (kpad), state (kpad is a multiple of 256: all aligned)
+    dacc = (double*)h->acx_acc.p;
+    hlam = (double*)h->damp.p;
+    hinc = (float*)(hlam + (size_t)3 * p.kpad);
+    X = hinc + (size_t)3 * p.kpad;
+    alpha = X + (size_t)6 * p.kpad;
+    ds = reinterpret_cast<DampState*>(alpha + p.kpad);
+    CK(cudaMemsetAsync(h->damp.p, 0, (size_t)p.kpad * (3 * 8 + 3 * 4 + 6 * 4 + 4) + 64, s));
+    CK(cudaMemsetAsync(dacc, 0, (size_t)p.kpad * 2 * 8, s));
   }
   const size_t zes = p.f64 ? 8 : 4;
   // host output: the iterate under test is copied out beside its evaluation
@@ -688,10 +646,18 @@ ipt_status solve_dense(ipt_handle* h, int64_t n, const void* M, int64_t ldm, int
       CK(cudaEventRecord(h->zcopied[cur], h->cs));
       copied_it = it;
     }
+    const int fbuf = free_buffer(cur, base);  // where this evaluation writes F
     v = evaluate(h, p, cur, base, stage, passes, rebase, &tm);
     if (v != IPT_OK) break;
     launch_control(dst(h), ca, s);
     h->launches += 1;
+    if (damped) {
+      CK(launch_damp_step(h->z[cur].p, h->z[fbuf].p, p.f64 ? 1 : 0, p.n, p.k, p.npad,
+                          (const double*)h->theta.p, (const int32_t*)h->icol.p,
+                          (const double*)h->d.p, opt.damping_model, dacc, hinc, hlam, X, alpha,
+                          ds, dst(h), s));
+      h->launches += 5;
+    }
     if (cudaMemcpyAsync(h->hst, dst(h), kStateHead, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess) {
       v = IPT_CUDA_ERROR;

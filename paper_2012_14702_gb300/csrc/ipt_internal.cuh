@@ -140,6 +140,7 @@ struct ControlArgs {
   int csr_n = 0;              // CSR solves: n (the window is clipped to [0, n)); 0 = dense
   int csr_window = 0;         // CSR: nonzero = evaluate only rows that can be nonzero
   int acx = 0;                // ACX: the iterate stays in buffer 0 (no ping-pong)
+  double step_scale = 1.0;    // largest ||Z_{t+1} - Z_t|| / ||F(Z_t) - Z_t|| (damping: 2)
   int test = 1;               // 0: no stopping test at this evaluation (ACX inner ones)
 };
 
@@ -162,9 +163,9 @@ struct DampState {
 };
 // After an evaluation at z (buffer) with F in f: per-column increments and
 // eigenvalues into the history, features, the model's alphas, and
-// z <- z + alpha (f - z).  acc: 2k FP64 (zero on entry, left zero); hinc: 3k
+// f <- z + alpha (f - z) (the next iterate).  acc: 2k FP64 (zero on entry, left zero); hinc: 3k
 // floats; hlam: 3k FP64; X: 6k floats; alpha: k floats.
-cudaError_t launch_damp_step(void* z, const void* f, int f64, int n, int k, int64_t ld,
+cudaError_t launch_damp_step(const void* z, void* f, int f64, int n, int k, int64_t ld,
                              const double* theta, const int32_t* icol, const double* d,
                              const void* model, double* acc, float* hinc, double* hlam,
                              float* X, float* alpha, DampState* ds, DevState* st,

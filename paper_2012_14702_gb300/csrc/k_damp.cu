@@ -1,5 +1,5 @@
-// Learned damping on the device: after an evaluation F(Z) the iterate moves
-// to Z + alpha_c (F(Z) - Z), one alpha per column, alpha_c from the damping
+// Learned damping on the device: after an evaluation F(Z) (written to its own
+// buffer) the next iterate Z + alpha_c (F(Z) - Z) replaces F there, one alpha per column, alpha_c from the damping
 // model (k_mlp.cu) fed the column's history of increment norms and
 // Rayleigh-quotient changes.  The first three steps (no history yet) and
 // every step after the fallback has tripped are plain Picard steps
@@ -105,33 +105,31 @@ __global__ void k_damp_count(DampState* ds, const DevState* st) {
   ds->steps += 1;
 }
 
-// Z <- Z + alpha_c (F - Z) in place (alpha_c = 1 before the model applies or
-// after the fallback).  Grid (column, row block).
+// F's buffer <- Z + alpha_c (F - Z): the next iterate (alpha_c = 1 before the
+// model applies or after the fallback leaves F as it is).  Grid (column, row block).
 template <typename T>
 __global__ void __launch_bounds__(256)
-    k_damp_update(T* __restrict__ z, const T* __restrict__ f, int n, int64_t ld,
+    k_damp_update(const T* __restrict__ z, T* __restrict__ f, int n, int64_t ld,
                   const float* __restrict__ alpha, const DampState* ds, const DevState* st) {
   if (st->done) return;
   const int c = blockIdx.x;
-  float a = 1.f;
-  if (ds->steps >= 3 && !ds->fallback) {
-    a = alpha[c];
-    if (!isfinite(a)) a = 1.f;
-  }
+  if (ds->steps < 3 || ds->fallback) return;
+  float a = alpha[c];
+  if (!isfinite(a)) a = 1.f;
   const int64_t col = (int64_t)c * ld;
 #pragma unroll
   for (int q = 0; q < RPT; ++q) {
     const int j = (blockIdx.y * RPT + q) * blockDim.x + threadIdx.x;
     if (j < n) {
       const T zv = z[col + j];
-      z[col + j] = zv + (T)a * (f[col + j] - zv);
+      f[col + j] = zv + (T)a * (f[col + j] - zv);
     }
   }
 }
 
 }  // namespace
 
-cudaError_t launch_damp_step(void* z, const void* f, int f64, int n, int k, int64_t ld,
+cudaError_t launch_damp_step(const void* z, void* f, int f64, int n, int k, int64_t ld,
                              const double* theta, const int32_t* icol, const double* d,
                              const void* model, double* acc, float* hinc, double* hlam,
                              float* X, float* alpha, DampState* ds, DevState* st,
@@ -147,9 +145,9 @@ cudaError_t launch_damp_step(void* z, const void* f, int f64, int n, int k, int6
   cudaError_t e = launch_mlp_forward(model, X, k, alpha, s);
   if (e != cudaSuccess) return e;
   if (f64)
-    k_damp_update<double><<<g, 256, 0, s>>>((double*)z, (const double*)f, n, ld, alpha, ds, st);
+    k_damp_update<double><<<g, 256, 0, s>>>((const double*)z, (double*)f, n, ld, alpha, ds, st);
   else
-    k_damp_update<float><<<g, 256, 0, s>>>((float*)z, (const float*)f, n, ld, alpha, ds, st);
+    k_damp_update<float><<<g, 256, 0, s>>>((const float*)z, (float*)f, n, ld, alpha, ds, st);
   return cudaGetLastError();
 }
 

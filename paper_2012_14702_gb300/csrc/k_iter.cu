@@ -571,7 +571,7 @@ __global__ void k_control(DevState* st, ControlArgs a) {
       if (passes > 0 && st->sv > 0.0 && pv > 0.0) kappa = pv / st->sv;
       st->kappa = kappa;
       const double sv_after = st->rebase ? 0.0 : st->sv;  // ||Z_t - Z_b|| bound
-      const double sv_next = sv_after + inc * sqrt(z2);    // ||Z_{t+1} - Z_b|| bound
+      const double sv_next = sv_after + a.step_scale * inc * sqrt(z2);  // ||Z_{t+1} - Z_b||
       if (st->rebase) st->base = cur;
       const double prev = st->prev_rho;
       double q = (it > 0 && prev > 0.0) ? rho / prev : inc;
