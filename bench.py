@@ -334,6 +334,9 @@ def run_batched(steps, warmup):
                     f"N(0,1)*{scale}/sqrt(n_p) symmetric, seed {seed}, all eigenpairs, "
                     f"tol 1e-6 residual",
         "ms_to_tol": ms, "problems_per_s": count / (ms / 1e3), "status": info["status"],
+        "tiles_by_class": {"n<=64": solver.batched_tiles[0], "n<=256": solver.batched_tiles[1],
+                           "n<=1024": solver.batched_tiles[2]},
+        "launch": "one CUDA graph (schedule copy, queue reset, persistent kernel)",
         "evaluations": {"min": int(its.min()), "max": int(its.max()),
                         "mean": float(its.mean())},
         "roofline": {"kernel": "k_batched (persistent, one CTA per problem, FP32 SIMT product "

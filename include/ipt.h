@@ -274,6 +274,21 @@ ipt_status ipt_solve_batched(ipt_handle* h, int64_t count, const int64_t* n, con
                              int32_t* iters, ipt_result* out);
 
 /*
+ * Output tile (rows x columns of Delta Z held by a block) of ipt_solve_batched,
+ * one per size class: n <= 64, n <= 256, n <= 1024.  Each class is tuned on
+ * the handle the first time a batch holds problems of that class (both tiles,
+ * 32 and 64, timed on up to 64 of its problems; the faster kept); a set value
+ * skips the tuning.  The solve's copy of the schedule, queue reset and kernel
+ * run as one CUDA graph, captured on the first call and replayed while the
+ * orders, pointers, tolerances and tiles repeat.
+ *   ipt_set_batched_tiles   tiles[3] host: 32, 64, or 0 = tune on first use
+ *   ipt_get_batched_tiles   tiles[3] host (written): the tiles in use, 0 = not tuned yet
+ * Both return IPT_INVALID_ARG for a NULL handle or array or another value.
+ */
+ipt_status ipt_set_batched_tiles(ipt_handle* h, const int32_t* tiles);
+ipt_status ipt_get_batched_tiles(const ipt_handle* h, int32_t* tiles);
+
+/*
  * The damping model of IPT_ACCEL_DAMPED and its training (no counterpart in the
  * paper).  A 6 -> 64 -> 64 -> 1 perceptron: h1 = tanh(x W1 + b1),
  * h2 = tanh(h1 W2 + b2), y = h2 W3 + b3, alpha = 2 / (1 + exp(-y)).  Parameters:

@@ -11,6 +11,7 @@
 
 #include <algorithm>
 #include <chrono>
+#include <vector>
 
 using namespace ipt;
 
@@ -44,6 +45,11 @@ struct ipt_handle {
   Buf acx_d, acx_acc, acx_sigma;    // ACX: d of the inner evaluations, step-length sums, steps
   Buf damp;                         // learned damping: history, features, alphas, state
   Buf bmeta, bscratch;              // batched: schedule and offsets, per-CTA iterate pairs
+  int btiles[kBatchClasses] = {};   // batched: tuned output tile per size class (0 = untuned)
+  cudaStream_t gs = nullptr;        // batched: capture stream (the handle's may be the legacy one)
+  cudaGraph_t bgraph = nullptr;     // batched: captured schedule copy + queue reset + kernel
+  cudaGraphExec_t bexec = nullptr;
+  uint64_t bkey = 0;                // hash of everything the captured graph depends on
   void* hmeta = nullptr;            // pinned staging of the batched schedule
   size_t hmeta_cap = 0;
   int* hstat = nullptr;             // pinned copy of per-problem statuses and counts
@@ -823,6 +829,9 @@ ipt_status ipt_destroy(ipt_handle* h) {
   if (h->hinit) cudaFreeHost(h->hinit);
   if (h->hmeta) cudaFreeHost(h->hmeta);
   if (h->hstat) cudaFreeHost(h->hstat);
+  if (h->bexec) cudaGraphExecDestroy(h->bexec);
+  if (h->bgraph) cudaGraphDestroy(h->bgraph);
+  if (h->gs) cudaStreamDestroy(h->gs);
   delete h;
   return IPT_OK;
 }
@@ -1168,7 +1177,9 @@ ipt_status ipt_solve_batched(ipt_handle* h, int64_t count, const int64_t* n, con
   cudaStream_t s = h->s;
   // schedule: offsets in input order, problems largest first
   const size_t cnt = (size_t)count;
-  const size_t meta_bytes = cnt * (8 + 8 + 4 + 4) + 16;
+  constexpr int kTuneSample = 64;  // problems per size class in a tuning run
+  const size_t meta_main = cnt * (8 + 8 + 4 + 4);
+  const size_t meta_bytes = meta_main + (size_t)kBatchClasses * kTuneSample * 4 + 64;
   if (h->hmeta_cap < meta_bytes) {
     if (h->hmeta) cudaFreeHost(h->hmeta);
     h->hmeta = nullptr;
@@ -1180,6 +1191,7 @@ ipt_status ipt_solve_batched(ipt_handle* h, int64_t count, const int64_t* n, con
   int64_t* v_off = m_off + cnt;
   int* nsz = reinterpret_cast<int*>(v_off + cnt);
   int* order = nsz + cnt;
+  int* sample = order + cnt;  // kBatchClasses x kTuneSample tuning schedules
   int64_t mo = 0, vo = 0;
   for (size_t p = 0; p < cnt; ++p) {
     m_off[p] = mo;
@@ -1195,25 +1207,105 @@ ipt_status ipt_solve_batched(ipt_handle* h, int64_t count, const int64_t* n, con
   CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
   const int ctas = (int)std::min<int64_t>(count, (int64_t)nsm * batched_ctas_per_sm());
   const int64_t max_n2 = max_n * max_n;
+  // the tuning schedules: up to kTuneSample problems of each class not tuned yet,
+  // evenly spread over the class (largest first)
+  int nsample[kBatchClasses] = {};
+  {
+    std::vector<int> members[kBatchClasses];
+    for (size_t i = 0; i < cnt; ++i) members[batch_class_host(nsz[order[i]])].push_back(order[i]);
+    for (int c = 0; c < kBatchClasses; ++c) {
+      if (h->btiles[c] != 0 || members[c].empty()) continue;
+      const size_t m = members[c].size(), take = std::min<size_t>(m, kTuneSample);
+      for (size_t q = 0; q < take; ++q)
+        sample[c * kTuneSample + q] = members[c][q * m / take];
+      nsample[c] = (int)take;
+    }
+  }
   CK(ensure(h->bmeta, meta_bytes + 16));
   CK(ensure(h->bscratch, (size_t)ctas * 2 * (size_t)max_n2 * 4));
   char* dm = static_cast<char*>(h->bmeta.p);
-  CK(cudaMemcpyAsync(dm, h->hmeta, cnt * (8 + 8 + 4 + 4), cudaMemcpyHostToDevice, s));
-  int* queue = reinterpret_cast<int*>(dm + cnt * (8 + 8 + 4 + 4));
-  CK(cudaMemsetAsync(queue, 0, sizeof(int), s));
+  int* queue = reinterpret_cast<int*>(dm + meta_bytes - 64);
+  const int64_t* d_moff = reinterpret_cast<const int64_t*>(dm);
+  const int64_t* d_voff = d_moff + cnt;
+  const int* d_nsz = reinterpret_cast<const int*>(dm + cnt * 16);
+  const int* d_order = reinterpret_cast<const int*>(dm + cnt * 20);
+  const int* d_sample = reinterpret_cast<const int*>(dm + meta_main);
+  bool tune = false;
+  for (int c = 0; c < kBatchClasses; ++c) tune |= nsample[c] > 0;
+  if (tune) CK(cudaMemcpyAsync(dm, h->hmeta, meta_bytes - 64, cudaMemcpyHostToDevice, s));
   Timing tm;
   tm.on = opt.record_timing != 0;
-  if (tm.on && ensure_events(h) != IPT_OK) {
+  if (ensure_events(h) != IPT_OK) {
     out->status = IPT_CUDA_ERROR;
     return IPT_CUDA_ERROR;
   }
+  // autotuner: for every size class met for the first time, time each output
+  // tile on a sample of the class's problems and keep the faster (the tuning
+  // runs write outputs that the full run below overwrites)
+  for (int c = 0; c < kBatchClasses; ++c) {
+    if (!nsample[c]) continue;
+    float best_ms = 0.f;
+    int best = 64;
+    for (int tile : {64, 32}) {
+      int tiles[kBatchClasses] = {64, 64, 64};
+      tiles[c] = tile;
+      float ms = 0.f;
+      for (int rep = 0; rep < 2; ++rep) {  // the first run warms caches and the clock
+        CK(cudaMemsetAsync(queue, 0, sizeof(int), s));
+        CK(cudaEventRecord(h->ev[0], s));
+        CK(launch_batched(M, theta, d_moff, d_voff, d_nsz, d_sample + c * kTuneSample,
+                          nsample[c], max_n2, tol, max_iter, opt.stop, opt.diverge_bound,
+                          lambda, Z, status, iters, static_cast<float*>(h->bscratch.p), queue,
+                          tiles, std::min(ctas, nsample[c]), s));
+        CK(cudaEventRecord(h->ev[1], s));
+        CK(cudaEventSynchronize(h->ev[1]));
+        CK(cudaEventElapsedTime(&ms, h->ev[0], h->ev[1]));
+      }
+      if (tile == 64 || ms < best_ms) {
+        best_ms = ms;
+        best = tile;
+      }
+    }
+    h->btiles[c] = best;
+  }
+  int tiles[kBatchClasses];
+  for (int c = 0; c < kBatchClasses; ++c) tiles[c] = h->btiles[c] ? h->btiles[c] : 64;
+  // the solve itself: schedule copy, queue reset and kernel as one CUDA graph,
+  // captured once per set of arguments and replayed while they repeat
+  uint64_t key = 1469598103934665603ull;
+  auto mix = [&](uint64_t x) { key = (key ^ x) * 1099511628211ull; };
+  for (size_t p = 0; p < cnt; ++p) mix((uint64_t)nsz[p]);
+  const void* ptrs[] = {M, theta, lambda, Z, status, iters, h->bscratch.p, h->bmeta.p, h->hmeta};
+  for (const void* q : ptrs) mix(reinterpret_cast<uintptr_t>(q));
+  uint64_t tb;
+  memcpy(&tb, &tol, 8);
+  mix(tb);
+  memcpy(&tb, &opt.diverge_bound, 8);
+  mix(tb);
+  mix((uint64_t)max_iter);
+  mix((uint64_t)opt.stop);
+  mix((uint64_t)cnt);
+  mix((uint64_t)ctas);
+  for (int c = 0; c < kBatchClasses; ++c) mix((uint64_t)tiles[c]);
+  if (!h->bexec || h->bkey != key) {
+    if (h->bexec) cudaGraphExecDestroy(h->bexec);
+    if (h->bgraph) cudaGraphDestroy(h->bgraph);
+    h->bexec = nullptr;
+    h->bgraph = nullptr;
+    if (!h->gs) CK(cudaStreamCreateWithFlags(&h->gs, cudaStreamNonBlocking));
+    cudaStream_t cs = h->gs;
+    CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    cudaMemcpyAsync(dm, h->hmeta, meta_main, cudaMemcpyHostToDevice, cs);
+    cudaMemsetAsync(queue, 0, sizeof(int), cs);
+    launch_batched(M, theta, d_moff, d_voff, d_nsz, d_order, (int)count, max_n2, tol, max_iter,
+                   opt.stop, opt.diverge_bound, lambda, Z, status, iters,
+                   static_cast<float*>(h->bscratch.p), queue, tiles, ctas, cs);
+    CK(cudaStreamEndCapture(cs, &h->bgraph));
+    CK(cudaGraphInstantiate(&h->bexec, h->bgraph, 0));
+    h->bkey = key;
+  }
   if (tm.on) cudaEventRecord(h->ev[2], s);
-  CK(launch_batched(M, theta, reinterpret_cast<const int64_t*>(dm),
-                    reinterpret_cast<const int64_t*>(dm) + cnt,
-                    reinterpret_cast<const int*>(dm + cnt * 16),
-                    reinterpret_cast<const int*>(dm + cnt * 20), (int)count, max_n2, tol,
-                    max_iter, opt.stop, opt.diverge_bound, lambda, Z, status, iters,
-                    static_cast<float*>(h->bscratch.p), queue, ctas, s));
+  CK(cudaGraphLaunch(h->bexec, s));
   if (tm.on) cudaEventRecord(h->ev[3], s);
   // per-problem outcomes for the aggregate result
   const size_t stat_bytes = cnt * 2 * sizeof(int);
@@ -1243,6 +1335,20 @@ ipt_status ipt_solve_batched(ipt_handle* h, int64_t count, const int64_t* n, con
   out->wall_ms =
       std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
   return (ipt_status)agg;
+}
+
+ipt_status ipt_set_batched_tiles(ipt_handle* h, const int32_t* tiles) {
+  if (!h || !tiles) return IPT_INVALID_ARG;
+  for (int c = 0; c < kBatchClasses; ++c)
+    if (tiles[c] != 0 && tiles[c] != 32 && tiles[c] != 64) return IPT_INVALID_ARG;
+  for (int c = 0; c < kBatchClasses; ++c) h->btiles[c] = tiles[c];
+  return IPT_OK;
+}
+
+ipt_status ipt_get_batched_tiles(const ipt_handle* h, int32_t* tiles) {
+  if (!h || !tiles) return IPT_INVALID_ARG;
+  for (int c = 0; c < kBatchClasses; ++c) tiles[c] = h->btiles[c];
+  return IPT_OK;
 }
 
 ipt_status ipt_damping_forward(int64_t B, const void* params, const float* x, float* alpha,

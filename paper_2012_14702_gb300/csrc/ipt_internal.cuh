@@ -171,13 +171,18 @@ cudaError_t launch_damp_step(const void* z, void* f, int f64, int n, int k, int6
                              float* X, float* alpha, DampState* ds, DevState* st,
                              cudaStream_t s);
 
-// Batched solve (k_batched.cu): largest problem order n.
+// Batched solve (k_batched.cu): largest problem order n; problem size classes
+// (n <= 64, <= 256, larger) each with their own output tile (32 or 64, host
+// array `tiles`).
 constexpr int kBatchMaxN = 1024;
+constexpr int kBatchClasses = 3;
+inline int batch_class_host(int64_t n) { return n <= 64 ? 0 : (n <= 256 ? 1 : 2); }
 cudaError_t launch_batched(const float* M, const double* theta, const int64_t* m_off,
                            const int64_t* v_off, const int* nsz, const int* order, int count,
                            int64_t max_n2, double tol, int max_iter, int stop,
                            double diverge_bound, double* lambda, float* Z, int* status,
-                           int* iters, float* scratch, int* queue, int ctas, cudaStream_t s);
+                           int* iters, float* scratch, int* queue, const int* tiles, int ctas,
+                           cudaStream_t s);
 int batched_ctas_per_sm();
 
 // Alg. 3 extrapolation of order p (2 or 3) in place: z (buffer of the

@@ -21,7 +21,7 @@ namespace ipt {
 
 namespace {
 
-constexpr int TB = 64;   // output tile (rows and columns)
+constexpr int TB = 64;   // largest output tile (rows and columns)
 constexpr int TK = 32;   // product depth per shared-memory stage
 constexpr int NT = 256;  // threads per CTA (16 x 16, 4 x 4 outputs each)
 
@@ -42,7 +42,10 @@ struct BatchArgs {
   int count;
   int max_iter, stop;
   double tol, diverge_bound;
+  int tiles[kBatchClasses];  // output tile (32 or 64) per size class
 };
+
+__device__ __forceinline__ int batch_class(int n) { return n <= 64 ? 0 : (n <= 256 ? 1 : 2); }
 
 struct __align__(16) Shared {
   float As[TB][TK + 1];  // Delta tile, [row][k]
@@ -65,6 +68,109 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
   return t;
 }
 
+// One product evaluation of a problem (P = Delta_{:,c} + Delta W, the map in
+// the tile epilogue), output tiles TBT x TBT (32 or 64), each of the 16 x 16
+// threads owning R x R outputs.
+template <int TBT>
+__device__ __forceinline__ void product_map(const BatchArgs& a, const float* __restrict__ M,
+                                            int n, const float* __restrict__ zc,
+                                            float* __restrict__ zn, Shared& sh, float& s_inc,
+                                            float& s_z, float& s_r) {
+  constexpr int R = TBT / 16;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  (void)a;
+  // P = Delta_{:,c} + Delta W tile by tile, the map in the epilogue.  Each
+  // column block starts with its diagonal tile, whose P_cc give the d_c
+  // (d_c = (Delta Z)_cc, Eq. dyn) that every tile of the block needs.
+  const int nt = (n + TBT - 1) / TBT;
+  for (int cb = 0; cb < nt; ++cb)
+    for (int rb = 0; rb < nt; ++rb) {
+      const int c0t = cb * TBT, r0t = ((cb + rb) % nt) * TBT;
+      float acc[R][R] = {};
+      // the next stage's tiles are fetched into registers while the
+      // current one is multiplied (A: Delta rows r0t.., columns k0..,
+      // Delta_jj = M_jj - theta_j formed in FP64; B: W rows k0..,
+      // columns c0t.., W_cc = Z_cc - 1 = 0)
+      float pa[TBT * TK / NT], pb[TBT * TK / NT];
+      auto fetch = [&](int k0) {
+#pragma unroll
+        for (int r = 0; r < TBT * TK / NT; ++r) {
+          const int e = tid + r * NT;
+          const int j = r0t + e / TK, m = k0 + e % TK;
+          float v = 0.f;
+          if (j < n && m < n) v = j != m ? M[(int64_t)j * n + m] : sh.ddiag[j];
+          pa[r] = v;
+          const int m2 = k0 + e / TBT, c = c0t + e % TBT;
+          pb[r] = (m2 < n && c < n && m2 != c) ? zc[(int64_t)m2 * n + c] : 0.f;
+        }
+      };
+      auto stage = [&]() {
+#pragma unroll
+        for (int r = 0; r < TBT * TK / NT; ++r) {
+          const int e = tid + r * NT;
+          sh.As[e / TK][e % TK] = pa[r];
+          sh.Bs[e / TBT][e % TBT] = pb[r];
+        }
+      };
+      fetch(0);
+      stage();
+      __syncthreads();
+      for (int k0 = 0; k0 < n; k0 += TK) {
+        const bool more = k0 + TK < n;
+        if (more) fetch(k0 + TK);
+#pragma unroll 8
+        for (int kk = 0; kk < TK; ++kk) {
+          float av[R], bv[R];
+#pragma unroll
+          for (int i = 0; i < R; ++i) {
+            av[i] = sh.As[ty * R + i][kk];
+            bv[i] = sh.Bs[kk][tx * R + i];
+          }
+#pragma unroll
+          for (int i = 0; i < R; ++i)
+#pragma unroll
+            for (int q = 0; q < R; ++q) acc[i][q] = fmaf(av[i], bv[q], acc[i][q]);
+        }
+        __syncthreads();
+        if (more) {
+          stage();
+          __syncthreads();
+        }
+      }
+      if (rb == 0) {  // diagonal tile (uniform over the CTA)
+#pragma unroll
+        for (int i = 0; i < R; ++i)
+#pragma unroll
+          for (int q = 0; q < R; ++q) {
+            const int c = c0t + tx * R + q;
+            if (ty * R + i == tx * R + q && c < n)
+              sh.d[c] = (double)(sh.ddiag[c] + acc[i][q]);
+          }
+        __syncthreads();
+      }
+#pragma unroll
+      for (int i = 0; i < R; ++i) {
+        const int j = r0t + ty * R + i;
+        if (j >= n) continue;
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+          const int c = c0t + tx * R + q;
+          if (c >= n) continue;
+          const float z = zc[(int64_t)j * n + c];
+          // P_jc = Delta_jc (the E part, exact) + (Delta W)_jc
+          const float pjc = (j != c ? M[(int64_t)j * n + c] : 0.f) + acc[i][q];
+          const float gap = gap2f(sh.th_hi[j], sh.th_lo[j], sh.th_hi[c], sh.th_lo[c]);
+          float f, r;
+          map_entry<float>(z, pjc, (float)sh.d[c], gap, j == c, f, r);
+          zn[(int64_t)j * n + c] = f;
+          s_inc = fmaf(f - z, f - z, s_inc);
+          s_z = fmaf(z, z, s_z);
+          s_r = fmaf(r, r, s_r);
+        }
+      }
+    }
+}
+
 __global__ void __launch_bounds__(NT, 3)
     k_batched(BatchArgs a) {
   __shared__ Shared sh;
@@ -80,6 +186,7 @@ __global__ void __launch_bounds__(NT, 3)
     __syncthreads();
     if (p < 0) return;
     const int n = a.nsz[p];
+    const int tb = a.tiles[batch_class(n)];
     const float* M = a.M + a.m_off[p];
     const int64_t vo = a.v_off[p];
     // theta (given or diag(M)) as an exact FP32 pair; degenerate / non-finite check
@@ -124,95 +231,8 @@ __global__ void __launch_bounds__(NT, 3)
           }
         s_z = tid == 0 ? (float)n : 0.f;
       } else {
-        // P = Delta_{:,c} + Delta W tile by tile, the map in the epilogue.  Each
-        // column block starts with its diagonal tile, whose P_cc give the d_c
-        // (d_c = (Delta Z)_cc, Eq. dyn) that every tile of the block needs.
-        const int nt = (n + TB - 1) / TB;
-        for (int cb = 0; cb < nt; ++cb)
-          for (int rb = 0; rb < nt; ++rb) {
-            const int c0t = cb * TB, r0t = ((cb + rb) % nt) * TB;
-            float acc[4][4] = {};
-            // the next stage's tiles are fetched into registers while the
-            // current one is multiplied (A: Delta rows r0t.., columns k0..,
-            // Delta_jj = M_jj - theta_j formed in FP64; B: W rows k0..,
-            // columns c0t.., W_cc = Z_cc - 1 = 0)
-            float pa[TB * TK / NT], pb[TB * TK / NT];
-            auto fetch = [&](int k0) {
-#pragma unroll
-              for (int r = 0; r < TB * TK / NT; ++r) {
-                const int e = tid + r * NT;
-                const int j = r0t + e / TK, m = k0 + e % TK;
-                float v = 0.f;
-                if (j < n && m < n) v = j != m ? M[(int64_t)j * n + m] : sh.ddiag[j];
-                pa[r] = v;
-                const int m2 = k0 + e / TB, c = c0t + e % TB;
-                pb[r] = (m2 < n && c < n && m2 != c) ? zc[(int64_t)m2 * n + c] : 0.f;
-              }
-            };
-            auto stage = [&]() {
-#pragma unroll
-              for (int r = 0; r < TB * TK / NT; ++r) {
-                const int e = tid + r * NT;
-                sh.As[e / TK][e % TK] = pa[r];
-                sh.Bs[e / TB][e % TB] = pb[r];
-              }
-            };
-            fetch(0);
-            stage();
-            __syncthreads();
-            for (int k0 = 0; k0 < n; k0 += TK) {
-              const bool more = k0 + TK < n;
-              if (more) fetch(k0 + TK);
-#pragma unroll 8
-              for (int kk = 0; kk < TK; ++kk) {
-                float av[4];
-#pragma unroll
-                for (int i = 0; i < 4; ++i) av[i] = sh.As[ty * 4 + i][kk];
-                const float4 b4 = *reinterpret_cast<const float4*>(&sh.Bs[kk][tx * 4]);
-                const float bv[4] = {b4.x, b4.y, b4.z, b4.w};
-#pragma unroll
-                for (int i = 0; i < 4; ++i)
-#pragma unroll
-                  for (int q = 0; q < 4; ++q) acc[i][q] = fmaf(av[i], bv[q], acc[i][q]);
-              }
-              __syncthreads();
-              if (more) {
-                stage();
-                __syncthreads();
-              }
-            }
-            if (rb == 0) {  // diagonal tile (uniform over the CTA)
-#pragma unroll
-              for (int i = 0; i < 4; ++i)
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                  const int c = c0t + tx * 4 + q;
-                  if (ty * 4 + i == tx * 4 + q && c < n)
-                    sh.d[c] = (double)(sh.ddiag[c] + acc[i][q]);
-                }
-              __syncthreads();
-            }
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-              const int j = r0t + ty * 4 + i;
-              if (j >= n) continue;
-#pragma unroll
-              for (int q = 0; q < 4; ++q) {
-                const int c = c0t + tx * 4 + q;
-                if (c >= n) continue;
-                const float z = zc[(int64_t)j * n + c];
-                // P_jc = Delta_jc (the E part, exact) + (Delta W)_jc
-                const float pjc = (j != c ? M[(int64_t)j * n + c] : 0.f) + acc[i][q];
-                const float gap = gap2f(sh.th_hi[j], sh.th_lo[j], sh.th_hi[c], sh.th_lo[c]);
-                float f, r;
-                map_entry<float>(z, pjc, (float)sh.d[c], gap, j == c, f, r);
-                zn[(int64_t)j * n + c] = f;
-                s_inc = fmaf(f - z, f - z, s_inc);
-                s_z = fmaf(z, z, s_z);
-                s_r = fmaf(r, r, s_r);
-              }
-            }
-          }
+        if (tb == 32) product_map<32>(a, M, n, zc, zn, sh, s_inc, s_z, s_r);
+        else product_map<64>(a, M, n, zc, zn, sh, s_inc, s_z, s_r);
       }
       // norms of this evaluation, Alg. 2's test, divergence, cap
       const double t_inc = block_sum((double)s_inc, sh.red[0]);
@@ -266,8 +286,10 @@ cudaError_t launch_batched(const float* M, const double* theta, const int64_t* m
                            const int64_t* v_off, const int* nsz, const int* order, int count,
                            int64_t max_n2, double tol, int max_iter, int stop,
                            double diverge_bound, double* lambda, float* Z, int* status,
-                           int* iters, float* scratch, int* queue, int ctas, cudaStream_t s) {
+                           int* iters, float* scratch, int* queue, const int* tiles, int ctas,
+                           cudaStream_t s) {
   BatchArgs a;
+  for (int c = 0; c < kBatchClasses; ++c) a.tiles[c] = tiles[c] == 32 ? 32 : 64;
   a.M = M;
   a.theta = theta;
   a.m_off = m_off;

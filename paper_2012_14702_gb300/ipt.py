@@ -245,6 +245,21 @@ class Solver:
                                _ptr(Z), _ptr(status), _ptr(iters), C.byref(r))
         return lam, Z, status, iters, r.to_dict()
 
+    @property
+    def batched_tiles(self):
+        """Output tile per size class (n <= 64, <= 256, <= 1024) of solve_batched;
+        0 = not tuned yet.  Assign a 3-sequence of 32/64/0 to fix or re-tune them."""
+        t = (C.c_int32 * 3)()
+        if _lib.ipt_get_batched_tiles(self._h, t) != 0:
+            raise RuntimeError("ipt_get_batched_tiles failed")
+        return tuple(t)
+
+    @batched_tiles.setter
+    def batched_tiles(self, tiles):
+        t = (C.c_int32 * 3)(*[int(x) for x in tiles])
+        if _lib.ipt_set_batched_tiles(self._h, t) != 0:
+            raise ValueError(f"batched tiles must be 32, 64 or 0, got {tuple(tiles)}")
+
     def step_dense(self, M, Z, theta=None, cols=None, precision="f32"):
         """One evaluation of F (Eq. dyn) at Z (n, k).  Returns (F (n, k), lam, norms)."""
         M = _dev(M, name="M")
@@ -295,6 +310,9 @@ def _batched_argtypes():
                                        C.POINTER(Options), _vp, _vp, _vp, _vp,
                                        C.POINTER(Result)]
     _lib.ipt_solve_batched.restype = _i32
+    for name in ("ipt_set_batched_tiles", "ipt_get_batched_tiles"):
+        getattr(_lib, name).argtypes = [_vp, C.POINTER(C.c_int32)]
+        getattr(_lib, name).restype = _i32
 
 
 _batched_argtypes()

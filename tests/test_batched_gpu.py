@@ -176,3 +176,75 @@ def test_batched_largest_orders(ipt):
             err = np.linalg.norm(Zs[p].reshape(n, n).T - ref["Z"]) / np.linalg.norm(
                 ref["Z"] - np.eye(n))
             assert err <= 1e-4, (p, err)
+
+
+def test_batched_tiles_give_identical_iterates(ipt):
+    """Both output tiles accumulate every product entry in the same order: forced
+    32 and 64 tiles give bit-identical fixed-iteration iterates, which match the
+    oracle."""
+    mats = small_batch(seed=24)
+    sizes, flat = pack(mats)
+    Mg = torch.as_tensor(flat, dtype=torch.float32, device="cuda")
+    outs = []
+    for tiles in [(32, 32, 32), (64, 64, 64), (32, 64, 32)]:
+        s = ipt.Solver()
+        s.batched_tiles = tiles
+        lam, Z, status, iters, _ = s.solve_batched(sizes, Mg, tol=0.0, max_iter=3,
+                                                   stop="increment")
+        assert s.batched_tiles == tiles
+        outs.append((lam, Z, iters))
+    for lam, Z, iters in outs[1:]:
+        assert torch.equal(lam, outs[0][0]) and torch.equal(Z, outs[0][1])
+        assert torch.equal(iters, outs[0][2])
+    Zs = blocks(outs[0][1].cpu().numpy(), sizes)
+    its = outs[0][2].cpu().numpy()
+    for p in [4, 9, 10]:
+        M, n = mats[p], mats[p].shape[0]
+        ref = oracle.ipt_solve(M, tol=0.0, max_iter=int(its[p]), stop="increment")
+        scale = max(np.max(np.abs(ref["Z"] - np.eye(n))), 1e-30)
+        assert np.max(np.abs(Zs[p].reshape(n, n).T - ref["Z"])) <= 2e-5 * scale + 1e-7
+
+
+def test_batched_autotuner_tunes_the_classes_met(ipt):
+    s = ipt.Solver()
+    assert s.batched_tiles == (0, 0, 0)
+    mats = small_batch(seed=25)  # orders up to 257: classes 0, 1 and 2
+    sizes, flat = pack(mats[:8])  # orders <= 100: classes 0 and 1 only
+    Mg = torch.as_tensor(flat, dtype=torch.float32, device="cuda")
+    *_, info = s.solve_batched(sizes, Mg, tol=1e-6, max_iter=50)
+    assert info["status"] == "OK"
+    t = s.batched_tiles
+    assert t[0] in (32, 64) and t[1] in (32, 64) and t[2] == 0, t
+    with pytest.raises(ValueError):
+        s.batched_tiles = (48, 64, 64)
+    assert s.batched_tiles == t
+
+
+def test_batched_graph_replay_reads_current_inputs(ipt):
+    """The captured graph is replayed while orders, pointers and tolerances
+    repeat: new contents of the same buffers give that batch's solution, and a
+    changed tolerance is captured anew."""
+    a = small_batch(seed=26)
+    b = small_batch(seed=27)
+    sizes, fa = pack(a)
+    _, fb = pack(b)
+    s = ipt.Solver()
+    Mg = torch.as_tensor(fa, dtype=torch.float32, device="cuda")
+    lam_a, Z_a, *_ = [x.clone() if torch.is_tensor(x) else x
+                      for x in s.solve_batched(sizes, Mg, tol=1e-6, max_iter=50)]
+    Mg.copy_(torch.as_tensor(fb, dtype=torch.float32))
+    lam_b, Z_b, _, _, info = s.solve_batched(sizes, Mg, tol=1e-6, max_iter=50)
+    assert info["status"] == "OK"
+    fresh = ipt.Solver()
+    fresh.batched_tiles = s.batched_tiles
+    lam_r, Z_r, *_ = fresh.solve_batched(sizes, torch.as_tensor(fb, dtype=torch.float32,
+                                                               device="cuda"), tol=1e-6,
+                                         max_iter=50)
+    assert torch.equal(lam_b, lam_r) and not torch.equal(lam_a, lam_b)
+    lam_c, _, _, iters_c, info = s.solve_batched(sizes, Mg, tol=0.0, max_iter=2,
+                                                 stop="increment")
+    assert info["iterations"] <= 2 and int(iters_c.max()) == 2
+    lams = blocks(lam_b.cpu().numpy(), sizes, square=False)
+    for p in [3, 12]:
+        ref = oracle.ipt_solve(b[p], tol=1e-13, max_iter=100)
+        np.testing.assert_allclose(lams[p], ref["lam"], rtol=1e-5)
