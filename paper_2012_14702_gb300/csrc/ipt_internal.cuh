@@ -246,6 +246,44 @@ __device__ __forceinline__ float warp_max(float v) {
   return v;
 }
 
+// Sums carried as an unevaluated FP32 pair hi + lo ("double-float"): the
+// pair addition is Knuth's TwoSum of the high parts with the low parts added
+// to its error term, then renormalised (Dekker's fast two-sum), worth ~44
+// significant bits.  Reductions of many FP32 partials use it instead of FP64,
+// whose pipe runs at a small fraction of the FP32 rate on this GPU.
+struct F2 {
+  float hi, lo;
+};
+__device__ __forceinline__ F2 f2_add(F2 a, F2 b) {
+  const float s = __fadd_rn(a.hi, b.hi);
+  const float bv = __fsub_rn(s, a.hi);
+  const float av = __fsub_rn(s, bv);
+  const float err = __fadd_rn(__fsub_rn(a.hi, av), __fsub_rn(b.hi, bv));
+  const float e = __fadd_rn(err, __fadd_rn(a.lo, b.lo));
+  const float h = __fadd_rn(s, e);
+  return {h, __fsub_rn(e, __fsub_rn(h, s))};
+}
+__device__ __forceinline__ F2 warp_sum(F2 v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const F2 w{__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
+    v = f2_add(v, w);
+  }
+  return v;
+}
+__device__ __forceinline__ double f2_value(F2 v) { return (double)v.hi + (double)v.lo; }
+// Sum over the block (blockDim.x a multiple of 32, at most 1024) as FP32
+// pairs; the total is valid in thread 0.  `sh` (32 pairs) must not be in use.
+__device__ __forceinline__ F2 block_sum(F2 v, F2* sh) {
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  F2 t{0.f, 0.f};
+  if (w == 0) t = warp_sum(lane < nw ? sh[lane] : F2{0.f, 0.f});
+  return t;
+}
+
 // Power-of-two operand scale s with mx * s in [2^13, 2^14): keeps scaled
 // values inside FP16's range (max 65504) with headroom; exponent clamped to
 // +-60 so products of two scales stay finite.  1 for zero / non-finite mx.

@@ -8,11 +8,15 @@
 // each column (or one s for the whole block); a column with Dp = 0 takes
 // s = 1, which makes the update the plain iterate f^p(z).
 //
-// Iterates are column-major (element (j, c) at c * ld + j).  The differences,
-// inner products and the update are formed in FP64 from the stored iterates
-// (FP32 inputs are exact in FP64, so no cancellation is lost); the result is
-// rounded once to the iterate's type.  Every kernel returns at entry once the
-// controller has stopped the solve.
+// Iterates are column-major (element (j, c) at c * ld + j).  FP64 iterates:
+// differences, inner products and the update in FP64.  FP32 iterates: in
+// FP32 (the FP64 pipe runs at a small fraction of the FP32 rate here), with
+// the higher differences formed from first differences of consecutive
+// iterates (f - z, f^2 - f, f^3 - f^2), which are exact whenever the two
+// entries lie within a factor of two of each other (Sterbenz) and otherwise
+// carry one rounding relative to themselves; per-block sums go to FP64
+// accumulators.  Every kernel returns at entry once the controller has
+// stopped the solve.
 #include "ipt_internal.cuh"
 
 namespace ipt {
@@ -21,18 +25,27 @@ namespace {
 
 constexpr int ROWS_PER_THREAD = 4;
 
-template <typename T>
-__device__ __forceinline__ void differences(const T* z, const T* f1, const T* f2, const T* f3,
-                                            int64_t o, int p, double& d1, double& d2,
-                                            double& d3) {
-  const double x = (double)z[o], a = (double)f1[o], b = (double)f2[o];
+__device__ __forceinline__ void differences(const double* z, const double* f1, const double* f2,
+                                            const double* f3, int64_t o, int p, double& d1,
+                                            double& d2, double& d3) {
+  const double x = z[o], a = f1[o], b = f2[o];
   d1 = a - x;
   d2 = b - 2.0 * a + x;
-  d3 = p == 3 ? ((double)f3[o] - 3.0 * b + 3.0 * a - x) : 0.0;
+  d3 = p == 3 ? (f3[o] - 3.0 * b + 3.0 * a - x) : 0.0;
 }
 
-// Per column: <Dp, D(p-1)> and ||Dp||^2 over rows, FP64 block partials added
-// into acc[2c], acc[2c + 1].  Grid (column, row block).
+__device__ __forceinline__ void differences(const float* z, const float* f1, const float* f2,
+                                            const float* f3, int64_t o, int p, float& d1,
+                                            float& d2, float& d3) {
+  const float x = z[o], a = f1[o], b = f2[o];
+  const float e1 = a - x, e2 = b - a;
+  d1 = e1;
+  d2 = e2 - e1;
+  d3 = p == 3 ? ((f3[o] - b) - e2) - d2 : 0.f;
+}
+
+// Per column: <Dp, D(p-1)> and ||Dp||^2 over rows, block partials added
+// into the FP64 acc[2c], acc[2c + 1].  Grid (column, row block).
 template <typename T>
 __global__ void __launch_bounds__(256)
     k_acx_dots(const T* __restrict__ z, const T* __restrict__ f1, const T* __restrict__ f2,
@@ -41,19 +54,19 @@ __global__ void __launch_bounds__(256)
   if (st->done) return;
   const int c = blockIdx.x;
   const int64_t col = (int64_t)c * ld;
-  double num = 0.0, den = 0.0;
+  T num = T(0), den = T(0);
 #pragma unroll
   for (int q = 0; q < ROWS_PER_THREAD; ++q) {
     const int j = (blockIdx.y * ROWS_PER_THREAD + q) * blockDim.x + threadIdx.x;
     if (j < n) {
-      double d1, d2, d3;
+      T d1, d2, d3;
       differences(z, f1, f2, f3, col + j, p, d1, d2, d3);
-      const double dp = p == 3 ? d3 : d2, dq = p == 3 ? d2 : d1;
-      num += dp * dq;
-      den += dp * dp;
+      const T dp = p == 3 ? d3 : d2, dq = p == 3 ? d2 : d1;
+      num = fma(dp, dq, num);
+      den = fma(dp, dp, den);
     }
   }
-  __shared__ double rn[8], rd[8];
+  __shared__ T rn[8], rd[8];
   num = warp_sum(num);
   den = warp_sum(den);
   if ((threadIdx.x & 31) == 0) {
@@ -62,13 +75,13 @@ __global__ void __launch_bounds__(256)
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double a = 0.0, b = 0.0;
+    T a = T(0), b = T(0);
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
       a += rn[w];
       b += rd[w];
     }
-    atomicAdd(&acc[2 * c], a);
-    atomicAdd(&acc[2 * c + 1], b);
+    atomicAdd(&acc[2 * c], (double)a);
+    atomicAdd(&acc[2 * c + 1], (double)b);
   }
 }
 
@@ -116,17 +129,17 @@ __global__ void __launch_bounds__(256)
   if (st->done) return;
   const int c = blockIdx.x;
   const int64_t col = (int64_t)c * ld;
-  const double s = sigma[c];
+  const T s = (T)sigma[c];
 #pragma unroll
   for (int q = 0; q < ROWS_PER_THREAD; ++q) {
     const int j = (blockIdx.y * ROWS_PER_THREAD + q) * blockDim.x + threadIdx.x;
     if (j < n) {
-      double d1, d2, d3;
+      T d1, d2, d3;
       differences(z, f1, f2, f3, col + j, p, d1, d2, d3);
-      const double x = (double)z[col + j];
-      const double y = p == 3 ? x + 3.0 * s * d1 + 3.0 * s * s * d2 + s * s * s * d3
-                              : x + 2.0 * s * d1 + s * s * d2;
-      z[col + j] = (T)y;
+      const T x = z[col + j];
+      const T y = p == 3 ? x + T(3) * s * d1 + T(3) * s * s * d2 + s * s * s * d3
+                         : x + T(2) * s * d1 + s * s * d2;
+      z[col + j] = y;
     }
   }
 }

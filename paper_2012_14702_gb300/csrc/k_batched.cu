@@ -52,21 +52,10 @@ struct __align__(16) Shared {
   float Bs[TK][TB + 4];  // W tile, [k][column]
   float th_hi[kBatchMaxN], th_lo[kBatchMaxN];
   float ddiag[kBatchMaxN];  // Delta_jj = M_jj - theta_j (formed in FP64 once per problem)
-  double d[kBatchMaxN];
-  double red[3][NT / 32];
-  int prob, flag;
-  double inc, rho;
+  float d[kBatchMaxN];      // d_c = (Delta Z)_cc of the current evaluation
+  F2 red[3][32];
+  int prob, flag, verdict;
 };
-
-// Sum over the CTA (every thread gets the total); `red` must not be in use.
-__device__ __forceinline__ double block_sum(double v, double* red) {
-  v = warp_sum(v);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
-  __syncthreads();
-  double t = 0.0;
-  for (int w = 0; w < NT / 32; ++w) t += red[w];
-  return t;
-}
 
 // One product evaluation of a problem (P = Delta_{:,c} + Delta W, the map in
 // the tile epilogue), output tiles TBT x TBT (32 or 64), each of the 16 x 16
@@ -144,7 +133,7 @@ __device__ __forceinline__ void product_map(const BatchArgs& a, const float* __r
           for (int q = 0; q < R; ++q) {
             const int c = c0t + tx * R + q;
             if (ty * R + i == tx * R + q && c < n)
-              sh.d[c] = (double)(sh.ddiag[c] + acc[i][q]);
+              sh.d[c] = sh.ddiag[c] + acc[i][q];
           }
         __syncthreads();
       }
@@ -161,7 +150,7 @@ __device__ __forceinline__ void product_map(const BatchArgs& a, const float* __r
           const float pjc = (j != c ? M[(int64_t)j * n + c] : 0.f) + acc[i][q];
           const float gap = gap2f(sh.th_hi[j], sh.th_lo[j], sh.th_hi[c], sh.th_lo[c]);
           float f, r;
-          map_entry<float>(z, pjc, (float)sh.d[c], gap, j == c, f, r);
+          map_entry<float>(z, pjc, sh.d[c], gap, j == c, f, r);
           zn[(int64_t)j * n + c] = f;
           s_inc = fmaf(f - z, f - z, s_inc);
           s_z = fmaf(z, z, s_z);
@@ -208,8 +197,9 @@ __global__ void __launch_bounds__(NT, 3)
     int status = IPT_MAXITER, it = 0;
     // ---------------------------------------------------------- evaluations
     for (it = 0; it < a.max_iter; ++it) {
-      // FP32 per-thread sums (FP64 arithmetic is a small fraction of the FP32
-      // rate here); the CTA reduction is FP64
+      // FP32 per-thread sums, CTA sums as FP32 pairs and the test in FP64 on
+      // one thread (the FP64 pipe runs at a small fraction of the FP32 rate
+      // here, so no per-entry or per-thread FP64 work)
       float s_inc = 0.f, s_z = 0.f, s_r = 0.f;
       if (it == 0) {
         // Z = E: product-free
@@ -224,7 +214,7 @@ __global__ void __launch_bounds__(NT, 3)
               r = djc;
               s_inc = fmaf(f, f, s_inc);
             } else {
-              sh.d[c] = (double)sh.ddiag[c];
+              sh.d[c] = sh.ddiag[c];
             }
             s_r = fmaf(r, r, s_r);
             zn[(int64_t)j * n + c] = f;
@@ -235,24 +225,26 @@ __global__ void __launch_bounds__(NT, 3)
         else product_map<64>(a, M, n, zc, zn, sh, s_inc, s_z, s_r);
       }
       // norms of this evaluation, Alg. 2's test, divergence, cap
-      const double t_inc = block_sum((double)s_inc, sh.red[0]);
-      const double t_z = block_sum((double)s_z, sh.red[1]);
-      const double t_r = block_sum((double)s_r, sh.red[2]);
-      if (it == 0) r0 = sqrt(t_r);
-      const double inc = sqrt(t_inc) / sqrt(t_z);
-      const double rho = r0 > 0.0 ? sqrt(t_r) / r0 : 0.0;
-      const int fl = sh.flag;
+      const F2 t_inc = block_sum(F2{s_inc, 0.f}, sh.red[0]);
+      const F2 t_z = block_sum(F2{s_z, 0.f}, sh.red[1]);
+      const F2 t_r = block_sum(F2{s_r, 0.f}, sh.red[2]);
+      if (tid == 0) {  // the totals are valid in thread 0
+        const double tr = f2_value(t_r), tz = f2_value(t_z);
+        if (it == 0) r0 = sqrt(tr);
+        const double inc = sqrt(f2_value(t_inc)) / sqrt(tz);
+        const double rho = r0 > 0.0 ? sqrt(tr) / r0 : 0.0;
+        int v = IPT_MAXITER;  // continue
+        if (sh.flag)
+          v = IPT_DEGENERATE_THETA;
+        else if (!isfinite(inc) || !isfinite(rho) || sqrt(tz) > a.diverge_bound * sqrt((double)n))
+          v = IPT_DIVERGED;
+        else if ((a.stop == IPT_STOP_INCREMENT ? inc : rho) <= a.tol)
+          v = IPT_OK;
+        sh.verdict = v;
+      }
       __syncthreads();
-      if (fl) {
-        status = IPT_DEGENERATE_THETA;
-        break;
-      }
-      if (!isfinite(inc) || !isfinite(rho) || sqrt(t_z) > a.diverge_bound * sqrt((double)n)) {
-        status = IPT_DIVERGED;
-        break;
-      }
-      if ((a.stop == IPT_STOP_INCREMENT ? inc : rho) <= a.tol) {
-        status = IPT_OK;
+      if (sh.verdict != IPT_MAXITER) {
+        status = sh.verdict;
         break;
       }
       if (it + 1 == a.max_iter) break;  // MAXITER: the returned Z is the last evaluated
@@ -270,7 +262,7 @@ __global__ void __launch_bounds__(NT, 3)
         Zout[(int64_t)c * n + j] = is_e ? (j == c ? 1.f : 0.f) : zc[(int64_t)j * n + c];
     for (int c = tid; c < n; c += NT) {
       const double t = a.theta ? a.theta[vo + c] : (double)M[(int64_t)c * n + c];
-      a.lambda[vo + c] = t + sh.d[c];
+      a.lambda[vo + c] = t + (double)sh.d[c];
     }
     if (tid == 0) {
       a.status[p] = status;

@@ -19,7 +19,9 @@ namespace {
 
 constexpr int RPT = 4;  // rows per thread
 
-// Per column: ||F_c - Z_c||^2 and ||Z_c||^2 (block partials into acc[2c], acc[2c+1]).
+// Per column: ||F_c - Z_c||^2 and ||Z_c||^2 (block partials into acc[2c],
+// acc[2c+1]), accumulated in the iterate's precision (the history features
+// need a few digits; FP64 per entry would run on the slow FP64 pipe).
 template <typename T>
 __global__ void __launch_bounds__(256)
     k_damp_colnorms(const T* __restrict__ z, const T* __restrict__ f, int n, int64_t ld,
@@ -27,17 +29,17 @@ __global__ void __launch_bounds__(256)
   if (st->done) return;
   const int c = blockIdx.x;
   const int64_t col = (int64_t)c * ld;
-  double a = 0.0, b = 0.0;
+  T a = T(0), b = T(0);
 #pragma unroll
   for (int q = 0; q < RPT; ++q) {
     const int j = (blockIdx.y * RPT + q) * blockDim.x + threadIdx.x;
     if (j < n) {
-      const double zv = (double)z[col + j], dv = (double)f[col + j] - zv;
-      a += dv * dv;
-      b += zv * zv;
+      const T zv = z[col + j], dv = f[col + j] - zv;
+      a = fma(dv, dv, a);
+      b = fma(zv, zv, b);
     }
   }
-  __shared__ double ra[8], rb[8];
+  __shared__ T ra[8], rb[8];
   a = warp_sum(a);
   b = warp_sum(b);
   if ((threadIdx.x & 31) == 0) {
@@ -46,13 +48,13 @@ __global__ void __launch_bounds__(256)
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double s = 0.0, t = 0.0;
+    T s = T(0), t = T(0);
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
       s += ra[w];
       t += rb[w];
     }
-    atomicAdd(&acc[2 * c], s);
-    atomicAdd(&acc[2 * c + 1], t);
+    atomicAdd(&acc[2 * c], (double)s);
+    atomicAdd(&acc[2 * c + 1], (double)t);
   }
 }
 

@@ -21,7 +21,7 @@ namespace {
 // ---------------------------------------------------------------- d = D(Delta Z)
 // One warp per column c: the contiguous row cols[c] of row-major Delta dotted
 // with the contiguous column c of Z.  FP32 data: compensated FP32 sums per
-// lane, FP64 across lanes; FP64 data: FP64 throughout.
+// lane, FP32 pairs (~44 bits) across lanes; FP64 data: FP64 throughout.
 template <typename T>
 __global__ void k_prepass(const T* __restrict__ Drow, const T* __restrict__ Z, int64_t ld,
                           const int32_t* __restrict__ icol, int kpad, double* __restrict__ d,
@@ -49,7 +49,7 @@ __global__ void k_prepass(const T* __restrict__ Drow, const T* __restrict__ Z, i
       comp = (t - s) - yy;
       s = t;
     }
-    tot = warp_sum((double)s - (double)comp);
+    tot = f2_value(warp_sum(F2{s, -comp}));
   } else {
     double s = 0.0;
     const double2* a2 = reinterpret_cast<const double2*>(a);
@@ -82,7 +82,7 @@ __device__ __forceinline__ void subtract_base(float4& y, const float4* b4, int m
 }
 
 // One warp per column c: d_c as in k_prepass (compensated FP32 per lane,
-// FP64 across lanes) and max |W_.c|; then W_.c * s_c split into hi/lo
+// FP32 pairs across lanes) and max |W_.c|; then W_.c * s_c split into hi/lo
 // (the column is re-read from cache).  Padding columns only get d = 0.
 template <bool BF16>
 __global__ void k_prepass_tc(const float* __restrict__ Drow, const float* __restrict__ Z,
@@ -117,7 +117,7 @@ __global__ void k_prepass_tc(const float* __restrict__ Drow, const float* __rest
     subtract_base(y, b4, m, i);
     mx = fmaxf(mx, fmaxf(fmaxf(fabsf(y.x), fabsf(y.y)), fmaxf(fabsf(y.z), fabsf(y.w))));
   }
-  const double tot = warp_sum((double)s - (double)comp);
+  const double tot = f2_value(warp_sum(F2{s, -comp}));
   mx = warp_max(mx);
   const float sc = pow2_scale(mx);
   uint2* h2 = reinterpret_cast<uint2*>(Wh + (int64_t)c * ld);
@@ -184,21 +184,21 @@ __global__ void __launch_bounds__(1024)
                            fmaxf(fabsf(y[q].z), fabsf(y[q].w))));
     }
   }
-  __shared__ double rs[32];
+  // d_c: the lanes' compensated sums (s - comp) reduced as FP32 pairs, the
+  // warps' pairs by warp 0
+  __shared__ F2 rs[32];
   __shared__ float rm[32];
-  const double ws = warp_sum((double)s - (double)comp);
+  const F2 ws = warp_sum(F2{s, -comp});
   const float wm = warp_max(mx);
   if (lane == 0) {
     rs[wid] = ws;
     rm[wid] = wm;
   }
   __syncthreads();
-  double tot = 0.0;
   float cmax = 0.f;
-  for (int w = 0; w < nw; ++w) {
-    tot += rs[w];
-    cmax = fmaxf(cmax, rm[w]);
-  }
+  for (int w = 0; w < nw; ++w) cmax = fmaxf(cmax, rm[w]);
+  F2 tot{0.f, 0.f};
+  if (wid == 0) tot = warp_sum(lane < nw ? rs[lane] : F2{0.f, 0.f});
   const float sc = pow2_scale(cmax);
   uint2* h2 = reinterpret_cast<uint2*>(Wh + (int64_t)c * ld);
   uint2* l2 = reinterpret_cast<uint2*>(Wl + (int64_t)c * ld);
@@ -216,7 +216,7 @@ __global__ void __launch_bounds__(1024)
     }
   }
   if (tid == 0) {
-    d[c] = tot;
+    d[c] = f2_value(tot);
     sinv[c] = 1.f / sc;
   }
 }
@@ -421,7 +421,7 @@ __global__ void __launch_bounds__(256)
 // R = Delta_{., cols[c]} off the unit entry.  Grid (column c, row block);
 // each thread maps 4 consecutive rows with 16-byte loads and stores.
 __global__ void __launch_bounds__(256)
-    k_map_first(MapArgs<float> a, double* __restrict__ d, double* __restrict__ part) {
+    k_map_first(MapArgs<float> a, double* __restrict__ d, float* __restrict__ part) {
   if (a.st->done) return;
   const int c = blockIdx.x;
   const int ic = a.icol[c];
@@ -465,38 +465,33 @@ __global__ void __launch_bounds__(256)
     red[2][w] = w2;
   }
   __syncthreads();
-  if (threadIdx.x < 3) {  // three arrays of per-block partials, one per norm
-    double t = 0.0;
-    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += (double)red[threadIdx.x][q];
+  if (threadIdx.x < 3) {  // three arrays of per-block FP32 partials, one per norm
+    float t = 0.f;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += red[threadIdx.x][q];
     const int64_t nb = (int64_t)gridDim.x * gridDim.y;
     part[threadIdx.x * nb + (int64_t)blockIdx.x * gridDim.y + blockIdx.y] = t;
   }
 }
 
-// One block: the evaluation's norm accumulators from per-block partials.
+// One block: the evaluation's norm accumulators from per-block partials
+// (summed as FP32 pairs, in a fixed order).
 __global__ void __launch_bounds__(1024)
-    k_sum_norms(const double* __restrict__ part, int64_t count, DevState* st) {
-  __shared__ double red[3][1024];
-  double t0 = 0.0, t1 = 0.0, t2 = 0.0;
-#pragma unroll 8
+    k_sum_norms(const float* __restrict__ part, int64_t count, DevState* st) {
+  __shared__ F2 sh[3][32];
+  F2 t0{0.f, 0.f}, t1{0.f, 0.f}, t2{0.f, 0.f};
+#pragma unroll 4
   for (int64_t i = threadIdx.x; i < count; i += blockDim.x) {  // coalesced, loads in flight
-    t0 += part[i];
-    t1 += part[count + i];
-    t2 += part[2 * count + i];
+    t0 = f2_add(t0, F2{part[i], 0.f});
+    t1 = f2_add(t1, F2{part[count + i], 0.f});
+    t2 = f2_add(t2, F2{part[2 * count + i], 0.f});
   }
-  red[0][threadIdx.x] = t0;
-  red[1][threadIdx.x] = t1;
-  red[2][threadIdx.x] = t2;
-  __syncthreads();
-  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
-    if ((int)threadIdx.x < h)
-      for (int q = 0; q < 3; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + h];
-    __syncthreads();
-  }
+  t0 = block_sum(t0, sh[0]);
+  t1 = block_sum(t1, sh[1]);
+  t2 = block_sum(t2, sh[2]);
   if (threadIdx.x == 0) {
-    st->acc_inc2 += red[0][0];
-    st->acc_z2 += red[1][0];
-    st->acc_r2 += red[2][0];
+    st->acc_inc2 += f2_value(t0);
+    st->acc_z2 += f2_value(t1);
+    st->acc_r2 += f2_value(t2);
   }
 }
 
@@ -679,8 +674,9 @@ void launch_control(DevState* st, ControlArgs a, cudaStream_t s) {
 void launch_map_first(const MapArgs<float>& a, int npad, int kpad, double* d, double* part,
                       cudaStream_t s) {
   dim3 g(kpad, (npad / 4 + 255) / 256);
-  k_map_first<<<g, 256, 0, s>>>(a, d, part);
-  k_sum_norms<<<1, 1024, 0, s>>>(part, (int64_t)g.x * g.y, a.st);
+  float* pf = reinterpret_cast<float*>(part);
+  k_map_first<<<g, 256, 0, s>>>(a, d, pf);
+  k_sum_norms<<<1, 1024, 0, s>>>(pf, (int64_t)g.x * g.y, a.st);
 }
 
 }  // namespace ipt

@@ -68,7 +68,7 @@ __global__ void k_cols_dup(const int32_t* icol, const int* count, int k, DevStat
 template <typename TM, typename TD>
 __global__ void k_form_delta(const TM* __restrict__ M, int64_t ldm, const double* theta, int n,
                              int npad, const int* count, TD* __restrict__ Drow,
-                             float* __restrict__ DT, double* __restrict__ r0part) {
+                             float* __restrict__ DT, float* __restrict__ r0part) {
   __shared__ float tile[32][33];
   const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
   const int tx = threadIdx.x, ty = threadIdx.y;
@@ -102,8 +102,8 @@ __global__ void k_form_delta(const TM* __restrict__ M, int64_t ldm, const double
   if (tx == 0) red[ty] = w;
   __syncthreads();
   if (tx == 0 && ty == 0) {
-    double t = 0.0;
-    for (int q = 0; q < 8; ++q) t += (double)red[q];
+    float t = 0.f;
+    for (int q = 0; q < 8; ++q) t += red[q];
     r0part[(int64_t)blockIdx.y * gridDim.x + blockIdx.x] = t;
   }
 }
@@ -112,11 +112,18 @@ __global__ void k_form_delta(const TM* __restrict__ M, int64_t ldm, const double
 // Each thread moves 4 consecutive columns of 4 rows with 16-byte loads and
 // stores (a row segment is 256 contiguous bytes); the transposed FP32 copy
 // goes through a 65-float padded shared tile and leaves as 256-byte column
-// segments (one float2 per lane).
+// segments (one float2 per lane).  The diagonal entries are copied as M_ii
+// by the streaming loop and then replaced, in the tiles on the diagonal only,
+// by M_ii - theta_i formed in FP64 (the FP64 pipe is far slower than the
+// FP32 one here: no per-entry FP64 work, not even a predicated one).
+__device__ __noinline__ float diag_delta(float m, double theta) {
+  return (float)((double)m - theta);
+}
+
 __global__ void __launch_bounds__(256)
     k_form_delta4(const float* __restrict__ M, int64_t ldm, const double* theta, int n,
                   int npad, const int* count, float* __restrict__ Drow, float* __restrict__ DT,
-                  double* __restrict__ r0part) {
+                  float* __restrict__ r0part) {
   __shared__ float tile[64][65];
   const int c0 = blockIdx.x * 64, r0 = blockIdx.y * 64;
   const int tx = threadIdx.x, ty = threadIdx.y;
@@ -144,19 +151,26 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     const int i = r0 + ty + 16 * q;
-    float v[4] = {m4[q].x, m4[q].y, m4[q].z, m4[q].w};
+    const float v[4] = {m4[q].x, m4[q].y, m4[q].z, m4[q].w};
     if (i < n) {
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        if (j + u == i) v[u] = (float)((double)v[u] - theta[i]);  // Delta_ii, formed in FP64
-        else if (req[u]) r0sum = fmaf(v[u], v[u], r0sum);
-      }
+      for (int u = 0; u < 4; ++u)
+        if (j + u != i && req[u]) r0sum = fmaf(v[u], v[u], r0sum);
     }
-    *reinterpret_cast<float4*>(Drow + (int64_t)i * npad + j) = make_float4(v[0], v[1], v[2], v[3]);
+    *reinterpret_cast<float4*>(Drow + (int64_t)i * npad + j) = m4[q];
 #pragma unroll
     for (int u = 0; u < 4; ++u) tile[ty + 16 * q][4 * tx + u] = v[u];
   }
   const int tid = ty * 16 + tx, lane = tid & 31, w = tid >> 5;
+  if (blockIdx.x == blockIdx.y) {  // a tile on the diagonal: Delta_ii = M_ii - theta_i
+    __syncthreads();
+    const int i = r0 + tid;
+    if (tid < 64 && i < n) {
+      const float dv = diag_delta(tile[tid][tid], theta[i]);
+      tile[tid][tid] = dv;
+      Drow[(int64_t)i * npad + i] = dv;
+    }
+  }
   if (DT) {
     __syncthreads();
 #pragma unroll
@@ -171,25 +185,22 @@ __global__ void __launch_bounds__(256)
   if (lane == 0) red[w] = ws;
   __syncthreads();
   if (tid == 0) {
-    double t = 0.0;
-    for (int q = 0; q < 8; ++q) t += (double)red[q];
+    float t = 0.f;
+    for (int q = 0; q < 8; ++q) t += red[q];
     r0part[(int64_t)blockIdx.y * gridDim.x + blockIdx.x] = t;
   }
 }
 
-// One block: st->r0acc = sum of the per-block partials, in a fixed order.
-__global__ void k_sum_partials(const double* __restrict__ part, int64_t count, DevState* st) {
-  __shared__ double red[1024];
-  double t = 0.0;
-#pragma unroll 8
-  for (int64_t i = threadIdx.x; i < count; i += blockDim.x) t += part[i];
-  red[threadIdx.x] = t;
-  __syncthreads();
-  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
-    if ((int)threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) st->r0acc = red[0];
+// One block: st->r0acc = sum of the per-block FP32 partials (as FP32 pairs,
+// in a fixed order).
+__global__ void __launch_bounds__(1024)
+    k_sum_partials(const float* __restrict__ part, int64_t count, DevState* st) {
+  __shared__ F2 sh[32];
+  F2 t{0.f, 0.f};
+#pragma unroll 4
+  for (int64_t i = threadIdx.x; i < count; i += blockDim.x) t = f2_add(t, F2{part[i], 0.f});
+  t = block_sum(t, sh);
+  if (threadIdx.x == 0) st->r0acc = f2_value(t);
 }
 
 // Tensor-core A operand: row j of Delta scaled by the power of two r_j that
@@ -348,7 +359,8 @@ void launch_validate(const int32_t* cols, int n, int k, int kpad, const double* 
 
 void launch_form_delta(const void* M, int64_t ldm, int m_dtype, const double* theta, int n,
                        int npad, const int* count, void* Drow, int drow_f64, float* DT,
-                       double* r0part, DevState* st, cudaStream_t s) {
+                       double* r0part_d, DevState* st, cudaStream_t s) {
+  float* r0part = reinterpret_cast<float*>(r0part_d);  // per-block FP32 partials
   dim3 b(32, 8);
   if (m_dtype == IPT_DTYPE_F32 && !drow_f64 && ldm % 4 == 0 &&
       (reinterpret_cast<uintptr_t>(M) & 15) == 0) {

@@ -61,20 +61,22 @@ def run_csr(name, solves, precision, tol, window=True):
             raise SystemExit(1)
 
 
-def run_batched(name, solves, tol):
+def run_batched(name, solves, tol, tiles=None):
     import torch
     from paper_2012_14702_gb300 import ipt
     count, nmin, nmax, scale, seed = workloads.BATCHED_CONFIGS[name]
     sizes, flat, _ = workloads.batched_dense(count, nmin, nmax, scale, seed)
     Mg = torch.as_tensor(flat, device="cuda")
     s = ipt.Solver()
+    if tiles:
+        s.batched_tiles = tiles  # fixed tiles: no tuning launches before the solves
     for i in range(solves):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         _, _, _, iters, info = s.solve_batched(sizes, Mg, tol=tol, max_iter=30)
         torch.cuda.synchronize()
         print(f"{name} solve {i}: {info['status']} evaluations {info['iterations']} (max) "
-              f"{1e3 * (time.perf_counter() - t0):.2f} ms", flush=True)
+              f"{1e3 * (time.perf_counter() - t0):.2f} ms, tiles {s.batched_tiles}", flush=True)
         if info["status"] != "OK":
             raise SystemExit(1)
 
@@ -89,11 +91,15 @@ def main(argv=None):
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--all-rows", action="store_true",
                     help="sparse workloads: evaluate every row (no active window)")
+    ap.add_argument("--tiles", default=None,
+                    help="batched workloads: output tiles per size class, e.g. 64,64,64 "
+                         "(default: tuned on the first solve)")
     a = ap.parse_args(argv)
     if a.workload in workloads.DENSE_CONFIGS:
         run_dense(a.workload, a.solves, a.precision, a.tol)
     elif a.workload in workloads.BATCHED_CONFIGS:
-        run_batched(a.workload, a.solves, a.tol)
+        tiles = [int(x) for x in a.tiles.split(",")] if a.tiles else None
+        run_batched(a.workload, a.solves, a.tol, tiles)
     else:
         run_csr(a.workload, a.solves, a.precision, a.tol, window=not a.all_rows)
 
