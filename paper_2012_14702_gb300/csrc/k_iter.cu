@@ -416,45 +416,70 @@ __global__ void __launch_bounds__(256)
 
 // ---------------------------------------------------------------- first evaluation
 // F(E) needs no product: at Z = E, P = Delta E is the column cols[c] of Delta
-// (DT, exact), d_c = Delta_{cols[c], cols[c]}, and Eq. (dyn) gives
-// F_jc = -Delta_{j, cols[c]} / (theta_j - theta_{cols[c]}) off the unit entry,
-// R = Delta_{., cols[c]} off the unit entry.  Grid (column c, row block);
-// each thread maps 4 consecutive rows with 16-byte loads and stores.
+// (DT, exact), d_c = Delta_{cols[c], cols[c]}, and Eq. (dyn) with Z_jc = 0
+// off the unit entry gives F_jc = -Delta_{j, cols[c]} / (theta_j -
+// theta_{cols[c]}) and R_jc = Delta_{j, cols[c]}; F = 1, R = 0 at the unit
+// entry.  Grid (column c, row block); each thread maps MF_RPT groups of 4
+// consecutive rows with 16-byte loads and stores.  A zero gap is collected
+// per thread and flagged once per warp.
+#ifndef IPT_MAPFIRST_RPT
+#define IPT_MAPFIRST_RPT 4
+#endif
+constexpr int MF_RPT = IPT_MAPFIRST_RPT;
+
 __global__ void __launch_bounds__(256)
     k_map_first(MapArgs<float> a, double* __restrict__ d, float* __restrict__ part) {
   if (a.st->done) return;
   const int c = blockIdx.x;
   const int ic = a.icol[c];
   const int64_t ld = a.ld;
-  const int j0 = (blockIdx.y * blockDim.x + threadIdx.x) * 4;
   float s_inc = 0.f, s_z = 0.f, s_r = 0.f;
-  if (ic < 0 && blockIdx.y == 0 && threadIdx.x == 0) d[c] = 0.0;
-  if (ic >= 0 && j0 < a.n) {
+  bool bad = false;
+  if (ic < 0) {
+    if (blockIdx.y == 0 && threadIdx.x == 0) d[c] = 0.0;
+  } else {
     const float* pc = a.DT + (int64_t)ic * ld;
-    const float4 p4 = *reinterpret_cast<const float4*>(pc + j0);
-    const float4 h4 = *reinterpret_cast<const float4*>(a.th_hi + j0);
-    const float4 l4 = *reinterpret_cast<const float4*>(a.th_lo + j0);
-    const float hi = a.th_hi[ic], li = a.th_lo[ic], dc = pc[ic];
-    const float pp[4] = {p4.x, p4.y, p4.z, p4.w};
-    const float hh[4] = {h4.x, h4.y, h4.z, h4.w};
-    const float ll[4] = {l4.x, l4.y, l4.z, l4.w};
-    float f[4];
+    const float hi = a.th_hi[ic], li = a.th_lo[ic];
+    float4 p4[MF_RPT], h4[MF_RPT], l4[MF_RPT];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int j = j0 + u;
-      const float z = j == ic ? 1.f : 0.f;
-      const float gap = gap2f(hh[u], ll[u], hi, li);
-      if (j < a.n && gap == 0.f && j != ic) flag_degenerate(a.st);
-      float r;
-      map_entry<float>(z, pp[u], dc, gap, j == ic, f[u], r);
-      if (j >= a.n) f[u] = 0.f, r = 0.f;  // padding rows stay zero
-      s_inc = fmaf(f[u] - z, f[u] - z, s_inc);
-      s_z = fmaf(z, z, s_z);
-      s_r = fmaf(r, r, s_r);
+    for (int q = 0; q < MF_RPT; ++q) {  // all loads first
+      const int j0 = ((blockIdx.y * MF_RPT + q) * blockDim.x + threadIdx.x) * 4;
+      if (j0 < a.n) {
+        p4[q] = *reinterpret_cast<const float4*>(pc + j0);
+        h4[q] = *reinterpret_cast<const float4*>(a.th_hi + j0);
+        l4[q] = *reinterpret_cast<const float4*>(a.th_lo + j0);
+      }
     }
-    *reinterpret_cast<float4*>(a.Fout + (int64_t)c * ld + j0) = make_float4(f[0], f[1], f[2], f[3]);
-    if (ic >= j0 && ic < j0 + 4) d[c] = (double)dc;
+#pragma unroll
+    for (int q = 0; q < MF_RPT; ++q) {
+      const int j0 = ((blockIdx.y * MF_RPT + q) * blockDim.x + threadIdx.x) * 4;
+      if (j0 >= a.n) continue;
+      const float pp[4] = {p4[q].x, p4[q].y, p4[q].z, p4[q].w};
+      const float hh[4] = {h4[q].x, h4[q].y, h4[q].z, h4[q].w};
+      const float ll[4] = {l4[q].x, l4[q].y, l4[q].z, l4[q].w};
+      float f[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int j = j0 + u;
+        if (j >= a.n) {
+          f[u] = 0.f;  // padding rows stay zero
+        } else if (j == ic) {
+          f[u] = 1.f;
+          s_z += 1.f;
+          d[c] = (double)pp[u];
+        } else {
+          const float gap = gap2f(hh[u], ll[u], hi, li);
+          bad |= gap == 0.f;
+          f[u] = -pp[u] * recip_nr(gap);
+          s_inc = fmaf(f[u], f[u], s_inc);
+          s_r = fmaf(pp[u], pp[u], s_r);
+        }
+      }
+      *reinterpret_cast<float4*>(a.Fout + (int64_t)c * ld + j0) =
+          make_float4(f[0], f[1], f[2], f[3]);
+    }
   }
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) flag_degenerate(a.st);
   // block partials of the three norms (summed by k_sum_norms)
   __shared__ float red[3][8];
   const float w0 = warp_sum(s_inc), w1 = warp_sum(s_z), w2 = warp_sum(s_r);
@@ -621,10 +646,14 @@ void launch_prepass(const void* Drow, const void* Z, int f64, int64_t ld, const 
                                        st);
 }
 
+#ifndef IPT_PREPASS_VPT
+#define IPT_PREPASS_VPT 8  // float4 slots of the column per thread
+#endif
+
 void launch_prepass_tc(const float* Drow, const float* Z, const float* Zbase, int64_t ld,
                        const int32_t* icol, int kpad, int bf16, double* d, uint16_t* Wh,
                        uint16_t* Wl, float* sinv, DevState* st, cudaStream_t s) {
-  constexpr int VPT = 8;
+  constexpr int VPT = IPT_PREPASS_VPT;
   const int64_t n4 = ld / 4;
   if (n4 <= (int64_t)VPT * 1024) {
     int threads = (int)((n4 + VPT - 1) / VPT);
@@ -673,7 +702,7 @@ void launch_control(DevState* st, ControlArgs a, cudaStream_t s) {
 
 void launch_map_first(const MapArgs<float>& a, int npad, int kpad, double* d, double* part,
                       cudaStream_t s) {
-  dim3 g(kpad, (npad / 4 + 255) / 256);
+  dim3 g(kpad, (npad / 4 + 256 * MF_RPT - 1) / (256 * MF_RPT));
   float* pf = reinterpret_cast<float*>(part);
   k_map_first<<<g, 256, 0, s>>>(a, d, pf);
   k_sum_norms<<<1, 1024, 0, s>>>(pf, (int64_t)g.x * g.y, a.st);
