@@ -62,6 +62,8 @@ def parse_args():
                     help="skip the sparse configuration's measurement")
     ap.add_argument("--no-acx", action="store_true",
                     help="skip the IPT-ACX configuration's measurement")
+    ap.add_argument("--no-eps-sweep", action="store_true",
+                    help="skip the dense eps in {1e-4, 1e-3, 3e-3} sweep")
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the batched configuration's measurement")
     ap.add_argument("--no-damped", action="store_true",
@@ -442,6 +444,45 @@ def run_damped(steps):
             "headline_workload": head}
 
 
+# ---------------------------------------------------------------- dense epsilon sweep
+def run_eps_sweep(steps):
+    """The dense n = 8192 configuration at each perturbation size eps in {1e-4,
+    1e-3, 3e-3}: time to rho <= 1e-6 of the staged FP16 and staged BF16 tensor-core
+    schedules and of plain FP32 IPT on the same GPU, with each result's residual
+    ||M Z - Z Lambda|| / ||R0|| recomputed in FP64 (outside the timed region)."""
+    import torch
+    from paper_2012_14702_gb300 import ipt, workloads
+    solver = ipt.Solver()
+    out = {}
+    for name in ["dense_n8192_eps1e-4", "dense_n8192_eps1e-3", "dense_n8192_eps3e-3"]:
+        n, step, scale, seed = workloads.DENSE_CONFIGS[name]
+        M, th = workloads.dense_symmetric(n, scale, seed, theta_step=step)
+        Mg = torch.as_tensor(M, dtype=torch.float32, device="cuda")
+        thg = torch.as_tensor(th, dtype=torch.float64, device="cuda")
+        del M
+        row = {}
+        for label, kw, reps in [("staged_fp16", {"precision": "staged"}, steps),
+                                ("staged_bf16", {"precision": "staged", "staged_bf16": True},
+                                 steps),
+                                ("plain_fp32", {"precision": "f32"}, 2)]:
+            solver.solve_dense(Mg, theta=thg, tol=TOL, max_iter=60, **kw)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(solver.stream)
+            for _ in range(reps):
+                _, _, info = solver.solve_dense(Mg, theta=thg, tol=TOL, max_iter=60, **kw)
+            e1.record(solver.stream)
+            torch.cuda.synchronize()
+            _, _, v = solver.solve_dense(Mg, theta=thg, tol=TOL, max_iter=60, verify_fp64=True,
+                                         **kw)
+            row[label] = {"ms_to_tol": e0.elapsed_time(e1) / reps, "status": info["status"],
+                          "iterations": info["iterations"], "stage_iters": info["stage_iters"],
+                          "rho": info["rho"], "rho_fp64": v["rho_fp64"]}
+        row["speedup_fp16_vs_plain"] = row["plain_fp32"]["ms_to_tol"] / row["staged_fp16"]["ms_to_tol"]
+        out[f"eps_{scale:g}"] = row
+        del Mg
+    return out
+
+
 # ---------------------------------------------------------------- reference arm
 def run_reference(args, rank):
     if rank != 0:
@@ -613,6 +654,8 @@ def run_ours(args, rank, world, local_rank):
         "gpu_launches": launches,
         "clocks": clocks,
     }
+    if not args.no_eps_sweep:
+        line["eps_sweep"] = run_eps_sweep(max(3, min(args.steps, 5)))
     if not args.no_csr:
         hbm = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("hbm_gbs", 6800.0) \
             if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6800.0

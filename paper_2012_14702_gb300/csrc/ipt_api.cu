@@ -992,7 +992,7 @@ ipt_status ipt_solve_csr(ipt_handle* h, int64_t n, int64_t nnz, const int32_t* r
   CK(ensure(h->theta, (size_t)n * 8));
   CK(ensure(h->thh, (size_t)n * 4));
   CK(ensure(h->thl, (size_t)n * 4));
-  CK(ensure(h->delta, (size_t)n * 8));
+  CK(ensure(h->delta, (size_t)n * 12));  // FP64 delta_j, then its FP32 copy
   CK(ensure(h->icol, (size_t)kk * 4));
   CK(ensure(h->count, (size_t)n * 4));
   CK(ensure(h->d, (size_t)kk * 8));

@@ -75,6 +75,7 @@ __global__ void __launch_bounds__(256)
     th_hi[j] = h;
     th_lo[j] = (float)(t - (double)h);
     delta[j] = mjj - t;
+    reinterpret_cast<float*>(delta + n)[j] = (float)(mjj - t);  // FP32 copy for the FP32 kernels
   }
   // block reduction; the shared words take one atomic per block, and only
   // when the block's value would change them (most blocks see the same band)
@@ -277,7 +278,9 @@ __global__ void __launch_bounds__(256, 4)
       if (!live) continue;
       const V4 zj4 = *reinterpret_cast<const V4*>(Zin + (int64_t)j * kk + cb);
       const T zj[4] = {zj4.x, zj4.y, zj4.z, zj4.w};
-      const T dj = (T)delta[j];
+      T dj;  // no per-row FP64 conversion in the FP32 kernel
+      if constexpr (sizeof(T) == 8) dj = delta[j];
+      else dj = reinterpret_cast<const float*>(delta + n)[j];
       const float hj = th_hi[j], lj = th_lo[j];
       T fo[4];
 #pragma unroll
