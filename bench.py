@@ -392,7 +392,7 @@ def run_damped(steps):
     """Learned damping (the committed model, trained on edge-family seeds 100-139)
     on held-out edge matrices: n = 4096, theta_i = i/4, Delta N(0,1)*0.04*s, seeds
     1000-1003 with s = 1.5, 1.3, 1.2, 1.0; time to rho <= 1e-6 beside the plain
-    staged solve and IPT-ACX on the same matrices."""
+    staged solve, IPT-ACX and depth-one Anderson mixing on the same matrices."""
     import torch
     from paper_2012_14702_gb300 import ipt, train_damping, workloads
     p16 = torch.as_tensor(np.load(train_damping.MODEL_PATH), device="cuda")
@@ -407,7 +407,7 @@ def run_damped(steps):
         row = {"seed": seed, "s": sc}
         for name, kw in [("plain_staged", {}), ("damped", {"accel": "damped",
                                                            "damping_model": p16}),
-                         ("acx", {"accel": "acx"})]:
+                         ("acx", {"accel": "acx"}), ("anderson", {"accel": "anderson"})]:
             solver.solve_dense(Mg, theta=tg, tol=TOL, max_iter=600, **kw)
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -439,7 +439,7 @@ def run_damped(steps):
                       "ms": e0.elapsed_time(e1) / 5}
     return {"workload": "dense symmetric n=4096, theta_i=i/4, Delta N(0,1)*0.04*s, held-out "
                         "seeds, k=n, tol 1e-6 residual; staged products (damped, plain) and "
-                        "split-FP16 products (ACX)",
+                        "split-FP16 products (ACX, Anderson)",
             "problems": rows,
             "headline_workload": head}
 

@@ -101,7 +101,8 @@ typedef struct {
                            needs an even number of 128-row blocks, else SINGLE is used).
                            Results are identical; only speed differs                     */
   int accel;            /* ipt_solve_dense: IPT_ACCEL_NONE (default, the Picard update of
-                           Alg. 1/2) or IPT_ACCEL_ACX (Alg. 3: each extrapolation evaluates
+                           Alg. 1/2), IPT_ACCEL_DAMPED, IPT_ACCEL_ANDERSON (below) or
+                           IPT_ACCEL_ACX (Alg. 3: each extrapolation evaluates
                            F at z, f(z) [, f^2(z)] and moves z by the order-3 / order-2
                            extrapolation, orders 3, 2, 3, 2, ...; the stopping test is made
                            at the extrapolated points; `iterations` counts evaluations).
@@ -122,9 +123,13 @@ typedef struct {
  * evaluation Z <- Z + alpha_c (F(Z) - Z), alpha_c in (0, 2) predicted per column by the
  * damping model from the column's increment-norm and Rayleigh-quotient-change history
  * (see ipt_damping_forward); plain Picard steps for the first three evaluations and
- * after a fallback (a residual above ten times the smallest seen).  Precision as for
- * ACX. */
-enum { IPT_ACCEL_NONE = 0, IPT_ACCEL_ACX = 1, IPT_ACCEL_DAMPED = 2 };
+ * after a fallback (a residual above ten times the smallest seen).  Runs inside the
+ * staged precision schedule.
+ * IPT_ACCEL_ANDERSON: depth-one Anderson mixing per column (also outside the paper):
+ * with g = F and f = g(z) - z, the next iterate is g(z_t) - gamma_c (g(z_t) - g(z_{t-1})),
+ * gamma_c = <f_t - f_{t-1}, f_t> / ||f_t - f_{t-1}||^2 (0 where that vanishes); the first
+ * step and every step after the same fallback are Picard steps.  Precision as for ACX. */
+enum { IPT_ACCEL_NONE = 0, IPT_ACCEL_ACX = 1, IPT_ACCEL_DAMPED = 2, IPT_ACCEL_ANDERSON = 3 };
 
 /* Values of ipt_options.product_kernel. */
 enum { IPT_PRODUCT_AUTO = 0, IPT_PRODUCT_SINGLE = 1, IPT_PRODUCT_PAIR = 2 };

@@ -6,3 +6,4 @@ from .ipt_oracle import (OK, MAXITER, DIVERGED, DEGENERATE_THETA, INVALID_ARG,  
                          rs_corrections, chart_jacobian, acx_differences, acx_sigma,
                          acx_update, ipt_solve_acx)
 from . import damping  # noqa: F401,E402
+from . import anderson  # noqa: F401,E402

@@ -527,6 +527,64 @@ ipt_status acx_loop(ipt_handle* h, const Plan& p, const ControlArgs& ca, const F
   return IPT_OK;
 }
 
+// Anderson mixing (IPT_ACCEL_ANDERSON).  Buffers: zc holds the iterate under
+// test, (zp, gp) the previous iterate and its map value, fr receives this
+// evaluation's map value.  The first step is a Picard step, so z_1 = g_0 stays
+// where g_0 was written (zc = gp); later steps write z_{t+1} over z_{t-1}.  One
+// host synchronisation per evaluation.
+ipt_status anderson_loop(ipt_handle* h, const Plan& p, const ControlArgs& ca,
+                         const FirstEval& fe, int max_iter, Timing* tm) {
+  cudaStream_t s = h->s;
+  DevState* st = dst(h);
+  const int split = (fe.stage == IPT_PREC_BF16X3 || fe.stage == IPT_PREC_FP16X3) ? 3 : 1;
+  double* acc = (double*)h->acx_acc.p;
+  double* gamma = (double*)h->acx_sigma.p;
+  AndState* as = reinterpret_cast<AndState*>(h->acx_d.p);
+  CK(cudaMemsetAsync(acc, 0, (size_t)p.kpad * 2 * 8, s));
+  CK(cudaMemsetAsync(as, 0, sizeof(AndState), s));
+  int zc = 0, zp = -1, gp = -1, fr = 1;
+  for (int it = 0; it < max_iter; ++it) {
+    const int passes = it == 0 ? fe.passes : (p.f64 ? 1 : split);
+    ControlArgs cq = ca;
+    cq.acx = 1;
+    cq.next_cur = it == 0 ? fr : zp;  // where the next iterate will be
+    ipt_status v = evaluate(h, p, zc, -1, fe.stage, passes, 0, tm, fr);
+    if (v != IPT_OK) return v;
+    launch_control(st, cq, s);
+    CK(launch_anderson_step(h->z[zc].p, h->z[fr].p, it ? h->z[zp].p : nullptr,
+                            it ? h->z[gp].p : nullptr, it ? h->z[zp].p : nullptr,
+                            p.f64 ? 1 : 0, p.n, p.k, p.npad, acc, gamma, as, st, it == 0, s));
+    h->launches += it == 0 ? 3 : 5;
+    if (cudaMemcpyAsync(h->hst, st, kStateHead, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      return IPT_CUDA_ERROR;
+    if (it == 0) {
+      const ipt_status fv = status_from_flags(h->hst->flags);
+      if (fv != IPT_OK) return fv;
+      if (tm && tm->on) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, h->ev[4], h->ev[5]) == cudaSuccess) tm->setup_ms = ms;
+      }
+    }
+    collect_timing(h, passes, tm);
+    if (h->hst->timeout) return IPT_DEVICE_TIMEOUT;
+    if (h->hst->done) break;
+    if (it == 0) {
+      zp = zc;
+      gp = fr;
+      zc = fr;
+    } else {
+      const int ozc = zc, ozp = zp;
+      zc = ozp;
+      zp = ozc;
+      gp = fr;
+    }
+    fr = 0;  // the buffer holding none of zc, zp, gp
+    while (fr == zc || fr == zp || fr == gp) ++fr;
+  }
+  return IPT_OK;
+}
+
 ipt_status solve_dense(ipt_handle* h, int64_t n, const void* M, int64_t ldm, int m_dtype,
                        const double* theta, int64_t k, const int32_t* cols, double tol,
                        int max_iter, const ipt_options* opt_in, double* lambda, void* Z,
@@ -544,7 +602,7 @@ ipt_status solve_dense(ipt_handle* h, int64_t n, const void* M, int64_t ldm, int
                       opt.product_kernel < IPT_PRODUCT_AUTO ||
                       opt.product_kernel > IPT_PRODUCT_PAIR ||
                       (opt.accel != IPT_ACCEL_NONE && opt.accel != IPT_ACCEL_ACX &&
-                       opt.accel != IPT_ACCEL_DAMPED) ||
+                       opt.accel != IPT_ACCEL_DAMPED && opt.accel != IPT_ACCEL_ANDERSON) ||
                       (opt.accel == IPT_ACCEL_DAMPED && !opt.damping_model) ||
                       (opt.acx_sigma != 0 && opt.acx_sigma != 1)))
     v = IPT_INVALID_ARG;
@@ -563,15 +621,16 @@ ipt_status solve_dense(ipt_handle* h, int64_t n, const void* M, int64_t ldm, int
   }
   const bool acx = opt.accel == IPT_ACCEL_ACX;
   const bool damped = opt.accel == IPT_ACCEL_DAMPED;
-  // ACX moves the iterate by extrapolation, outside the staged schedule's
-  // error model: a staged request runs every product as the split stage.
-  // (Damped steps stay inside it with a step bound of 2 increments.)
-  const int prec = (acx && opt.precision == IPT_PREC_STAGED)
+  const bool anderson = opt.accel == IPT_ACCEL_ANDERSON;
+  // ACX and Anderson mixing move the iterate by extrapolation, outside the
+  // staged schedule's error model: a staged request runs every product as the
+  // split stage.  (Damped steps stay inside it with a step bound of 2 increments.)
+  const int prec = ((acx || anderson) && opt.precision == IPT_PREC_STAGED)
                        ? (opt.staged_bf16 ? IPT_PREC_BF16X3 : IPT_PREC_FP16X3)
                        : opt.precision;
   Plan p = make_plan(n, k, prec, opt.staged_bf16 != 0);
   p.product_kernel = opt.product_kernel;
-  p.acx = acx;
+  p.acx = acx || anderson;  // four iterate buffers and the per-column scratch
   p.damped = damped;
   const int low = p.bf16 ? IPT_PREC_BF16 : IPT_PREC_FP16;
   const int high = p.bf16 ? IPT_PREC_BF16X3 : IPT_PREC_FP16X3;
@@ -585,7 +644,7 @@ ipt_status solve_dense(ipt_handle* h, int64_t n, const void* M, int64_t ldm, int
                   : ((fe.stage == IPT_PREC_BF16X3 || fe.stage == IPT_PREC_FP16X3) ? 3 : 1);
   fe.rebase = (p.staged && opt.z0) ? 1 : 0;
   fe.accurate = 1;
-  fe.defer_e = !acx && !damped && !hz;  // the update / the copy-out reads z = E
+  fe.defer_e = !acx && !damped && !anderson && !hz;  // the update / copy-out reads z = E
   v = alloc_dense(h, p);
   if (v == IPT_OK) {
     if (tm.on) cudaEventRecord(h->ev[4], h->s);
@@ -612,6 +671,9 @@ ipt_status solve_dense(ipt_handle* h, int64_t n, const void* M, int64_t ldm, int
   if (acx) {
     v = acx_loop(h, p, ca, fe, max_iter, opt.acx_sigma, &tm);
     max_iter = 0;  // the Picard loop below does not run
+  } else if (anderson) {
+    v = anderson_loop(h, p, ca, fe, max_iter, &tm);
+    max_iter = 0;
   }
   // learned damping: history, features, alphas and the damped next iterate,
   // formed in F's buffer after each evaluation that does not stop the solve

@@ -142,6 +142,7 @@ struct ControlArgs {
   int acx = 0;                // ACX: the iterate stays in buffer 0 (no ping-pong)
   double step_scale = 1.0;    // largest ||Z_{t+1} - Z_t|| / ||F(Z_t) - Z_t|| (damping: 2)
   int test = 1;               // 0: no stopping test at this evaluation (ACX inner ones)
+  int next_cur = -1;          // with acx: the buffer of the next iterate (Anderson), -1 keep
 };
 
 // Learned-damping model (k_mlp.cu): 6 -> 64 -> 64 -> 1, FP16 parameters.
@@ -154,6 +155,20 @@ cudaError_t launch_mlp_grad(const void* params, const float* X, const float* tar
                             float* grad, double* loss, cudaStream_t s);
 cudaError_t launch_mlp_adam(float* master, void* params, float* grad, float* m, float* v,
                             float lr, float b1, float b2, float eps, int step, cudaStream_t s);
+
+// Anderson mixing in the solve (k_anderson.cu): per-solve state.
+struct AndState {
+  double best_rho;  // smallest residual seen
+  int steps;        // evaluations processed
+  int fallback;     // nonzero: Picard steps from now on
+};
+// After the evaluation g = F(z) (z_prev, g_prev: the previous pair): the
+// per-column mixing weights and out = g - gamma (g - g_prev); `first` (no
+// previous pair) only records the residual.
+cudaError_t launch_anderson_step(const void* z, const void* g, const void* zp, const void* gp,
+                                 void* out, int f64, int n, int k, int64_t ld, double* acc,
+                                 double* gamma, AndState* as, DevState* st, int first,
+                                 cudaStream_t s);
 
 // Learned damping in the solve (k_damp.cu): per-solve state of the model's use.
 struct DampState {

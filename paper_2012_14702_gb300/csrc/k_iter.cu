@@ -629,6 +629,7 @@ __global__ void k_control(DevState* st, ControlArgs a) {
       st->nz_hi = -1;
     }
     if (!a.acx) st->cur = out;
+    else if (a.next_cur >= 0) st->cur = a.next_cur;
   }
   st->prev_rho = rho;
 }

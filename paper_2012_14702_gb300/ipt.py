@@ -167,8 +167,9 @@ class Solver:
         product_kernel: "auto", "single" (one CTA per tile) or "pair" (two CTAs
         per 256-row tile); selects the tensor-core product kernel only.
         accel: None (Picard update), "acx" (Alg. 3, with acx_sigma "column" —
-        one step length per column — or "global") or "damped" (learned damping,
-        damping_model = the model's FP16 parameters as a CUDA tensor)."""
+        one step length per column — or "global"), "damped" (learned damping,
+        damping_model = the model's FP16 parameters as a CUDA tensor) or
+        "anderson" (depth-one Anderson mixing per column)."""
         M = _dev(M, name="M")
         n = M.shape[0]
         if M.dim() != 2 or M.shape[1] != n or M.dtype not in DTYPE:
@@ -185,10 +186,11 @@ class Solver:
             z0t = None
         o = make_options(precision, stop, diverge_bound, stage_switch, verify_fp64, z0t,
                          staged_bf16, record_timing, product_kernel)
-        if accel not in (None, "none", "acx", "damped") or acx_sigma not in ("column", "global"):
-            raise ValueError("accel must be None, 'acx' or 'damped'; acx_sigma 'column' or "
-                             "'global'")
-        o.accel = {"acx": 1, "damped": 2}.get(accel, 0)
+        if accel not in (None, "none", "acx", "damped", "anderson") or \
+                acx_sigma not in ("column", "global"):
+            raise ValueError("accel must be None, 'acx', 'damped' or 'anderson'; acx_sigma "
+                             "'column' or 'global'")
+        o.accel = {"acx": 1, "damped": 2, "anderson": 3}.get(accel, 0)
         o.acx_sigma = 1 if acx_sigma == "global" else 0
         if damping_model is not None:
             damping_model = _dev(damping_model, torch.float16, "damping_model")
@@ -201,8 +203,10 @@ class Solver:
 
     def solve_dense_host(self, M, theta=None, cols=None, tol=1e-6, max_iter=100,
                          precision="staged", stop="residual", z_dtype=torch.float32,
-                         lam_out=None, zt_out=None, record_timing=False):
-        """The same solve from host tensors (pinned for speed); copies are inside the call."""
+                         lam_out=None, zt_out=None, record_timing=False, accel=None,
+                         acx_sigma="column", damping_model=None):
+        """The same solve from host tensors (pinned for speed); copies are inside the call.
+        accel / acx_sigma / damping_model as in solve_dense (the model stays a CUDA tensor)."""
         if M.is_cuda:
             raise ValueError("solve_dense_host takes host tensors")
         M = M.contiguous()
@@ -213,6 +217,12 @@ class Solver:
         lam = lam_out if lam_out is not None else torch.empty(k, dtype=torch.float64)
         Zt = zt_out if zt_out is not None else torch.empty((k, n), dtype=z_dtype)
         o = make_options(precision, stop, record_timing=record_timing)
+        if accel not in (None, "none", "acx", "damped", "anderson"):
+            raise ValueError("accel must be None, 'acx', 'damped' or 'anderson'")
+        o.accel = {"acx": 1, "damped": 2, "anderson": 3}.get(accel, 0)
+        o.acx_sigma = 1 if acx_sigma == "global" else 0
+        if damping_model is not None:
+            o.damping_model = damping_model.data_ptr()
         r = Result()
         _lib.ipt_solve_dense_host(self._h, n, _ptr(M), M.stride(0), DTYPE[M.dtype], _ptr(theta),
                                   k, _ptr(cols), float(tol), int(max_iter), C.byref(o), _ptr(lam),

@@ -100,7 +100,7 @@ def test_acx_option_errors(ipt):
     Mg = cuda(M, torch.float32)
     s = ipt.Solver()
     with pytest.raises(ValueError):
-        s.solve_dense(Mg, accel="anderson")
+        s.solve_dense(Mg, accel="newton")
     o = ipt.make_options("f32", "residual")
     o.accel = 7
     r = ipt.Result()

@@ -557,3 +557,54 @@ def test_damped_solve_secant_rule_extends_domain():
     r = dm.damped_solve(M, th, tol=1e-8, max_iter=400, alpha_fn=rule)
     assert r["status"] == oracle.OK
     np.testing.assert_allclose(np.sort(r["lam"]), np.linalg.eigvalsh(M), atol=1e-8)
+
+
+# ---------------------------------------------------------------- Anderson mixing
+def test_anderson_step_lands_on_fixed_point_of_scalar_multiplier_maps():
+    """For g(z) = z* + a_c (z - z*) (one multiplier per column, contracting or not),
+    a Picard step followed by one depth-one Anderson step gives z* exactly: both
+    residuals are parallel to the first error, and the least-squares weight
+    a/(a-1) cancels it.  A dropped term, a wrong sign or the two residuals swapped
+    breaks this."""
+    from oracle import anderson as an
+    g = np.random.default_rng(7)
+    n, a = 9, np.array([0.5, -0.8, 1.7, -2.5, 0.95, 3.0])
+    zs = g.standard_normal((n, a.size))
+    mapping = lambda z: zs + a[None, :] * (z - zs)
+    z0 = g.standard_normal((n, a.size))
+    g0 = mapping(z0)
+    z1 = g0
+    g1 = mapping(z1)
+    gamma = an.anderson_gamma(g1 - z1, g0 - z0)
+    np.testing.assert_allclose(gamma, a / (a - 1.0), rtol=1e-12)
+    z2 = an.anderson_update(g1, g0, gamma)
+    np.testing.assert_allclose(z2, zs, rtol=1e-10, atol=1e-12)
+    # a vanishing residual difference gives a Picard step
+    assert np.all(an.anderson_gamma(g1 - z1, g1 - z1) == 0.0)
+
+
+def test_anderson_solve_first_step_is_picard_and_keeps_unit_entries():
+    from oracle import anderson as an
+    M, th = w.dense_symmetric(80, 0.05, 3, theta_step=0.25)
+    cols = np.array([3, 17, 40, 79])
+    for m in [1, 2]:
+        a = an.ipt_solve_anderson(M, th, cols=cols, tol=0.0, max_iter=m, stop="increment")
+        p = oracle.ipt_solve(M, th, cols=cols, tol=0.0, max_iter=m, stop="increment")
+        np.testing.assert_array_equal(a["Z"], p["Z"])
+    a = an.ipt_solve_anderson(M, th, cols=cols, tol=0.0, max_iter=7, stop="increment",
+                              history=True)
+    assert np.all(a["Z"][cols, np.arange(cols.size)] == 1.0)
+    assert len(a["gamma"]) == 6 and np.all(a["gamma"][0] == 0.0)
+
+
+def test_anderson_solve_converges_outside_picard_domain_to_eigh():
+    """n = 128, theta_i = i/4, Delta N(0,1)*0.08: the Picard iteration does not reach
+    rho <= 1e-10 in 300 evaluations; Anderson mixing does, and its eigenvalues are
+    LAPACK's."""
+    from oracle import anderson as an
+    M, th = w.dense_symmetric(128, 0.08, 3, theta_step=0.25)
+    p = oracle.ipt_solve(M, th, tol=1e-10, max_iter=300, stop="residual")
+    assert p["status"] != oracle.OK
+    a = an.ipt_solve_anderson(M, th, tol=1e-10, max_iter=300)
+    assert a["status"] == oracle.OK
+    np.testing.assert_allclose(np.sort(a["lam"]), np.linalg.eigvalsh(M), atol=1e-9)
