@@ -35,6 +35,9 @@ cudaError_t ensure(Buf& b, size_t bytes) {
 
 // Sparse solves enqueue this many evaluations per host synchronisation.
 constexpr int kCsrChunk = 4;
+// Dense tensor-core solves (device-chosen operands) likewise.
+constexpr int kDenseChunk = 6;
+constexpr int kEvbSlots = kDenseChunk > kCsrChunk ? kDenseChunk : kCsrChunk;
 
 }  // namespace
 
@@ -61,7 +64,7 @@ struct ipt_handle {
   DevState* hst = nullptr;          // pinned mirror of the controller's words
   DevState* hinit = nullptr;        // pinned initial controller words of a solve
   cudaEvent_t ev[8] = {};           // pre-pass / product / setup / finalize brackets
-  cudaEvent_t evb[4 * kCsrChunk] = {};  // per-evaluation brackets of a sparse chunk
+  cudaEvent_t evb[4 * kEvbSlots] = {};  // per-evaluation brackets of an enqueued chunk
   cudaStream_t cs = nullptr;        // host-buffer entry point: device-to-host copy stream
   cudaEvent_t zready = nullptr;     // an iterate is complete on the solve stream
   cudaEvent_t zcopied[3] = {};      // the last copy out of Z buffer b has finished
@@ -298,17 +301,13 @@ struct Timing {
 ipt_status ensure_events(ipt_handle* h) {
   for (int i = 0; i < 8; ++i)
     if (!h->ev[i]) CK(cudaEventCreate(&h->ev[i]));
-  for (int i = 0; i < 4 * kCsrChunk; ++i)
+  for (int i = 0; i < 4 * kEvbSlots; ++i)
     if (!h->evb[i]) CK(cudaEventCreate(&h->evb[i]));
   return IPT_OK;
 }
 
 // Buffer receiving F: neither the current iterate nor the base.
-int free_buffer(int cur, int base) {
-  for (int b = 0; b < 3; ++b)
-    if (b != cur && b != base) return b;
-  return 0;
-}
+int free_buffer(int cur, int base) { return zbuf_free(cur, base); }
 
 // One evaluation at Z buffer `cur`: d, product of V = Z - Z_base (in `passes`
 // passes of arithmetic `stage`; 0 = product-free first evaluation at Z = E),
@@ -387,6 +386,49 @@ ipt_status evaluate(ipt_handle* h, const Plan& p, int cur, int base, int stage, 
     }
   }
   CK(cudaGetLastError());
+  if (t) CK(cudaEventRecord(ev[3], s));
+  h->launches += 2;
+  return IPT_OK;
+}
+
+// One tensor-core evaluation whose operands the device chooses (MapArgs::dyn,
+// DynZ): the current iterate, the base, the pass count and the re-base come
+// from the controller's state, so the host can enqueue evaluations without
+// reading its choices.  Events ev[0..3] as in evaluate().
+ipt_status evaluate_dyn(ipt_handle* h, const Plan& p, Timing* tm, cudaEvent_t* ev) {
+  cudaStream_t s = h->s;
+  DevState* st = dst(h);
+  const bool t = tm && tm->on;
+  if (t) CK(cudaEventRecord(ev[0], s));
+  DynZ dz;
+  for (int b = 0; b < 3; ++b) dz.z[b] = (const float*)h->z[b].p;
+  dz.dyn = 1;
+  launch_prepass_tc((const float*)h->drow.p, nullptr, nullptr, p.npad, (const int32_t*)h->icol.p,
+                    p.kpad, p.bf16 ? 1 : 0, (double*)h->d.p, (uint16_t*)h->wh.p,
+                    (uint16_t*)h->wl.p, (float*)h->sinv.p, st, s, dz);
+  if (t) {
+    CK(cudaEventRecord(ev[1], s));
+    CK(cudaEventRecord(ev[2], s));
+  }
+  MapArgs<float> a{};
+  a.DT = (const float*)h->dt.p;
+  a.d = (const double*)h->d.p;
+  a.icol = (const int32_t*)h->icol.p;
+  a.th_hi = (const float*)h->thh.p;
+  a.th_lo = (const float*)h->thl.p;
+  a.rinv = (const float*)h->rinv.p;
+  a.sinv = (const float*)h->sinv.p;
+  a.ld = p.npad;
+  a.n = p.n;
+  a.k = p.k;
+  a.st = st;
+  for (int b = 0; b < 3; ++b) a.zsel[b] = (float*)h->z[b].p;
+  a.pstore = p.staged ? (float*)h->pbuf.p : nullptr;
+  a.dyn = 1;
+  // the pass count given here only sizes nothing: the kernel reads it from st
+  CK(launch_gemm_tc((const uint16_t*)h->dh.p, (const uint16_t*)h->dl.p,
+                    (const uint16_t*)h->wh.p, (const uint16_t*)h->wl.p, a, p.npad, p.kpad, 1,
+                    p.bf16 ? 1 : 0, p.product_kernel, s));
   if (t) CK(cudaEventRecord(ev[3], s));
   h->launches += 2;
   return IPT_OK;
@@ -521,6 +563,58 @@ ipt_status acx_loop(ipt_handle* h, const Plan& p, const ControlArgs& ca, const F
       collect_timing(h, passes, tm, h->evb + 4 * q);
     }
     done_evals = h->hst->iter;
+    if (h->hst->timeout) return IPT_DEVICE_TIMEOUT;
+    if (h->hst->done) break;
+  }
+  return IPT_OK;
+}
+
+// The Picard loop of a tensor-core solve without per-evaluation host work:
+// the first evaluation as planned by the host, then evaluations with
+// device-chosen operands, kDenseChunk per host synchronisation (every kernel
+// returns at entry once the controller has stopped, so the evaluations
+// enqueued past the stop cost only their launches).
+ipt_status dense_chunked_loop(ipt_handle* h, const Plan& p, const ControlArgs& ca,
+                              const FirstEval& fe, int max_iter, Timing* tm) {
+  cudaStream_t s = h->s;
+  DevState* st = dst(h);
+  const bool t = tm && tm->on;
+  for (int it0 = 0; it0 < max_iter; it0 += kDenseChunk) {
+    const int nb = std::min(kDenseChunk, max_iter - it0);
+    for (int q = 0; q < nb; ++q) {
+      cudaEvent_t* ev = h->evb + 4 * q;
+      const ipt_status v = it0 + q == 0
+                               ? evaluate(h, p, 0, -1, fe.stage, fe.passes, fe.rebase, tm, -1,
+                                          nullptr, ev)
+                               : evaluate_dyn(h, p, tm, ev);
+      if (v != IPT_OK) return v;
+      launch_control(st, ca, s);
+      h->launches += 1;
+    }
+    // with timing, the stage history tells each evaluation's pass count
+    if (cudaGetLastError() != cudaSuccess ||
+        cudaMemcpyAsync(h->hst, st, t ? sizeof(DevState) : kStateHead, cudaMemcpyDeviceToHost,
+                        s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      return IPT_CUDA_ERROR;
+    if (it0 == 0) {
+      const ipt_status fv = status_from_flags(h->hst->flags);
+      if (fv != IPT_OK) return fv;
+      if (t) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, h->ev[4], h->ev[5]) == cudaSuccess) tm->setup_ms = ms;
+      }
+    }
+    if (t) {
+      const int ran = std::min(nb, h->hst->iter - it0);
+      for (int q = 0; q < ran; ++q) {
+        const int e = it0 + q;
+        const int stg = e < IPT_MAX_HISTORY ? h->hst->hist_stage[e] : p.prec;
+        const int passes =
+            stg < 0 ? 0 : ((stg == IPT_PREC_BF16X3 || stg == IPT_PREC_FP16X3) ? 3 : 1);
+        collect_timing(h, passes, tm, h->evb + 4 * q);
+      }
+    }
     if (h->hst->timeout) return IPT_DEVICE_TIMEOUT;
     if (h->hst->done) break;
   }
@@ -673,6 +767,9 @@ ipt_status solve_dense(ipt_handle* h, int64_t n, const void* M, int64_t ldm, int
     max_iter = 0;  // the Picard loop below does not run
   } else if (anderson) {
     v = anderson_loop(h, p, ca, fe, max_iter, &tm);
+    max_iter = 0;
+  } else if (p.tc && !damped && !hz) {
+    v = dense_chunked_loop(h, p, ca, fe, max_iter, &tm);
     max_iter = 0;
   }
   // learned damping: history, features, alphas and the damped next iterate,
@@ -881,7 +978,7 @@ ipt_status ipt_destroy(ipt_handle* h) {
     if (b->p) cudaFree(b->p);
   for (int i = 0; i < 8; ++i)
     if (h->ev[i]) cudaEventDestroy(h->ev[i]);
-  for (int i = 0; i < 4 * kCsrChunk; ++i)
+  for (int i = 0; i < 4 * kEvbSlots; ++i)
     if (h->evb[i]) cudaEventDestroy(h->evb[i]);
   if (h->zready) cudaEventDestroy(h->zready);
   for (int b = 0; b < 3; ++b)

@@ -93,7 +93,30 @@ struct MapArgs {
   int64_t ld;            // npad
   int n, k;
   DevState* st;
+  // Device-chosen operands (tensor-core evaluations enqueued ahead of the
+  // host): with dyn set, the kernels take the iterate zsel[cur], write F into
+  // zsel[zbuf_free(cur, base)], read P_b from pstore (base >= 0) or DT by
+  // cols[c] (Z_b = E), store P into pstore when rebase, and run the pass count
+  // of the device state, all read from st at entry.
+  T* zsel[3];
+  float* pstore;
+  int dyn;
 };
+
+// Device-chosen pre-pass operands (see MapArgs::dyn): with dyn set, Z is
+// z[cur], Z_b is z[base] (none for base -1) and the lo split is written only
+// for a 3-pass product, all read from the device state at entry.
+struct DynZ {
+  const float* z[3];
+  int dyn;
+};
+
+// The Z buffer receiving F: neither the current iterate nor the base.
+__host__ __device__ inline int zbuf_free(int cur, int base) {
+  for (int b = 0; b < 3; ++b)
+    if (b != cur && b != base) return b;
+  return 0;
+}
 
 // ---------------------------------------------------------------- launchers
 // setup (k_setup.cu)
@@ -122,7 +145,8 @@ void launch_prepass(const void* Drow, const void* Z, int f64, int64_t ld, const 
 // Wl == nullptr: the lo part is not written (a 1-pass product follows)
 void launch_prepass_tc(const float* Drow, const float* Z, const float* Zbase, int64_t ld,
                        const int32_t* icol, int kpad, int bf16, double* d, uint16_t* Wh,
-                       uint16_t* Wl, float* sinv, DevState* st, cudaStream_t s);
+                       uint16_t* Wl, float* sinv, DevState* st, cudaStream_t s,
+                       const DynZ& dz = DynZ{});
 // The evaluation at Z = E with no product (P = Delta E exactly): F = E - G o Delta_{., cols}.
 void launch_map_first(const MapArgs<float>& a, int npad, int kpad, double* d, double* part,
                       cudaStream_t s);

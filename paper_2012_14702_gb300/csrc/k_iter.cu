@@ -90,8 +90,13 @@ __global__ void k_prepass_tc(const float* __restrict__ Drow, const float* __rest
                              const int32_t* __restrict__ icol, int kpad,
                              double* __restrict__ d, uint16_t* __restrict__ Wh,
                              uint16_t* __restrict__ Wl, float* __restrict__ sinv,
-                             const DevState* st) {
+                             const DevState* st, DynZ dz) {
   if (st->done) return;
+  if (dz.dyn) {
+    Z = dz.z[st->cur];
+    Zbase = st->base >= 0 ? dz.z[st->base] : nullptr;
+    if (st->passes != 3) Wl = nullptr;
+  }
   const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (c >= kpad) return;
   const int i = icol[c];
@@ -149,8 +154,13 @@ __global__ void __launch_bounds__(1024)
                      const float* __restrict__ Zbase, int64_t ld,
                      const int32_t* __restrict__ icol, double* __restrict__ d,
                      uint16_t* __restrict__ Wh, uint16_t* __restrict__ Wl,
-                     float* __restrict__ sinv, const DevState* st) {
+                     float* __restrict__ sinv, const DevState* st, DynZ dz) {
   if (st->done) return;
+  if (dz.dyn) {
+    Z = dz.z[st->cur];
+    Zbase = st->base >= 0 ? dz.z[st->base] : nullptr;
+    if (st->passes != 3) Wl = nullptr;
+  }
   const int c = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int nw = blockDim.x >> 5;
   const int i = icol[c];
@@ -536,12 +546,6 @@ __global__ void __launch_bounds__(1024)
 // otherwise the next evaluation uses the split product and stores its P as
 // the new base.  Only evaluations whose predicted product error is below a
 // tenth of tol may declare convergence.
-__device__ __forceinline__ int free_buffer(int cur, int base) {
-  for (int b = 0; b < 3; ++b)
-    if (b != cur && b != base) return b;
-  return 0;
-}
-
 __global__ void k_control(DevState* st, ControlArgs a) {
   if (st->done) return;
   const int it = st->iter;
@@ -585,7 +589,7 @@ __global__ void k_control(DevState* st, ControlArgs a) {
     st->answer = st->cur;
   } else {
     const int cur = st->cur, base = st->base;
-    const int out = free_buffer(cur, base);  // where this evaluation wrote F
+    const int out = zbuf_free(cur, base);  // where this evaluation wrote F
     if (staged) {
       double kappa = st->kappa > 0.0 ? st->kappa : r0 / sqrt((double)a.k);
       if (passes > 0 && st->sv > 0.0 && pv > 0.0) kappa = pv / st->sv;
@@ -653,7 +657,8 @@ void launch_prepass(const void* Drow, const void* Z, int f64, int64_t ld, const 
 
 void launch_prepass_tc(const float* Drow, const float* Z, const float* Zbase, int64_t ld,
                        const int32_t* icol, int kpad, int bf16, double* d, uint16_t* Wh,
-                       uint16_t* Wl, float* sinv, DevState* st, cudaStream_t s) {
+                       uint16_t* Wl, float* sinv, DevState* st, cudaStream_t s,
+                       const DynZ& dz) {
   constexpr int VPT = IPT_PREPASS_VPT;
   const int64_t n4 = ld / 4;
   if (n4 <= (int64_t)VPT * 1024) {
@@ -661,17 +666,19 @@ void launch_prepass_tc(const float* Drow, const float* Z, const float* Zbase, in
     threads = ((threads + 31) / 32) * 32;
     if (bf16)
       k_prepass_tc_reg<true, VPT><<<kpad, threads, 0, s>>>(Drow, Z, Zbase, ld, icol, d, Wh, Wl,
-                                                            sinv, st);
+                                                            sinv, st, dz);
     else
       k_prepass_tc_reg<false, VPT><<<kpad, threads, 0, s>>>(Drow, Z, Zbase, ld, icol, d, Wh, Wl,
-                                                             sinv, st);
+                                                             sinv, st, dz);
     return;
   }
   unsigned g = (unsigned)((kpad + 7) / 8);
   if (bf16)
-    k_prepass_tc<true><<<g, 256, 0, s>>>(Drow, Z, Zbase, ld, icol, kpad, d, Wh, Wl, sinv, st);
+    k_prepass_tc<true><<<g, 256, 0, s>>>(Drow, Z, Zbase, ld, icol, kpad, d, Wh, Wl, sinv, st,
+                                         dz);
   else
-    k_prepass_tc<false><<<g, 256, 0, s>>>(Drow, Z, Zbase, ld, icol, kpad, d, Wh, Wl, sinv, st);
+    k_prepass_tc<false><<<g, 256, 0, s>>>(Drow, Z, Zbase, ld, icol, kpad, d, Wh, Wl, sinv, st,
+                                          dz);
 }
 
 void launch_gemm_simt_f64(const double* Drow, const MapArgs<double>& a, int npad, int kpad,

@@ -352,6 +352,21 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   constexpr int B_BYTES = Shape<MODE>::B_BYTES;
   constexpr int STAGE_BYTES = Shape<MODE>::STAGE_BYTES;
   if (a.st->done) return;  // uniform over the grid, so over each cluster
+  // operands: as launched, or (dyn) chosen by the controller's state
+  const float* Zin = a.Zin;
+  float* Fout = a.Fout;
+  const float* Pbase = a.Pbase;
+  int pbase_by_icol = a.pbase_by_icol;
+  float* Pout = a.Pout;
+  if (a.dyn) {
+    const int cur = a.st->cur, base = a.st->base;
+    passes = a.st->passes;
+    Zin = a.zsel[cur];
+    Fout = a.zsel[zbuf_free(cur, base)];
+    Pbase = base >= 0 ? a.pstore : a.DT;
+    pbase_by_icol = base >= 0 ? 0 : 1;
+    Pout = a.st->rebase ? a.pstore : nullptr;
+  }
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
@@ -582,9 +597,9 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
           const int64_t o = (int64_t)(cbase + c0 + i) * ld + j;
           // P_base: column cols[c] of Delta (Z_base = E) or the stored P of column c.
           // Streamed once: evict-first, so the reused operand panels stay in L2.
-          const int64_t ob = a.pbase_by_icol ? (int64_t)ic * ld + j : o;
-          z[i] = (jok && ic >= 0) ? __ldcs(a.Zin + o) : 0.f;
-          pb[i] = (jok && ic >= 0) ? __ldcs(a.Pbase + ob) : 0.f;
+          const int64_t ob = pbase_by_icol ? (int64_t)ic * ld + j : o;
+          z[i] = (jok && ic >= 0) ? __ldcs(Zin + o) : 0.f;
+          pb[i] = (jok && ic >= 0) ? __ldcs(Pbase + ob) : 0.f;
         }
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
@@ -594,13 +609,13 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
           const int64_t o = (int64_t)(cbase + c0 + i) * ld + j;
           const float dv = v[i] * (rj * ci.s);  // Delta V, scales undone exactly
           const float p = pb[i] + dv;           // P = P_base + Delta V
-          if (a.Pout) __stcs(a.Pout + o, p);
+          if (Pout) __stcs(Pout + o, p);
           s_pv = fmaf(dv, dv, s_pv);
           float f, r;
           const float gap = gap2f(hj, lj, ci.hi, ci.lo);
           if (gap == 0.f && j != ic) flag_degenerate(a.st);
           map_entry<float>(z[i], p, ci.d, gap, j == ic, f, r);
-          __stcs(a.Fout + o, f);
+          __stcs(Fout + o, f);
           const float df = f - z[i];
           s_inc = fmaf(df, df, s_inc);
           s_z = fmaf(z[i], z[i], s_z);
