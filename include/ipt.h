@@ -294,6 +294,24 @@ ipt_status ipt_set_batched_tiles(ipt_handle* h, const int32_t* tiles);
 ipt_status ipt_get_batched_tiles(const ipt_handle* h, int32_t* tiles);
 
 /*
+ * Check of the failure path of the device-side waits.  Every wait of the
+ * tensor-core product kernel on a shared-memory barrier gives up after a time
+ * limit (2 s), records a timeout in the solve's device state and lets the
+ * kernel drain and return, and the solve reports IPT_DEVICE_TIMEOUT.  This call
+ * runs the same wait in a one-CTA kernel on the caller's stream (NULL = legacy
+ * default stream) and synchronises that stream:
+ *   arrive      nonzero: a second warp arrives on the barrier (the wait succeeds);
+ *               0: nothing ever arrives (the wait must give up)
+ *   limit_s     the wait's time limit in seconds, 0 < limit_s <= 10
+ *   succeeded   host (written): 1 if the wait completed, 0 if it gave up
+ *   waited_s    host (written, may be NULL): seconds the wait took
+ * Returns IPT_INVALID_ARG for a bad limit or NULL `succeeded`, IPT_CUDA_ERROR on
+ * a CUDA failure, else IPT_OK.  No GPU fault or hang is involved either way.
+ */
+ipt_status ipt_check_bounded_wait(int arrive, double limit_s, void* stream, int32_t* succeeded,
+                                  double* waited_s);
+
+/*
  * The damping model of IPT_ACCEL_DAMPED and its training (no counterpart in the
  * paper).  A 6 -> 64 -> 64 -> 1 perceptron: h1 = tanh(x W1 + b1),
  * h2 = tanh(h1 W2 + b2), y = h2 W3 + b3, alpha = 2 / (1 + exp(-y)).  Parameters:

@@ -1496,6 +1496,24 @@ ipt_status ipt_solve_batched(ipt_handle* h, int64_t count, const int64_t* n, con
   return (ipt_status)agg;
 }
 
+ipt_status ipt_check_bounded_wait(int arrive, double limit_s, void* stream, int32_t* succeeded,
+                                  double* waited_s) {
+  if (!succeeded || !(limit_s > 0.0) || limit_s > 10.0) return IPT_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  long long* d = nullptr;
+  if (cudaMalloc(&d, 2 * sizeof(long long)) != cudaSuccess) return IPT_CUDA_ERROR;
+  long long hv[2] = {0, 0};
+  const bool ok =
+      launch_wait_check(arrive ? 1 : 0, (uint64_t)(limit_s * 1e9), d, s) == cudaSuccess &&
+      cudaMemcpyAsync(hv, d, sizeof(hv), cudaMemcpyDeviceToHost, s) == cudaSuccess &&
+      cudaStreamSynchronize(s) == cudaSuccess;
+  cudaFree(d);
+  if (!ok) return IPT_CUDA_ERROR;
+  *succeeded = (int32_t)hv[0];
+  if (waited_s) *waited_s = (double)hv[1] * 1e-9;
+  return IPT_OK;
+}
+
 ipt_status ipt_set_batched_tiles(ipt_handle* h, const int32_t* tiles) {
   if (!h || !tiles) return IPT_INVALID_ARG;
   for (int c = 0; c < kBatchClasses; ++c)

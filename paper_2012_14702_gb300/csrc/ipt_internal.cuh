@@ -180,6 +180,9 @@ cudaError_t launch_mlp_grad(const void* params, const float* X, const float* tar
 cudaError_t launch_mlp_adam(float* master, void* params, float* grad, float* m, float* v,
                             float lr, float b1, float b2, float eps, int step, cudaStream_t s);
 
+// Bounded-wait check (k_diag.cu): out[0] = 1 if the wait succeeded, out[1] = ns waited.
+cudaError_t launch_wait_check(int arrive, uint64_t limit_ns, long long* out, cudaStream_t s);
+
 // Anderson mixing in the solve (k_anderson.cu): per-solve state.
 struct AndState {
   double best_rho;  // smallest residual seen

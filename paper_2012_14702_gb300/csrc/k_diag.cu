@@ -1,0 +1,38 @@
+// Bounded-wait check: exercises the give-up path of the shared-memory barrier
+// wait that every waiting role of the tensor-core product kernel uses, without
+// any fault or hang.  One CTA; thread 0 initialises a barrier for one arrival
+// and waits on its first phase with a caller-given limit.  With `arrive` a
+// thread of the second warp arrives and the wait must succeed; without it
+// nothing ever arrives and the wait must give up once the limit has passed.
+#include "ipt_internal.cuh"
+#include "mbar.cuh"
+
+namespace ipt {
+
+namespace {
+
+__global__ void k_wait_check(int arrive, uint64_t limit_ns, long long* out) {
+  __shared__ uint64_t bar;
+  __shared__ int abort_flag;
+  if (threadIdx.x == 0) {
+    mbar::mbar_init(&bar, 1);
+    abort_flag = 0;
+  }
+  __syncthreads();
+  if (threadIdx.x == 32 && arrive) mbar::mbar_arrive(&bar);
+  if (threadIdx.x == 0) {
+    const uint64_t t0 = mbar::gtimer();
+    const bool ok = mbar::wait_bounded(&bar, 0u, &abort_flag, limit_ns);
+    out[0] = ok ? 1 : 0;
+    out[1] = (long long)(mbar::gtimer() - t0);
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_wait_check(int arrive, uint64_t limit_ns, long long* out, cudaStream_t s) {
+  k_wait_check<<<1, 64, 0, s>>>(arrive, limit_ns, out);
+  return cudaGetLastError();
+}
+
+}  // namespace ipt

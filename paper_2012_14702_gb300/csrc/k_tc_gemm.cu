@@ -29,12 +29,15 @@
 // Every mbarrier wait is bounded (globaltimer); on expiry the CTA records a
 // timeout in DevState, drains its TMA loads and MMAs, frees TMEM and returns.
 #include "ipt_internal.cuh"
+#include "mbar.cuh"
 
 #include <cuda.h>
 
 namespace ipt {
 
 namespace {
+
+using namespace mbar;
 
 constexpr int BM = 128, BN = 256, BK = 64;
 constexpr int A_BYTES = BM * BK * 2;
@@ -62,7 +65,7 @@ constexpr int EPI_WARPS = 8;  // two per TMEM lane quarter, each owning half of 
 constexpr int NUM_THREADS = 64 + 32 * EPI_WARPS;
 constexpr int EPI_THREADS = 32 * EPI_WARPS;
 constexpr int EPI_COLS = BN / 2;  // columns of a tile one epilogue warp handles
-constexpr uint64_t kTimeoutNs = 2000000000ull;  // 2 s: far above any legitimate wait
+constexpr uint64_t kTimeoutNs = kWaitLimitNs;
 #ifndef IPT_GROUP_M
 #define IPT_GROUP_M 16
 #endif
@@ -113,64 +116,6 @@ constexpr uint32_t idesc_for(bool bf16, int m) {
          ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
 }
 
-__device__ __forceinline__ uint32_t su32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ uint64_t gtimer() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)),
-               "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(b)) : "memory");
-}
-__device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(su32(b)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// The same test with cluster-scope acquire: for barriers that threads of the
-// peer CTA arrive on.
-__device__ __forceinline__ bool mbar_try_cluster(uint64_t* b, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(su32(b)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// Wait for the phase `parity` of barrier b.  False on timeout or when another
-// role has aborted (then the caller stops issuing and falls through to drain).
-template <bool CLUSTER = false>
-__device__ __noinline__ bool wait_bounded(uint64_t* b, uint32_t parity, volatile int* abort) {
-  auto test = [&]() { return CLUSTER ? mbar_try_cluster(b, parity) : mbar_try(b, parity); };
-  if (test()) return true;
-  const uint64_t t0 = gtimer();
-  for (;;) {
-#pragma unroll 1
-    for (int i = 0; i < 32; ++i)
-      if (test()) return true;
-    if (*abort) return false;
-    if (gtimer() - t0 > kTimeoutNs) return false;
-  }
-}
 // Shared::cluster address of the object at the same offset as `p` in the CTA
 // of cluster rank `rank`.
 __device__ __forceinline__ uint32_t peer_addr(const void* p, uint32_t rank) {

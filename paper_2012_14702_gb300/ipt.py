@@ -315,11 +315,27 @@ class Solver:
         return lam, Zt.t(), r.to_dict()
 
 
+def check_bounded_wait(arrive, limit_s=0.2, stream=None):
+    """Run the product kernel's bounded barrier wait in a one-CTA kernel (see
+    ipt_check_bounded_wait): returns (succeeded, seconds waited)."""
+    ok = C.c_int32()
+    waited = C.c_double()
+    s = torch.cuda.current_stream().cuda_stream if stream is None else stream
+    st = _lib.ipt_check_bounded_wait(int(arrive), float(limit_s), C.c_void_p(s), C.byref(ok),
+                                     C.byref(waited))
+    if st != 0:
+        raise RuntimeError(f"ipt_check_bounded_wait: {STATUS.get(st, st)}")
+    return bool(ok.value), waited.value
+
+
 def _batched_argtypes():
     _lib.ipt_solve_batched.argtypes = [_vp, _i64, C.POINTER(C.c_int64), _vp, _vp, _d, _i32,
                                        C.POINTER(Options), _vp, _vp, _vp, _vp,
                                        C.POINTER(Result)]
     _lib.ipt_solve_batched.restype = _i32
+    _lib.ipt_check_bounded_wait.argtypes = [C.c_int, _d, _vp, C.POINTER(C.c_int32),
+                                            C.POINTER(C.c_double)]
+    _lib.ipt_check_bounded_wait.restype = _i32
     for name in ("ipt_set_batched_tiles", "ipt_get_batched_tiles"):
         getattr(_lib, name).argtypes = [_vp, C.POINTER(C.c_int32)]
         getattr(_lib, name).restype = _i32
