@@ -307,3 +307,29 @@ def test_n8192_staged_sampled_columns_match_oracle(ipt, eps, seed):
     E = oracle.unit_columns(n, sample)
     err = np.linalg.norm(Zs - ref["Z"]) / np.linalg.norm(ref["Z"] - E)
     assert err <= 1e-4, err
+
+
+@pytest.mark.parametrize("symmetric", [False, True])
+def test_paper_dense_family_full_spectrum(ipt, symmetric):
+    """The paper's own full-spectrum family, M = diag(i) + 0.01 R with R ~ U[0, 1]
+    (non-symmetric, and its symmetrisation), n = 1024: FP64 to an increment of
+    1e-12 (the paper's tolerance) within 1e-10 relative of the oracle's eigenvalues,
+    and the staged tensor-core solve to rho <= 1e-6 within 1e-5."""
+    n = 1024
+    M, th = w.dense_paper(n, 1e-2, seed=9, symmetric=symmetric)
+    ref = oracle.ipt_solve(M, th, tol=1e-12, max_iter=100, stop="increment")
+    assert ref["status"] == oracle.OK
+    s = ipt.Solver()
+    lam, Z, info = s.solve_dense(torch.as_tensor(M, device="cuda"),
+                                 theta=torch.as_tensor(th, device="cuda"), tol=1e-12,
+                                 max_iter=100, precision="f64", stop="increment",
+                                 z_dtype=torch.float64)
+    assert info["status"] == "OK" and abs(info["iterations"] - ref["iterations"]) <= 1
+    np.testing.assert_allclose(lam.cpu().numpy(), ref["lam"], rtol=1e-10)
+    err = np.linalg.norm(Z.cpu().numpy() - ref["Z"]) / np.linalg.norm(ref["Z"] - np.eye(n))
+    assert err <= 1e-8, err
+    lam32, Z32, info32 = s.solve_dense(torch.as_tensor(M, dtype=torch.float32, device="cuda"),
+                                       theta=torch.as_tensor(th, device="cuda"), tol=1e-6,
+                                       max_iter=60, precision="staged", verify_fp64=True)
+    assert info32["status"] == "OK" and info32["rho_fp64"] <= 2e-6, info32
+    np.testing.assert_allclose(lam32.cpu().numpy(), ref["lam"], rtol=1e-5)
