@@ -253,15 +253,17 @@ ipt_status ipt_solve_csr(ipt_handle* h, int64_t n, int64_t nnz, const int32_t* r
  * Many independent dense problems, each solved by Alg. 2 (all n_p eigenpairs,
  * theta = the given partition or diag(M_p)) with its own stopping test, in
  * one persistent launch: the GPU takes the problems largest first and runs
- * every evaluation of a problem without host involvement.  FP32 product and
- * iterate with the exact Delta E term (as IPT_PREC_F32).
+ * every evaluation of a problem without host involvement.  The exact Delta E
+ * term plus the product Delta W (W = Z - E): opt->precision IPT_PREC_BF16X3
+ * runs it on the tensor cores as split-BF16 x3 (128 x 128 tiles), IPT_PREC_BF16
+ * as one BF16 pass, anything else as an FP32 SIMT product; FP32 iterate.
  *   count          number of problems (>= 1)
  *   n              HOST array of count problem orders, 1 <= n_p <= 1024
  *   M              device, FP32, the problems packed back to back: problem p is
  *                  row-major n_p x n_p at element offset sum_{q<p} n_q^2
  *   theta          device FP64, packed at offset sum_{q<p} n_q, or NULL = diag(M_p)
  *   tol, max_iter  as in ipt_solve_dense (max_iter per problem)
- *   opt            stop and diverge_bound are used (NULL = defaults)
+ *   opt            precision, stop and diverge_bound are used (NULL = defaults: FP32)
  *   lambda         device FP64, packed like theta (written)
  *   Z              device FP32, packed like M, each block column-major (column c =
  *                  eigenvector continued from e_c) (written)

@@ -1364,12 +1364,15 @@ ipt_status ipt_solve_batched(ipt_handle* h, int64_t count, const int64_t* n, con
   int dev = 0, nsm = 0;
   CK(cudaGetDevice(&dev));
   CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-  const int ctas = (int)std::min<int64_t>(count, (int64_t)nsm * batched_ctas_per_sm());
+  // BF16 tensor-core products (split x3 or one pass) or the FP32 SIMT product
+  const int tc_passes =
+      opt.precision == IPT_PREC_BF16X3 ? 3 : (opt.precision == IPT_PREC_BF16 ? 1 : 0);
+  const int ctas = (int)std::min<int64_t>(count, (int64_t)nsm * batched_ctas_per_sm(tc_passes));
   const int64_t max_n2 = max_n * max_n;
   // the tuning schedules: up to kTuneSample problems of each class not tuned yet,
   // evenly spread over the class (largest first)
   int nsample[kBatchClasses] = {};
-  {
+  if (!tc_passes) {
     std::vector<int> members[kBatchClasses];
     for (size_t i = 0; i < cnt; ++i) members[batch_class_host(nsz[order[i]])].push_back(order[i]);
     for (int c = 0; c < kBatchClasses; ++c) {
@@ -1415,7 +1418,7 @@ ipt_status ipt_solve_batched(ipt_handle* h, int64_t count, const int64_t* n, con
         CK(launch_batched(M, theta, d_moff, d_voff, d_nsz, d_sample + c * kTuneSample,
                           nsample[c], max_n2, tol, max_iter, opt.stop, opt.diverge_bound,
                           lambda, Z, status, iters, static_cast<float*>(h->bscratch.p), queue,
-                          tiles, std::min(ctas, nsample[c]), s));
+                          tiles, std::min(ctas, nsample[c]), 0, s));
         CK(cudaEventRecord(h->ev[1], s));
         CK(cudaEventSynchronize(h->ev[1]));
         CK(cudaEventElapsedTime(&ms, h->ev[0], h->ev[1]));
@@ -1446,6 +1449,7 @@ ipt_status ipt_solve_batched(ipt_handle* h, int64_t count, const int64_t* n, con
   mix((uint64_t)cnt);
   mix((uint64_t)ctas);
   for (int c = 0; c < kBatchClasses; ++c) mix((uint64_t)tiles[c]);
+  mix((uint64_t)tc_passes);
   if (!h->bexec || h->bkey != key) {
     if (h->bexec) cudaGraphExecDestroy(h->bexec);
     if (h->bgraph) cudaGraphDestroy(h->bgraph);
@@ -1458,7 +1462,7 @@ ipt_status ipt_solve_batched(ipt_handle* h, int64_t count, const int64_t* n, con
     cudaMemsetAsync(queue, 0, sizeof(int), cs);
     launch_batched(M, theta, d_moff, d_voff, d_nsz, d_order, (int)count, max_n2, tol, max_iter,
                    opt.stop, opt.diverge_bound, lambda, Z, status, iters,
-                   static_cast<float*>(h->bscratch.p), queue, tiles, ctas, cs);
+                   static_cast<float*>(h->bscratch.p), queue, tiles, ctas, tc_passes, cs);
     CK(cudaStreamEndCapture(cs, &h->bgraph));
     CK(cudaGraphInstantiate(&h->bexec, h->bgraph, 0));
     h->bkey = key;

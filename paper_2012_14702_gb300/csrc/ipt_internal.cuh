@@ -224,8 +224,9 @@ cudaError_t launch_batched(const float* M, const double* theta, const int64_t* m
                            int64_t max_n2, double tol, int max_iter, int stop,
                            double diverge_bound, double* lambda, float* Z, int* status,
                            int* iters, float* scratch, int* queue, const int* tiles, int ctas,
-                           cudaStream_t s);
-int batched_ctas_per_sm();
+                           int tc_passes, cudaStream_t s);
+// resident CTAs per SM of the batched kernel (tc: the tensor-core variant)
+int batched_ctas_per_sm(int tc);
 
 // Alg. 3 extrapolation of order p (2 or 3) in place: z (buffer of the
 // extrapolated iterate) from f1 = f(z), f2, f3 (column-major, leading dim ld).

@@ -230,11 +230,13 @@ class Solver:
         return lam, Zt.t(), r.to_dict()
 
     def solve_batched(self, sizes, M, theta=None, tol=1e-6, max_iter=100, stop="residual",
-                      diverge_bound=1e8, record_timing=False):
+                      diverge_bound=1e8, record_timing=False, precision="f32"):
         """Many dense problems in one launch (Alg. 2 on each, all eigenpairs).
 
         sizes: the problem orders (host sequence); M: CUDA float32 tensor with the
         problems packed row-major back to back; theta: packed CUDA float64 or None.
+        precision: "f32" (FP32 SIMT product), "bf16x3" (split-BF16 tensor-core
+        product, three passes) or "bf16" (one BF16 pass).
         Returns (lam packed f64, Z packed f32 (each block column-major), status
         int32[count], iterations int32[count], info dict)."""
         sizes = np.ascontiguousarray(np.asarray(sizes, dtype=np.int64))
@@ -247,7 +249,9 @@ class Solver:
         Z = torch.empty(M.numel(), dtype=torch.float32, device=M.device)
         status = torch.empty(count, dtype=torch.int32, device=M.device)
         iters = torch.empty(count, dtype=torch.int32, device=M.device)
-        o = make_options("f32", stop, diverge_bound, record_timing=record_timing)
+        if precision not in ("f32", "bf16x3", "bf16"):
+            raise ValueError("batched precision must be 'f32', 'bf16x3' or 'bf16'")
+        o = make_options(precision, stop, diverge_bound, record_timing=record_timing)
         r = Result()
         _lib.ipt_solve_batched(self._h, count,
                                sizes.ctypes.data_as(C.POINTER(C.c_int64)), _ptr(M),

@@ -61,7 +61,7 @@ def run_csr(name, solves, precision, tol, window=True):
             raise SystemExit(1)
 
 
-def run_batched(name, solves, tol, tiles=None):
+def run_batched(name, solves, tol, tiles=None, precision="f32"):
     import torch
     from paper_2012_14702_gb300 import ipt
     count, nmin, nmax, scale, seed = workloads.BATCHED_CONFIGS[name]
@@ -73,7 +73,8 @@ def run_batched(name, solves, tol, tiles=None):
     for i in range(solves):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        _, _, _, iters, info = s.solve_batched(sizes, Mg, tol=tol, max_iter=30)
+        _, _, _, iters, info = s.solve_batched(sizes, Mg, tol=tol, max_iter=30,
+                                               precision=precision)
         torch.cuda.synchronize()
         print(f"{name} solve {i}: {info['status']} evaluations {info['iterations']} (max) "
               f"{1e3 * (time.perf_counter() - t0):.2f} ms, tiles {s.batched_tiles}", flush=True)
@@ -99,7 +100,8 @@ def main(argv=None):
         run_dense(a.workload, a.solves, a.precision, a.tol)
     elif a.workload in workloads.BATCHED_CONFIGS:
         tiles = [int(x) for x in a.tiles.split(",")] if a.tiles else None
-        run_batched(a.workload, a.solves, a.tol, tiles)
+        prec = a.precision if a.precision in ("bf16x3", "bf16") else "f32"
+        run_batched(a.workload, a.solves, a.tol, tiles, prec)
     else:
         run_csr(a.workload, a.solves, a.precision, a.tol, window=not a.all_rows)
 

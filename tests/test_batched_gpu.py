@@ -248,3 +248,72 @@ def test_batched_graph_replay_reads_current_inputs(ipt):
     for p in [3, 12]:
         ref = oracle.ipt_solve(b[p], tol=1e-13, max_iter=100)
         np.testing.assert_allclose(lams[p], ref["lam"], rtol=1e-5)
+
+
+@pytest.mark.parametrize("m", [1, 2, 3])
+def test_batched_bf16x3_tensor_core_iterates_match_oracle(ipt, m):
+    """The tensor-core variant (split BF16 x3 products in 128 x 128 tiles): the
+    iterates of a fixed number of evaluations within 2e-5 of max |Z - E| of the
+    oracle's (the product's relative error is ~2^-16)."""
+    mats = small_batch(seed=28)
+    sizes, flat = pack(mats)
+    lam, Z, status, iters, info = ipt.Solver().solve_batched(
+        sizes, torch.as_tensor(flat, dtype=torch.float32, device="cuda"), tol=0.0, max_iter=m,
+        stop="increment", precision="bf16x3")
+    st, it = status.cpu().numpy(), iters.cpu().numpy()
+    Zs = blocks(Z.cpu().numpy(), sizes)
+    lams = blocks(lam.cpu().numpy(), sizes, square=False)
+    for p, M in enumerate(mats):
+        n = M.shape[0]
+        ref = oracle.ipt_solve(M, tol=0.0, max_iter=int(it[p]), stop="increment")
+        if st[p] != oracle.OK:
+            assert st[p] == oracle.MAXITER and it[p] == m, (p, n, st[p], it[p])
+        Zg = Zs[p].reshape(n, n).T
+        scale = max(np.max(np.abs(ref["Z"] - np.eye(n))), 1e-30)
+        assert np.max(np.abs(Zg - ref["Z"])) <= 2e-5 * scale + 1e-7, (p, n)
+        np.testing.assert_allclose(lams[p], ref["lam"], rtol=1e-6, atol=1e-6)
+
+
+@pytest.mark.parametrize("precision,tol", [("bf16x3", 1e-6), ("bf16", 1e-4)])
+def test_batched_tensor_core_converged_match_oracle(ipt, precision, tol):
+    mats = small_batch(seed=29) + [np.diag(np.arange(1.0, 301.0))]
+    g = w.rng(30)
+    for n in [384, 513]:
+        a = g.standard_normal((n, n)) * 1e-2 / np.sqrt(n)
+        a = np.triu(a, 1)
+        a = a + a.T
+        a[np.diag_indices(n)] = np.arange(1, n + 1) * 1.0
+        mats.append(a)
+    sizes, flat = pack(mats)
+    lam, Z, status, iters, info = ipt.Solver().solve_batched(
+        sizes, torch.as_tensor(flat, dtype=torch.float32, device="cuda"), tol=tol, max_iter=60,
+        precision=precision)
+    assert info["status"] == "OK", (info, status.cpu().numpy())
+    Zs = blocks(Z.cpu().numpy(), sizes)
+    lams = blocks(lam.cpu().numpy(), sizes, square=False)
+    for p, M in enumerate(mats):
+        n = M.shape[0]
+        ref = oracle.ipt_solve(M, tol=1e-13, max_iter=100)
+        np.testing.assert_allclose(lams[p], ref["lam"], rtol=1e-5 if tol < 1e-5 else 1e-4)
+        if n > 1 and np.any(ref["Z"] != np.eye(n)):
+            err = np.linalg.norm(Zs[p].reshape(n, n).T - ref["Z"]) / np.linalg.norm(
+                ref["Z"] - np.eye(n))
+            assert err <= (1e-4 if tol < 1e-5 else 1e-2), (p, n, err)
+
+
+def test_batched_bf16x3_full_size_configuration(ipt):
+    count, nmin, nmax, scale, seed = w.BATCHED_CONFIGS["batched_4096_n32_512"]
+    sizes, flat, th = w.batched_dense(count, nmin, nmax, scale, seed)
+    lam, Z, status, iters, info = ipt.Solver().solve_batched(
+        sizes, torch.as_tensor(flat, device="cuda"), tol=1e-6, max_iter=30, precision="bf16x3")
+    assert info["status"] == "OK", info
+    offs = np.concatenate([[0], np.cumsum(sizes * sizes)])
+    voffs = np.concatenate([[0], np.cumsum(sizes)])
+    for p in [0, 5, 2048, 4095, int(np.argmax(sizes))]:
+        n = int(sizes[p])
+        M = flat[offs[p]:offs[p + 1]].astype(np.float64).reshape(n, n)
+        ref = oracle.ipt_solve(M, th[voffs[p]:voffs[p + 1]], tol=1e-13, max_iter=100)
+        np.testing.assert_allclose(lam[voffs[p]:voffs[p + 1]].cpu().numpy(), ref["lam"],
+                                   rtol=1e-5)
+        Zg = Z[offs[p]:offs[p + 1]].cpu().numpy().reshape(n, n).T
+        assert np.linalg.norm(Zg - ref["Z"]) / np.linalg.norm(ref["Z"] - np.eye(n)) <= 1e-4
