@@ -347,7 +347,43 @@ def run_batched(steps, warmup):
                      "unit": "TFLOP/s", "frac": achieved / FP32_ALU_PEAK, "traffic": None,
                      "flops_per_launch": flops, "avg_launch_ms": k_ms,
                      "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz"},
+        "bf16x3_tensor_cores": run_batched_tc(solver, sizes, Mg, steps),
     }
+
+
+def run_batched_tc(solver, sizes, Mg, steps):
+    """The same batch with the product on the tensor cores (split BF16 x3, tcgen05,
+    128 x 128 tiles).  Roofline: the executed flops (three passes of 2 n_p^3 per
+    product evaluation) against the measured dense BF16 peak."""
+    import torch
+    solver.solve_batched(sizes, Mg, tol=TOL, max_iter=30, precision="bf16x3")
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    kern = []
+    e0.record(solver.stream)
+    for _ in range(steps):
+        _, _, status, iters, info = solver.solve_batched(sizes, Mg, tol=TOL, max_iter=30,
+                                                         record_timing=True,
+                                                         precision="bf16x3")
+        kern.append(info["product_ms"][0])
+    e1.record(solver.stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    its = iters.cpu().numpy().astype(np.int64)
+    flops = float(np.sum(2.0 * sizes.astype(np.float64) ** 3 * np.maximum(its - 1, 0)))
+    k_ms = float(np.mean(kern))
+    burst, _, src = measured_peak()
+    executed = 3.0 * flops / (k_ms / 1e3) / 1e12
+    return {"ms_to_tol": ms, "status": info["status"],
+            "evaluations": {"min": int(its.min()), "max": int(its.max()),
+                            "mean": float(its.mean())},
+            "algorithmic_tflops": flops / (k_ms / 1e3) / 1e12,
+            "roofline": {"kernel": "k_batched<tensor cores> (tcgen05 split-BF16 x3, 128 x 128 "
+                                   "tiles, staged operands)",
+                         "bound": "tensor", "achieved": executed, "peak": burst,
+                         "unit": "TFLOP/s", "frac": executed / burst if burst else None,
+                         "traffic": None, "avg_launch_ms": k_ms,
+                         "peak_source": f"{src} burst bf16"}}
 
 
 # ---------------------------------------------------------------- ACX configuration
