@@ -343,20 +343,27 @@ __device__ bool product_map_tc(const BatchArgs& a, const float* __restrict__ M, 
         tc::tmem_ld16(taddr + (uint32_t)cc, v);
         if (j >= n) continue;
         const float hj = sh.th_hi[j], lj = sh.th_lo[j];
+        float zv[16];  // the chunk's iterate loads all in flight before their use
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          const int c = c0 + ch_half * 64 + cc + i;
+          zv[i] = c < n ? zc[(int64_t)c * n + j] : 0.f;
+        }
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
           const int cl = ch_half * 64 + cc + i, c = c0 + cl;
-          if (c >= n) break;
-          const float z = zc[(int64_t)c * n + j];
-          // P_jc = Delta_jc (the E part, exact) + (Delta W)_jc
-          const float pjc = sdel[row * TC_PAD + cl] + v[i];
-          const float gap = gap2f(hj, lj, sh.th_hi[c], sh.th_lo[c]);
-          float f, r;
-          map_entry<float>(z, pjc, sh.d[c], gap, j == c, f, r);
-          zn[(int64_t)c * n + j] = f;
-          s_inc = fmaf(f - z, f - z, s_inc);
-          s_z = fmaf(z, z, s_z);
-          s_r = fmaf(r, r, s_r);
+          if (c < n) {
+            const float z = zv[i];
+            // P_jc = Delta_jc (the E part, exact) + (Delta W)_jc
+            const float pjc = sdel[row * TC_PAD + cl] + v[i];
+            const float gap = gap2f(hj, lj, sh.th_hi[c], sh.th_lo[c]);
+            float f, r;
+            map_entry<float>(z, pjc, sh.d[c], gap, j == c, f, r);
+            zn[(int64_t)c * n + j] = f;
+            s_inc = fmaf(f - z, f - z, s_inc);
+            s_z = fmaf(z, z, s_z);
+            s_r = fmaf(r, r, s_r);
+          }
         }
       }
       tc::tc_fence_before();
