@@ -159,13 +159,20 @@ __device__ __forceinline__ void product_map(const BatchArgs& a, const float* __r
       for (int i = 0; i < R; ++i) {
         const int j = r0t + ty * R + i;
         if (j >= n) continue;
+        float zv[R], mv[R];  // the row's loads all in flight before their use
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+          const int c = c0t + tx * R + q;
+          zv[q] = c < n ? zc[(int64_t)j * n + c] : 0.f;
+          mv[q] = (c < n && j != c) ? M[(int64_t)j * n + c] : 0.f;
+        }
 #pragma unroll
         for (int q = 0; q < R; ++q) {
           const int c = c0t + tx * R + q;
           if (c >= n) continue;
-          const float z = zc[(int64_t)j * n + c];
+          const float z = zv[q];
           // P_jc = Delta_jc (the E part, exact) + (Delta W)_jc
-          const float pjc = (j != c ? M[(int64_t)j * n + c] : 0.f) + acc[i][q];
+          const float pjc = mv[q] + acc[i][q];
           const float gap = gap2f(sh.th_hi[j], sh.th_lo[j], sh.th_hi[c], sh.th_lo[c]);
           float f, r;
           map_entry<float>(z, pjc, sh.d[c], gap, j == c, f, r);
