@@ -1,6 +1,6 @@
 """GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
 
-Tolerances.  FP64 results follow the benchmark spec's 1e-10 relative eigenvalue
+Tolerances.  FP64 results are held to a 1e-10 relative eigenvalue
 error.  For the FP32 / tensor-core forms the eigenvalue tolerance is 1e-5
 relative and the stopping residual is rho <= 1e-6; single-step tolerances
 come from the arithmetic of the product P = Delta Z (see each test).
