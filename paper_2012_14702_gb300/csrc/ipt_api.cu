@@ -1337,7 +1337,7 @@ ipt_status ipt_solve_batched(ipt_handle* h, int64_t count, const int64_t* n, con
   // schedule: offsets in input order, problems largest first
   const size_t cnt = (size_t)count;
   constexpr int kTuneSample = 64;  // problems per size class in a tuning run
-  const size_t meta_main = cnt * (8 + 8 + 4 + 4);
+  const size_t meta_main = cnt * (8 + 8 + 4 + 4 + 8);
   const size_t meta_bytes = meta_main + (size_t)kBatchClasses * kTuneSample * 4 + 64;
   if (h->hmeta_cap < meta_bytes) {
     if (h->hmeta) cudaFreeHost(h->hmeta);
@@ -1350,15 +1350,18 @@ ipt_status ipt_solve_batched(ipt_handle* h, int64_t count, const int64_t* n, con
   int64_t* v_off = m_off + cnt;
   int* nsz = reinterpret_cast<int*>(v_off + cnt);
   int* order = nsz + cnt;
-  int* sample = order + cnt;  // kBatchClasses x kTuneSample tuning schedules
-  int64_t mo = 0, vo = 0;
+  int64_t* t_off = reinterpret_cast<int64_t*>(order + cnt);  // tensor-core tile sets
+  int* sample = reinterpret_cast<int*>(t_off + cnt);  // kBatchClasses x kTuneSample schedules
+  int64_t mo = 0, vo = 0, to = 0;
   for (size_t p = 0; p < cnt; ++p) {
     m_off[p] = mo;
     v_off[p] = vo;
+    t_off[p] = to;
     nsz[p] = (int)n[p];
     order[p] = (int)p;
     mo += n[p] * n[p];
     vo += n[p];
+    to += batched_tc_tile_bytes(n[p]);
   }
   std::stable_sort(order, order + cnt, [&](int a, int b) { return nsz[a] > nsz[b]; });
   int dev = 0, nsm = 0;
@@ -1367,7 +1370,9 @@ ipt_status ipt_solve_batched(ipt_handle* h, int64_t count, const int64_t* n, con
   // BF16 tensor-core products (split x3 or one pass) or the FP32 SIMT product
   const int tc_passes =
       opt.precision == IPT_PREC_BF16X3 ? 3 : (opt.precision == IPT_PREC_BF16 ? 1 : 0);
-  const int ctas = (int)std::min<int64_t>(count, (int64_t)nsm * batched_ctas_per_sm(tc_passes));
+  // tensor cores: one CTA per SM (its shared-memory ring); FP32: the occupancy
+  const int per_sm = tc_passes ? 1 : batched_ctas_per_sm();
+  const int ctas = (int)std::min<int64_t>(count, (int64_t)nsm * per_sm);
   const int64_t max_n2 = max_n * max_n;
   // the tuning schedules: up to kTuneSample problems of each class not tuned yet,
   // evenly spread over the class (largest first)
@@ -1384,13 +1389,17 @@ ipt_status ipt_solve_batched(ipt_handle* h, int64_t count, const int64_t* n, con
     }
   }
   CK(ensure(h->bmeta, meta_bytes + 16));
-  CK(ensure(h->bscratch, (size_t)ctas * 2 * (size_t)max_n2 * 4));
+  // tensor cores: the CTAs' workspaces, then the prologue's per-problem outputs
+  const size_t ws_all = ((size_t)ctas * (size_t)batched_tc_workspace(max_n) + 1023) / 1024 * 1024;
+  CK(ensure(h->bscratch, tc_passes ? ws_all + (size_t)batched_tc_prep_bytes(to, mo, (int)count)
+                                   : (size_t)ctas * 2 * (size_t)max_n2 * 4));
   char* dm = static_cast<char*>(h->bmeta.p);
   int* queue = reinterpret_cast<int*>(dm + meta_bytes - 64);
   const int64_t* d_moff = reinterpret_cast<const int64_t*>(dm);
   const int64_t* d_voff = d_moff + cnt;
   const int* d_nsz = reinterpret_cast<const int*>(dm + cnt * 16);
   const int* d_order = reinterpret_cast<const int*>(dm + cnt * 20);
+  const int64_t* d_toff = reinterpret_cast<const int64_t*>(dm + cnt * 24);
   const int* d_sample = reinterpret_cast<const int*>(dm + meta_main);
   bool tune = false;
   for (int c = 0; c < kBatchClasses; ++c) tune |= nsample[c] > 0;
@@ -1418,7 +1427,7 @@ ipt_status ipt_solve_batched(ipt_handle* h, int64_t count, const int64_t* n, con
         CK(launch_batched(M, theta, d_moff, d_voff, d_nsz, d_sample + c * kTuneSample,
                           nsample[c], max_n2, tol, max_iter, opt.stop, opt.diverge_bound,
                           lambda, Z, status, iters, static_cast<float*>(h->bscratch.p), queue,
-                          tiles, std::min(ctas, nsample[c]), 0, s));
+                          tiles, std::min(ctas, nsample[c]), s));
         CK(cudaEventRecord(h->ev[1], s));
         CK(cudaEventSynchronize(h->ev[1]));
         CK(cudaEventElapsedTime(&ms, h->ev[0], h->ev[1]));
@@ -1460,9 +1469,15 @@ ipt_status ipt_solve_batched(ipt_handle* h, int64_t count, const int64_t* n, con
     CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
     cudaMemcpyAsync(dm, h->hmeta, meta_main, cudaMemcpyHostToDevice, cs);
     cudaMemsetAsync(queue, 0, sizeof(int), cs);
-    launch_batched(M, theta, d_moff, d_voff, d_nsz, d_order, (int)count, max_n2, tol, max_iter,
-                   opt.stop, opt.diverge_bound, lambda, Z, status, iters,
-                   static_cast<float*>(h->bscratch.p), queue, tiles, ctas, tc_passes, cs);
+    if (tc_passes)
+      launch_batched_tc(M, theta, d_moff, d_voff, d_toff, d_nsz, d_order, (int)count, max_n, to,
+                        mo, tol, max_iter, opt.stop, opt.diverge_bound, lambda, Z, status,
+                        iters, h->bscratch.p, static_cast<char*>(h->bscratch.p) + ws_all, queue,
+                        ctas, tc_passes, cs);
+    else
+      launch_batched(M, theta, d_moff, d_voff, d_nsz, d_order, (int)count, max_n2, tol,
+                     max_iter, opt.stop, opt.diverge_bound, lambda, Z, status, iters,
+                     static_cast<float*>(h->bscratch.p), queue, tiles, ctas, cs);
     CK(cudaStreamEndCapture(cs, &h->bgraph));
     CK(cudaGraphInstantiate(&h->bexec, h->bgraph, 0));
     h->bkey = key;
@@ -1489,7 +1504,7 @@ ipt_status ipt_solve_batched(ipt_handle* h, int64_t count, const int64_t* n, con
   }
   out->status = agg;
   out->iterations = most;
-  out->kernel_launches = 1;
+  out->kernel_launches = tc_passes ? 2 : 1;  // tensor cores: the prologue and the solve
   out->product_launches[0] = 1;
   if (tm.on) {
     float ms = 0.f;

@@ -224,9 +224,25 @@ cudaError_t launch_batched(const float* M, const double* theta, const int64_t* m
                            int64_t max_n2, double tol, int max_iter, int stop,
                            double diverge_bound, double* lambda, float* Z, int* status,
                            int* iters, float* scratch, int* queue, const int* tiles, int ctas,
-                           int tc_passes, cudaStream_t s);
-// resident CTAs per SM of the batched kernel (tc: the tensor-core variant)
-int batched_ctas_per_sm(int tc);
+                           cudaStream_t s);
+// resident CTAs per SM of the batched FP32 kernel
+int batched_ctas_per_sm();
+// Batched solve with tensor-core products (k_batched_tc.cu; passes 3 or 1):
+// a prologue launch (one CTA per problem) and the main launch (one CTA per
+// SM).  ws holds ctas x batched_tc_workspace(max_n) bytes; prep holds
+// batched_tc_prep_bytes(...) bytes, where tiles_total sums
+// batched_tc_tile_bytes(n) over the problems (t_off: its prefix sums) and
+// total_n2 sums n^2.
+int64_t batched_tc_tile_bytes(int64_t n);
+int64_t batched_tc_workspace(int64_t max_n);
+int64_t batched_tc_prep_bytes(int64_t tiles_total, int64_t total_n2, int count);
+cudaError_t launch_batched_tc(const float* M, const double* theta, const int64_t* m_off,
+                              const int64_t* v_off, const int64_t* t_off, const int* nsz,
+                              const int* order, int count, int64_t max_n, int64_t tiles_total,
+                              int64_t total_n2, double tol, int max_iter, int stop,
+                              double diverge_bound, double* lambda, float* Z, int* status,
+                              int* iters, void* ws, void* prep, int* queue, int ctas, int passes,
+                              cudaStream_t s);
 
 // Alg. 3 extrapolation of order p (2 or 3) in place: z (buffer of the
 // extrapolated iterate) from f1 = f(z), f2, f3 (column-major, leading dim ld).
