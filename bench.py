@@ -353,8 +353,10 @@ def run_batched(steps, warmup):
 
 def run_batched_tc(solver, sizes, Mg, steps):
     """The same batch with the product on the tensor cores (split BF16 x3, tcgen05,
-    128 x 128 tiles).  Roofline: the executed flops (three passes of 2 n_p^3 per
-    product evaluation) against the measured dense BF16 peak."""
+    128 x 128 tiles; a prologue launch and the warp-specialised solve).  Roofline:
+    the executed flops (three passes of 2 n_p^3 per product evaluation) against the
+    measured dense BF16 peak; the kernel is bound by memory traffic and latency far
+    below that peak (its ncu summary gives the DRAM figures)."""
     import torch
     solver.solve_batched(sizes, Mg, tol=TOL, max_iter=30, precision="bf16x3")
     torch.cuda.synchronize()
@@ -378,8 +380,8 @@ def run_batched_tc(solver, sizes, Mg, steps):
             "evaluations": {"min": int(its.min()), "max": int(its.max()),
                             "mean": float(its.mean())},
             "algorithmic_tflops": flops / (k_ms / 1e3) / 1e12,
-            "roofline": {"kernel": "k_batched<tensor cores> (tcgen05 split-BF16 x3, 128 x 128 "
-                                   "tiles, staged operands)",
+            "roofline": {"kernel": "k_batched_tc_prep + k_batched_tc (tcgen05 split-BF16 x3, "
+                                   "128 x 128 tiles, bulk-copied pre-split operands)",
                          "bound": "tensor", "achieved": executed, "peak": burst,
                          "unit": "TFLOP/s", "frac": executed / burst if burst else None,
                          "traffic": None, "avg_launch_ms": k_ms,

@@ -256,7 +256,10 @@ ipt_status ipt_solve_csr(ipt_handle* h, int64_t n, int64_t nnz, const int32_t* r
  * every evaluation of a problem without host involvement.  The exact Delta E
  * term plus the product Delta W (W = Z - E): opt->precision IPT_PREC_BF16X3
  * runs it on the tensor cores as split-BF16 x3 (128 x 128 tiles), IPT_PREC_BF16
- * as one BF16 pass, anything else as an FP32 SIMT product; FP32 iterate.
+ * as one BF16 pass, anything else as an FP32 SIMT product; FP32 iterate.  The
+ * tensor-core forms add a prologue launch before the persistent one (the
+ * operands' BF16 tiles and the first evaluation, one block per problem) and
+ * use Z as working memory while they run.
  *   count          number of problems (>= 1)
  *   n              HOST array of count problem orders, 1 <= n_p <= 1024
  *   M              device, FP32, the problems packed back to back: problem p is
@@ -272,7 +275,7 @@ ipt_status ipt_solve_csr(ipt_handle* h, int64_t n, int64_t nnz, const int32_t* r
  *   out            host: status IPT_OK when every problem converged, else the
  *                  status of the first problem (by index) that did not;
  *                  iterations = the largest evaluation count; product_ms[0] =
- *                  the kernel's device time with record_timing
+ *                  the kernels' device time with record_timing
  * Returns out->status (argument errors before any launch: IPT_INVALID_ARG).
  */
 ipt_status ipt_solve_batched(ipt_handle* h, int64_t count, const int64_t* n, const float* M,
