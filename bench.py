@@ -301,7 +301,7 @@ def run_csr(steps, warmup, hbm_peak):
 FP32_ALU_PEAK = 152 * 128 * 2 * 2.07e9 / 1e12  # TFLOP/s: SMs x FP32 lanes x FMA x max clock
 
 
-def run_batched(steps, warmup):
+def run_batched(steps, warmup, hbm_peak):
     """4096 independent dense problems, n_p ~ U{32..512}, theta_i = i, symmetric
     N(0,1)*0.01/sqrt(n_p) perturbations (seed 4), all eigenpairs of every problem
     to rho <= 1e-6 in one persistent launch.  Roofline: the FP32 product flops
@@ -347,16 +347,18 @@ def run_batched(steps, warmup):
                      "unit": "TFLOP/s", "frac": achieved / FP32_ALU_PEAK, "traffic": None,
                      "flops_per_launch": flops, "avg_launch_ms": k_ms,
                      "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz"},
-        "bf16x3_tensor_cores": run_batched_tc(solver, sizes, Mg, steps),
+        "bf16x3_tensor_cores": run_batched_tc(solver, sizes, Mg, steps, hbm_peak),
     }
 
 
-def run_batched_tc(solver, sizes, Mg, steps):
+def run_batched_tc(solver, sizes, Mg, steps, hbm_peak):
     """The same batch with the product on the tensor cores (split BF16 x3, tcgen05,
     128 x 128 tiles; a prologue launch and the warp-specialised solve).  Roofline:
-    the executed flops (three passes of 2 n_p^3 per product evaluation) against the
-    measured dense BF16 peak; the kernel is bound by memory traffic and latency far
-    below that peak (its ncu summary gives the DRAM figures)."""
+    HBM, the batch's arithmetic intensity (~n_p / 6 flop per byte) being below the
+    tensor cores' ridge.  Algorithmic bytes: 12 n_p^2 per product evaluation (read
+    Delta and Z, write F in FP32) and 8 n_p^2 for the product-free first one (read
+    Delta, write F); the executed tensor flops (three passes of 2 n_p^3 per product
+    evaluation) against the measured dense BF16 peak are reported beside it."""
     import torch
     solver.solve_batched(sizes, Mg, tol=TOL, max_iter=30, precision="bf16x3")
     torch.cuda.synchronize()
@@ -376,16 +378,23 @@ def run_batched_tc(solver, sizes, Mg, steps):
     k_ms = float(np.mean(kern))
     burst, _, src = measured_peak()
     executed = 3.0 * flops / (k_ms / 1e3) / 1e12
+    n2 = sizes.astype(np.float64) ** 2
+    alg_bytes = float(np.sum(12.0 * n2 * np.maximum(its - 1, 0) + 8.0 * n2))
+    gbs = alg_bytes / (k_ms / 1e3) / 1e9
     return {"ms_to_tol": ms, "status": info["status"],
             "evaluations": {"min": int(its.min()), "max": int(its.max()),
                             "mean": float(its.mean())},
             "algorithmic_tflops": flops / (k_ms / 1e3) / 1e12,
             "roofline": {"kernel": "k_batched_tc_prep + k_batched_tc (tcgen05 split-BF16 x3, "
                                    "128 x 128 tiles, bulk-copied pre-split operands)",
-                         "bound": "tensor", "achieved": executed, "peak": burst,
-                         "unit": "TFLOP/s", "frac": executed / burst if burst else None,
-                         "traffic": None, "avg_launch_ms": k_ms,
-                         "peak_source": f"{src} burst bf16"}}
+                         "bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": gbs / hbm_peak, "traffic": None,
+                         "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_ms": k_ms,
+                         "peak_source": "measured HBM copy",
+                         "tensor_executed": {"achieved": executed, "peak": burst,
+                                             "unit": "TFLOP/s",
+                                             "frac": executed / burst if burst else None,
+                                             "peak_source": f"{src} burst bf16"}}}
 
 
 # ---------------------------------------------------------------- ACX configuration
@@ -735,14 +744,14 @@ def run_ours(args, rank, world, local_rank):
     if not args.no_eps_sweep:
         line["eps_sweep"] = run_eps_sweep(max(3, min(args.steps, 5)))
         line["paper_family"] = run_paper_family(max(3, min(args.steps, 5)))
+    hbm = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("hbm_gbs", 6800.0) \
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6800.0
     if not args.no_csr:
-        hbm = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("hbm_gbs", 6800.0) \
-            if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6800.0
         line["csr"] = run_csr(max(3, min(args.steps, 10)), 2, hbm)
     if not args.no_acx:
         line["acx"] = run_acx(max(3, min(args.steps, 10)), 2)
     if not args.no_batched:
-        line["batched"] = run_batched(max(3, min(args.steps, 10)), 2)
+        line["batched"] = run_batched(max(3, min(args.steps, 10)), 2, hbm)
     if not args.no_damped:
         line["damped"] = run_damped(2)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
