@@ -55,7 +55,8 @@ constexpr int kEpi = kEpiWarps * 32;
 constexpr int kCopyWarp = 8, kMmaWarp = 9;
 constexpr int kThreads = kEpi + 64;
 constexpr int kTPad = kT + 1;       // row stride of the transposing buffer (floats)
-constexpr int kU = 16;              // loads in flight per thread in the per-problem passes
+constexpr int kU = 16;              // loads in flight per thread in the output copy
+constexpr int kPI = 4;              // prologue: K pairs (8 loads) in flight per thread
 static_assert(kK * kTPad * 4 <= kStages * kStage, "transposing buffer fits the ring");
 // kind::f16 instruction descriptor: F32 accumulator, BF16 A and B, both
 // K-major, N = 128, M = 128.
@@ -117,6 +118,19 @@ __device__ __forceinline__ void put_split(uint8_t* pair, int off, float x, bool 
         __float2bfloat16_rn(x - __bfloat162float(h));
 }
 
+// Two K-adjacent values (x0 at the even K index, byte offset `off`) as packed
+// BF16 hi (and lo) pairs; the same roundings as put_split.
+__device__ __forceinline__ void put_split2(uint8_t* pair, int off, float x0, float x1,
+                                           bool with_lo) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
+  *reinterpret_cast<__nv_bfloat162*>(pair + off) = h;
+  if (with_lo) {
+    const float2 hf = __bfloat1622float2(h);
+    *reinterpret_cast<__nv_bfloat162*>(pair + kTile + off) =
+        __floats2bfloat162_rn(x0 - hf.x, x1 - hf.y);
+  }
+}
+
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
                                          uint64_t* bar) {
   asm volatile(
@@ -136,11 +150,11 @@ __device__ __forceinline__ void tile_of(int ti, int nt, int& rb, int& cb) {
 constexpr int kPT = 256;  // prologue threads per CTA
 
 // Prologue, one CTA per problem (largest first).  Per 128 x 64 block (rb, ks)
-// of Delta: kU loads in flight per thread, the BF16 split tile (rb, ks), and
+// of Delta: 2 kPI loads in flight per thread, the BF16 split tile (rb, ks), and
 // the block transposed through shared memory for the column-major outputs:
-// DT and W0's tile entries (F0_jc = -Delta_jc / (theta_j - theta_c) off the
-// diagonal, 1 on it) (row c, K index j).  W0's rows past the blocks' extent
-// are zero padding.
+// DT and W0's tile entries (row c, K index j; F0_jc = -Delta_jc / (theta_j -
+// theta_c) off the diagonal, 1 on it).  Stores go as packed BF16 pairs of
+// K-adjacent entries.  W0's rows past the blocks' extent are zero padding.
 __global__ void __launch_bounds__(kPT, 4) k_batched_tc_prep(TcArgs a) {
   __shared__ float th_hi[kBatchMaxN], th_lo[kBatchMaxN], ddiag[kBatchMaxN];
   __shared__ float tbuf[kK * kTPad];
@@ -172,53 +186,61 @@ __global__ void __launch_bounds__(kPT, 4) k_batched_tc_prep(TcArgs a) {
   for (int blk = 0; blk < nt * nks; ++blk) {
     const int rb = blk / nks, ks = blk % nks;
     uint8_t* pair = A + (int64_t)blk * kPair;
-    for (int base = tid; base < kT * kK; base += kU * kPT) {
-      float raw[kU];
+    // items (row r, K pair 2q, 2q + 1): a warp covers one row's 64 K values;
+    // kPI items' loads in flight per thread before any store
+    for (int base = tid; base < kT * (kK / 2); base += kPI * kPT) {
+      float v0[kPI], v1[kPI];
 #pragma unroll
-      for (int u = 0; u < kU; ++u) {
-        const int e = base + u * kPT, j = rb * kT + (e >> 6), m = ks * kK + (e & 63);
-        raw[u] = (e < kT * kK && j < n && m < n) ? M[(int64_t)j * n + m] : 0.f;
+      for (int u = 0; u < kPI; ++u) {
+        const int it = base + u * kPT, j = rb * kT + (it >> 5), m = ks * kK + 2 * (it & 31);
+        const float* row = M + (int64_t)j * n;
+        v0[u] = (j < n && m < n) ? row[m] : 0.f;
+        v1[u] = (j < n && m + 1 < n) ? row[m + 1] : 0.f;
       }
 #pragma unroll
-      for (int u = 0; u < kU; ++u) {
-        const int e = base + u * kPT, r = e >> 6, ml = e & 63;
+      for (int u = 0; u < kPI; ++u) {
+        const int it = base + u * kPT, r = it >> 5, ml = 2 * (it & 31);
         const int j = rb * kT + r, m = ks * kK + ml;
-        if (e < kT * kK) {
-          put_split(pair, sw128(r, ml), (j < n && j == m) ? ddiag[j] : raw[u], three);
-          tbuf[ml * kTPad + r] = raw[u];
-        }
+        put_split2(pair, sw128(r, ml), (j < n && j == m) ? ddiag[j] : v0[u],
+                   (j < n && j == m + 1) ? ddiag[j] : v1[u], three);
+        tbuf[ml * kTPad + r] = v0[u];
+        tbuf[(ml + 1) * kTPad + r] = v1[u];
       }
     }
     __syncthreads();
-    // column c = m of the block, rows j: DT and W0 entry (c, j)
-    for (int e = tid; e < kK * kT; e += kPT) {
-      const int ml = e >> 7, r = e & 127, c = ks * kK + ml, j = rb * kT + r;
+    // items (column c = m, row pair j, j + 1): DT and W0's entries (c, j), (c,
+    // j + 1); a warp covers 64 rows of one column
+    for (int it = tid; it < kK * (kT / 2); it += kPT) {
+      const int ml = it >> 6, r = 2 * (it & 63), c = ks * kK + ml, j = rb * kT + r;
       if (j >= kw) continue;  // past W0's K extent (and past n)
-      float w = 0.f;
-      if (c < n && j < n) {
-        const float djc = tbuf[ml * kTPad + r];
-        float f = 1.f;
-        if (j != c) {
-          const float gap = gap2f(th_hi[j], th_lo[j], th_hi[c], th_lo[c]);
-          if (gap == 0.f) atomicOr(&flag, 2);
-          f = -djc * recip_nr(gap);
-          s_inc = fmaf(f, f, s_inc);
-          s_r = fmaf(djc, djc, s_r);
-          w = f;
+      float w[2] = {0.f, 0.f};
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int jj = j + h;
+        if (c < n && jj < n) {
+          const float djc = tbuf[ml * kTPad + r + h];
+          if (jj != c) {
+            const float gap = gap2f(th_hi[jj], th_lo[jj], th_hi[c], th_lo[c]);
+            if (gap == 0.f) atomicOr(&flag, 2);
+            const float f = -djc * recip_nr(gap);
+            s_inc = fmaf(f, f, s_inc);
+            s_r = fmaf(djc, djc, s_r);
+            w[h] = f;
+          }
+          DT[(int64_t)c * n + jj] = djc;
         }
-        DT[(int64_t)c * n + j] = djc;
       }
-      put_split(W + (int64_t)((c >> 7) * nks + (j >> 6)) * kPair, sw128(c & 127, j & 63), w,
-                three);
+      put_split2(W + (int64_t)((c >> 7) * nks + (j >> 6)) * kPair, sw128(c & 127, j & 63), w[0],
+                 w[1], three);
     }
     __syncthreads();
   }
   // W0's rows c in [nks * 64, nt * 128) (all past n): zero
-  const int pad_rows = nt * kT - kw;
-  for (int e = tid; e < pad_rows * kw; e += kPT) {
-    const int c = kw + e / kw, j = e % kw;
-    put_split(W + (int64_t)((c >> 7) * nks + (j >> 6)) * kPair, sw128(c & 127, j & 63), 0.f,
-              three);
+  const int pad_rows = nt * kT - kw, kp = kw / 2;
+  for (int it = tid; it < pad_rows * kp; it += kPT) {
+    const int c = kw + it / kp, j = 2 * (it % kp);
+    put_split2(W + (int64_t)((c >> 7) * nks + (j >> 6)) * kPair, sw128(c & 127, j & 63), 0.f, 0.f,
+               three);
   }
   const F2 t_inc = block_sum(F2{s_inc, 0.f}, red[0]);
   const F2 t_r = block_sum(F2{s_r, 0.f}, red[1]);

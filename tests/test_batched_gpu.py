@@ -317,3 +317,31 @@ def test_batched_bf16x3_full_size_configuration(ipt):
                                    rtol=1e-5)
         Zg = Z[offs[p]:offs[p + 1]].cpu().numpy().reshape(n, n).T
         assert np.linalg.norm(Zg - ref["Z"]) / np.linalg.norm(ref["Z"] - np.eye(n)) <= 1e-4
+
+
+@pytest.mark.parametrize("precision", ["f32", "bf16x3"])
+def test_batched_largest_orders_converge(ipt, precision):
+    """The largest order the batched solve takes (1024: eight 128-row blocks and
+    sixteen 64-deep slices per product on the tensor cores) beside ragged orders
+    just under it and a tiny one, converged to rho <= 1e-6 against the oracle."""
+    g = w.rng(41)
+    mats = []
+    for n in [1024, 1023, 897, 3]:
+        a = g.standard_normal((n, n)) * 1e-2 / np.sqrt(n)
+        a = np.triu(a, 1)
+        a = a + a.T
+        a[np.diag_indices(n)] = np.arange(1, n + 1) * 1.0
+        mats.append(a)
+    sizes, flat = pack(mats)
+    lam, Z, status, iters, info = ipt.Solver().solve_batched(
+        sizes, torch.as_tensor(flat, dtype=torch.float32, device="cuda"), tol=1e-6, max_iter=40,
+        precision=precision)
+    assert info["status"] == "OK", (info, status.cpu().numpy())
+    Zs = blocks(Z.cpu().numpy(), sizes)
+    lams = blocks(lam.cpu().numpy(), sizes, square=False)
+    for p, M in enumerate(mats):
+        n = M.shape[0]
+        ref = oracle.ipt_solve(M, tol=1e-13, max_iter=100)
+        np.testing.assert_allclose(lams[p], ref["lam"], rtol=1e-5)
+        err = np.linalg.norm(Zs[p].reshape(n, n).T - ref["Z"]) / np.linalg.norm(ref["Z"] - np.eye(n))
+        assert err <= 1e-4, (p, n, err)
