@@ -100,7 +100,8 @@ def test_batched_converged_match_oracle_and_theta_forms(ipt):
         assert abs(int(its[p]) - ref6["iterations"]) <= 1, (p, its[p], ref6["iterations"])
 
 
-def test_batched_per_problem_statuses(ipt):
+@pytest.mark.parametrize("precision", ["f32", "bf16x3"])
+def test_batched_per_problem_statuses(ipt, precision):
     mats = small_batch(seed=23)
     # problem 3 degenerate (repeated theta), problem 7 far outside the domain
     th = [np.diag(M).copy() for M in mats]
@@ -112,7 +113,8 @@ def test_batched_per_problem_statuses(ipt):
     sizes, flat = pack(mats)
     lam, Z, status, iters, info = ipt.Solver().solve_batched(
         sizes, torch.as_tensor(flat, dtype=torch.float32, device="cuda"),
-        theta=torch.as_tensor(np.concatenate(th), device="cuda"), tol=1e-6, max_iter=60)
+        theta=torch.as_tensor(np.concatenate(th), device="cuda"), tol=1e-6, max_iter=60,
+        precision=precision)
     st = status.cpu().numpy()
     assert st[3] == oracle.DEGENERATE_THETA
     assert st[7] in (oracle.DIVERGED, oracle.MAXITER)
