@@ -21,13 +21,15 @@
 // So a 64-deep slice of a 128 x 128 output tile is two contiguous bulk copies
 // (cp.async.bulk, 32 KB each for three passes), and the CTA is warp-
 // specialised:
-//   warp 8   copies slices into a 3-stage shared-memory ring (mbarriers),
-//   warp 9   issues the MMAs of each slice (one thread) into one of two
+//   warp 16  copies slices into a 3-stage shared-memory ring (mbarriers),
+//   warp 17  issues the MMAs of each slice (one thread) into one of two
 //            128-column TMEM accumulators and commits them,
-//   warps 0-7 run the epilogue of the previous tile meanwhile: tcgen05.ld of
-//            the accumulator (warp w reads TMEM lanes 32 (w mod 4).. and
-//            column half w / 4), the map, the FP32 iterate and W's split
-//            tiles for the next evaluation.
+//   warps 0-15 run the epilogue of the previous tile meanwhile: tcgen05.ld of
+//            the accumulator (warp w reads TMEM lanes 32 (w mod 4).. and the
+//            column quarter w / 4, 8 columns at a time), the map, the FP32
+//            iterate and W's split tiles for the next evaluation.  (Sixteen
+//            epilogue warps at 96 registers issue faster than eight at 164:
+//            the epilogue sets the pace.)
 // Output tiles go column block by column block, each block's diagonal tile
 // first (it yields d_c = Delta_cc + (Delta W)_cc for the block).  Every wait
 // is bounded; a wait that gives up ends the CTA's work with
@@ -50,9 +52,9 @@ constexpr int kPair = 2 * kTile;    // hi tile, then lo tile
 constexpr int kStages = 3;
 constexpr int kStage = 2 * kPair;   // A pair + B pair
 constexpr int kSmem = kStages * kStage + 1024;
-constexpr int kEpiWarps = 8;
+constexpr int kEpiWarps = 16;
 constexpr int kEpi = kEpiWarps * 32;
-constexpr int kCopyWarp = 8, kMmaWarp = 9;
+constexpr int kCopyWarp = 16, kMmaWarp = 17;
 constexpr int kThreads = kEpi + 64;
 constexpr int kTPad = kT + 1;       // row stride of the transposing buffer (floats)
 constexpr int kU = 16;              // loads in flight per thread in the output copy
@@ -129,6 +131,21 @@ __device__ __forceinline__ void put_split2(uint8_t* pair, int off, float x0, flo
     *reinterpret_cast<__nv_bfloat162*>(pair + kTile + off) =
         __floats2bfloat162_rn(x0 - hf.x, x1 - hf.y);
   }
+}
+
+// 8 consecutive accumulator columns of this thread's TMEM lane (load and
+// completion wait in one asm statement).
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
+  uint32_t r[8];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7])
+      : "r"(taddr)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
 }
 
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
@@ -419,7 +436,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_batched_tc(TcArgs a) {
           __syncwarp();
         } else {
           // ---------------------------------------------- epilogue
-          const int q = warp & 3, half = warp >> 2;
+          const int q = warp & 3, cq = warp >> 2;  // TMEM lane quarter, column quarter
           const int row = q * 32 + lane;
           for (int ti = 0; ti < ntiles; ++ti, ++te) {
             int rb, cb;
@@ -431,17 +448,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_batched_tc(TcArgs a) {
               break;
             }
             tc::tc_fence_after();
-            const uint32_t taddr = tmem + b * kT + ((uint32_t)(q * 32) << 16) + (uint32_t)(half * 64);
+            const uint32_t taddr = tmem + b * kT + ((uint32_t)(q * 32) << 16) + (uint32_t)(cq * 32);
             if (rb == cb) {
               // d_c = Delta_cc + (Delta W)_cc: the diagonal entries of lane
-              // quarter q's rows are columns q*32 .. q*32+31, in the column half
-              // of one of the quarter's two warps (warp-uniform test)
-              const int dcol = q * 32 - half * 64;
-              if (dcol >= 0 && dcol < 64) {
+              // quarter q's rows are columns q*32 .. q*32+31: the column quarter
+              // of the quarter's warp with cq == q (warp-uniform test)
+              if (cq == q) {
                 float v0[16], v1[16];
                 __syncwarp();
-                tc::tmem_ld16(taddr + (uint32_t)dcol, v0);
-                tc::tmem_ld16(taddr + (uint32_t)(dcol + 16), v1);
+                tc::tmem_ld16(taddr, v0);
+                tc::tmem_ld16(taddr + 16u, v1);
                 float dv = 0.f;
 #pragma unroll
                 for (int i = 0; i < 16; ++i) {
@@ -462,22 +478,22 @@ __global__ void __launch_bounds__(kThreads, 1) k_batched_tc(TcArgs a) {
             uint8_t* brow = Bn + (int64_t)(cb * nks + (j < nks * kK ? j / kK : 0)) * kPair;
             const int kin = j % kK;
 #pragma unroll 1
-            for (int cc = 0; cc < 64; cc += 16) {
-              float v[16];
+            for (int cc = 0; cc < 32; cc += 8) {
+              float v[8];
               __syncwarp();  // the TMEM load is warp-collective
-              tc::tmem_ld16(taddr + (uint32_t)cc, v);
+              tmem_ld8(taddr + (uint32_t)cc, v);
               if (!wrow) continue;
-              const int cl0 = half * 64 + cc;
-              float zv[16], dv[16];  // the chunk's loads all in flight before their use
+              const int cl0 = cq * 32 + cc;
+              float zv[8], dv[8];  // the chunk's loads all in flight before their use
 #pragma unroll
-              for (int i = 0; i < 16; ++i) {
+              for (int i = 0; i < 8; ++i) {
                 const int c = c0 + cl0 + i;
                 const bool in = j < n && c < n;
                 zv[i] = in && zc ? zc[(int64_t)c * n + j] : 0.f;
                 dv[i] = in && j != c ? DT[(int64_t)c * n + j] : 0.f;
               }
 #pragma unroll
-              for (int i = 0; i < 16; ++i) {
+              for (int i = 0; i < 8; ++i) {
                 const int cl = cl0 + i, c = c0 + cl;
                 float w = 0.f;
                 if (j < n && c < n) {
