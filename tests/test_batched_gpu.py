@@ -222,7 +222,8 @@ def test_batched_autotuner_tunes_the_classes_met(ipt):
     assert s.batched_tiles == t
 
 
-def test_batched_graph_replay_reads_current_inputs(ipt):
+@pytest.mark.parametrize("precision", ["f32", "bf16x3"])
+def test_batched_graph_replay_reads_current_inputs(ipt, precision):
     """The captured graph is replayed while orders, pointers and tolerances
     repeat: new contents of the same buffers give that batch's solution, and a
     changed tolerance is captured anew."""
@@ -233,18 +234,20 @@ def test_batched_graph_replay_reads_current_inputs(ipt):
     s = ipt.Solver()
     Mg = torch.as_tensor(fa, dtype=torch.float32, device="cuda")
     lam_a, Z_a, *_ = [x.clone() if torch.is_tensor(x) else x
-                      for x in s.solve_batched(sizes, Mg, tol=1e-6, max_iter=50)]
+                      for x in s.solve_batched(sizes, Mg, tol=1e-6, max_iter=50,
+                                               precision=precision)]
     Mg.copy_(torch.as_tensor(fb, dtype=torch.float32))
-    lam_b, Z_b, _, _, info = s.solve_batched(sizes, Mg, tol=1e-6, max_iter=50)
+    lam_b, Z_b, _, _, info = s.solve_batched(sizes, Mg, tol=1e-6, max_iter=50,
+                                             precision=precision)
     assert info["status"] == "OK"
     fresh = ipt.Solver()
     fresh.batched_tiles = s.batched_tiles
     lam_r, Z_r, *_ = fresh.solve_batched(sizes, torch.as_tensor(fb, dtype=torch.float32,
                                                                device="cuda"), tol=1e-6,
-                                         max_iter=50)
+                                         max_iter=50, precision=precision)
     assert torch.equal(lam_b, lam_r) and not torch.equal(lam_a, lam_b)
     lam_c, _, _, iters_c, info = s.solve_batched(sizes, Mg, tol=0.0, max_iter=2,
-                                                 stop="increment")
+                                                 stop="increment", precision=precision)
     assert info["iterations"] <= 2 and int(iters_c.max()) == 2
     lams = blocks(lam_b.cpu().numpy(), sizes, square=False)
     for p in [3, 12]:
