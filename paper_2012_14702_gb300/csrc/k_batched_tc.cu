@@ -95,9 +95,10 @@ struct TcArgs {
 };
 
 struct __align__(16) SmemTc {
-  float th_hi[kBatchMaxN], th_lo[kBatchMaxN];
+  // per column c: theta_c as an FP32 pair and d_c = (Delta Z)_cc of the current
+  // evaluation, one 16-byte load in the epilogue
+  float4 col[kBatchMaxN];   // (th_hi, th_lo, d, 0)
   float ddiag[kBatchMaxN];  // Delta_jj = M_jj - theta_j (formed in FP64 once per problem)
-  float d[kBatchMaxN];      // d_c = (Delta Z)_cc of the current evaluation
   F2 red[3][32];
   uint64_t full[kStages], empty[kStages], acc_full[2], acc_empty[2];
   uint64_t dbar;  // a diagonal tile's d_c written (the four warps holding the diagonal)
@@ -334,10 +335,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_batched_tc(TcArgs a) {
     for (int j = tid; j < n; j += kThreads) {
       const double t = a.theta ? a.theta[vo + j] : (double)M[(int64_t)j * n + j];
       const float h = (float)t;
-      sh.th_hi[j] = h;
-      sh.th_lo[j] = (float)(t - (double)h);
+      sh.col[j].x = h;
+      sh.col[j].y = (float)(t - (double)h);
+      sh.col[j].w = 0.f;
       sh.ddiag[j] = (float)((double)M[(int64_t)j * n + j] - t);
-      sh.d[j] = sh.ddiag[j];  // d at Z = E
+      sh.col[j].z = sh.ddiag[j];  // d at Z = E
     }
     if (tid == 0) sh.flag = a.prep_flag[p];
     __syncthreads();
@@ -464,7 +466,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_batched_tc(TcArgs a) {
                   if (i == lane) dv = v0[i];
                   if (i + 16 == lane) dv = v1[i];
                 }
-                if (j < n) sh.d[j] = sh.ddiag[j] + dv;
+                if (j < n) sh.col[j].z = sh.ddiag[j] + dv;
                 __syncwarp();
                 if (lane == 0) mbar::mbar_arrive(&sh.dbar);
               }
@@ -474,7 +476,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_batched_tc(TcArgs a) {
               ++td;
             }
             const bool wrow = j < nks * kK;  // rows carrying W entries (zeros past n)
-            const float hj = j < n ? sh.th_hi[j] : 0.f, lj = j < n ? sh.th_lo[j] : 0.f;
+            const float hj = j < n ? sh.col[j].x : 0.f, lj = j < n ? sh.col[j].y : 0.f;
             uint8_t* brow = Bn + (int64_t)(cb * nks + (j < nks * kK ? j / kK : 0)) * kPair;
             const int kin = j % kK;
 #pragma unroll 1
@@ -498,11 +500,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_batched_tc(TcArgs a) {
                 float w = 0.f;
                 if (j < n && c < n) {
                   const float pjc = dv[i] + v[i];  // P_jc = Delta_jc (exact) + (Delta W)_jc
-                  const float gap = gap2f(hj, lj, sh.th_hi[c], sh.th_lo[c]);
+                  const float4 cc4 = sh.col[c];
+                  const float gap = gap2f(hj, lj, cc4.x, cc4.y);
                   // Z = F0 at the first product
                   const float z = zc ? zv[i] : (j == c ? 1.f : -dv[i] * recip_nr(gap));
                   float f, r;
-                  map_entry<float>(z, pjc, sh.d[c], gap, j == c, f, r);
+                  map_entry<float>(z, pjc, cc4.z, gap, j == c, f, r);
                   zn[(int64_t)c * n + j] = f;
                   s_inc = fmaf(f - z, f - z, s_inc);
                   s_z = fmaf(z, z, s_z);
@@ -577,7 +580,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_batched_tc(TcArgs a) {
           if (!is_e && zc) {
             z = v[u];
           } else if (!is_e && j != c) {
-            z = -v[u] * recip_nr(gap2f(sh.th_hi[j], sh.th_lo[j], sh.th_hi[c], sh.th_lo[c]));
+            z = -v[u] * recip_nr(gap2f(sh.col[j].x, sh.col[j].y, sh.col[c].x, sh.col[c].y));
           }
           Zout[e] = z;
         }
@@ -585,7 +588,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_batched_tc(TcArgs a) {
     }
     for (int c = tid; c < n; c += kThreads) {
       const double t = a.theta ? a.theta[vo + c] : (double)M[(int64_t)c * n + c];
-      a.lambda[vo + c] = t + (double)sh.d[c];
+      a.lambda[vo + c] = t + (double)sh.col[c].z;
     }
     if (tid == 0) {
       a.status[p] = status;
