@@ -103,6 +103,8 @@ struct __align__(16) SmemTc {
   uint64_t full[kStages], empty[kStages], acc_full[2], acc_empty[2];
   uint64_t dbar;  // a diagonal tile's d_c written (the four warps holding the diagonal)
   uint32_t tmem;
+  uint32_t gc, gm, tm;  // pipeline positions of the copy and MMA threads (kept here, not
+                        // in every thread's registers)
   int abort, prob, flag, verdict;
 };
 
@@ -294,6 +296,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_batched_tc(TcArgs a) {
     }
     mbar::mbar_init(&sh.dbar, 4);
     sh.abort = 0;
+    sh.gc = sh.gm = sh.tm = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -310,9 +313,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_batched_tc(TcArgs a) {
   volatile int* abort = &sh.abort;
 
   // pipeline positions, kept across problems (barrier phases persist)
-  uint32_t gc = 0;  // copy warp: slices issued
-  uint32_t gm = 0;  // MMA warp: slices consumed
-  uint32_t tm = 0;  // MMA warp: tiles accumulated
   uint32_t te = 0;  // epilogue warps: tiles finished
   uint32_t td = 0;  // epilogue warps: diagonal tiles passed
   bool cta_stalled = false;
@@ -365,6 +365,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_batched_tc(TcArgs a) {
         if (warp == kCopyWarp) {
           // ---------------------------------------------- copies
           if (lane == 0) {
+            uint32_t gc = sh.gc;  // slices issued
             for (int ti = 0; ti < ntiles && !*abort; ++ti) {
               int rb, cb;
               tile_of(ti, nt, rb, cb);
@@ -388,11 +389,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_batched_tc(TcArgs a) {
                 }
               }
             }
+            sh.gc = gc;
           }
           __syncwarp();
         } else if (warp == kMmaWarp) {
           // ---------------------------------------------- MMAs
           if (lane == 0) {
+            uint32_t gm = sh.gm, tm = sh.tm;  // slices consumed, tiles accumulated
             for (int ti = 0; ti < ntiles && !*abort; ++ti, ++tm) {
               const uint32_t b = tm & 1u, use_b = tm >> 1;
               if (!mbar::wait_bounded(&sh.acc_empty[b], (use_b & 1u) ^ 1u, abort)) {
@@ -434,6 +437,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_batched_tc(TcArgs a) {
               }
               tc::mma_commit(&sh.acc_full[b]);
             }
+            sh.gm = gm;
+            sh.tm = tm;
           }
           __syncwarp();
         } else {
@@ -606,13 +611,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_batched_tc(TcArgs a) {
     __shared__ int no_abort;
     if (tid == 0) no_abort = 0;
     __syncthreads();
-    if (warp == kCopyWarp && lane == 0 && gc > 0) {
-      const uint32_t last = gc - 1;
+    if (warp == kCopyWarp && lane == 0 && sh.gc > 0) {
+      const uint32_t last = sh.gc - 1;
       mbar::wait_bounded(&sh.full[last % kStages], (last / kStages) & 1u, &no_abort,
                          mbar::kWaitLimitNs / 4);
     }
-    if (warp == kMmaWarp && lane == 0 && gm > 0) {
-      const uint32_t last = gm - 1;
+    if (warp == kMmaWarp && lane == 0 && sh.gm > 0) {
+      const uint32_t last = sh.gm - 1;
       mbar::wait_bounded(&sh.empty[last % kStages], (last / kStages) & 1u, &no_abort,
                          mbar::kWaitLimitNs / 4);
     }
