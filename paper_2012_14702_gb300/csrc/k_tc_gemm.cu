@@ -45,13 +45,12 @@ constexpr int BM = 128, BN = 256, BK = 64;
 constexpr int A_BYTES = BM * BK * 2;
 constexpr int TMEM_COLS = 2 * BN;
 
-// Kernel modes.  SINGLE: one CTA per 128 x 256 tile.  MULTICAST: 2-CTA
-// clusters computing two vertically adjacent single tiles whose shared B tile
-// is loaded half by each CTA and multicast.  PAIR: 2-CTA clusters issuing one
-// paired MMA (cta_group::2, M = 256) per K step; each CTA holds its own 128 A
-// rows and one 128-row half of B, so a CTA's shared memory takes 32 KB per
-// K step instead of 48 KB for the same 128 x 256 x 64 of its own output.
-enum { MODE_SINGLE = 0, MODE_MULTICAST = 1, MODE_PAIR = 2 };
+// Kernel modes.  SINGLE: one CTA per 128 x 256 tile.  PAIR: 2-CTA clusters
+// issuing one paired MMA (cta_group::2, M = 256) per K step; each CTA holds its
+// own 128 A rows and one 128-row half of B, so a CTA's shared memory takes
+// 32 KB per K step instead of 48 KB for the same 128 x 256 x 64 of its own
+// output.  Every operand load is a plain (non-multicast) TMA load.
+enum { MODE_SINGLE = 0, MODE_PAIR = 2 };
 #ifndef IPT_PAIR_STAGES
 #define IPT_PAIR_STAGES 6
 #endif
@@ -140,18 +139,6 @@ __device__ __forceinline__ void tma_load(void* dst, const CUtensorMap* map, uint
       : "memory");
 }
 
-// The same load with cluster multicast: the box lands at the same shared
-// memory offset in every CTA of `mask`, and each one's mbarrier at the same
-// offset receives the byte count.
-__device__ __forceinline__ void tma_load_mc(void* dst, const CUtensorMap* map, uint64_t* bar,
-                                            int x, int y, uint16_t mask) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
-      ".multicast::cluster [%0], [%1, {%3, %4}], [%2], %5;" ::"r"(su32(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(su32(bar)), "r"(x), "r"(y), "h"(mask)
-      : "memory");
-}
-
 // Load whose completion is counted on an mbarrier of either CTA of the pair
 // (`bar` is a shared::cluster address, here always the pair's first CTA).
 __device__ __forceinline__ void tma_load_pair(void* dst, const CUtensorMap* map, uint32_t bar,
@@ -199,15 +186,6 @@ __device__ __forceinline__ void mma_commit_pair(uint64_t* bar) {
           su32(bar))
       : "memory");
 }
-// Completion of this CTA's MMAs arrives on the barrier at the same offset in
-// every CTA of `mask` (releases a shared operand stage in both CTAs).
-__device__ __forceinline__ void mma_commit_mc(uint64_t* bar, uint16_t mask) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
-      " [%0], %1;" ::"r"(su32(bar)),
-      "h"(mask)
-      : "memory");
-}
 
 __device__ __forceinline__ void tile_coords(int t, int num_m, int num_n, int& mb, int& nb) {
   const int per_group = GROUP_M * num_n;
@@ -224,12 +202,6 @@ __device__ __forceinline__ void fail(Ctl* ctl, DevState* st, int code) {
   atomicCAS(&st->timeout, 0, code);
 }
 
-// MULTICAST (cluster of 2 along M): the two CTAs of a cluster compute the
-// vertically adjacent tiles (2p, nb) and (2p+1, nb), which share the B tile;
-// each CTA loads one 128-row half of it and multicasts the half to both.  A
-// stage is released only when both CTAs' MMAs are done with it (two arrivals
-// on the empty barrier, one multicast commit from each CTA).
-//
 // PAIR (cluster of 2 along M): the same two tiles as one 256 x 256 paired
 // product.  Each CTA's producer loads its 128 A rows and its half of B into
 // its own shared memory, counting the bytes on the first CTA's full barrier
@@ -277,7 +249,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&ctl->full[s], 1);
-      mbar_init(&ctl->empty[s], MODE == MODE_MULTICAST ? 2 : 1);
+      mbar_init(&ctl->empty[s], 1);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&ctl->tfull[b], 1);
@@ -348,11 +320,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
           } else {
             mbar_expect_tx(&ctl->full[stage], STAGE_BYTES);
             tma_load(sA + stage * A_BYTES, mA, &ctl->full[stage], kx, mb * BM);
-            if constexpr (MODE == MODE_MULTICAST)
-              tma_load_mc(sB + stage * B_BYTES + rank * (B_BYTES / 2), mB, &ctl->full[stage], kx,
-                          nb * BN + rank * (BN / 2), (uint16_t)0x3);
-            else
-              tma_load(sB + stage * B_BYTES, mB, &ctl->full[stage], kx, nb * BN);
+            tma_load(sB + stage * B_BYTES, mB, &ctl->full[stage], kx, nb * BN);
           }
           pend_parity[stage] = (int)phase;
           if (++stage == STAGES) {
@@ -411,8 +379,6 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
               mma_f16(dt, sw128_desc(ab + k * 32), sw128_desc(bb + k * 32), idesc, (kb | k) != 0);
           }
           if constexpr (PAIR) mma_commit_pair_mc(&ctl->empty[stage], (uint16_t)0x3);
-          else if constexpr (MODE == MODE_MULTICAST)
-            mma_commit_mc(&ctl->empty[stage], (uint16_t)0x3);
           else mma_commit(&ctl->empty[stage]);
           if (++stage == STAGES) {
             stage = 0;
@@ -608,14 +574,6 @@ bool make_map(CUtensorMap* m, const void* base, uint64_t inner, uint64_t outer,
 
 }  // namespace
 
-// Two-CTA clusters with multicast B halves (IPT_TC_MULTICAST=1 at compile
-// time, in place of the single-CTA kernel) halve each CTA's L2 operand reads
-// but not its shared-memory traffic; at n = 8192 they measured no faster than
-// single CTAs.
-#ifndef IPT_TC_MULTICAST
-#define IPT_TC_MULTICAST 0
-#endif
-
 template <int MODE>
 cudaError_t configure(int dev) {
   static int configured = -1;
@@ -666,9 +624,8 @@ cudaError_t launch_gemm_tc(const uint16_t* Dh, const uint16_t* Dl, const uint16_
   const bool bf = bf16 != 0;
   const int num_m = npad / BM, num_n = kpad / BN, num_kb = npad / BK;
   const bool pair = mode != IPT_PRODUCT_SINGLE && num_m % 2 == 0;
-  const bool mc = !pair && IPT_TC_MULTICAST && num_m % 2 == 0;
   CUtensorMap mDh, mDl, mWh, mWl;
-  const uint32_t bbox = (pair || mc) ? BN / 2 : BN;
+  const uint32_t bbox = pair ? BN / 2 : BN;
   if (!make_map(&mDh, Dh, npad, npad, BM, bf) || !make_map(&mDl, Dl, npad, npad, BM, bf) ||
       !make_map(&mWh, Wh, npad, kpad, bbox, bf) || !make_map(&mWl, Wl, npad, kpad, bbox, bf))
     return cudaErrorInvalidValue;
@@ -685,11 +642,6 @@ cudaError_t launch_gemm_tc(const uint16_t* Dh, const uint16_t* Dl, const uint16_
     if ((e = configure<MODE_PAIR>(dev)) != cudaSuccess) return e;
     return launch_cluster<MODE_PAIR>(mDh, mDl, mWh, mWl, a, num_m, num_n, num_kb, passes,
                                      idesc_for(bf, 2 * BM), num_sms, s);
-  }
-  if (mc) {
-    if ((e = configure<MODE_MULTICAST>(dev)) != cudaSuccess) return e;
-    return launch_cluster<MODE_MULTICAST>(mDh, mDl, mWh, mWl, a, num_m, num_n, num_kb, passes,
-                                          idesc_for(bf, BM), num_sms, s);
   }
   if ((e = configure<MODE_SINGLE>(dev)) != cudaSuccess) return e;
   const int tiles = num_m * num_n;
