@@ -120,6 +120,83 @@ def cpu_baseline(M, th, ks_arg):
                       f"{spent:.1f} s of CPU time"}
 
 
+# ---------------------------------------------------------------- per-result error vs the oracle
+def sample_columns(n, k=16, seed=99):
+    """A fixed, seeded sample of k column indices (the first and last included)."""
+    g = np.random.Generator(np.random.PCG64(seed))
+    mid = g.choice(np.arange(1, n - 1), size=min(k - 2, n - 2), replace=False)
+    return np.unique(np.concatenate([[0, n - 1], mid])).astype(np.int64)
+
+
+def oracle_reference(M32, th, oc, accel=None):
+    """FP64 oracle eigenpairs of the requested columns `oc` of the matrix as the
+    GPU sees it (FP32-rounded, in float64), outside any timed region: Alg. 1 per
+    column, or past the Picard domain (accel="acx") the oracle's IPT-ACX with one
+    step length per column, whose fixed points are the same eigenpairs."""
+    import oracle
+    oc = np.asarray(oc)
+    if accel == "acx":
+        ref = oracle.ipt_solve_acx(M32, th, cols=oc, tol=1e-12, max_iter=800, stop="residual")
+    else:
+        ref = oracle.ipt_solve(M32, th, cols=oc, tol=1e-12, max_iter=200, stop="residual")
+    ref["cols"] = oc
+    ref["n"] = M32.shape[0]
+    ref["how"] = ("FP64 numpy oracle, " + ("IPT-ACX per column" if accel == "acx" else "Alg. 1")
+                  + f" to rho <= 1e-12 on {len(oc)} sampled columns")
+    return ref
+
+
+def oracle_error(ref, lam, Z, idx):
+    """Largest relative eigenvalue error and the eigenvector error of a GPU result
+    (lam, Z on the device) on its columns `idx`, which requested ref's columns."""
+    import oracle
+    import torch
+    if ref["status"] != oracle.OK:
+        return {"oracle_status": int(ref["status"])}
+    idx = np.asarray(idx)
+    lam_s = lam.cpu().numpy()[idx]
+    Zs = Z[:, torch.as_tensor(idx, device=Z.device)].double().cpu().numpy()
+    lam_err = float(np.max(np.abs(lam_s - ref["lam"]) / np.maximum(np.abs(ref["lam"]), 1e-300)))
+    E = oracle.unit_columns(ref["n"], ref["cols"])
+    z_err = float(np.linalg.norm(Zs - ref["Z"]) / max(np.linalg.norm(ref["Z"] - E), 1e-300))
+    return {"lam_rel_err_max": lam_err, "z_rel_err": z_err, "oracle": ref["how"]}
+
+
+def batched_oracle_error(sizes, flat, lam, Z, picks):
+    """Largest relative eigenvalue error and eigenvector error, over the sampled
+    problems `picks` of a batched result, against the FP64 oracle's full-spectrum
+    Alg. 2 on each problem (theta = diag(M_p), as the batched solve uses)."""
+    import oracle
+    mo = np.concatenate([[0], np.cumsum(sizes * sizes)])
+    vo = np.concatenate([[0], np.cumsum(sizes)])
+    lam_h = lam.cpu().numpy()
+    lam_err = z_err = 0.0
+    for p in picks:
+        n = int(sizes[p])
+        M = flat[mo[p]:mo[p] + n * n].astype(np.float64).reshape(n, n)
+        th = np.diag(M).copy()
+        ref = oracle.ipt_solve(M, th, tol=1e-12, max_iter=200, stop="residual")
+        if ref["status"] != oracle.OK:
+            return {"oracle_status": int(ref["status"]), "problem": int(p)}
+        Zp = Z[int(mo[p]):int(mo[p]) + n * n].view(n, n).t().double().cpu().numpy()
+        lp = lam_h[vo[p]:vo[p] + n]
+        lam_err = max(lam_err, float(np.max(np.abs(lp - ref["lam"]) / np.abs(ref["lam"]))))
+        z_err = max(z_err, float(np.linalg.norm(Zp - ref["Z"]) /
+                                 max(np.linalg.norm(ref["Z"] - np.eye(n)), 1e-300)))
+    return {"lam_rel_err_max": lam_err, "z_rel_err_max": z_err,
+            "oracle": f"FP64 numpy oracle, Alg. 2 to rho <= 1e-12 on {len(picks)} sampled "
+                      f"problems (all their eigenpairs)"}
+
+
+def dense_reference(Mg, th, idx, accel=None):
+    """oracle_reference for a dense FP32 device matrix, full spectrum (column c
+    requested e_c), on the result columns idx."""
+    M32 = Mg.double().cpu().numpy()
+    ref = oracle_reference(M32, th, idx, accel)
+    del M32
+    return ref
+
+
 # ---------------------------------------------------------------- clocks
 CLOCK_Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
            "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -277,12 +354,28 @@ def run_csr(steps, warmup, hbm_peak):
                              "setup": sum(i["setup_ms"] for i in infos) / steps,
                              "finalize": sum(i["finalize_ms"] for i in infos) / steps}}
     full, win = out[False], out[True]
+    # the result against the FP64 oracle (CSR Alg. 1 on the FP32-rounded values)
+    # on 8 of the 64 columns, outside the timed region
+    import oracle
+    lam_c, Z_c, vinfo = solver.solve_csr(rp, ci, vv, CSR_N, cols=cg, tol=TOL, max_iter=50,
+                                         verify_fp64=True)
+    pick = np.array([0, 1, 2, 15, 31, 47, 62, 63])
+    vals32 = vals.astype(np.float32).astype(np.float64)
+    ref = oracle.ipt_solve_csr(rowptr, colind, vals32, CSR_N, cols=cols[pick], tol=1e-12,
+                               max_iter=100)
+    ref["cols"], ref["n"] = cols[pick], CSR_N
+    ref["how"] = "FP64 numpy oracle, Alg. 1 (CSR) to an increment of 1e-12 on 8 columns"
+    win["oracle_error"] = oracle_error(ref, lam_c, Z_c, pick)
+    win["rho_fp64"] = vinfo["rho_fp64"]
+    win["rho_error_model"] = vinfo["rho_error"]
+    del Z_c
     bytes_launch = 4 * (CSR_N + 1) + 8 * nnz + 16 * CSR_N + 8 * CSR_N * kk
     achieved = bytes_launch / (full["spmm_ms_per_launch"] / 1e3) / 1e9
     return {
         "workload": f"CSR n=2^20, nnz={nnz}, 8 offsets/row in 1..2048 mirrored + diagonal, "
                     f"N(0,1)*1e-3, theta_i=i*1e-2+U(0,1e-3), seed 3, k=64 lowest, FP32",
         "ms_to_tol": win["ms_to_tol"], "iterations": win["iterations"], "rho": win["rho"],
+        "rho_fp64": win["rho_fp64"], "oracle_error": win["oracle_error"],
         "active_window": win,
         "all_rows": full,
         "roofline": {"kernel": "k_csr_spmm_map over all rows (half-warp-per-row SpMM + fused "
@@ -312,7 +405,7 @@ def run_batched(steps, warmup, hbm_peak):
     count, nmin, nmax, scale, seed = workloads.BATCHED_CONFIGS["batched_4096_n32_512"]
     sizes, flat, _ = workloads.batched_dense(count, nmin, nmax, scale, seed)
     Mg = torch.as_tensor(flat, device="cuda")
-    del flat
+    picks = np.sort(np.random.Generator(np.random.PCG64(5)).choice(count, 8, replace=False))
     solver = ipt.Solver()
     for _ in range(warmup):
         solver.solve_batched(sizes, Mg, tol=TOL, max_iter=30)
@@ -321,8 +414,8 @@ def run_batched(steps, warmup, hbm_peak):
     kern = []
     e0.record(solver.stream)
     for _ in range(steps):
-        _, _, status, iters, info = solver.solve_batched(sizes, Mg, tol=TOL, max_iter=30,
-                                                         record_timing=True)
+        lam_b, Z_b, status, iters, info = solver.solve_batched(sizes, Mg, tol=TOL, max_iter=30,
+                                                               record_timing=True)
         kern.append(info["product_ms"][0])
     e1.record(solver.stream)
     torch.cuda.synchronize()
@@ -336,6 +429,7 @@ def run_batched(steps, warmup, hbm_peak):
                     f"N(0,1)*{scale}/sqrt(n_p) symmetric, seed {seed}, all eigenpairs, "
                     f"tol 1e-6 residual",
         "ms_to_tol": ms, "problems_per_s": count / (ms / 1e3), "status": info["status"],
+        "oracle_error": batched_oracle_error(sizes, flat, lam_b, Z_b, picks),
         "tiles_by_class": {"n<=64": solver.batched_tiles[0], "n<=256": solver.batched_tiles[1],
                            "n<=1024": solver.batched_tiles[2]},
         "launch": "one CUDA graph (schedule copy, queue reset, persistent kernel)",
@@ -347,11 +441,11 @@ def run_batched(steps, warmup, hbm_peak):
                      "unit": "TFLOP/s", "frac": achieved / FP32_ALU_PEAK, "traffic": None,
                      "flops_per_launch": flops, "avg_launch_ms": k_ms,
                      "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz"},
-        "bf16x3_tensor_cores": run_batched_tc(solver, sizes, Mg, steps, hbm_peak),
+        "bf16x3_tensor_cores": run_batched_tc(solver, sizes, Mg, steps, hbm_peak, flat, picks),
     }
 
 
-def run_batched_tc(solver, sizes, Mg, steps, hbm_peak):
+def run_batched_tc(solver, sizes, Mg, steps, hbm_peak, flat, picks):
     """The same batch with the product on the tensor cores (split BF16 x3, tcgen05,
     128 x 128 tiles; a prologue launch and the warp-specialised solve).  Roofline:
     HBM, the batch's arithmetic intensity (~n_p / 6 flop per byte) being below the
@@ -366,9 +460,9 @@ def run_batched_tc(solver, sizes, Mg, steps, hbm_peak):
     kern = []
     e0.record(solver.stream)
     for _ in range(steps):
-        _, _, status, iters, info = solver.solve_batched(sizes, Mg, tol=TOL, max_iter=30,
-                                                         record_timing=True,
-                                                         precision="bf16x3")
+        lam_b, Z_b, status, iters, info = solver.solve_batched(sizes, Mg, tol=TOL, max_iter=30,
+                                                               record_timing=True,
+                                                               precision="bf16x3")
         kern.append(info["product_ms"][0])
     e1.record(solver.stream)
     torch.cuda.synchronize()
@@ -382,6 +476,7 @@ def run_batched_tc(solver, sizes, Mg, steps, hbm_peak):
     alg_bytes = float(np.sum(12.0 * n2 * np.maximum(its - 1, 0) + 8.0 * n2))
     gbs = alg_bytes / (k_ms / 1e3) / 1e9
     return {"ms_to_tol": ms, "status": info["status"],
+            "oracle_error": batched_oracle_error(sizes, flat, lam_b, Z_b, picks),
             "evaluations": {"min": int(its.min()), "max": int(its.max()),
                             "mean": float(its.mean())},
             "algorithmic_tflops": flops / (k_ms / 1e3) / 1e12,
@@ -401,8 +496,10 @@ def run_batched_tc(solver, sizes, Mg, steps, hbm_peak):
 def run_acx(steps, warmup):
     """IPT-ACX (Alg. 3) past the Picard iteration's domain: n = 4096, theta_i = i/4,
     Delta symmetric N(0,1)*0.06 (seed 31), all 4096 eigenpairs to rho <= 1e-6 with
-    split-FP16 tensor-core products; the plain staged solve on the same matrix is
-    run beside it for its status (it diverges here)."""
+    split-FP16 tensor-core products (a compensated FP32 re-base when their sampled
+    error asks for it); the plain staged solve on the same matrix is run beside it
+    for its status (it diverges here).  Each result carries its FP64 residual and
+    its error against the FP64 oracle on 16 sampled columns."""
     import torch
     from paper_2012_14702_gb300 import ipt, workloads
     n, step, scale, seed = workloads.DENSE_CONFIGS["dense_n4096_edge_sd6e-2"]
@@ -411,29 +508,32 @@ def run_acx(steps, warmup):
     tg = torch.as_tensor(th, dtype=torch.float64, device="cuda")
     del M
     solver = ipt.Solver()
+    idx = sample_columns(n)
+    ref = dense_reference(Mg, th, idx, accel="acx")
     out = {"workload": f"dense symmetric n={n}, theta_i=i/4, Delta N(0,1)*{scale}, seed {seed}, "
                        f"k=n, tol 1e-6 residual"}
-    for sig in ["column", "global"]:
+    for name, kw in [("acx_column_sigma", {"accel": "acx", "acx_sigma": "column"}),
+                     ("acx_global_sigma", {"accel": "acx", "acx_sigma": "global"}),
+                     ("anderson", {"accel": "anderson"})]:
         for _ in range(warmup):
-            solver.solve_dense(Mg, theta=tg, tol=TOL, max_iter=400, accel="acx", acx_sigma=sig)
+            solver.solve_dense(Mg, theta=tg, tol=TOL, max_iter=400, **kw)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(solver.stream)
         for _ in range(steps):
-            _, _, info = solver.solve_dense(Mg, theta=tg, tol=TOL, max_iter=400, accel="acx",
-                                            acx_sigma=sig)
+            _, _, info = solver.solve_dense(Mg, theta=tg, tol=TOL, max_iter=400, **kw)
         e1.record(solver.stream)
         torch.cuda.synchronize()
-        _, _, v = solver.solve_dense(Mg, theta=tg, tol=TOL, max_iter=400, accel="acx",
-                                     acx_sigma=sig, verify_fp64=True)
-        out[f"acx_{sig}_sigma"] = {"ms_to_tol": e0.elapsed_time(e1) / steps,
-                                   "status": info["status"], "evaluations": info["iterations"],
-                                   "rho": info["rho"], "rho_fp64": v["rho_fp64"]}
+        lv, Zv, v = solver.solve_dense(Mg, theta=tg, tol=TOL, max_iter=400, verify_fp64=True,
+                                       record_timing=True, **kw)
+        out[name] = {"ms_to_tol": e0.elapsed_time(e1) / steps,
+                     "status": info["status"], "evaluations": info["iterations"],
+                     "compensated_rebases": v["acc_launches"], "rho": info["rho"],
+                     "rho_error_model": v["rho_error"], "rho_fp64": v["rho_fp64"],
+                     "oracle_error": oracle_error(ref, lv, Zv, idx)}
+        del Zv
     _, _, plain = solver.solve_dense(Mg, theta=tg, tol=TOL, max_iter=400)
     out["plain_staged"] = {"status": plain["status"], "evaluations": plain["iterations"]}
-    out["note"] = ("the stopping test uses the device residual of the split-FP16 product; the "
-                   "FP64-verified residual shows that product's floor at this perturbation "
-                   "(~2e-6: the iterate is far from E, and the product is taken relative to E)")
     return out
 
 
@@ -455,6 +555,8 @@ def run_damped(steps):
         tg = torch.as_tensor(th, dtype=torch.float64, device="cuda")
         del M
         row = {"seed": seed, "s": sc}
+        idx = sample_columns(train_damping.EDGE_N, 8)
+        ref = dense_reference(Mg, th, idx, accel="acx")
         for name, kw in [("plain_staged", {}), ("damped", {"accel": "damped",
                                                            "damping_model": p16}),
                          ("acx", {"accel": "acx"}), ("anderson", {"accel": "anderson"})]:
@@ -468,6 +570,12 @@ def run_damped(steps):
             torch.cuda.synchronize()
             row[name] = {"status": info["status"], "evaluations": info["iterations"],
                          "ms": e0.elapsed_time(e1) / steps}
+            if info["status"] == "OK":
+                lv, Zv, v = solver.solve_dense(Mg, theta=tg, tol=TOL, max_iter=600,
+                                               verify_fp64=True, **kw)
+                row[name]["rho_fp64"] = v["rho_fp64"]
+                row[name]["oracle_error"] = oracle_error(ref, lv, Zv, idx)
+                del Zv
         rows.append(row)
     # the headline workload with the learned damping on top of the staged products
     M, th = workload(N_DEFAULT)
@@ -511,6 +619,8 @@ def run_eps_sweep(steps):
         thg = torch.as_tensor(th, dtype=torch.float64, device="cuda")
         del M
         row = {}
+        idx = sample_columns(n, 8)
+        ref = dense_reference(Mg, th, idx)
         for label, kw, reps in [("staged_fp16", {"precision": "staged"}, steps),
                                 ("staged_bf16", {"precision": "staged", "staged_bf16": True},
                                  steps),
@@ -522,11 +632,13 @@ def run_eps_sweep(steps):
                 _, _, info = solver.solve_dense(Mg, theta=thg, tol=TOL, max_iter=60, **kw)
             e1.record(solver.stream)
             torch.cuda.synchronize()
-            _, _, v = solver.solve_dense(Mg, theta=thg, tol=TOL, max_iter=60, verify_fp64=True,
-                                         **kw)
+            lv, Zv, v = solver.solve_dense(Mg, theta=thg, tol=TOL, max_iter=60,
+                                           verify_fp64=True, **kw)
             row[label] = {"ms_to_tol": e0.elapsed_time(e1) / reps, "status": info["status"],
                           "iterations": info["iterations"], "stage_iters": info["stage_iters"],
-                          "rho": info["rho"], "rho_fp64": v["rho_fp64"]}
+                          "rho": info["rho"], "rho_error_model": v["rho_error"],
+                          "rho_fp64": v["rho_fp64"], "oracle_error": oracle_error(ref, lv, Zv, idx)}
+            del Zv
         row["speedup_fp16_vs_plain"] = row["plain_fp32"]["ms_to_tol"] / row["staged_fp16"]["ms_to_tol"]
         out[f"eps_{scale:g}"] = row
         del Mg
@@ -550,6 +662,8 @@ def run_paper_family(steps):
         thg = torch.as_tensor(th, dtype=torch.float64, device="cuda")
         del M
         row = {}
+        idx = sample_columns(N_DEFAULT, 8)
+        ref = dense_reference(Mg, th, idx)
         for label, kw, reps in [("staged_fp16", {"precision": "staged"}, steps),
                                 ("plain_fp32", {"precision": "f32"}, 2)]:
             solver.solve_dense(Mg, theta=thg, tol=TOL, max_iter=60, **kw)
@@ -559,11 +673,13 @@ def run_paper_family(steps):
                 _, _, info = solver.solve_dense(Mg, theta=thg, tol=TOL, max_iter=60, **kw)
             e1.record(solver.stream)
             torch.cuda.synchronize()
-            _, _, v = solver.solve_dense(Mg, theta=thg, tol=TOL, max_iter=60, verify_fp64=True,
-                                         **kw)
+            lv, Zv, v = solver.solve_dense(Mg, theta=thg, tol=TOL, max_iter=60,
+                                           verify_fp64=True, **kw)
             row[label] = {"ms_to_tol": e0.elapsed_time(e1) / reps, "status": info["status"],
                           "iterations": info["iterations"], "stage_iters": info["stage_iters"],
-                          "rho_fp64": v["rho_fp64"]}
+                          "rho_error_model": v["rho_error"], "rho_fp64": v["rho_fp64"],
+                          "oracle_error": oracle_error(ref, lv, Zv, idx)}
+            del Zv
         out["symmetric" if sym else "nonsymmetric"] = row
         del Mg
     out["workload"] = f"M = diag(i) + 0.01 U[0,1], n={N_DEFAULT}, seed 9, theta = diag(M), k=n"
@@ -647,11 +763,15 @@ def run_ours(args, rank, world, local_rank):
     t1 = sum(i["product_ms"][0] for i in infos)
     t3 = sum(i["product_ms"][1] for i in infos)
     tp = sum(i["prepass_ms"] for i in infos)
-    gemm_flops = 2.0 * n * n * n  # one 16-bit GEMM product Delta W, n x n x n
+    gemm_flops = 2.0 * n * n * n  # algorithmic work of one product Delta V, n x n x n
     burst, sustained, peak_src = measured_peak()
     timed_s = ms * args.steps / 1e3
     peak = sustained if timed_s >= 1.0 else burst
-    achieved = (l1 * gemm_flops + 3 * l3 * gemm_flops) / ((t1 + t3) / 1e3) / 1e12
+    # algorithmic: every product launch does 2 n^3 of the method's work, whatever
+    # its pass count; the split launch's three passes are reported as executed work
+    achieved = (l1 + l3) * gemm_flops / ((t1 + t3) / 1e3) / 1e12
+    a1 = gemm_flops / (t1 / max(l1, 1) / 1e3) / 1e12 if l1 else None
+    a3 = gemm_flops / (t3 / max(l3, 1) / 1e3) / 1e12 if l3 else None
     tr = profiled_traffic("k_gemm_tc_dense_n8192.md", "k_tc_gemm.cu",
                           ["traffic_bytes_per_launch_1pass", "traffic_bytes_per_launch_3pass"])
     # per launch of the timed mix of 1-pass and 3-pass launches, like `achieved`
@@ -662,19 +782,28 @@ def run_ours(args, rank, world, local_rank):
         "kernel": "k_gemm_tc (tcgen05 FP16 product + fused IPT map epilogue)",
         "bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
         "frac": achieved / peak if peak else None, "traffic": traffic,
+        "definition": "algorithmic 2 n^3 flop per product launch (1-pass and 3-pass alike) / "
+                      "mean CUDA-event launch time over the timed mix",
+        "per_launch_kind": {
+            "1pass": {"achieved": a1, "frac": a1 / peak if a1 else None},
+            "3pass": {"achieved": a3, "frac": a3 / peak if a3 else None,
+                      "executed": 3 * a3 if a3 else None,
+                      "executed_frac": 3 * a3 / peak if a3 else None}},
         "traffic_per_launch": None if tr is None else {
             "1pass": tr["traffic_bytes_per_launch_1pass"],
             "3pass": tr["traffic_bytes_per_launch_3pass"]},
         "algorithmic_bytes_per_launch": {"1pass": 16 * n * n, "3pass": 24 * n * n},
         "peak_source": f"{peak_src} {'sustained' if peak == sustained else 'burst'} bf16 "
                        f"(FP16 dense rate equals BF16)",
-        "flops_per_launch": {"1pass": gemm_flops, "3pass": 3 * gemm_flops},
+        "flops_per_launch": gemm_flops,
         "launches": {"1pass": l1, "3pass": l3},
         "avg_launch_ms": {"1pass": t1 / max(l1, 1), "3pass": t3 / max(l3, 1)},
         "prepass_ms_per_eval": tp / max(l1 + l3, 1),
     }
-    ipt_flops = 2.0 * n * n * n  # algorithmic flops of one IPT evaluation (Delta Z)
-    tflops_iter = ipt_flops * iters / (ms / 1e3) / 1e12
+    # per-iteration TFLOP/s: the algorithmic flops of the evaluations that run a
+    # product (the product-free first evaluation at Z = E does none) over the solve
+    products_per_solve = (l1 + l3 + sum(i["acc_launches"] for i in infos)) / len(infos)
+    tflops_iter = gemm_flops * products_per_solve / (ms / 1e3) / 1e12
 
     # plain FP32 IPT on the same GPU, same stopping rule
     solve(precision="f32")
@@ -686,9 +815,15 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     plain_ms = (time.perf_counter() - p0) * 1e3 / reps
 
-    # FP64-verified residual of both results (outside the timed region)
-    _, _, vinfo = solve(precision="staged", verify_fp64=True)
-    _, _, pvinfo = solve(precision="f32", verify_fp64=True)
+    # FP64-verified residual of both results (outside the timed region), and
+    # their error against the FP64 oracle on sampled columns
+    lam_v, Z_v, vinfo = solve(precision="staged", verify_fp64=True)
+    lam_p, Z_p, pvinfo = solve(precision="f32", verify_fp64=True)
+    idx = sample_columns(n)
+    ref = dense_reference(Mg, th, idx)
+    err_staged = oracle_error(ref, lam_v, Z_v, idx)
+    err_plain = oracle_error(ref, lam_p, Z_p, idx)
+    del Z_v, Z_p
 
     # end to end through the host-buffer C ABI call: pinned M in, Lambda and Z out
     Mh = torch.as_tensor(M, dtype=torch.float32).pin_memory()
@@ -730,11 +865,14 @@ def run_ours(args, rank, world, local_rank):
         "iterations": iters,
         "stage_iters": infos[-1]["stage_iters"],
         "rho": infos[-1]["rho"], "rho_fp64": vinfo["rho_fp64"],
+        "rho_error_model": vinfo["rho_error"],
+        "oracle_error": err_staged,
         "tflops_per_iter": tflops_iter,
+        "products_per_solve": products_per_solve,
         "breakdown_ms": breakdown,
         "plain_fp32": {"ms": plain_ms, "iterations": pinfo["iterations"],
                        "rho": pinfo["rho"], "rho_fp64": pvinfo["rho_fp64"],
-                       "speedup": plain_ms / ms},
+                       "speedup": plain_ms / ms, "oracle_error": err_plain},
         "roofline": roofline,
         "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": n * n * 4 + n * 8,
                 "d2h_bytes_per_step": n * n * 4 + n * 8},

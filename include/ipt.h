@@ -48,7 +48,11 @@ typedef enum {
   IPT_INVALID_ARG = 4,      /* bad size, pointer, dtype, column index or option      */
   IPT_CUDA_ERROR = 5,       /* a CUDA runtime call failed                            */
   IPT_DEVICE_TIMEOUT = 6,   /* a bounded device-side wait gave up                    */
-  IPT_UNSUPPORTED = 7       /* valid request this build cannot serve                 */
+  IPT_UNSUPPORTED = 7,      /* valid request this build cannot serve                 */
+  IPT_INACCURATE = 8        /* residual stop with a fixed product precision: the test held
+                               in the product's arithmetic, but rho plus the predicted error
+                               of that arithmetic exceeds tol (the outputs hold that iterate;
+                               IPT_PREC_STAGED escalates instead)                     */
 } ipt_status;
 
 /* Element types of inputs and outputs. */
@@ -72,7 +76,10 @@ typedef enum {
                           ipt_options.staged_bf16).  Only evaluations whose predicted
                           product error is below tol / 10 may declare convergence   */
   IPT_PREC_FP16 = 5,   /* FP16 tensor-core product, FP32 accumulate/iterate            */
-  IPT_PREC_FP16X3 = 6  /* split-FP16 x3 tensor-core product                            */
+  IPT_PREC_FP16X3 = 6, /* split-FP16 x3 tensor-core product                            */
+  IPT_PREC_F32C = 7    /* FP32 FMA product of Delta W with compensated sums: FP32
+                          partials of 32 products added as FP32 pairs (TwoSum); the
+                          staged schedule's accurate re-base                          */
 } ipt_precision;
 
 /* Stopping test. */
@@ -100,8 +107,8 @@ typedef struct {
                            IPT_PRODUCT_PAIR (two CTAs per 256 x 256 tile, one paired MMA;
                            needs an even number of 128-row blocks, else SINGLE is used).
                            Results are identical; only speed differs                     */
-  int accel;            /* ipt_solve_dense: IPT_ACCEL_NONE (default, the Picard update of
-                           Alg. 1/2), IPT_ACCEL_DAMPED, IPT_ACCEL_ANDERSON (below) or
+  int accel;            /* IPT_ACCEL_NONE (default, the Picard update of Alg. 1/2),
+                           IPT_ACCEL_DAMPED, IPT_ACCEL_ANDERSON (below; dense only) or
                            IPT_ACCEL_ACX (Alg. 3: each extrapolation evaluates
                            F at z, f(z) [, f^2(z)] and moves z by the order-3 / order-2
                            extrapolation, orders 3, 2, 3, 2, ...; the stopping test is made
@@ -162,6 +169,11 @@ typedef struct {
                                       -1 for the product-free first evaluation           */
   long long rows_evaluated; /* ipt_solve_csr: rows the products evaluated, summed over
                                evaluations (n per evaluation without the active window)  */
+  int acc_launches;     /* compensated FP32 product launches (IPT_PREC_F32C evaluations)  */
+  double acc_ms;        /* their summed device time (record_timing), else 0               */
+  double rho_error;     /* predicted |rho - rho_true| of the returned pair: the error model
+                           of the products and of the iterate's arithmetic (residual
+                           stop: IPT_OK means rho + rho_error <= tol)                    */
 } ipt_result;
 
 typedef struct ipt_handle ipt_handle;
@@ -240,8 +252,13 @@ ipt_status ipt_step_dense(ipt_handle* h, int64_t n, const void* M, int64_t ldm, 
  * Every other argument as in ipt_solve_dense.  Product arithmetic: FP32
  * (IPT_PREC_F32; IPT_PREC_STAGED, the option default, also selects it) or
  * FP64 (IPT_PREC_F64); other precisions return IPT_UNSUPPORTED.  A warm start
- * (opt->z0) is not accepted here (IPT_INVALID_ARG); verify_fp64 is ignored
- * (rho_fp64 = -1).  n < 2^30, nnz < 2^31.
+ * (opt->z0) is not accepted here (IPT_INVALID_ARG).  opt->accel may be
+ * IPT_ACCEL_NONE or IPT_ACCEL_ACX (Alg. 3 as for dense M, on the row-major
+ * iterates and the active window widened by the band after each extrapolation;
+ * acx_sigma as there); the other accelerations return IPT_UNSUPPORTED.
+ * verify_fp64 recomputes
+ * ||M Z - Z Lambda||_F of the result in FP64 over all n rows from the stored
+ * entries (result.rho_fp64).  n < 2^30, nnz < 2^31.
  */
 ipt_status ipt_solve_csr(ipt_handle* h, int64_t n, int64_t nnz, const int32_t* rowptr,
                          const int32_t* colind, const void* vals, int v_dtype,
@@ -317,6 +334,20 @@ ipt_status ipt_check_bounded_wait(int arrive, double limit_s, void* stream, int3
                                   double* waited_s);
 
 /*
+ * Check of the FP32 map's division (no counterpart in the paper, which fixes no
+ * precision).  The FP32 epilogues form F = u / (theta_j - theta_{i_c}) as u times
+ * the hardware reciprocal estimate of the gap refined by one Newton-Raphson step;
+ * this call applies that same device function elementwise,
+ *   quotient[i] = u[i] * refined_reciprocal(gap[i]),  i < count,
+ * to device FP32 arrays, enqueued on `stream` (NULL = legacy default stream)
+ * without synchronising, so that it can be compared with IEEE division.
+ * Returns IPT_INVALID_ARG for count < 0 or a NULL array, IPT_CUDA_ERROR on a
+ * launch error.
+ */
+ipt_status ipt_check_map_division(int64_t count, const float* gap, const float* u,
+                                  float* quotient, void* stream);
+
+/*
  * The damping model of IPT_ACCEL_DAMPED and its training (no counterpart in the
  * paper).  A 6 -> 64 -> 64 -> 1 perceptron: h1 = tanh(x W1 + b1),
  * h2 = tanh(h1 W2 + b2), y = h2 W3 + b3, alpha = 2 / (1 + exp(-y)).  Parameters:
@@ -346,20 +377,23 @@ ipt_status ipt_damping_adam(float* master, void* params, float* grad, float* m, 
 /*
  * ||M Z - Z Lambda||_F in FP64, allocating no device memory.  The paper has
  * no counterpart: this is a library service for callers that cannot call
- * cudaMalloc -- work recorded by CUDA stream capture, processes whose device
- * memory belongs to another allocator (e.g. a framework's caching pool), and
- * loops where an allocation's implicit device synchronisation is not
- * acceptable.  Its only scratch is a fixed file-scope device array of 16384
- * FP64 partial sums (128 KiB per device, held until the library is unloaded).
- *   n, M, ldm, m_dtype   dense M as for ipt_solve_dense (device)
+ * cudaMalloc -- processes whose device memory belongs to another allocator
+ * (e.g. a framework's caching pool, or a fixed memory budget) that forbids
+ * side allocations, and loops where an allocation's implicit device
+ * synchronisation is not acceptable.  Its only scratch is a fixed file-scope
+ * device array of 16384 FP64 partial sums (128 KiB on every device that loads
+ * the library, held until the library is unloaded).
+ *   n, M, ldm, m_dtype   dense M as for ipt_solve_dense (device, row-major)
  *   k, Z, ldz, z_dtype   n x k column-major eigenvector block (device)
  *   lambda               device, k doubles
  *   out                  device, 1 double: the norm is written there
  *   stream               cudaStream_t the two kernels are enqueued on (NULL =
  *                        legacy default stream); the call does not synchronise
  * Limit: ceil(n/64) * ceil(k/64) <= 16384 (e.g. n = k = 8192); larger sizes
- * return IPT_UNSUPPORTED without launching anything.  The first call on a
- * device looks up the array's device address (once per device); make that
+ * return IPT_UNSUPPORTED without launching anything.  A CUDA error already
+ * pending on the calling thread returns IPT_CUDA_ERROR without launching and
+ * is left pending for the caller.  The first call on a device (and the first
+ * after a cudaDeviceReset) looks up the array's device address; make that
  * first call before any stream capture begins.  All calls share the array:
  * calls whose kernels overlap on the GPU (different streams, no ordering)
  * race on it and may return wrong norms.  Nothing in the array needs to start

@@ -4,6 +4,6 @@ from .ipt_oracle import (OK, MAXITER, DIVERGED, DEGENERATE_THETA, INVALID_ARG,  
                          partition, unit_columns, inverse_gaps, ipt_map, residual,
                          initial_residual_norm, ipt_solve, ipt_solve_csr,
                          rs_corrections, chart_jacobian, acx_differences, acx_sigma,
-                         acx_update, ipt_solve_acx)
+                         acx_update, ipt_solve_acx, ipt_solve_acx_csr)
 from . import damping  # noqa: F401,E402
 from . import anderson  # noqa: F401,E402

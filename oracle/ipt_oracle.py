@@ -203,6 +203,22 @@ def ipt_solve_csr(rowptr, colind, vals, n, theta=None, cols=None, **kw):
                      product=lambda Z: np.asarray(Delta @ Z), **kw)
 
 
+def ipt_solve_acx_csr(rowptr, colind, vals, n, theta=None, cols=None, **kw):
+    """IPT-ACX (Alg. 3) for a sparse M given in CSR, as ipt_solve_csr does for
+    Alg. 1/2: Delta = M - diag(theta) (theta = diag(M) by default) and the
+    product Delta Z by scipy's CSR times dense product."""
+    import scipy.sparse as sp
+
+    M = sp.csr_matrix((np.asarray(vals, dtype=np.float64), np.asarray(colind),
+                       np.asarray(rowptr)), shape=(n, n))
+    if theta is None:
+        theta = M.diagonal().astype(np.float64)
+    theta = np.asarray(theta, dtype=np.float64)
+    Delta = (M - sp.diags(theta)).tocsr()
+    return ipt_solve_acx(None, theta=theta, cols=cols, Delta=Delta,
+                         product=lambda Z: np.asarray(Delta @ Z), **kw)
+
+
 def acx_differences(z, fs):
     """Alg. 3 lines 4-6 and 11: the differences of the iterates z, f(z), f^2(z), ...
 

@@ -38,13 +38,16 @@ constexpr int kCsrChunk = 4;
 // Dense tensor-core solves (device-chosen operands) likewise.
 constexpr int kDenseChunk = 6;
 constexpr int kEvbSlots = kDenseChunk > kCsrChunk ? kDenseChunk : kCsrChunk;
+// Accumulation term of the split products' error model (see set_error_model).
+constexpr double kSplitAccum = 0.66;
 
 }  // namespace
 
 struct ipt_handle {
   cudaStream_t s = nullptr;
   int dev = 0;
-  Buf drow, dt, dh, dl, z[4], pbuf, wh, wl, rinv, sinv;
+  Buf drow, dt, dh, dl, z[5], pbuf, wh, wl, rinv, sinv;  // z[4]: accelerated solves' base
+  Buf smp;                          // sampled product entries (error estimate)
   Buf acx_d, acx_acc, acx_sigma;    // ACX: d of the inner evaluations, step-length sums, steps
   Buf damp;                         // learned damping: history, features, alphas, state
   Buf bmeta, bscratch;              // batched: schedule and offsets, per-CTA iterate pairs
@@ -119,6 +122,7 @@ struct Plan {
   bool staged;  // third Z buffer and stored-P buffer (base re-use)
   int product_kernel = IPT_PRODUCT_AUTO;  // tensor-core product kernel variant
   bool acx = false;  // four Z buffers (z, f, f^2, f^3) and the extrapolation scratch
+  bool acx_base = false;  // accelerated staged solve: fifth Z buffer (the base) and P_b
   bool damped = false;  // learned damping buffers
 };
 
@@ -128,7 +132,7 @@ ipt_status check_dense_args(ipt_handle* h, int64_t n, const void* M, int64_t ldm
   if (n < 1 || n > (1 << 20) || k < 1 || k > n || ldm < n || ldz < n) return IPT_INVALID_ARG;
   if (m_dtype != IPT_DTYPE_F64 && m_dtype != IPT_DTYPE_F32) return IPT_INVALID_ARG;
   if (z_dtype != IPT_DTYPE_F64 && z_dtype != IPT_DTYPE_F32) return IPT_INVALID_ARG;
-  if (prec < IPT_PREC_F64 || prec > IPT_PREC_FP16X3) return IPT_INVALID_ARG;
+  if (prec < IPT_PREC_F64 || prec > IPT_PREC_F32C) return IPT_INVALID_ARG;
   return IPT_OK;
 }
 
@@ -146,6 +150,10 @@ ipt_status alloc_dense(ipt_handle* h, const Plan& p) {
     CK(ensure(h->acx_acc, (size_t)p.kpad * 2 * 8));
     CK(ensure(h->damp, (size_t)p.kpad * (3 * 8 + 3 * 4 + 6 * 4 + 4) + 64));
   }
+  if (p.acx_base) {
+    CK(ensure(h->z[4], kn * ez));
+    CK(ensure(h->pbuf, kn * 4));
+  }
   if (p.acx) {
     CK(ensure(h->z[2], kn * ez));
     CK(ensure(h->z[3], kn * ez));
@@ -161,6 +169,7 @@ ipt_status alloc_dense(ipt_handle* h, const Plan& p) {
     CK(ensure(h->wl, kn * 2));
     CK(ensure(h->rinv, (size_t)p.npad * 4));
     CK(ensure(h->sinv, (size_t)p.kpad * 4));
+    CK(ensure(h->smp, (size_t)kSampleRows * p.kpad * 4));
   }
   CK(ensure(h->theta, (size_t)p.npad * 8));
   CK(ensure(h->thh, (size_t)p.npad * 4));
@@ -176,6 +185,21 @@ ipt_status alloc_dense(ipt_handle* h, const Plan& p) {
 }
 
 DevState* dst(ipt_handle* h) { return static_cast<DevState*>(h->st.p); }
+
+// Sampled rows of the product-error estimate: j_r = r * stride + stride / 2.
+inline int sample_stride(const Plan& p) { return p.npad / kSampleRows; }
+inline int sample_rows(const Plan& p) {
+  int r = 0;
+  for (int q = 0; q < kSampleRows; ++q) r += q * sample_stride(p) + sample_stride(p) / 2 < p.n;
+  return r;
+}
+void set_sampling(ipt_handle* h, const Plan& p, MapArgs<float>& a, bool on) {
+  a.psmp = on ? (float*)h->smp.p : nullptr;
+  a.smp_stride = sample_stride(p);
+  a.smp_off = sample_stride(p) / 2;
+  a.smp_kpad = p.kpad;
+}
+
 
 ipt_status status_from_flags(int flags) {
   if (flags & (FLAG_COL_RANGE | FLAG_COL_DUP | FLAG_ZERO_PIVOT | FLAG_CSR_INDEX))
@@ -255,8 +279,10 @@ ipt_status setup_dense(ipt_handle* h, const Plan& p, const void* M, int64_t ldm,
   }
   const size_t kn = (size_t)p.kpad * p.npad;
   const size_t ez = p.f64 ? 8 : 4;
-  // Z buffers 1.. receive F only at rows < n of columns < k: zero the rest once
-  for (int b = 1; b < (p.acx ? 4 : p.staged ? 3 : 2); ++b) {
+  // Z buffers receive F only at rows < n of columns < k: zero the rest once
+  // (buffer 0 too: with the deferred unit columns nothing else writes it before
+  // an evaluation stores F there, and later pre-passes read every row of a column)
+  for (int b = 0; b < (p.acx ? (p.acx_base ? 5 : 4) : p.staged ? 3 : 2); ++b) {
     if (p.npad > p.n)
       CK(cudaMemset2DAsync((char*)h->z[b].p + (size_t)p.n * ez, (size_t)p.npad * ez, 0,
                            (size_t)(p.npad - p.n) * ez, (size_t)p.kpad, s));
@@ -292,8 +318,8 @@ ipt_status setup_dense(ipt_handle* h, const Plan& p, const void* M, int64_t ldm,
 
 struct Timing {
   bool on = false;
-  double product_ms[2] = {0.0, 0.0};
-  int product_launches[2] = {0, 0};
+  double product_ms[3] = {0.0, 0.0, 0.0};  // 1-pass, 3-pass, compensated FP32
+  int product_launches[3] = {0, 0, 0};
   double prepass_ms = 0.0;
   double setup_ms = 0.0, finalize_ms = 0.0;
 };
@@ -316,7 +342,7 @@ int free_buffer(int cur, int base) { return zbuf_free(cur, base); }
 // receiving d (else the handle's), `ev` the four timing events (else the handle's).
 ipt_status evaluate(ipt_handle* h, const Plan& p, int cur, int base, int stage, int passes,
                     int rebase, Timing* tm, int out = -1, double* dv = nullptr,
-                    cudaEvent_t* ev = nullptr) {
+                    cudaEvent_t* ev = nullptr, int measure = 0) {
   cudaStream_t s = h->s;
   DevState* st = dst(h);
   const int nxt = out >= 0 ? out : free_buffer(cur, base);
@@ -360,12 +386,16 @@ ipt_status evaluate(ipt_handle* h, const Plan& p, int cur, int base, int stage, 
         CK(cudaEventRecord(ev[1], s));
         CK(cudaEventRecord(ev[2], s));
       }
-    } else if (stage == IPT_PREC_F32) {
+    } else if (stage == IPT_PREC_F32 || stage == IPT_PREC_F32C) {
+      // products of W = Z - E (base E, P_b = Delta E exact); the compensated one
+      // may store its P as the new base
       launch_prepass(h->drow.p, h->z[cur].p, 0, p.npad, (const int32_t*)h->icol.p, p.kpad,
                      dd, st, s);
       if (t) CK(cudaEventRecord(ev[1], s));
       if (t) CK(cudaEventRecord(ev[2], s));
-      launch_gemm_simt_f32((const float*)h->drow.p, a, p.npad, p.kpad, s);
+      a.Pout = rebase ? (float*)h->pbuf.p : nullptr;
+      launch_gemm_simt_f32((const float*)h->drow.p, a, p.npad, p.kpad,
+                           stage == IPT_PREC_F32C ? 1 : 0, s);
     } else {
       const float* zb = base >= 0 ? (const float*)h->z[base].p : nullptr;
       launch_prepass_tc((const float*)h->drow.p, (const float*)h->z[cur].p, zb, p.npad,
@@ -379,10 +409,18 @@ ipt_status evaluate(ipt_handle* h, const Plan& p, int cur, int base, int stage, 
       a.Pbase = base >= 0 ? (const float*)h->pbuf.p : (const float*)h->dt.p;
       a.pbase_by_icol = base >= 0 ? 0 : 1;
       a.Pout = rebase ? (float*)h->pbuf.p : nullptr;
+      set_sampling(h, p, a, measure != 0);
       if (t) CK(cudaEventRecord(ev[2], s));
       CK(launch_gemm_tc((const uint16_t*)h->dh.p, (const uint16_t*)h->dl.p,
                         (const uint16_t*)h->wh.p, (const uint16_t*)h->wl.p, a, p.npad, p.kpad,
                         passes, p.bf16 ? 1 : 0, p.product_kernel, s));
+      if (measure) {
+        launch_sample_exact((const float*)h->drow.p, (const float*)h->z[cur].p,
+                            (const int32_t*)h->icol.p, p.n, p.k, p.kpad, p.npad,
+                            (const float*)h->smp.p, sample_stride(p), sample_stride(p) / 2, st,
+                            DynZ{}, s);
+        h->launches += 1;
+      }
     }
   }
   CK(cudaGetLastError());
@@ -425,23 +463,29 @@ ipt_status evaluate_dyn(ipt_handle* h, const Plan& p, Timing* tm, cudaEvent_t* e
   for (int b = 0; b < 3; ++b) a.zsel[b] = (float*)h->z[b].p;
   a.pstore = p.staged ? (float*)h->pbuf.p : nullptr;
   a.dyn = 1;
+  set_sampling(h, p, a, true);  // stored only when the state asks for a sample
   // the pass count given here only sizes nothing: the kernel reads it from st
   CK(launch_gemm_tc((const uint16_t*)h->dh.p, (const uint16_t*)h->dl.p,
                     (const uint16_t*)h->wh.p, (const uint16_t*)h->wl.p, a, p.npad, p.kpad, 1,
                     p.bf16 ? 1 : 0, p.product_kernel, s));
+  launch_sample_exact((const float*)h->drow.p, nullptr, (const int32_t*)h->icol.p, p.n, p.k,
+                      p.kpad, p.npad, (const float*)h->smp.p, sample_stride(p),
+                      sample_stride(p) / 2, st, dz, s);
+  h->launches += 1;
   if (t) CK(cudaEventRecord(ev[3], s));
   h->launches += 2;
   return IPT_OK;
 }
 
 // After the stream is synchronised: add this evaluation's event times.
-void collect_timing(ipt_handle* h, int passes, Timing* tm, const cudaEvent_t* ev = nullptr) {
+void collect_timing(ipt_handle* h, int passes, Timing* tm, const cudaEvent_t* ev = nullptr,
+                    int stage = -1) {
   if (!tm || !tm->on) return;
   if (!ev) ev = h->ev;
   float a = 0.f, b = 0.f;
   if (cudaEventElapsedTime(&a, ev[0], ev[1]) == cudaSuccess) tm->prepass_ms += a;
   if (passes == 0) return;
-  const int slot = passes == 3 ? 1 : 0;
+  const int slot = stage == IPT_PREC_F32C ? 2 : (passes == 3 ? 1 : 0);
   if (cudaEventElapsedTime(&b, ev[2], ev[3]) == cudaSuccess) tm->product_ms[slot] += b;
   tm->product_launches[slot] += 1;
 }
@@ -454,6 +498,9 @@ void fill_result(const DevState& hs, const Timing& tm, int launches, ipt_result*
     out->product_launches[i] = tm.product_launches[i];
     out->product_ms[i] = tm.product_ms[i];
   }
+  out->acc_launches = tm.product_launches[2];
+  out->acc_ms = tm.product_ms[2];
+  out->rho_error = hs.e_rel;
   out->prepass_ms = tm.prepass_ms;
   out->status = hs.status;
   out->iterations = hs.iter;
@@ -509,6 +556,28 @@ Plan make_plan(int64_t n, int64_t k, int prec, bool staged_bf16) {
   return p;
 }
 
+// Unit errors of the product kinds, relative to ||Delta V|| (see k_control),
+// for sums of length K = npad.  1-pass 16-bit: the operands' rounding (2^-11
+// each for FP16, 2^-8 for BF16), taken as 2^-10 / 2^-7.  Split x3: the tensor
+// core's FP32 accumulation, which drops low bits at each accumulate so its
+// error grows with the K/16 accumulates of a pass: measured at n = 4096 and
+// 8192 from 0.015 (K/16) 2^-24 (random-sign terms, the far K blocks first) to
+// 0.66 (K/16) 2^-24 (the paper's U[0,1] family, whose sums grow coherently),
+// taken at the upper end; for BF16 also the ~2^-16 of the split operands.
+// FP32 SIMT: sequential FMA sums, 0.1-0.6 sqrt(K) 2^-24 measured, taken as
+// 1.2.  Compensated FP32: one 32-long FP32 partial plus the pair's rounding.
+// FP32 iterate arithmetic: 2^-23 of ||R0|| + ||Delta W||.
+void set_error_model(ControlArgs& ca, const Plan& p) {
+  const double K = (double)p.npad, u24 = ldexp(1.0, -24);
+  ca.u_low = p.bf16 ? ldexp(1.0, -7) : ldexp(1.0, -10);
+  ca.u_high = std::max(p.bf16 ? ldexp(1.0, -15) : ldexp(1.0, -20),
+                       kSplitAccum * (K / 16.0) * u24);
+  ca.u_f32 = 1.2 * sqrt(K) * u24;
+  ca.u_acc = (0.6 * sqrt(32.0) + 2.0) * u24;
+  ca.e_arith = p.f64 ? ldexp(1.0, -51) : ldexp(1.0, -23);
+  ca.guard = 1;
+}
+
 // IPT-ACX (Alg. 3 in place of the Picard update of Alg. 1/2).  Buffer 0
 // holds the extrapolated iterate z, buffers 1..3 hold f(z), f^2(z), f^3(z).
 // An extrapolation of order p evaluates F at z (with Alg. 3's stopping test;
@@ -516,6 +585,10 @@ Plan make_plan(int64_t n, int64_t k, int prec, bool staged_bf16) {
 // test), then moves z in place.  Orders 3, 2, 3, 2, ...  One host
 // synchronisation per extrapolation; every kernel returns at entry once the
 // controller has stopped.
+// Accelerated staged solves (p.acx_base): when the controller asks for it
+// (want_acc), the next tested evaluation runs the compensated FP32 product,
+// stores its P as the base product P_b and z is copied to buffer 4 as Z_b;
+// later split products are of V = Z - Z_b.
 ipt_status acx_loop(ipt_handle* h, const Plan& p, const ControlArgs& ca, const FirstEval& fe,
                     int max_iter, int sigma_global, Timing* tm) {
   cudaStream_t s = h->s;
@@ -523,21 +596,46 @@ ipt_status acx_loop(ipt_handle* h, const Plan& p, const ControlArgs& ca, const F
   const int split = (fe.stage == IPT_PREC_BF16X3 || fe.stage == IPT_PREC_FP16X3) ? 3 : 1;
   double* dinner = (double*)h->acx_d.p;
   CK(cudaMemsetAsync(h->acx_acc.p, 0, (size_t)p.kpad * 2 * 8, s));
-  int done_evals = 0;
+  const size_t zbytes = (size_t)p.kpad * p.npad * (p.f64 ? 8 : 4);
+  int done_evals = 0, base = -1;
+  bool acc_next = false;
+  double last_rho = 1.0;  // the last tested residual (sampling starts near tol)
+  int stg_of[3] = {0, 0, 0}, passes_of[3] = {0, 0, 0};
   for (int step = 0; done_evals < max_iter; ++step) {
     const int order = (step % 2 == 0) ? 3 : 2;
     const int planned = std::min(order, max_iter - done_evals);
     for (int q = 0; q < planned; ++q) {
-      const int passes = (done_evals + q == 0) ? fe.passes : (p.f64 ? 1 : split);
+      int stg = fe.stage, passes = (done_evals + q == 0) ? fe.passes : (p.f64 ? 1 : split);
+      int eb = base, rebase = 0;
+      if (q == 0 && acc_next && p.acx_base) {
+        stg = IPT_PREC_F32C;
+        passes = 1;
+        eb = -1;
+        rebase = 1;
+      }
+      stg_of[q] = stg;
+      passes_of[q] = passes;
+      // tested tensor-core evaluations near tol sample their product error
+      const int meas = (q == 0 && p.tc && passes > 0 && stg != IPT_PREC_F32C &&
+                        last_rho <= 100.0 * ca.tol) ? 1 : 0;
       ControlArgs cq = ca;
       cq.acx = 1;
       cq.test = q == 0 ? 1 : 0;
-      ipt_status v = evaluate(h, p, q, -1, fe.stage, passes, 0, tm, q + 1,
+      cq.host_base = eb;
+      cq.host_rebase = rebase;
+      cq.host_stage = stg;
+      cq.host_passes = passes;
+      cq.host_measure = meas;
+      ipt_status v = evaluate(h, p, q, eb, stg, passes, rebase, tm, q + 1,
                               q == 0 ? nullptr : dinner + (size_t)(q - 1) * p.kpad,
-                              h->evb + 4 * q);
+                              h->evb + 4 * q, meas);
       if (v != IPT_OK) return v;
       launch_control(st, cq, s);
       h->launches += 1;
+      if (rebase) {  // Z_b = z (buffer 0 is not moved before the extrapolation)
+        CK(cudaMemcpyAsync(h->z[4].p, h->z[0].p, zbytes, cudaMemcpyDeviceToDevice, s));
+        base = 4;
+      }
     }
     if (planned == order) {
       launch_acx_combine(h->z[0].p, h->z[1].p, h->z[2].p, h->z[order == 3 ? 3 : 2].p,
@@ -558,13 +656,12 @@ ipt_status acx_loop(ipt_handle* h, const Plan& p, const ControlArgs& ca, const F
       }
     }
     const int ran = std::min(planned, h->hst->iter - done_evals);
-    for (int q = 0; q < ran; ++q) {
-      const int passes = (done_evals + q == 0) ? fe.passes : (p.f64 ? 1 : split);
-      collect_timing(h, passes, tm, h->evb + 4 * q);
-    }
+    for (int q = 0; q < ran; ++q) collect_timing(h, passes_of[q], tm, h->evb + 4 * q, stg_of[q]);
     done_evals = h->hst->iter;
     if (h->hst->timeout) return IPT_DEVICE_TIMEOUT;
     if (h->hst->done) break;
+    acc_next = p.acx_base && h->hst->want_acc;
+    last_rho = h->hst->rho;
   }
   return IPT_OK;
 }
@@ -573,17 +670,30 @@ ipt_status acx_loop(ipt_handle* h, const Plan& p, const ControlArgs& ca, const F
 // the first evaluation as planned by the host, then evaluations with
 // device-chosen operands, kDenseChunk per host synchronisation (every kernel
 // returns at entry once the controller has stopped, so the evaluations
-// enqueued past the stop cost only their launches).
-ipt_status dense_chunked_loop(ipt_handle* h, const Plan& p, const ControlArgs& ca,
+// enqueued past the stop cost only their launches).  When the controller
+// chooses a compensated FP32 re-base, which the enqueued tensor-core kernels
+// cannot run, it pauses them; the host then runs that evaluation itself and
+// goes on.
+ipt_status dense_chunked_loop(ipt_handle* h, const Plan& p, const ControlArgs& ca_in,
                               const FirstEval& fe, int max_iter, Timing* tm) {
   cudaStream_t s = h->s;
   DevState* st = dst(h);
   const bool t = tm && tm->on;
-  for (int it0 = 0; it0 < max_iter; it0 += kDenseChunk) {
-    const int nb = std::min(kDenseChunk, max_iter - it0);
+  ControlArgs ca = ca_in;
+  ca.pause_on_acc = 1;
+  int done_evals = 0;
+  bool first = true;
+  auto sync_state = [&]() -> bool {
+    return cudaGetLastError() == cudaSuccess &&
+           cudaMemcpyAsync(h->hst, st, t ? sizeof(DevState) : kStateHead,
+                           cudaMemcpyDeviceToHost, s) == cudaSuccess &&
+           cudaStreamSynchronize(s) == cudaSuccess;
+  };
+  while (done_evals < max_iter) {
+    const int nb = std::min(kDenseChunk, max_iter - done_evals);
     for (int q = 0; q < nb; ++q) {
       cudaEvent_t* ev = h->evb + 4 * q;
-      const ipt_status v = it0 + q == 0
+      const ipt_status v = (first && q == 0)
                                ? evaluate(h, p, 0, -1, fe.stage, fe.passes, fe.rebase, tm, -1,
                                           nullptr, ev)
                                : evaluate_dyn(h, p, tm, ev);
@@ -592,12 +702,8 @@ ipt_status dense_chunked_loop(ipt_handle* h, const Plan& p, const ControlArgs& c
       h->launches += 1;
     }
     // with timing, the stage history tells each evaluation's pass count
-    if (cudaGetLastError() != cudaSuccess ||
-        cudaMemcpyAsync(h->hst, st, t ? sizeof(DevState) : kStateHead, cudaMemcpyDeviceToHost,
-                        s) != cudaSuccess ||
-        cudaStreamSynchronize(s) != cudaSuccess)
-      return IPT_CUDA_ERROR;
-    if (it0 == 0) {
+    if (!sync_state()) return IPT_CUDA_ERROR;
+    if (first) {
       const ipt_status fv = status_from_flags(h->hst->flags);
       if (fv != IPT_OK) return fv;
       if (t) {
@@ -605,18 +711,34 @@ ipt_status dense_chunked_loop(ipt_handle* h, const Plan& p, const ControlArgs& c
         if (cudaEventElapsedTime(&ms, h->ev[4], h->ev[5]) == cudaSuccess) tm->setup_ms = ms;
       }
     }
+    first = false;
     if (t) {
-      const int ran = std::min(nb, h->hst->iter - it0);
+      const int ran = std::min(nb, h->hst->iter - done_evals);
       for (int q = 0; q < ran; ++q) {
-        const int e = it0 + q;
+        const int e = done_evals + q;
         const int stg = e < IPT_MAX_HISTORY ? h->hst->hist_stage[e] : p.prec;
         const int passes =
             stg < 0 ? 0 : ((stg == IPT_PREC_BF16X3 || stg == IPT_PREC_FP16X3) ? 3 : 1);
         collect_timing(h, passes, tm, h->evb + 4 * q);
       }
     }
+    done_evals = h->hst->iter;
     if (h->hst->timeout) return IPT_DEVICE_TIMEOUT;
     if (h->hst->done) break;
+    if (h->hst->pause) {
+      CK(cudaMemsetAsync(&st->pause, 0, sizeof(int), s));
+      const int stg = h->hst->stage;
+      const ipt_status v = evaluate(h, p, h->hst->cur, h->hst->base, stg, h->hst->passes,
+                                    h->hst->rebase, tm, -1, nullptr, h->ev);
+      if (v != IPT_OK) return v;
+      launch_control(st, ca, s);
+      h->launches += 1;
+      if (!sync_state()) return IPT_CUDA_ERROR;
+      collect_timing(h, 1, tm, h->ev, stg);
+      done_evals = h->hst->iter;
+      if (h->hst->timeout) return IPT_DEVICE_TIMEOUT;
+      if (h->hst->done) break;
+    }
   }
   return IPT_OK;
 }
@@ -625,7 +747,8 @@ ipt_status dense_chunked_loop(ipt_handle* h, const Plan& p, const ControlArgs& c
 // test, (zp, gp) the previous iterate and its map value, fr receives this
 // evaluation's map value.  The first step is a Picard step, so z_1 = g_0 stays
 // where g_0 was written (zc = gp); later steps write z_{t+1} over z_{t-1}.  One
-// host synchronisation per evaluation.
+// host synchronisation per evaluation.  Accelerated staged solves re-base as in
+// acx_loop (Z_b in buffer 4).
 ipt_status anderson_loop(ipt_handle* h, const Plan& p, const ControlArgs& ca,
                          const FirstEval& fe, int max_iter, Timing* tm) {
   cudaStream_t s = h->s;
@@ -637,14 +760,36 @@ ipt_status anderson_loop(ipt_handle* h, const Plan& p, const ControlArgs& ca,
   CK(cudaMemsetAsync(acc, 0, (size_t)p.kpad * 2 * 8, s));
   CK(cudaMemsetAsync(as, 0, sizeof(AndState), s));
   int zc = 0, zp = -1, gp = -1, fr = 1;
+  const size_t zbytes = (size_t)p.kpad * p.npad * (p.f64 ? 8 : 4);
+  int base = -1;
+  bool acc_next = false;
+  double last_rho = 1.0;
   for (int it = 0; it < max_iter; ++it) {
-    const int passes = it == 0 ? fe.passes : (p.f64 ? 1 : split);
+    int stg = fe.stage, passes = it == 0 ? fe.passes : (p.f64 ? 1 : split);
+    int eb = base, rebase = 0;
+    if (acc_next) {
+      stg = IPT_PREC_F32C;
+      passes = 1;
+      eb = -1;
+      rebase = 1;
+    }
     ControlArgs cq = ca;
     cq.acx = 1;
     cq.next_cur = it == 0 ? fr : zp;  // where the next iterate will be
-    ipt_status v = evaluate(h, p, zc, -1, fe.stage, passes, 0, tm, fr);
+    const int meas =
+        (p.tc && passes > 0 && stg != IPT_PREC_F32C && last_rho <= 100.0 * ca.tol) ? 1 : 0;
+    cq.host_base = eb;
+    cq.host_rebase = rebase;
+    cq.host_stage = stg;
+    cq.host_passes = passes;
+    cq.host_measure = meas;
+    ipt_status v = evaluate(h, p, zc, eb, stg, passes, rebase, tm, fr, nullptr, nullptr, meas);
     if (v != IPT_OK) return v;
     launch_control(st, cq, s);
+    if (rebase) {
+      CK(cudaMemcpyAsync(h->z[4].p, h->z[zc].p, zbytes, cudaMemcpyDeviceToDevice, s));
+      base = 4;
+    }
     CK(launch_anderson_step(h->z[zc].p, h->z[fr].p, it ? h->z[zp].p : nullptr,
                             it ? h->z[gp].p : nullptr, it ? h->z[zp].p : nullptr,
                             p.f64 ? 1 : 0, p.n, p.k, p.npad, acc, gamma, as, st, it == 0, s));
@@ -660,9 +805,11 @@ ipt_status anderson_loop(ipt_handle* h, const Plan& p, const ControlArgs& ca,
         if (cudaEventElapsedTime(&ms, h->ev[4], h->ev[5]) == cudaSuccess) tm->setup_ms = ms;
       }
     }
-    collect_timing(h, passes, tm);
+    collect_timing(h, passes, tm, nullptr, stg);
     if (h->hst->timeout) return IPT_DEVICE_TIMEOUT;
     if (h->hst->done) break;
+    acc_next = p.acx_base && h->hst->want_acc;
+    last_rho = h->hst->rho;
     if (it == 0) {
       zp = zc;
       gp = fr;
@@ -717,14 +864,17 @@ ipt_status solve_dense(ipt_handle* h, int64_t n, const void* M, int64_t ldm, int
   const bool damped = opt.accel == IPT_ACCEL_DAMPED;
   const bool anderson = opt.accel == IPT_ACCEL_ANDERSON;
   // ACX and Anderson mixing move the iterate by extrapolation, outside the
-  // staged schedule's error model: a staged request runs every product as the
-  // split stage.  (Damped steps stay inside it with a step bound of 2 increments.)
-  const int prec = ((acx || anderson) && opt.precision == IPT_PREC_STAGED)
-                       ? (opt.staged_bf16 ? IPT_PREC_BF16X3 : IPT_PREC_FP16X3)
-                       : opt.precision;
+  // staged schedule's step model: a staged request runs the split products,
+  // first of W = Z - E and, once their error model asks for it, of Z minus a
+  // base stored by one compensated FP32 evaluation.  (Damped steps stay inside
+  // the staged schedule with a step bound of 2 increments.)
+  const bool accel_staged = (acx || anderson) && opt.precision == IPT_PREC_STAGED;
+  const int prec = accel_staged ? (opt.staged_bf16 ? IPT_PREC_BF16X3 : IPT_PREC_FP16X3)
+                                : opt.precision;
   Plan p = make_plan(n, k, prec, opt.staged_bf16 != 0);
   p.product_kernel = opt.product_kernel;
   p.acx = acx || anderson;  // four iterate buffers and the per-column scratch
+  p.acx_base = accel_staged;
   p.damped = damped;
   const int low = p.bf16 ? IPT_PREC_BF16 : IPT_PREC_FP16;
   const int high = p.bf16 ? IPT_PREC_BF16X3 : IPT_PREC_FP16X3;
@@ -759,7 +909,14 @@ ipt_status solve_dense(ipt_handle* h, int64_t n, const void* M, int64_t ldm, int
   ca.k = (int)k;
   ca.low_stage = low;
   ca.high_stage = high;
-  ca.low_unit = p.bf16 ? 1.0 / 128.0 : 1.0 / 1024.0;  // 2^-7 (BF16), 2^-10 (FP16)
+  set_error_model(ca, p);
+  ca.escalate = p.staged ? 1 : 0;
+  ca.accel_staged = accel_staged ? 1 : 0;
+  ca.smp_rows = p.tc ? sample_rows(p) : 0;
+  ca.n_rows = p.n;
+  // fixed-precision tensor-core Picard solves sample the product error of the
+  // evaluations that may end the solve
+  ca.measure_below = (p.tc && !p.staged && !acx && !anderson) ? 3.0 * tol : 0.0;
   cudaStream_t s = h->s;
   int cur = 0, base = -1, stage = fe.stage, passes = fe.passes, rebase = fe.rebase;
   if (acx) {
@@ -812,7 +969,8 @@ ipt_status solve_dense(ipt_handle* h, int64_t n, const void* M, int64_t ldm, int
       copied_it = it;
     }
     const int fbuf = free_buffer(cur, base);  // where this evaluation writes F
-    v = evaluate(h, p, cur, base, stage, passes, rebase, &tm);
+    v = evaluate(h, p, cur, base, stage, passes, rebase, &tm, -1, nullptr, nullptr,
+                 it > 0 && p.tc ? h->hst->measure : 0);
     if (v != IPT_OK) break;
     launch_control(dst(h), ca, s);
     h->launches += 1;
@@ -943,6 +1101,7 @@ const char* ipt_status_string(int status) {
     case IPT_CUDA_ERROR: return "IPT_CUDA_ERROR";
     case IPT_DEVICE_TIMEOUT: return "IPT_DEVICE_TIMEOUT";
     case IPT_UNSUPPORTED: return "IPT_UNSUPPORTED";
+    case IPT_INACCURATE: return "IPT_INACCURATE";
     default: return "IPT_UNKNOWN_STATUS";
   }
 }
@@ -1054,7 +1213,7 @@ ipt_status ipt_solve_dense_host(ipt_handle* h, int64_t n, const void* M, int64_t
   }
   v = solve_dense(h, n, h->hM.p, n, m_dtype, dth, k, dcols, tol, max_iter, &o,
                   (double*)h->hLam.p, h->hZ.p, n, z_dtype, out, direct ? &ho : nullptr);
-  if (v == IPT_OK || v == IPT_MAXITER || v == IPT_DIVERGED) {
+  if (v == IPT_OK || v == IPT_MAXITER || v == IPT_DIVERGED || v == IPT_INACCURATE) {
     CK(cudaMemcpyAsync(lambda, h->hLam.p, (size_t)k * 8, cudaMemcpyDeviceToHost, s));
     if (!direct)
       CK(cudaMemcpy2DAsync(Z, ldz * ez, h->hZ.p, n * ez, n * ez, k, cudaMemcpyDeviceToHost, s));
@@ -1122,10 +1281,15 @@ ipt_status ipt_solve_csr(ipt_handle* h, int64_t n, int64_t nnz, const int32_t* r
       ldz < n || !(tol >= 0.0) || max_iter < 1 ||
       (v_dtype != IPT_DTYPE_F64 && v_dtype != IPT_DTYPE_F32) ||
       (z_dtype != IPT_DTYPE_F64 && z_dtype != IPT_DTYPE_F32) ||
-      (opt.stop != IPT_STOP_INCREMENT && opt.stop != IPT_STOP_RESIDUAL) || opt.z0)
+      (opt.stop != IPT_STOP_INCREMENT && opt.stop != IPT_STOP_RESIDUAL) || opt.z0 ||
+      opt.accel < IPT_ACCEL_NONE || opt.accel > IPT_ACCEL_ANDERSON ||
+      (opt.acx_sigma != 0 && opt.acx_sigma != 1))
     v = IPT_INVALID_ARG;
   int prec = opt.precision == IPT_PREC_STAGED ? IPT_PREC_F32 : opt.precision;
   if (v == IPT_OK && prec != IPT_PREC_F32 && prec != IPT_PREC_F64) v = IPT_UNSUPPORTED;
+  if (v == IPT_OK && opt.accel != IPT_ACCEL_NONE && opt.accel != IPT_ACCEL_ACX)
+    v = IPT_UNSUPPORTED;
+  const bool acx = opt.accel == IPT_ACCEL_ACX;
   if (v != IPT_OK) {
     out->status = v;
     return v;
@@ -1148,6 +1312,13 @@ ipt_status ipt_solve_csr(ipt_handle* h, int64_t n, int64_t nnz, const int32_t* r
   const int nblk = (nsm > 0 ? nsm : 148) * 8;
   CK(ensure(h->z[0], nk * ez));
   CK(ensure(h->z[1], nk * ez));
+  if (acx) {  // f^2(z), f^3(z), the inner evaluations' d and the step lengths
+    CK(ensure(h->z[2], nk * ez));
+    CK(ensure(h->z[3], nk * ez));
+    CK(ensure(h->acx_d, (size_t)kk * 2 * 8));
+    CK(ensure(h->acx_acc, (size_t)kk * 2 * 8));
+    CK(ensure(h->acx_sigma, (size_t)kk * 8));
+  }
   CK(ensure(h->theta, (size_t)n * 8));
   CK(ensure(h->thh, (size_t)n * 4));
   CK(ensure(h->thl, (size_t)n * 4));
@@ -1187,6 +1358,11 @@ ipt_status ipt_solve_csr(ipt_handle* h, int64_t n, int64_t nnz, const int32_t* r
     if (clr_hi > clr_lo)
       CK(cudaMemsetAsync((char*)h->z[b].p + clr_lo * row_bytes, 0, (clr_hi - clr_lo) * row_bytes,
                          s));
+  if (acx) {  // buffers 2 and 3 are written only inside the windows of this solve
+    CK(cudaMemsetAsync(h->z[2].p, 0, nk * ez, s));
+    CK(cudaMemsetAsync(h->z[3].p, 0, nk * ez, s));
+    CK(cudaMemsetAsync(h->acx_acc.p, 0, (size_t)kk * 2 * 8, s));
+  }
   h->csr_n = -1;  // contents unknown until this solve ends
   CK(cudaMemsetAsync(h->count.p, 0, (size_t)n * 4, s));
   launch_validate(cols, ni, ki, kk, nullptr, (int32_t*)h->icol.p, (int*)h->count.p, st, s);
@@ -1207,13 +1383,73 @@ ipt_status ipt_solve_csr(ipt_handle* h, int64_t n, int64_t nnz, const int32_t* r
   ca.k = ki;
   ca.low_stage = prec;
   ca.high_stage = prec;
-  ca.low_unit = 0.0;
+  // error model: the SpMM's short FP32 row sums and the FP32 map arithmetic,
+  // together taken as 2^-22 of ||R0|| (FP64: 2^-51); the guard as for dense solves
+  ca.e_arith = f64 ? ldexp(1.0, -51) : ldexp(1.0, -22);
+  ca.guard = 1;
   ca.csr_n = ni;
   ca.csr_window = opt.csr_window ? 1 : 0;
+  // IPT-ACX (Alg. 3) on the sparse path: buffer 0 holds z, buffers 1..3 f(z),
+  // f^2(z), f^3(z) (row-major like the Picard iterates); an extrapolation of
+  // order p evaluates F at z (tested; d in the handle's d, so Lambda is z's) and
+  // at f(z) [, f^2(z)], then moves z in place over the window rows and widens
+  // the window by the band.  One host synchronisation per extrapolation.
+  for (int step = 0, done_evals = 0; acx && done_evals < max_iter; ++step) {
+    const int order = (step % 2 == 0) ? 3 : 2;
+    const int planned = std::min(order, max_iter - done_evals);
+    double* dinner = (double*)h->acx_d.p;
+    for (int q = 0; q < planned; ++q) {
+      double* dq = q == 0 ? (double*)h->d.p : dinner + (size_t)(q - 1) * kk;
+      if (tm.on) cudaEventRecord(h->evb[4 * q], s);
+      launch_csr_prepass(rowptr, colind, vals, v_dtype, (const double*)h->delta.p,
+                         (const int32_t*)h->icol.p, kk, h->z[q].p, f64 ? 1 : 0, dq, st, s);
+      if (tm.on) {
+        cudaEventRecord(h->evb[4 * q + 1], s);
+        cudaEventRecord(h->evb[4 * q + 2], s);
+      }
+      launch_csr_spmm_map(rowptr, colind, vals, v_dtype, (const double*)h->delta.p,
+                          (const double*)h->theta.p, (const float*)h->thh.p,
+                          (const float*)h->thl.p, (const int32_t*)h->icol.p, dq, ni, ki, kk,
+                          h->z[q].p, h->z[q + 1].p, f64 ? 1 : 0, nblk, st, s);
+      if (tm.on) cudaEventRecord(h->evb[4 * q + 3], s);
+      ControlArgs cq = ca;
+      cq.acx = 1;
+      cq.test = q == 0 ? 1 : 0;
+      launch_control(st, cq, s);
+      h->launches += 3;
+    }
+    if (planned == order) {
+      launch_acx_combine_rm(h->z[0].p, h->z[1].p, h->z[2].p, h->z[order == 3 ? 3 : 2].p,
+                            f64 ? 1 : 0, order, ni, ki, kk, opt.csr_window ? 1 : 0,
+                            opt.acx_sigma, (double*)h->acx_acc.p, (double*)h->acx_sigma.p, st,
+                            nblk / 2, s);
+      h->launches += opt.csr_window ? 4 : 3;
+    }
+    if (cudaGetLastError() != cudaSuccess ||
+        cudaMemcpyAsync(h->hst, st, kStateHead, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+      v = IPT_CUDA_ERROR;
+      break;
+    }
+    if (step == 0) {
+      v = status_from_flags(h->hst->flags);
+      if (v != IPT_OK) break;
+      if (tm.on) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, h->ev[4], h->ev[5]) == cudaSuccess) tm.setup_ms = ms;
+      }
+    }
+    if (tm.on) {
+      const int ran = std::min(planned, h->hst->iter - done_evals);
+      for (int q = 0; q < ran; ++q) collect_timing(h, 1, &tm, h->evb + 4 * q);
+    }
+    done_evals = h->hst->iter;
+    if (h->hst->done) break;
+  }
   // Evaluations are enqueued kCsrChunk at a time with one host sync per chunk:
   // every kernel returns at entry once the controller has stopped, and with
   // two Z buffers the iterate alternates (evaluation i reads buffer i & 1).
-  for (int it0 = 0; it0 < max_iter; it0 += kCsrChunk) {
+  for (int it0 = 0; !acx && it0 < max_iter; it0 += kCsrChunk) {
     const int nb = std::min(kCsrChunk, max_iter - it0);
     for (int q = 0; q < nb; ++q) {
       const int cur = (it0 + q) & 1;
@@ -1304,6 +1540,20 @@ ipt_status ipt_solve_csr(ipt_handle* h, int64_t n, int64_t nnz, const int32_t* r
   fill_result(hs, tm, h->launches, out);
   out->wall_ms =
       std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+  if (opt.verify_fp64) {
+    // ||M Z - Z Lambda||_F of the returned pair in FP64, over all rows
+    CK(ensure(h->racc, 8));
+    CK(cudaMemsetAsync(h->racc.p, 0, 8, s));
+    launch_csr_residual64(rowptr, colind, vals, v_dtype, ni, ki, kk, h->z[hs.answer].p,
+                          f64 ? 1 : 0, lambda, (double*)h->racc.p, s);
+    h->launches += 1;
+    double r2 = 0.0;
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(&r2, h->racc.p, 8, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    out->rho_fp64 = hs.r0acc > 0.0 ? sqrt(r2) / sqrt(hs.r0acc) : 0.0;
+    out->kernel_launches = h->launches;
+  }
   return (ipt_status)out->status;
 }
 
@@ -1531,6 +1781,15 @@ ipt_status ipt_check_bounded_wait(int arrive, double limit_s, void* stream, int3
   *succeeded = (int32_t)hv[0];
   if (waited_s) *waited_s = (double)hv[1] * 1e-9;
   return IPT_OK;
+}
+
+ipt_status ipt_check_map_division(int64_t count, const float* gap, const float* u,
+                                  float* quotient, void* stream) {
+  if (count < 0 || (count > 0 && (!gap || !u || !quotient))) return IPT_INVALID_ARG;
+  return launch_recip_check(count, gap, u, quotient, static_cast<cudaStream_t>(stream)) ==
+                 cudaSuccess
+             ? IPT_OK
+             : IPT_CUDA_ERROR;
 }
 
 ipt_status ipt_set_batched_tiles(ipt_handle* h, const int32_t* tiles) {

@@ -47,6 +47,20 @@ struct DevState {
   double inc, rho, prev_rho;
   double kappa;     // ||Delta V|| / ||V|| of the last product (staged schedule)
   double sv;        // bound on ||Z - Z_base|| of the current iterate (staged schedule)
+  // Error model of the products (absolute, in the units of ||R||):
+  double e_base;    // predicted error of the stored base product P_b (0 for Z_b = E)
+  double pw_base;   // bound on ||Delta (Z_b - E)|| of the base iterate
+  double e_rel;     // predicted |rho - rho_true| of the last tested evaluation
+  double rho_best;  // smallest residual of a tested evaluation so far (0: none yet)
+  int acc_based;    // the current base came from a compensated FP32 product
+  int pause;   // nonzero: the next evaluation needs a kernel the enqueued ones do not
+               // run (compensated FP32); enqueued kernels return at entry until cleared
+  int want_acc;  // accelerated staged solves: the next tested evaluation should re-base
+                 // on a compensated FP32 product
+  int measure;   // the next evaluation samples its product error (k_sample_exact)
+  double acc_dp2;  // sum of squared product errors at the sampled entries
+  double acc_dpn;  // number of sampled entries
+  double e_meas;   // the last sampled estimate of ||P - Delta Z||_F (safety included)
   int done;    // nonzero: stop; every later kernel of the solve returns at entry
   int status;  // ipt_status once done
   int stage;   // ipt_precision of the next evaluation
@@ -93,6 +107,12 @@ struct MapArgs {
   int64_t ld;            // npad
   int n, k;
   DevState* st;
+  // Sampled product error: with psmp set (and, with dyn, the state's measure
+  // flag), the epilogue stores P at the rows j = r * smp_stride + smp_off,
+  // r < kSampleRows, into psmp[r * kpad + c]; k_sample_exact compares them with
+  // compensated FP32 dot products.
+  float* psmp;
+  int smp_stride, smp_off, smp_kpad;
   // Device-chosen operands (tensor-core evaluations enqueued ahead of the
   // host): with dyn set, the kernels take the iterate zsel[cur], write F into
   // zsel[zbuf_free(cur, base)], read P_b from pstore (base >= 0) or DT by
@@ -117,6 +137,9 @@ __host__ __device__ inline int zbuf_free(int cur, int base) {
     if (b != cur && b != base) return b;
   return 0;
 }
+
+// Rows of each product whose entries are recomputed to estimate its error.
+constexpr int kSampleRows = 16;
 
 // ---------------------------------------------------------------- launchers
 // setup (k_setup.cu)
@@ -152,15 +175,35 @@ void launch_map_first(const MapArgs<float>& a, int npad, int kpad, double* d, do
                       cudaStream_t s);
 void launch_gemm_simt_f64(const double* Drow, const MapArgs<double>& a, int npad, int kpad,
                           cudaStream_t s);
+// compensated != 0: two-level (FP32 partials of 32 products, TwoSum pairs) sums
 void launch_gemm_simt_f32(const float* Drow, const MapArgs<float>& a, int npad, int kpad,
-                          cudaStream_t s);
+                          int compensated, cudaStream_t s);
 void launch_residual_f64(const double* M64, const double* Z64, int64_t ld, const double* lam,
                          int n, int k, int npad, int kpad, double* acc, cudaStream_t s);
 struct ControlArgs {
   double tol, diverge_bound, stage_switch;  // stage_switch: safety fraction of the staged rule
   int max_iter, stop, mode, k;
   int low_stage, high_stage;  // STAGED: the 1-pass stage and the split stage it switches to
-  double low_unit;            // STAGED: relative error model of a 1-pass product
+  // Error model: a product of V = Z - Z_b errs by about u * ||Delta V||, u per kind
+  // (1-pass 16-bit, 3-pass split 16-bit, FP32 SIMT, compensated FP32 SIMT); the
+  // FP32 (FP64) iterate arithmetic adds about e_arith * (||R0|| + ||Delta (Z - E)||).
+  double u_low = 0.0, u_high = 0.0, u_f32 = 0.0, u_acc = 0.0, e_arith = 0.0;
+  int guard = 0;        // residual stop: only rho + predicted error <= tol stops the solve
+  int escalate = 0;     // STAGED: re-base on a compensated FP32 product when the split
+                        // product's base error is what keeps the residual from tol
+  int pause_on_acc = 0; // STAGED, device-chosen operands: pause before such an evaluation
+  int accel_staged = 0; // accelerated staged solves: request that re-base (want_acc)
+  int host_base = -2;   // host-driven evaluations: the base this one used (-1: E), or -2
+                        // for the controller's own (staged Picard) base
+  int host_rebase = 0;  // with host_base >= -1: this evaluation stored its P as the base
+  int host_stage = -1;  // with host_base >= -1: the stage and pass count this one ran
+  int host_passes = -1;
+  int host_measure = -1;  // host-driven: 1 if this evaluation's product error was sampled
+                          // (k_sample_exact), 0 if not; -1: as the device state says
+  double measure_below = 0.0;  // non-staged solves: sample the next evaluation's product
+                               // error once rho is predicted below this (0: never)
+  int smp_rows = 0;  // sampled rows of the product error estimate (0: no sampling)
+  int n_rows = 0;    // n
   int csr_n = 0;              // CSR solves: n (the window is clipped to [0, n)); 0 = dense
   int csr_window = 0;         // CSR: nonzero = evaluate only rows that can be nonzero
   int acx = 0;                // ACX: the iterate stays in buffer 0 (no ping-pong)
@@ -180,6 +223,9 @@ cudaError_t launch_mlp_grad(const void* params, const float* X, const float* tar
 cudaError_t launch_mlp_adam(float* master, void* params, float* grad, float* m, float* v,
                             float lr, float b1, float b2, float eps, int step, cudaStream_t s);
 
+// The FP32 map's division (k_diag.cu): q[i] = u[i] * recip_nr(gap[i]).
+cudaError_t launch_recip_check(int64_t count, const float* gap, const float* u, float* q,
+                               cudaStream_t s);
 // Bounded-wait check (k_diag.cu): out[0] = 1 if the wait succeeded, out[1] = ns waited.
 cudaError_t launch_wait_check(int arrive, uint64_t limit_ns, long long* out, cudaStream_t s);
 
@@ -250,7 +296,22 @@ cudaError_t launch_batched_tc(const float* M, const double* theta, const int64_t
 void launch_acx_combine(void* z, const void* f1, const void* f2, const void* f3, int f64, int p,
                         int n, int k, int64_t ld, int global, double* acc, double* sigma,
                         DevState* st, cudaStream_t s);
+// The same for the sparse path's row-major n x kk iterates over the state's
+// window rows (blocks: persistent grid); with `window` the window is then
+// widened by the band (the extrapolated iterate's rows need it).
+void launch_acx_combine_rm(void* z, const void* f1, const void* f2, const void* f3, int f64,
+                           int p, int n, int k, int kk, int window, int global, double* acc,
+                           double* sigma, DevState* st, int blocks, cudaStream_t s);
 void launch_control(DevState* st, ControlArgs a, cudaStream_t s);
+
+// Sampled error of the product just computed (k_sample.cu): the exact
+// (compensated FP32) Delta Z at the sample rows of psmp against the stored P,
+// sum of squared differences into st->acc_dp2.  Z: the evaluation's iterate, or
+// with dz.dyn the state's current buffer (and nothing is done unless
+// st->measure).  Drow: FP32 row-major Delta.
+void launch_sample_exact(const float* Drow, const float* Z, const int32_t* icol, int n, int k,
+                         int kpad, int64_t ld, const float* psmp, int stride, int off,
+                         DevState* st, const DynZ& dz, cudaStream_t s);
 
 // tensor-core product (k_tc_gemm.cu).  passes = 1 (Dh Wh) or 3 (+ Dh Wl + Dl Wh);
 // bf16 selects BF16 operands, else FP16.  Returns a cudaError_t of the launch
@@ -276,6 +337,10 @@ void launch_csr_spmm_map(const int32_t* rowptr, const int32_t* colind, const voi
                          const float* th_hi, const float* th_lo, const int32_t* icol,
                          const double* d, int n, int k, int kk, const void* Zin, void* Fout,
                          int f64, int nblk, DevState* st, cudaStream_t s);
+// adds ||M Z - Z Lambda||_F^2 (FP64) of the row-major iterate to *acc
+void launch_csr_residual64(const int32_t* rowptr, const int32_t* colind, const void* vals,
+                           int v_dtype, int n, int k, int kk, const void* Z, int f64,
+                           const double* lam, double* acc, cudaStream_t s);
 // rows [j_lo, n) of the row-major iterate into the caller's column-major Z
 void launch_csr_out(const void* Z, int f64, int j_lo, int n, int k, int kk, void* out,
                     int64_t ldo, int out_f64, cudaStream_t s);

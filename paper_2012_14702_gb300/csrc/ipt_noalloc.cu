@@ -1,16 +1,15 @@
 // ipt_residual_dense_noalloc: the FP64 residual ||M Z - Z Lambda||_F computed
 // without any device allocation.
 //
-// Who needs this: code that must not call cudaMalloc -- work being recorded
-// by CUDA stream capture (an allocation there is not captured and may
-// invalidate the capture), processes whose device memory is owned by another
-// allocator (a framework's caching pool) that forbids side allocations, and
-// latency-critical loops where cudaMalloc / cudaFree would synchronise the
-// device.  The solver's own verification path converts M and Z into
-// handle-allocated FP64 copies and accumulates into an allocated scalar; this
-// variant reads the caller's M and Z in place (FP64 or FP32) and keeps its
-// only scratch -- one FP64 partial sum per thread block -- in a fixed-size
-// file-scope device array that lives as long as the library is loaded.
+// Who needs this: code that must not call cudaMalloc -- processes whose
+// device memory is owned by another allocator (a framework's caching pool, a
+// fixed memory budget) that forbids side allocations, and latency-critical
+// loops where cudaMalloc / cudaFree would synchronise the device.  The
+// solver's own verification path converts M and Z into handle-allocated FP64
+// copies and accumulates into an allocated scalar; this variant reads the
+// caller's M and Z in place (FP64 or FP32) and keeps its only scratch -- one
+// FP64 partial sum per thread block -- in a fixed-size file-scope device array
+// that lives as long as the library is loaded.
 #include <math.h>
 #include <mutex>
 
@@ -106,19 +105,52 @@ __global__ void k_residual_noalloc_final(const double* __restrict__ partials, in
   if (threadIdx.x == 0) *out = sqrt(red[0]);
 }
 
-// Device address of the scratch array, looked up once per device.
+// Device address of the scratch array, looked up once per device and CUDA
+// context (a cudaDeviceReset ends the context the cached address belongs to;
+// the next call sees a new context id and looks the address up again).
+typedef int (*CtxGetCurrentFn)(void**);
+typedef int (*CtxGetIdFn)(void*, unsigned long long*);
+
 std::mutex g_mu;
 double* g_ptr[64] = {};
+unsigned long long g_ctx[64] = {};
+
+// Id of the current context (0 if the driver cannot tell).
+unsigned long long current_context_id() {
+  static CtxGetCurrentFn get_cur = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  static bool looked_up = false;
+  if (!looked_up) {
+    void* a = nullptr;
+    void* b = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &a, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_cur = reinterpret_cast<CtxGetCurrentFn>(a);
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &b, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<CtxGetIdFn>(b);
+    looked_up = true;
+  }
+  void* ctx = nullptr;
+  unsigned long long id = 0;
+  if (get_cur && get_id && get_cur(&ctx) == 0 && ctx && get_id(ctx, &id) == 0) return id;
+  return 0;
+}
 
 ipt_status scratch_for_current_device(double** ptr) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return IPT_CUDA_ERROR;
   std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_ptr[dev]) {
+  const unsigned long long ctx = current_context_id();
+  if (!g_ptr[dev] || g_ctx[dev] != ctx) {
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_noalloc_partials) != cudaSuccess || !p)
       return IPT_CUDA_ERROR;
     g_ptr[dev] = static_cast<double*>(p);
+    g_ctx[dev] = ctx;
   }
   *ptr = g_ptr[dev];
   return IPT_OK;
@@ -137,6 +169,9 @@ extern "C" ipt_status ipt_residual_dense_noalloc(int64_t n, const void* M, int64
     return IPT_INVALID_ARG;
   const int64_t bx = (k + TILE - 1) / TILE, by = (n + TILE - 1) / TILE;
   if (bx * by > NOALLOC_MAX_BLOCKS) return IPT_UNSUPPORTED;  // beyond the fixed scratch
+  // an error left by earlier work stays the caller's to read: report it without
+  // launching and without clearing it
+  if (cudaPeekAtLastError() != cudaSuccess) return IPT_CUDA_ERROR;
   double* partials = nullptr;
   ipt_status st = scratch_for_current_device(&partials);
   if (st != IPT_OK) return st;

@@ -144,6 +144,76 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+// Row-major iterates of the sparse path (element (j, c) at j * kk + c): only
+// the rows of the state's window [win_lo, win_hi) are visited, every other row
+// being zero in all four buffers.  A persistent grid strides over the rows;
+// a thread owns one column of a 64-wide chunk and every fourth row.
+template <typename T>
+__global__ void __launch_bounds__(256)
+    k_acx_dots_rm(const T* __restrict__ z, const T* __restrict__ f1, const T* __restrict__ f2,
+                  const T* __restrict__ f3, int p, int k, int kk, double* __restrict__ acc,
+                  const DevState* st) {
+  if (st->done) return;
+  const int64_t lo = st->win_lo, hi = st->win_hi;
+  const int cl = threadIdx.x & 63, rq = threadIdx.x >> 6;
+  __shared__ T rn[4][64], rd[4][64];
+  for (int c0 = 0; c0 < kk; c0 += 64) {
+    const int c = c0 + cl;
+    T num = T(0), den = T(0);
+    if (c < k) {
+      for (int64_t j = lo + (int64_t)blockIdx.x * 4 + rq; j < hi; j += (int64_t)gridDim.x * 4) {
+        T d1, d2, d3;
+        differences(z, f1, f2, f3, j * kk + c, p, d1, d2, d3);
+        const T dp = p == 3 ? d3 : d2, dq = p == 3 ? d2 : d1;
+        num = fma(dp, dq, num);
+        den = fma(dp, dp, den);
+      }
+    }
+    rn[rq][cl] = num;
+    rd[rq][cl] = den;
+    __syncthreads();
+    if (rq == 0 && c < k) {
+      const T a = (rn[0][cl] + rn[1][cl]) + (rn[2][cl] + rn[3][cl]);
+      const T b = (rd[0][cl] + rd[1][cl]) + (rd[2][cl] + rd[3][cl]);
+      if (a != T(0)) atomicAdd(&acc[2 * c], (double)a);
+      if (b != T(0)) atomicAdd(&acc[2 * c + 1], (double)b);
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+    k_acx_update_rm(T* __restrict__ z, const T* __restrict__ f1, const T* __restrict__ f2,
+                    const T* __restrict__ f3, int p, int k, int kk,
+                    const double* __restrict__ sigma, const DevState* st) {
+  if (st->done) return;
+  const int64_t lo = st->win_lo, hi = st->win_hi;
+  const int cl = threadIdx.x & 63, rq = threadIdx.x >> 6;
+  for (int c0 = 0; c0 < kk; c0 += 64) {
+    const int c = c0 + cl;
+    if (c >= k) continue;
+    const T s = (T)sigma[c];
+    for (int64_t j = lo + (int64_t)blockIdx.x * 4 + rq; j < hi; j += (int64_t)gridDim.x * 4) {
+      T d1, d2, d3;
+      const int64_t o = j * kk + c;
+      differences(z, f1, f2, f3, o, p, d1, d2, d3);
+      const T x = z[o];
+      z[o] = p == 3 ? x + T(3) * s * d1 + T(3) * s * s * d2 + s * s * s * d3
+                    : x + T(2) * s * d1 + s * s * d2;
+    }
+  }
+}
+
+// After an extrapolation of the sparse path: the new iterate is nonzero only in
+// rows already evaluated, so the next product must cover them widened by the
+// band (the window only grows).
+__global__ void k_acx_widen(DevState* st, int n) {
+  if (st->done) return;
+  st->win_lo = max(0, st->win_lo - st->band);
+  st->win_hi = (int)min((int64_t)n, (int64_t)st->win_hi + st->band);
+}
+
 }  // namespace
 
 void launch_acx_combine(void* z, const void* f1, const void* f2, const void* f3, int f64, int p,
@@ -163,6 +233,28 @@ void launch_acx_combine(void* z, const void* f1, const void* f2, const void* f3,
     k_acx_update<float><<<g, 256, 0, s>>>((float*)z, (const float*)f1, (const float*)f2,
                                           (const float*)f3, p, n, ld, sigma, st);
   }
+}
+
+void launch_acx_combine_rm(void* z, const void* f1, const void* f2, const void* f3, int f64,
+                           int p, int n, int k, int kk, int window, int global, double* acc,
+                           double* sigma, DevState* st, int blocks, cudaStream_t s) {
+  if (f64) {
+    k_acx_dots_rm<double><<<blocks, 256, 0, s>>>((const double*)z, (const double*)f1,
+                                                 (const double*)f2, (const double*)f3, p, k, kk,
+                                                 acc, st);
+    k_acx_sigma<<<1, 1024, 0, s>>>(acc, k, global, sigma, st);
+    k_acx_update_rm<double><<<blocks, 256, 0, s>>>((double*)z, (const double*)f1,
+                                                   (const double*)f2, (const double*)f3, p, k,
+                                                   kk, sigma, st);
+  } else {
+    k_acx_dots_rm<float><<<blocks, 256, 0, s>>>((const float*)z, (const float*)f1,
+                                                (const float*)f2, (const float*)f3, p, k, kk,
+                                                acc, st);
+    k_acx_sigma<<<1, 1024, 0, s>>>(acc, k, global, sigma, st);
+    k_acx_update_rm<float><<<blocks, 256, 0, s>>>((float*)z, (const float*)f1, (const float*)f2,
+                                                  (const float*)f3, p, k, kk, sigma, st);
+  }
+  if (window) k_acx_widen<<<1, 1, 0, s>>>(st, n);
 }
 
 }  // namespace ipt

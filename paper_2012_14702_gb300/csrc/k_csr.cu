@@ -3,8 +3,9 @@
 //
 // Layout.  Internally Z is row-major n x kk (kk = k rounded up to 64), so the
 // gather Z[m, :] of one column index m is a single coalesced 64-wide read
-// (256 B in FP32).  One warp owns one row j of Delta at a time; lane l owns
-// the columns c = 64*chunk + 2l, 2l+1.  The diagonal of Delta,
+// (256 B in FP32).  In the SpMM a half-warp owns one row j of Delta at a time
+// and lane l of the half the columns c = 64*chunk + 4l .. 4l+3 (one 16-byte
+// gather per neighbour row).  The diagonal of Delta,
 // delta_j = M_jj - theta_j (0 when theta = diag(M)), is applied separately, so
 // the CSR loop skips stored diagonal entries.
 //
@@ -436,6 +437,54 @@ void launch_csr_out(const void* Z, int f64, int j_lo, int n, int k, int kk, void
   else
     k_csr_transpose_out<float, float><<<g, b, 0, s>>>((const float*)Z, j_lo, n, k, kk,
                                                       (float*)out, ldo);
+}
+
+namespace {
+
+// ||M Z - Z Lambda||_F^2 in FP64 (verification of a sparse result): the stored
+// entries of M (diagonal included) against the row-major iterate; one warp per
+// row, lane l the columns c = c0 + l of each 32-column chunk.
+template <typename T>
+__global__ void __launch_bounds__(256)
+    k_csr_residual64(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colind,
+                     const void* __restrict__ vals, int v_dtype, int n, int k, int kk,
+                     const T* __restrict__ Z, const double* __restrict__ lam,
+                     double* __restrict__ acc) {
+  const int lane = threadIdx.x & 31;
+  const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  double s = 0.0;
+  for (int64_t j = w0; j < n; j += nw) {
+    const int e0 = rowptr[j], e1 = rowptr[j + 1];
+    for (int c0 = 0; c0 < k; c0 += 32) {
+      const int c = c0 + lane;
+      if (c >= k) continue;
+      double a = 0.0;
+      for (int e = e0; e < e1; ++e) {
+        const double v = v_dtype == IPT_DTYPE_F64 ? static_cast<const double*>(vals)[e]
+                                                  : (double)static_cast<const float*>(vals)[e];
+        a = fma(v, (double)Z[(int64_t)colind[e] * kk + c], a);
+      }
+      const double r = a - (double)Z[j * kk + c] * lam[c];
+      s += r * r;
+    }
+  }
+  s = warp_sum(s);
+  if (lane == 0) atomicAdd(acc, s);
+}
+
+}  // namespace
+
+void launch_csr_residual64(const int32_t* rowptr, const int32_t* colind, const void* vals,
+                           int v_dtype, int n, int k, int kk, const void* Z, int f64,
+                           const double* lam, double* acc, cudaStream_t s) {
+  const int blocks = (int)std::min<int64_t>(((int64_t)n + 7) / 8, 152 * 16);
+  if (f64)
+    k_csr_residual64<double><<<blocks, 256, 0, s>>>(rowptr, colind, vals, v_dtype, n, k, kk,
+                                                    (const double*)Z, lam, acc);
+  else
+    k_csr_residual64<float><<<blocks, 256, 0, s>>>(rowptr, colind, vals, v_dtype, n, k, kk,
+                                                   (const float*)Z, lam, acc);
 }
 
 }  // namespace ipt

@@ -1,3 +1,5 @@
+// Checks of two device-side building blocks, without any fault or hang.
+//
 // Bounded-wait check: exercises the give-up path of the shared-memory barrier
 // wait that every waiting role of the tensor-core product kernel uses, without
 // any fault or hang.  One CTA; thread 0 initialises a barrier for one arrival
@@ -28,7 +30,22 @@ __global__ void k_wait_check(int arrive, uint64_t limit_ns, long long* out) {
   }
 }
 
+// The FP32 map's division u / gap as the epilogues compute it (u times the
+// refined reciprocal), one entry per thread.
+__global__ void k_recip_check(int64_t count, const float* __restrict__ gap,
+                              const float* __restrict__ u, float* __restrict__ q) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < count) q[i] = u[i] * recip_nr(gap[i]);
+}
+
 }  // namespace
+
+cudaError_t launch_recip_check(int64_t count, const float* gap, const float* u, float* q,
+                               cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  k_recip_check<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(count, gap, u, q);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_wait_check(int arrive, uint64_t limit_ns, long long* out, cudaStream_t s) {
   k_wait_check<<<1, 64, 0, s>>>(arrive, limit_ns, out);

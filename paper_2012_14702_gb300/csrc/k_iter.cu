@@ -91,7 +91,7 @@ __global__ void k_prepass_tc(const float* __restrict__ Drow, const float* __rest
                              double* __restrict__ d, uint16_t* __restrict__ Wh,
                              uint16_t* __restrict__ Wl, float* __restrict__ sinv,
                              const DevState* st, DynZ dz) {
-  if (st->done) return;
+  if (st->done || (dz.dyn && st->pause)) return;
   if (dz.dyn) {
     Z = dz.z[st->cur];
     Zbase = st->base >= 0 ? dz.z[st->base] : nullptr;
@@ -155,7 +155,7 @@ __global__ void __launch_bounds__(1024)
                      const int32_t* __restrict__ icol, double* __restrict__ d,
                      uint16_t* __restrict__ Wh, uint16_t* __restrict__ Wl,
                      float* __restrict__ sinv, const DevState* st, DynZ dz) {
-  if (st->done) return;
+  if (st->done || (dz.dyn && st->pause)) return;
   if (dz.dyn) {
     Z = dz.z[st->cur];
     Zbase = st->base >= 0 ? dz.z[st->base] : nullptr;
@@ -239,7 +239,14 @@ __global__ void __launch_bounds__(1024)
 // A = Delta row-major (lda = ld), B = Z column-major (K = rows contiguous).
 // FP32 (WFORM): B = W = Z - E (the unit entry is subtracted as the tile is
 // loaded) and the epilogue adds the exact column Delta_{., cols[c]} from the
-// column-major copy DT, so the FP32 accumulators carry only Delta W.
+// column-major copy DT, so the FP32 accumulators carry only Delta W; the
+// epilogue also sums ||Delta W||^2 (the product's error model) and stores P
+// when a.Pout is set (the evaluation becomes a base).
+// COMP > 0 (FP32 only): compensated sums.  Each output's FMAs run in a fresh
+// FP32 partial for COMP slabs of BK steps (COMP * BK products), and the
+// partials are added into an FP32 pair (hi, lo) by Knuth's TwoSum, so the
+// rounding error of the whole K-long sum is that of one COMP * BK-long
+// sequential sum plus the pair's ~2^-48, instead of a K-long one.
 enum { EPI_MAP = 0, EPI_RESIDUAL = 1 };
 
 template <typename T>
@@ -253,10 +260,11 @@ struct Vec<double> {
   using V4 = double2;  // 16-byte vector
 };
 
-template <typename T, int BM, int BN, int BK, int TM, int TN, int EPI>
+template <typename T, int BM, int BN, int BK, int TM, int TN, int EPI, int COMP = 0>
 __global__ void __launch_bounds__(256)
     k_gemm_simt(const T* __restrict__ A, MapArgs<T> a, const double* __restrict__ lam,
                 double* __restrict__ racc) {
+  static_assert(COMP == 0 || sizeof(T) == 4, "compensated sums are FP32 only");
   constexpr int HM = TM / 2, HN = TN / 2;
   constexpr int VEC = 16 / sizeof(T);          // elements per 16-byte load
   constexpr int LPR = BK / VEC;                // loads per tile row
@@ -281,6 +289,13 @@ __global__ void __launch_bounds__(256)
   for (int i = 0; i < TM; ++i)
 #pragma unroll
     for (int j = 0; j < TN; ++j) acc[i][j] = T(0);
+  // compensated sums: the pair (chi, clo) of each output (COMP > 0)
+  constexpr int CM = COMP ? TM : 1, CN = COMP ? TN : 1;
+  float chi[CM][CN], clo[CM][CN];
+#pragma unroll
+  for (int i = 0; i < CM; ++i)
+#pragma unroll
+    for (int j = 0; j < CN; ++j) chi[i][j] = clo[i][j] = 0.f;
 
   // column this thread loads, and the row of its unit entry (W-form)
   const int ic_load = WFORM ? a.icol[c0 + lr] : -1;
@@ -333,12 +348,28 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
         for (int j = 0; j < TN; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
     }
+    if constexpr (COMP > 0) {
+      if ((kt + 1) % COMP == 0 || kt + 1 == KT) {
+#pragma unroll
+        for (int i = 0; i < TM; ++i)
+#pragma unroll
+          for (int j = 0; j < TN; ++j) {
+            const float x = (float)acc[i][j], h0 = chi[i][j];
+            const float sm = __fadd_rn(h0, x);
+            const float bv = __fsub_rn(sm, h0);
+            const float er = __fadd_rn(__fsub_rn(h0, __fsub_rn(sm, bv)), __fsub_rn(x, bv));
+            chi[i][j] = sm;
+            clo[i][j] = __fadd_rn(clo[i][j], er);
+            acc[i][j] = T(0);
+          }
+      }
+    }
     if (kt + 1 < KT) stash(buf ^ 1);
     __syncthreads();
   }
 
   // ---------------- fused epilogue
-  T s_inc = T(0), s_z = T(0), s_r = T(0);
+  T s_inc = T(0), s_z = T(0), s_r = T(0), s_pv = T(0);
 #pragma unroll
   for (int jj = 0; jj < TN; ++jj) {
     const int c = c0 + (jj < HN ? tn * HN + jj : BN / 2 + tn * HN + (jj - HN));
@@ -367,8 +398,14 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
       for (int q = 0; q < HM; ++q) {
         const int j = jb + q;
-        T p = acc[h * HM + q][jj];
-        if constexpr (WFORM) p += dcol[q];
+        T p;
+        if constexpr (COMP > 0) p = __fadd_rn(chi[h * HM + q][jj], clo[h * HM + q][jj]);
+        else p = acc[h * HM + q][jj];
+        if constexpr (WFORM) {
+          s_pv += p * p;  // Delta W (zero in padding rows)
+          p += dcol[q];
+          if (a.Pout && j < a.n) a.Pout[o + q] = p;
+        }
         f[q] = z[q];
         if (j >= a.n) continue;
         if constexpr (EPI == EPI_MAP) {
@@ -395,28 +432,31 @@ __global__ void __launch_bounds__(256)
       }
     }
   }
-  // block reduction of the three partial sums
-  __shared__ double red[3][8];
+  // block reduction of the four partial sums
+  __shared__ double red[4][8];
   const double b_inc = warp_sum((double)s_inc), b_z = warp_sum((double)s_z),
-               b_r = warp_sum((double)s_r);
+               b_r = warp_sum((double)s_r), b_pv = warp_sum((double)s_pv);
   const int w = tid >> 5, l = tid & 31;
   if (l == 0) {
     red[0][w] = b_inc;
     red[1][w] = b_z;
     red[2][w] = b_r;
+    red[3][w] = b_pv;
   }
   __syncthreads();
   if (w == 0) {
     double x0 = l < 8 ? red[0][l] : 0.0, x1 = l < 8 ? red[1][l] : 0.0,
-           x2 = l < 8 ? red[2][l] : 0.0;
+           x2 = l < 8 ? red[2][l] : 0.0, x3 = l < 8 ? red[3][l] : 0.0;
     x0 = warp_sum(x0);
     x1 = warp_sum(x1);
     x2 = warp_sum(x2);
+    x3 = warp_sum(x3);
     if (l == 0) {
       if constexpr (EPI == EPI_MAP) {
         atomicAdd(&a.st->acc_inc2, x0);
         atomicAdd(&a.st->acc_z2, x1);
         atomicAdd(&a.st->acc_r2, x2);
+        if constexpr (WFORM) atomicAdd(&a.st->acc_pv2, x3);
       } else {
         atomicAdd(racc, x2);
       }
@@ -536,25 +576,41 @@ __global__ void __launch_bounds__(1024)
 // and iteration caps, records history, chooses the next evaluation and
 // clears the accumulators.
 //
-// Staged schedule.  Every tensor-core evaluation computes P = P_b + Delta V,
-// V = Z - Z_b, for a base (Z_b, P_b) whose product is known accurately
-// (first E with P_b = Delta E exactly).  A 1-pass product of V errs by about
-// low_unit * ||Delta V||; the controller predicts ||Delta V|| of the next
-// evaluation as kappa * (bound on ||V||) and uses the 1-pass product when that
-// error is below stage_switch (0.1) times the predicted next residual, or
-// below tol / 10;
-// otherwise the next evaluation uses the split product and stores its P as
-// the new base.  Only evaluations whose predicted product error is below a
-// tenth of tol may declare convergence.
+// Error model.  Every product is P = P_b + Delta V with V = Z - Z_b for a base
+// (Z_b, P_b): Z_b = E with P_b = Delta E exactly (FP32 SIMT forms and the first
+// tensor-core evaluations), or an earlier iterate whose P was stored.  The
+// product of V errs by about u * ||Delta V|| (u per product kind, measured
+// ||Delta V|| of this evaluation), the stored P_b by its own error e_base, and
+// the FP32 map arithmetic by about e_arith * (||R0|| + ||Delta (Z - E)||).  The
+// device residual rho therefore differs from the true one by at most about
+// e_rel = (e_base + u ||Delta V|| + arithmetic) / ||R0||.  With the guard
+// (residual stop), an evaluation stops the solve only if rho + e_rel <= tol.
+// A fixed-precision solve whose test holds but whose guard does not ends with
+// IPT_INACCURATE; a staged solve goes on and escalates its products.
+//
+// Staged schedule.  After an evaluation the controller predicts ||Delta V|| of
+// the next one as kappa * (bound on ||V||) and uses the 1-pass product when its
+// error is below stage_switch (0.1) times the predicted next residual, or below
+// tol / 10; otherwise a split product that stores its P as the new base (the
+// base error grows by that product's error).  The base error is a floor under
+// the residual: when it would leave less than half of tol, the schedule
+// re-bases on a compensated FP32 product of Delta (Z - E) instead (base E).
+__device__ __forceinline__ bool split_stage(int stage) {
+  return stage == IPT_PREC_BF16X3 || stage == IPT_PREC_FP16X3;
+}
+
 __global__ void k_control(DevState* st, ControlArgs a) {
-  if (st->done) return;
+  if (st->done || st->pause) return;
   const int it = st->iter;
   const double z2 = st->acc_z2;
   const double inc = sqrt(st->acc_inc2) / sqrt(z2);
   const double r0 = sqrt(st->r0acc);
   const double rho = r0 > 0.0 ? sqrt(st->acc_r2) / r0 : 0.0;
   const double pv = sqrt(st->acc_pv2);
-  const int stage = st->stage, passes = st->passes;
+  const bool host_driven = a.host_base >= -1;
+  const int stage = host_driven && a.host_stage >= 0 ? a.host_stage : st->stage;
+  const int passes = host_driven && a.host_passes >= 0 ? a.host_passes : st->passes;
+  const bool measured = (a.host_measure >= 0 ? a.host_measure : st->measure) != 0;
   if (it < IPT_MAX_HISTORY) {
     st->hist_inc[it] = inc;
     st->hist_rho[it] = rho;
@@ -563,9 +619,38 @@ __global__ void k_control(DevState* st, ControlArgs a) {
   if (a.csr_n > 0) st->rows_eval += st->win_hi - st->win_lo;
   if (passes == 1 && (stage == IPT_PREC_BF16 || stage == IPT_PREC_FP16)) st->stage_iters[0]++;
   else if (passes != 0) st->stage_iters[1]++;
+  // this evaluation's predicted error (see above)
+  const bool w_form = passes == 0 || stage == IPT_PREC_F32 || stage == IPT_PREC_F32C ||
+                      stage == IPT_PREC_F64;  // products relative to E
+  const int ebase = a.host_base >= -1 ? a.host_base : st->base;
+  const int erebase = a.host_base >= -1 ? a.host_rebase : st->rebase;
+  double u = 0.0;
+  if (passes > 0) {
+    if (stage == IPT_PREC_F32) u = a.u_f32;
+    else if (stage == IPT_PREC_F32C) u = a.u_acc;
+    else if (stage == IPT_PREC_F64) u = 0.0;
+    else u = (passes == 3 || split_stage(stage)) ? a.u_high : a.u_low;
+  }
+  const bool on_base = !w_form && ebase >= 0;
+  const double e_b = on_base ? st->e_base : 0.0;
+  const double pw = on_base ? st->pw_base + pv : pv;  // ~ ||Delta (Z - E)||
+  // the product's error: sampled (with a safety factor for the sample's
+  // spread), else the model
+  double e_prod = e_b + u * pv;
+  if (measured && a.smp_rows > 0 && st->acc_dpn > 0.0) {
+    const double cnt = st->acc_dpn;
+    const double entries = (double)(a.n_rows - 1) * (double)a.k;  // off the unit entries
+    e_prod = sqrt(st->acc_dp2 * entries / cnt) * (1.25 + 4.0 / sqrt(cnt));
+    st->e_meas = e_prod;
+  }
+  st->acc_dp2 = 0.0;
+  st->acc_dpn = 0.0;
+  const double e_abs = e_prod + a.e_arith * (r0 + pw);
+  const double e_rel = r0 > 0.0 ? e_abs / r0 : 0.0;
   if (a.test) {  // the reported pair is the last tested iterate
     st->inc = inc;
     st->rho = rho;
+    st->e_rel = e_rel;
   }
   st->iter = it + 1;
   st->acc_inc2 = 0.0;
@@ -574,13 +659,42 @@ __global__ void k_control(DevState* st, ControlArgs a) {
   st->acc_pv2 = 0.0;
   const double test = a.stop == IPT_STOP_INCREMENT ? inc : rho;
   const bool staged = a.mode == IPT_PREC_STAGED;
-  const bool can_stop = (!staged || st->accurate) && a.test;
+  const bool guarded = a.guard && a.stop == IPT_STOP_RESIDUAL;
+  const bool met = a.test && test <= a.tol;
+  const bool certified = !guarded || rho + e_rel <= a.tol;
+  // a met but uncertified test is final (IPT_INACCURATE) once the residual no
+  // longer falls (or, fixed precision, once the error model alone takes half
+  // of tol) and no more accurate product is left to escalate to
+  const double best = st->rho_best > 0.0 ? st->rho_best : INFINITY;
+  const bool stalled = rho > 0.9 * best;
+  if (a.test) st->rho_best = fmin(best, rho);
+  const bool can_escalate = (staged || a.accel_staged) && !st->acc_based;
+  const bool give_up = met && !certified && !can_escalate &&
+                       (stalled || (!staged && !a.accel_staged && e_rel >= 0.5 * a.tol));
+  if (a.accel_staged && a.test) {
+    // ask for an accurate re-base once the split products' sampled error is a
+    // sizeable part of the residual (or blocks the stop), if it would shrink it
+    const double e_acc = (a.u_acc * pw + a.e_arith * (r0 + pw)) / fmax(r0, 1e-300);
+    st->want_acc = measured && (e_rel >= 0.1 * fmax(rho, a.tol) || (met && !certified)) &&
+                   e_acc < 0.5 * e_rel;
+  }
+  if (erebase && passes > 0) {
+    // this evaluation's P is the new base product
+    st->e_base = e_prod;
+    st->pw_base = pw;
+    st->acc_based = stage == IPT_PREC_F32C;
+  }
   if (!isfinite(inc) || !isfinite(rho) || sqrt(z2) > a.diverge_bound * sqrt((double)a.k)) {
     st->status = IPT_DIVERGED;
     st->done = 1;
     st->answer = st->cur;
-  } else if (can_stop && test <= a.tol) {
+  } else if (met && certified) {
     st->status = IPT_OK;
+    st->done = 1;
+    st->answer = st->cur;
+  } else if (give_up) {
+    // the products' arithmetic cannot certify tol
+    st->status = IPT_INACCURATE;
     st->done = 1;
     st->answer = st->cur;
   } else if (it + 1 >= a.max_iter) {
@@ -592,7 +706,7 @@ __global__ void k_control(DevState* st, ControlArgs a) {
     const int out = zbuf_free(cur, base);  // where this evaluation wrote F
     if (staged) {
       double kappa = st->kappa > 0.0 ? st->kappa : r0 / sqrt((double)a.k);
-      if (passes > 0 && st->sv > 0.0 && pv > 0.0) kappa = pv / st->sv;
+      if (passes > 0 && !w_form && st->sv > 0.0 && pv > 0.0) kappa = pv / st->sv;
       st->kappa = kappa;
       const double sv_after = st->rebase ? 0.0 : st->sv;  // ||Z_t - Z_b|| bound
       const double sv_next = sv_after + a.step_scale * inc * sqrt(z2);  // ||Z_{t+1} - Z_b||
@@ -601,22 +715,47 @@ __global__ void k_control(DevState* st, ControlArgs a) {
       double q = (it > 0 && prev > 0.0) ? rho / prev : inc;
       q = fmin(fmax(q, 1e-3), 1.0);
       const double need = fmax(a.stage_switch * rho * q, 0.1 * a.tol);
-      const double e_low = r0 > 0.0 ? a.low_unit * kappa * sv_next / r0 : 0.0;
-      if (e_low <= need) {
+      const double rr = fmax(r0, 1e-300);
+      const double dv_next = kappa * sv_next;  // predicted ||Delta V|| of the next product
+      const double eb = (st->base >= 0 ? st->e_base : 0.0) / rr;
+      const double e_low = a.u_low * dv_next / rr;
+      const double e_high = a.u_high * dv_next / rr;
+      const double pw_next = (st->base >= 0 ? st->pw_base : 0.0) + dv_next;
+      const double e_acc = a.u_acc * pw_next / rr;
+      // the base error is a floor, not a disturbance of the iteration: it may
+      // stand while it leaves half of tol for the residual and the arithmetic
+      const double room = fmax(need, 0.5 * a.tol - a.e_arith * (1.0 + pw_next / rr));
+      // escalate on the base error known so far (a re-base's is sampled); the
+      // split product's own error is sampled when it re-bases
+      const bool low_ok = e_low <= need;
+      (void)e_high;
+      const bool improves = a.escalate && e_acc < 0.5 * eb;
+      if (eb > room && improves) {
+        st->stage = IPT_PREC_F32C;
+        st->passes = 1;
+        st->rebase = 1;
+        st->accurate = 1;
+        if (a.pause_on_acc) st->pause = 1;
+      } else if (low_ok) {
         st->stage = a.low_stage;
         st->passes = 1;
         st->rebase = 0;
-        st->accurate = e_low <= 0.1 * a.tol;
+        st->accurate = eb + e_low <= 0.5 * a.tol;
       } else {
         st->stage = a.high_stage;
         st->passes = 3;
         st->rebase = 1;
-        st->accurate = 1;
+        st->accurate = eb + e_high <= 0.5 * a.tol;
       }
+      st->measure = st->passes == 3 && a.smp_rows > 0;
       st->sv = sv_next;
-    } else if (passes == 0) {
-      // non-staged tensor-core / FP32 solve after its product-free first evaluation
-      st->passes = (stage == IPT_PREC_BF16X3 || stage == IPT_PREC_FP16X3) ? 3 : 1;
+    } else {
+      if (passes == 0)  // non-staged solve after its product-free first evaluation
+        st->passes = split_stage(stage) ? 3 : 1;
+      // sample the product error of an evaluation that may be the last one
+      const double prev = st->prev_rho;
+      const double q = (it > 0 && prev > 0.0) ? fmin(rho / prev, 1.0) : 1.0;
+      st->measure = a.smp_rows > 0 && a.measure_below > 0.0 && rho * q <= a.measure_below;
     }
     if (a.csr_n > 0) {
       // CSR: the next iterate is this evaluation's F; its nonzero rows widened
@@ -687,10 +826,19 @@ void launch_gemm_simt_f64(const double* Drow, const MapArgs<double>& a, int npad
   k_gemm_simt<double, 64, 64, 8, 4, 4, EPI_MAP><<<g, 256, 0, s>>>(Drow, a, nullptr, nullptr);
 }
 
+#ifndef IPT_COMP_SLABS
+#define IPT_COMP_SLABS 4  // BK-slabs per compensated add: 32 products per FP32 partial
+#endif
+
 void launch_gemm_simt_f32(const float* Drow, const MapArgs<float>& a, int npad, int kpad,
-                          cudaStream_t s) {
+                          int compensated, cudaStream_t s) {
   dim3 g(kpad / 128, npad / 128);
-  k_gemm_simt<float, 128, 128, 8, 8, 8, EPI_MAP><<<g, 256, 0, s>>>(Drow, a, nullptr, nullptr);
+  if (compensated)
+    k_gemm_simt<float, 128, 128, 8, 8, 8, EPI_MAP, IPT_COMP_SLABS><<<g, 256, 0, s>>>(
+        Drow, a, nullptr, nullptr);
+  else
+    k_gemm_simt<float, 128, 128, 8, 8, 8, EPI_MAP><<<g, 256, 0, s>>>(Drow, a, nullptr,
+                                                                      nullptr);
 }
 
 void launch_residual_f64(const double* M64, const double* Z64, int64_t ld, const double* lam,

@@ -197,6 +197,23 @@ __device__ __forceinline__ void tile_coords(int t, int num_m, int num_n, int& mb
   nb = r / gm;
 }
 
+// Order of the K blocks within one pass: farthest from the tile's own column
+// block first, that block last.  Near the fixed point of a near-diagonal
+// problem the entries W_mc of a column fall off with |theta_m - theta_c|, so
+// the terms with m near the tile's columns dominate each sum.  The tensor
+// core's FP32 accumulation loses low bits relative to the running sum at each
+// accumulate; adding the many small far terms while the sum is still small and
+// the few dominant ones last keeps that loss at a fraction of |P|.
+struct KOrder {
+  int lo, hi, center;
+  __device__ void reset(int nb, int num_kb) {
+    lo = 0;
+    hi = num_kb - 1;
+    center = min((nb * BN + BN / 2) / BK, num_kb - 1);
+  }
+  __device__ int next() { return (center - lo >= hi - center) ? lo++ : hi--; }
+};
+
 __device__ __forceinline__ void fail(Ctl* ctl, DevState* st, int code) {
   *reinterpret_cast<volatile int*>(&ctl->abort) = 1;
   atomicCAS(&st->timeout, 0, code);
@@ -219,13 +236,16 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   constexpr int STAGES = Shape<MODE>::STAGES;
   constexpr int B_BYTES = Shape<MODE>::B_BYTES;
   constexpr int STAGE_BYTES = Shape<MODE>::STAGE_BYTES;
-  if (a.st->done) return;  // uniform over the grid, so over each cluster
+  // uniform over the grid, so over each cluster; a paused solve runs its next
+  // evaluation with a kernel of another kind first
+  if (a.st->done || (a.dyn && a.st->pause)) return;
   // operands: as launched, or (dyn) chosen by the controller's state
   const float* Zin = a.Zin;
   float* Fout = a.Fout;
   const float* Pbase = a.Pbase;
   int pbase_by_icol = a.pbase_by_icol;
   float* Pout = a.Pout;
+  float* psmp = a.psmp;  // sampled P entries (error estimate), or none
   if (a.dyn) {
     const int cur = a.st->cur, base = a.st->base;
     passes = a.st->passes;
@@ -234,6 +254,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     Pbase = base >= 0 ? a.pstore : a.DT;
     pbase_by_icol = base >= 0 ? 0 : 1;
     Pout = a.st->rebase ? a.pstore : nullptr;
+    if (!a.st->measure) psmp = nullptr;
   }
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>(
@@ -299,6 +320,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         int mb, nb;
         tile_coords(t, sched_m, num_n, mb, nb);
         if (CLUSTER) mb = 2 * mb + rank;
+        KOrder ko;
         for (int kb = 0; kb < total_kb; ++kb) {
           if (!wait_bounded(&ctl->empty[stage], phase ^ 1u, abort)) {
             fail(ctl, a.st, 1);
@@ -306,7 +328,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             break;
           }
           const int pass = kb / num_kb;
-          const int kx = (kb - pass * num_kb) * BK;
+          if (kb == pass * num_kb) ko.reset(nb, num_kb);
+          const int kx = ko.next() * BK;
           // passes = 1: Dh Wh.  passes = 3: (Dh Wl, Dl Wh, Dh Wh), or with the
           // main product first (Dh Wh, Dh Wl, Dl Wh).
           const int role = passes == 1 ? 0 : (IPT_CORRECTIONS_FIRST ? (pass + 1) % 3 : pass);
@@ -445,6 +468,9 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       const int j = mb * BM + row;
       const bool jok = j < a.n;
       const float hj = a.th_hi[j], lj = a.th_lo[j], rj = a.rinv[j];
+      // this row's slot among the sampled rows, or -1
+      const int jr = (psmp && j % a.smp_stride == a.smp_off) ? j / a.smp_stride : -1;
+      float* prow = jr >= 0 && jr < kSampleRows ? psmp + (int64_t)jr * a.smp_kpad : nullptr;
 #pragma unroll 1
       for (int ch = 0; ch < EPI_COLS / 16; ++ch) {
         float v[16];
@@ -472,6 +498,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
           const float dv = v[i] * (rj * ci.s);  // Delta V, scales undone exactly
           const float p = pb[i] + dv;           // P = P_base + Delta V
           if (Pout) __stcs(Pout + o, p);
+          if (prow) prow[cbase + c0 + i] = p;
           s_pv = fmaf(dv, dv, s_pv);
           float f, r;
           const float gap = gap2f(hj, lj, ci.hi, ci.lo);

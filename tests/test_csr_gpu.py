@@ -225,7 +225,7 @@ def test_csr_handle_reuse_across_problems_and_dense(ipt):
     cb = cuda(np.arange(4000, 4012, dtype=np.int32), torch.int32)
     fresh = {}
     for name, cg in [("a", ca), ("b", cb)]:
-        lam, Z, info = ipt.Solver().solve_csr(rp, ci, vv, n, cols=cg, tol=1e-7, max_iter=40)
+        lam, Z, info = ipt.Solver().solve_csr(rp, ci, vv, n, cols=cg, tol=1e-6, max_iter=40)
         assert info["status"] == "OK"
         fresh[name] = Z.cpu().numpy()
     s = ipt.Solver()
@@ -237,9 +237,9 @@ def test_csr_handle_reuse_across_problems_and_dense(ipt):
                           max_iter=30)
             continue
         if name == "window-off":
-            s.solve_csr(rp, ci, vv, n, cols=cb, tol=1e-7, max_iter=40, window=False)
+            s.solve_csr(rp, ci, vv, n, cols=cb, tol=1e-6, max_iter=40, window=False)
             continue
-        lam, Z, info = s.solve_csr(rp, ci, vv, n, cols=cg, tol=1e-7, max_iter=40)
+        lam, Z, info = s.solve_csr(rp, ci, vv, n, cols=cg, tol=1e-6, max_iter=40)
         assert info["status"] == "OK"
         assert np.array_equal(Z.cpu().numpy(), fresh[name]), name
 
@@ -272,3 +272,31 @@ def test_csr_all_rows_equals_active_window_at_scale(ipt, band, k, vdt):
     Zs = Z_a[:, torch.as_tensor(pick, device="cuda")].double().cpu().numpy()
     E = oracle.unit_columns(n, cols[pick])
     assert np.linalg.norm(Zs - ref["Z"]) / np.linalg.norm(ref["Z"] - E) <= 1e-4
+
+
+@pytest.mark.parametrize("window,vdt", [(True, torch.float32), (False, torch.float32),
+                                        (True, torch.float64)])
+def test_csr_verify_fp64_matches_oracle_residual(ipt, window, vdt):
+    """The sparse solve's FP64 verification (rho_fp64 * r0) equals the oracle's
+    ||M Z - Z Lambda||_F (M from the CSR arrays, the values as the GPU sees them)
+    on the GPU's own result, within both FP64 evaluations' rounding bounds."""
+    sp = pytest.importorskip("scipy.sparse")
+    n, k = 20000, 24
+    rowptr, colind, vals, th = w.csr_banded(n, 6, 400, 1e-3, seed=21, theta_step=0.01)
+    cols = w.lowest_columns(th, k)
+    rp, ci, vv = csr_on_gpu(rowptr, colind, vals, vdt)
+    lam, Z, info = ipt.Solver().solve_csr(rp, ci, vv, n, cols=cuda(cols, torch.int32),
+                                          tol=1e-6, max_iter=40, window=window,
+                                          verify_fp64=True)
+    assert info["status"] == "OK", info
+    v64 = vv.double().cpu().numpy()
+    M = sp.csr_matrix((v64, colind, rowptr), shape=(n, n))
+    Zh, lh = Z.double().cpu().numpy(), lam.cpu().numpy()
+    ref = np.linalg.norm(M @ Zh - Zh * lh[None, :])
+    u = 2.0 ** -53
+    Ma = sp.csr_matrix((np.abs(v64), colind, rowptr), shape=(n, n))
+    row_len = np.diff(rowptr).max() + 1
+    bound = 2 * row_len * u * np.linalg.norm(Ma @ np.abs(Zh) + np.abs(Zh) * np.abs(lh)[None, :])
+    got = info["rho_fp64"] * info["r0"]
+    assert info["rho_fp64"] >= 0 and abs(got - ref) <= bound + 1e-12 * ref, (got, ref, bound)
+    assert info["rho_fp64"] <= 1e-6

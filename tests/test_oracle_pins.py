@@ -608,3 +608,21 @@ def test_anderson_solve_converges_outside_picard_domain_to_eigh():
     a = an.ipt_solve_anderson(M, th, tol=1e-10, max_iter=300)
     assert a["status"] == oracle.OK
     np.testing.assert_allclose(np.sort(a["lam"]), np.linalg.eigvalsh(M), atol=1e-9)
+
+
+def test_acx_csr_front_end_equals_dense_acx():
+    """The sparse IPT-ACX entry (CSR product) takes the same steps as the dense
+    one on the same matrix: the tridiagonal Morgan matrix of Section 6.1 at
+    eps = 1, outside the Picard domain, and a banded random matrix."""
+    import scipy.sparse as sp
+    for M, th, cols in [(*w.morgan_tridiagonal(120, 1.0), [0, 1, 5]),
+                        (*w.dense_symmetric(150, 0.05, seed=3, theta_step=0.25), [2, 40, 99])]:
+        S = sp.csr_matrix(M)
+        for sigma in ["column", "global"]:
+            a = oracle.ipt_solve_acx(M, th, cols=cols, tol=1e-13, max_iter=300, sigma=sigma)
+            b = oracle.ipt_solve_acx_csr(S.indptr, S.indices, S.data, M.shape[0], theta=th,
+                                         cols=cols, tol=1e-13, max_iter=300, sigma=sigma)
+            assert a["status"] == b["status"] == oracle.OK
+            assert a["iterations"] == b["iterations"]
+            np.testing.assert_allclose(b["lam"], a["lam"], rtol=1e-13)
+            np.testing.assert_allclose(b["Z"], a["Z"], atol=1e-12)
