@@ -626,3 +626,92 @@ def test_acx_csr_front_end_equals_dense_acx():
             assert a["iterations"] == b["iterations"]
             np.testing.assert_allclose(b["lam"], a["lam"], rtol=1e-13)
             np.testing.assert_allclose(b["Z"], a["Z"], atol=1e-12)
+
+
+# ------------------------------------------------------------------ learned damping + mixing
+def test_mixing_model_gradient_matches_finite_differences():
+    """The two-output backward pass against central differences of its own forward
+    pass in float64 (FP16 parameters perturbed in float64), both outputs."""
+    from oracle import mixing as mx
+    g = np.random.default_rng(15)
+    p16 = mx.init_params(4)
+    X = g.standard_normal((40, 7))
+    t = np.stack([g.uniform(0.1, 1.9, 40), g.uniform(-1.5, 1.5, 40)], axis=1)
+    _, grad = mx.loss_and_grad(p16, X, t)
+    base = p16.astype(np.float64)
+
+    def loss_at(flat64):
+        pp = mx.unpack(flat64)
+        h1 = np.tanh(X @ pp["W1"] + pp["b1"])
+        h2 = np.tanh(h1 @ pp["W2"] + pp["b2"])
+        y = h2 @ pp["W3"] + pp["b3"]
+        a = 2.0 / (1.0 + np.exp(-y[:, 0]))
+        gm = 2.0 * np.tanh(y[:, 1])
+        return np.mean((a - t[:, 0]) ** 2 + (gm - t[:, 1]) ** 2)
+
+    idx = np.concatenate([g.choice(mx.N_PARAMS, 60, replace=False),
+                          np.arange(mx.N_PARAMS - 130, mx.N_PARAMS)])  # all of W3, b3
+    for i in idx:
+        e = np.zeros(mx.N_PARAMS)
+        e[i] = 1e-6
+        fd = (loss_at(base + e) - loss_at(base - e)) / 2e-6
+        assert abs(fd - grad[i]) <= 1e-6 + 1e-5 * abs(fd), (i, fd, grad[i])
+
+
+def test_mixed_update_special_cases_and_exact_targets():
+    """gamma = 0 is the damped step and alpha = 1 Anderson mixing; on maps with one
+    multiplier a per column (f(z) = (a - 1)(z - z*)) the targets land exactly:
+    after a Picard step z_t = F(z_{t-1}) the Anderson candidate's point is z*
+    (gamma* = gamma_ls = a / (a - 1))."""
+    from oracle import anderson as an
+    from oracle import mixing as mx
+    g = np.random.default_rng(16)
+    n, k = 9, 4
+    zp, zs = (g.standard_normal((n, k)) for _ in range(2))
+    a = np.array([0.5, -0.8, 2.5, -3.0])
+    fz = lambda x: (a[None, :] - 1.0) * (x - zs)
+    z = zp + fz(zp)  # z_t = F(z_{t-1}): a Picard step
+    f, fp = fz(z), fz(zp)
+    al, gm = g.uniform(0.3, 1.7, k), g.uniform(-1, 1, k)
+    np.testing.assert_allclose(mx.mixed_update(z, f, zp, fp, al, np.zeros(k)),
+                               z + al[None, :] * f, atol=1e-13)
+    np.testing.assert_allclose(mx.mixed_update(z, f, zp, fp, np.ones(k), gm),
+                               an.anderson_update(z + f, zp + fp, gm), atol=1e-12)
+    alpha, gamma = mx.targets(z, f, zp, fp, fz)
+    g_ls = np.clip(a / (a - 1.0), -mx.GAMMA_CLIP, mx.GAMMA_CLIP)
+    np.testing.assert_allclose(gamma, np.where(np.abs(a / (a - 1.0)) <= mx.GAMMA_CLIP,
+                                               g_ls, 0.0), atol=1e-9)
+    # r = f - gamma* df vanishes there, so any alpha* lands on z*
+    np.testing.assert_allclose(mx.mixed_update(z, f, zp, fp, alpha, gamma), zs, atol=1e-9)
+    # the Picard candidate alone (z_{t-1} unrelated): its secant alpha* = 1 / (1 - a)
+    # makes the damped step exact
+    zq = g.standard_normal((n, k))
+    fq = fz(zq)
+    r, Jr = fq, fz(zq + fq) - fq
+    np.testing.assert_allclose(mx.secant_alpha(r, Jr, lo=-1e9, hi=1e9), 1.0 / (1.0 - a),
+                               rtol=1e-12)
+
+
+def test_mixed_solve_reduces_to_picard_damping_and_anderson():
+    """model = (1, 0) is Alg. 2's Picard iteration; model = (alpha, 0) the damped
+    solve; model = (1, gamma_ls) depth-one Anderson after the first steps."""
+    from oracle import damping as dm
+    from oracle import mixing as mx
+    M, th = w.dense_symmetric(90, 0.01, seed=8, theta_step=0.5)
+    a = mx.mixed_solve(M, th, tol=1e-12, max_iter=60,
+                       model_fn=lambda X: (np.ones(len(X)), np.zeros(len(X))))
+    b = oracle.ipt_solve(M, th, tol=1e-12, max_iter=60, stop="residual")
+    assert a["status"] == b["status"] == oracle.OK and a["iterations"] == b["iterations"]
+    np.testing.assert_array_equal(a["Z"], b["Z"])
+    rule = lambda X: np.clip(1.0 / np.where(np.abs(1.0 - X[:, 3]) > 1e-12, 1.0 - X[:, 3],
+                                            1e-12), 0.05, 2.0)
+    M, th = w.dense_symmetric(128, 0.03, seed=7, theta_step=0.125)
+    c = mx.mixed_solve(M, th, tol=1e-9, max_iter=200, model_fn=lambda X: (rule(X[:, :6]),
+                                                                          np.zeros(len(X))))
+    d = dm.damped_solve(M, th, tol=1e-9, max_iter=200, alpha_fn=rule)
+    assert c["status"] == d["status"] and c["iterations"] == d["iterations"]
+    np.testing.assert_allclose(c["Z"], d["Z"], atol=1e-12)
+    e = mx.mixed_solve(M, th, tol=1e-9, max_iter=200,
+                       model_fn=lambda X: (np.ones(len(X)), X[:, 6]))
+    assert e["status"] == oracle.OK
+    np.testing.assert_allclose(np.sort(e["lam"]), np.linalg.eigvalsh(M), atol=1e-9)
