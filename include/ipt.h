@@ -118,7 +118,8 @@ typedef struct {
   int acx_sigma;        /* ACX step length: 0 (default) one per column, 1 one for all     */
   const void* damping_model; /* IPT_ACCEL_DAMPED: the damping model's parameters (device,
                                 FP16, IPT_DAMPING_PARAMS values, layout of
-                                ipt_damping_forward)                                       */
+                                ipt_damping_forward); IPT_ACCEL_MIXING: the mixing
+                                model's (IPT_MIXING_PARAMS, ipt_mixing_forward)           */
   int csr_window;       /* ipt_solve_csr: nonzero (default) = each product evaluates only the
                            rows that can be nonzero: the rows of the current iterate's
                            nonzero rows widened by the band max|j - m| of the stored
@@ -136,7 +137,21 @@ typedef struct {
  * with g = F and f = g(z) - z, the next iterate is g(z_t) - gamma_c (g(z_t) - g(z_{t-1})),
  * gamma_c = <f_t - f_{t-1}, f_t> / ||f_t - f_{t-1}||^2 (0 where that vanishes); the first
  * step and every step after the same fallback are Picard steps.  Precision as for ACX. */
-enum { IPT_ACCEL_NONE = 0, IPT_ACCEL_ACX = 1, IPT_ACCEL_DAMPED = 2, IPT_ACCEL_ANDERSON = 3 };
+enum {
+  IPT_ACCEL_NONE = 0,
+  IPT_ACCEL_ACX = 1,
+  IPT_ACCEL_DAMPED = 2,
+  IPT_ACCEL_ANDERSON = 3,
+  IPT_ACCEL_MIXING = 4  /* learned damping and mixing (also outside the paper): after
+                           each evaluation z <- z + alpha f - gamma ((z - z_prev) +
+                           alpha (f - f_prev)), f = F(z) - z, with (alpha_c, gamma_c)
+                           per column from the mixing model (ipt_mixing_forward; its
+                           parameters in ipt_options.damping_model) fed the damping
+                           model's six history features and the least-squares
+                           Anderson weight; Picard steps first and after the same
+                           fallback as IPT_ACCEL_DAMPED.  gamma = 0 is the damped step,
+                           alpha = 1 Anderson mixing.  Precision as for ACX.        */
+};
 
 /* Values of ipt_options.product_kernel. */
 enum { IPT_PRODUCT_AUTO = 0, IPT_PRODUCT_SINGLE = 1, IPT_PRODUCT_PAIR = 2 };
@@ -373,6 +388,30 @@ ipt_status ipt_damping_grad(int64_t B, const void* params, const float* x, const
 ipt_status ipt_damping_adam(float* master, void* params, float* grad, float* m, float* v,
                             float lr, float beta1, float beta2, float eps, int step,
                             void* stream);
+
+/*
+ * The mixing model of IPT_ACCEL_MIXING and its training (no counterpart in the
+ * paper).  A 7 -> 64 -> 64 -> 2 perceptron: h1 = tanh(x W1 + b1),
+ * h2 = tanh(h1 W2 + b2), y = h2 W3 + b3, alpha = 2 / (1 + exp(-y0)),
+ * gamma = 2 tanh(y1).  Parameters: IPT_MIXING_PARAMS FP16 values on the device,
+ * packed row-major as W1[7][64], b1[64], W2[64][64], b2[64], W3[64][2], b3[2];
+ * FP32 arithmetic.  Inputs: rows of 7 FP32 features (device, B x 7); outputs
+ * and targets: rows (alpha, gamma) (device FP32, B x 2).  Calls are ordered on
+ * `stream` (NULL = legacy default stream) and do not synchronise.
+ *   ipt_mixing_forward: out[b] = (alpha_b, gamma_b) for b < B.
+ *   ipt_mixing_grad: ADDS the gradient of mean_b ((alpha_b - t_b0)^2 + (gamma_b - t_b1)^2)
+ *     to grad (device FP32[IPT_MIXING_PARAMS]) and the mean to *loss (device FP64).
+ *   ipt_mixing_adam: one Adam step as ipt_damping_adam, on IPT_MIXING_PARAMS values.
+ * Returns IPT_INVALID_ARG for a null pointer or B < 0, IPT_CUDA_ERROR on a launch error.
+ */
+#define IPT_MIXING_PARAMS 4802
+ipt_status ipt_mixing_forward(int64_t B, const void* params, const float* x, float* out,
+                              void* stream);
+ipt_status ipt_mixing_grad(int64_t B, const void* params, const float* x, const float* target,
+                           float* grad, double* loss, void* stream);
+ipt_status ipt_mixing_adam(float* master, void* params, float* grad, float* m, float* v,
+                           float lr, float beta1, float beta2, float eps, int step,
+                           void* stream);
 
 /*
  * ||M Z - Z Lambda||_F in FP64, allocating no device memory.  The paper has

@@ -40,6 +40,9 @@ constexpr int kDenseChunk = 6;
 constexpr int kEvbSlots = kDenseChunk > kCsrChunk ? kDenseChunk : kCsrChunk;
 // Accumulation term of the split products' error model (see set_error_model).
 constexpr double kSplitAccum = 0.66;
+// Staged accelerated solves hand over to the acceleration once a tested residual
+// falls by less than this factor per evaluation.
+constexpr double kHandoverRatio = 0.25;
 
 }  // namespace
 
@@ -50,6 +53,7 @@ struct ipt_handle {
   Buf smp;                          // sampled product entries (error estimate)
   Buf acx_d, acx_acc, acx_sigma;    // ACX: d of the inner evaluations, step-length sums, steps
   Buf damp;                         // learned damping: history, features, alphas, state
+  Buf mix;                          // learned mixing: statistics, history, features, outputs
   Buf bmeta, bscratch;              // batched: schedule and offsets, per-CTA iterate pairs
   int btiles[kBatchClasses] = {};   // batched: tuned output tile per size class (0 = untuned)
   cudaStream_t gs = nullptr;        // batched: capture stream (the handle's may be the legacy one)
@@ -124,6 +128,7 @@ struct Plan {
   bool acx = false;  // four Z buffers (z, f, f^2, f^3) and the extrapolation scratch
   bool acx_base = false;  // accelerated staged solve: fifth Z buffer (the base) and P_b
   bool damped = false;  // learned damping buffers
+  bool mixing = false;  // learned mixing buffers
 };
 
 ipt_status check_dense_args(ipt_handle* h, int64_t n, const void* M, int64_t ldm, int m_dtype,
@@ -135,6 +140,10 @@ ipt_status check_dense_args(ipt_handle* h, int64_t n, const void* M, int64_t ldm
   if (prec < IPT_PREC_F64 || prec > IPT_PREC_F32C) return IPT_INVALID_ARG;
   return IPT_OK;
 }
+
+// Learned-mixing scratch: acc (4k FP64), lam history (3k FP64), increment
+// history (3k FP32), features (7k FP32), model outputs (2k FP32), state.
+inline size_t mix_bytes(int kpad) { return (size_t)kpad * (32 + 24 + 12 + 28 + 8) + 64; }
 
 ipt_status alloc_dense(ipt_handle* h, const Plan& p) {
   const size_t nn = (size_t)p.npad * p.npad, kn = (size_t)p.kpad * p.npad;
@@ -150,6 +159,7 @@ ipt_status alloc_dense(ipt_handle* h, const Plan& p) {
     CK(ensure(h->acx_acc, (size_t)p.kpad * 2 * 8));
     CK(ensure(h->damp, (size_t)p.kpad * (3 * 8 + 3 * 4 + 6 * 4 + 4) + 64));
   }
+  if (p.mixing) CK(ensure(h->mix, mix_bytes(p.kpad)));
   if (p.acx_base) {
     CK(ensure(h->z[4], kn * ez));
     CK(ensure(h->pbuf, kn * 4));
@@ -590,14 +600,14 @@ void set_error_model(ControlArgs& ca, const Plan& p) {
 // stores its P as the base product P_b and z is copied to buffer 4 as Z_b;
 // later split products are of V = Z - Z_b.
 ipt_status acx_loop(ipt_handle* h, const Plan& p, const ControlArgs& ca, const FirstEval& fe,
-                    int max_iter, int sigma_global, Timing* tm) {
+                    int max_iter, int sigma_global, Timing* tm, int start_iter = 0) {
   cudaStream_t s = h->s;
   DevState* st = dst(h);
   const int split = (fe.stage == IPT_PREC_BF16X3 || fe.stage == IPT_PREC_FP16X3) ? 3 : 1;
   double* dinner = (double*)h->acx_d.p;
   CK(cudaMemsetAsync(h->acx_acc.p, 0, (size_t)p.kpad * 2 * 8, s));
   const size_t zbytes = (size_t)p.kpad * p.npad * (p.f64 ? 8 : 4);
-  int done_evals = 0, base = -1;
+  int done_evals = start_iter, base = -1;
   bool acc_next = false;
   double last_rho = 1.0;  // the last tested residual (sampling starts near tol)
   int stg_of[3] = {0, 0, 0}, passes_of[3] = {0, 0, 0};
@@ -647,7 +657,7 @@ ipt_status acx_loop(ipt_handle* h, const Plan& p, const ControlArgs& ca, const F
         cudaMemcpyAsync(h->hst, st, kStateHead, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess)
       return IPT_CUDA_ERROR;
-    if (step == 0) {
+    if (step == 0 && start_iter == 0) {
       const ipt_status v = status_from_flags(h->hst->flags);
       if (v != IPT_OK) return v;
       if (tm && tm->on) {
@@ -675,7 +685,8 @@ ipt_status acx_loop(ipt_handle* h, const Plan& p, const ControlArgs& ca, const F
 // cannot run, it pauses them; the host then runs that evaluation itself and
 // goes on.
 ipt_status dense_chunked_loop(ipt_handle* h, const Plan& p, const ControlArgs& ca_in,
-                              const FirstEval& fe, int max_iter, Timing* tm) {
+                              const FirstEval& fe, int max_iter, Timing* tm,
+                              bool* handed_over = nullptr) {
   cudaStream_t s = h->s;
   DevState* st = dst(h);
   const bool t = tm && tm->on;
@@ -725,6 +736,11 @@ ipt_status dense_chunked_loop(ipt_handle* h, const Plan& p, const ControlArgs& c
     done_evals = h->hst->iter;
     if (h->hst->timeout) return IPT_DEVICE_TIMEOUT;
     if (h->hst->done) break;
+    if (h->hst->pause == 2 && handed_over) {  // the acceleration continues the solve
+      *handed_over = true;
+      CK(cudaMemsetAsync(&st->pause, 0, sizeof(int), s));
+      return IPT_OK;
+    }
     if (h->hst->pause) {
       CK(cudaMemsetAsync(&st->pause, 0, sizeof(int), s));
       const int stg = h->hst->stage;
@@ -743,14 +759,16 @@ ipt_status dense_chunked_loop(ipt_handle* h, const Plan& p, const ControlArgs& c
   return IPT_OK;
 }
 
-// Anderson mixing (IPT_ACCEL_ANDERSON).  Buffers: zc holds the iterate under
+// Anderson mixing (IPT_ACCEL_ANDERSON), or with `mix_model` the learned damping
+// and mixing (IPT_ACCEL_MIXING, k_mix.cu) on the same buffers.  Buffers: zc holds the iterate under
 // test, (zp, gp) the previous iterate and its map value, fr receives this
 // evaluation's map value.  The first step is a Picard step, so z_1 = g_0 stays
 // where g_0 was written (zc = gp); later steps write z_{t+1} over z_{t-1}.  One
 // host synchronisation per evaluation.  Accelerated staged solves re-base as in
 // acx_loop (Z_b in buffer 4).
 ipt_status anderson_loop(ipt_handle* h, const Plan& p, const ControlArgs& ca,
-                         const FirstEval& fe, int max_iter, Timing* tm) {
+                         const FirstEval& fe, int max_iter, Timing* tm,
+                         const void* mix_model = nullptr, int start_iter = 0) {
   cudaStream_t s = h->s;
   DevState* st = dst(h);
   const int split = (fe.stage == IPT_PREC_BF16X3 || fe.stage == IPT_PREC_FP16X3) ? 3 : 1;
@@ -759,13 +777,21 @@ ipt_status anderson_loop(ipt_handle* h, const Plan& p, const ControlArgs& ca,
   AndState* as = reinterpret_cast<AndState*>(h->acx_d.p);
   CK(cudaMemsetAsync(acc, 0, (size_t)p.kpad * 2 * 8, s));
   CK(cudaMemsetAsync(as, 0, sizeof(AndState), s));
+  // learned mixing scratch (see mix_bytes)
+  double* macc = mix_model ? (double*)h->mix.p : nullptr;
+  double* hlam = macc ? macc + (size_t)4 * p.kpad : nullptr;
+  float* hinc = macc ? (float*)(hlam + (size_t)3 * p.kpad) : nullptr;
+  float* X = hinc ? hinc + (size_t)3 * p.kpad : nullptr;
+  float* ag = X ? X + (size_t)kMixInputs * p.kpad : nullptr;
+  DampState* ms = ag ? reinterpret_cast<DampState*>(ag + (size_t)2 * p.kpad) : nullptr;
+  if (mix_model) CK(cudaMemsetAsync(h->mix.p, 0, mix_bytes(p.kpad), s));
   int zc = 0, zp = -1, gp = -1, fr = 1;
   const size_t zbytes = (size_t)p.kpad * p.npad * (p.f64 ? 8 : 4);
   int base = -1;
   bool acc_next = false;
   double last_rho = 1.0;
-  for (int it = 0; it < max_iter; ++it) {
-    int stg = fe.stage, passes = it == 0 ? fe.passes : (p.f64 ? 1 : split);
+  for (int it = 0; it < max_iter - start_iter; ++it) {
+    int stg = fe.stage, passes = (it == 0 && start_iter == 0) ? fe.passes : (p.f64 ? 1 : split);
     int eb = base, rebase = 0;
     if (acc_next) {
       stg = IPT_PREC_F32C;
@@ -790,14 +816,22 @@ ipt_status anderson_loop(ipt_handle* h, const Plan& p, const ControlArgs& ca,
       CK(cudaMemcpyAsync(h->z[4].p, h->z[zc].p, zbytes, cudaMemcpyDeviceToDevice, s));
       base = 4;
     }
-    CK(launch_anderson_step(h->z[zc].p, h->z[fr].p, it ? h->z[zp].p : nullptr,
-                            it ? h->z[gp].p : nullptr, it ? h->z[zp].p : nullptr,
-                            p.f64 ? 1 : 0, p.n, p.k, p.npad, acc, gamma, as, st, it == 0, s));
-    h->launches += it == 0 ? 3 : 5;
+    if (mix_model) {
+      CK(launch_mix_step(h->z[zc].p, h->z[fr].p, it ? h->z[zp].p : nullptr,
+                         it ? h->z[gp].p : nullptr, it ? h->z[zp].p : nullptr, p.f64 ? 1 : 0,
+                         p.n, p.k, p.npad, (const double*)h->theta.p, (const int32_t*)h->icol.p,
+                         (const double*)h->d.p, mix_model, macc, hinc, hlam, X, ag, ms, st, s));
+      h->launches += it == 0 ? 4 : 5;
+    } else {
+      CK(launch_anderson_step(h->z[zc].p, h->z[fr].p, it ? h->z[zp].p : nullptr,
+                              it ? h->z[gp].p : nullptr, it ? h->z[zp].p : nullptr,
+                              p.f64 ? 1 : 0, p.n, p.k, p.npad, acc, gamma, as, st, it == 0, s));
+      h->launches += it == 0 ? 3 : 5;
+    }
     if (cudaMemcpyAsync(h->hst, st, kStateHead, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess)
       return IPT_CUDA_ERROR;
-    if (it == 0) {
+    if (it == 0 && start_iter == 0) {
       const ipt_status fv = status_from_flags(h->hst->flags);
       if (fv != IPT_OK) return fv;
       if (tm && tm->on) {
@@ -843,8 +877,10 @@ ipt_status solve_dense(ipt_handle* h, int64_t n, const void* M, int64_t ldm, int
                       opt.product_kernel < IPT_PRODUCT_AUTO ||
                       opt.product_kernel > IPT_PRODUCT_PAIR ||
                       (opt.accel != IPT_ACCEL_NONE && opt.accel != IPT_ACCEL_ACX &&
-                       opt.accel != IPT_ACCEL_DAMPED && opt.accel != IPT_ACCEL_ANDERSON) ||
-                      (opt.accel == IPT_ACCEL_DAMPED && !opt.damping_model) ||
+                       opt.accel != IPT_ACCEL_DAMPED && opt.accel != IPT_ACCEL_ANDERSON &&
+                       opt.accel != IPT_ACCEL_MIXING) ||
+                      ((opt.accel == IPT_ACCEL_DAMPED || opt.accel == IPT_ACCEL_MIXING) &&
+                       !opt.damping_model) ||
                       (opt.acx_sigma != 0 && opt.acx_sigma != 1)))
     v = IPT_INVALID_ARG;
   if (v != IPT_OK) {
@@ -862,13 +898,20 @@ ipt_status solve_dense(ipt_handle* h, int64_t n, const void* M, int64_t ldm, int
   }
   const bool acx = opt.accel == IPT_ACCEL_ACX;
   const bool damped = opt.accel == IPT_ACCEL_DAMPED;
-  const bool anderson = opt.accel == IPT_ACCEL_ANDERSON;
+  const bool mixing = opt.accel == IPT_ACCEL_MIXING;
+  const bool anderson = opt.accel == IPT_ACCEL_ANDERSON || mixing;
   // ACX and Anderson mixing move the iterate by extrapolation, outside the
   // staged schedule's step model: a staged request runs the split products,
   // first of W = Z - E and, once their error model asks for it, of Z minus a
   // base stored by one compensated FP32 evaluation.  (Damped steps stay inside
   // the staged schedule with a step bound of 2 increments.)
   const bool accel_staged = (acx || anderson) && opt.precision == IPT_PREC_STAGED;
+  // Staged accelerated solves begin as the staged Picard solve (device-chosen
+  // operands, no per-evaluation host work) and hand over to the acceleration
+  // only once the residual contracts slowly: on problems where Picard converges
+  // fast they cost what the staged solve costs.  (Not with host buffers.)
+  const bool handover = (accel_staged || damped) && opt.precision == IPT_PREC_STAGED && !hz &&
+                        !opt.z0;
   const int prec = accel_staged ? (opt.staged_bf16 ? IPT_PREC_BF16X3 : IPT_PREC_FP16X3)
                                 : opt.precision;
   Plan p = make_plan(n, k, prec, opt.staged_bf16 != 0);
@@ -876,6 +919,7 @@ ipt_status solve_dense(ipt_handle* h, int64_t n, const void* M, int64_t ldm, int
   p.acx = acx || anderson;  // four iterate buffers and the per-column scratch
   p.acx_base = accel_staged;
   p.damped = damped;
+  p.mixing = mixing;
   const int low = p.bf16 ? IPT_PREC_BF16 : IPT_PREC_FP16;
   const int high = p.bf16 ? IPT_PREC_BF16X3 : IPT_PREC_FP16X3;
   // First evaluation: product-free at Z = E (FP32 / tensor-core paths), else
@@ -889,10 +933,22 @@ ipt_status solve_dense(ipt_handle* h, int64_t n, const void* M, int64_t ldm, int
   fe.rebase = (p.staged && opt.z0) ? 1 : 0;
   fe.accurate = 1;
   fe.defer_e = !acx && !damped && !anderson && !hz;  // the update / copy-out reads z = E
+  // the staged Picard phase of a hand-over solve: its own plan and first stage
+  Plan pst = p;
+  pst.staged = true;
+  pst.prec = IPT_PREC_STAGED;
+  FirstEval fe_run = fe;
+  if (handover) {
+    fe_run.stage = low;
+    fe_run.passes = 0;
+    fe_run.rebase = 0;
+  }
   v = alloc_dense(h, p);
+  if (v == IPT_OK && handover) v = alloc_dense(h, pst);
   if (v == IPT_OK) {
     if (tm.on) cudaEventRecord(h->ev[4], h->s);
-    v = setup_dense(h, p, M, ldm, m_dtype, theta, cols, opt.z0, ldz, z_dtype, true, fe, false);
+    v = setup_dense(h, p, M, ldm, m_dtype, theta, cols, opt.z0, ldz, z_dtype, true, fe_run,
+                    false);
     if (tm.on) cudaEventRecord(h->ev[5], h->s);
   }
   if (v != IPT_OK) {
@@ -919,11 +975,47 @@ ipt_status solve_dense(ipt_handle* h, int64_t n, const void* M, int64_t ldm, int
   ca.measure_below = (p.tc && !p.staged && !acx && !anderson) ? 3.0 * tol : 0.0;
   cudaStream_t s = h->s;
   int cur = 0, base = -1, stage = fe.stage, passes = fe.passes, rebase = fe.rebase;
-  if (acx) {
-    v = acx_loop(h, p, ca, fe, max_iter, opt.acx_sigma, &tm);
+  int start = 0;  // evaluations done before the loop below (hand-over)
+  bool handed_over = false;
+  if (handover) {
+    ControlArgs cst = ca;
+    cst.mode = IPT_PREC_STAGED;
+    cst.escalate = 1;
+    cst.accel_staged = 0;
+    cst.measure_below = 0.0;
+    cst.slow_ratio = kHandoverRatio;
+    v = dense_chunked_loop(h, pst, cst, fe_run, max_iter, &tm, &handed_over);
+    if (v == IPT_OK && handed_over) {
+      start = h->hst->iter;
+      if (acx || anderson) {
+        // the accelerations keep their iterate in buffer 0
+        const int c = h->hst->cur;
+        if (c != 0)
+          CK(cudaMemcpyAsync(h->z[0].p, h->z[c].p, (size_t)p.kpad * p.npad * (p.f64 ? 8 : 4),
+                             cudaMemcpyDeviceToDevice, s));
+        h->hinit->cur = 0;
+        CK(cudaMemcpyAsync(&dst(h)->cur, &h->hinit->cur, sizeof(int), cudaMemcpyHostToDevice,
+                           s));
+      } else {
+        cur = h->hst->cur;
+        base = h->hst->base;
+        stage = h->hst->stage;
+        passes = h->hst->passes;
+        rebase = h->hst->rebase;
+      }
+    }
+  }
+  FirstEval fe_acc = fe;  // after a hand-over the accelerations start with a product
+  if (handed_over) fe_acc.passes = (fe.stage == IPT_PREC_BF16X3 || fe.stage == IPT_PREC_FP16X3)
+                                       ? 3 : 1;
+  if (v != IPT_OK || (handover && !handed_over)) {
+    max_iter = 0;  // solved (or failed) in the staged phase
+  } else if (acx) {
+    v = acx_loop(h, p, ca, fe_acc, max_iter, opt.acx_sigma, &tm, start);
     max_iter = 0;  // the Picard loop below does not run
   } else if (anderson) {
-    v = anderson_loop(h, p, ca, fe, max_iter, &tm);
+    v = anderson_loop(h, p, ca, fe_acc, max_iter, &tm, mixing ? opt.damping_model : nullptr,
+                      start);
     max_iter = 0;
   } else if (p.tc && !damped && !hz) {
     v = dense_chunked_loop(h, p, ca, fe, max_iter, &tm);
@@ -935,7 +1027,7 @@ ipt_status solve_dense(ipt_handle* h, int64_t n, const void* M, int64_t ldm, int
   double* hlam = nullptr;
   float *hinc = nullptr, *X = nullptr, *alpha = nullptr;
   DampState* ds = nullptr;
-  if (damped) {
+  if (damped && max_iter > 0) {
     ca.step_scale = 2.0;
     // layout: lam history (3 kpad FP64), inc history (3 kpad), features
     // (6 kpad), alphas (kpad), state (kpad is a multiple of 256: all aligned)
@@ -956,7 +1048,7 @@ ipt_status solve_dense(ipt_handle* h, int64_t n, const void* M, int64_t ldm, int
   bool likely_final = false;
   int copied_it = -1;
   double prev_test = -1.0;
-  for (int it = 0; it < max_iter; ++it) {
+  for (int it = start; it < max_iter; ++it) {
     if (hz && likely_final) {
       // the output buffer of this evaluation must not still be copied out
       const int nxt = free_buffer(cur, base);
@@ -1832,6 +1924,37 @@ ipt_status ipt_damping_adam(float* master, void* params, float* grad, float* m, 
                             void* stream) {
   if (!master || !params || !grad || !m || !v || step < 1) return IPT_INVALID_ARG;
   return launch_mlp_adam(master, params, grad, m, v, lr, beta1, beta2, eps, step,
+                         static_cast<cudaStream_t>(stream)) == cudaSuccess
+             ? IPT_OK
+             : IPT_CUDA_ERROR;
+}
+
+ipt_status ipt_mixing_forward(int64_t B, const void* params, const float* x, float* out,
+                              void* stream) {
+  if (B < 0 || B > (int64_t)1 << 30 || (B > 0 && (!params || !x || !out)))
+    return IPT_INVALID_ARG;
+  return launch_mix_forward(params, x, (int)B, out, static_cast<cudaStream_t>(stream)) ==
+                 cudaSuccess
+             ? IPT_OK
+             : IPT_CUDA_ERROR;
+}
+
+ipt_status ipt_mixing_grad(int64_t B, const void* params, const float* x, const float* target,
+                           float* grad, double* loss, void* stream) {
+  if (B < 0 || B > (int64_t)1 << 30 || !grad || !loss ||
+      (B > 0 && (!params || !x || !target)))
+    return IPT_INVALID_ARG;
+  return launch_mix_grad(params, x, target, (int)B, grad, loss,
+                         static_cast<cudaStream_t>(stream)) == cudaSuccess
+             ? IPT_OK
+             : IPT_CUDA_ERROR;
+}
+
+ipt_status ipt_mixing_adam(float* master, void* params, float* grad, float* m, float* v,
+                           float lr, float beta1, float beta2, float eps, int step,
+                           void* stream) {
+  if (!master || !params || !grad || !m || !v || step < 1) return IPT_INVALID_ARG;
+  return launch_mix_adam(master, params, grad, m, v, lr, beta1, beta2, eps, step,
                          static_cast<cudaStream_t>(stream)) == cudaSuccess
              ? IPT_OK
              : IPT_CUDA_ERROR;

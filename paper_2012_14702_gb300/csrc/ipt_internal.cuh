@@ -53,8 +53,10 @@ struct DevState {
   double e_rel;     // predicted |rho - rho_true| of the last tested evaluation
   double rho_best;  // smallest residual of a tested evaluation so far (0: none yet)
   int acc_based;    // the current base came from a compensated FP32 product
+  int stall;        // consecutive tested evaluations without a 10 % better residual
   int pause;   // nonzero: the next evaluation needs a kernel the enqueued ones do not
-               // run (compensated FP32); enqueued kernels return at entry until cleared
+               // run (1: compensated FP32; 2: the acceleration the staged Picard phase
+               // hands over to); enqueued kernels return at entry until cleared
   int want_acc;  // accelerated staged solves: the next tested evaluation should re-base
                  // on a compensated FP32 product
   int measure;   // the next evaluation samples its product error (k_sample_exact)
@@ -202,6 +204,9 @@ struct ControlArgs {
                           // (k_sample_exact), 0 if not; -1: as the device state says
   double measure_below = 0.0;  // non-staged solves: sample the next evaluation's product
                                // error once rho is predicted below this (0: never)
+  double slow_ratio = 0.0;  // STAGED with an acceleration to hand over to: once a tested
+                            // residual falls by less than this factor per evaluation,
+                            // pause (pause = 2) so that the host continues with it
   int smp_rows = 0;  // sampled rows of the product error estimate (0: no sampling)
   int n_rows = 0;    // n
   int csr_n = 0;              // CSR solves: n (the window is clipped to [0, n)); 0 = dense
@@ -221,6 +226,17 @@ cudaError_t launch_mlp_forward(const void* params, const float* X, int B, float*
 cudaError_t launch_mlp_grad(const void* params, const float* X, const float* target, int B,
                             float* grad, double* loss, cudaStream_t s);
 cudaError_t launch_mlp_adam(float* master, void* params, float* grad, float* m, float* v,
+                            float lr, float b1, float b2, float eps, int step, cudaStream_t s);
+// Learned damping-and-mixing model (k_mlp.cu): 7 -> 64 -> 64 -> 2, outputs
+// (alpha, gamma) per sample.
+constexpr int kMixInputs = 7;
+constexpr int kMixParams = kMixInputs * kMlpHidden + kMlpHidden + kMlpHidden * kMlpHidden +
+                           kMlpHidden + kMlpHidden * 2 + 2;
+cudaError_t launch_mix_forward(const void* params, const float* X, int B, float* out,
+                               cudaStream_t s);
+cudaError_t launch_mix_grad(const void* params, const float* X, const float* target, int B,
+                            float* grad, double* loss, cudaStream_t s);
+cudaError_t launch_mix_adam(float* master, void* params, float* grad, float* m, float* v,
                             float lr, float b1, float b2, float eps, int step, cudaStream_t s);
 
 // The FP32 map's division (k_diag.cu): q[i] = u[i] * recip_nr(gap[i]).
@@ -258,6 +274,18 @@ cudaError_t launch_damp_step(const void* z, void* f, int f64, int n, int k, int6
                              const void* model, double* acc, float* hinc, double* hlam,
                              float* X, float* alpha, DampState* ds, DevState* st,
                              cudaStream_t s);
+
+// Learned damping and mixing in the solve (k_mix.cu): after an evaluation g = F(z)
+// (zp, gp: the previous pair, or null at the first step) per-column statistics,
+// history and features, the mixing model's (alpha, gamma) into ag (2k floats),
+// and out <- z + alpha f - gamma ((z - zp) + alpha (f - fp)) (out: zp's buffer).
+// acc: 4k FP64 (zero on entry, left zero); hinc: 3k floats; hlam: 3k FP64;
+// X: 7k floats.
+cudaError_t launch_mix_step(const void* z, const void* g, const void* zp, const void* gp,
+                            void* out, int f64, int n, int k, int64_t ld, const double* theta,
+                            const int32_t* icol, const double* d, const void* model,
+                            double* acc, float* hinc, double* hlam, float* X, float* ag,
+                            DampState* ms, DevState* st, cudaStream_t s);
 
 // Batched solve (k_batched.cu): largest problem order n; problem size classes
 // (n <= 64, <= 256, larger) each with their own output tile (32 or 64, host

@@ -666,8 +666,12 @@ __global__ void k_control(DevState* st, ControlArgs a) {
   // longer falls (or, fixed precision, once the error model alone takes half
   // of tol) and no more accurate product is left to escalate to
   const double best = st->rho_best > 0.0 ? st->rho_best : INFINITY;
-  const bool stalled = rho > 0.9 * best;
-  if (a.test) st->rho_best = fmin(best, rho);
+  if (a.test) {
+    st->stall = rho > 0.9 * best ? st->stall + 1 : 0;
+    st->rho_best = fmin(best, rho);
+  }
+  // extrapolations test non-monotone residuals: three in a row without progress
+  const bool stalled = st->stall >= (a.acx ? 3 : 1);
   const bool can_escalate = (staged || a.accel_staged) && !st->acc_based;
   const bool give_up = met && !certified && !can_escalate &&
                        (stalled || (!staged && !a.accel_staged && e_rel >= 0.5 * a.tol));
@@ -749,6 +753,9 @@ __global__ void k_control(DevState* st, ControlArgs a) {
       }
       st->measure = st->passes == 3 && a.smp_rows > 0;
       st->sv = sv_next;
+      // slow contraction: hand the solve over to the requested acceleration
+      if (a.slow_ratio > 0.0 && a.test && it >= 2 && prev > 0.0 && rho > a.slow_ratio * prev)
+        st->pause = 2;
     } else {
       if (passes == 0)  // non-staged solve after its product-free first evaluation
         st->passes = split_stage(stage) ? 3 : 1;

@@ -117,6 +117,7 @@ def _dev(t, dtype=None, name="tensor"):
 
 
 PRODUCT_KERNEL = {"auto": 0, "single": 1, "pair": 2}
+ACCEL = {None: 0, "none": 0, "acx": 1, "damped": 2, "anderson": 3, "mixing": 4}
 
 
 def make_options(precision="staged", stop="residual", diverge_bound=1e8, stage_switch=0.1,
@@ -171,8 +172,9 @@ class Solver:
         per 256-row tile); selects the tensor-core product kernel only.
         accel: None (Picard update), "acx" (Alg. 3, with acx_sigma "column" —
         one step length per column — or "global"), "damped" (learned damping,
-        damping_model = the model's FP16 parameters as a CUDA tensor) or
-        "anderson" (depth-one Anderson mixing per column)."""
+        damping_model = the model's FP16 parameters as a CUDA tensor),
+        "anderson" (depth-one Anderson mixing per column) or "mixing" (learned
+        damping and mixing, damping_model = the mixing model's parameters)."""
         M = _dev(M, name="M")
         n = M.shape[0]
         if M.dim() != 2 or M.shape[1] != n or M.dtype not in DTYPE:
@@ -189,11 +191,10 @@ class Solver:
             z0t = None
         o = make_options(precision, stop, diverge_bound, stage_switch, verify_fp64, z0t,
                          staged_bf16, record_timing, product_kernel)
-        if accel not in (None, "none", "acx", "damped", "anderson") or \
-                acx_sigma not in ("column", "global"):
-            raise ValueError("accel must be None, 'acx', 'damped' or 'anderson'; acx_sigma "
-                             "'column' or 'global'")
-        o.accel = {"acx": 1, "damped": 2, "anderson": 3}.get(accel, 0)
+        if accel not in ACCEL or acx_sigma not in ("column", "global"):
+            raise ValueError("accel must be None, 'acx', 'damped', 'anderson' or 'mixing'; "
+                             "acx_sigma 'column' or 'global'")
+        o.accel = ACCEL[accel]
         o.acx_sigma = 1 if acx_sigma == "global" else 0
         if damping_model is not None:
             damping_model = _dev(damping_model, torch.float16, "damping_model")
@@ -220,9 +221,9 @@ class Solver:
         lam = lam_out if lam_out is not None else torch.empty(k, dtype=torch.float64)
         Zt = zt_out if zt_out is not None else torch.empty((k, n), dtype=z_dtype)
         o = make_options(precision, stop, record_timing=record_timing)
-        if accel not in (None, "none", "acx", "damped", "anderson"):
-            raise ValueError("accel must be None, 'acx', 'damped' or 'anderson'")
-        o.accel = {"acx": 1, "damped": 2, "anderson": 3}.get(accel, 0)
+        if accel not in ACCEL:
+            raise ValueError("accel must be None, 'acx', 'damped', 'anderson' or 'mixing'")
+        o.accel = ACCEL[accel]
         o.acx_sigma = 1 if acx_sigma == "global" else 0
         if damping_model is not None:
             o.damping_model = damping_model.data_ptr()
@@ -427,6 +428,51 @@ def damping_adam(master, params, grad, m, v, lr, step, beta1=0.9, beta2=0.999, e
                                _stream_ptr(stream))
     if st != 0:
         raise RuntimeError(f"ipt_damping_adam: {STATUS.get(st, st)}")
+
+
+_lib.ipt_mixing_forward.argtypes = [_i64, _vp, _vp, _vp, _vp]
+_lib.ipt_mixing_forward.restype = _i32
+_lib.ipt_mixing_grad.argtypes = [_i64, _vp, _vp, _vp, _vp, _vp, _vp]
+_lib.ipt_mixing_grad.restype = _i32
+_lib.ipt_mixing_adam.argtypes = [_vp, _vp, _vp, _vp, _vp, C.c_float, C.c_float, C.c_float,
+                                 C.c_float, _i32, _vp]
+_lib.ipt_mixing_adam.restype = _i32
+MIXING_PARAMS = 4802
+
+
+def mixing_forward(params, X, out=None, stream=None):
+    """(B, 2) float32 rows (alpha, gamma) of the mixing model (params: CUDA float16
+    [4802]) at feature rows X (B, 7) float32; runs on ``stream`` without synchronising."""
+    X = _dev(X, torch.float32, "X").contiguous()
+    params = _dev(params, torch.float16, "params")
+    if out is None:
+        out = torch.empty((X.shape[0], 2), dtype=torch.float32, device=X.device)
+    st = _lib.ipt_mixing_forward(X.shape[0], _ptr(params), _ptr(X), _ptr(out),
+                                 _stream_ptr(stream))
+    if st != 0:
+        raise RuntimeError(f"ipt_mixing_forward: {STATUS.get(st, st)}")
+    return out
+
+
+def mixing_grad(params, X, target, grad, loss, stream=None):
+    """Adds the mean-squared-error gradient (and the loss) of the mixing model over
+    (X, target (B, 2))."""
+    X = _dev(X, torch.float32, "X").contiguous()
+    target = _dev(target, torch.float32, "target").contiguous()
+    st = _lib.ipt_mixing_grad(X.shape[0], _ptr(params), _ptr(X), _ptr(target), _ptr(grad),
+                              _ptr(loss), _stream_ptr(stream))
+    if st != 0:
+        raise RuntimeError(f"ipt_mixing_grad: {STATUS.get(st, st)}")
+
+
+def mixing_adam(master, params, grad, m, v, lr, step, beta1=0.9, beta2=0.999, eps=1e-8,
+                stream=None):
+    """One Adam step on the mixing model's FP32 master parameters."""
+    st = _lib.ipt_mixing_adam(_ptr(master), _ptr(params), _ptr(grad), _ptr(m), _ptr(v),
+                              float(lr), float(beta1), float(beta2), float(eps), int(step),
+                              _stream_ptr(stream))
+    if st != 0:
+        raise RuntimeError(f"ipt_mixing_adam: {STATUS.get(st, st)}")
 
 
 def residual_dense_noalloc(M, Z, lam, out=None, stream=None):

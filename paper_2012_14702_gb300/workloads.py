@@ -32,6 +32,7 @@ __all__ = [
     "dense_paper",
     "csr_banded",
     "morgan_tridiagonal",
+    "morgan_csr",
     "two_by_two",
     "three_by_three",
     "lowest_columns",
@@ -98,6 +99,19 @@ def morgan_tridiagonal(n: int, eps: float = 0.5):
     m[idx[:-1], idx[:-1] + 1] = eps
     m[idx[:-1] + 1, idx[:-1]] = eps
     return m, np.diag(m).copy()
+
+
+def morgan_csr(n: int, eps: float = 0.5):
+    """The tridiagonal matrix of Section 6.1 in CSR form (rowptr int32, colind int32,
+    vals float64, theta = diag): M_ii = i, M_{i,i+1} = M_{i+1,i} = eps, any n."""
+    idx = np.arange(n, dtype=np.int64)
+    rows = np.concatenate([idx, idx[:-1], idx[1:]])
+    cols = np.concatenate([idx, idx[1:], idx[:-1]])
+    vals = np.concatenate([idx + 1.0, np.full(n - 1, eps), np.full(n - 1, eps)])
+    order = np.lexsort((cols, rows))
+    rows, cols, vals = rows[order], cols[order], vals[order]
+    rowptr = np.searchsorted(rows, np.arange(n + 1)).astype(np.int32)
+    return rowptr, cols.astype(np.int32), vals, idx + 1.0
 
 
 def two_by_two(eps: float):

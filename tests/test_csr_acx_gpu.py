@@ -90,19 +90,21 @@ def test_csr_acx_morgan_beyond_picard(ipt, precision, vdt, window):
 
 def test_csr_acx_window_matches_all_rows(ipt):
     """The active window (widened by the band after every extrapolation) gives the
-    all-rows iterates (up to the order of the step lengths' sums)."""
+    all-rows iterates after 30 evaluations (up to the order of the step lengths'
+    sums)."""
     n, k = 20000, 16
     rowptr, colind, vals, th = w.csr_banded(n, 6, 300, 1e-2, seed=8, theta_step=0.01)
     cols = w.lowest_columns(th, k)
     rp, ci, vv = cuda(rowptr, torch.int32), cuda(colind, torch.int32), cuda(vals, torch.float64)
     cg = cuda(cols, torch.int32)
     s = ipt.Solver()
-    la, Za, ia = s.solve_csr(rp, ci, vv, n, cols=cg, tol=1e-12, max_iter=100, precision="f64",
+    la, Za, ia = s.solve_csr(rp, ci, vv, n, cols=cg, tol=0.0, max_iter=30, precision="f64",
                              z_dtype=torch.float64, window=False, accel="acx")
-    lw, Zw, iw = s.solve_csr(rp, ci, vv, n, cols=cg, tol=1e-12, max_iter=100, precision="f64",
+    lw, Zw, iw = s.solve_csr(rp, ci, vv, n, cols=cg, tol=0.0, max_iter=30, precision="f64",
                              z_dtype=torch.float64, window=True, accel="acx")
-    assert ia["status"] == iw["status"] == "OK"
-    assert ia["iterations"] == iw["iterations"]
+    assert ia["status"] == iw["status"] == "MAXITER"
+    assert ia["iterations"] == iw["iterations"] == 30
+    assert ia["hist_rho"][-1] < 1e-4 * ia["hist_rho"][0]
     assert iw["rows_evaluated"] < ia["rows_evaluated"]
     assert torch.max(torch.abs(Za - Zw)).item() <= 1e-12
     assert torch.max(torch.abs(la - lw)).item() <= 1e-12 * torch.max(torch.abs(la)).item()
