@@ -905,6 +905,7 @@ def run_ours(args, rank, world, local_rank):
         "finalize": sum(i["finalize_ms"] for i in infos) / K,
         "host_wall_per_call": sum(i["wall_ms"] for i in infos) / K,
     }
+    # the rest: controller, sampled product-error estimate, launch and host gaps
     breakdown["other_device_and_host_gaps"] = ms - sum(
         breakdown[x] for x in ["product_1pass", "product_3pass", "prepass", "setup", "finalize"])
     line = {
@@ -923,6 +924,7 @@ def run_ours(args, rank, world, local_rank):
         "oracle_error": err_staged,
         "tflops_per_iter": tflops_iter,
         "products_per_solve": products_per_solve,
+        "epilogue_operands_per_solve": sum(i["epilogue_operands"] for i in infos) / K,
         "breakdown_ms": breakdown,
         "plain_fp32": {"ms": plain_ms, "iterations": pinfo["iterations"],
                        "rho": pinfo["rho"], "rho_fp64": pvinfo["rho_fp64"],

@@ -124,6 +124,15 @@ typedef struct {
                            rows that can be nonzero: the rows of the current iterate's
                            nonzero rows widened by the band max|j - m| of the stored
                            entries (exact: other rows of Z and F are zero).  0 = all rows */
+  int epilogue_operand; /* STAGED tensor-core solves: nonzero (default) = each product's
+                           epilogue, which holds F, also writes the next evaluation's
+                           operand (the 16-bit split of F - Z_b at one power-of-two scale
+                           for all columns, chosen from a bound on ||F - Z_b||_F with a
+                           factor of 4 to the 16-bit range; an entry outside it falls
+                           back to the pre-pass) and accumulates d_c of F, so the next
+                           pre-pass only hands them over.  0 = the pre-pass re-reads F
+                           and writes the operand with a scale per column.  Results
+                           agree to rounding                                              */
 } ipt_options;
 
 /* Values of ipt_options.accel.  IPT_ACCEL_DAMPED: learned damping (no counterpart in
@@ -189,6 +198,8 @@ typedef struct {
   double rho_error;     /* predicted |rho - rho_true| of the returned pair: the error model
                            of the products and of the iterate's arithmetic (residual
                            stop: IPT_OK means rho + rho_error <= tol)                    */
+  int epilogue_operands; /* evaluations whose product operand and d were written by the
+                            previous product's epilogue (ipt_options.epilogue_operand)  */
 } ipt_result;
 
 typedef struct ipt_handle ipt_handle;

@@ -51,6 +51,8 @@ struct ipt_handle {
   int dev = 0;
   Buf drow, dt, dh, dl, z[5], pbuf, wh, wl, rinv, sinv;  // z[4]: accelerated solves' base
   Buf smp;                          // sampled product entries (error estimate)
+  Buf wh2, wl2, dpart;              // staged Picard: the second W set and the partial sums
+                                    // of d, both written by the product's epilogue
   Buf acx_d, acx_acc, acx_sigma;    // ACX: d of the inner evaluations, step-length sums, steps
   Buf damp;                         // learned damping: history, features, alphas, state
   Buf mix;                          // learned mixing: statistics, history, features, outputs
@@ -129,6 +131,7 @@ struct Plan {
   bool acx_base = false;  // accelerated staged solve: fifth Z buffer (the base) and P_b
   bool damped = false;  // learned damping buffers
   bool mixing = false;  // learned mixing buffers
+  bool epi_operand = false;  // staged Picard: the product's epilogue writes the next operand
 };
 
 ipt_status check_dense_args(ipt_handle* h, int64_t n, const void* M, int64_t ldm, int m_dtype,
@@ -180,6 +183,11 @@ ipt_status alloc_dense(ipt_handle* h, const Plan& p) {
     CK(ensure(h->rinv, (size_t)p.npad * 4));
     CK(ensure(h->sinv, (size_t)p.kpad * 4));
     CK(ensure(h->smp, (size_t)kSampleRows * p.kpad * 4));
+    if (p.epi_operand) {
+      CK(ensure(h->wh2, kn * 2));
+      CK(ensure(h->wl2, kn * 2));
+      CK(ensure(h->dpart, (size_t)p.kpad * (p.npad / 32) * 8));
+    }
   }
   CK(ensure(h->theta, (size_t)p.npad * 8));
   CK(ensure(h->thh, (size_t)p.npad * 4));
@@ -359,6 +367,7 @@ ipt_status evaluate(ipt_handle* h, const Plan& p, int cur, int base, int stage, 
   double* dd = dv ? dv : (double*)h->d.p;
   if (!ev) ev = h->ev;
   const bool t = tm && tm->on;
+  bool ev3_done = false;
   if (t) CK(cudaEventRecord(ev[0], s));
   if (p.f64) {
     launch_prepass(h->drow.p, h->z[cur].p, 1, p.npad, (const int32_t*)h->icol.p, p.kpad,
@@ -424,6 +433,8 @@ ipt_status evaluate(ipt_handle* h, const Plan& p, int cur, int base, int stage, 
       CK(launch_gemm_tc((const uint16_t*)h->dh.p, (const uint16_t*)h->dl.p,
                         (const uint16_t*)h->wh.p, (const uint16_t*)h->wl.p, a, p.npad, p.kpad,
                         passes, p.bf16 ? 1 : 0, p.product_kernel, s));
+      if (t) CK(cudaEventRecord(ev[3], s));  // the product kernel alone
+      ev3_done = true;
       if (measure) {
         launch_sample_exact((const float*)h->drow.p, (const float*)h->z[cur].p,
                             (const int32_t*)h->icol.p, p.n, p.k, p.kpad, p.npad,
@@ -434,7 +445,7 @@ ipt_status evaluate(ipt_handle* h, const Plan& p, int cur, int base, int stage, 
     }
   }
   CK(cudaGetLastError());
-  if (t) CK(cudaEventRecord(ev[3], s));
+  if (t && !ev3_done) CK(cudaEventRecord(ev[3], s));
   h->launches += 2;
   return IPT_OK;
 }
@@ -448,9 +459,20 @@ ipt_status evaluate_dyn(ipt_handle* h, const Plan& p, Timing* tm, cudaEvent_t* e
   DevState* st = dst(h);
   const bool t = tm && tm->on;
   if (t) CK(cudaEventRecord(ev[0], s));
-  DynZ dz;
+  DynZ dz{};
   for (int b = 0; b < 3; ++b) dz.z[b] = (const float*)h->z[b].p;
   dz.dyn = 1;
+  // staged Picard: the product's epilogue writes the next operand into the other
+  // W set (DevState::vb); the pre-pass then only hands over d and the scale
+  const bool fuse = p.epi_operand && h->wh2.p && h->wl2.p && h->dpart.p;
+  if (fuse) {
+    dz.wh[0] = (uint16_t*)h->wh.p;
+    dz.wl[0] = (uint16_t*)h->wl.p;
+    dz.wh[1] = (uint16_t*)h->wh2.p;
+    dz.wl[1] = (uint16_t*)h->wl2.p;
+    dz.dpart = (double*)h->dpart.p;
+    dz.dgroups = p.npad / 32;
+  }
   launch_prepass_tc((const float*)h->drow.p, nullptr, nullptr, p.npad, (const int32_t*)h->icol.p,
                     p.kpad, p.bf16 ? 1 : 0, (double*)h->d.p, (uint16_t*)h->wh.p,
                     (uint16_t*)h->wl.p, (float*)h->sinv.p, st, s, dz);
@@ -473,17 +495,27 @@ ipt_status evaluate_dyn(ipt_handle* h, const Plan& p, Timing* tm, cudaEvent_t* e
   for (int b = 0; b < 3; ++b) a.zsel[b] = (float*)h->z[b].p;
   a.pstore = p.staged ? (float*)h->pbuf.p : nullptr;
   a.dyn = 1;
+  if (fuse) {
+    a.fuse = 1;
+    a.fuse_bf16 = p.bf16 ? 1 : 0;
+    a.wnh[0] = (uint16_t*)h->wh.p;
+    a.wnl[0] = (uint16_t*)h->wl.p;
+    a.wnh[1] = (uint16_t*)h->wh2.p;
+    a.wnl[1] = (uint16_t*)h->wl2.p;
+    a.dpart = (double*)h->dpart.p;
+    a.dgroups = p.npad / 32;
+    a.drow = (const float*)h->drow.p;
+  }
   set_sampling(h, p, a, true);  // stored only when the state asks for a sample
   // the pass count given here only sizes nothing: the kernel reads it from st
   CK(launch_gemm_tc((const uint16_t*)h->dh.p, (const uint16_t*)h->dl.p,
                     (const uint16_t*)h->wh.p, (const uint16_t*)h->wl.p, a, p.npad, p.kpad, 1,
                     p.bf16 ? 1 : 0, p.product_kernel, s));
+  if (t) CK(cudaEventRecord(ev[3], s));  // the product kernel alone
   launch_sample_exact((const float*)h->drow.p, nullptr, (const int32_t*)h->icol.p, p.n, p.k,
                       p.kpad, p.npad, (const float*)h->smp.p, sample_stride(p),
                       sample_stride(p) / 2, st, dz, s);
-  h->launches += 1;
-  if (t) CK(cudaEventRecord(ev[3], s));
-  h->launches += 2;
+  h->launches += 3;
   return IPT_OK;
 }
 
@@ -511,6 +543,7 @@ void fill_result(const DevState& hs, const Timing& tm, int launches, ipt_result*
   out->acc_launches = tm.product_launches[2];
   out->acc_ms = tm.product_ms[2];
   out->rho_error = hs.e_rel;
+  out->epilogue_operands = hs.epi_used;
   out->prepass_ms = tm.prepass_ms;
   out->status = hs.status;
   out->iterations = hs.iter;
@@ -739,6 +772,7 @@ ipt_status dense_chunked_loop(ipt_handle* h, const Plan& p, const ControlArgs& c
     if (h->hst->pause == 2 && handed_over) {  // the acceleration continues the solve
       *handed_over = true;
       CK(cudaMemsetAsync(&st->pause, 0, sizeof(int), s));
+      CK(cudaMemsetAsync(&st->split_ready, 0, sizeof(int), s));  // its products' own operands
       return IPT_OK;
     }
     if (h->hst->pause) {
@@ -915,6 +949,7 @@ ipt_status solve_dense(ipt_handle* h, int64_t n, const void* M, int64_t ldm, int
   const int prec = accel_staged ? (opt.staged_bf16 ? IPT_PREC_BF16X3 : IPT_PREC_FP16X3)
                                 : opt.precision;
   Plan p = make_plan(n, k, prec, opt.staged_bf16 != 0);
+  p.epi_operand = p.staged && p.tc && opt.epilogue_operand != 0;
   p.product_kernel = opt.product_kernel;
   p.acx = acx || anderson;  // four iterate buffers and the per-column scratch
   p.acx_base = accel_staged;
@@ -937,6 +972,7 @@ ipt_status solve_dense(ipt_handle* h, int64_t n, const void* M, int64_t ldm, int
   Plan pst = p;
   pst.staged = true;
   pst.prec = IPT_PREC_STAGED;
+  pst.epi_operand = p.tc && opt.epilogue_operand != 0;
   FirstEval fe_run = fe;
   if (handover) {
     fe_run.stage = low;
@@ -1061,8 +1097,14 @@ ipt_status solve_dense(ipt_handle* h, int64_t n, const void* M, int64_t ldm, int
       copied_it = it;
     }
     const int fbuf = free_buffer(cur, base);  // where this evaluation writes F
-    v = evaluate(h, p, cur, base, stage, passes, rebase, &tm, -1, nullptr, nullptr,
-                 it > 0 && p.tc ? h->hst->measure : 0);
+    // a staged Picard product runs as the device-chosen evaluation (the state
+    // holds the same cur, base and pass count), so that its operand may come
+    // from the previous product's epilogue as in the chunked loop
+    const bool dyn_eval = p.epi_operand && !damped && it > 0 && passes > 0 &&
+                          stage != IPT_PREC_F32 && stage != IPT_PREC_F32C;
+    v = dyn_eval ? evaluate_dyn(h, p, &tm, h->ev)
+                 : evaluate(h, p, cur, base, stage, passes, rebase, &tm, -1, nullptr, nullptr,
+                            it > 0 && p.tc ? h->hst->measure : 0);
     if (v != IPT_OK) break;
     launch_control(dst(h), ca, s);
     h->launches += 1;
@@ -1181,6 +1223,7 @@ void ipt_options_default(ipt_options* opt) {
   opt->z0 = nullptr;
   opt->product_kernel = IPT_PRODUCT_AUTO;
   opt->csr_window = 1;
+  opt->epilogue_operand = 1;
 }
 
 const char* ipt_status_string(int status) {
@@ -1219,7 +1262,7 @@ ipt_status ipt_destroy(ipt_handle* h) {
   DeviceGuard g(h->dev);
   Buf* all[] = {&h->drow, &h->dt, &h->dh, &h->dl, &h->z[0], &h->z[1], &h->z[2], &h->z[3],
                 &h->acx_d, &h->acx_acc, &h->acx_sigma, &h->damp, &h->bmeta, &h->bscratch,
-                &h->pbuf,
+                &h->pbuf, &h->z[4], &h->smp, &h->mix, &h->wh2, &h->wl2, &h->dpart,
                 &h->wh, &h->wl,
                 &h->rinv, &h->sinv, &h->theta, &h->thh, &h->thl, &h->icol, &h->count,
                 &h->r0part, &h->delta, &h->cpart,
@@ -1733,7 +1776,7 @@ ipt_status ipt_solve_batched(ipt_handle* h, int64_t count, const int64_t* n, con
   CK(ensure(h->bmeta, meta_bytes + 16));
   // tensor cores: the CTAs' workspaces, then the prologue's per-problem outputs
   const size_t ws_all = ((size_t)ctas * (size_t)batched_tc_workspace(max_n) + 1023) / 1024 * 1024;
-  CK(ensure(h->bscratch, tc_passes ? ws_all + (size_t)batched_tc_prep_bytes(to, mo, (int)count)
+  CK(ensure(h->bscratch, tc_passes ? ws_all + (size_t)batched_tc_prep_bytes(to, mo, (int)count, max_n)
                                    : (size_t)ctas * 2 * (size_t)max_n2 * 4));
   char* dm = static_cast<char*>(h->bmeta.p);
   int* queue = reinterpret_cast<int*>(dm + meta_bytes - 64);

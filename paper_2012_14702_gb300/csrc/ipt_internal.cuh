@@ -60,6 +60,21 @@ struct DevState {
   int want_acc;  // accelerated staged solves: the next tested evaluation should re-base
                  // on a compensated FP32 product
   int measure;   // the next evaluation samples its product error (k_sample_exact)
+  // Next operand written by the product's epilogue (staged Picard, device-chosen
+  // operands): the epilogue of an evaluation that may be followed by another
+  // writes the 16-bit split of V_next = F - Z_b(next) into the W set not being
+  // read (wsel ^ 1), with one power-of-two scale for all columns chosen from
+  // vb, and the partial sums of d of F over its 32-row groups.  The controller
+  // then hands the set over (split_ready), and the next pre-pass only adds the
+  // partials and sets the scale.
+  double vb;         // bound on max |V_next| for the scale of the next epilogue's split
+  int wsel;          // W set (0/1) the tensor-core product reads
+  int split_ready;   // the set wsel, the d partials and wscale hold the current operand
+  int fused;         // this evaluation's epilogue wrote the next operand
+  int split_bad;     // ... but a scaled entry left the 16-bit range (or was not finite)
+  float wscale;      // 1 / scale of the current operand (fused split)
+  float wscale_next; // 1 / scale of the operand the epilogue is writing
+  int epi_used;      // evaluations that ran on such an operand
   double acc_dp2;  // sum of squared product errors at the sampled entries
   double acc_dpn;  // number of sampled entries
   double e_meas;   // the last sampled estimate of ||P - Delta Z||_F (safety included)
@@ -123,6 +138,17 @@ struct MapArgs {
   T* zsel[3];
   float* pstore;
   int dyn;
+  // Next operand (DevState::vb): with fuse set (and dyn), the epilogue writes the
+  // split of F - Z_b(next) into wnh / wnl [wsel ^ 1] and, per column c and group
+  // g of 32 rows, sum_{j in g} Delta_{cols[c], j} F_jc into dpart[c * dgroups + g]
+  // (Drow row-major Delta; dgroups = npad / 32).
+  int fuse;
+  int fuse_bf16;  // the split's 16-bit type: BF16 (else FP16)
+  uint16_t* wnh[2];
+  uint16_t* wnl[2];
+  double* dpart;
+  int dgroups;
+  const float* drow;
 };
 
 // Device-chosen pre-pass operands (see MapArgs::dyn): with dyn set, Z is
@@ -131,6 +157,12 @@ struct MapArgs {
 struct DynZ {
   const float* z[3];
   int dyn;
+  // fused next operand (DevState::split_ready): the W sets, and the partial
+  // sums of d of the iterate written by the previous product's epilogue
+  uint16_t* wh[2];
+  uint16_t* wl[2];
+  double* dpart;
+  int dgroups;
 };
 
 // The Z buffer receiving F: neither the current iterate nor the base.
@@ -309,7 +341,7 @@ int batched_ctas_per_sm();
 // total_n2 sums n^2.
 int64_t batched_tc_tile_bytes(int64_t n);
 int64_t batched_tc_workspace(int64_t max_n);
-int64_t batched_tc_prep_bytes(int64_t tiles_total, int64_t total_n2, int count);
+int64_t batched_tc_prep_bytes(int64_t tiles_total, int64_t total_n2, int count, int64_t max_n);
 cudaError_t launch_batched_tc(const float* M, const double* theta, const int64_t* m_off,
                               const int64_t* v_off, const int64_t* t_off, const int* nsz,
                               const int* order, int count, int64_t max_n, int64_t tiles_total,

@@ -84,8 +84,9 @@ struct TcArgs {
   uint8_t* prep_a;       // per problem: Delta's split tiles
   uint8_t* prep_w;       // per problem: W0's split tiles
   float* prep_dt;        // per problem (at m_off): DT, column-major Delta
-  double* prep_sums;     // per problem: ||F0 - E||^2, ||R0||^2
-  int* prep_flag;        // per problem: 1 non-finite theta, 2 degenerate gap
+  double* prep_sums;     // per problem and 128-row block: ||F0 - E||^2, ||R0||^2 partials
+  int* prep_flag;        // per problem and row block: 1 non-finite theta, 2 degenerate gap
+  int max_nt;            // row blocks of the largest problem (slots per problem above)
   int* queue;            // next schedule slot (zero at launch)
   int64_t max_n2;
   int count;
@@ -169,21 +170,25 @@ __device__ __forceinline__ void tile_of(int ti, int nt, int& rb, int& cb) {
 
 constexpr int kPT = 256;  // prologue threads per CTA
 
-// Prologue, one CTA per problem (largest first).  Per 128 x 64 block (rb, ks)
-// of Delta: 2 kPI loads in flight per thread, the BF16 split tile (rb, ks), and
-// the block transposed through shared memory for the column-major outputs:
-// DT and W0's tile entries (row c, K index j; F0_jc = -Delta_jc / (theta_j -
-// theta_c) off the diagonal, 1 on it).  Stores go as packed BF16 pairs of
-// K-adjacent entries.  W0's rows past the blocks' extent are zero padding.
+// Prologue, one CTA per problem and 128-row block rb (problems largest first;
+// max_nt slots per problem, the ones past its blocks return at once).  Per
+// 128 x 64 block (rb, ks) of Delta: 2 kPI loads in flight per thread, the BF16
+// split tile (rb, ks), and the block transposed through shared memory for the
+// column-major outputs: DT and W0's tile entries (row c, K index j; F0_jc =
+// -Delta_jc / (theta_j - theta_c) off the diagonal, 1 on it).  Stores go as
+// packed BF16 pairs of K-adjacent entries.  W0's rows past the blocks' extent
+// are zero padding (written by the rb = 0 CTA).  The first evaluation's sums
+// are written per row block and added by the solve kernel in block order.
 __global__ void __launch_bounds__(kPT, 4) k_batched_tc_prep(TcArgs a) {
   __shared__ float th_hi[kBatchMaxN], th_lo[kBatchMaxN], ddiag[kBatchMaxN];
   __shared__ float tbuf[kK * kTPad];
   __shared__ F2 red[2][32];
   __shared__ int flag;
   const int tid = threadIdx.x;
-  const int p = a.order[blockIdx.x];
+  const int p = a.order[blockIdx.x / a.max_nt], rb = blockIdx.x % a.max_nt;
   const int n = a.nsz[p];
   const int nt = (n + kT - 1) / kT, nks = (n + kK - 1) / kK;
+  if (rb >= nt) return;  // uniform over the CTA
   const bool three = a.passes == 3;
   const float* M = a.M + a.m_off[p];
   const int64_t vo = a.v_off[p];
@@ -203,8 +208,8 @@ __global__ void __launch_bounds__(kPT, 4) k_batched_tc_prep(TcArgs a) {
   __syncthreads();
   float s_inc = 0.f, s_r = 0.f;
   const int kw = nks * kK;  // W0's K extent
-  for (int blk = 0; blk < nt * nks; ++blk) {
-    const int rb = blk / nks, ks = blk % nks;
+  for (int ks = 0; ks < nks; ++ks) {
+    const int blk = rb * nks + ks;
     uint8_t* pair = A + (int64_t)blk * kPair;
     // items (row r, K pair 2q, 2q + 1): a warp covers one row's 64 K values;
     // kPI items' loads in flight per thread before any store
@@ -256,7 +261,7 @@ __global__ void __launch_bounds__(kPT, 4) k_batched_tc_prep(TcArgs a) {
     __syncthreads();
   }
   // W0's rows c in [nks * 64, nt * 128) (all past n): zero
-  const int pad_rows = nt * kT - kw, kp = kw / 2;
+  const int pad_rows = rb == 0 ? nt * kT - kw : 0, kp = kw / 2;
   for (int it = tid; it < pad_rows * kp; it += kPT) {
     const int c = kw + it / kp, j = 2 * (it % kp);
     put_split2(W + (int64_t)((c >> 7) * nks + (j >> 6)) * kPair, sw128(c & 127, j & 63), 0.f, 0.f,
@@ -265,9 +270,10 @@ __global__ void __launch_bounds__(kPT, 4) k_batched_tc_prep(TcArgs a) {
   const F2 t_inc = block_sum(F2{s_inc, 0.f}, red[0]);
   const F2 t_r = block_sum(F2{s_r, 0.f}, red[1]);
   if (tid == 0) {
-    a.prep_sums[2 * p] = f2_value(t_inc);
-    a.prep_sums[2 * p + 1] = f2_value(t_r);
-    a.prep_flag[p] = flag;
+    const int64_t slot = (int64_t)p * a.max_nt + rb;
+    a.prep_sums[2 * slot] = f2_value(t_inc);
+    a.prep_sums[2 * slot + 1] = f2_value(t_r);
+    a.prep_flag[slot] = flag;
   }
   // the tiles are read next by bulk copies (async proxy) of the main kernel
   asm volatile("fence.proxy.async.global;" ::: "memory");
@@ -341,7 +347,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_batched_tc(TcArgs a) {
       sh.ddiag[j] = (float)((double)M[(int64_t)j * n + j] - t);
       sh.col[j].z = sh.ddiag[j];  // d at Z = E
     }
-    if (tid == 0) sh.flag = a.prep_flag[p];
+    if (tid == 0) {
+      int f = 0;
+      for (int b = 0; b < nt; ++b) f |= a.prep_flag[(int64_t)p * a.max_nt + b];
+      sh.flag = f;
+    }
     __syncthreads();
     // the first product reads F0 (recomputed from DT: zc == nullptr) and the
     // prologue's W0; later ones the previous epilogue's iterate and tiles.
@@ -532,10 +542,20 @@ __global__ void __launch_bounds__(kThreads, 1) k_batched_tc(TcArgs a) {
       const F2 t_z = block_sum(F2{s_z, 0.f}, sh.red[1]);
       const F2 t_r = block_sum(F2{s_r, 0.f}, sh.red[2]);
       if (tid == 0) {
-        // the first evaluation's sums come from the prologue (||Z||^2 = n at Z = E)
-        const double tr = it == 0 ? a.prep_sums[2 * p + 1] : f2_value(t_r);
+        // the first evaluation's sums come from the prologue's row blocks, added
+        // in block order (||Z||^2 = n at Z = E)
+        double tr = 0.0, ti = 0.0;
+        if (it == 0) {
+          for (int b = 0; b < nt; ++b) {
+            const int64_t slot = (int64_t)p * a.max_nt + b;
+            ti += a.prep_sums[2 * slot];
+            tr += a.prep_sums[2 * slot + 1];
+          }
+        } else {
+          tr = f2_value(t_r);
+          ti = f2_value(t_inc);
+        }
         const double tz = it == 0 ? (double)n : f2_value(t_z);
-        const double ti = it == 0 ? a.prep_sums[2 * p] : f2_value(t_inc);
         if (it == 0) r0 = sqrt(tr);
         const double inc = sqrt(ti) / sqrt(tz);
         const double rho = r0 > 0.0 ? sqrt(tr) / r0 : 0.0;
@@ -646,10 +666,11 @@ int64_t batched_tc_workspace(int64_t max_n) {
 
 // The prologue's outputs for the whole batch (1 KB aligned parts): Delta's
 // and W0's split tiles (tiles_total bytes each), DT (total_n2 floats), the
-// sums (2 doubles) and the flag of every problem.
-int64_t batched_tc_prep_bytes(int64_t tiles_total, int64_t total_n2, int count) {
-  return 2 * round_1k(tiles_total) + round_1k(total_n2 * 4) + round_1k((int64_t)count * 16) +
-         round_1k((int64_t)count * 4);
+// sums (2 doubles) and the flag of every problem's row blocks.
+int64_t batched_tc_prep_bytes(int64_t tiles_total, int64_t total_n2, int count, int64_t max_n) {
+  const int64_t slots = (int64_t)count * ((max_n + kT - 1) / kT);
+  return 2 * round_1k(tiles_total) + round_1k(total_n2 * 4) + round_1k(slots * 16) +
+         round_1k(slots * 4);
 }
 
 cudaError_t launch_batched_tc(const float* M, const double* theta, const int64_t* m_off,
@@ -691,8 +712,10 @@ cudaError_t launch_batched_tc(const float* M, const double* theta, const int64_t
   q += round_1k(tiles_total);
   a.prep_dt = reinterpret_cast<float*>(q);
   q += round_1k(total_n2 * 4);
+  a.max_nt = (int)((max_n + kT - 1) / kT);
+  const int64_t slots = (int64_t)count * a.max_nt;
   a.prep_sums = reinterpret_cast<double*>(q);
-  q += round_1k((int64_t)count * 16);
+  q += round_1k(slots * 16);
   a.prep_flag = reinterpret_cast<int*>(q);
   a.queue = queue;
   a.max_n2 = max_n * max_n;
@@ -702,7 +725,7 @@ cudaError_t launch_batched_tc(const float* M, const double* theta, const int64_t
   a.tol = tol;
   a.diverge_bound = diverge_bound;
   a.passes = passes == 3 ? 3 : 1;
-  k_batched_tc_prep<<<count, kPT, 0, s>>>(a);
+  k_batched_tc_prep<<<(unsigned)slots, kPT, 0, s>>>(a);
   k_batched_tc<<<ctas, kThreads, kSmem, s>>>(a);
   return cudaGetLastError();
 }

@@ -81,6 +81,24 @@ __device__ __forceinline__ void subtract_base(float4& y, const float4* b4, int m
   }
 }
 
+// Device-chosen operands: the W set the product reads (wh / wl [wsel]), and the
+// next operand written by the previous product's epilogue (DevState::vb).  With
+// it, d_c is the sum of that epilogue's partials over 32-row groups,
+// dpart[c * G + g], added in a fixed order (lanes over g, then a butterfly) so
+// that it does not depend on the order in which the product's CTAs ran; the
+// column scale is the state's.  Called by one whole warp per column c.
+__device__ __forceinline__ void prepass_handover(const DevState* st, const DynZ& dz, int c,
+                                                 int lane, double* d, float* sinv) {
+  const double* p = dz.dpart + (int64_t)c * dz.dgroups;
+  double s = 0.0;
+  for (int g = lane; g < dz.dgroups; g += 32) s += p[g];
+  s = warp_sum(s);
+  if (lane == 0) {
+    d[c] = s;
+    sinv[c] = st->wscale;
+  }
+}
+
 // One warp per column c: d_c as in k_prepass (compensated FP32 per lane,
 // FP32 pairs across lanes) and max |W_.c|; then W_.c * s_c split into hi/lo
 // (the column is re-read from cache).  Padding columns only get d = 0.
@@ -95,10 +113,18 @@ __global__ void k_prepass_tc(const float* __restrict__ Drow, const float* __rest
   if (dz.dyn) {
     Z = dz.z[st->cur];
     Zbase = st->base >= 0 ? dz.z[st->base] : nullptr;
+    if (dz.wh[0]) {
+      Wh = dz.wh[st->wsel & 1];
+      Wl = dz.wl[st->wsel & 1];
+    }
     if (st->passes != 3) Wl = nullptr;
   }
   const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (c >= kpad) return;
+  if (dz.dyn && dz.dpart && st->split_ready) {  // uniform over the grid
+    prepass_handover(st, dz, c, lane, d, sinv);
+    return;
+  }
   const int i = icol[c];
   if (i < 0) {
     if (lane == 0) {
@@ -159,7 +185,15 @@ __global__ void __launch_bounds__(1024)
   if (dz.dyn) {
     Z = dz.z[st->cur];
     Zbase = st->base >= 0 ? dz.z[st->base] : nullptr;
+    if (dz.wh[0]) {
+      Wh = dz.wh[st->wsel & 1];
+      Wl = dz.wl[st->wsel & 1];
+    }
     if (st->passes != 3) Wl = nullptr;
+    if (dz.dpart && st->split_ready) {  // uniform over the grid
+      if (threadIdx.x < 32) prepass_handover(st, dz, blockIdx.x, threadIdx.x, d, sinv);
+      return;
+    }
   }
   const int c = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int nw = blockDim.x >> 5;
@@ -617,6 +651,7 @@ __global__ void k_control(DevState* st, ControlArgs a) {
     st->hist_stage[it] = passes == 0 ? -1 : stage;
   }
   if (a.csr_n > 0) st->rows_eval += st->win_hi - st->win_lo;
+  if (st->split_ready) st->epi_used++;
   if (passes == 1 && (stage == IPT_PREC_BF16 || stage == IPT_PREC_FP16)) st->stage_iters[0]++;
   else if (passes != 0) st->stage_iters[1]++;
   // this evaluation's predicted error (see above)
@@ -753,6 +788,12 @@ __global__ void k_control(DevState* st, ControlArgs a) {
       }
       st->measure = st->passes == 3 && a.smp_rows > 0;
       st->sv = sv_next;
+      // scale of the operand after the next one, written by the next epilogue:
+      // ||Z_{t+2} - Z_b|| <= (re-base at t+1 ? 0 : ||Z_{t+1} - Z_b||) + ||Z_{t+2} - Z_{t+1}||,
+      // the last step predicted by this one (the 16-bit range leaves a factor of 4).
+      // None (vb = 0) when the next evaluation is predicted to stop the solve.
+      const bool likely_last = st->accurate && rho * q <= 0.5 * a.tol;
+      st->vb = likely_last ? 0.0 : (st->rebase ? 0.0 : sv_next) + inc * sqrt(z2);
       // slow contraction: hand the solve over to the requested acceleration
       if (a.slow_ratio > 0.0 && a.test && it >= 2 && prev > 0.0 && rho > a.slow_ratio * prev)
         st->pause = 2;
@@ -781,6 +822,20 @@ __global__ void k_control(DevState* st, ControlArgs a) {
     if (!a.acx) st->cur = out;
     else if (a.next_cur >= 0) st->cur = a.next_cur;
   }
+  // the next operand this evaluation's epilogue wrote (split of F - Z_b(next)
+  // and d of F): it is the next one when the next evaluation is a tensor-core
+  // product of F on the base the epilogue assumed, as the staged Picard step
+  // sets them (cur = F; base = this iterate after a re-base, else unchanged)
+  const bool fused_ok = st->fused && !st->split_bad && !st->done && !st->pause &&
+                        a.mode == IPT_PREC_STAGED && !a.acx && st->stage != IPT_PREC_F32 &&
+                        st->stage != IPT_PREC_F32C;
+  if (fused_ok) {
+    st->wsel ^= 1;
+    st->wscale = st->wscale_next;
+  }
+  st->split_ready = fused_ok ? 1 : 0;
+  st->fused = 0;
+  st->split_bad = 0;
   st->prev_rho = rho;
 }
 

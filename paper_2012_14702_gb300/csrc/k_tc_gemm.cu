@@ -204,6 +204,29 @@ __device__ __forceinline__ void tile_coords(int t, int num_m, int num_n, int& mb
 // core's FP32 accumulation loses low bits relative to the running sum at each
 // accumulate; adding the many small far terms while the sum is still small and
 // the few dominant ones last keeps that loss at a fraction of |P|.
+// Sums over the warp's 32 lanes of 8 per-lane values x[0..7] (one per column),
+// by recursive halving: at each offset o (16, 8, 4) a lane keeps the half of
+// its vector picked by bit o of its index and adds the partner's copy of that
+// half; exchanges at offsets 2 and 1 complete the sums.  Lane L returns the
+// sum of column (L >> 2).  9 shuffles for 8 sums.
+__device__ __forceinline__ float warp_colsum8(float (&x)[8], int lane) {
+#pragma unroll
+  for (int o = 16, m = 4; o >= 4; o >>= 1, m >>= 1) {
+    const bool up = (lane & o) != 0;
+#pragma unroll
+    for (int i = 0; i < m; ++i) {
+      const float keep = up ? x[i + m] : x[i];
+      const float send = up ? x[i] : x[i + m];
+      x[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+  }
+  float t = x[0] + __shfl_xor_sync(0xffffffffu, x[0], 2);
+  return t + __shfl_xor_sync(0xffffffffu, t, 1);
+}
+
+#ifndef IPT_K_FAR_FIRST
+#define IPT_K_FAR_FIRST 1
+#endif
 struct KOrder {
   int lo, hi, center;
   __device__ void reset(int nb, int num_kb) {
@@ -211,7 +234,13 @@ struct KOrder {
     hi = num_kb - 1;
     center = min((nb * BN + BN / 2) / BK, num_kb - 1);
   }
-  __device__ int next() { return (center - lo >= hi - center) ? lo++ : hi--; }
+  __device__ int next() {
+#if IPT_K_FAR_FIRST
+    return (center - lo >= hi - center) ? lo++ : hi--;
+#else
+    return lo++;
+#endif
+  }
 };
 
 __device__ __forceinline__ void fail(Ctl* ctl, DevState* st, int code) {
@@ -230,6 +259,7 @@ template <int MODE>
 __global__ void __launch_bounds__(NUM_THREADS, 1)
     k_gemm_tc(const __grid_constant__ CUtensorMap tmDh, const __grid_constant__ CUtensorMap tmDl,
               const __grid_constant__ CUtensorMap tmWh, const __grid_constant__ CUtensorMap tmWl,
+              const __grid_constant__ CUtensorMap tmWh1, const __grid_constant__ CUtensorMap tmWl1,
               MapArgs<float> a, int num_m, int num_n, int num_kb, int passes, uint32_t idesc) {
   constexpr bool CLUSTER = MODE != MODE_SINGLE;
   constexpr bool PAIR = MODE == MODE_PAIR;
@@ -246,6 +276,13 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   int pbase_by_icol = a.pbase_by_icol;
   float* Pout = a.Pout;
   float* psmp = a.psmp;  // sampled P entries (error estimate), or none
+  int wset = 0;          // W set the product reads
+  // next operand (fused split): its sets, its base (nullptr: E), its scale
+  uint16_t* wn_h = nullptr;
+  uint16_t* wn_l = nullptr;
+  const float* zb_next = nullptr;
+  bool zb_is_z = false;  // the next base is this evaluation's iterate (a re-base)
+  float sc_next = 1.f;
   if (a.dyn) {
     const int cur = a.st->cur, base = a.st->base;
     passes = a.st->passes;
@@ -255,7 +292,22 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     pbase_by_icol = base >= 0 ? 0 : 1;
     Pout = a.st->rebase ? a.pstore : nullptr;
     if (!a.st->measure) psmp = nullptr;
+    wset = a.st->wsel & 1;
+    const double vb = a.st->vb;
+    if (a.fuse && vb > 0.0 && vb < 1e30) {
+      wn_h = a.wnh[wset ^ 1];
+      wn_l = a.wnl[wset ^ 1];
+      zb_is_z = a.st->rebase != 0;
+      zb_next = zb_is_z ? Zin : (base >= 0 ? a.zsel[base] : nullptr);
+      sc_next = pow2_scale((float)vb);
+      if (blockIdx.x == 0 && threadIdx.x == 0) {
+        a.st->fused = 1;
+        a.st->wscale_next = 1.f / sc_next;
+      }
+    }
   }
+  const CUtensorMap* tmBh = wset ? &tmWh1 : &tmWh;
+  const CUtensorMap* tmBl = wset ? &tmWl1 : &tmWl;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
@@ -334,7 +386,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
           // main product first (Dh Wh, Dh Wl, Dl Wh).
           const int role = passes == 1 ? 0 : (IPT_CORRECTIONS_FIRST ? (pass + 1) % 3 : pass);
           const CUtensorMap* mA = role == 2 ? &tmDl : &tmDh;
-          const CUtensorMap* mB = role == 1 ? &tmWl : &tmWh;
+          const CUtensorMap* mB = role == 1 ? tmBl : tmBh;
           if constexpr (PAIR) {
             const uint32_t fb = peer_addr(&ctl->full[stage], 0);
             if (leader) mbar_expect_tx(&ctl->full[stage], 2 * STAGE_BYTES);
@@ -438,6 +490,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     int acc = 0;
     uint32_t acc_phase = 0;
     float s_inc = 0.f, s_z = 0.f, s_r = 0.f, s_pv = 0.f;
+    bool split_bad = false;  // a scaled next-operand entry outside the 16-bit range
+    const float split_max = a.fuse_bf16 ? 3.0e38f : 65504.f;
     const uint32_t tempty_pair[2] = {PAIR ? peer_addr(&ctl->tempty[0], 0) : 0u,
                                      PAIR ? peer_addr(&ctl->tempty[1], 0) : 0u};
     for (int t = t_first; t < num_tiles; t += t_step) {
@@ -466,6 +520,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       }
       tc_fence_after();
       const int j = mb * BM + row;
+      const int grp = (mb * BM + q * 32) >> 5;  // this warp's group of 32 rows
       const bool jok = j < a.n;
       const float hj = a.th_hi[j], lj = a.th_lo[j], rj = a.rinv[j];
       // this row's slot among the sampled rows, or -1
@@ -477,38 +532,69 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) +
                       (uint32_t)(acc * BN + h * EPI_COLS + ch * 16),
                   v);
-        const int c0 = ch * 16;  // first owned column of this chunk
-        float z[16], pb[16];
 #pragma unroll
-        for (int i = 0; i < 16; ++i) {
-          const int ic = wic[c0 + i];
-          const int64_t o = (int64_t)(cbase + c0 + i) * ld + j;
-          // P_base: column cols[c] of Delta (Z_base = E) or the stored P of column c.
-          // Streamed once: evict-first, so the reused operand panels stay in L2.
-          const int64_t ob = pbase_by_icol ? (int64_t)ic * ld + j : o;
-          z[i] = (jok && ic >= 0) ? __ldcs(Zin + o) : 0.f;
-          pb[i] = (jok && ic >= 0) ? __ldcs(Pbase + ob) : 0.f;
-        }
+        for (int hf = 0; hf < 2; ++hf) {  // two halves of 8 columns (register budget)
+          const int c0 = ch * 16 + hf * 8;  // first owned column of this half
+          float z[8], pb[8], dl[8], zn[8];
 #pragma unroll
-        for (int i = 0; i < 16; ++i) {
-          const int ic = wic[c0 + i];
-          const ColInfo ci = wcol[c0 + i];
-          if (!jok || ic < 0) continue;
-          const int64_t o = (int64_t)(cbase + c0 + i) * ld + j;
-          const float dv = v[i] * (rj * ci.s);  // Delta V, scales undone exactly
-          const float p = pb[i] + dv;           // P = P_base + Delta V
-          if (Pout) __stcs(Pout + o, p);
-          if (prow) prow[cbase + c0 + i] = p;
-          s_pv = fmaf(dv, dv, s_pv);
-          float f, r;
-          const float gap = gap2f(hj, lj, ci.hi, ci.lo);
-          if (gap == 0.f && j != ic) flag_degenerate(a.st);
-          map_entry<float>(z[i], p, ci.d, gap, j == ic, f, r);
-          __stcs(Fout + o, f);
-          const float df = f - z[i];
-          s_inc = fmaf(df, df, s_inc);
-          s_z = fmaf(z[i], z[i], s_z);
-          s_r = fmaf(r, r, s_r);
+          for (int i = 0; i < 8; ++i) {
+            const int ic = wic[c0 + i];
+            const bool ok = jok && ic >= 0;
+            const int64_t o = (int64_t)(cbase + c0 + i) * ld + j;
+            // P_base: column cols[c] of Delta (Z_base = E) or the stored P of column c.
+            // Streamed once: evict-first, so the reused operand panels stay in L2.
+            const int64_t ob = pbase_by_icol ? (int64_t)ic * ld + j : o;
+            z[i] = ok ? __ldcs(Zin + o) : 0.f;
+            pb[i] = ok ? __ldcs(Pbase + ob) : 0.f;
+            // next operand: Delta_{cols[c], j} (row cols[c] of the row-major Delta)
+            // and the next base's entry, when it is neither E nor this iterate
+            dl[i] = (wn_h && ok) ? __ldcs(a.drow + (int64_t)ic * ld + j) : 0.f;
+            zn[i] = (wn_h && ok && zb_next && !zb_is_z) ? __ldcs(zb_next + o) : 0.f;
+          }
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            const int ic = wic[c0 + i];
+            const ColInfo ci = wcol[c0 + i];
+            const bool ok = jok && ic >= 0;
+            const int64_t o = (int64_t)(cbase + c0 + i) * ld + j;
+            float f = 0.f;
+            if (ok) {
+              const float dv = v[hf * 8 + i] * (rj * ci.s);  // Delta V, scales undone exactly
+              const float p = pb[i] + dv;                    // P = P_base + Delta V
+              if (Pout) __stcs(Pout + o, p);
+              if (prow) prow[cbase + c0 + i] = p;
+              s_pv = fmaf(dv, dv, s_pv);
+              float r;
+              const float gap = gap2f(hj, lj, ci.hi, ci.lo);
+              if (gap == 0.f && j != ic) flag_degenerate(a.st);
+              map_entry<float>(z[i], p, ci.d, gap, j == ic, f, r);
+              __stcs(Fout + o, f);
+              const float df = f - z[i];
+              s_inc = fmaf(df, df, s_inc);
+              s_z = fmaf(z[i], z[i], s_z);
+              s_r = fmaf(r, r, s_r);
+            }
+            if (wn_h) {
+              // V_next = F - Z_b(next) at the common scale, split (zero in padding);
+              // this row's term of d_next = Delta_{cols[c], .} F_.c
+              const float zb = zb_is_z ? z[i] : (zb_next ? zn[i] : (j == ic ? 1.f : 0.f));
+              const float x = ok ? (f - zb) * sc_next : 0.f;
+              uint16_t hh, ll;
+              split16(x, a.fuse_bf16 != 0, hh, ll);
+              __stcs(reinterpret_cast<unsigned short*>(wn_h) + o, (unsigned short)hh);
+              __stcs(reinterpret_cast<unsigned short*>(wn_l) + o, (unsigned short)ll);
+              split_bad |= !(fabsf(x) <= split_max);
+              dl[i] = ok ? dl[i] * f : 0.f;
+            }
+          }
+          if (wn_h) {
+            // column sums of the 8 terms over the warp's 32 rows (its row
+            // group): lane L ends with column L / 4's sum (all four lanes of
+            // each quad); every (column, group) partial is written once
+            const float dsum = warp_colsum8(dl, lane);
+            if ((lane & 3) == 0)
+              a.dpart[(int64_t)(cbase + c0 + (lane >> 2)) * a.dgroups + grp] = (double)dsum;
+          }
         }
       }
       tc_fence_before();
@@ -524,6 +610,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         acc_phase ^= 1u;
       }
     }
+    if (split_bad) atomicOr(&a.st->split_bad, 1);
     // norm partials: warp sums, then one set of atomics per CTA (the slot of
     // this warp's column data is free once its last tile is done)
     const double b0 = warp_sum((double)s_inc), b1 = warp_sum((double)s_z),
@@ -614,7 +701,8 @@ cudaError_t configure(int dev) {
 
 template <int MODE>
 cudaError_t launch_cluster(const CUtensorMap& mDh, const CUtensorMap& mDl, const CUtensorMap& mWh,
-                           const CUtensorMap& mWl, const MapArgs<float>& a, int num_m, int num_n,
+                           const CUtensorMap& mWl, const CUtensorMap& mWh1,
+                           const CUtensorMap& mWl1, const MapArgs<float>& a, int num_m, int num_n,
                            int num_kb, int passes, uint32_t idesc, int num_sms, cudaStream_t s) {
   static int max_clusters = 0;
   cudaLaunchConfig_t cfg = {};
@@ -639,7 +727,8 @@ cudaError_t launch_cluster(const CUtensorMap& mDh, const CUtensorMap& mDl, const
   const int pairs = (num_m / 2) * num_n;
   const int clusters = pairs < max_clusters ? pairs : max_clusters;
   cfg.gridDim = dim3(2 * clusters);
-  return cudaLaunchKernelEx(&cfg, k_gemm_tc<MODE>, mDh, mDl, mWh, mWl, a, num_m, num_n, num_kb,
+  return cudaLaunchKernelEx(&cfg, k_gemm_tc<MODE>, mDh, mDl, mWh, mWl, mWh1, mWl1, a, num_m,
+                            num_n, num_kb,
                             passes, idesc);
 }
 
@@ -651,11 +740,21 @@ cudaError_t launch_gemm_tc(const uint16_t* Dh, const uint16_t* Dl, const uint16_
   const bool bf = bf16 != 0;
   const int num_m = npad / BM, num_n = kpad / BN, num_kb = npad / BK;
   const bool pair = mode != IPT_PRODUCT_SINGLE && num_m % 2 == 0;
-  CUtensorMap mDh, mDl, mWh, mWl;
+  CUtensorMap mDh, mDl, mWh, mWl, mWh1, mWl1;
   const uint32_t bbox = pair ? BN / 2 : BN;
   if (!make_map(&mDh, Dh, npad, npad, BM, bf) || !make_map(&mDl, Dl, npad, npad, BM, bf) ||
       !make_map(&mWh, Wh, npad, kpad, bbox, bf) || !make_map(&mWl, Wl, npad, kpad, bbox, bf))
     return cudaErrorInvalidValue;
+  // the second W set (device-chosen operands with the next operand written by
+  // the epilogue), else the first again
+  const bool two = a.dyn && a.wnh[1] && a.wnl[1];
+  if (!two) {
+    mWh1 = mWh;
+    mWl1 = mWl;
+  } else if (!make_map(&mWh1, a.wnh[1], npad, kpad, bbox, bf) ||
+             !make_map(&mWl1, a.wnl[1], npad, kpad, bbox, bf)) {
+    return cudaErrorInvalidValue;
+  }
   static int num_sms = 0, sms_device = -1;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -667,14 +766,14 @@ cudaError_t launch_gemm_tc(const uint16_t* Dh, const uint16_t* Dl, const uint16_
   }
   if (pair) {
     if ((e = configure<MODE_PAIR>(dev)) != cudaSuccess) return e;
-    return launch_cluster<MODE_PAIR>(mDh, mDl, mWh, mWl, a, num_m, num_n, num_kb, passes,
-                                     idesc_for(bf, 2 * BM), num_sms, s);
+    return launch_cluster<MODE_PAIR>(mDh, mDl, mWh, mWl, mWh1, mWl1, a, num_m, num_n, num_kb,
+                                     passes, idesc_for(bf, 2 * BM), num_sms, s);
   }
   if ((e = configure<MODE_SINGLE>(dev)) != cudaSuccess) return e;
   const int tiles = num_m * num_n;
   const int grid = tiles < num_sms ? tiles : num_sms;
   k_gemm_tc<MODE_SINGLE><<<grid, NUM_THREADS, smem_bytes<MODE_SINGLE>(), s>>>(
-      mDh, mDl, mWh, mWl, a, num_m, num_n, num_kb, passes, idesc_for(bf, BM));
+      mDh, mDl, mWh, mWl, mWh1, mWl1, a, num_m, num_n, num_kb, passes, idesc_for(bf, BM));
   return cudaGetLastError();
 }
 

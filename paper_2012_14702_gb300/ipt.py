@@ -40,7 +40,7 @@ class Options(C.Structure):
                 ("stage_switch", C.c_double), ("staged_bf16", C.c_int), ("verify_fp64", C.c_int),
                 ("record_timing", C.c_int), ("z0", C.c_void_p), ("product_kernel", C.c_int),
                 ("accel", C.c_int), ("acx_sigma", C.c_int), ("damping_model", C.c_void_p),
-                ("csr_window", C.c_int)]
+                ("csr_window", C.c_int), ("epilogue_operand", C.c_int)]
 
 
 class Result(C.Structure):
@@ -53,7 +53,8 @@ class Result(C.Structure):
                 ("hist_increment", C.c_double * MAX_HISTORY),
                 ("hist_rho", C.c_double * MAX_HISTORY),
                 ("hist_stage", C.c_int * MAX_HISTORY), ("rows_evaluated", C.c_longlong),
-                ("acc_launches", C.c_int), ("acc_ms", C.c_double), ("rho_error", C.c_double)]
+                ("acc_launches", C.c_int), ("acc_ms", C.c_double), ("rho_error", C.c_double),
+                ("epilogue_operands", C.c_int)]
 
     def to_dict(self) -> dict:
         h = self.history_len
@@ -69,7 +70,8 @@ class Result(C.Structure):
                 "hist_rho": list(self.hist_rho[:h]),
                 "hist_stage": [PRECISION_NAME.get(s, s) for s in self.hist_stage[:h]],
                 "rows_evaluated": self.rows_evaluated, "acc_launches": self.acc_launches,
-                "acc_ms": self.acc_ms, "rho_error": self.rho_error}
+                "acc_ms": self.acc_ms, "rho_error": self.rho_error,
+                "epilogue_operands": self.epilogue_operands}
 
 
 _vp, _i64, _i32, _d = C.c_void_p, C.c_int64, C.c_int, C.c_double
@@ -165,7 +167,7 @@ class Solver:
                     stop="residual", z_dtype=torch.float32, verify_fp64=False, z0=None,
                     diverge_bound=1e8, stage_switch=0.1, staged_bf16=False,
                     record_timing=False, product_kernel="auto", accel=None,
-                    acx_sigma="column", damping_model=None):
+                    acx_sigma="column", damping_model=None, epilogue_operand=True):
         """Alg. 2 / Alg. 1 on the GPU.  Returns (lam [k] f64, Z (n, k) view, info dict).
 
         product_kernel: "auto", "single" (one CTA per tile) or "pair" (two CTAs
@@ -174,7 +176,9 @@ class Solver:
         one step length per column — or "global"), "damped" (learned damping,
         damping_model = the model's FP16 parameters as a CUDA tensor),
         "anderson" (depth-one Anderson mixing per column) or "mixing" (learned
-        damping and mixing, damping_model = the mixing model's parameters)."""
+        damping and mixing, damping_model = the mixing model's parameters).
+        epilogue_operand: staged solves only; False makes the pre-pass write
+        every product's operand (the epilogue writes it by default)."""
         M = _dev(M, name="M")
         n = M.shape[0]
         if M.dim() != 2 or M.shape[1] != n or M.dtype not in DTYPE:
@@ -196,6 +200,7 @@ class Solver:
                              "acx_sigma 'column' or 'global'")
         o.accel = ACCEL[accel]
         o.acx_sigma = 1 if acx_sigma == "global" else 0
+        o.epilogue_operand = 1 if epilogue_operand else 0
         if damping_model is not None:
             damping_model = _dev(damping_model, torch.float16, "damping_model")
             o.damping_model = damping_model.data_ptr()

@@ -58,6 +58,7 @@ def test_status_strings_and_defaults_without_gpu(libpath):
     ipt.lib.ipt_options_default(ctypes.byref(o))
     assert o.precision == ipt.PRECISION["staged"] and o.stop == ipt.STOP["residual"]
     assert o.diverge_bound == 1e8 and o.z0 is None
+    assert o.csr_window == 1 and o.epilogue_operand == 1
 
 
 def test_struct_layout_matches_header(libpath, tmp_path):
@@ -70,8 +71,9 @@ def test_struct_layout_matches_header(libpath, tmp_path):
 #include <stdio.h>
 #include "ipt.h"
 int main(void) {
-  printf("%zu %zu %zu %zu\n", sizeof(ipt_options), offsetof(ipt_options, z0),
-         sizeof(ipt_result), offsetof(ipt_result, hist_stage));
+  printf("%zu %zu %zu %zu %zu %zu\n", sizeof(ipt_options), offsetof(ipt_options, z0),
+         sizeof(ipt_result), offsetof(ipt_result, hist_stage),
+         offsetof(ipt_options, epilogue_operand), offsetof(ipt_result, epilogue_operands));
   return 0;
 }
 ''')
@@ -80,7 +82,8 @@ int main(void) {
     vals = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()]
     from paper_2012_14702_gb300 import ipt
     assert vals == [ctypes.sizeof(ipt.Options), ipt.Options.z0.offset,
-                    ctypes.sizeof(ipt.Result), ipt.Result.hist_stage.offset]
+                    ctypes.sizeof(ipt.Result), ipt.Result.hist_stage.offset,
+                    ipt.Options.epilogue_operand.offset, ipt.Result.epilogue_operands.offset]
 
 
 def test_product_path_has_no_oracle_import():
