@@ -134,6 +134,11 @@ struct Plan {
   bool epi_operand = false;  // staged Picard: the product's epilogue writes the next operand
 };
 
+// the sampled P entries, then (256-byte aligned) the estimator's scratch
+inline size_t smp_scratch_off(const Plan& p) {
+  return ((size_t)kSampleRows * p.kpad * 4 + 255) / 256 * 256;
+}
+
 ipt_status check_dense_args(ipt_handle* h, int64_t n, const void* M, int64_t ldm, int m_dtype,
                             int64_t k, int prec, int64_t ldz, int z_dtype) {
   if (!h || !M) return IPT_INVALID_ARG;
@@ -182,7 +187,7 @@ ipt_status alloc_dense(ipt_handle* h, const Plan& p) {
     CK(ensure(h->wl, kn * 2));
     CK(ensure(h->rinv, (size_t)p.npad * 4));
     CK(ensure(h->sinv, (size_t)p.kpad * 4));
-    CK(ensure(h->smp, (size_t)kSampleRows * p.kpad * 4));
+    CK(ensure(h->smp, smp_scratch_off(p) + (size_t)sample_scratch_bytes()));
     if (p.epi_operand) {
       CK(ensure(h->wh2, kn * 2));
       CK(ensure(h->wl2, kn * 2));
@@ -288,6 +293,9 @@ ipt_status setup_dense(ipt_handle* h, const Plan& p, const void* M, int64_t ldm,
     h->launches += 1;
   }
   if (p.tc) {
+    // the error estimator's arrival counters start at zero (each launch leaves them so)
+    CK(cudaMemsetAsync((char*)h->smp.p + smp_scratch_off(p), 0, (size_t)sample_scratch_bytes(),
+                       s));
     // padding columns of the W operand stay zero (the pre-pass skips them)
     const size_t pad = (size_t)(p.kpad - p.k) * p.npad * 2;
     if (pad) {
@@ -438,8 +446,8 @@ ipt_status evaluate(ipt_handle* h, const Plan& p, int cur, int base, int stage, 
       if (measure) {
         launch_sample_exact((const float*)h->drow.p, (const float*)h->z[cur].p,
                             (const int32_t*)h->icol.p, p.n, p.k, p.kpad, p.npad,
-                            (const float*)h->smp.p, sample_stride(p), sample_stride(p) / 2, st,
-                            DynZ{}, s);
+                            (const float*)h->smp.p, sample_stride(p), sample_stride(p) / 2,
+                            (char*)h->smp.p + smp_scratch_off(p), st, DynZ{}, s);
         h->launches += 1;
       }
     }
@@ -514,7 +522,7 @@ ipt_status evaluate_dyn(ipt_handle* h, const Plan& p, Timing* tm, cudaEvent_t* e
   if (t) CK(cudaEventRecord(ev[3], s));  // the product kernel alone
   launch_sample_exact((const float*)h->drow.p, nullptr, (const int32_t*)h->icol.p, p.n, p.k,
                       p.kpad, p.npad, (const float*)h->smp.p, sample_stride(p),
-                      sample_stride(p) / 2, st, dz, s);
+                      sample_stride(p) / 2, (char*)h->smp.p + smp_scratch_off(p), st, dz, s);
   h->launches += 3;
   return IPT_OK;
 }

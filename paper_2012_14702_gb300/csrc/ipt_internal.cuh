@@ -369,9 +369,13 @@ void launch_control(DevState* st, ControlArgs a, cudaStream_t s);
 // sum of squared differences into st->acc_dp2.  Z: the evaluation's iterate, or
 // with dz.dyn the state's current buffer (and nothing is done unless
 // st->measure).  Drow: FP32 row-major Delta.
+// scratch: sample_scratch_bytes() of device memory whose trailing counters
+// (the last kMaxBlocks ints) are zero before the first launch; every launch
+// leaves them zero.
+int64_t sample_scratch_bytes();
 void launch_sample_exact(const float* Drow, const float* Z, const int32_t* icol, int n, int k,
                          int kpad, int64_t ld, const float* psmp, int stride, int off,
-                         DevState* st, const DynZ& dz, cudaStream_t s);
+                         void* scratch, DevState* st, const DynZ& dz, cudaStream_t s);
 
 // tensor-core product (k_tc_gemm.cu).  passes = 1 (Dh Wh) or 3 (+ Dh Wl + Dl Wh);
 // bf16 selects BF16 operands, else FP16.  Returns a cudaError_t of the launch

@@ -29,66 +29,96 @@ __device__ __forceinline__ T ldval(const void* v, int64_t i, int dt) {
                              : (T) static_cast<const float*>(v)[i];
 }
 
-// One pass over the rows, a half-warp per row (lanes over the row's stored
-// entries, so the column-index and value reads of a row are contiguous and a
-// row's gathers of count[] are in flight together; a persistent grid strides
-// over the rows): the CSR structure check (row bounds within [0, nnz] and
-// ascending, column indices in [0, n); a bad row is flagged and skipped, and the
-// later CSR kernels then do nothing), the stored diagonal M_jj (0 if the row
-// stores none), theta_j (given, or M_jj), its FP32 split and
-// delta_j = M_jj - theta_j; non-finite theta is flagged; the per-block partial of
-// ||M Z0 - Z0 Lambda0||^2, the squared off-diagonal entries in requested columns
-// (count[col] > 0); the band max |j - m| of the stored entries and the row range
-// of the requested rows (the support of Z0 = E).
+// One pass over the rows, a block per 256 consecutive rows [j0, j0 + 256):
+// the block streams the stored entries of its rows, rowptr[j0] ..
+// rowptr[j0 + 256], with consecutive threads on consecutive entries (the
+// column-index and value reads are coalesced and all in flight at once; an
+// entry's row is found by a binary search of the block's row bounds in shared
+// memory).  Per row: the CSR structure check (row bounds within [0, nnz] and
+// ascending, column indices in [0, n); a bad row is flagged, and the later CSR
+// kernels then do nothing), the stored diagonal M_jj (0 if the row stores
+// none; repeated diagonal entries add up, as in the product), theta_j (given,
+// or M_jj), its FP32 split and delta_j = M_jj - theta_j; non-finite theta is
+// flagged.  Per block: the partial of ||M Z0 - Z0 Lambda0||^2 (the squared
+// off-diagonal entries in requested columns, count[col] > 0), the band
+// max |j - m| of the stored entries and the row range of the requested rows
+// (the support of Z0 = E).
 __global__ void __launch_bounds__(256)
     k_csr_rows(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colind,
                const void* __restrict__ vals, int v_dtype, const double* __restrict__ theta_in,
                int n, int64_t nnz, const int* __restrict__ count, double* __restrict__ theta,
                float* __restrict__ th_hi, float* __restrict__ th_lo, double* __restrict__ delta,
                double* __restrict__ part, DevState* st) {
-  const int hw = threadIdx.x >> 4, lane = threadIdx.x & 15;
-  const unsigned hmask = 0xffffu << (threadIdx.x & 16);  // this half-warp's lanes
+  __shared__ int sp[257];        // the block's row bounds, clamped to [0, nnz]
+  __shared__ double sdiag[256];  // stored diagonal of each row
+  const int t = threadIdx.x, j0 = blockIdx.x * 256;
+  const int rows = min(256, n - j0);
+  for (int i = t; i <= rows; i += 256)
+    sp[i] = (int)min((int64_t)max(rowptr[j0 + i], 0), nnz);
+  sdiag[t] = 0.0;
   float r0 = 0.f;
   int band = 0, lo = n, hi = -1;
-  for (int64_t jj = (int64_t)blockIdx.x * 16 + hw; jj < n; jj += (int64_t)gridDim.x * 16) {
-    const int j = (int)jj;
-    if (lane == 0 && count[j] > 0) {
-      lo = min(lo, j);
-      hi = max(hi, j);
-    }
+  bool bad = false;
+  if (t < rows) {
+    const int j = j0 + t;
     const int e0 = rowptr[j], e1 = rowptr[j + 1];
-    const bool rows_ok = e0 >= 0 && e0 <= e1 && (int64_t)e1 <= nnz && (j > 0 || e0 == 0) &&
-                         (j + 1 < n || (int64_t)e1 == nnz);
-    double mjj = 0.0;
-    bool bad = !rows_ok;
-    for (int e = e0 + lane; rows_ok && e < e1; e += 16) {
-      const int m = colind[e];
-      if (m < 0 || m >= n) {
-        bad = true;
-        break;
-      }
-      band = max(band, abs(m - j));
-      if (m == j) {
-        mjj = ldval<double>(vals, e, v_dtype);
-      } else if (count[m] > 0) {
-        const float v = ldval<float>(vals, e, v_dtype);
-        r0 = fmaf(v, v, r0);
-      }
-    }
-    bad = __any_sync(hmask, bad);
+    bad = !(e0 >= 0 && e0 <= e1 && (int64_t)e1 <= nnz && (j > 0 || e0 == 0) &&
+            (j + 1 < n || (int64_t)e1 == nnz));
+    if (count[j] > 0) lo = hi = j;
+  }
+  __syncthreads();
+  const int eb = sp[0], ee = max(sp[rows], eb);
+  // kU entries per thread per step, their loads (and then their gathers of
+  // count[]) all issued before any is used
+  constexpr int kU = 4;
+  for (int e = eb + t; e < ee; e += 256 * kU) {
+    int m[kU], cnt[kU];
+    float v[kU];  // FP32: FP64 conversions run on the narrow FP64 pipe
 #pragma unroll
-    for (int o = 8; o > 0; o >>= 1) mjj += __shfl_xor_sync(hmask, mjj, o);
-    if (lane == 0) {
-      if (bad) atomicOr(&st->flags, FLAG_CSR_INDEX);
-      const double t = theta_in ? theta_in[j] : mjj;
-      if (!isfinite(t)) atomicOr(&st->flags, FLAG_THETA_NONFINITE);
-      theta[j] = t;
-      const float h = (float)t;
-      th_hi[j] = h;
-      th_lo[j] = (float)(t - (double)h);
-      delta[j] = mjj - t;
-      reinterpret_cast<float*>(delta + n)[j] = (float)(mjj - t);  // FP32 copy for FP32 kernels
+    for (int u = 0; u < kU; ++u) {
+      const int x = e + 256 * u;
+      m[u] = x < ee ? colind[x] : -1;
+      v[u] = x < ee ? ldval<float>(vals, x, v_dtype) : 0.f;
     }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) cnt[u] = (m[u] >= 0 && m[u] < n) ? count[m[u]] : 0;
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int x = e + 256 * u;
+      if (x >= ee) break;
+      if (m[u] < 0 || m[u] >= n) {
+        bad = true;
+        continue;
+      }
+      // the entry's row: the last r with sp[r] <= x
+      int a = 0, b = rows - 1;
+      while (a < b) {
+        const int mid = (a + b + 1) >> 1;
+        if (sp[mid] <= x) a = mid;
+        else b = mid - 1;
+      }
+      const int j = j0 + a;
+      band = max(band, abs(m[u] - j));
+      if (m[u] == j) {
+        atomicAdd(&sdiag[a], ldval<double>(vals, x, v_dtype));  // once per row
+      } else if (cnt[u] > 0) {
+        r0 = fmaf(v[u], v[u], r0);
+      }
+    }
+  }
+  __syncthreads();
+  if (bad) atomicOr(&st->flags, FLAG_CSR_INDEX);
+  if (t < rows) {
+    const int j = j0 + t;
+    const double mjj = sdiag[t];
+    const double th = theta_in ? theta_in[j] : mjj;
+    if (!isfinite(th)) atomicOr(&st->flags, FLAG_THETA_NONFINITE);
+    theta[j] = th;
+    const float h = (float)th;
+    th_hi[j] = h;
+    th_lo[j] = (float)(th - (double)h);
+    delta[j] = mjj - th;
+    reinterpret_cast<float*>(delta + n)[j] = (float)(mjj - th);  // FP32 copy for FP32 kernels
   }
   // block reduction; the shared words take one atomic per block, and only
   // when the block's value would change them (most blocks see the same band)
@@ -395,11 +425,7 @@ void launch_csr_rows(const int32_t* rowptr, const int32_t* colind, const void* v
                      const double* theta_in, int n, int64_t nnz, const int* count, double* theta,
                      float* th_hi, float* th_lo, double* delta, double* part, int window,
                      DevState* st, cudaStream_t s) {
-  // persistent grid, at most one block per 256 rows (the partials' capacity)
-  int nsm = 0, dev = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  const unsigned g = std::min<unsigned>(nblocks(n, 256), (unsigned)(nsm > 0 ? nsm : 148) * 8);
+  const unsigned g = nblocks(n, 256);  // one block per 256 rows (the partials' capacity)
   k_csr_rows<<<g, 256, 0, s>>>(rowptr, colind, vals, v_dtype, theta_in, n, nnz, count, theta, th_hi,
                                th_lo, delta, part, st);
   k_csr_sum_r0<<<1, 1024, 0, s>>>(part, (int)g, n, window, st);

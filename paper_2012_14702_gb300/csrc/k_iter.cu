@@ -633,7 +633,7 @@ __device__ __forceinline__ bool split_stage(int stage) {
   return stage == IPT_PREC_BF16X3 || stage == IPT_PREC_FP16X3;
 }
 
-__global__ void k_control(DevState* st, ControlArgs a) {
+__device__ void control_step(DevState* st, const ControlArgs& a) {
   if (st->done || st->pause) return;
   const int it = st->iter;
   const double z2 = st->acc_z2;
@@ -838,6 +838,8 @@ __global__ void k_control(DevState* st, ControlArgs a) {
   st->split_bad = 0;
   st->prev_rho = rho;
 }
+
+__global__ void k_control(DevState* st, ControlArgs a) { control_step(st, a); }
 
 }  // namespace
 

@@ -68,7 +68,7 @@ constexpr int EPI_THREADS = 32 * EPI_WARPS;
 constexpr int EPI_COLS = BN / 2;  // columns of a tile one epilogue warp handles
 constexpr uint64_t kTimeoutNs = kWaitLimitNs;
 #ifndef IPT_GROUP_M
-#define IPT_GROUP_M 16
+#define IPT_GROUP_M 8
 #endif
 constexpr int GROUP_M = IPT_GROUP_M;             // row blocks per L2 raster group
 
@@ -77,6 +77,9 @@ constexpr int GROUP_M = IPT_GROUP_M;             // row blocks per L2 raster gro
 // accumulator, and the main product Dh Wh last: adding ~1000 tiny partial
 // sums into an accumulator that already holds the whole product would round
 // each of them against the large value.
+#ifndef IPT_SPLIT_INTERLEAVED
+#define IPT_SPLIT_INTERLEAVED 0
+#endif
 #ifndef IPT_CORRECTIONS_FIRST
 #define IPT_CORRECTIONS_FIRST 1
 #endif
@@ -358,7 +361,14 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   const int num_tiles = sched_m * num_n;
   const int t_first = CLUSTER ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;
   const int t_step = CLUSTER ? (int)(gridDim.x >> 1) : (int)gridDim.x;
-  const int total_kb = passes * num_kb;
+  // split products interleaved per K block: a stage is two ring slots holding
+  // Dh, Dl, Wh and Wl of one K block, and each K step issues the three MMAs
+  // (corrections first), so every operand tile is loaded once instead of in
+  // two of the three passes
+  const bool inter = IPT_SPLIT_INTERLEAVED && passes == 3;
+  const int nstages = inter ? STAGES / 2 : STAGES;
+  const int total_kb = inter ? num_kb : passes * num_kb;
+  static_assert(STAGES % 2 == 0, "interleaved stages take two slots");
 
   if (warp == 0) {
     // ------------------------------------------------ TMA producer
@@ -382,6 +392,30 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
           const int pass = kb / num_kb;
           if (kb == pass * num_kb) ko.reset(nb, num_kb);
           const int kx = ko.next() * BK;
+          if (inter) {
+            uint8_t* a0 = sA + (2 * stage) * A_BYTES;
+            uint8_t* b0 = sB + (2 * stage) * B_BYTES;
+            if constexpr (PAIR) {
+              const uint32_t fb = peer_addr(&ctl->full[stage], 0);
+              if (leader) mbar_expect_tx(&ctl->full[stage], 4 * STAGE_BYTES);
+              tma_load_pair(a0, &tmDh, fb, kx, mb * BM);
+              tma_load_pair(a0 + A_BYTES, &tmDl, fb, kx, mb * BM);
+              tma_load_pair(b0, tmBh, fb, kx, nb * BN + rank * (BN / 2));
+              tma_load_pair(b0 + B_BYTES, tmBl, fb, kx, nb * BN + rank * (BN / 2));
+            } else {
+              mbar_expect_tx(&ctl->full[stage], 2 * STAGE_BYTES);
+              tma_load(a0, &tmDh, &ctl->full[stage], kx, mb * BM);
+              tma_load(a0 + A_BYTES, &tmDl, &ctl->full[stage], kx, mb * BM);
+              tma_load(b0, tmBh, &ctl->full[stage], kx, nb * BN);
+              tma_load(b0 + B_BYTES, tmBl, &ctl->full[stage], kx, nb * BN);
+            }
+            pend_parity[stage] = (int)phase;
+            if (++stage == nstages) {
+              stage = 0;
+              phase ^= 1u;
+            }
+            continue;
+          }
           // passes = 1: Dh Wh.  passes = 3: (Dh Wl, Dl Wh, Dh Wh), or with the
           // main product first (Dh Wh, Dh Wl, Dl Wh).
           const int role = passes == 1 ? 0 : (IPT_CORRECTIONS_FIRST ? (pass + 1) % 3 : pass);
@@ -398,7 +432,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             tma_load(sB + stage * B_BYTES, mB, &ctl->full[stage], kx, nb * BN);
           }
           pend_parity[stage] = (int)phase;
-          if (++stage == STAGES) {
+          if (++stage == nstages) {
             stage = 0;
             phase ^= 1u;
           }
@@ -444,18 +478,39 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             break;
           }
           tc_fence_after();
-          const uint32_t ab = su32(sA + stage * A_BYTES), bb = su32(sB + stage * B_BYTES);
+          if (inter) {
+            // Dh Wl, Dl Wh, Dh Wh at each K step of the block
+            const uint32_t ah = su32(sA + (2 * stage) * A_BYTES), al = ah + A_BYTES;
+            const uint32_t bh = su32(sB + (2 * stage) * B_BYTES), bl = bh + B_BYTES;
 #pragma unroll
-          for (int k = 0; k < BK / 16; ++k) {
-            if constexpr (PAIR)
-              mma_f16_pair(dt, sw128_desc(ab + k * 32), sw128_desc(bb + k * 32), idesc,
-                           (kb | k) != 0);
-            else
-              mma_f16(dt, sw128_desc(ab + k * 32), sw128_desc(bb + k * 32), idesc, (kb | k) != 0);
+            for (int k = 0; k < BK / 16; ++k) {
+              const uint64_t dah = sw128_desc(ah + k * 32), dal = sw128_desc(al + k * 32);
+              const uint64_t dbh = sw128_desc(bh + k * 32), dbl = sw128_desc(bl + k * 32);
+              if constexpr (PAIR) {
+                mma_f16_pair(dt, dah, dbl, idesc, (kb | k) != 0);
+                mma_f16_pair(dt, dal, dbh, idesc, true);
+                mma_f16_pair(dt, dah, dbh, idesc, true);
+              } else {
+                mma_f16(dt, dah, dbl, idesc, (kb | k) != 0);
+                mma_f16(dt, dal, dbh, idesc, true);
+                mma_f16(dt, dah, dbh, idesc, true);
+              }
+            }
+          } else {
+            const uint32_t ab = su32(sA + stage * A_BYTES), bb = su32(sB + stage * B_BYTES);
+#pragma unroll
+            for (int k = 0; k < BK / 16; ++k) {
+              if constexpr (PAIR)
+                mma_f16_pair(dt, sw128_desc(ab + k * 32), sw128_desc(bb + k * 32), idesc,
+                             (kb | k) != 0);
+              else
+                mma_f16(dt, sw128_desc(ab + k * 32), sw128_desc(bb + k * 32), idesc,
+                        (kb | k) != 0);
+            }
           }
           if constexpr (PAIR) mma_commit_pair_mc(&ctl->empty[stage], (uint16_t)0x3);
           else mma_commit(&ctl->empty[stage]);
-          if (++stage == STAGES) {
+          if (++stage == nstages) {
             stage = 0;
             phase ^= 1u;
           }
