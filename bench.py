@@ -525,6 +525,11 @@ def run_batched_tc(solver, sizes, Mg, steps, hbm_peak, flat, picks):
     n2 = sizes.astype(np.float64) ** 2
     alg_bytes = float(np.sum(12.0 * n2 * np.maximum(its - 1, 0) + 8.0 * n2))
     gbs = alg_bytes / (k_ms / 1e3) / 1e9
+    # ncu DRAM bytes of a 512-problem solve of the same size mix, per matrix entry,
+    # scaled to this batch's entries
+    tr = profiled_traffic("k_batched_tc_512_n32_512.md", "k_batched_tc.cu",
+                          ["traffic_bytes_per_matrix_entry"])
+    traffic = None if tr is None else tr["traffic_bytes_per_matrix_entry"] * float(np.sum(n2))
     return {"ms_to_tol": ms, "status": info["status"],
             "oracle_error": batched_oracle_error(sizes, flat, lam_b, Z_b, picks),
             "evaluations": {"min": int(its.min()), "max": int(its.max()),
@@ -533,7 +538,9 @@ def run_batched_tc(solver, sizes, Mg, steps, hbm_peak, flat, picks):
             "roofline": {"kernel": "k_batched_tc_prep + k_batched_tc (tcgen05 split-BF16 x3, "
                                    "128 x 128 tiles, bulk-copied pre-split operands)",
                          "bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
-                         "frac": gbs / hbm_peak, "traffic": None,
+                         "frac": gbs / hbm_peak, "traffic": traffic,
+                         "traffic_source": "profiles/k_batched_tc_512_n32_512.md, scaled by "
+                                           "the batch's matrix entries",
                          "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_ms": k_ms,
                          "peak_source": "measured HBM copy",
                          "tensor_executed": {"achieved": executed, "peak": burst,
@@ -846,7 +853,9 @@ def run_ours(args, rank, world, local_rank):
         "traffic_per_launch": None if tr is None else {
             "1pass": tr["traffic_bytes_per_launch_1pass"],
             "3pass": tr["traffic_bytes_per_launch_3pass"]},
-        "algorithmic_bytes_per_launch": {"1pass": 16 * n * n, "3pass": 24 * n * n},
+        # operands once, the epilogue's Z, P_b and F (and the re-base's P), and the
+        # next operand it writes (row of Delta for d in, 16-bit split out)
+        "algorithmic_bytes_per_launch": {"1pass": 24 * n * n, "3pass": 32 * n * n},
         "peak_source": f"{peak_src} {'sustained' if peak == sustained else 'burst'} bf16 "
                        f"(FP16 dense rate equals BF16)",
         "flops_per_launch": gemm_flops,

@@ -374,6 +374,24 @@ ipt_status ipt_check_map_division(int64_t count, const float* gap, const float* 
                                   float* quotient, void* stream);
 
 /*
+ * Check of the exact conversions the sparse setup pass builds from IEEE bit
+ * patterns with integer instructions (no counterpart in the paper): for i < count,
+ *   hi[i], lo[i]  the two-float split of x[i] (hi = x rounded to FP32, lo = x - hi
+ *                 rounded to FP32),
+ *   f[i]          x[i] rounded to FP32,
+ *   back[i]       f[i] converted back to FP64,
+ *   ok[i]         bit 0: the split, bit 1: the rounding, bit 2: the conversion back
+ *                 were inside the range the integer forms handle (outside it the
+ *                 solver uses the hardware conversion; the outputs are then
+ *                 unspecified),
+ * on device arrays, enqueued on `stream` without synchronising, so that they can
+ * be compared with the hardware conversions.  Returns IPT_INVALID_ARG for
+ * count < 0 or a NULL array, IPT_CUDA_ERROR on a launch error.
+ */
+ipt_status ipt_check_conversions(int64_t count, const double* x, float* hi, float* lo,
+                                 float* f, double* back, int32_t* ok, void* stream);
+
+/*
  * The damping model of IPT_ACCEL_DAMPED and its training (no counterpart in the
  * paper).  A 6 -> 64 -> 64 -> 1 perceptron: h1 = tanh(x W1 + b1),
  * h2 = tanh(h1 W2 + b2), y = h2 W3 + b3, alpha = 2 / (1 + exp(-y)).  Parameters:

@@ -21,8 +21,8 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIBDIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(LIBDIR, "libipt.so")
-SOURCES = ["ipt_api.cu", "k_setup.cu", "k_iter.cu", "k_tc_gemm.cu", "k_csr.cu", "k_acx.cu",
-           "k_batched.cu", "k_batched_tc.cu", "k_mlp.cu", "k_damp.cu", "k_anderson.cu",
+SOURCES = ["ipt_api.cu", "k_setup.cu", "k_iter.cu", "k_tc_gemm.cu", "k_csr.cu", "k_csr_setup.cu",
+           "k_acx.cu", "k_batched.cu", "k_batched_tc.cu", "k_mlp.cu", "k_damp.cu", "k_anderson.cu",
            "k_diag.cu", "k_sample.cu", "k_mix.cu", "ipt_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]

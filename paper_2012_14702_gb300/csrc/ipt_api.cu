@@ -1935,6 +1935,16 @@ ipt_status ipt_check_map_division(int64_t count, const float* gap, const float* 
              : IPT_CUDA_ERROR;
 }
 
+ipt_status ipt_check_conversions(int64_t count, const double* x, float* hi, float* lo,
+                                 float* f, double* back, int32_t* ok, void* stream) {
+  if (count < 0 || (count > 0 && (!x || !hi || !lo || !f || !back || !ok)))
+    return IPT_INVALID_ARG;
+  return launch_conv_check(count, x, hi, lo, f, back, ok, static_cast<cudaStream_t>(stream)) ==
+                 cudaSuccess
+             ? IPT_OK
+             : IPT_CUDA_ERROR;
+}
+
 ipt_status ipt_set_batched_tiles(ipt_handle* h, const int32_t* tiles) {
   if (!h || !tiles) return IPT_INVALID_ARG;
   for (int c = 0; c < kBatchClasses; ++c)

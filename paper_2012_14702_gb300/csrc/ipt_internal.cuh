@@ -272,6 +272,8 @@ cudaError_t launch_mix_adam(float* master, void* params, float* grad, float* m, 
                             float lr, float b1, float b2, float eps, int step, cudaStream_t s);
 
 // The FP32 map's division (k_diag.cu): q[i] = u[i] * recip_nr(gap[i]).
+cudaError_t launch_conv_check(int64_t count, const double* x, float* hi, float* lo, float* f,
+                              double* back, int32_t* ok, cudaStream_t s);
 cudaError_t launch_recip_check(int64_t count, const float* gap, const float* u, float* q,
                                cudaStream_t s);
 // Bounded-wait check (k_diag.cu): out[0] = 1 if the wait succeeded, out[1] = ns waited.
@@ -470,6 +472,68 @@ __device__ __forceinline__ F2 block_sum(F2 v, F2* sh) {
   F2 t{0.f, 0.f};
   if (w == 0) t = warp_sum(lane < nw ? sh[lane] : F2{0.f, 0.f});
   return t;
+}
+
+// Exact FP32 <-> FP64 conversions and the two-float split of a double built
+// from the IEEE bit patterns with integer instructions.  On this GPU the
+// conversion instructions run on the narrow FP64 pipe, which per-row setup
+// passes over millions of rows would otherwise saturate.  Each returns ok =
+// false outside the range it handles (zero is handled; subnormal, infinite or
+// NaN inputs and results are not), and the caller then uses the hardware
+// conversion; within the range the results equal the hardware's.
+//
+// FP64 -> FP32, round to nearest even (normal FP32 results and zero).
+__device__ __forceinline__ float f64_to_f32_rn_bits(double x, bool& ok) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+  if ((b << 1) == 0ull) {
+    ok = true;
+    return __uint_as_float(sign);
+  }
+  const int e = (int)((b >> 52) & 0x7ffu) - 1023;
+  const unsigned m23 = (unsigned)((b >> 29) & 0x7fffffu);
+  const unsigned rem = (unsigned)(b & 0x1fffffffu);  // the 29 bits below FP32's last
+  unsigned em = ((unsigned)(e + 127) << 23) | m23;
+  if (rem > 0x10000000u || (rem == 0x10000000u && (m23 & 1u))) em += 1u;  // carry ok
+  ok = e >= -126 && e <= 127 && em < 0x7f800000u;
+  return __uint_as_float(sign | em);
+}
+
+// FP32 -> FP64 (exact; normal inputs and zero).
+__device__ __forceinline__ double f32_to_f64_bits(float v, bool& ok) {
+  const unsigned u = __float_as_uint(v);
+  const unsigned e8 = (u >> 23) & 0xffu;
+  const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
+  ok = true;
+  if ((u << 1) == 0u) return __longlong_as_double((long long)sign);
+  ok = e8 != 0u && e8 != 0xffu;
+  const unsigned long long bits = sign | ((unsigned long long)(e8 - 127u + 1023u) << 52) |
+                                  ((unsigned long long)(u & 0x7fffffu) << 29);
+  return __longlong_as_double((long long)bits);
+}
+
+// x = hi + lo to ~2^-48 relative: hi = RN_f32(x), lo = RN_f32(x - hi); x - hi is
+// the 29 low bits (minus 2^29 when hi rounded up) at x's exponent, exact in an
+// int, so lo is that int rounded to FP32 and scaled by a power of two.
+__device__ __forceinline__ void split_f64_bits(double x, float& hi, float& lo, bool& ok) {
+  hi = f64_to_f32_rn_bits(x, ok);
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  if (!ok || (b << 1) == 0ull) {
+    lo = 0.f;
+    return;
+  }
+  const int e = (int)((b >> 52) & 0x7ffu) - 1023;
+  const unsigned m23 = (unsigned)((b >> 29) & 0x7fffffu);
+  const int rem = (int)(b & 0x1fffffffu);
+  const bool up = rem > 0x10000000 || (rem == 0x10000000 && (m23 & 1u));
+  const int r = up ? rem - (1 << 29) : rem;
+  if (e - 52 < -126) {  // the remainder's scale is not a normal FP32 power of two
+    ok = false;
+    return;
+  }
+  const float scale = __uint_as_float((unsigned)(e - 52 + 127) << 23);
+  // signed in the integer, so that a zero remainder is +0 as x - hi gives it
+  lo = __int2float_rn((b >> 63) ? -r : r) * scale;  // exact: scaling by a power of two
 }
 
 // Power-of-two operand scale s with mx * s in [2^13, 2^14): keeps scaled

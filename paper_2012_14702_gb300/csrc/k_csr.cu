@@ -9,10 +9,10 @@
 // delta_j = M_jj - theta_j (0 when theta = diag(M)), is applied separately, so
 // the CSR loop skips stored diagonal entries.
 //
-// Kernels: setup (theta, delta_j, residual normaliser, Z = E), the diagonal
-// pre-pass d_c = (Delta Z)_{cols[c], c} (one warp per column: a sparse row
-// dot product), the SpMM + map, and the transpose of the result to the
-// column-major output of the C ABI.
+// Kernels: the diagonal pre-pass d_c = (Delta Z)_{cols[c], c} (one warp per
+// column: a sparse row dot product), the SpMM + map, and the transpose of the
+// result to the column-major output of the C ABI.  The setup pass over the rows
+// and the FP64 residual are in k_csr_setup.cu.
 #include "ipt_internal.cuh"
 
 #include <math.h>
@@ -27,169 +27,6 @@ template <typename T>
 __device__ __forceinline__ T ldval(const void* v, int64_t i, int dt) {
   return dt == IPT_DTYPE_F64 ? (T) static_cast<const double*>(v)[i]
                              : (T) static_cast<const float*>(v)[i];
-}
-
-// One pass over the rows, a block per 256 consecutive rows [j0, j0 + 256):
-// the block streams the stored entries of its rows, rowptr[j0] ..
-// rowptr[j0 + 256], with consecutive threads on consecutive entries (the
-// column-index and value reads are coalesced and all in flight at once; an
-// entry's row is found by a binary search of the block's row bounds in shared
-// memory).  Per row: the CSR structure check (row bounds within [0, nnz] and
-// ascending, column indices in [0, n); a bad row is flagged, and the later CSR
-// kernels then do nothing), the stored diagonal M_jj (0 if the row stores
-// none; repeated diagonal entries add up, as in the product), theta_j (given,
-// or M_jj), its FP32 split and delta_j = M_jj - theta_j; non-finite theta is
-// flagged.  Per block: the partial of ||M Z0 - Z0 Lambda0||^2 (the squared
-// off-diagonal entries in requested columns, count[col] > 0), the band
-// max |j - m| of the stored entries and the row range of the requested rows
-// (the support of Z0 = E).
-__global__ void __launch_bounds__(256)
-    k_csr_rows(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colind,
-               const void* __restrict__ vals, int v_dtype, const double* __restrict__ theta_in,
-               int n, int64_t nnz, const int* __restrict__ count, double* __restrict__ theta,
-               float* __restrict__ th_hi, float* __restrict__ th_lo, double* __restrict__ delta,
-               double* __restrict__ part, DevState* st) {
-  __shared__ int sp[257];        // the block's row bounds, clamped to [0, nnz]
-  __shared__ double sdiag[256];  // stored diagonal of each row
-  const int t = threadIdx.x, j0 = blockIdx.x * 256;
-  const int rows = min(256, n - j0);
-  for (int i = t; i <= rows; i += 256)
-    sp[i] = (int)min((int64_t)max(rowptr[j0 + i], 0), nnz);
-  sdiag[t] = 0.0;
-  float r0 = 0.f;
-  int band = 0, lo = n, hi = -1;
-  bool bad = false;
-  if (t < rows) {
-    const int j = j0 + t;
-    const int e0 = rowptr[j], e1 = rowptr[j + 1];
-    bad = !(e0 >= 0 && e0 <= e1 && (int64_t)e1 <= nnz && (j > 0 || e0 == 0) &&
-            (j + 1 < n || (int64_t)e1 == nnz));
-    if (count[j] > 0) lo = hi = j;
-  }
-  __syncthreads();
-  const int eb = sp[0], ee = max(sp[rows], eb);
-  // kU entries per thread per step, their loads (and then their gathers of
-  // count[]) all issued before any is used
-  constexpr int kU = 4;
-  for (int e = eb + t; e < ee; e += 256 * kU) {
-    int m[kU], cnt[kU];
-    float v[kU];  // FP32: FP64 conversions run on the narrow FP64 pipe
-#pragma unroll
-    for (int u = 0; u < kU; ++u) {
-      const int x = e + 256 * u;
-      m[u] = x < ee ? colind[x] : -1;
-      v[u] = x < ee ? ldval<float>(vals, x, v_dtype) : 0.f;
-    }
-#pragma unroll
-    for (int u = 0; u < kU; ++u) cnt[u] = (m[u] >= 0 && m[u] < n) ? count[m[u]] : 0;
-#pragma unroll
-    for (int u = 0; u < kU; ++u) {
-      const int x = e + 256 * u;
-      if (x >= ee) break;
-      if (m[u] < 0 || m[u] >= n) {
-        bad = true;
-        continue;
-      }
-      // the entry's row: the last r with sp[r] <= x
-      int a = 0, b = rows - 1;
-      while (a < b) {
-        const int mid = (a + b + 1) >> 1;
-        if (sp[mid] <= x) a = mid;
-        else b = mid - 1;
-      }
-      const int j = j0 + a;
-      band = max(band, abs(m[u] - j));
-      if (m[u] == j) {
-        atomicAdd(&sdiag[a], ldval<double>(vals, x, v_dtype));  // once per row
-      } else if (cnt[u] > 0) {
-        r0 = fmaf(v[u], v[u], r0);
-      }
-    }
-  }
-  __syncthreads();
-  if (bad) atomicOr(&st->flags, FLAG_CSR_INDEX);
-  if (t < rows) {
-    const int j = j0 + t;
-    const double mjj = sdiag[t];
-    const double th = theta_in ? theta_in[j] : mjj;
-    if (!isfinite(th)) atomicOr(&st->flags, FLAG_THETA_NONFINITE);
-    theta[j] = th;
-    const float h = (float)th;
-    th_hi[j] = h;
-    th_lo[j] = (float)(th - (double)h);
-    delta[j] = mjj - th;
-    reinterpret_cast<float*>(delta + n)[j] = (float)(mjj - th);  // FP32 copy for FP32 kernels
-  }
-  // block reduction; the shared words take one atomic per block, and only
-  // when the block's value would change them (most blocks see the same band)
-  __shared__ float red[8];
-  __shared__ int rb[8], rl[8], rh[8];
-  const int wq = threadIdx.x >> 5;
-  const float w = warp_sum(r0);
-  band = warp_max_int(band);
-  lo = warp_min_int(lo);
-  hi = warp_max_int(hi);
-  if ((threadIdx.x & 31) == 0) {
-    red[wq] = w;
-    rb[wq] = band;
-    rl[wq] = lo;
-    rh[wq] = hi;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double tot = 0.0;
-    int b = 0, l = n, hh = -1;
-    for (int q = 0; q < 8; ++q) {
-      tot += (double)red[q];
-      b = max(b, rb[q]);
-      l = min(l, rl[q]);
-      hh = max(hh, rh[q]);
-    }
-    part[blockIdx.x] = tot;
-    if (b > *(volatile int*)&st->band) atomicMax(&st->band, b);
-    if (hh >= 0) {
-      atomicMin(&st->z_lo, l);
-      atomicMax(&st->z_hi, hh);
-    }
-  }
-}
-
-// One block: ||R0||^2 from the row pass's partials, and the rows the first
-// product evaluates: all of them, or (window) the requested rows widened by
-// the band (rows further away have no stored entry in a nonzero row of E).
-__global__ void __launch_bounds__(1024)
-    k_csr_sum_r0(const double* __restrict__ part, int count, int n, int window, DevState* st) {
-  __shared__ double red[1024];
-  double t = 0.0;
-  for (int i = threadIdx.x; i < count; i += blockDim.x) t += part[i];
-  red[threadIdx.x] = t;
-  __syncthreads();
-  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
-    if ((int)threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) {
-    st->r0acc = red[0];
-    st->nz_lo = n;
-    st->nz_hi = -1;
-    if (window && st->z_hi >= st->z_lo) {
-      st->win_lo = max(0, st->z_lo - st->band);
-      st->win_hi = (int)min((int64_t)n, (int64_t)st->z_hi + 1 + st->band);
-    } else {
-      st->win_lo = 0;
-      st->win_hi = n;
-    }
-  }
-}
-
-// Z = E in the row-major layout (Z[j*kk + c] = 1 at j = cols[c]); padding
-// zero.  Block: 64 columns x 4 rows; each thread writes one entry per row step.
-template <typename T>
-__global__ void k_csr_units(const int32_t* __restrict__ icol, int k, int kk, T* __restrict__ Z) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= k) return;
-  const int i = icol[c];  // -1 for a column index out of range (flagged)
-  if (i >= 0) Z[(int64_t)i * kk + c] = T(1);
 }
 
 // d_c = sum_m Delta_{i_c, m} Z_{m, c} = delta_{i_c} Z_{i_c, c} + sum over the
@@ -360,11 +197,23 @@ __global__ void __launch_bounds__(256, 4)
   __shared__ double red[3][8];
   __shared__ int rlo[8], rhi[8], rwork[8];
   const int w = threadIdx.x >> 5;
-  const double b0 = warp_sum((double)s_inc), b1 = warp_sum((double)s_z),
-               b2 = warp_sum((double)s_r);
+  const int worked = __any_sync(0xffffffffu, wlo + half0 - (lane >> 4) < whi);
+  // warp sums (FP32 pairs for FP32 iterates: FP64 adds run on the narrow FP64
+  // pipe), skipped by the idle warps of the persistent grid
+  double b0 = 0.0, b1 = 0.0, b2 = 0.0;
+  if (worked) {
+    if constexpr (sizeof(T) == 4) {
+      b0 = f2_value(warp_sum(F2{(float)s_inc, 0.f}));
+      b1 = f2_value(warp_sum(F2{(float)s_z, 0.f}));
+      b2 = f2_value(warp_sum(F2{(float)s_r, 0.f}));
+    } else {
+      b0 = warp_sum((double)s_inc);
+      b1 = warp_sum((double)s_z);
+      b2 = warp_sum((double)s_r);
+    }
+  }
   f_lo = warp_min_int(f_lo);
   f_hi = warp_max_int(f_hi);
-  const int worked = __any_sync(0xffffffffu, wlo + half0 - (lane >> 4) < whi);
   if (lane == 0) {
     red[0][w] = b0;
     red[1][w] = b1;
@@ -378,9 +227,11 @@ __global__ void __launch_bounds__(256, 4)
     double t0 = 0.0, t1 = 0.0, t2 = 0.0;
     int lo = n, hi = -1, any = 0;
     for (int q = 0; q < (int)(blockDim.x >> 5); ++q) {
-      t0 += red[0][q];
-      t1 += red[1][q];
-      t2 += red[2][q];
+      if (rwork[q]) {
+        t0 += red[0][q];
+        t1 += red[1][q];
+        t2 += red[2][q];
+      }
       lo = min(lo, rlo[q]);
       hi = max(hi, rhi[q]);
       any |= rwork[q];
@@ -421,21 +272,6 @@ inline unsigned nblocks(int64_t total, int bs) { return (unsigned)((total + bs -
 }  // namespace
 
 // ---------------------------------------------------------------- launchers
-void launch_csr_rows(const int32_t* rowptr, const int32_t* colind, const void* vals, int v_dtype,
-                     const double* theta_in, int n, int64_t nnz, const int* count, double* theta,
-                     float* th_hi, float* th_lo, double* delta, double* part, int window,
-                     DevState* st, cudaStream_t s) {
-  const unsigned g = nblocks(n, 256);  // one block per 256 rows (the partials' capacity)
-  k_csr_rows<<<g, 256, 0, s>>>(rowptr, colind, vals, v_dtype, theta_in, n, nnz, count, theta, th_hi,
-                               th_lo, delta, part, st);
-  k_csr_sum_r0<<<1, 1024, 0, s>>>(part, (int)g, n, window, st);
-}
-
-void launch_csr_units(const int32_t* icol, int k, int kk, void* Z, int f64, cudaStream_t s) {
-  if (f64) k_csr_units<double><<<nblocks(k, 256), 256, 0, s>>>(icol, k, kk, (double*)Z);
-  else k_csr_units<float><<<nblocks(k, 256), 256, 0, s>>>(icol, k, kk, (float*)Z);
-}
-
 void launch_csr_prepass(const int32_t* rowptr, const int32_t* colind, const void* vals,
                         int v_dtype, const double* delta, const int32_t* icol, int kk,
                         const void* Z, int f64, double* d, DevState* st, cudaStream_t s) {
@@ -479,54 +315,6 @@ void launch_csr_out(const void* Z, int f64, int j_lo, int n, int k, int kk, void
   else
     k_csr_transpose_out<float, float><<<g, b, 0, s>>>((const float*)Z, j_lo, n, k, kk,
                                                       (float*)out, ldo);
-}
-
-namespace {
-
-// ||M Z - Z Lambda||_F^2 in FP64 (verification of a sparse result): the stored
-// entries of M (diagonal included) against the row-major iterate; one warp per
-// row, lane l the columns c = c0 + l of each 32-column chunk.
-template <typename T>
-__global__ void __launch_bounds__(256)
-    k_csr_residual64(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colind,
-                     const void* __restrict__ vals, int v_dtype, int n, int k, int kk,
-                     const T* __restrict__ Z, const double* __restrict__ lam,
-                     double* __restrict__ acc) {
-  const int lane = threadIdx.x & 31;
-  const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  double s = 0.0;
-  for (int64_t j = w0; j < n; j += nw) {
-    const int e0 = rowptr[j], e1 = rowptr[j + 1];
-    for (int c0 = 0; c0 < k; c0 += 32) {
-      const int c = c0 + lane;
-      if (c >= k) continue;
-      double a = 0.0;
-      for (int e = e0; e < e1; ++e) {
-        const double v = v_dtype == IPT_DTYPE_F64 ? static_cast<const double*>(vals)[e]
-                                                  : (double)static_cast<const float*>(vals)[e];
-        a = fma(v, (double)Z[(int64_t)colind[e] * kk + c], a);
-      }
-      const double r = a - (double)Z[j * kk + c] * lam[c];
-      s += r * r;
-    }
-  }
-  s = warp_sum(s);
-  if (lane == 0) atomicAdd(acc, s);
-}
-
-}  // namespace
-
-void launch_csr_residual64(const int32_t* rowptr, const int32_t* colind, const void* vals,
-                           int v_dtype, int n, int k, int kk, const void* Z, int f64,
-                           const double* lam, double* acc, cudaStream_t s) {
-  const int blocks = (int)std::min<int64_t>(((int64_t)n + 7) / 8, 152 * 16);
-  if (f64)
-    k_csr_residual64<double><<<blocks, 256, 0, s>>>(rowptr, colind, vals, v_dtype, n, k, kk,
-                                                    (const double*)Z, lam, acc);
-  else
-    k_csr_residual64<float><<<blocks, 256, 0, s>>>(rowptr, colind, vals, v_dtype, n, k, kk,
-                                                   (const float*)Z, lam, acc);
 }
 
 }  // namespace ipt

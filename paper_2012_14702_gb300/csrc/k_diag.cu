@@ -1,4 +1,4 @@
-// Checks of two device-side building blocks, without any fault or hang.
+// Checks of device-side building blocks, without any fault or hang.
 //
 // Bounded-wait check: exercises the give-up path of the shared-memory barrier
 // wait that every waiting role of the tensor-core product kernel uses, without
@@ -38,7 +38,32 @@ __global__ void k_recip_check(int64_t count, const float* __restrict__ gap,
   if (i < count) q[i] = u[i] * recip_nr(gap[i]);
 }
 
+// The integer-ALU conversions of the sparse setup pass, one entry per thread.
+__global__ void k_conv_check(int64_t count, const double* __restrict__ x, float* __restrict__ hi,
+                             float* __restrict__ lo, float* __restrict__ f,
+                             double* __restrict__ back, int32_t* __restrict__ ok) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  bool a, b, c;
+  float h, l;
+  split_f64_bits(x[i], h, l, a);
+  const float r = f64_to_f32_rn_bits(x[i], b);
+  const double d = f32_to_f64_bits(r, c);
+  hi[i] = h;
+  lo[i] = l;
+  f[i] = r;
+  back[i] = d;
+  ok[i] = (a ? 1 : 0) | (b ? 2 : 0) | (c ? 4 : 0);
+}
+
 }  // namespace
+
+cudaError_t launch_conv_check(int64_t count, const double* x, float* hi, float* lo, float* f,
+                              double* back, int32_t* ok, cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  k_conv_check<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(count, x, hi, lo, f, back, ok);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_recip_check(int64_t count, const float* gap, const float* u, float* q,
                                cudaStream_t s) {

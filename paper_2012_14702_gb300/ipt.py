@@ -341,6 +341,29 @@ _lib.ipt_check_map_division.argtypes = [_i64, _vp, _vp, _vp, _vp]
 _lib.ipt_check_map_division.restype = _i32
 
 
+_lib.ipt_check_conversions.argtypes = [_i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
+_lib.ipt_check_conversions.restype = _i32
+
+
+def check_conversions(x, stream=None):
+    """The integer-ALU conversions of the sparse setup for a CUDA float64 vector:
+    returns (hi, lo, f, back, ok) as ipt_check_conversions defines them
+    (synchronises the stream)."""
+    x = _dev(x, torch.float64, "x").contiguous()
+    hi = torch.empty(x.numel(), dtype=torch.float32, device=x.device)
+    lo = torch.empty_like(hi)
+    f = torch.empty_like(hi)
+    back = torch.empty(x.numel(), dtype=torch.float64, device=x.device)
+    ok = torch.empty(x.numel(), dtype=torch.int32, device=x.device)
+    s = stream if stream is not None else torch.cuda.current_stream()
+    st = _lib.ipt_check_conversions(x.numel(), _ptr(x), _ptr(hi), _ptr(lo), _ptr(f), _ptr(back),
+                                    _ptr(ok), C.c_void_p(s.cuda_stream))
+    if st != 0:
+        raise RuntimeError(f"ipt_check_conversions: {STATUS.get(st, st)}")
+    s.synchronize()
+    return hi, lo, f, back, ok
+
+
 def check_map_division(gap, u, stream=None):
     """u / gap as the FP32 map computes it (refined reciprocal), for CUDA float32
     vectors of equal length; returns the quotients (synchronises the stream)."""
