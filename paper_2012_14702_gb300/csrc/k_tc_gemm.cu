@@ -133,23 +133,39 @@ __device__ __forceinline__ void mbar_arrive_cluster(uint32_t cluster_addr) {
                : "memory");
 }
 
+// Operand loads carry an L2 policy: with IPT_OPERAND_EVICT_LAST the operand
+// panels are marked evict-last, so the epilogue's streamed iterate, P_b and F
+// (evict-first) do not push them out of L2 between the tiles that reuse them.
+#ifndef IPT_OPERAND_EVICT_LAST
+#define IPT_OPERAND_EVICT_LAST 1
+#endif
+__device__ __forceinline__ uint64_t operand_policy() {
+  uint64_t p;
+#if IPT_OPERAND_EVICT_LAST
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+#else
+  asm volatile("createpolicy.fractional.L2::evict_normal.b64 %0, 1.0;" : "=l"(p));
+#endif
+  return p;
+}
+
 __device__ __forceinline__ void tma_load(void* dst, const CUtensorMap* map, uint64_t* bar, int x,
-                                         int y) {
+                                         int y, uint64_t policy) {
   asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%3, %4}], [%2];" ::"r"(su32(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(su32(bar)), "r"(x), "r"(y)
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
+      " [%0], [%1, {%3, %4}], [%2], %5;" ::"r"(su32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(su32(bar)), "r"(x), "r"(y), "l"(policy)
       : "memory");
 }
 
 // Load whose completion is counted on an mbarrier of either CTA of the pair
 // (`bar` is a shared::cluster address, here always the pair's first CTA).
 __device__ __forceinline__ void tma_load_pair(void* dst, const CUtensorMap* map, uint32_t bar,
-                                              int x, int y) {
+                                              int x, int y, uint64_t policy) {
   asm volatile(
       "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%3, %4}], [%2];" ::"r"(su32(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(x), "r"(y)
+      ".L2::cache_hint [%0], [%1, {%3, %4}], [%2], %5;" ::"r"(su32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(x), "r"(y), "l"(policy)
       : "memory");
 }
 
@@ -373,6 +389,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   if (warp == 0) {
     // ------------------------------------------------ TMA producer
     if (lane == 0) {
+      const uint64_t pol = operand_policy();
       int pend_parity[STAGES];
       for (int s = 0; s < STAGES; ++s) pend_parity[s] = -1;
       int stage = 0;
@@ -398,16 +415,16 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             if constexpr (PAIR) {
               const uint32_t fb = peer_addr(&ctl->full[stage], 0);
               if (leader) mbar_expect_tx(&ctl->full[stage], 4 * STAGE_BYTES);
-              tma_load_pair(a0, &tmDh, fb, kx, mb * BM);
-              tma_load_pair(a0 + A_BYTES, &tmDl, fb, kx, mb * BM);
-              tma_load_pair(b0, tmBh, fb, kx, nb * BN + rank * (BN / 2));
-              tma_load_pair(b0 + B_BYTES, tmBl, fb, kx, nb * BN + rank * (BN / 2));
+              tma_load_pair(a0, &tmDh, fb, kx, mb * BM, pol);
+              tma_load_pair(a0 + A_BYTES, &tmDl, fb, kx, mb * BM, pol);
+              tma_load_pair(b0, tmBh, fb, kx, nb * BN + rank * (BN / 2), pol);
+              tma_load_pair(b0 + B_BYTES, tmBl, fb, kx, nb * BN + rank * (BN / 2), pol);
             } else {
               mbar_expect_tx(&ctl->full[stage], 2 * STAGE_BYTES);
-              tma_load(a0, &tmDh, &ctl->full[stage], kx, mb * BM);
-              tma_load(a0 + A_BYTES, &tmDl, &ctl->full[stage], kx, mb * BM);
-              tma_load(b0, tmBh, &ctl->full[stage], kx, nb * BN);
-              tma_load(b0 + B_BYTES, tmBl, &ctl->full[stage], kx, nb * BN);
+              tma_load(a0, &tmDh, &ctl->full[stage], kx, mb * BM, pol);
+              tma_load(a0 + A_BYTES, &tmDl, &ctl->full[stage], kx, mb * BM, pol);
+              tma_load(b0, tmBh, &ctl->full[stage], kx, nb * BN, pol);
+              tma_load(b0 + B_BYTES, tmBl, &ctl->full[stage], kx, nb * BN, pol);
             }
             pend_parity[stage] = (int)phase;
             if (++stage == nstages) {
@@ -424,12 +441,12 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
           if constexpr (PAIR) {
             const uint32_t fb = peer_addr(&ctl->full[stage], 0);
             if (leader) mbar_expect_tx(&ctl->full[stage], 2 * STAGE_BYTES);
-            tma_load_pair(sA + stage * A_BYTES, mA, fb, kx, mb * BM);
-            tma_load_pair(sB + stage * B_BYTES, mB, fb, kx, nb * BN + rank * (BN / 2));
+            tma_load_pair(sA + stage * A_BYTES, mA, fb, kx, mb * BM, pol);
+            tma_load_pair(sB + stage * B_BYTES, mB, fb, kx, nb * BN + rank * (BN / 2), pol);
           } else {
             mbar_expect_tx(&ctl->full[stage], STAGE_BYTES);
-            tma_load(sA + stage * A_BYTES, mA, &ctl->full[stage], kx, mb * BM);
-            tma_load(sB + stage * B_BYTES, mB, &ctl->full[stage], kx, nb * BN);
+            tma_load(sA + stage * A_BYTES, mA, &ctl->full[stage], kx, mb * BM, pol);
+            tma_load(sB + stage * B_BYTES, mB, &ctl->full[stage], kx, nb * BN, pol);
           }
           pend_parity[stage] = (int)phase;
           if (++stage == nstages) {
