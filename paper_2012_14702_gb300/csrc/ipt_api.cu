@@ -1508,12 +1508,12 @@ ipt_status ipt_solve_csr(ipt_handle* h, int64_t n, int64_t nnz, const int32_t* r
   }
   h->csr_n = -1;  // contents unknown until this solve ends
   CK(cudaMemsetAsync(h->count.p, 0, (size_t)n * 4, s));
-  launch_validate(cols, ni, ki, kk, nullptr, (int32_t*)h->icol.p, (int*)h->count.p, st, s);
+  launch_validate_csr(cols, ni, ki, kk, (int32_t*)h->icol.p, (int*)h->count.p, h->z[0].p,
+                      f64 ? 1 : 0, st, s);
   launch_csr_rows(rowptr, colind, vals, v_dtype, theta, ni, nnz, (const int*)h->count.p,
                   (double*)h->theta.p, (float*)h->thh.p, (float*)h->thl.p, (double*)h->delta.p,
                   (double*)h->cpart.p, opt.csr_window ? 1 : 0, st, s);
-  launch_csr_units((const int32_t*)h->icol.p, ki, kk, h->z[0].p, f64 ? 1 : 0, s);
-  h->launches += 5;
+  h->launches += 2;
   CK(cudaGetLastError());
   if (tm.on) cudaEventRecord(h->ev[5], s);
   ControlArgs ca;
@@ -1543,23 +1543,16 @@ ipt_status ipt_solve_csr(ipt_handle* h, int64_t n, int64_t nnz, const int32_t* r
     double* dinner = (double*)h->acx_d.p;
     for (int q = 0; q < planned; ++q) {
       double* dq = q == 0 ? (double*)h->d.p : dinner + (size_t)(q - 1) * kk;
-      if (tm.on) cudaEventRecord(h->evb[4 * q], s);
-      launch_csr_prepass(rowptr, colind, vals, v_dtype, (const double*)h->delta.p,
-                         (const int32_t*)h->icol.p, kk, h->z[q].p, f64 ? 1 : 0, dq, st, s);
-      if (tm.on) {
-        cudaEventRecord(h->evb[4 * q + 1], s);
-        cudaEventRecord(h->evb[4 * q + 2], s);
-      }
-      launch_csr_spmm_map(rowptr, colind, vals, v_dtype, (const double*)h->delta.p,
-                          (const double*)h->theta.p, (const float*)h->thh.p,
-                          (const float*)h->thl.p, (const int32_t*)h->icol.p, dq, ni, ki, kk,
-                          h->z[q].p, h->z[q + 1].p, f64 ? 1 : 0, nblk, st, s);
-      if (tm.on) cudaEventRecord(h->evb[4 * q + 3], s);
+      h->launches += launch_csr_evaluate(
+          rowptr, colind, vals, v_dtype, (const double*)h->delta.p, (const double*)h->theta.p,
+          (const float*)h->thh.p, (const float*)h->thl.p, (const int32_t*)h->icol.p, dq, ni, ki,
+          kk, h->z[q].p, h->z[q + 1].p, f64 ? 1 : 0, nblk, st, s,
+          tm.on ? h->evb + 4 * q : nullptr);
       ControlArgs cq = ca;
       cq.acx = 1;
       cq.test = q == 0 ? 1 : 0;
-      launch_control(st, cq, s);
-      h->launches += 3;
+      launch_control(st, cq, s, true);
+      h->launches += 1;
     }
     if (planned == order) {
       launch_acx_combine_rm(h->z[0].p, h->z[1].p, h->z[2].p, h->z[order == 3 ? 3 : 2].p,
@@ -1569,7 +1562,7 @@ ipt_status ipt_solve_csr(ipt_handle* h, int64_t n, int64_t nnz, const int32_t* r
       h->launches += opt.csr_window ? 4 : 3;
     }
     if (cudaGetLastError() != cudaSuccess ||
-        cudaMemcpyAsync(h->hst, st, kStateHead, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemcpyAsync(h->hst, st, sizeof(DevState), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess) {
       v = IPT_CUDA_ERROR;
       break;
@@ -1596,25 +1589,16 @@ ipt_status ipt_solve_csr(ipt_handle* h, int64_t n, int64_t nnz, const int32_t* r
     const int nb = std::min(kCsrChunk, max_iter - it0);
     for (int q = 0; q < nb; ++q) {
       const int cur = (it0 + q) & 1;
-      if (tm.on) cudaEventRecord(h->evb[4 * q], s);
-      launch_csr_prepass(rowptr, colind, vals, v_dtype, (const double*)h->delta.p,
-                         (const int32_t*)h->icol.p, kk, h->z[cur].p, f64 ? 1 : 0,
-                         (double*)h->d.p, st, s);
-      if (tm.on) {
-        cudaEventRecord(h->evb[4 * q + 1], s);
-        cudaEventRecord(h->evb[4 * q + 2], s);
-      }
-      launch_csr_spmm_map(rowptr, colind, vals, v_dtype, (const double*)h->delta.p,
-                          (const double*)h->theta.p, (const float*)h->thh.p,
-                          (const float*)h->thl.p, (const int32_t*)h->icol.p,
-                          (const double*)h->d.p, ni, ki, kk, h->z[cur].p, h->z[cur ^ 1].p,
-                          f64 ? 1 : 0, nblk, st, s);
-      if (tm.on) cudaEventRecord(h->evb[4 * q + 3], s);
-      launch_control(st, ca, s);
-      h->launches += 3;
+      h->launches += launch_csr_evaluate(
+          rowptr, colind, vals, v_dtype, (const double*)h->delta.p, (const double*)h->theta.p,
+          (const float*)h->thh.p, (const float*)h->thl.p, (const int32_t*)h->icol.p,
+          (double*)h->d.p, ni, ki, kk, h->z[cur].p, h->z[cur ^ 1].p, f64 ? 1 : 0, nblk, st, s,
+          tm.on ? h->evb + 4 * q : nullptr);
+      launch_control(st, ca, s, true);
+      h->launches += 1;
     }
     if (cudaGetLastError() != cudaSuccess ||
-        cudaMemcpyAsync(h->hst, st, kStateHead, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemcpyAsync(h->hst, st, sizeof(DevState), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess) {
       v = IPT_CUDA_ERROR;
       break;
@@ -1644,12 +1628,9 @@ ipt_status ipt_solve_csr(ipt_handle* h, int64_t n, int64_t nnz, const int32_t* r
     out->status = v;
     return v;
   }
-  DevState hs;
-  if (cudaMemcpyAsync(&hs, st, sizeof(DevState), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-      cudaStreamSynchronize(s) != cudaSuccess) {
-    out->status = IPT_CUDA_ERROR;
-    return IPT_CUDA_ERROR;
-  }
+  // the whole state came back with the last loop synchronisation, after which
+  // no kernel of the solve ran
+  const DevState& hs = *h->hst;
   if (tm.on) cudaEventRecord(h->ev[6], s);
   launch_lambda((const double*)h->theta.p, (const int32_t*)h->icol.p, (const double*)h->d.p, ki,
                 lambda, s);

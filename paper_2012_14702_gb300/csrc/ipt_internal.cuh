@@ -91,6 +91,7 @@ struct DevState {
   int flags;   // validation flags
   int timeout; // bounded device wait gave up (code of the waiting role)
   int stage_iters[2];
+  int rows_done;       // blocks of the sparse row pass that have finished
   // CSR active window (rows outside it are exactly zero in Z and in F):
   int band;            // largest |j - m| over the stored entries of M
   int z_lo, z_hi;      // every nonzero row of the current iterate lies in [z_lo, z_hi]
@@ -182,6 +183,12 @@ void launch_theta(const void* M, int64_t ldm, int m_dtype, const double* theta_i
                   cudaStream_t s);
 void launch_validate(const int32_t* cols, int n, int k, int kpad, const double* theta,
                      int32_t* icol, int* count, DevState* st, cudaStream_t s);
+// The sparse path's form (one launch): cols[] checked and counted as above,
+// the requested columns' row range [z_lo, z_hi] recorded, and the unit entries
+// of Z0 = E written into the row-major n x kk iterate Z (zero elsewhere
+// already); duplicates are flagged by the row pass (count[j] > 1).
+void launch_validate_csr(const int32_t* cols, int n, int k, int kk, int32_t* icol, int* count,
+                         void* Z, int zf64, DevState* st, cudaStream_t s);
 void launch_form_delta(const void* M, int64_t ldm, int m_dtype, const double* theta, int n,
                        int npad, const int* count, void* Drow, int drow_f64, float* DT,
                        double* r0part, DevState* st, cudaStream_t s);
@@ -364,7 +371,8 @@ void launch_acx_combine(void* z, const void* f1, const void* f2, const void* f3,
 void launch_acx_combine_rm(void* z, const void* f1, const void* f2, const void* f3, int f64,
                            int p, int n, int k, int kk, int window, int global, double* acc,
                            double* sigma, DevState* st, int blocks, cudaStream_t s);
-void launch_control(DevState* st, ControlArgs a, cudaStream_t s);
+// pdl: programmatic dependent launch (the sparse loop's chain of launches)
+void launch_control(DevState* st, ControlArgs a, cudaStream_t s, bool pdl = false);
 
 // Sampled error of the product just computed (k_sample.cu): the exact
 // (compensated FP32) Delta Z at the sample rows of psmp against the stored P,
@@ -393,16 +401,18 @@ void launch_csr_rows(const int32_t* rowptr, const int32_t* colind, const void* v
                      const double* theta_in, int n, int64_t nnz, const int* count, double* theta,
                      float* th_hi, float* th_lo, double* delta, double* part, int window,
                      DevState* st, cudaStream_t s);
-// Z[cols[c], c] = 1 in the row-major n x kk iterate (the rest already zero).
-void launch_csr_units(const int32_t* icol, int k, int kk, void* Z, int f64, cudaStream_t s);
 void launch_csr_prepass(const int32_t* rowptr, const int32_t* colind, const void* vals,
                         int v_dtype, const double* delta, const int32_t* icol, int kk,
                         const void* Z, int f64, double* d, DevState* st, cudaStream_t s);
-void launch_csr_spmm_map(const int32_t* rowptr, const int32_t* colind, const void* vals,
-                         int v_dtype, const double* delta, const double* theta,
-                         const float* th_hi, const float* th_lo, const int32_t* icol,
-                         const double* d, int n, int k, int kk, const void* Zin, void* Fout,
-                         int f64, int nblk, DevState* st, cudaStream_t s);
+// One sparse evaluation: d (in the SpMM for kk <= 512 columns, else a separate
+// pre-pass launch) and the SpMM + map.  With `ev` (4 events): ev[0], ev[1]
+// around the separate pre-pass, ev[2], ev[3] around the SpMM.  Returns the
+// number of kernel launches.
+int launch_csr_evaluate(const int32_t* rowptr, const int32_t* colind, const void* vals,
+                        int v_dtype, const double* delta, const double* theta,
+                        const float* th_hi, const float* th_lo, const int32_t* icol, double* d,
+                        int n, int k, int kk, const void* Zin, void* Fout, int f64, int nblk,
+                        DevState* st, cudaStream_t s, const cudaEvent_t* ev = nullptr);
 // adds ||M Z - Z Lambda||_F^2 (FP64) of the row-major iterate to *acc
 void launch_csr_residual64(const int32_t* rowptr, const int32_t* colind, const void* vals,
                            int v_dtype, int n, int k, int kk, const void* Z, int f64,
@@ -412,6 +422,34 @@ void launch_csr_out(const void* Z, int f64, int j_lo, int n, int k, int kk, void
                     int64_t ldo, int out_f64, cudaStream_t s);
 
 // ---------------------------------------------------------------- device helpers
+// Programmatic dependent launch.  A kernel launched with launch_pdl may be
+// scheduled while the previous kernel of its stream is still running; it runs
+// griddep_wait() (which returns once that kernel has completed and its memory
+// is visible; at once for a plain launch) before it touches any memory the
+// earlier kernels read or write.  griddep_launch() lets the next such launch
+// be scheduled early.
+__device__ __forceinline__ void griddep_wait() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+__device__ __forceinline__ void griddep_launch() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                              cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

@@ -10,8 +10,9 @@
 // the CSR loop skips stored diagonal entries.
 //
 // Kernels: the diagonal pre-pass d_c = (Delta Z)_{cols[c], c} (one warp per
-// column: a sparse row dot product), the SpMM + map, and the transpose of the
-// result to the column-major output of the C ABI.  The setup pass over the rows
+// column: a sparse row dot product; inside the SpMM for up to kFusedD
+// columns), the SpMM + map, and the transpose of the result to the
+// column-major output of the C ABI.  The setup pass over the rows
 // and the FP64 residual are in k_csr_setup.cu.
 #include "ipt_internal.cuh"
 
@@ -30,7 +31,34 @@ __device__ __forceinline__ T ldval(const void* v, int64_t i, int dt) {
 }
 
 // d_c = sum_m Delta_{i_c, m} Z_{m, c} = delta_{i_c} Z_{i_c, c} + sum over the
-// off-diagonal stored entries of row i_c.  One warp per column.
+// off-diagonal stored entries of row i_c, by a group of 4 consecutive lanes
+// (`sub` = lane & 3): each lane sums every 4th entry in storage order, the
+// group adds its four sums pairwise (valid in every lane of the group).  Rows
+// of the sparse workloads hold ~17 entries, so one dependent chain of loads
+// per column, with 8 columns per warp in flight.
+template <typename T>
+__device__ __forceinline__ double csr_d_column(const int32_t* __restrict__ rowptr,
+                                               const int32_t* __restrict__ colind,
+                                               const void* __restrict__ vals, int v_dtype,
+                                               const double* __restrict__ delta,
+                                               const int32_t* __restrict__ icol, int kk,
+                                               const T* __restrict__ Z, int c, int sub) {
+  const int i = c < kk ? icol[c] : -1;
+  double s = 0.0;
+  if (i >= 0) {
+    const int e1 = rowptr[i + 1];
+    for (int e = rowptr[i] + sub; e < e1; e += 4) {
+      const int m = colind[e];
+      if (m != i) s += ldval<double>(vals, e, v_dtype) * (double)Z[(int64_t)m * kk + c];
+    }
+  }
+  s += __shfl_xor_sync(0xffffffffu, s, 1);
+  s += __shfl_xor_sync(0xffffffffu, s, 2);
+  return i >= 0 ? s + delta[i] * (double)Z[(int64_t)i * kk + c] : 0.0;
+}
+
+// The pre-pass as its own launch (iterates wider than the SpMM's shared d):
+// four lanes per column.
 template <typename T>
 __global__ void k_csr_prepass(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colind,
                               const void* __restrict__ vals, int v_dtype,
@@ -38,21 +66,17 @@ __global__ void k_csr_prepass(const int32_t* __restrict__ rowptr, const int32_t*
                               int kk, const T* __restrict__ Z, double* __restrict__ d,
                               const DevState* st) {
   if (st->done || (st->flags & FLAG_CSR_INDEX)) return;
-  const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-  if (c >= kk) return;
-  const int i = icol[c];
-  if (i < 0) {
-    if (lane == 0) d[c] = 0.0;
-    return;
-  }
-  double s = 0.0;
-  for (int e = rowptr[i] + lane; e < rowptr[i + 1]; e += 32) {
-    const int m = colind[e];
-    if (m != i) s += ldval<double>(vals, e, v_dtype) * (double)Z[(int64_t)m * kk + c];
-  }
-  s = warp_sum(s);
-  if (lane == 0) d[c] = s + delta[i] * (double)Z[(int64_t)i * kk + c];
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int c = t >> 2;  // whole warps stay in the loop (the group shuffles)
+  const double v = csr_d_column<T>(rowptr, colind, vals, v_dtype, delta, icol, kk, Z, c, t & 3);
+  if ((t & 3) == 0 && c < kk) d[c] = v;
 }
+
+// Widest iterate (kk columns) whose d the SpMM computes itself, in shared memory.
+#ifndef IPT_CSR_FUSED_D
+#define IPT_CSR_FUSED_D 512
+#endif
+constexpr int kFusedD = IPT_CSR_FUSED_D;
 
 template <typename T>
 struct Two;
@@ -85,14 +109,21 @@ struct Four<double> {
 // applied in the epilogue).  Only rows [win_lo, win_hi) are evaluated (all
 // rows unless the active window is on); the row range of the nonzero rows of
 // F is recorded for the next window.  Norm partials: one atomic per warp.
+// With fuse_d (kk <= kFusedD) the kernel forms d itself: every CTA that
+// evaluates a row computes all kk values into shared memory (four lanes per
+// column, as the separate pre-pass does, so the values are the same), and the
+// first CTA also stores them to d_out; otherwise d comes from the pre-pass.
 template <typename T>
 __global__ void __launch_bounds__(256, 4)
     k_csr_spmm_map(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colind,
                    const void* __restrict__ vals, int v_dtype, const double* __restrict__ delta,
                    const double* __restrict__ theta, const float* __restrict__ th_hi,
                    const float* __restrict__ th_lo, const int32_t* __restrict__ icol,
-                   const double* __restrict__ d, int n, int k, int kk, const T* __restrict__ Zin,
-                   T* __restrict__ Fout, DevState* st) {
+                   const double* __restrict__ d, double* __restrict__ d_out, int fuse_d, int n,
+                   int k, int kk, const T* __restrict__ Zin, T* __restrict__ Fout,
+                   DevState* st) {
+  griddep_wait();  // launched with programmatic dependent launch in the loop
+  griddep_launch();
   if (st->done || (st->flags & FLAG_CSR_INDEX)) return;
   using V4 = typename Four<T>::V;
   const int lane = threadIdx.x & 31, hl = lane & 15;
@@ -100,6 +131,21 @@ __global__ void __launch_bounds__(256, 4)
   const int half0 = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 2 + (lane >> 4);
   const int nhalves = gridDim.x * (blockDim.x >> 5) * 2;
   const int wlo = st->win_lo, whi = st->win_hi;
+  __shared__ double sd[kFusedD > 0 ? kFusedD : 1];
+  if (fuse_d) {
+    if (wlo + (int)blockIdx.x * (int)(blockDim.x >> 5) * 2 < whi || blockIdx.x == 0) {
+      for (int c0 = 0; c0 < kk; c0 += (int)blockDim.x >> 2) {
+        const int c = c0 + (threadIdx.x >> 2);
+        const double v = csr_d_column<T>(rowptr, colind, vals, v_dtype, delta, icol, kk, Zin,
+                                         c, threadIdx.x & 3);
+        if ((threadIdx.x & 3) == 0 && c < kk) {
+          sd[c] = v;
+          if (blockIdx.x == 0) d_out[c] = v;
+        }
+      }
+    }
+    __syncthreads();
+  }
   T s_inc = T(0), s_z = T(0), s_r = T(0);
   int f_lo = n, f_hi = -1;
   for (int ch = 0; ch < kk; ch += 64) {
@@ -111,7 +157,7 @@ __global__ void __launch_bounds__(256, 4)
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       ic[u] = icol[cb + u];
-      dc[u] = (T)d[cb + u];
+      dc[u] = (T)(fuse_d ? sd[cb + u] : d[cb + u]);
       tc[u] = ic[u] >= 0 ? theta[ic[u]] : 0.0;
       hc[u] = ic[u] >= 0 ? th_hi[ic[u]] : 0.f;
       lc[u] = ic[u] >= 0 ? th_lo[ic[u]] : 0.f;
@@ -275,7 +321,7 @@ inline unsigned nblocks(int64_t total, int bs) { return (unsigned)((total + bs -
 void launch_csr_prepass(const int32_t* rowptr, const int32_t* colind, const void* vals,
                         int v_dtype, const double* delta, const int32_t* icol, int kk,
                         const void* Z, int f64, double* d, DevState* st, cudaStream_t s) {
-  const unsigned g = nblocks((int64_t)kk * 32, 256);
+  const unsigned g = nblocks((int64_t)kk * 4, 256);
   if (f64)
     k_csr_prepass<double><<<g, 256, 0, s>>>(rowptr, colind, vals, v_dtype, delta, icol, kk,
                                             (const double*)Z, d, st);
@@ -284,19 +330,28 @@ void launch_csr_prepass(const int32_t* rowptr, const int32_t* colind, const void
                                            (const float*)Z, d, st);
 }
 
-void launch_csr_spmm_map(const int32_t* rowptr, const int32_t* colind, const void* vals,
-                         int v_dtype, const double* delta, const double* theta,
-                         const float* th_hi, const float* th_lo, const int32_t* icol,
-                         const double* d, int n, int k, int kk, const void* Zin, void* Fout,
-                         int f64, int nblk, DevState* st, cudaStream_t s) {
+int launch_csr_evaluate(const int32_t* rowptr, const int32_t* colind, const void* vals,
+                        int v_dtype, const double* delta, const double* theta,
+                        const float* th_hi, const float* th_lo, const int32_t* icol, double* d,
+                        int n, int k, int kk, const void* Zin, void* Fout, int f64, int nblk,
+                        DevState* st, cudaStream_t s, const cudaEvent_t* ev) {
+  const int fuse = kk <= kFusedD ? 1 : 0;
+  if (ev) cudaEventRecord(ev[0], s);
+  if (!fuse) launch_csr_prepass(rowptr, colind, vals, v_dtype, delta, icol, kk, Zin, f64, d, st, s);
+  if (ev) {
+    cudaEventRecord(ev[1], s);
+    cudaEventRecord(ev[2], s);
+  }
   if (f64)
-    k_csr_spmm_map<double><<<nblk, 256, 0, s>>>(rowptr, colind, vals, v_dtype, delta, theta,
-                                                th_hi, th_lo, icol, d, n, k, kk,
-                                                (const double*)Zin, (double*)Fout, st);
+    launch_pdl(k_csr_spmm_map<double>, dim3(nblk), dim3(256), 0, s, rowptr, colind, vals,
+               v_dtype, delta, theta, th_hi, th_lo, icol, (const double*)d, d, fuse, n, k, kk,
+               (const double*)Zin, (double*)Fout, st);
   else
-    k_csr_spmm_map<float><<<nblk, 256, 0, s>>>(rowptr, colind, vals, v_dtype, delta, theta,
-                                               th_hi, th_lo, icol, d, n, k, kk,
-                                               (const float*)Zin, (float*)Fout, st);
+    launch_pdl(k_csr_spmm_map<float>, dim3(nblk), dim3(256), 0, s, rowptr, colind, vals,
+               v_dtype, delta, theta, th_hi, th_lo, icol, (const double*)d, d, fuse, n, k, kk,
+               (const float*)Zin, (float*)Fout, st);
+  if (ev) cudaEventRecord(ev[3], s);
+  return fuse ? 1 : 2;
 }
 
 void launch_csr_out(const void* Z, int f64, int j_lo, int n, int k, int kk, void* out,

@@ -1,10 +1,11 @@
 // Sparse IPT, the kernels outside the evaluation loop: the one setup pass over
 // the rows of M (CSR structure check, theta, delta_j = M_jj - theta_j, the
-// residual normaliser ||M Z0 - Z0 Lambda0||, the band and the support of
-// Z0 = E), the unit columns of Z0, and the FP64 residual ||M Z - Z Lambda||_F
-// that verifies a result.
+// residual normaliser ||M Z0 - Z0 Lambda0|| and the band; the support of
+// Z0 = E and its unit entries come from the column validation), and the FP64
+// residual ||M Z - Z Lambda||_F that verifies a result.
 #include "ipt_internal.cuh"
 
+#include <limits.h>
 #include <math.h>
 
 #include <algorithm>
@@ -13,50 +14,88 @@ namespace ipt {
 
 namespace {
 
-template <typename T>
-__device__ __forceinline__ T ldval(const void* v, int64_t i, int dt) {
-  return dt == IPT_DTYPE_F64 ? (T) static_cast<const double*>(v)[i]
-                             : (T) static_cast<const float*>(v)[i];
-}
-
 inline unsigned nblocks(int64_t total, int bs) { return (unsigned)((total + bs - 1) / bs); }
+
+// The per-row values of the row pass with plain FP64 arithmetic, for the rows
+// the integer conversions do not cover (repeated diagonal entries of FP32
+// input, values outside FP32's normal range).  Out of line, so that the common
+// path issues no FP64-pipe instructions.  The stored diagonal: the first entry
+// as stored, later ones (repeated entries) added in FP64 in storage order.
+struct RowValues {
+  double mjj, th, dj;
+  float h, l, d;
+};
+__device__ __noinline__ RowValues csr_row_values_slow(const int32_t* __restrict__ colind,
+                                                      const void* __restrict__ vals,
+                                                      int v_dtype, int j, int e0, int e1,
+                                                      const double* __restrict__ theta_in,
+                                                      double mjj) {
+  if (v_dtype != IPT_DTYPE_F64) {
+    const float* v32 = static_cast<const float*>(vals);
+    double first = 0.0, rest = 0.0;
+    bool seen = false;
+    for (int x = e0; x < e1; ++x) {
+      if (colind[x] != j) continue;
+      if (seen) rest += (double)v32[x];
+      else first = (double)v32[x];
+      seen = true;
+    }
+    mjj = first + rest;
+  }
+  RowValues r;
+  r.mjj = mjj;
+  r.th = theta_in ? theta_in[j] : mjj;
+  r.h = (float)r.th;
+  r.l = (float)(r.th - (double)r.h);
+  r.dj = theta_in ? mjj - r.th : 0.0;
+  r.d = (float)r.dj;
+  return r;
+}
 
 // One pass over the rows, a block per 256 consecutive rows, a warp per 32 of
 // them: the warp copies its rows' stored entries (one contiguous range of the
 // CSR arrays) into shared memory in chunks with coalesced loads, then each lane
-// walks its own row there, with the gathers of count[] of kU entries in flight
-// at a time.  Per row: the CSR structure check (row bounds within [0, nnz] and
-// ascending, column indices in [0, n); a bad row is flagged, and the later CSR
-// kernels then do nothing), the stored diagonal M_jj (0 if the row stores
+// walks its own row there, keeping the row's smallest and largest column
+// index (its bounds check and its band).  Per row: the CSR structure check
+// (row bounds within [0, nnz] and ascending, column indices in [0, n); a bad
+// row is flagged, and the later CSR kernels then do nothing), the stored
+// diagonal M_jj (0 if the row stores
 // none; repeated diagonal entries add up, as in the product), theta_j (given,
 // or M_jj), its FP32 split and delta_j = M_jj - theta_j; non-finite theta is
 // flagged.  Per block: the partial of ||M Z0 - Z0 Lambda0||^2 (the squared
-// off-diagonal entries in requested columns, count[col] > 0), the band
-// max |j - m| of the stored entries and the row range of the requested rows
-// (the support of Z0 = E).
+// off-diagonal entries in requested columns, count[col] > 0) and the band
+// max |j - m| of the stored entries; the last block to finish sums the
+// partials and sets the first window.  The requested columns' range
+// [z_lo, z_hi] (set by the column validation before this pass) filters the
+// count[] gathers: an entry outside it is in no requested column.
 __global__ void __launch_bounds__(256, 4)
     k_csr_rows(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colind,
                const void* __restrict__ vals, int v_dtype, const double* __restrict__ theta_in,
                int n, int64_t nnz, const int* __restrict__ count, double* __restrict__ theta,
                float* __restrict__ th_hi, float* __restrict__ th_lo, double* __restrict__ delta,
-               double* __restrict__ part, DevState* st) {
-  constexpr int kW = 512, kU = 4;  // entries per warp chunk; gathers in flight per lane
+               double* __restrict__ part, int window, DevState* st) {
+  constexpr int kW = 512;  // entries per warp chunk
   __shared__ int scol[8][kW];
-  __shared__ float sval[8][kW];
+  __shared__ float sval[8][kW];  // FP32 input only
   const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
   const int j = blockIdx.x * 256 + threadIdx.x;  // this lane's row
   const bool live = j < n;
+  const bool f64in = v_dtype == IPT_DTYPE_F64;
   float r0 = 0.f;
-  int band = 0, lo = n, hi = -1;
+  int band = 0;
   bool bad = false;
+  // requested columns: [clo, chi] (none if chi < clo)
+  const int clo = st->z_lo, chi = st->z_hi;
+  const bool anyreq = chi >= clo;
+  const unsigned span = (unsigned)(chi - clo);
   int e0 = 0, e1 = 0;  // the row's entries, clamped to [0, nnz]
   if (live) {
+    if (count[j] > 1) atomicOr(&st->flags, FLAG_COL_DUP);  // a column requested twice
     const int r0p = rowptr[j], r1p = rowptr[j + 1];
     bad = !(r0p >= 0 && r0p <= r1p && (int64_t)r1p <= nnz && (j > 0 || r0p == 0) &&
             (j + 1 < n || (int64_t)r1p == nnz));
     e0 = (int)min((int64_t)max(r0p, 0), nnz);
     e1 = max(e0, (int)min((int64_t)max(r1p, 0), nnz));
-    if (count[j] > 0) lo = hi = j;
   }
   // the warp's range: from its first live row's start to its last live row's end
   const unsigned live_mask = __ballot_sync(0xffffffffu, live);
@@ -64,168 +103,143 @@ __global__ void __launch_bounds__(256, 4)
   E0 = __shfl_sync(0xffffffffu, E0, live_mask ? __ffs(live_mask) - 1 : 0);
   E1 = __shfl_sync(0xffffffffu, E1, live_mask ? 31 - __clz(live_mask) : 0);
   E1 = max(E1, E0);
-  // the stored diagonal: the first entry kept as stored, later ones (repeated
-  // entries) added in FP64
-  int ndiag = 0;
+  // per row: the smallest and largest column index (bounds and band), and the
+  // stored diagonal: FP64 input summed in FP64; FP32 input's first entry
+  int mmin = INT_MAX, mmax = INT_MIN, ndiag = 0;
   float d32 = 0.f;
   double d64 = 0.0;
   for (int cs = E0; cs < E1; cs += kW) {
     const int ce = min(cs + kW, E1);
     __syncwarp();
     // all of the chunk's loads of a lane (kW / 32 of each array) in flight before
-    // its shared-memory stores
+    // its shared-memory stores; FP64 values stay in global memory (read for the
+    // diagonal and the requested columns only)
     constexpr int kPer = kW / 32;
     int cv[kPer];
     float vv[kPer];
-    if (v_dtype == IPT_DTYPE_F64) {
-      const double* v64 = static_cast<const double*>(vals);
+    const float* v32 = static_cast<const float*>(vals);
 #pragma unroll
-      for (int q = 0; q < kPer; ++q) {
-        const int x = cs + lane + 32 * q;
-        cv[q] = x < ce ? colind[x] : 0;
-        vv[q] = x < ce ? (float)v64[x] : 0.f;
-      }
-    } else {  // FP32 values stay FP32 (FP64 conversions run on the narrow FP64 pipe)
-      const float* v32 = static_cast<const float*>(vals);
-#pragma unroll
-      for (int q = 0; q < kPer; ++q) {
-        const int x = cs + lane + 32 * q;
-        cv[q] = x < ce ? colind[x] : 0;
-        vv[q] = x < ce ? v32[x] : 0.f;
-      }
+    for (int q = 0; q < kPer; ++q) {
+      const int x = cs + lane + 32 * q;
+      cv[q] = x < ce ? colind[x] : 0;
+      vv[q] = (!f64in && x < ce) ? v32[x] : 0.f;
     }
 #pragma unroll
     for (int q = 0; q < kPer; ++q) {
       scol[wq][lane + 32 * q] = cv[q];
-      sval[wq][lane + 32 * q] = vv[q];
+      if (!f64in) sval[wq][lane + 32 * q] = vv[q];
     }
     __syncwarp();
     const int xb = max(e0, cs), xe = min(e1, ce);
-    for (int x = xb; x < xe; x += kU) {
-      int m[kU], cnt[kU];
-#pragma unroll
-      for (int u = 0; u < kU; ++u) {
-        m[u] = x + u < xe ? scol[wq][x + u - cs] : -1;
-        cnt[u] = (m[u] >= 0 && m[u] < n && m[u] != j) ? count[m[u]] : 0;
-      }
-#pragma unroll
-      for (int u = 0; u < kU; ++u) {
-        if (x + u >= xe) break;
-        if (m[u] < 0 || m[u] >= n) {
-          bad = true;
-          continue;
-        }
-        band = max(band, abs(m[u] - j));
-        if (m[u] == j) {
-          if (v_dtype == IPT_DTYPE_F64 || ndiag > 0) d64 += ldval<double>(vals, x + u, v_dtype);
-          else d32 = sval[wq][x + u - cs];  // FP32 input: the value is exact in FP32
-          ++ndiag;
-        } else if (cnt[u] > 0) {
-          const float v = sval[wq][x + u - cs];
-          r0 = fmaf(v, v, r0);
-        }
+#pragma unroll 4
+    for (int x = xb; x < xe; ++x) {
+      const int m = scol[wq][x - cs];
+      mmin = min(mmin, m);
+      mmax = max(mmax, m);
+      // count[] only inside the requested columns' range (so also inside [0, n))
+      const int cm = (anyreq && (unsigned)(m - clo) <= span) ? count[m] : 0;
+      if (m == j) {
+        if (f64in) d64 += static_cast<const double*>(vals)[x];
+        else if (ndiag == 0) d32 = sval[wq][x - cs];
+        ++ndiag;
+      } else if (cm > 0) {
+        const float v = f64in ? (float)static_cast<const double*>(vals)[x] : sval[wq][x - cs];
+        r0 = fmaf(v, v, r0);
       }
     }
+  }
+  if (live && e1 > e0) {
+    if (mmin < 0 || mmax >= n) bad = true;
+    else band = max(j - mmin, mmax - j);
   }
   if (bad) atomicOr(&st->flags, FLAG_CSR_INDEX);
   if (live) {
     // the FP32 <-> FP64 conversions go through the integer ALU (the FP64 pipe
-    // is narrow); only a given theta costs one FP64 subtraction per row
+    // is narrow); only a given theta costs one FP64 subtraction per row, and
+    // the rare rows the integer forms do not cover take the out-of-line path
+    bool ok = true, ok1;
     double mjj = d64;
     if (v_dtype != IPT_DTYPE_F64 && ndiag > 0) {
-      bool ok;
-      const double v = f32_to_f64_bits(d32, ok);
-      mjj = ok ? v : (double)d32;
-      if (ndiag > 1) mjj += d64;
+      mjj = f32_to_f64_bits(d32, ok1);
+      ok = ok1 && ndiag == 1;
     }
-    const double th = theta_in ? theta_in[j] : mjj;
+    double th = theta_in ? theta_in[j] : mjj;
+    float h, l;
+    split_f64_bits(th, h, l, ok1);
+    ok = ok && ok1;
+    double dj = theta_in ? mjj - th : 0.0;  // theta = M_jj exactly otherwise
+    float d = f64_to_f32_rn_bits(dj, ok1);
+    ok = ok && ok1;
+    if (!ok) {
+      const RowValues r = csr_row_values_slow(colind, vals, v_dtype, j, e0, e1, theta_in, mjj);
+      th = r.th;
+      h = r.h;
+      l = r.l;
+      dj = r.dj;
+      d = r.d;
+    }
     const unsigned long long tb = (unsigned long long)__double_as_longlong(th);
     if (((tb >> 52) & 0x7ffu) == 0x7ffu) atomicOr(&st->flags, FLAG_THETA_NONFINITE);
     theta[j] = th;
-    float h, l;
-    bool ok;
-    split_f64_bits(th, h, l, ok);
-    if (!ok) {
-      h = (float)th;
-      l = (float)(th - (double)h);
-    }
     th_hi[j] = h;
     th_lo[j] = l;
-    const double dj = theta_in ? mjj - th : 0.0;  // theta = M_jj exactly otherwise
     delta[j] = dj;
-    float d = f64_to_f32_rn_bits(dj, ok);
-    if (!ok) d = (float)dj;
     reinterpret_cast<float*>(delta + n)[j] = d;  // FP32 copy for FP32 kernels
   }
-  // block reduction; the shared words take one atomic per block, and only
-  // when the block's value would change them (most blocks see the same band)
+  // block reduction; the band takes one atomic per block, and only when the
+  // block's value would change it (most blocks see the same band)
   __shared__ float red[8];
-  __shared__ int rb[8], rl[8], rh[8];
+  __shared__ int rb[8];
   const float w = warp_sum(r0);
   band = warp_max_int(band);
-  lo = warp_min_int(lo);
-  hi = warp_max_int(hi);
   if ((threadIdx.x & 31) == 0) {
     red[wq] = w;
     rb[wq] = band;
-    rl[wq] = lo;
-    rh[wq] = hi;
   }
+  __shared__ int last;
   __syncthreads();
   if (threadIdx.x == 0) {
     double tot = 0.0;
-    int b = 0, l = n, hh = -1;
+    int b = 0;
     for (int q = 0; q < 8; ++q) {
       tot += (double)red[q];
       b = max(b, rb[q]);
-      l = min(l, rl[q]);
-      hh = max(hh, rh[q]);
     }
     part[blockIdx.x] = tot;
     if (b > *(volatile int*)&st->band) atomicMax(&st->band, b);
-    if (hh >= 0) {
-      atomicMin(&st->z_lo, l);
-      atomicMax(&st->z_hi, hh);
-    }
+    __threadfence();  // this block's partial and band before its arrival
+    last = atomicAdd(&st->rows_done, 1) == (int)gridDim.x - 1;
   }
-}
-
-// One block: ||R0||^2 from the row pass's partials, and the rows the first
-// product evaluates: all of them, or (window) the requested rows widened by
-// the band (rows further away have no stored entry in a nonzero row of E).
-__global__ void __launch_bounds__(1024)
-    k_csr_sum_r0(const double* __restrict__ part, int count, int n, int window, DevState* st) {
-  __shared__ double red[1024];
-  double t = 0.0;
-  for (int i = threadIdx.x; i < count; i += blockDim.x) t += part[i];
-  red[threadIdx.x] = t;
   __syncthreads();
-  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
-    if ((int)threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+  if (!last) return;
+  // The last block to finish: ||R0||^2 from the block partials (a fixed
+  // order: per-thread strided sums, then a tree), and the rows the first
+  // product evaluates: all of them, or (window) the requested rows widened by
+  // the band (rows further away have no stored entry in a nonzero row of E).
+  __threadfence();
+  __shared__ double tree[256];
+  double t = 0.0;
+  for (int i = threadIdx.x; i < (int)gridDim.x; i += 256) t += __ldcg(part + i);
+  tree[threadIdx.x] = t;
+  __syncthreads();
+  for (int h = 128; h > 0; h >>= 1) {
+    if ((int)threadIdx.x < h) tree[threadIdx.x] += tree[threadIdx.x + h];
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    st->r0acc = red[0];
+    volatile DevState* vs = st;
+    const int zl = vs->z_lo, zh = vs->z_hi, bd = vs->band;
+    st->r0acc = tree[0];
     st->nz_lo = n;
     st->nz_hi = -1;
-    if (window && st->z_hi >= st->z_lo) {
-      st->win_lo = max(0, st->z_lo - st->band);
-      st->win_hi = (int)min((int64_t)n, (int64_t)st->z_hi + 1 + st->band);
+    if (window && zh >= zl) {
+      st->win_lo = max(0, zl - bd);
+      st->win_hi = (int)min((int64_t)n, (int64_t)zh + 1 + bd);
     } else {
       st->win_lo = 0;
       st->win_hi = n;
     }
   }
-}
-
-// Z = E in the row-major layout (Z[j*kk + c] = 1 at j = cols[c]); padding
-// zero.  Block: 64 columns x 4 rows; each thread writes one entry per row step.
-template <typename T>
-__global__ void k_csr_units(const int32_t* __restrict__ icol, int k, int kk, T* __restrict__ Z) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= k) return;
-  const int i = icol[c];  // -1 for a column index out of range (flagged)
-  if (i >= 0) Z[(int64_t)i * kk + c] = T(1);
 }
 
 }  // namespace
@@ -236,13 +250,7 @@ void launch_csr_rows(const int32_t* rowptr, const int32_t* colind, const void* v
                      DevState* st, cudaStream_t s) {
   const unsigned g = nblocks(n, 256);  // one block per 256 rows (the partials' capacity)
   k_csr_rows<<<g, 256, 0, s>>>(rowptr, colind, vals, v_dtype, theta_in, n, nnz, count, theta, th_hi,
-                               th_lo, delta, part, st);
-  k_csr_sum_r0<<<1, 1024, 0, s>>>(part, (int)g, n, window, st);
-}
-
-void launch_csr_units(const int32_t* icol, int k, int kk, void* Z, int f64, cudaStream_t s) {
-  if (f64) k_csr_units<double><<<nblocks(k, 256), 256, 0, s>>>(icol, k, kk, (double*)Z);
-  else k_csr_units<float><<<nblocks(k, 256), 256, 0, s>>>(icol, k, kk, (float*)Z);
+                               th_lo, delta, part, window, st);
 }
 
 namespace {

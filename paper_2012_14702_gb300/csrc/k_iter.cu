@@ -839,7 +839,11 @@ __device__ void control_step(DevState* st, const ControlArgs& a) {
   st->prev_rho = rho;
 }
 
-__global__ void k_control(DevState* st, ControlArgs a) { control_step(st, a); }
+__global__ void k_control(DevState* st, ControlArgs a) {
+  griddep_wait();
+  griddep_launch();
+  control_step(st, a);
+}
 
 }  // namespace
 
@@ -916,8 +920,9 @@ void launch_residual_f64(const double* M64, const double* Z64, int64_t ld, const
   k_gemm_simt<double, 64, 64, 8, 4, 4, EPI_RESIDUAL><<<g, 256, 0, s>>>(M64, a, lam, acc);
 }
 
-void launch_control(DevState* st, ControlArgs a, cudaStream_t s) {
-  k_control<<<1, 1, 0, s>>>(st, a);
+void launch_control(DevState* st, ControlArgs a, cudaStream_t s, bool pdl) {
+  if (pdl) launch_pdl(k_control, dim3(1), dim3(1), 0, s, st, a);
+  else k_control<<<1, 1, 0, s>>>(st, a);
 }
 
 void launch_map_first(const MapArgs<float>& a, int npad, int kpad, double* d, double* part,

@@ -33,7 +33,7 @@ __global__ void k_theta(const void* M, int64_t ldm, int m_dtype, const double* t
 
 // icol[c] = cols[c] (or c), range check, occurrence count per index.
 __global__ void k_cols(const int32_t* cols, int n, int k, int kpad, int32_t* icol, int* count,
-                       DevState* st) {
+                       DevState* st, int col_range, void* zunit, int kk, int zf64) {
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= kpad) return;
   if (c >= k) {
@@ -48,6 +48,14 @@ __global__ void k_cols(const int32_t* cols, int n, int k, int kpad, int32_t* ico
   }
   icol[c] = i;
   atomicAdd(&count[i], 1);
+  if (col_range) {  // the support of Z0 = E: rows [z_lo, z_hi] (sparse solves)
+    atomicMin(&st->z_lo, i);
+    atomicMax(&st->z_hi, i);
+  }
+  if (zunit) {  // Z0 = E in the sparse path's row-major n x kk iterate
+    if (zf64) static_cast<double*>(zunit)[(int64_t)i * kk + c] = 1.0;
+    else static_cast<float*>(zunit)[(int64_t)i * kk + c] = 1.f;
+  }
 }
 
 // Duplicate requested columns (after k_cols has counted occurrences).
@@ -353,8 +361,13 @@ void launch_theta(const void* M, int64_t ldm, int m_dtype, const double* theta_i
 void launch_validate(const int32_t* cols, int n, int k, int kpad, const double* theta,
                      int32_t* icol, int* count, DevState* st, cudaStream_t s) {
   (void)theta;
-  k_cols<<<blocks(kpad, 256), 256, 0, s>>>(cols, n, k, kpad, icol, count, st);
+  k_cols<<<blocks(kpad, 256), 256, 0, s>>>(cols, n, k, kpad, icol, count, st, 0, nullptr, 0, 0);
   k_cols_dup<<<blocks(k, 256), 256, 0, s>>>(icol, count, k, st);
+}
+
+void launch_validate_csr(const int32_t* cols, int n, int k, int kk, int32_t* icol, int* count,
+                         void* Z, int zf64, DevState* st, cudaStream_t s) {
+  k_cols<<<blocks(kk, 256), 256, 0, s>>>(cols, n, k, kk, icol, count, st, 1, Z, kk, zf64);
 }
 
 void launch_form_delta(const void* M, int64_t ldm, int m_dtype, const double* theta, int n,

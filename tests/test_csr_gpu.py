@@ -123,6 +123,68 @@ def test_csr_statuses(ipt):
     assert info["status"] == "OK"
 
 
+def _split_repeated(rowptr, colind, vals, dtype, seed):
+    """The same matrix with repeated stored entries: on every 5th row the diagonal
+    is stored as two or three pieces (first, middle and last of the row's
+    entries), on every 7th row one off-diagonal entry as two; the pieces are
+    values of `dtype`, and their sum is the matrix both sides solve."""
+    g = w.rng(seed)
+    rp, ci, vv = [0], [], []
+    for i in range(len(rowptr) - 1):
+        c = list(colind[rowptr[i]:rowptr[i + 1]])
+        v = [float(x) for x in np.asarray(vals[rowptr[i]:rowptr[i + 1]]).astype(dtype)]
+        if i % 5 == 0 and i in c:
+            d = c.index(i)
+            dv = v[d]
+            p1 = float(np.asarray(dv * g.uniform(0.2, 0.8)).astype(dtype))
+            pieces = [p1, float(np.asarray(dv - p1).astype(dtype))]
+            if i % 10 == 0:
+                p2 = float(np.asarray(pieces[1] * 0.5).astype(dtype))
+                pieces = [p1, p2, float(np.asarray(pieces[1] - p2).astype(dtype))]
+            del c[d], v[d]
+            c = [i] + c + [i] * (len(pieces) - 1)
+            v = [pieces[0]] + v + pieces[1:]
+        if i % 7 == 0 and len(c) > 2:
+            k = 1 if c[1] != i else 2
+            half = float(np.asarray(v[k] * 0.5).astype(dtype))
+            c.append(c[k])
+            v.append(float(np.asarray(v[k] - half).astype(dtype)))
+            v[k] = half
+        ci += c
+        vv += v
+        rp.append(len(ci))
+    return (np.asarray(rp, np.int32), np.asarray(ci, np.int32), np.asarray(vv, np.float64))
+
+
+@pytest.mark.parametrize("vdt,npdt,lam_tol", [(torch.float32, np.float32, 1e-5),
+                                              (torch.float64, np.float64, 1e-10)])
+@pytest.mark.parametrize("theta_given", [False, True])
+def test_csr_repeated_entries_add_up(ipt, vdt, npdt, lam_tol, theta_given):
+    """Repeated stored entries add up, as in the oracle's scipy CSR matrix: the
+    diagonal (theta = diag(M) and delta_j = M_jj - theta_j) and the product.
+    Rows with a repeated FP32 diagonal take the row pass's out-of-line FP64 path."""
+    n = 600
+    rowptr, colind, vals, th = w.csr_banded(n, 3, 30, 1e-2, seed=5, theta_step=0.1)
+    rp_, ci_, vv_ = _split_repeated(rowptr, colind, vals, npdt, seed=12)
+    assert len(ci_) > len(colind)
+    cols = w.lowest_columns(th, 8)
+    theta = th if theta_given else None
+    tol = 1e-6 if vdt == torch.float32 else 1e-12
+    ref = oracle.ipt_solve_csr(rp_, ci_, vv_, n, theta=theta, cols=cols, tol=1e-13,
+                               max_iter=200)
+    assert ref["status"] == oracle.OK
+    rp, ci, vv = csr_on_gpu(rp_, ci_, vv_, vdt)
+    for window in (True, False):
+        lam, Z, info = ipt.Solver().solve_csr(
+            rp, ci, vv, n, theta=None if theta is None else cuda(theta, torch.float64),
+            cols=cuda(cols, torch.int32), tol=tol, max_iter=100,
+            precision="f32" if vdt == torch.float32 else "f64", window=window,
+            z_dtype=torch.float64)
+        assert info["status"] == "OK", info
+        lam = lam.cpu().numpy()
+        assert np.max(np.abs(lam - ref["lam"]) / np.abs(ref["lam"])) <= lam_tol
+
+
 def test_csr_full_size_sampled_columns_match_oracle(ipt):
     """The sparse configuration at full size: n = 2^20, 8 offsets per row in
     {1..2048} mirrored, values N(0,1)*1e-3, theta_i = i*1e-2 + U(0,1e-3); the 64
