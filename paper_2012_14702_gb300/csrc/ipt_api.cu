@@ -750,7 +750,7 @@ ipt_status dense_chunked_loop(ipt_handle* h, const Plan& p, const ControlArgs& c
                                           nullptr, ev)
                                : evaluate_dyn(h, p, tm, ev);
       if (v != IPT_OK) return v;
-      launch_control(st, ca, s);
+      launch_control(st, ca, s, true);
       h->launches += 1;
     }
     // with timing, the stage history tells each evaluation's pass count
@@ -789,7 +789,7 @@ ipt_status dense_chunked_loop(ipt_handle* h, const Plan& p, const ControlArgs& c
       const ipt_status v = evaluate(h, p, h->hst->cur, h->hst->base, stg, h->hst->passes,
                                     h->hst->rebase, tm, -1, nullptr, h->ev);
       if (v != IPT_OK) return v;
-      launch_control(st, ca, s);
+      launch_control(st, ca, s, true);
       h->launches += 1;
       if (!sync_state()) return IPT_CUDA_ERROR;
       collect_timing(h, 1, tm, h->ev, stg);

@@ -109,6 +109,8 @@ __global__ void k_prepass_tc(const float* __restrict__ Drow, const float* __rest
                              double* __restrict__ d, uint16_t* __restrict__ Wh,
                              uint16_t* __restrict__ Wl, float* __restrict__ sinv,
                              const DevState* st, DynZ dz) {
+  griddep_wait();  // launched with programmatic dependent launch
+  griddep_launch();
   if (st->done || (dz.dyn && st->pause)) return;
   if (dz.dyn) {
     Z = dz.z[st->cur];
@@ -181,6 +183,8 @@ __global__ void __launch_bounds__(1024)
                      const int32_t* __restrict__ icol, double* __restrict__ d,
                      uint16_t* __restrict__ Wh, uint16_t* __restrict__ Wl,
                      float* __restrict__ sinv, const DevState* st, DynZ dz) {
+  griddep_wait();  // launched with programmatic dependent launch
+  griddep_launch();
   if (st->done || (dz.dyn && st->pause)) return;
   if (dz.dyn) {
     Z = dz.z[st->cur];
@@ -872,20 +876,20 @@ void launch_prepass_tc(const float* Drow, const float* Z, const float* Zbase, in
     int threads = (int)((n4 + VPT - 1) / VPT);
     threads = ((threads + 31) / 32) * 32;
     if (bf16)
-      k_prepass_tc_reg<true, VPT><<<kpad, threads, 0, s>>>(Drow, Z, Zbase, ld, icol, d, Wh, Wl,
-                                                            sinv, st, dz);
+      launch_pdl(k_prepass_tc_reg<true, VPT>, dim3(kpad), dim3(threads), 0, s, Drow, Z, Zbase,
+                 ld, icol, d, Wh, Wl, sinv, (const DevState*)st, dz);
     else
-      k_prepass_tc_reg<false, VPT><<<kpad, threads, 0, s>>>(Drow, Z, Zbase, ld, icol, d, Wh, Wl,
-                                                             sinv, st, dz);
+      launch_pdl(k_prepass_tc_reg<false, VPT>, dim3(kpad), dim3(threads), 0, s, Drow, Z, Zbase,
+                 ld, icol, d, Wh, Wl, sinv, (const DevState*)st, dz);
     return;
   }
   unsigned g = (unsigned)((kpad + 7) / 8);
   if (bf16)
-    k_prepass_tc<true><<<g, 256, 0, s>>>(Drow, Z, Zbase, ld, icol, kpad, d, Wh, Wl, sinv, st,
-                                         dz);
+    launch_pdl(k_prepass_tc<true>, dim3(g), dim3(256), 0, s, Drow, Z, Zbase, ld, icol, kpad, d,
+               Wh, Wl, sinv, (const DevState*)st, dz);
   else
-    k_prepass_tc<false><<<g, 256, 0, s>>>(Drow, Z, Zbase, ld, icol, kpad, d, Wh, Wl, sinv, st,
-                                          dz);
+    launch_pdl(k_prepass_tc<false>, dim3(g), dim3(256), 0, s, Drow, Z, Zbase, ld, icol, kpad, d,
+               Wh, Wl, sinv, (const DevState*)st, dz);
 }
 
 void launch_gemm_simt_f64(const double* Drow, const MapArgs<double>& a, int npad, int kpad,

@@ -52,6 +52,8 @@ __global__ void __launch_bounds__(256)
                    const int32_t* __restrict__ icol, int n, int k, int kpad, int64_t ld,
                    const float* __restrict__ psmp, int stride, int off, double* __restrict__ part,
                    int* __restrict__ arrived, DevState* st, DynZ dz) {
+  griddep_wait();  // launched with programmatic dependent launch
+  griddep_launch();
   if (st->done) return;
   if (dz.dyn) {
     if (st->pause || !st->measure) return;
@@ -206,8 +208,8 @@ void launch_sample_exact(const float* Drow, const float* Z, const int32_t* icol,
   const int blocks = kpad / SC < kMaxBlocks ? kpad / SC : kMaxBlocks;
   double* part = static_cast<double*>(scratch);
   int* arrived = reinterpret_cast<int*>(part + (int64_t)kMaxBlocks * KS * SR * SC);
-  k_sample_exact<<<(unsigned)(blocks * KS), 256, 0, s>>>(Drow, Z, icol, n, k, kpad, ld, psmp,
-                                                         stride, off, part, arrived, st, dz);
+  launch_pdl(k_sample_exact, dim3((unsigned)(blocks * KS)), dim3(256), 0, s, Drow, Z, icol, n, k,
+             kpad, ld, psmp, stride, off, part, arrived, st, dz);
 }
 
 }  // namespace ipt

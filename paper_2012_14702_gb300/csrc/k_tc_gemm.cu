@@ -285,6 +285,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   constexpr int STAGES = Shape<MODE>::STAGES;
   constexpr int B_BYTES = Shape<MODE>::B_BYTES;
   constexpr int STAGE_BYTES = Shape<MODE>::STAGE_BYTES;
+  griddep_wait();  // launched with programmatic dependent launch (paired mode)
+  griddep_launch();
   // uniform over the grid, so over each cluster; a paused solve runs its next
   // evaluation with a kernel of another kind first
   if (a.st->done || (a.dyn && a.st->pause)) return;
@@ -778,11 +780,15 @@ cudaError_t launch_cluster(const CUtensorMap& mDh, const CUtensorMap& mDl, const
                            int num_kb, int passes, uint32_t idesc, int num_sms, cudaStream_t s) {
   static int max_clusters = 0;
   cudaLaunchConfig_t cfg = {};
-  cudaLaunchAttribute attr[1];
+  cudaLaunchAttribute attr[2];
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = 2;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
+  // programmatic dependent launch: scheduled while the pre-pass finishes; the
+  // kernel waits for it (griddep_wait) before it reads anything
+  attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[1].val.programmaticStreamSerializationAllowed = 1;
   cfg.blockDim = dim3(NUM_THREADS);
   cfg.dynamicSmemBytes = smem_bytes<MODE>();
   cfg.stream = s;
@@ -799,6 +805,7 @@ cudaError_t launch_cluster(const CUtensorMap& mDh, const CUtensorMap& mDl, const
   const int pairs = (num_m / 2) * num_n;
   const int clusters = pairs < max_clusters ? pairs : max_clusters;
   cfg.gridDim = dim3(2 * clusters);
+  cfg.numAttrs = 2;
   return cudaLaunchKernelEx(&cfg, k_gemm_tc<MODE>, mDh, mDl, mWh, mWl, mWh1, mWl1, a, num_m,
                             num_n, num_kb,
                             passes, idesc);
