@@ -91,7 +91,6 @@ struct DevState {
   int flags;   // validation flags
   int timeout; // bounded device wait gave up (code of the waiting role)
   int stage_iters[2];
-  int rows_done;       // blocks of the sparse row pass that have finished
   // CSR active window (rows outside it are exactly zero in Z and in F):
   int band;            // largest |j - m| over the stored entries of M
   int z_lo, z_hi;      // every nonzero row of the current iterate lies in [z_lo, z_hi]

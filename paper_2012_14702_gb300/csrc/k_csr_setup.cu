@@ -64,8 +64,7 @@ __device__ __noinline__ RowValues csr_row_values_slow(const int32_t* __restrict_
 // or M_jj), its FP32 split and delta_j = M_jj - theta_j; non-finite theta is
 // flagged.  Per block: the partial of ||M Z0 - Z0 Lambda0||^2 (the squared
 // off-diagonal entries in requested columns, count[col] > 0) and the band
-// max |j - m| of the stored entries; the last block to finish sums the
-// partials and sets the first window.  The requested columns' range
+// max |j - m| of the stored entries.  The requested columns' range
 // [z_lo, z_hi] (set by the column validation before this pass) filters the
 // count[] gathers: an entry outside it is in no requested column.
 __global__ void __launch_bounds__(256, 4)
@@ -73,7 +72,7 @@ __global__ void __launch_bounds__(256, 4)
                const void* __restrict__ vals, int v_dtype, const double* __restrict__ theta_in,
                int n, int64_t nnz, const int* __restrict__ count, double* __restrict__ theta,
                float* __restrict__ th_hi, float* __restrict__ th_lo, double* __restrict__ delta,
-               double* __restrict__ part, int window, DevState* st) {
+               double* __restrict__ part, DevState* st) {
   constexpr int kW = 512;  // entries per warp chunk
   __shared__ int scol[8][kW];
   __shared__ float sval[8][kW];  // FP32 input only
@@ -196,7 +195,6 @@ __global__ void __launch_bounds__(256, 4)
     red[wq] = w;
     rb[wq] = band;
   }
-  __shared__ int last;
   __syncthreads();
   if (threadIdx.x == 0) {
     double tot = 0.0;
@@ -207,34 +205,35 @@ __global__ void __launch_bounds__(256, 4)
     }
     part[blockIdx.x] = tot;
     if (b > *(volatile int*)&st->band) atomicMax(&st->band, b);
-    __threadfence();  // this block's partial and band before its arrival
-    last = atomicAdd(&st->rows_done, 1) == (int)gridDim.x - 1;
   }
-  __syncthreads();
-  if (!last) return;
-  // The last block to finish: ||R0||^2 from the block partials (a fixed
-  // order: per-thread strided sums, then a tree), and the rows the first
-  // product evaluates: all of them, or (window) the requested rows widened by
-  // the band (rows further away have no stored entry in a nonzero row of E).
-  __threadfence();
-  __shared__ double tree[256];
+}
+
+// One block: ||R0||^2 from the row pass's partials (a fixed order), and the
+// rows the first product evaluates: all of them, or (window) the requested
+// rows widened by the band (rows further away have no stored entry in a
+// nonzero row of E).  Launched with programmatic dependent launch after the
+// row pass (a last-block reduction inside the row pass, measured, cost every
+// block a memory fence: 63 -> 77 us).
+__global__ void __launch_bounds__(1024)
+    k_csr_sum_r0(const double* __restrict__ part, int count, int n, int window, DevState* st) {
+  griddep_wait();
+  griddep_launch();
+  __shared__ double red[1024];
   double t = 0.0;
-  for (int i = threadIdx.x; i < (int)gridDim.x; i += 256) t += __ldcg(part + i);
-  tree[threadIdx.x] = t;
+  for (int i = threadIdx.x; i < count; i += blockDim.x) t += part[i];
+  red[threadIdx.x] = t;
   __syncthreads();
-  for (int h = 128; h > 0; h >>= 1) {
-    if ((int)threadIdx.x < h) tree[threadIdx.x] += tree[threadIdx.x + h];
+  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+    if ((int)threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    volatile DevState* vs = st;
-    const int zl = vs->z_lo, zh = vs->z_hi, bd = vs->band;
-    st->r0acc = tree[0];
+    st->r0acc = red[0];
     st->nz_lo = n;
     st->nz_hi = -1;
-    if (window && zh >= zl) {
-      st->win_lo = max(0, zl - bd);
-      st->win_hi = (int)min((int64_t)n, (int64_t)zh + 1 + bd);
+    if (window && st->z_hi >= st->z_lo) {
+      st->win_lo = max(0, st->z_lo - st->band);
+      st->win_hi = (int)min((int64_t)n, (int64_t)st->z_hi + 1 + st->band);
     } else {
       st->win_lo = 0;
       st->win_hi = n;
@@ -250,7 +249,8 @@ void launch_csr_rows(const int32_t* rowptr, const int32_t* colind, const void* v
                      DevState* st, cudaStream_t s) {
   const unsigned g = nblocks(n, 256);  // one block per 256 rows (the partials' capacity)
   k_csr_rows<<<g, 256, 0, s>>>(rowptr, colind, vals, v_dtype, theta_in, n, nnz, count, theta, th_hi,
-                               th_lo, delta, part, window, st);
+                               th_lo, delta, part, st);
+  launch_pdl(k_csr_sum_r0, dim3(1), dim3(1024), 0, s, (const double*)part, (int)g, n, window, st);
 }
 
 namespace {
