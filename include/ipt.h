@@ -240,13 +240,17 @@ ipt_status ipt_solve_dense(ipt_handle* h, int64_t n, const void* M, int64_t ldm,
 
 /*
  * ipt_solve_dense with HOST buffers: M, theta, cols, lambda and Z are host
- * pointers (pinned memory gives the fastest copies).  The call copies the
- * inputs to the handle's workspace, solves, and copies Lambda and Z back.  When
- * Z's dtype is the iterate's (FP32, or FP64 with IPT_PREC_F64) and no
- * acceleration is asked for, the iterate predicted to be returned is copied to
- * Z on a second stream while the evaluation that tests it runs; Z may then
- * hold an earlier iterate if the call ends with a status other than IPT_OK,
- * IPT_MAXITER or IPT_DIVERGED.  Every copy has finished when the call returns.
+ * pointers.  The call copies the inputs to the handle's workspace, solves, and
+ * copies Lambda and Z back.  A pinned (page-locked, device-mapped) M is read in
+ * place by the setup, which forms Delta from it over the host link (no staging
+ * copy).  When Z's dtype is the iterate's (FP32, or FP64 with IPT_PREC_F64) and
+ * no acceleration is asked for, the iterate predicted to be returned reaches Z
+ * early: copied on a second stream while the evaluation that tests it runs, or,
+ * for a pinned Z and a tensor-core product, stored into Z by the epilogue of the
+ * product that forms it (predicted when the test two evaluations on is expected
+ * to pass).  Z may then hold another iterate if the call ends with a status
+ * other than IPT_OK, IPT_MAXITER or IPT_DIVERGED.  Every copy and store has
+ * finished when the call returns; M and Z must not be changed meanwhile.
  */
 ipt_status ipt_solve_dense_host(ipt_handle* h, int64_t n, const void* M, int64_t ldm, int m_dtype,
                                 const double* theta, int64_t k, const int32_t* cols, double tol,

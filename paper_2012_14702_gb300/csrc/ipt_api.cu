@@ -51,6 +51,8 @@ struct ipt_handle {
   int dev = 0;
   Buf drow, dt, dh, dl, z[5], pbuf, wh, wl, rinv, sinv;  // z[4]: accelerated solves' base
   Buf smp;                          // sampled product entries (error estimate)
+  float* host_f = nullptr;          // host entry point: the next tensor-core epilogue also
+  int64_t host_ld = 0;              // stores F here (device address of the host output)
   Buf wh2, wl2, dpart;              // staged Picard: the second W set and the partial sums
                                     // of d, both written by the product's epilogue
   Buf acx_d, acx_acc, acx_sigma;    // ACX: d of the inner evaluations, step-length sums, steps
@@ -243,6 +245,7 @@ ipt_status status_from_flags(int flags) {
 struct HostOut {
   void* Z = nullptr;  // host, column-major n x k, ldz, the iterate's dtype
   int64_t ldz = 0;
+  void* Zdev = nullptr;  // Z's device address (mapped pinned memory), else null
 };
 
 // Initial controller state: the first evaluation's stage, product passes
@@ -437,6 +440,8 @@ ipt_status evaluate(ipt_handle* h, const Plan& p, int cur, int base, int stage, 
       a.pbase_by_icol = base >= 0 ? 0 : 1;
       a.Pout = rebase ? (float*)h->pbuf.p : nullptr;
       set_sampling(h, p, a, measure != 0);
+      a.host_f = h->host_f;
+      a.host_ld = h->host_ld;
       if (t) CK(cudaEventRecord(ev[2], s));
       CK(launch_gemm_tc((const uint16_t*)h->dh.p, (const uint16_t*)h->dl.p,
                         (const uint16_t*)h->wh.p, (const uint16_t*)h->wl.p, a, p.npad, p.kpad,
@@ -515,6 +520,8 @@ ipt_status evaluate_dyn(ipt_handle* h, const Plan& p, Timing* tm, cudaEvent_t* e
     a.drow = (const float*)h->drow.p;
   }
   set_sampling(h, p, a, true);  // stored only when the state asks for a sample
+  a.host_f = h->host_f;
+  a.host_ld = h->host_ld;
   // the pass count given here only sizes nothing: the kernel reads it from st
   CK(launch_gemm_tc((const uint16_t*)h->dh.p, (const uint16_t*)h->dl.p,
                     (const uint16_t*)h->wh.p, (const uint16_t*)h->wl.p, a, p.npad, p.kpad, 1,
@@ -1089,10 +1096,20 @@ ipt_status solve_dense(ipt_handle* h, int64_t n, const void* M, int64_t ldm, int
   // when that evaluation is predicted to pass the test (test value times the
   // last contraction below tol, and a product accurate enough to stop on);
   // otherwise the returned iterate is copied after the loop
-  bool likely_final = false;
-  int copied_it = -1;
+  // With the host output mapped into the device's address space, an evaluation
+  // whose F is predicted to be the returned iterate (the test two evaluations on
+  // passes: test value times the last contraction squared below tol) stores F
+  // there from the product's epilogue, during the product.
+  bool likely_final = false, write_next = false;
+  int copied_it = -1, host_written_it = -1;
+  struct HostFClear {  // never left set for a later launch, whatever the exit
+    ipt_handle* h;
+    ~HostFClear() { h->host_f = nullptr; }
+  } host_f_clear{h};
+  cudaEvent_t copy_in_flight = nullptr;
   double prev_test = -1.0;
   for (int it = start; it < max_iter; ++it) {
+    if (hz && likely_final && host_written_it == it - 1) likely_final = false;  // on the host
     if (hz && likely_final) {
       // the output buffer of this evaluation must not still be copied out
       const int nxt = free_buffer(cur, base);
@@ -1102,7 +1119,19 @@ ipt_status solve_dense(ipt_handle* h, int64_t n, const void* M, int64_t ldm, int
       CK(cudaMemcpy2DAsync(hz->Z, (size_t)hz->ldz * zes, h->z[cur].p, (size_t)p.npad * zes,
                            (size_t)p.n * zes, (size_t)p.k, cudaMemcpyDeviceToHost, h->cs));
       CK(cudaEventRecord(h->zcopied[cur], h->cs));
+      copy_in_flight = h->zcopied[cur];
       copied_it = it;
+    }
+    // this evaluation's tensor-core epilogue writes F to the host output: after
+    // any copy into the same buffer has finished
+    const bool host_write = hz && hz->Zdev && write_next && p.tc && passes > 0 &&
+                            stage != IPT_PREC_F32 && stage != IPT_PREC_F32C &&
+                            stage != IPT_PREC_F64;
+    if (host_write) {
+      if (copy_in_flight) CK(cudaStreamWaitEvent(s, copy_in_flight, 0));
+      h->host_f = (float*)hz->Zdev;
+      h->host_ld = hz->ldz;
+      host_written_it = it;
     }
     const int fbuf = free_buffer(cur, base);  // where this evaluation writes F
     // a staged Picard product runs as the device-chosen evaluation (the state
@@ -1113,6 +1142,7 @@ ipt_status solve_dense(ipt_handle* h, int64_t n, const void* M, int64_t ldm, int
     v = dyn_eval ? evaluate_dyn(h, p, &tm, h->ev)
                  : evaluate(h, p, cur, base, stage, passes, rebase, &tm, -1, nullptr, nullptr,
                             it > 0 && p.tc ? h->hst->measure : 0);
+    h->host_f = nullptr;
     if (v != IPT_OK) break;
     launch_control(dst(h), ca, s);
     h->launches += 1;
@@ -1152,6 +1182,7 @@ ipt_status solve_dense(ipt_handle* h, int64_t n, const void* M, int64_t ldm, int
       const double test = opt.stop == IPT_STOP_INCREMENT ? h->hst->inc : h->hst->rho;
       const double q = prev_test > 0.0 ? std::min(test / prev_test, 1.0) : 1.0;
       likely_final = (!p.staged || h->hst->accurate) && test * q <= tol;
+      write_next = !likely_final && test * q * q <= tol;
       prev_test = test;
     }
   }
@@ -1179,8 +1210,10 @@ ipt_status solve_dense(ipt_handle* h, int64_t n, const void* M, int64_t ldm, int
                 p.k, lambda, s);
   h->launches += 1;
   if (hz) {
-    if (copied_it != (int)hs.iter - 1) {
-      // the returned iterate was not copied out beside its evaluation
+    if (copied_it != (int)hs.iter - 1 &&
+        !(host_written_it >= 0 && host_written_it == (int)hs.iter - 2)) {
+      // the returned iterate was not copied out beside its evaluation, nor
+      // written out by the epilogue of the evaluation that formed it
       CK(cudaStreamSynchronize(h->cs));
       CK(cudaMemcpy2DAsync(hz->Z, (size_t)hz->ldz * zes, h->z[ans].p, (size_t)p.npad * zes,
                            (size_t)p.n * zes, (size_t)p.k, cudaMemcpyDeviceToHost, s));
@@ -1322,10 +1355,25 @@ ipt_status ipt_solve_dense_host(ipt_handle* h, int64_t n, const void* M, int64_t
   DeviceGuard g(h->dev);
   cudaStream_t s = h->s;
   const size_t em = m_dtype == IPT_DTYPE_F64 ? 8 : 4, ez = z_dtype == IPT_DTYPE_F64 ? 8 : 4;
-  CK(ensure(h->hM, (size_t)n * n * em));
+  // Pinned (mapped) host buffers are used in place: the setup reads M over the
+  // host link while it forms Delta (no staging copy), and the product epilogue
+  // of the evaluation predicted to form the returned iterate stores it into Z.
+  // Pageable buffers go through device copies.
+  auto mapped = [](const void* ptr) -> void* {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+  };
+  const void* Mdev = mapped(M);
   CK(ensure(h->hLam, (size_t)k * 8));
   CK(ensure(h->hZ, (size_t)n * k * ez));
-  CK(cudaMemcpy2DAsync(h->hM.p, n * em, M, ldm * em, n * em, n, cudaMemcpyHostToDevice, s));
+  if (!Mdev) {
+    CK(ensure(h->hM, (size_t)n * n * em));
+    CK(cudaMemcpy2DAsync(h->hM.p, n * em, M, ldm * em, n * em, n, cudaMemcpyHostToDevice, s));
+  }
   const bool iter_f64 = o.precision == IPT_PREC_F64;
   const bool direct = o.accel == IPT_ACCEL_NONE && (z_dtype == IPT_DTYPE_F64) == iter_f64;
   HostOut ho;
@@ -1353,9 +1401,11 @@ ipt_status ipt_solve_dense_host(ipt_handle* h, int64_t n, const void* M, int64_t
   if (direct) {
     ho.Z = Z;
     ho.ldz = ldz;
+    ho.Zdev = mapped(Z);
   }
-  v = solve_dense(h, n, h->hM.p, n, m_dtype, dth, k, dcols, tol, max_iter, &o,
-                  (double*)h->hLam.p, h->hZ.p, n, z_dtype, out, direct ? &ho : nullptr);
+  v = solve_dense(h, n, Mdev ? Mdev : h->hM.p, Mdev ? ldm : n, m_dtype, dth, k, dcols, tol,
+                  max_iter, &o, (double*)h->hLam.p, h->hZ.p, n, z_dtype, out,
+                  direct ? &ho : nullptr);
   if (v == IPT_OK || v == IPT_MAXITER || v == IPT_DIVERGED || v == IPT_INACCURATE) {
     CK(cudaMemcpyAsync(lambda, h->hLam.p, (size_t)k * 8, cudaMemcpyDeviceToHost, s));
     if (!direct)

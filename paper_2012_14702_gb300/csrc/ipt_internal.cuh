@@ -149,6 +149,12 @@ struct MapArgs {
   double* dpart;
   int dgroups;
   const float* drow;
+  // Host-buffer entry point: the tensor-core epilogue also stores F into the
+  // caller's host output (column-major n x k, leading dimension host_ld; the
+  // device address of mapped pinned memory) when this evaluation's F is
+  // predicted to be the returned iterate, so its copy overlaps the product.
+  T* host_f;
+  int64_t host_ld;
 };
 
 // Device-chosen pre-pass operands (see MapArgs::dyn): with dyn set, Z is

@@ -643,6 +643,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
               if (gap == 0.f && j != ic) flag_degenerate(a.st);
               map_entry<float>(z[i], p, ci.d, gap, j == ic, f, r);
               __stcs(Fout + o, f);
+              if (a.host_f && cbase + c0 + i < a.k)
+                __stcs(a.host_f + (int64_t)(cbase + c0 + i) * a.host_ld + j, f);
               const float df = f - z[i];
               s_inc = fmaf(df, df, s_inc);
               s_z = fmaf(z[i], z[i], s_z);

@@ -250,17 +250,25 @@ def test_divergence_and_cycle_statuses(ipt):
 
 
 @pytest.mark.parametrize("precision,z_dtype,max_iter,status", [
-    ("staged", torch.float32, 50, "OK"),      # iterate copied out while it is tested
+    ("staged", torch.float32, 50, "OK"),      # the returned iterate written by the epilogue
     ("staged", torch.float64, 50, "OK"),      # through a device conversion
     ("f32", torch.float32, 2, "MAXITER"),     # the last tested iterate
     ("fp16x3", torch.float32, 1, "MAXITER"),  # Z = E
     ("f64", torch.float64, 50, "OK")])
-def test_host_entry_point_matches_device_entry_point(ipt, precision, z_dtype, max_iter, status):
+@pytest.mark.parametrize("pinned", [True, False])
+def test_host_entry_point_matches_device_entry_point(ipt, precision, z_dtype, max_iter, status,
+                                                     pinned):
+    """The host-buffer entry point returns the device entry point's result bit for
+    bit: with pinned buffers (M read in place by the setup, the iterate predicted
+    to be returned stored into Z by the product's epilogue) and with pageable ones
+    (staging copies)."""
     n = 600
     M, th = w.dense_symmetric(n, 1e-3, seed=4, theta_step=0.125)
-    Mt = torch.as_tensor(M, dtype=torch.float32).pin_memory()
+    Mt = torch.as_tensor(M, dtype=torch.float32)
+    Mt = Mt.pin_memory() if pinned else Mt.clone()
     s = ipt.Solver()
-    zt = torch.empty((n, n), dtype=z_dtype).pin_memory()
+    zt = torch.empty((n, n), dtype=z_dtype)
+    zt = zt.pin_memory() if pinned else zt
     lam_h, Z_h, info_h = s.solve_dense_host(Mt, tol=1e-6, max_iter=max_iter,
                                             precision=precision, z_dtype=z_dtype, zt_out=zt)
     lam_d, Z_d, info_d = s.solve_dense(Mt.cuda(), tol=1e-6, max_iter=max_iter,
