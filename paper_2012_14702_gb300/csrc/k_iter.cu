@@ -172,20 +172,26 @@ __global__ void k_prepass_tc(const float* __restrict__ Drow, const float* __rest
   }
 }
 
-// The same pre-pass with the column held in registers (V = Z - Z_base): one CTA per column,
-// each thread owns up to VPT float4 slots of it, so Z is read from memory
-// once (the two-pass warp kernel above re-reads the column, which at n = 8192
-// no longer fits in L1/L2 between its passes).  Used when npad <= 4*VPT*1024.
+// The same pre-pass with the column held in registers (V = Z - Z_base): a CTA
+// per column at a time, on a persistent grid of a few CTAs per SM that walks
+// the columns (a launch that only hands over the epilogue's operand, or
+// returns at entry, then costs a few microseconds instead of a grid of kpad
+// CTAs); each thread owns up to VPT float4 slots of the column, so Z is read
+// from memory once (the two-pass warp kernel above re-reads the column, which
+// at n = 8192 no longer fits in L1/L2 between its passes).  Used when
+// npad <= 4*VPT*1024.
 template <bool BF16, int VPT>
 __global__ void __launch_bounds__(1024)
     k_prepass_tc_reg(const float* __restrict__ Drow, const float* __restrict__ Z,
                      const float* __restrict__ Zbase, int64_t ld,
-                     const int32_t* __restrict__ icol, double* __restrict__ d,
+                     const int32_t* __restrict__ icol, int kpad, double* __restrict__ d,
                      uint16_t* __restrict__ Wh, uint16_t* __restrict__ Wl,
                      float* __restrict__ sinv, const DevState* st, DynZ dz) {
   griddep_wait();  // launched with programmatic dependent launch
   griddep_launch();
   if (st->done || (dz.dyn && st->pause)) return;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int nw = blockDim.x >> 5;
   if (dz.dyn) {
     Z = dz.z[st->cur];
     Zbase = st->base >= 0 ? dz.z[st->base] : nullptr;
@@ -194,78 +200,80 @@ __global__ void __launch_bounds__(1024)
       Wl = dz.wl[st->wsel & 1];
     }
     if (st->passes != 3) Wl = nullptr;
-    if (dz.dpart && st->split_ready) {  // uniform over the grid
-      if (threadIdx.x < 32) prepass_handover(st, dz, blockIdx.x, threadIdx.x, d, sinv);
+    if (dz.dpart && st->split_ready) {  // uniform over the grid: a warp per column
+      for (int c = blockIdx.x * nw + wid; c < kpad; c += gridDim.x * nw)
+        prepass_handover(st, dz, c, lane, d, sinv);
       return;
     }
   }
-  const int c = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  const int nw = blockDim.x >> 5;
-  const int i = icol[c];
-  if (i < 0) {
-    if (tid == 0) {
-      d[c] = 0.0;
-      sinv[c] = 1.f;
-    }
-    return;
-  }
   const int n4 = (int)(ld / 4);
-  const float4* a4 = reinterpret_cast<const float4*>(Drow + (int64_t)i * ld);
-  const float4* z4 = reinterpret_cast<const float4*>(Z + (int64_t)c * ld);
-  const float4* b4 = Zbase ? reinterpret_cast<const float4*>(Zbase + (int64_t)c * ld) : nullptr;
-  float4 y[VPT];
-  float s = 0.f, comp = 0.f, mx = 0.f;
-#pragma unroll
-  for (int q = 0; q < VPT; ++q) {
-    const int m = tid + q * blockDim.x;
-    y[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (m < n4) {
-      const float4 x = __ldg(a4 + m);
-      y[q] = __ldg(z4 + m);
-      const float y0 = x.x * y[q].x + x.y * y[q].y + x.z * y[q].z + x.w * y[q].w;
-      const float yy = y0 - comp;
-      const float t = s + yy;
-      comp = (t - s) - yy;
-      s = t;
-      subtract_base(y[q], b4, m, i);
-      mx = fmaxf(mx, fmaxf(fmaxf(fabsf(y[q].x), fabsf(y[q].y)),
-                           fmaxf(fabsf(y[q].z), fabsf(y[q].w))));
-    }
-  }
-  // d_c: the lanes' compensated sums (s - comp) reduced as FP32 pairs, the
-  // warps' pairs by warp 0
   __shared__ F2 rs[32];
   __shared__ float rm[32];
-  const F2 ws = warp_sum(F2{s, -comp});
-  const float wm = warp_max(mx);
-  if (lane == 0) {
-    rs[wid] = ws;
-    rm[wid] = wm;
-  }
-  __syncthreads();
-  float cmax = 0.f;
-  for (int w = 0; w < nw; ++w) cmax = fmaxf(cmax, rm[w]);
-  F2 tot{0.f, 0.f};
-  if (wid == 0) tot = warp_sum(lane < nw ? rs[lane] : F2{0.f, 0.f});
-  const float sc = pow2_scale(cmax);
-  uint2* h2 = reinterpret_cast<uint2*>(Wh + (int64_t)c * ld);
-  uint2* l2 = reinterpret_cast<uint2*>(Wl + (int64_t)c * ld);
-#pragma unroll
-  for (int q = 0; q < VPT; ++q) {
-    const int m = tid + q * blockDim.x;
-    if (m < n4) {
-      uint16_t h[4], l[4];
-      split16(y[q].x * sc, BF16, h[0], l[0]);
-      split16(y[q].y * sc, BF16, h[1], l[1]);
-      split16(y[q].z * sc, BF16, h[2], l[2]);
-      split16(y[q].w * sc, BF16, h[3], l[3]);
-      h2[m] = make_uint2(h[0] | ((uint32_t)h[1] << 16), h[2] | ((uint32_t)h[3] << 16));
-      if (Wl) l2[m] = make_uint2(l[0] | ((uint32_t)l[1] << 16), l[2] | ((uint32_t)l[3] << 16));
+  for (int c = blockIdx.x; c < kpad; c += gridDim.x) {  // block-uniform
+    const int i = icol[c];
+    if (i < 0) {
+      if (tid == 0) {
+        d[c] = 0.0;
+        sinv[c] = 1.f;
+      }
+      continue;
     }
-  }
-  if (tid == 0) {
-    d[c] = f2_value(tot);
-    sinv[c] = 1.f / sc;
+    const float4* a4 = reinterpret_cast<const float4*>(Drow + (int64_t)i * ld);
+    const float4* z4 = reinterpret_cast<const float4*>(Z + (int64_t)c * ld);
+    const float4* b4 = Zbase ? reinterpret_cast<const float4*>(Zbase + (int64_t)c * ld) : nullptr;
+    float4 y[VPT];
+    float s = 0.f, comp = 0.f, mx = 0.f;
+#pragma unroll
+    for (int q = 0; q < VPT; ++q) {
+      const int m = tid + q * blockDim.x;
+      y[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (m < n4) {
+        const float4 x = __ldg(a4 + m);
+        y[q] = __ldg(z4 + m);
+        const float y0 = x.x * y[q].x + x.y * y[q].y + x.z * y[q].z + x.w * y[q].w;
+        const float yy = y0 - comp;
+        const float t = s + yy;
+        comp = (t - s) - yy;
+        s = t;
+        subtract_base(y[q], b4, m, i);
+        mx = fmaxf(mx, fmaxf(fmaxf(fabsf(y[q].x), fabsf(y[q].y)),
+                             fmaxf(fabsf(y[q].z), fabsf(y[q].w))));
+      }
+    }
+    // d_c: the lanes' compensated sums (s - comp) reduced as FP32 pairs, the
+    // warps' pairs by warp 0
+    const F2 ws = warp_sum(F2{s, -comp});
+    const float wm = warp_max(mx);
+    if (lane == 0) {
+      rs[wid] = ws;
+      rm[wid] = wm;
+    }
+    __syncthreads();
+    float cmax = 0.f;
+    for (int w = 0; w < nw; ++w) cmax = fmaxf(cmax, rm[w]);
+    F2 tot{0.f, 0.f};
+    if (wid == 0) tot = warp_sum(lane < nw ? rs[lane] : F2{0.f, 0.f});
+    __syncthreads();  // rs / rm are reused by the next column
+    const float sc = pow2_scale(cmax);
+    uint2* h2 = reinterpret_cast<uint2*>(Wh + (int64_t)c * ld);
+    uint2* l2 = reinterpret_cast<uint2*>(Wl + (int64_t)c * ld);
+#pragma unroll
+    for (int q = 0; q < VPT; ++q) {
+      const int m = tid + q * blockDim.x;
+      if (m < n4) {
+        uint16_t h[4], l[4];
+        split16(y[q].x * sc, BF16, h[0], l[0]);
+        split16(y[q].y * sc, BF16, h[1], l[1]);
+        split16(y[q].z * sc, BF16, h[2], l[2]);
+        split16(y[q].w * sc, BF16, h[3], l[3]);
+        h2[m] = make_uint2(h[0] | ((uint32_t)h[1] << 16), h[2] | ((uint32_t)h[3] << 16));
+        if (Wl) l2[m] = make_uint2(l[0] | ((uint32_t)l[1] << 16), l[2] | ((uint32_t)l[3] << 16));
+      }
+    }
+    if (tid == 0) {
+      d[c] = f2_value(tot);
+      sinv[c] = 1.f / sc;
+    }
   }
 }
 
@@ -875,12 +883,23 @@ void launch_prepass_tc(const float* Drow, const float* Z, const float* Zbase, in
   if (n4 <= (int64_t)VPT * 1024) {
     int threads = (int)((n4 + VPT - 1) / VPT);
     threads = ((threads + 31) / 32) * 32;
+    // persistent: 2048 threads' worth of CTAs per SM at most, none idle
+    static int nsm = 0;
+    if (nsm <= 0) {
+      int dev = 0;
+      cudaGetDevice(&dev);
+      if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+          nsm <= 0)
+        nsm = 148;
+    }
+    const int per_sm = std::max(1, 2048 / threads);
+    const int blocks = std::min(kpad, nsm * per_sm);
     if (bf16)
-      launch_pdl(k_prepass_tc_reg<true, VPT>, dim3(kpad), dim3(threads), 0, s, Drow, Z, Zbase,
-                 ld, icol, d, Wh, Wl, sinv, (const DevState*)st, dz);
+      launch_pdl(k_prepass_tc_reg<true, VPT>, dim3(blocks), dim3(threads), 0, s, Drow, Z, Zbase,
+                 ld, icol, kpad, d, Wh, Wl, sinv, (const DevState*)st, dz);
     else
-      launch_pdl(k_prepass_tc_reg<false, VPT>, dim3(kpad), dim3(threads), 0, s, Drow, Z, Zbase,
-                 ld, icol, d, Wh, Wl, sinv, (const DevState*)st, dz);
+      launch_pdl(k_prepass_tc_reg<false, VPT>, dim3(blocks), dim3(threads), 0, s, Drow, Z,
+                 Zbase, ld, icol, kpad, d, Wh, Wl, sinv, (const DevState*)st, dz);
     return;
   }
   unsigned g = (unsigned)((kpad + 7) / 8);
