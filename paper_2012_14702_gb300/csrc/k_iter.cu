@@ -518,12 +518,18 @@ __global__ void __launch_bounds__(256)
 // entry.  Grid (column c, row block); each thread maps MF_RPT groups of 4
 // consecutive rows with 16-byte loads and stores.  A zero gap is collected
 // per thread and flagged once per warp.
+// Two groups per thread and five CTAs per SM (at most 51 registers): 121 us
+// against 162 us for four groups at one CTA per SM's register budget (ncu,
+// n = 8192, same box); the kernel is bound by the latency of its loads.
 #ifndef IPT_MAPFIRST_RPT
-#define IPT_MAPFIRST_RPT 4
+#define IPT_MAPFIRST_RPT 2
 #endif
 constexpr int MF_RPT = IPT_MAPFIRST_RPT;
+#ifndef IPT_MAPFIRST_MINB
+#define IPT_MAPFIRST_MINB 5
+#endif
 
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, IPT_MAPFIRST_MINB)
     k_map_first(MapArgs<float> a, double* __restrict__ d, float* __restrict__ part) {
   if (a.st->done) return;
   const int c = blockIdx.x;
