@@ -53,6 +53,8 @@ struct ipt_handle {
   Buf smp;                          // sampled product entries (error estimate)
   float* host_f = nullptr;          // host entry point: the next tensor-core epilogue also
   int64_t host_ld = 0;              // stores F here (device address of the host output)
+  float* out_z = nullptr;           // device entry point: the caller's Z, stored by the
+  int64_t out_ld = 0;               // epilogue the controller picks (DevState::write_out)
   Buf wh2, wl2, dpart;              // staged Picard: the second W set and the partial sums
                                     // of d, both written by the product's epilogue
   Buf acx_d, acx_acc, acx_sigma;    // ACX: d of the inner evaluations, step-length sums, steps
@@ -270,6 +272,7 @@ ipt_status setup_dense(ipt_handle* h, const Plan& p, const void* M, int64_t ldm,
     init.rebase = fe.rebase;
     init.accurate = fe.accurate;
     init.base = -1;
+    init.out_iter = -1;
     CK(cudaMemcpyAsync(st, h->hinit, kStateHead, cudaMemcpyHostToDevice, s));
   }
   CK(cudaMemsetAsync(h->count.p, 0, (size_t)p.npad * 4, s));
@@ -522,6 +525,8 @@ ipt_status evaluate_dyn(ipt_handle* h, const Plan& p, Timing* tm, cudaEvent_t* e
   set_sampling(h, p, a, true);  // stored only when the state asks for a sample
   a.host_f = h->host_f;
   a.host_ld = h->host_ld;
+  a.out_z = h->out_z;
+  a.out_ld = h->out_ld;
   // the pass count given here only sizes nothing: the kernel reads it from st
   CK(launch_gemm_tc((const uint16_t*)h->dh.p, (const uint16_t*)h->dl.p,
                     (const uint16_t*)h->wh.p, (const uint16_t*)h->wl.p, a, p.npad, p.kpad, 1,
@@ -965,6 +970,7 @@ ipt_status solve_dense(ipt_handle* h, int64_t n, const void* M, int64_t ldm, int
                                 : opt.precision;
   Plan p = make_plan(n, k, prec, opt.staged_bf16 != 0);
   p.epi_operand = p.staged && p.tc && opt.epilogue_operand != 0;
+  bool out_direct = false;  // the returned iterate may be stored into Z by its product
   p.product_kernel = opt.product_kernel;
   p.acx = acx || anderson;  // four iterate buffers and the per-column scratch
   p.acx_base = accel_staged;
@@ -1069,7 +1075,20 @@ ipt_status solve_dense(ipt_handle* h, int64_t n, const void* M, int64_t ldm, int
                       start);
     max_iter = 0;
   } else if (p.tc && !damped && !hz) {
-    v = dense_chunked_loop(h, p, ca, fe, max_iter, &tm);
+    // a staged Picard solve into an FP32 Z: the product that forms the
+    // predicted result stores it into Z as well (no copy after the loop then)
+    struct OutClear {
+      ipt_handle* h;
+      ~OutClear() { h->out_z = nullptr; }
+    } out_clear{h};
+    ControlArgs cc = ca;
+    if (p.staged && !p.f64 && z_dtype == IPT_DTYPE_F32) {
+      h->out_z = static_cast<float*>(Z);
+      h->out_ld = ldz;
+      cc.out_pred = 1;
+      out_direct = true;
+    }
+    v = dense_chunked_loop(h, p, cc, fe, max_iter, &tm);
     max_iter = 0;
   }
   // learned damping: history, features, alphas and the damped next iterate,
@@ -1220,7 +1239,8 @@ ipt_status solve_dense(ipt_handle* h, int64_t n, const void* M, int64_t ldm, int
     } else {
       CK(cudaStreamSynchronize(h->cs));
     }
-  } else {
+  } else if (!(out_direct && hs.out_iter >= 0 && hs.out_iter == (int)hs.iter - 2)) {
+    // (else the evaluation that formed the returned iterate stored it into Z)
     launch_copy_z(h->z[ans].p, p.f64 ? 1 : 0, p.npad, p.n, p.k, Z, ldz,
                   z_dtype == IPT_DTYPE_F64 ? 1 : 0, s);
     h->launches += 1;

@@ -75,6 +75,12 @@ struct DevState {
   float wscale;      // 1 / scale of the current operand (fused split)
   float wscale_next; // 1 / scale of the operand the epilogue is writing
   int epi_used;      // evaluations that ran on such an operand
+  // The caller's output Z (device entry point): the controller predicts that
+  // the next evaluation forms the returned iterate (write_out), its product
+  // epilogue then also stores F into Z and records its evaluation index
+  // (out_iter; -1 for none), so no copy is needed after the loop.
+  int write_out;
+  int out_iter;
   double acc_dp2;  // sum of squared product errors at the sampled entries
   double acc_dpn;  // number of sampled entries
   double e_meas;   // the last sampled estimate of ||P - Delta Z||_F (safety included)
@@ -155,6 +161,10 @@ struct MapArgs {
   // predicted to be the returned iterate, so its copy overlaps the product.
   T* host_f;
   int64_t host_ld;
+  // Device entry point: the same store into the caller's Z (column-major n x k,
+  // out_ld), made only by an evaluation whose state asks for it (dyn, write_out).
+  T* out_z;
+  int64_t out_ld;
 };
 
 // Device-chosen pre-pass operands (see MapArgs::dyn): with dyn set, Z is
@@ -238,6 +248,8 @@ struct ControlArgs {
   int escalate = 0;     // STAGED: re-base on a compensated FP32 product when the split
                         // product's base error is what keeps the residual from tol
   int pause_on_acc = 0; // STAGED, device-chosen operands: pause before such an evaluation
+  int out_pred = 0;     // STAGED, device-chosen operands: predict the evaluation that
+                        // forms the returned iterate (DevState::write_out)
   int accel_staged = 0; // accelerated staged solves: request that re-base (want_acc)
   int host_base = -2;   // host-driven evaluations: the base this one used (-1: E), or -2
                         // for the controller's own (staged Picard) base

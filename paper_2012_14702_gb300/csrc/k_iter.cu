@@ -653,6 +653,7 @@ __device__ __forceinline__ bool split_stage(int stage) {
 
 __device__ void control_step(DevState* st, const ControlArgs& a) {
   if (st->done || st->pause) return;
+  st->write_out = 0;  // set again below for the next evaluation
   const int it = st->iter;
   const double z2 = st->acc_z2;
   const double inc = sqrt(st->acc_inc2) / sqrt(z2);
@@ -812,6 +813,9 @@ __device__ void control_step(DevState* st, const ControlArgs& a) {
       // None (vb = 0) when the next evaluation is predicted to stop the solve.
       const bool likely_last = st->accurate && rho * q <= 0.5 * a.tol;
       st->vb = likely_last ? 0.0 : (st->rebase ? 0.0 : sv_next) + inc * sqrt(z2);
+      // the next evaluation forms the returned iterate when the test after it
+      // passes (and its own does not): it also stores F into the caller's Z
+      st->write_out = a.out_pred && a.test && !(rho * q <= a.tol) && rho * q * q <= a.tol;
       // slow contraction: hand the solve over to the requested acceleration
       if (a.slow_ratio > 0.0 && a.test && it >= 2 && prev > 0.0 && rho > a.slow_ratio * prev)
         st->pause = 2;

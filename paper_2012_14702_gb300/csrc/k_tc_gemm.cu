@@ -327,6 +327,15 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       }
     }
   }
+  // second store of F: the host output, or (device-chosen evaluations) the
+  // caller's Z when the state predicts this evaluation forms the result
+  float* oz = a.host_f;
+  int64_t oz_ld = a.host_ld;
+  if (!oz && a.dyn && a.out_z && a.st->write_out) {
+    oz = a.out_z;
+    oz_ld = a.out_ld;
+    if (blockIdx.x == 0 && threadIdx.x == 0) a.st->out_iter = a.st->iter;
+  }
   const CUtensorMap* tmBh = wset ? &tmWh1 : &tmWh;
   const CUtensorMap* tmBl = wset ? &tmWl1 : &tmWl;
   extern __shared__ uint8_t smem_raw[];
@@ -643,8 +652,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
               if (gap == 0.f && j != ic) flag_degenerate(a.st);
               map_entry<float>(z[i], p, ci.d, gap, j == ic, f, r);
               __stcs(Fout + o, f);
-              if (a.host_f && cbase + c0 + i < a.k)
-                __stcs(a.host_f + (int64_t)(cbase + c0 + i) * a.host_ld + j, f);
+              if (oz) __stcs(oz + (int64_t)(cbase + c0 + i) * oz_ld + j, f);
               const float df = f - z[i];
               s_inc = fmaf(df, df, s_inc);
               s_z = fmaf(z[i], z[i], s_z);

@@ -251,6 +251,7 @@ def test_divergence_and_cycle_statuses(ipt):
 
 @pytest.mark.parametrize("precision,z_dtype,max_iter,status", [
     ("staged", torch.float32, 50, "OK"),      # the returned iterate written by the epilogue
+    ("staged", torch.float32, 4, "MAXITER"),  # ... predicted, but the cap ends the solve first
     ("staged", torch.float64, 50, "OK"),      # through a device conversion
     ("f32", torch.float32, 2, "MAXITER"),     # the last tested iterate
     ("fp16x3", torch.float32, 1, "MAXITER"),  # Z = E
