@@ -81,6 +81,11 @@ struct DevState {
   // (out_iter; -1 for none), so no copy is needed after the loop.
   int write_out;
   int out_iter;
+  // The operand the next epilogue writes carries its lo part only when the
+  // evaluation that reads it is predicted to run the split (3-pass) product
+  // (write_lo); fused_lo records what that epilogue wrote.
+  int write_lo;
+  int fused_lo;
   double acc_dp2;  // sum of squared product errors at the sampled entries
   double acc_dpn;  // number of sampled entries
   double e_meas;   // the last sampled estimate of ||P - Delta Z||_F (safety included)

@@ -813,6 +813,12 @@ __device__ void control_step(DevState* st, const ControlArgs& a) {
       // None (vb = 0) when the next evaluation is predicted to stop the solve.
       const bool likely_last = st->accurate && rho * q <= 0.5 * a.tol;
       st->vb = likely_last ? 0.0 : (st->rebase ? 0.0 : sv_next) + inc * sqrt(z2);
+      // the pass count of the evaluation after the next one, predicted the same
+      // way one contraction step further: the next epilogue writes the lo part
+      // of the operand it forms only for a split product
+      const double sv2 = (st->rebase ? 0.0 : sv_next) + a.step_scale * inc * q * sqrt(z2);
+      const double need2 = fmax(a.stage_switch * rho * q * q, 0.1 * a.tol);
+      st->write_lo = !(a.u_low * kappa * sv2 / rr <= need2);
       // the next evaluation forms the returned iterate when the test after it
       // passes (and its own does not): it also stores F into the caller's Z
       st->write_out = a.out_pred && a.test && !(rho * q <= a.tol) && rho * q * q <= a.tol;
@@ -850,7 +856,7 @@ __device__ void control_step(DevState* st, const ControlArgs& a) {
   // sets them (cur = F; base = this iterate after a re-base, else unchanged)
   const bool fused_ok = st->fused && !st->split_bad && !st->done && !st->pause &&
                         a.mode == IPT_PREC_STAGED && !a.acx && st->stage != IPT_PREC_F32 &&
-                        st->stage != IPT_PREC_F32C;
+                        st->stage != IPT_PREC_F32C && (st->passes != 3 || st->fused_lo);
   if (fused_ok) {
     st->wsel ^= 1;
     st->wscale = st->wscale_next;

@@ -316,13 +316,15 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     wset = a.st->wsel & 1;
     const double vb = a.st->vb;
     if (a.fuse && vb > 0.0 && vb < 1e30) {
+      const int write_lo = a.st->write_lo;  // the lo part only for a split product
       wn_h = a.wnh[wset ^ 1];
-      wn_l = a.wnl[wset ^ 1];
+      wn_l = write_lo ? a.wnl[wset ^ 1] : nullptr;
       zb_is_z = a.st->rebase != 0;
       zb_next = zb_is_z ? Zin : (base >= 0 ? a.zsel[base] : nullptr);
       sc_next = pow2_scale((float)vb);
       if (blockIdx.x == 0 && threadIdx.x == 0) {
         a.st->fused = 1;
+        a.st->fused_lo = write_lo;
         a.st->wscale_next = 1.f / sc_next;
       }
     }
@@ -666,7 +668,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
               uint16_t hh, ll;
               split16(x, a.fuse_bf16 != 0, hh, ll);
               __stcs(reinterpret_cast<unsigned short*>(wn_h) + o, (unsigned short)hh);
-              __stcs(reinterpret_cast<unsigned short*>(wn_l) + o, (unsigned short)ll);
+              if (wn_l) __stcs(reinterpret_cast<unsigned short*>(wn_l) + o, (unsigned short)ll);
               split_bad |= !(fabsf(x) <= split_max);
               dl[i] = ok ? dl[i] * f : 0.f;
             }
